@@ -1,0 +1,190 @@
+"""ctypes front end of the FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
+this package.  It never touches the CUDA library; the CUDA library never
+touches it.  Problems come from workloads/ (seeded inputs shared by both).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ORA_MAXSPEC = 4
+_RIEMANN = {"lhlld": 0, "hlld": 1, "hll": 2}
+_EOS = {"ideal": 0, "stellar": 1}
+
+_dp = C.POINTER(C.c_double)
+
+
+class OraCfg(C.Structure):
+    _fields_ = [
+        ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("bc", (C.c_int * 2) * 3), ("eos", C.c_int), ("gamma", C.c_double),
+        ("nspec", C.c_int), ("A", C.c_double * ORA_MAXSPEC), ("Z", C.c_double * ORA_MAXSPEC),
+        ("g", C.c_double * 3),
+        ("bg_rho_c", _dp), ("bg_p_c", _dp), ("bg_rho_f", _dp), ("bg_p_f", _dp),
+        ("bg_ge_c", _dp), ("bg_gc_c", _dp), ("bg_ge_f", _dp), ("bg_gc_f", _dp),
+        ("heat", _dp), ("cfl", C.c_double), ("rk", C.c_int), ("riemann", C.c_int),
+        ("eps_sf", C.c_double), ("mach_thr", C.c_double), ("newton_tol", C.c_double),
+        ("newton_maxit", C.c_int), ("eos_table", C.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.ora_run.restype = C.c_int
+        L.ora_run.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp, _dp, _dp, C.c_int, C.c_double, _dp, _dp]
+        L.ora_dt.restype = C.c_double
+        L.ora_dt.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp, _dp, _dp]
+        L.ora_stage.restype = C.c_int
+        L.ora_stage.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                C.c_double, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
+        L.ora_riemann.restype = None
+        L.ora_riemann.argtypes = [_dp, _dp, C.c_double, C.c_int, C.c_int, C.c_double, _dp]
+        L.ora_divb.restype = C.c_double
+        L.ora_divb.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp]
+        L.ora_mlp_forward.restype = None
+        L.ora_mlp_forward.argtypes = [_dp, C.c_int, C.c_int, _dp, C.c_long, _dp]
+        L.ora_mlp_loss_grad.restype = C.c_double
+        L.ora_mlp_loss_grad.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp, C.c_long, _dp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+class Oracle:
+    """Holds a problem's configuration (and keeps its arrays alive)."""
+
+    def __init__(self, pr, rk: int = 3, riemann: str | None = None, eps_sf: float | None = None,
+                 cfl: float | None = None, wb: bool = True, newton_tol: float = 1e-11,
+                 newton_maxit: int = 50, eos_table=None, mach_thr: float | None = None):
+        self.pr = pr
+        c = OraCfg()
+        for d in range(3):
+            c.n[d] = pr.n[d]
+            c.lo[d] = pr.lo[d]
+            c.hi[d] = pr.hi[d]
+            c.bc[d][0], c.bc[d][1] = pr.bc[d]
+            c.g[d] = pr.g[d]
+        c.eos = _EOS[pr.eos]
+        c.gamma = pr.gamma
+        c.nspec = pr.nspec
+        for l, (a, z) in enumerate(zip(pr.meta.get("A", []), pr.meta.get("Z", []))):
+            c.A[l], c.Z[l] = a, z
+        self._keep = []
+        if pr.bg is not None and wb:
+            for key in ("rho_c", "p_c", "rho_f", "p_f", "ge_c", "gc_c", "ge_f", "gc_f"):
+                if key in pr.bg:
+                    arr = np.ascontiguousarray(pr.bg[key], dtype=np.float64)
+                    self._keep.append(arr)
+                    setattr(c, "bg_" + key, _ptr(arr))
+        if pr.heat is not None:
+            h = np.ascontiguousarray(pr.heat, dtype=np.float64)
+            self._keep.append(h)
+            c.heat = _ptr(h)
+        c.cfl = pr.cfl if cfl is None else cfl
+        c.rk = rk
+        c.riemann = _RIEMANN[riemann or pr.riemann]
+        c.eps_sf = pr.eps_sf if eps_sf is None else eps_sf
+        c.mach_thr = pr.mach_thr if mach_thr is None else mach_thr
+        c.newton_tol = newton_tol
+        c.newton_maxit = newton_maxit
+        c.eos_table = eos_table
+        self.cfg = c
+
+    # ------------------------------------------------------------------
+    def run(self, nsteps, state=None, dt_fixed=0.0):
+        """Advance nsteps; returns (state dict, t, dt_last).  Input state untouched."""
+        pr = self.pr
+        st = state or dict(cons=pr.cons, bx=pr.bx, by=pr.by, bz=pr.bz, T=pr.T)
+        cons = np.ascontiguousarray(st["cons"], dtype=np.float64).copy()
+        bx = np.ascontiguousarray(st["bx"], dtype=np.float64).copy()
+        by = np.ascontiguousarray(st["by"], dtype=np.float64).copy()
+        bz = np.ascontiguousarray(st["bz"], dtype=np.float64).copy()
+        T = None if st.get("T") is None else np.ascontiguousarray(st["T"], dtype=np.float64).copy()
+        t = C.c_double(0.0)
+        dtl = C.c_double(0.0)
+        rc = lib().ora_run(C.byref(self.cfg), _ptr(cons), _ptr(bx), _ptr(by), _ptr(bz), _ptr(T),
+                           int(nsteps), float(dt_fixed), C.byref(t), C.byref(dtl))
+        if rc != 0:
+            raise RuntimeError(f"oracle run failed with code {rc}")
+        return dict(cons=cons, bx=bx, by=by, bz=bz, T=T), t.value, dtl.value
+
+    def run_to(self, t_end, state=None, max_steps=10 ** 7):
+        """Advance to exactly t_end (last step shortened)."""
+        st = state or dict(cons=self.pr.cons, bx=self.pr.bx, by=self.pr.by, bz=self.pr.bz, T=self.pr.T)
+        t = 0.0
+        steps = 0
+        while t < t_end * (1 - 1e-14) and steps < max_steps:
+            dt = self.dt(st)
+            if t + dt > t_end:
+                dt = t_end - t
+            st, _, _ = self.run(1, st, dt_fixed=dt)
+            t += dt
+            steps += 1
+        return st, t, steps
+
+    def dt(self, state=None):
+        pr = self.pr
+        st = state or dict(cons=pr.cons, bx=pr.bx, by=pr.by, bz=pr.bz, T=pr.T)
+        T = None if st.get("T") is None else np.ascontiguousarray(st["T"]).copy()
+        return lib().ora_dt(C.byref(self.cfg), _ptr(np.ascontiguousarray(st["cons"])),
+                            _ptr(np.ascontiguousarray(st["bx"])), _ptr(np.ascontiguousarray(st["by"])),
+                            _ptr(np.ascontiguousarray(st["bz"])), _ptr(T))
+
+    def divb(self, state):
+        return lib().ora_divb(C.byref(self.cfg), _ptr(np.ascontiguousarray(state["bx"])),
+                              _ptr(np.ascontiguousarray(state["by"])), _ptr(np.ascontiguousarray(state["bz"])))
+
+    def stage(self, state_in, state_base, a, b, dt):
+        cons_o = np.empty_like(state_in["cons"])
+        bo = [np.empty_like(state_in[k]) for k in ("bx", "by", "bz")]
+        T = None if state_in.get("T") is None else np.ascontiguousarray(state_in["T"]).copy()
+        rc = lib().ora_stage(C.byref(self.cfg), *[_ptr(np.ascontiguousarray(state_in[k])) for k in ("cons", "bx", "by", "bz")],
+                             _ptr(T), *[_ptr(np.ascontiguousarray(state_base[k])) for k in ("cons", "bx", "by", "bz")],
+                             a, b, dt, _ptr(cons_o), *[_ptr(x) for x in bo])
+        if rc != 0:
+            raise RuntimeError(f"oracle stage failed with code {rc}")
+        return dict(cons=cons_o, bx=bo[0], by=bo[1], bz=bo[2], T=T)
+
+
+def riemann(wl, wr, bn, solver="lhlld", mach_thr=0.6, nspec=0):
+    """Single-face flux in the normal frame (see oracle.h)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    f = np.zeros(7 + nspec)
+    lib().ora_riemann(_ptr(wl), _ptr(wr), float(bn), int(nspec), _RIEMANN[solver], float(mach_thr), _ptr(f))
+    return f
+
+
+def mlp_forward(w, nin, nh, x):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros(x.shape[0])
+    lib().ora_mlp_forward(_ptr(w), nin, nh, _ptr(x), x.shape[0], _ptr(y))
+    return y
+
+
+def mlp_loss_grad(w, nin, nh, x, t):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    g = np.zeros_like(w)
+    loss = lib().ora_mlp_loss_grad(_ptr(w), nin, nh, _ptr(x), _ptr(t), x.shape[0], _ptr(g))
+    return loss, g

@@ -1,0 +1,115 @@
+/*
+ * oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU implementation of one explicit finite-volume MHD
+ * update of PHLEGETHON (arXiv 2604.12672, Sect. 2): primitive recovery and EOS
+ * (Sect. 2.2), deviation well-balancing (Sect. 2.8), van Leer PLM (Sect. 2.5),
+ * LHLLD / HLL Riemann fluxes (Sect. 2.6), shock flattening (Sect. 2.7),
+ * Contact-CT (Sect. 2.4), SSP-RK stages and the CFL step (Sect. 2.9).
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load
+ * it.  It shares no code, header, table or helper with the CUDA library; both
+ * consume the same seeded inputs (workloads/).  Compiled with
+ * -ffp-contract=off so that every operation rounds as written.
+ *
+ * Array layout (same as the library's ABI, x fastest, no ghosts):
+ *   cons[v][nz][ny][nx], v = rho, mx, my, mz, E, rhoX_0..;
+ *   bx[nz][ny][nx+1], by[nz][ny+1][nx], bz[nz+1][ny][nx]; T[nz][ny][nx].
+ */
+#ifndef PHL_ORACLE_H
+#define PHL_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORA_PERIODIC = 0, ORA_REFLECT = 1, ORA_OUTFLOW = 2 };
+enum { ORA_EOS_IDEAL = 0, ORA_EOS_STELLAR = 1 };
+enum { ORA_LHLLD = 0, ORA_HLLD = 1, ORA_HLL = 2 };
+#define ORA_MAXSPEC 4
+
+typedef struct {
+  int n[3];                 /* cells per dimension; a dimension with n = 1 is inactive */
+  double lo[3], hi[3];
+  int bc[3][2];             /* ORA_PERIODIC / ORA_REFLECT / ORA_OUTFLOW */
+  int eos;                  /* ORA_EOS_IDEAL or ORA_EOS_STELLAR */
+  double gamma;
+  int nspec;
+  double A[ORA_MAXSPEC], Z[ORA_MAXSPEC];
+  double g[3];              /* constant gravitational acceleration */
+  /* background along z with 3 ghost layers (NULL: no well-balancing) */
+  const double *bg_rho_c, *bg_p_c;   /* nz+6 */
+  const double *bg_rho_f, *bg_p_f;   /* nz+7 */
+  const double *bg_ge_c, *bg_gc_c, *bg_ge_f, *bg_gc_f; /* NULL: gamma */
+  const double *heat;       /* NULL or volumetric heating per z-cell [nz] */
+  double cfl;
+  int rk;                   /* 2 or 3 */
+  int riemann;              /* ORA_LHLLD / ORA_HLLD / ORA_HLL */
+  double eps_sf;            /* 0: no shock flattening */
+  double mach_thr;          /* LHLLD threshold (0.6) */
+  double newton_tol;        /* stellar EOS */
+  int newton_maxit;
+  const void *eos_table;    /* stellar EOS table (ora_eos_table_build) */
+} ora_cfg;
+
+/* Advance nsteps SSP-RK steps in place.  dt_fixed > 0 uses that step;
+ * otherwise each step's dt comes from the CFL condition on U^n.
+ * t (nullable) accumulates time; dt_last (nullable) receives the last dt.
+ * Returns 0 or a negative code (-1 bad input, -2 non-positive rho/P, -3 Newton). */
+int ora_run(const ora_cfg *cfg, double *cons, double *bx, double *by, double *bz,
+            double *T, int nsteps, double dt_fixed, double *t, double *dt_last);
+
+/* CFL time step of the state (Eq. cfl). */
+double ora_dt(const ora_cfg *cfg, const double *cons, const double *bx,
+              const double *by, const double *bz, double *T);
+
+/* One stage: out = a*base + b*(in - dt*R(in)) for cells and faces. */
+int ora_stage(const ora_cfg *cfg, const double *cons_in, const double *bx_in,
+              const double *by_in, const double *bz_in, double *T,
+              const double *cons_base, const double *bx_base, const double *by_base,
+              const double *bz_base, double a, double b, double dt,
+              double *cons_out, double *bx_out, double *by_out, double *bz_out);
+
+/* Single-face Riemann flux in the face-normal frame.
+ * wl, wr: rho, un, ut1, ut2, Bt1, Bt2, P, gamma_e, gamma_c, X_0..X_{nspec-1}
+ * f: rho, mn, mt1, mt2, E, Bt1, Bt2, rhoX_0.. */
+void ora_riemann(const double *wl, const double *wr, double bn, int nspec,
+                 int solver, double mach_thr, double *f);
+
+/* Divergence max|div B| * min(dx) over interior cells (Eq. divb). */
+double ora_divb(const ora_cfg *cfg, const double *bx, const double *by, const double *bz);
+
+/* ---------------- stellar EOS (eos.c) ---------------- */
+typedef struct ora_eos_table ora_eos_table;
+ora_eos_table *ora_eos_table_build(double lrho_lo, double lrho_hi, int nrho,
+                                   double lT_lo, double lT_hi, int nT);
+void ora_eos_table_free(ora_eos_table *t);
+int ora_eos_table_export(const ora_eos_table *t, double *out, long nout);
+long ora_eos_table_size(const ora_eos_table *t);
+
+/* Direct (quadrature) electron-positron gas at (rho*Ye, T): P, e (per gram of
+ * the mixture with Ye), free energy f = e - T s, s, eta.  Returns 0 or -1. */
+int ora_ep_direct(double rho, double ye, double T, double *P, double *e,
+                  double *s, double *eta, double *npos);
+/* Generalised Fermi-Dirac integral F_k(eta, beta). */
+double ora_fd(double k, double eta, double beta);
+
+/* Full stellar EOS (ions + radiation + e-/e+) at (rho, T, X):
+ * P, e_int, c_v, dP/drho|T, dP/dT|rho, gamma_e, gamma_c.  table NULL: direct. */
+int ora_eos_rt(const ora_cfg *cfg, double rho, double T, const double *X,
+               double *P, double *e, double *cv, double *dPdr, double *dPdT,
+               double *ge, double *gc);
+/* Newton inversion e_int -> T (Sect. 2.2); T_inout holds the guess. */
+int ora_eos_invert(const ora_cfg *cfg, double rho, double eint, const double *X,
+                   double *T_inout, double *P, double *ge, double *gc, int *iters);
+
+/* ---------------- MLP (mlp.c) ---------------- */
+void ora_mlp_forward(const double *w, int nin, int nh, const double *x, long n,
+                     double *y);
+double ora_mlp_loss_grad(const double *w, int nin, int nh, const double *x,
+                         const double *t, long n, double *grad);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

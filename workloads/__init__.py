@@ -1,0 +1,395 @@
+"""Seeded synthetic workloads for the explicit MHD stage.
+
+This module builds problem descriptions and initial data: grid sizes, boundary
+conditions, gravity, the hydrostatic background profiles, and the conserved
+state (rho, rho*u, rho*e, rho*X_l) plus the face-centred normal magnetic field.
+It is the one module that both the CUDA path's tests/benchmarks and the CPU
+oracle consume. It holds none of the scheme's arithmetic: no reconstruction, no
+Riemann flux, no constrained transport, no EOS inversion. Conserved energy is
+assembled from the primitive initial data with the definition of the total
+energy density (Sect. 2.1, below Eq. energy), using the face-average cell field.
+
+Array layout (the library's ABI layout, x fastest, no ghost cells):
+  cons[v, k, j, i]   v = rho, mx, my, mz, E, rho*X_0, ...      shape (nv, nz, ny, nx)
+  bx[k, j, i]        normal B on x-faces i-1/2, i = 0..nx          (nz, ny, nx+1)
+  by[k, j, i]        normal B on y-faces j-1/2, j = 0..ny          (nz, ny+1, nx)
+  bz[k, j, i]        normal B on z-faces k-1/2, k = 0..nz          (nz+1, ny, nx)
+Inactive dimensions have one cell; their face arrays hold 2 equal layers.
+
+Background profiles (well-balanced deviation method, Sect. 2.8) vary along z
+only and are given with 3 ghost layers on each side:
+  rho_c, p_c : cell centres k = -3 .. nz+2          (length nz+6, index k+3)
+  rho_f, p_f : z-faces k-1/2, k = -3 .. nz+3        (length nz+7, index k+3)
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+PERIODIC, REFLECT, OUTFLOW = 0, 1, 2
+NG_BG = 3  # ghost layers carried by background profiles
+
+
+@dataclasses.dataclass
+class Problem:
+    name: str
+    ndim: int
+    n: tuple                      # (nx, ny, nz)
+    lo: tuple
+    hi: tuple
+    bc: tuple                     # ((xlo, xhi), (ylo, yhi), (zlo, zhi))
+    gamma: float
+    cons: np.ndarray
+    bx: np.ndarray
+    by: np.ndarray
+    bz: np.ndarray
+    g: tuple = (0.0, 0.0, 0.0)
+    bg: Optional[dict] = None     # rho_c, p_c, rho_f, p_f (see module doc)
+    heat: Optional[np.ndarray] = None   # volumetric heating rate per z-cell (nz,)
+    cfl: float = 0.4
+    riemann: str = "lhlld"        # lhlld | hlld | hll
+    eps_sf: float = 0.2           # shock-flattening threshold; 0 switches it off
+    mach_thr: float = 0.6
+    nspec: int = 0
+    eos: str = "ideal"
+    T: Optional[np.ndarray] = None
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def nv(self) -> int:
+        return 5 + self.nspec
+
+    @property
+    def ncells(self) -> int:
+        return int(self.n[0] * self.n[1] * self.n[2])
+
+    def copy(self) -> "Problem":
+        p = dataclasses.replace(self)
+        p.cons = self.cons.copy()
+        p.bx, p.by, p.bz = self.bx.copy(), self.by.copy(), self.bz.copy()
+        p.T = None if self.T is None else self.T.copy()
+        return p
+
+    def dx(self):
+        return tuple((self.hi[d] - self.lo[d]) / self.n[d] for d in range(3))
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+
+def _centres(lo, hi, n):
+    d = (hi - lo) / n
+    return lo + (np.arange(n) + 0.5) * d
+
+
+def _faces(lo, hi, n):
+    d = (hi - lo) / n
+    return lo + np.arange(n + 1) * d
+
+
+def _assemble(name, ndim, n, lo, hi, bc, gamma, rho, vel, p, bx, by, bz, **kw):
+    """Build conserved variables from point values of the primitive fields.
+
+    rho, p and vel[3] are cell-centred arrays of shape (nz, ny, nx); the cell
+    magnetic field is the mean of the two face values (used only to form E).
+    """
+    nx, ny, nz = n
+    bcx = 0.5 * (bx[:, :, :-1] + bx[:, :, 1:])
+    bcy = 0.5 * (by[:, :-1, :] + by[:, 1:, :])
+    bcz = 0.5 * (bz[:-1, :, :] + bz[1:, :, :])
+    nspec = kw.get("nspec", 0)
+    cons = np.zeros((5 + nspec, nz, ny, nx))
+    cons[0] = rho
+    for d in range(3):
+        cons[1 + d] = rho * vel[d]
+    kin = 0.5 * rho * (vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)
+    mag = 0.5 * (bcx ** 2 + bcy ** 2 + bcz ** 2)
+    if "eint_density" in kw:
+        cons[4] = kw.pop("eint_density") + kin + mag
+    else:
+        cons[4] = p / (gamma - 1.0) + kin + mag
+    if nspec:
+        X = kw.pop("X")
+        for l in range(nspec):
+            cons[5 + l] = rho * X[l]
+    kw.pop("nspec", None)
+    return Problem(name=name, ndim=ndim, n=tuple(n), lo=tuple(lo), hi=tuple(hi),
+                   bc=tuple(tuple(b) for b in bc), gamma=gamma, cons=cons,
+                   bx=bx, by=by, bz=bz, nspec=nspec, **kw)
+
+
+def _faces_from_az(az_corner, dx, dy, nz):
+    """Face normal fields of B = curl(A_z z^) from A_z at cell corners.
+
+    az_corner[j, i] is A_z at (x_{i-1/2}, y_{j-1/2}), shape (ny+1, nx+1).
+    Discrete curl: divergence-free to round-off by construction.
+    """
+    bx2 = (az_corner[1:, :] - az_corner[:-1, :]) / dy          # (ny, nx+1)
+    by2 = -(az_corner[:, 1:] - az_corner[:, :-1]) / dx         # (ny+1, nx)
+    bx = np.repeat(bx2[None], nz, axis=0)
+    by = np.repeat(by2[None], nz, axis=0)
+    return bx, by
+
+
+# ----------------------------------------------------------------------------
+# 1D problems
+# ----------------------------------------------------------------------------
+
+def shock_tube(n, left, right, gamma, bxn=0.0, x0=0.5, name="tube", cfl=0.4, **kw):
+    """1D Riemann problem on x in [0,1]; left/right = (rho, vx, vy, vz, By, Bz, P)."""
+    x = _centres(0.0, 1.0, n)
+    sel = x < x0
+    st = np.where(sel[None, :], np.array(left)[:, None], np.array(right)[:, None])
+    rho, vx, vy, vz, byc, bzc, p = st
+    shp = (1, 1, n)
+    bx = np.full((1, 1, n + 1), float(bxn))
+    by = np.repeat(byc.reshape(shp), 2, axis=1)
+    bz = np.repeat(bzc.reshape(shp), 2, axis=0)
+    return _assemble(name, 1, (n, 1, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0),
+                     ((OUTFLOW, OUTFLOW), (PERIODIC, PERIODIC), (PERIODIC, PERIODIC)),
+                     gamma, rho.reshape(shp), [vx.reshape(shp), vy.reshape(shp), vz.reshape(shp)],
+                     p.reshape(shp), bx, by, bz, cfl=cfl, **kw)
+
+
+def sod(n, **kw):
+    """Sod tube: (rho, p) = (1, 1) | (0.125, 0.1), gamma = 1.4, B = 0."""
+    return shock_tube(n, (1.0, 0, 0, 0, 0, 0, 1.0), (0.125, 0, 0, 0, 0, 0, 0.1), 1.4,
+                      name=f"sod{n}", **kw)
+
+
+def brio_wu(n, **kw):
+    """Brio-Wu tube (Sect. 3.1): gamma = 2, Bx = 0.75, By = +1 | -1."""
+    return shock_tube(n, (1.0, 0, 0, 0, 1.0, 0, 1.0), (0.125, 0, 0, 0, -1.0, 0, 0.1), 2.0,
+                      bxn=0.75, name=f"briowu{n}", **kw)
+
+
+def alfven_1d(n, amp=1e-6, rho0=1.0, p0=0.1, b0=1.0, gamma=5.0 / 3.0, cfl=0.4):
+    """Right-going linear Alfven wave along x, periodic on [0,1]: dB_y = -sqrt(rho) dv_y."""
+    x = _centres(0.0, 1.0, n)
+    xf = _faces(0.0, 1.0, n)
+    shp = (1, 1, n)
+    vy = amp * np.sin(2 * np.pi * x)
+    rho = np.full(shp, rho0)
+    p = np.full(shp, p0)
+    bx = np.full((1, 1, n + 1), b0)
+    byc = -math.sqrt(rho0) * vy
+    by = np.repeat(byc.reshape(shp), 2, axis=1)
+    bz = np.zeros((2, 1, n))
+    pr = _assemble(f"alfven1d_{n}", 1, (n, 1, 1), (0, 0, 0), (1, 1, 1),
+                   ((PERIODIC,) * 2,) * 3, gamma, rho, [np.zeros(shp), vy.reshape(shp), np.zeros(shp)],
+                   p, bx, by, bz, cfl=cfl)
+    pr.meta.update(period=1.0 / (b0 / math.sqrt(rho0)), amp=amp, xf=xf)
+    return pr
+
+
+# ----------------------------------------------------------------------------
+# 2D problems
+# ----------------------------------------------------------------------------
+
+def orszag_tang(n, cfl=0.4, **kw):
+    """Orszag-Tang vortex on [0,1]^2, gamma = 5/3 (configuration C1)."""
+    gamma = 5.0 / 3.0
+    dx = 1.0 / n
+    x = _centres(0.0, 1.0, n)
+    X, Y = np.meshgrid(x, x, indexing="xy")          # [j, i]
+    b0 = 1.0 / math.sqrt(4 * math.pi)
+    xf = _faces(0.0, 1.0, n)
+    XF, YF = np.meshgrid(xf, xf, indexing="xy")
+    az = b0 * (np.cos(4 * np.pi * XF) / (4 * np.pi) + np.cos(2 * np.pi * YF) / (2 * np.pi))
+    bx, by = _faces_from_az(az, dx, dx, 1)
+    bz = np.zeros((2, n, n))
+    rho = np.full((1, n, n), 25.0 / (36.0 * math.pi))
+    p = np.full((1, n, n), 5.0 / (12.0 * math.pi))
+    vx = (-np.sin(2 * np.pi * Y))[None]
+    vy = (np.sin(2 * np.pi * X))[None]
+    return _assemble(f"orszag_tang{n}", 2, (n, n, 1), (0, 0, 0), (1, 1, 1),
+                     ((PERIODIC,) * 2,) * 3, gamma, rho, [vx, vy, np.zeros_like(vx)], p,
+                     bx, by, bz, cfl=cfl, **kw)
+
+
+def alfven_2d(n, amp=1e-6, cfl=0.4):
+    """Linear Alfven wave along the diagonal of the periodic unit square.
+
+    B0 = (1,1)/sqrt(2) (|B0| = 1), rho = 1, P = 0.1, gamma = 5/3; in-plane
+    perturbation along (-1,1)/sqrt(2); wavelength 1/sqrt(2), period 1/sqrt(2).
+    """
+    gamma = 5.0 / 3.0
+    dx = 1.0 / n
+    x = _centres(0.0, 1.0, n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    xf = _faces(0.0, 1.0, n)
+    XF, YF = np.meshgrid(xf, xf, indexing="xy")
+    b = 1.0 / math.sqrt(2.0)
+    az = b * (YF - XF) + amp * np.cos(2 * np.pi * (XF + YF)) / (2 * math.sqrt(2) * np.pi)
+    bx, by = _faces_from_az(az, dx, dx, 1)
+    bz = np.zeros((2, n, n))
+    ph = 2 * np.pi * (X + Y)
+    dbx = -amp / math.sqrt(2) * np.sin(ph)
+    dby = amp / math.sqrt(2) * np.sin(ph)
+    vx, vy = -dbx, -dby
+    rho = np.ones((1, n, n))
+    p = np.full((1, n, n), 0.1)
+    pr = _assemble(f"alfven2d_{n}", 2, (n, n, 1), (0, 0, 0), (1, 1, 1),
+                   ((PERIODIC,) * 2,) * 3, gamma, rho, [vx[None], vy[None], np.zeros((1, n, n))],
+                   p, bx, by, bz, cfl=cfl)
+    pr.meta.update(period=1.0 / math.sqrt(2.0), amp=amp)
+    return pr
+
+
+def balsara_vortex(n, u_tilde, beta_k, cfl=0.8, **kw):
+    """Balsara (2004) MHD vortex on (-5,5)^2 advected along the diagonal (Sect. 3.2)."""
+    gamma = 5.0 / 3.0
+    dx = 10.0 / n
+    x = _centres(-5.0, 5.0, n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    xf = _faces(-5.0, 5.0, n)
+    XF, YF = np.meshgrid(xf, xf, indexing="xy")
+    b_tilde = u_tilde * math.sqrt(beta_k)
+    az = b_tilde * np.exp(0.5 * (1.0 - (XF ** 2 + YF ** 2)))
+    bx, by = _faces_from_az(az, dx, dx, 1)
+    bz = np.zeros((2, n, n))
+    r2 = X ** 2 + Y ** 2
+    f = np.exp(0.5 * (1.0 - r2))
+    vx = -u_tilde * f * Y + u_tilde / math.sqrt(2.0)
+    vy = u_tilde * f * X + u_tilde / math.sqrt(2.0)
+    p = 1.0 + (0.5 * b_tilde ** 2 * (1.0 - r2) - 0.5 * u_tilde ** 2) * np.exp(1.0 - r2)
+    rho = np.ones((1, n, n))
+    pr = _assemble(f"balsara{n}", 2, (n, n, 1), (-5, -5, 0), (5, 5, 1),
+                   ((PERIODIC,) * 2,) * 3, gamma, rho, [vx[None], vy[None], np.zeros((1, n, n))],
+                   p[None], bx, by, bz, cfl=cfl, **kw)
+    pr.meta.update(tau=10.0 * math.sqrt(2.0) / u_tilde, b_tilde=b_tilde)
+    return pr
+
+
+# ----------------------------------------------------------------------------
+# stratified 3D boxes (configurations C2 / C4)
+# ----------------------------------------------------------------------------
+
+def polytrope_profile(z, n_poly=1.5, g0=1.0, rho_b=1.0, rho_top=0.1, ztop=1.0):
+    """Hydrostatic polytrope P = K rho^(1+1/n) under constant downward g0.
+
+    rho^(1/n)(z) = rho_b^(1/n) - g0 z / (K (n+1)); K fixed by rho(ztop) = rho_top.
+    """
+    K = g0 * ztop / ((n_poly + 1.0) * (rho_b ** (1.0 / n_poly) - rho_top ** (1.0 / n_poly)))
+    base = rho_b ** (1.0 / n_poly) - g0 * z / (K * (n_poly + 1.0))
+    rho = base ** n_poly
+    return rho, K * rho ** (1.0 + 1.0 / n_poly), K
+
+
+def background_profiles(nz, lo, hi, fn):
+    dz = (hi - lo) / nz
+    zc = lo + (np.arange(-NG_BG, nz + NG_BG) + 0.5) * dz
+    zf = lo + np.arange(-NG_BG, nz + NG_BG + 1) * dz
+    rc, pc = fn(zc)[:2]
+    rf, pf = fn(zf)[:2]
+    return dict(rho_c=np.ascontiguousarray(rc), p_c=np.ascontiguousarray(pc),
+                rho_f=np.ascontiguousarray(rf), p_f=np.ascontiguousarray(pf))
+
+
+def stratified_box(nx, ny, nz, seed=1234, amp=1e-3, beta=1e6, mach_heat=1e-3,
+                   n_poly=1.5, rho_top=0.1, cfl=0.4, gamma=5.0 / 3.0, heat=True,
+                   name=None, **kw):
+    """3D stratified low-Mach magnetoconvection box (configuration C2 shape).
+
+    Domain [0,1]^3, g = (0,0,-1), polytrope n = 1.5 with rho(0) = 1, rho(1) = 0.1,
+    isobaric density noise rho = rho_hat (1 + amp U(-1,1)) from numpy PCG64(seed),
+    uniform B_x with plasma beta 2 P_hat(1/2) / B^2 = beta, uniform heating in
+    z < 0.1 sized so (q * 0.1 / rho_b)^(1/3) = mach_heat * c_s(z=0).
+    Periodic x, y; reflecting z.
+    """
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    fn = lambda z: polytrope_profile(z, n_poly=n_poly, rho_top=rho_top)
+    bg = background_profiles(nz, 0.0, 1.0, fn)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    noise = rng.uniform(-1.0, 1.0, size=(nz, ny, nx))
+    rho_c = bg["rho_c"][NG_BG:NG_BG + nz][:, None, None]
+    p_c = bg["p_c"][NG_BG:NG_BG + nz][:, None, None]
+    rho = rho_c * (1.0 + amp * noise)
+    p = np.broadcast_to(p_c, (nz, ny, nx)).copy()
+    _, p_mid, _ = fn(np.array([0.5]))
+    b0 = math.sqrt(2.0 * float(p_mid[0]) / beta)
+    bx = np.full((nz, ny, nx + 1), b0)
+    by = np.zeros((nz, ny + 1, nx))
+    bz = np.zeros((nz + 1, ny, nx))
+    zero = np.zeros((nz, ny, nx))
+    q = None
+    if heat:
+        cs_b = math.sqrt(gamma * float(fn(np.array([0.0]))[1][0]) / 1.0)
+        qv = (mach_heat * cs_b) ** 3 * 1.0 / 0.1
+        zc = (np.arange(nz) + 0.5) / nz
+        q = np.where(zc < 0.1, qv, 0.0)
+    pr = _assemble(name or f"box{nx}x{ny}x{nz}", 3, (nx, ny, nz), lo, hi,
+                   ((PERIODIC, PERIODIC), (PERIODIC, PERIODIC), (REFLECT, REFLECT)),
+                   gamma, rho, [zero, zero, zero], p, bx, by, bz,
+                   g=(0.0, 0.0, -1.0), bg=bg, heat=q, cfl=cfl, **kw)
+    pr.meta.update(seed=seed, amp=amp, beta=beta, b0=b0)
+    return pr
+
+
+def isothermal_atmosphere(nx, nz, c2=1.0, g0=1.0, ndim=2, cfl=0.4, b0=0.0):
+    """Isothermal hydrostatic atmosphere rho = exp(-g0 z / c2), P = c2 rho, at rest.
+
+    2D (x, z-like second axis mapped to z via a 3D grid with ny = 1) would need
+    z active; here the box is (nx, 1, nz) with x periodic and z reflecting.
+    """
+    fn = lambda z: (np.exp(-g0 * z / c2), c2 * np.exp(-g0 * z / c2))
+    bg = background_profiles(nz, 0.0, 1.0, fn)
+    rho = np.broadcast_to(bg["rho_c"][NG_BG:NG_BG + nz][:, None, None], (nz, 1, nx)).copy()
+    p = c2 * rho
+    bx = np.full((nz, 1, nx + 1), b0)
+    by = np.zeros((nz, 2, nx))
+    bz = np.zeros((nz + 1, 1, nx))
+    zero = np.zeros((nz, 1, nx))
+    return _assemble(f"isothermal{nx}x{nz}", 3, (nx, 1, nz), (0, 0, 0), (1, 1, 1),
+                     ((PERIODIC, PERIODIC), (PERIODIC, PERIODIC), (REFLECT, REFLECT)),
+                     1.4, rho, [zero, zero, zero], p, bx, by, bz,
+                     g=(0.0, 0.0, -g0), bg=bg, cfl=cfl)
+
+
+def ensemble_dims(nbox=24, seed=2024, choices=(64, 96, 128, 160, 192)):
+    """Box edge lengths of the batched ensemble (configuration C4)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [tuple(int(c) for c in rng.choice(choices, size=3)) for _ in range(nbox)]
+
+
+def ensemble(nbox=24, seed=2024, choices=(64, 96, 128, 160, 192), **kw):
+    dims = ensemble_dims(nbox, seed, choices)
+    return [stratified_box(nx, ny, nz, seed=seed + 1 + b, name=f"ens{b}_{nx}x{ny}x{nz}", **kw)
+            for b, (nx, ny, nz) in enumerate(dims)]
+
+
+def permute_axes(pr: Problem, perm) -> Problem:
+    """Relabel the axes of a problem: new axis d is old axis perm[d].
+
+    Used by invariance tests: a problem run along x, y or z must give the same
+    (relabelled) result.  Backgrounds are only supported along z, so this is
+    for problems without a background.
+    """
+    assert pr.bg is None and pr.heat is None
+    inv = [perm.index(d) for d in range(3)]
+    n = tuple(pr.n[perm[d]] for d in range(3))
+    # array axis order is (z, y, x) = reversed dims
+    def tr(a):
+        # a has axes (z, y, x) -> old dims (2,1,0); new axes (z', y', x') = old (perm[2], perm[1], perm[0])
+        return np.ascontiguousarray(np.transpose(a, [2 - perm[2], 2 - perm[1], 2 - perm[0]]))
+    cons = np.empty((pr.nv,) + (n[2], n[1], n[0]))
+    cons[0] = tr(pr.cons[0])
+    cons[4:] = [tr(c) for c in pr.cons[4:]]
+    for d in range(3):
+        cons[1 + d] = tr(pr.cons[1 + perm[d]])
+    faces_old = [pr.bx, pr.by, pr.bz]
+    faces = [tr(faces_old[perm[d]]) for d in range(3)]
+    q = dataclasses.replace(pr)
+    q.n = n
+    q.lo = tuple(pr.lo[perm[d]] for d in range(3))
+    q.hi = tuple(pr.hi[perm[d]] for d in range(3))
+    q.bc = tuple(pr.bc[perm[d]] for d in range(3))
+    q.g = tuple(pr.g[perm[d]] for d in range(3))
+    q.cons, q.bx, q.by, q.bz = cons, faces[0], faces[1], faces[2]
+    q.ndim = 3 if min(n) > 1 else pr.ndim
+    q.meta = dict(pr.meta, perm=tuple(perm), inv=tuple(inv))
+    return q
