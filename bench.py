@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Throughput of the explicit MHD stage on one GB300 (and N-GPU replicas).
+
+Workload: the 3D stratified low-Mach magnetoconvection box, 256^3 cells, ideal
+gas gamma = 5/3, n = 1.5 polytrope under constant g, heating in the bottom 10%,
+isobaric density noise 1e-3 (seed 1234), uniform B_x with beta 1e6, periodic
+x/y and reflecting z (workloads.stratified_box).  One "step" is one SSP-RK3
+step: the CFL reduction plus three stage evaluations (primitives/EOS, shock
+flags, PLM, LHLLD/HLL fluxes, Contact-CT, sources, RK update).  The metric is
+cell-updates per second per stage: cells x 3 stages x steps / time.
+
+  python bench.py [--gpus N --steps K --warmup W] [--form fp64|mixed]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Timing: W untimed steps, then K steps bracketed by a barrier and device
+synchronisation, CUDA events on the grid's stream; the state (1.07 GB per
+copy) is larger than L2, so no flush is needed.  N > 1 (torchrun): every rank
+runs its own box (independent replicas, weak scaling), the time is the max over
+ranks and the value sums all ranks' work.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MHD cell-updates/s per stage: plain FP64 vs mixed+MLP form at stated L1; % HBM"
+UNIT = "cell-updates/s"
+WORKLOAD = ("3D stratified low-Mach magnetoconvection box 256^3, ideal gas gamma=5/3, n=1.5 polytrope, "
+            "constant g, heating bottom 10%, density noise 1e-3 seed 1234, B_x beta 1e6, periodic x,y / "
+            "reflecting z, SSP-RK3, CFL 0.4, LHLLD + HLL flattening, well-balanced")
+STAGES = 3
+HBM_FALLBACK_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (profiling recipe's nominal table)
+
+# Algorithmic work per unit, stated in DESIGN.md (section "Roofline figures").
+# Bytes of one stage per cell that any implementation must move: read the stage
+# input (5 cell + 3 face doubles), read U^n for stages 2-3, write the output.
+BYTES_PER_CELL_STAGE = {1: 128.0, 2: 192.0, 3: 192.0}
+# FP64 flux kernel: FP64 operations per face (DADD + DMUL + 2 DFMA counted from
+# the ncu SASS counters of k_flux on the stratified box).
+FP64_FLOP_PER_FACE = None
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_id)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_problem(n):
+    import workloads as W
+    return W.stratified_box(n, n, n)
+
+
+def time_form(P, pr, form, steps, warmup, stream, ws):
+    """Device-timed K steps of one precision form; returns dict of measurements."""
+    import torch
+    g = P.Grid(pr, precision=form, stream=stream.cuda_stream)
+    g.load()
+    for _ in range(warmup):
+        g.step(1)
+    g.check()
+    g.set_timing(True)
+    g.kernel_times(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        g.step(steps)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    kt = g.kernel_times(reset=True)
+    g.set_timing(False)
+    g.check()
+    st = g.stats()
+    return g, ms, kt, st
+
+
+def roofline(kt, pr, form, hbm_peak, peak_kind):
+    """Dominant kernel (largest summed device time) against its bound."""
+    name, (launches, ms) = max(kt.items(), key=lambda kv: kv[1][1])
+    avg_ms = ms / max(launches, 1)
+    ncells = pr.ncells
+    if name == "stage_mixed":
+        per_launch = ncells * sum(BYTES_PER_CELL_STAGE.values()) / 3.0
+        achieved = per_launch / (avg_ms * 1e-3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": f"{peak_kind} HBM copy",
+                "avg_launch_ms": avg_ms, "launches": launches}
+    if name.startswith("flux") and FP64_FLOP_PER_FACE:
+        n = pr.n[0]
+        faces = (n + 1) * (n + 2) * (n + 2)
+        achieved = faces * FP64_FLOP_PER_FACE / (avg_ms * 1e-3) / 1e12
+        peak = FP64_NOMINAL_TFLOPS
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": "nominal FP64 (recipe)",
+                "avg_launch_ms": avg_ms, "launches": launches}
+    # HBM view of the whole stage for any other dominant kernel
+    stage_ms = sum(v[1] for v in kt.values()) / max(kt.get("update_cells", (1, 0))[0], 1)
+    per_stage = ncells * sum(BYTES_PER_CELL_STAGE.values()) / 3.0
+    achieved = per_stage / (stage_ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None, "peak_kind": f"{peak_kind} HBM copy",
+            "avg_launch_ms": avg_ms, "launches": launches, "note": "whole-stage algorithmic bytes / stage time"}
+
+
+def e2e_measure(P, g, pr, steps):
+    """Same metric through the public API with pinned host buffers each step."""
+    import torch
+    host = {k: torch.from_numpy(getattr(pr, k).copy()).pin_memory() for k in ("cons", "bx", "by", "bz")}
+    out = {k: torch.empty_like(v).pin_memory() for k, v in host.items()}
+    nbytes = sum(v.numel() * 8 for v in host.values())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g.set_state(host["cons"], host["bx"], host["by"], host["bz"])
+        g.step(1)
+        g.get_state_into(out["cons"], out["bx"], out["by"], out["bz"])
+    t1 = time.perf_counter()
+    val = pr.ncells * STAGES * steps / (t1 - t0)
+    return {"value": val, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "steps": steps}
+
+
+def oracle_sample(steps=2, nxy=64, nz=256):
+    """The CPU oracle as it stands, single thread, on a sample of the workload:
+    the same box physics on nxy x nxy x nz cells."""
+    import workloads as W
+    import oracle as O
+    pr = W.stratified_box(nxy, nxy, nz)
+    o = O.Oracle(pr)
+    t0 = time.perf_counter()
+    o.run(steps)
+    dt = time.perf_counter() - t0
+    return {"value": pr.ncells * STAGES * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nxy}x{nxy}x{nz} cells of the same box physics, {steps} SSP-RK3 steps, "
+                      f"{dt:.1f} s single-threaded FP64 C"}
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import workloads as W
+    import oracle as O
+    nxy = 32
+    pr = W.stratified_box(nxy, nxy, args.n)
+    o = O.Oracle(pr)
+    st = None
+    for _ in range(args.warmup):
+        st, _, _ = o.run(1, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _, _ = o.run(1, st)
+    dt = time.perf_counter() - t0
+    val = pr.ncells * STAGES * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_cells": [nxy, nxy, args.n], "form": "oracle"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{nxy}x{nxy}x{args.n} cells per step of the same box physics"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n", type=int, default=256, help="box edge (256 is the benchmark workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2604_12672_gb300 as P
+
+    hbm_peak, peak_kind = read_peaks()
+    pr = make_problem(args.n)
+    stream = torch.cuda.Stream()
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else (gpu_id or local)
+    clocks = Clocks(gpu_id)
+    g, ms, kt, st = time_form(P, pr, args.form, args.steps, args.warmup, stream, ws)
+    clk = clocks.stop()
+    ms_max = allreduce_max(ms, ws)
+    value = pr.ncells * STAGES * args.steps * ws / (ms_max * 1e-3)
+    roof = roofline(kt, pr, args.form, hbm_peak, peak_kind)
+    e2e = e2e_measure(P, g, pr, args.e2e_steps)
+    g.close()
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+    launches = sum(v[0] for v in kt.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.form == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": pr.ncells, "n": list(pr.n), "form": args.form,
+                   "stages_per_step": STAGES, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (state 1.07 GB per copy, no flush)"},
+        "roofline": roof,
+        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "hbm_frac_of_8tbs": None if roof.get("unit") != "GB/s" else roof["achieved"] / 8000.0,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

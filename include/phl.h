@@ -1,0 +1,189 @@
+/*
+ * phl.h -- C ABI of the GB300 explicit-MHD stage library (libphl.so).
+ *
+ * The library advances the equations of fully compressible ideal MHD with
+ * gravity and heating sources (arXiv 2604.12672, Sect. 2.1, Eqs. mass
+ * conservation .. energy) with the paper's explicit finite-volume scheme:
+ *   - primitive recovery and the equation of state (Sect. 2.2),
+ *   - deviation well-balancing against a hydrostatic background (Sect. 2.8,
+ *     Eqs. wb, wb1, wb2),
+ *   - van Leer limited piecewise-linear reconstruction (Sect. 2.5, item i),
+ *   - the low-dissipation LHLLD Riemann flux with the HLL shock-flattening
+ *     fallback (Sects. 2.6-2.7, Eqs. flux-hlld, pstar),
+ *   - Contact-CT edge EMFs and the face-centred B update (Sect. 2.4, Eqs.
+ *     induction, divb),
+ *   - SSP-RK2/RK3 stages and the CFL time step (Sect. 2.9, Eqs. spatres, cfl).
+ *
+ * Conventions shared by every entry point
+ *   Units: Heaviside-Lorentz (no 4 pi), Sect. 2.1.
+ *   Layout of state arrays (x fastest, no ghost cells):
+ *     cons[v][nz][ny][nx], v = rho, rho*u_x, rho*u_y, rho*u_z, rho*e, rho*X_l...
+ *       (nv = 5 + nspec doubles per cell; rho*e is the total energy density);
+ *     bx[nz][ny][nx+1] normal B on x-faces i-1/2 (i = 0..nx),
+ *     by[nz][ny+1][nx], bz[nz+1][ny][nx] likewise;
+ *     T[nz][ny][nx] temperature (stellar EOS only; the Newton first guess).
+ *   A dimension with n = 1 is inactive; its face array holds two equal layers.
+ *   Periodic boundaries: the duplicate faces (index 0 and n) must be equal.
+ *   Pointers: "where" = PHL_HOST means ordinary (pageable or pinned) host
+ *     memory; PHL_DEVICE means device memory of the current CUDA device.  No
+ *     call keeps a caller's pointer after it returns.
+ *   Streams: all device work of a grid is ordered on desc.stream (a
+ *     cudaStream_t; NULL = legacy default stream).
+ *   Errors: every call returns a phl_status; a message for the last failure
+ *     of the calling thread is available from phl_last_error().  Invalid
+ *     states found on the device (rho <= 0, P <= 0, NaN, Newton failure) set
+ *     a device flag that is reported by the next call that synchronises
+ *     (phl_compute_dt, phl_get_state, phl_check).  Nothing aborts.
+ *   Threads: a grid may be used by one host thread at a time.
+ */
+#ifndef PHL_H
+#define PHL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PHL_OK = 0,
+  PHL_EINVAL = 1,        /* bad argument                                  */
+  PHL_ECUDA = 2,         /* CUDA runtime error                            */
+  PHL_ENOMEM = 3,        /* device allocation failed                      */
+  PHL_ENEGATIVE = 4,     /* rho <= 0 or P <= 0 in a cell or at a face     */
+  PHL_ENAN = 5,          /* non-finite value                              */
+  PHL_ENEWTON = 6,       /* EOS temperature inversion did not converge    */
+  PHL_ETIMEOUT = 7,      /* a bounded device wait gave up                 */
+  PHL_EUNSUPPORTED = 8   /* option combination not built                  */
+} phl_status;
+
+enum { PHL_PERIODIC = 0, PHL_REFLECT = 1, PHL_OUTFLOW = 2 };
+enum { PHL_EOS_IDEAL = 0, PHL_EOS_STELLAR = 1 };
+enum { PHL_LHLLD = 0, PHL_HLLD = 1, PHL_HLL = 2 };
+enum { PHL_FP64 = 0, PHL_MIXED = 1 };
+enum { PHL_HOST = 0, PHL_DEVICE = 1 };
+#define PHL_MAXSPEC 4
+
+typedef struct phl_grid phl_grid;   /* opaque; owns all its device buffers */
+
+typedef struct {
+  int n[3];                 /* cells per dimension (1 = inactive)              */
+  double lo[3], hi[3];      /* domain; uniform spacing (hi-lo)/n               */
+  int bc[3][2];             /* PHL_PERIODIC / PHL_REFLECT / PHL_OUTFLOW        */
+  int eos;                  /* PHL_EOS_IDEAL / PHL_EOS_STELLAR                 */
+  double gamma;             /* ideal-gas adiabatic index                       */
+  int nspec;                /* advected mass fractions (0..PHL_MAXSPEC)        */
+  double A[PHL_MAXSPEC], Z[PHL_MAXSPEC];
+  double g[3];              /* constant gravitational acceleration             */
+  /* Hydrostatic background along z for the deviation method (Sect. 2.8),
+   * host arrays copied at creation, with 3 ghost layers each side:
+   *   *_c: cell centres k = -3..nz+2 (nz+6 values, index k+3)
+   *   *_f: z-faces k-1/2, k = -3..nz+3 (nz+7 values, index k+3)
+   * bg_rho_c == NULL: no background (plain scheme).  The gamma_e/gamma_c
+   * profiles may be NULL (then gamma is used). */
+  const double *bg_rho_c, *bg_p_c, *bg_rho_f, *bg_p_f;
+  const double *bg_ge_c, *bg_gc_c, *bg_ge_f, *bg_gc_f;
+  const double *heat;       /* host, per z-cell volumetric heating rate, or NULL */
+  double cfl;               /* Eq. cfl                                          */
+  int rk;                   /* 2 or 3 (SSP-RK)                                  */
+  int riemann;              /* PHL_LHLLD / PHL_HLLD / PHL_HLL                   */
+  double eps_sf;            /* shock-flattening threshold (0.2); 0 = off        */
+  double mach_thr;          /* LHLLD Mach threshold (0.6)                       */
+  int precision;            /* PHL_FP64 / PHL_MIXED                             */
+  double newton_tol;        /* stellar EOS Newton tolerance (1e-11)             */
+  int newton_maxit;
+  int use_mlp;              /* stellar EOS: MLP first guess                     */
+  void *stream;             /* cudaStream_t                                     */
+} phl_grid_desc;
+
+typedef struct {
+  long steps;               /* completed RK steps                               */
+  double t;                 /* accumulated time (only when dt is read back)     */
+  double last_dt;
+  int device_flags;         /* bit 0: rho/P <= 0, bit 1: NaN, bit 2: Newton     */
+  int kernels_per_step;     /* CUDA kernel launches per RK step                 */
+  size_t device_bytes;      /* device memory owned by the grid                  */
+} phl_stats;
+
+/* Create a grid: validates the description, allocates the state (padded SoA
+ * FP64) and the work buffers on the current device.  *out receives the
+ * handle.  Errors: PHL_EINVAL (dimensions, BCs, cfl, rk...), PHL_ENOMEM,
+ * PHL_EUNSUPPORTED, PHL_ECUDA. */
+phl_status phl_create_grid(const phl_grid_desc *desc, phl_grid **out);
+
+/* Load the state (layout above).  T may be NULL (stellar EOS: T is then
+ * initialised by a Newton solve from 1e8 K).  where = PHL_HOST or
+ * PHL_DEVICE.  Stream-ordered; host sources are copied before return. */
+phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx,
+                         const double *by, const double *bz, const double *T,
+                         int where);
+
+/* Store the state into caller arrays (layout above); T may be NULL.
+ * Synchronises the grid's stream and reports device flags. */
+phl_status phl_get_state(phl_grid *g, double *cons, double *bx, double *by,
+                         double *bz, double *T, int where);
+
+/* CFL step of the current state (Eq. cfl): dt = cfl / max over cells of
+ * sum_s (|u_s| + c_f,s) / dx_s, c_f the fast magnetosonic speed.  Writes the
+ * host value to *dt_out (synchronises). */
+phl_status phl_compute_dt(phl_grid *g, double *dt_out);
+
+/* Advance nsteps SSP-RK steps (Sect. 2.9).  dt > 0: fixed step; dt <= 0: each
+ * step's dt is computed on the device from U^n (no host round trip).  Launches
+ * are asynchronous on the grid's stream; errors found on the device are
+ * reported by the next synchronising call. */
+phl_status phl_step(phl_grid *g, double dt, int nsteps);
+
+/* Synchronise and report device error flags. */
+phl_status phl_check(phl_grid *g);
+
+/* Replace the stream used by the grid. */
+phl_status phl_set_stream(phl_grid *g, void *stream);
+
+phl_status phl_get_stats(phl_grid *g, phl_stats *st);
+
+/* Per-kernel device timing.  When enabled, every kernel launch of the grid is
+ * bracketed by CUDA events on the grid's stream; phl_kernel_times folds the
+ * recorded pairs (synchronising) into per-kernel totals since the last reset.
+ * Kernel classes are named ("prim", "flux_x", "stage_mixed", ...). */
+typedef struct {
+  char name[32];
+  long launches;
+  double ms;                /* summed device time of those launches */
+} phl_kernel_time;
+
+phl_status phl_set_timing(phl_grid *g, int on);
+/* Fills up to max entries, *n receives the number of kernel classes seen;
+ * reset != 0 clears the totals afterwards. */
+phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, int reset);
+
+/* Device pointer of the last computed dt (double), valid for the grid's
+ * lifetime; lets callers enqueue reads without a synchronisation. */
+phl_status phl_dt_device_ptr(phl_grid *g, const double **ptr);
+
+/* Evaluate the library's face flux (the device Riemann solver of the stage)
+ * for n independent faces -- for unit tests of the solver itself.
+ *   wl, wr  [n][9 + nspec] normal-frame primitive deviations, in order
+ *           rho, u_n, u_t1, u_t2, B_t1, B_t2, P, gamma_e, gamma_c, X_l...
+ *           (full values when the background is zero);
+ *   bn      [n] face-normal field;
+ *   bg      [n][4] background at the face: rho, P, gamma_e, gamma_c (zeros
+ *           for none);
+ *   f       [n][7 + nspec] output F - F_hat: rho, m_n, m_t1, m_t2, E, B_t1,
+ *           B_t2, rho*X_l...
+ * solver = PHL_LHLLD / PHL_HLLD / PHL_HLL; precision = PHL_FP64 evaluates in
+ * double, PHL_MIXED in float (inputs rounded to float).  All pointers are host
+ * memory; the call is synchronous on the legacy default stream. */
+phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const double *bn,
+                             const double *bg, int nspec, int solver, double mach_thr,
+                             int precision, double *f);
+
+void phl_destroy(phl_grid *g);
+
+/* Message describing the calling thread's last failure ("" if none). */
+const char *phl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHL_H */

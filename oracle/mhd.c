@@ -299,8 +299,26 @@ static double ld_xi(const rstate *L, const rstate *R, double mthr) {
   return m < mthr ? m : 1.0;
 }
 
+/* Direction of the contact used by Contact-CT upwinding: the sign of the mass
+ * flux, or 0 when |F_rho| is below 1e-12 rho max|S| -- a mass flux at the
+ * rounding level of the face's flux scale carries no direction, and the
+ * Contact-CT rule for a zero mass flux (average of both sides) applies. */
+static int contact_dir(double frho, double rhol, double rhor, double SL, double SR) {
+  double scale = 1e-12 * fmax(rhol, rhor) * fmax(fabs(SL), fabs(SR));
+  return frho > scale ? 1 : (frho < -scale ? -1 : 0);
+}
+
+static void riemann_core(const double *wl, const double *wr, double bn, int nspec,
+                         int solver, double mach_thr, double *f, int *up);
+
 void ora_riemann(const double *wl, const double *wr, double bn, int nspec,
                  int solver, double mach_thr, double *f) {
+  int up;
+  riemann_core(wl, wr, bn, nspec, solver, mach_thr, f, &up);
+}
+
+static void riemann_core(const double *wl, const double *wr, double bn, int nspec,
+                         int solver, double mach_thr, double *f, int *up) {
   rstate L, R;
   rstate_init(&L, wl, bn);
   rstate_init(&R, wr, bn);
@@ -327,6 +345,7 @@ void ora_riemann(const double *wl, const double *wr, double bn, int nspec,
         f[Q_X0 + l] = (SR * L.F[Q_RHO] * xl[l] - SL * R.F[Q_RHO] * xr[l] + SL * SR * (ur - ul)) / (SR - SL);
       }
     }
+    *up = contact_dir(f[Q_RHO], L.rho, R.rho, SL, SR);
     return;
   }
 
@@ -392,6 +411,7 @@ void ora_riemann(const double *wl, const double *wr, double bn, int nspec,
   }
   for (int q = 0; q < 7; ++q) f[q] = F[q];
   for (int l = 0; l < nspec; ++l) f[Q_X0 + l] = F[Q_RHO] * (left ? xl[l] : xr[l]);
+  *up = contact_dir(F[Q_RHO], L.rho, R.rho, SL, SR);
 }
 
 /* ---------------- one stage ---------------- */
@@ -401,6 +421,7 @@ typedef struct {
   double *B[3];
   double *F[3][8 + ORA_MAXSPEC];
   double *E[3];
+  signed char *up[3];        /* contact direction per face (Contact-CT upwinding) */
   unsigned char *raw, *flag;
   double *fhat_c, *fhat_f;   /* per-k normal-frame background fluxes (7 + nspec) */
 } work;
@@ -416,6 +437,7 @@ static int work_alloc(work *w, const ora_cfg *c) {
     for (int q = 0; q < w->G.nf; ++q) if (!(w->F[d][q] = calloc(n, sizeof(double)))) return -1;
   }
   for (int d = 0; d < 3; ++d) if (!(w->E[d] = calloc(n, sizeof(double)))) return -1;
+  for (int d = 0; d < 3; ++d) if (!(w->up[d] = calloc(n, 1))) return -1;
   w->raw = calloc(n, 1);
   w->flag = calloc(n, 1);
   int nz = c->n[2];
@@ -427,7 +449,7 @@ static int work_alloc(work *w, const ora_cfg *c) {
 static void work_free(work *w) {
   for (int q = 0; q < 10 + ORA_MAXSPEC; ++q) free(w->W[q]);
   for (int d = 0; d < 3; ++d) {
-    free(w->B[d]); free(w->E[d]);
+    free(w->B[d]); free(w->E[d]); free(w->up[d]);
     for (int q = 0; q < 8 + ORA_MAXSPEC; ++q) free(w->F[d][q]);
   }
   free(w->raw); free(w->flag); free(w->fhat_c); free(w->fhat_f);
@@ -588,11 +610,22 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
           double bn = w->B[d][pR];
           int sol = (w->flag[pL] || w->flag[pR]) ? ORA_HLL : solver;
           double fq[Q_X0 + ORA_MAXSPEC];
-          ora_riemann(rl, rr, bn, nspec, sol, c->mach_thr, fq);
+          int updir;
+          riemann_core(rl, rr, bn, nspec, sol, c->mach_thr, fq, &updir);
           if (has_bg) {
             const double *fh = (d == 2) ? &w->fhat_f[(k + NG) * 16] : &w->fhat_c[(k + NG) * 16];
             for (int q = 0; q < 7 + nspec; ++q) fq[q] -= fh[q];
           }
+          /* A reflecting wall face is a symmetry plane of its Riemann problem
+           * (Table bcs: u_n = 0, B_n = 0): every flux component except the
+           * normal momentum vanishes there.  Set them to zero instead of to the
+           * solver's rounding residue. */
+          if ((c3[d] == 0 && c->bc[d][0] == ORA_REFLECT) || (c3[d] == G->n[d] && c->bc[d][1] == ORA_REFLECT))
+            for (int q = 0; q < 7 + nspec; ++q) {
+              if (q != Q_MN) fq[q] = 0.0;
+              updir = 0;
+            }
+          w->up[d][pR] = (signed char)updir;
           w->F[d][F_RHO][pR] = fq[Q_RHO];
           w->F[d][F_MX + d][pR] = fq[Q_MN];
           w->F[d][F_MX + t1][pR] = fq[Q_MT1];
@@ -631,8 +664,9 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
             double Ea0 = -w->F[a][F_BX + b][p - sb];     /* a-face (c_a, c_b-1) */
             double Eb1 = w->F[b][F_BX + a][p];           /* b-face (c_a, c_b)   */
             double Eb0 = w->F[b][F_BX + a][p - sa];      /* b-face (c_a-1, c_b) */
-            double ma1 = w->F[a][F_RHO][p], ma0 = w->F[a][F_RHO][p - sb];
-            double mb1 = w->F[b][F_RHO][p], mb0 = w->F[b][F_RHO][p - sa];
+            /* contact directions (signs of the mass fluxes) on those faces */
+            int ma1 = w->up[a][p], ma0 = w->up[a][p - sb];
+            int mb1 = w->up[b][p], mb0 = w->up[b][p - sa];
             /* cell reference EMFs at (c_a-1|c_a, c_b-1|c_b) */
             long q00 = p - sa - sb, q10 = p - sb, q01 = p - sa, q11 = p;
 #define ECELL(q) (-(w->W[W_VX + a][q] * w->W[W_BX + b][q] - w->W[W_VX + b][q] * w->W[W_BX + a][q]))
@@ -641,19 +675,26 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
             /* derivatives along b on the a-faces, upwinded in a */
             double lo_l = Eb0 - E00, lo_r = Eb1 - E10;    /* below the corner */
             double up_l = E01 - Eb0, up_r = E11 - Eb1;    /* above the corner */
-            double dlo = ma0 > 0.0 ? lo_l : (ma0 < 0.0 ? lo_r : 0.5 * (lo_l + lo_r));
-            double dup = ma1 > 0.0 ? up_l : (ma1 < 0.0 ? up_r : 0.5 * (up_l + up_r));
+            double dlo = ma0 > 0 ? lo_l : (ma0 < 0 ? lo_r : 0.5 * (lo_l + lo_r));
+            double dup = ma1 > 0 ? up_l : (ma1 < 0 ? up_r : 0.5 * (up_l + up_r));
             /* derivatives along a on the b-faces, upwinded in b */
             double le_d = Ea0 - E00, le_u = Ea1 - E01;    /* left of the corner  */
             double ri_d = E10 - Ea0, ri_u = E11 - Ea1;    /* right of the corner */
-            double dle = mb0 > 0.0 ? le_d : (mb0 < 0.0 ? le_u : 0.5 * (le_d + le_u));
-            double dri = mb1 > 0.0 ? ri_d : (mb1 < 0.0 ? ri_u : 0.5 * (ri_d + ri_u));
+            double dle = mb0 > 0 ? le_d : (mb0 < 0 ? le_u : 0.5 * (le_d + le_u));
+            double dri = mb1 > 0 ? ri_d : (mb1 < 0 ? ri_u : 0.5 * (ri_d + ri_u));
             Ed = 0.25 * (Ea1 + Ea0 + Eb1 + Eb0) + 0.25 * (dlo - dup) + 0.25 * (dle - dri);
           } else if (G->act[a]) {
             Ed = -w->F[a][F_BX + b][p];
           } else if (G->act[b]) {
             Ed = w->F[b][F_BX + a][p];
           }
+          /* An edge lying on a reflecting wall: u_n = 0 and B_n = 0 there
+           * (Table bcs) make the tangential EMF -(u x B)_t vanish. */
+          if ((G->act[a] && ((cc[a] == 0 && c->bc[a][0] == ORA_REFLECT) ||
+                             (cc[a] == G->n[a] && c->bc[a][1] == ORA_REFLECT))) ||
+              (G->act[b] && ((cc[b] == 0 && c->bc[b][0] == ORA_REFLECT) ||
+                             (cc[b] == G->n[b] && c->bc[b][1] == ORA_REFLECT))))
+            Ed = 0.0;
           w->E[d][p] = Ed;
         }
   }

@@ -1,0 +1,234 @@
+"""GB300-native explicit MHD stage (arXiv 2604.12672, Sect. 2): Python binding.
+
+A thin ctypes layer over the C ABI of libphl.so (include/phl.h): it only
+marshals arguments.  Every step of the scheme runs in the library's CUDA
+kernels; there is no CPU fallback -- if libphl.so is missing or fails to load,
+every entry point raises.  torch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libphl.so")
+
+PHL_MAXSPEC = 4
+PERIODIC, REFLECT, OUTFLOW = 0, 1, 2
+EOS = {"ideal": 0, "stellar": 1}
+RIEMANN = {"lhlld": 0, "hlld": 1, "hll": 2}
+PRECISION = {"fp64": 0, "mixed": 1}
+HOST, DEVICE = 0, 1
+STATUS = {0: "PHL_OK", 1: "PHL_EINVAL", 2: "PHL_ECUDA", 3: "PHL_ENOMEM", 4: "PHL_ENEGATIVE",
+          5: "PHL_ENAN", 6: "PHL_ENEWTON", 7: "PHL_ETIMEOUT", 8: "PHL_EUNSUPPORTED"}
+
+_dp = C.POINTER(C.c_double)
+
+
+class PhlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(C.Structure):
+    _fields_ = [
+        ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("bc", (C.c_int * 2) * 3), ("eos", C.c_int), ("gamma", C.c_double),
+        ("nspec", C.c_int), ("A", C.c_double * PHL_MAXSPEC), ("Z", C.c_double * PHL_MAXSPEC),
+        ("g", C.c_double * 3),
+        ("bg_rho_c", _dp), ("bg_p_c", _dp), ("bg_rho_f", _dp), ("bg_p_f", _dp),
+        ("bg_ge_c", _dp), ("bg_gc_c", _dp), ("bg_ge_f", _dp), ("bg_gc_f", _dp),
+        ("heat", _dp), ("cfl", C.c_double), ("rk", C.c_int), ("riemann", C.c_int),
+        ("eps_sf", C.c_double), ("mach_thr", C.c_double), ("precision", C.c_int),
+        ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("use_mlp", C.c_int),
+        ("stream", C.c_void_p),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_long), ("t", C.c_double), ("last_dt", C.c_double),
+                ("device_flags", C.c_int), ("kernels_per_step", C.c_int), ("device_bytes", C.c_size_t)]
+
+
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_long), ("ms", C.c_double)]
+
+
+_lib = None
+
+# every exported symbol of include/phl.h with (restype, argtypes)
+_SIGS = {
+    "phl_create_grid": (C.c_int, [C.POINTER(GridDesc), C.POINTER(C.c_void_p)]),
+    "phl_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_compute_dt": (C.c_int, [C.c_void_p, _dp]),
+    "phl_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "phl_check": (C.c_int, [C.c_void_p]),
+    "phl_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "phl_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "phl_dt_device_ptr": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "phl_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "phl_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "phl_destroy": (None, [C.c_void_p]),
+    "phl_last_error": (C.c_char_p, []),
+    "phl_riemann_batch": (C.c_int, [C.c_long, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                    C.c_int, C.c_double, C.c_int, C.c_void_p]),
+}
+
+
+def lib():
+    """Load libphl.so (in-tree build).  Raises if it is missing: no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise PhlError(st, lib().phl_last_error().decode())
+
+
+def _ptr(a):
+    """Raw pointer and location of a numpy array or a torch tensor."""
+    if a is None:
+        return None, HOST
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "float64 C-contiguous array expected"
+        return a.ctypes.data, HOST
+    # torch tensor
+    assert a.is_contiguous(), "contiguous tensor expected"
+    return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
+
+
+def riemann_batch(wl, wr, bn, bg=None, nspec=0, solver="lhlld", mach_thr=0.6, precision="fp64"):
+    """Device Riemann solver on n faces (see phl_riemann_batch in include/phl.h)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    bn = np.ascontiguousarray(bn, dtype=np.float64)
+    n = wl.shape[0]
+    bg = np.zeros((n, 4)) if bg is None else np.ascontiguousarray(bg, dtype=np.float64)
+    f = np.zeros((n, 7 + nspec))
+    _check(lib().phl_riemann_batch(n, wl.ctypes.data, wr.ctypes.data, bn.ctypes.data, bg.ctypes.data, nspec,
+                                   RIEMANN[solver], float(mach_thr), PRECISION[precision], f.ctypes.data))
+    return f
+
+
+class Grid:
+    """One simulation box on the current CUDA device (see include/phl.h)."""
+
+    def __init__(self, pr, precision="fp64", riemann=None, eps_sf=None, cfl=None, rk=3, wb=True,
+                 stream=None, mach_thr=None):
+        self.pr = pr
+        d = GridDesc()
+        for k in range(3):
+            d.n[k] = pr.n[k]
+            d.lo[k] = pr.lo[k]
+            d.hi[k] = pr.hi[k]
+            d.bc[k][0], d.bc[k][1] = pr.bc[k]
+            d.g[k] = pr.g[k]
+        d.eos = EOS[pr.eos]
+        d.gamma = pr.gamma
+        d.nspec = pr.nspec
+        self._keep = []
+        if pr.bg is not None and wb:
+            for key in ("rho_c", "p_c", "rho_f", "p_f", "ge_c", "gc_c", "ge_f", "gc_f"):
+                if key in pr.bg:
+                    arr = np.ascontiguousarray(pr.bg[key], dtype=np.float64)
+                    self._keep.append(arr)
+                    setattr(d, "bg_" + key, arr.ctypes.data_as(_dp))
+        if pr.heat is not None:
+            h = np.ascontiguousarray(pr.heat, dtype=np.float64)
+            self._keep.append(h)
+            d.heat = h.ctypes.data_as(_dp)
+        d.cfl = pr.cfl if cfl is None else cfl
+        d.rk = rk
+        d.riemann = RIEMANN[riemann or pr.riemann]
+        d.eps_sf = pr.eps_sf if eps_sf is None else eps_sf
+        d.mach_thr = pr.mach_thr if mach_thr is None else mach_thr
+        d.precision = PRECISION[precision]
+        d.newton_tol = 1e-11
+        d.newton_maxit = 50
+        d.use_mlp = 0
+        d.stream = stream
+        self.desc = d
+        h = C.c_void_p()
+        _check(lib().phl_create_grid(C.byref(d), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().phl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def set_state(self, cons, bx, by, bz, T=None):
+        ptrs = [_ptr(a) for a in (cons, bx, by, bz, T)]
+        where = ptrs[0][1]
+        _check(lib().phl_set_state(self.h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[4][0], where))
+
+    def load(self, st=None):
+        st = st or dict(cons=self.pr.cons, bx=self.pr.bx, by=self.pr.by, bz=self.pr.bz, T=self.pr.T)
+        self.set_state(np.ascontiguousarray(st["cons"]), np.ascontiguousarray(st["bx"]),
+                       np.ascontiguousarray(st["by"]), np.ascontiguousarray(st["bz"]), st.get("T"))
+
+    def get_state_into(self, cons, bx, by, bz, T=None):
+        ptrs = [_ptr(a) for a in (cons, bx, by, bz, T)]
+        _check(lib().phl_get_state(self.h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[4][0], ptrs[0][1]))
+
+    def get_state(self):
+        pr = self.pr
+        cons = np.empty_like(pr.cons)
+        bx, by, bz = np.empty_like(pr.bx), np.empty_like(pr.by), np.empty_like(pr.bz)
+        self.get_state_into(cons, bx, by, bz)
+        return dict(cons=cons, bx=bx, by=by, bz=bz, T=None)
+
+    def step(self, nsteps=1, dt=0.0):
+        _check(lib().phl_step(self.h, float(dt), int(nsteps)))
+
+    def compute_dt(self):
+        v = C.c_double()
+        _check(lib().phl_compute_dt(self.h, C.byref(v)))
+        return v.value
+
+    def check(self):
+        _check(lib().phl_check(self.h))
+
+    def set_stream(self, stream):
+        _check(lib().phl_set_stream(self.h, stream))
+
+    def stats(self):
+        s = Stats()
+        _check(lib().phl_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def set_timing(self, on=True):
+        _check(lib().phl_set_timing(self.h, int(bool(on))))
+
+    def kernel_times(self, reset=True):
+        """{kernel class: (launches, total ms)} since the last reset (synchronises)."""
+        arr = (KernelTime * 32)()
+        n = C.c_int()
+        _check(lib().phl_kernel_times(self.h, arr, 32, C.byref(n), int(bool(reset))))
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].ms) for i in range(min(n.value, 32))}
+
+    def dt_device_ptr(self):
+        p = C.c_void_p()
+        _check(lib().phl_dt_device_ptr(self.h, C.byref(p)))
+        return p.value

@@ -1,0 +1,381 @@
+// phl_api.cu -- host implementation of the C ABI declared in include/phl.h.
+//
+// A phl_grid owns: the state (U^n and one stage buffer, cell and face
+// fields), the device copies of the background profiles, the per-stage work
+// arrays of the FP64 path, and three device scalars (dt, the running max of
+// the CFL sum, an error word).  Every launch goes to the grid's stream; the
+// time step can stay on the device so that a whole step needs no host sync.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "phl.h"
+#include "phl_internal.cuh"
+
+using namespace phl;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+phl_status fail(phl_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+phl_status cuda_fail(cudaError_t e, const char *what) {
+  cudaGetLastError();
+  return fail(e == cudaErrorMemoryAllocation ? PHL_ENOMEM : PHL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                              \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+}  // namespace
+
+struct phl_grid {
+  phl_grid_desc desc;
+  DevGeo G;
+  cudaStream_t stream;
+  // state
+  double *U = nullptr, *U1 = nullptr, *B = nullptr, *B1 = nullptr, *T = nullptr;
+  // background and heating profiles
+  double *bg = nullptr, *heat = nullptr;
+  // work
+  double *W = nullptr, *F[3] = {nullptr, nullptr, nullptr}, *E = nullptr;
+  uint8_t *raw = nullptr, *flag = nullptr;
+  // scalars
+  double *dt = nullptr;
+  unsigned long long *dmax = nullptr;
+  int *dflag = nullptr;
+  std::vector<void *> allocs;
+  size_t bytes = 0;
+  long steps = 0;
+  double last_dt = 0.0;
+  int launches_per_step = 0;
+  Prof prof;
+};
+
+namespace {
+
+template <typename T>
+phl_status dalloc(phl_grid *g, T **p, size_t n) {
+  void *q = nullptr;
+  size_t bytes = n * sizeof(T);
+  if (bytes == 0) bytes = sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  e = cudaMemset(q, 0, bytes);
+  if (e != cudaSuccess) { cudaFree(q); return cuda_fail(e, "cudaMemset"); }
+  g->allocs.push_back(q);
+  g->bytes += bytes;
+  *p = (T *)q;
+  return PHL_OK;
+}
+
+// Copy between the ABI layout (dense) and the padded device layout.
+// ext = (nx', ny', nz') extents of the field; to_dev selects the direction.
+phl_status copy_field(phl_grid *g, double *dev, const double *abi_src, double *abi_dst, int ex, int ey, int ez,
+                      bool to_dev) {
+  const DevGeo &G = g->G;
+  cudaMemcpy3DParms p;
+  memset(&p, 0, sizeof(p));
+  cudaPitchedPtr dptr = make_cudaPitchedPtr(dev, (size_t)G.sy * sizeof(double), (size_t)G.sy, (size_t)(G.sz / G.sy));
+  if (to_dev) {
+    p.srcPtr = make_cudaPitchedPtr((void *)abi_src, (size_t)ex * sizeof(double), (size_t)ex, (size_t)ey);
+    p.dstPtr = dptr;
+  } else {
+    p.srcPtr = dptr;
+    p.dstPtr = make_cudaPitchedPtr((void *)abi_dst, (size_t)ex * sizeof(double), (size_t)ex, (size_t)ey);
+  }
+  p.extent = make_cudaExtent((size_t)ex * sizeof(double), (size_t)ey, (size_t)ez);
+  p.kind = cudaMemcpyDefault;
+  CK(cudaMemcpy3DAsync(&p, g->stream), "cudaMemcpy3DAsync");
+  return PHL_OK;
+}
+
+phl_status check_flags(phl_grid *g) {
+  int f = 0;
+  CK(cudaMemcpyAsync(&f, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream), "read flags");
+  CK(cudaStreamSynchronize(g->stream), "sync");
+  if (f & FLAG_NAN) return fail(PHL_ENAN, "non-finite value in the state");
+  if (f & FLAG_NEG) return fail(PHL_ENEGATIVE, "non-positive density or pressure");
+  if (f & FLAG_NEWTON) return fail(PHL_ENEWTON, "EOS Newton iteration did not converge");
+  return PHL_OK;
+}
+
+void do_stage(phl_grid *g, const double *Uin, const double *Bin, double *Uout, double *Bout, double a,
+              double b, int *nl) {
+  StageBufs S;
+  S.Uin = Uin; S.Bin = Bin; S.Ubase = g->U; S.Bbase = g->B;
+  S.Uout = Uout; S.Bout = Bout; S.a = a; S.b = b; S.dt = g->dt;
+  S.W = g->W; S.F[0] = g->F[0]; S.F[1] = g->F[1]; S.F[2] = g->F[2]; S.E = g->E;
+  S.raw = g->raw; S.flag = g->flag; S.T = g->T; S.dflag = g->dflag;
+  launch_stage_fp64(g->G, S, g->stream, nl, g->prof.on ? &g->prof : nullptr);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *phl_last_error(void) { return g_err; }
+
+phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
+  g_err[0] = 0;
+  if (!d || !out) return fail(PHL_EINVAL, "null argument");
+  *out = nullptr;
+  for (int k = 0; k < 3; ++k) {
+    if (d->n[k] < 1) return fail(PHL_EINVAL, "n[%d] = %d < 1", k, d->n[k]);
+    if (d->n[k] > 1 && d->n[k] < 4) return fail(PHL_EINVAL, "active dimension %d needs n >= 4", k);
+    if (!(d->hi[k] > d->lo[k])) return fail(PHL_EINVAL, "hi[%d] <= lo[%d]", k, k);
+    for (int s = 0; s < 2; ++s)
+      if (d->bc[k][s] < 0 || d->bc[k][s] > 2) return fail(PHL_EINVAL, "bad boundary condition");
+    if ((d->bc[k][0] == PHL_PERIODIC) != (d->bc[k][1] == PHL_PERIODIC))
+      return fail(PHL_EINVAL, "periodic boundaries must be periodic on both sides");
+  }
+  if (d->nspec < 0 || d->nspec > PHL_MAXSPEC) return fail(PHL_EINVAL, "nspec out of range");
+  if (d->eos != PHL_EOS_IDEAL) return fail(PHL_EUNSUPPORTED, "stellar EOS not available in this build");
+  if (!(d->gamma > 1.0)) return fail(PHL_EINVAL, "gamma must exceed 1");
+  if (!(d->cfl > 0.0)) return fail(PHL_EINVAL, "cfl must be positive");
+  if (d->rk != 2 && d->rk != 3) return fail(PHL_EINVAL, "rk must be 2 or 3");
+  if (d->riemann < 0 || d->riemann > 2) return fail(PHL_EINVAL, "bad riemann solver");
+  if (d->precision != PHL_FP64) return fail(PHL_EUNSUPPORTED, "precision mode not available in this build");
+  if (d->bg_rho_c && (!d->bg_p_c || !d->bg_rho_f || !d->bg_p_f))
+    return fail(PHL_EINVAL, "incomplete background profiles");
+  const long ncell = (long)d->n[0] * d->n[1] * d->n[2];
+  if (ncell > (1L << 31)) return fail(PHL_EINVAL, "grid too large");
+
+  phl_grid *g = new phl_grid();
+  g->desc = *d;
+  g->stream = (cudaStream_t)d->stream;
+  DevGeo &G = g->G;
+  memset(&G, 0, sizeof(G));
+  for (int k = 0; k < 3; ++k) {
+    G.n[k] = d->n[k];
+    G.act[k] = d->n[k] > 1;
+    G.bc[k][0] = d->bc[k][0];
+    G.bc[k][1] = d->bc[k][1];
+    G.dx[k] = (d->hi[k] - d->lo[k]) / d->n[k];
+    G.idx[k] = 1.0 / G.dx[k];
+    G.ge[k] = G.act[k] ? NGW : 0;
+    G.g[k] = d->g[k];
+  }
+  const long pitch = ((long)d->n[0] + 1 + 3) / 4 * 4;
+  G.sy = pitch;
+  G.sz = pitch * (d->n[1] + 1);
+  G.plane = G.sz * (d->n[2] + 1);
+  G.wy = d->n[0] + 2L * G.ge[0] + 1;
+  G.wz = G.wy * (d->n[1] + 2L * G.ge[1] + 1);
+  G.wtot = G.wz * (d->n[2] + 2L * G.ge[2] + 1);
+  G.nspec = d->nspec;
+  G.nv = 5 + d->nspec;
+  G.nw = 10 + d->nspec;
+  G.nf = 8 + d->nspec;
+  G.eos = d->eos;
+  G.gamma = d->gamma;
+  G.riemann = d->riemann;
+  G.eps_sf = d->eps_sf;
+  G.mach_thr = d->mach_thr;
+  G.cfl = d->cfl;
+
+  phl_status st = PHL_OK;
+#define AL(p, n)                                  \
+  do {                                            \
+    st = dalloc(g, p, (size_t)(n));               \
+    if (st != PHL_OK) { phl_destroy(g); return st; } \
+  } while (0)
+  AL(&g->U, G.nv * G.plane);
+  AL(&g->U1, G.nv * G.plane);
+  AL(&g->B, 3 * G.plane);
+  AL(&g->B1, 3 * G.plane);
+  AL(&g->W, (long)G.nw * G.wtot);
+  for (int k = 0; k < 3; ++k)
+    if (G.act[k]) AL(&g->F[k], (long)(G.nf + 1) * G.wtot);   // + contact direction
+  AL(&g->E, 3 * G.wtot);
+  AL(&g->raw, ncell);
+  AL(&g->flag, G.wtot);
+  AL(&g->dt, 1);
+  AL(&g->dmax, 1);
+  AL(&g->dflag, 1);
+  const int nz = d->n[2];
+  const long nbg = 8L * (nz + 2 * BG_NG + 1);
+  AL(&g->bg, nbg);
+  if (d->bg_rho_c) {
+    std::vector<double> h(nbg, 0.0);
+    const long L = nz + 2 * BG_NG + 1;
+    const double *src[8] = {d->bg_rho_c, d->bg_p_c, d->bg_rho_f, d->bg_p_f,
+                            d->bg_ge_c, d->bg_gc_c, d->bg_ge_f, d->bg_gc_f};
+    for (int q = 0; q < 8; ++q) {
+      if (!src[q]) continue;
+      const long cnt = (q == 2 || q == 3 || q == 6 || q == 7) ? L : L - 1;
+      memcpy(&h[q * L], src[q], cnt * sizeof(double));
+    }
+    cudaError_t e = cudaMemcpy(g->bg, h.data(), nbg * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { phl_destroy(g); return cuda_fail(e, "copy background"); }
+    G.has_bg = 1;
+    G.bg_rho_c = g->bg; G.bg_p_c = g->bg + L; G.bg_rho_f = g->bg + 2 * L; G.bg_p_f = g->bg + 3 * L;
+    G.bg_ge_c = d->bg_ge_c ? g->bg + 4 * L : nullptr;
+    G.bg_gc_c = d->bg_gc_c ? g->bg + 5 * L : nullptr;
+    G.bg_ge_f = d->bg_ge_f ? g->bg + 6 * L : nullptr;
+    G.bg_gc_f = d->bg_gc_f ? g->bg + 7 * L : nullptr;
+  }
+  if (d->heat) {
+    AL(&g->heat, nz);
+    cudaError_t e = cudaMemcpy(g->heat, d->heat, nz * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { phl_destroy(g); return cuda_fail(e, "copy heating"); }
+    G.heat = g->heat;
+  }
+#undef AL
+  *out = g;
+  return PHL_OK;
+}
+
+void phl_destroy(phl_grid *g) {
+  if (!g) return;
+  g->prof.release();
+  for (void *p : g->allocs) cudaFree(p);
+  delete g;
+}
+
+phl_status phl_set_stream(phl_grid *g, void *stream) {
+  if (!g) return fail(PHL_EINVAL, "null grid");
+  g->stream = (cudaStream_t)stream;
+  return PHL_OK;
+}
+
+phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx, const double *by,
+                         const double *bz, const double *T, int where) {
+  if (!g || !cons || !bx || !by || !bz) return fail(PHL_EINVAL, "null argument");
+  if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
+  (void)T;
+  const DevGeo &G = g->G;
+  const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+  const long nc = (long)nx * ny * nz;
+  phl_status st;
+  for (int v = 0; v < G.nv; ++v)
+    if ((st = copy_field(g, g->U + v * G.plane, cons + v * nc, nullptr, nx, ny, nz, true)) != PHL_OK) return st;
+  if ((st = copy_field(g, g->B, bx, nullptr, nx + 1, ny, nz, true)) != PHL_OK) return st;
+  if ((st = copy_field(g, g->B + G.plane, by, nullptr, nx, ny + 1, nz, true)) != PHL_OK) return st;
+  if ((st = copy_field(g, g->B + 2 * G.plane, bz, nullptr, nx, ny, nz + 1, true)) != PHL_OK) return st;
+  CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream), "reset flags");
+  if (where == PHL_HOST) CK(cudaStreamSynchronize(g->stream), "sync");
+  return PHL_OK;
+}
+
+phl_status phl_get_state(phl_grid *g, double *cons, double *bx, double *by, double *bz, double *T, int where) {
+  if (!g || !cons || !bx || !by || !bz) return fail(PHL_EINVAL, "null argument");
+  if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
+  (void)T;
+  const DevGeo &G = g->G;
+  const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+  const long nc = (long)nx * ny * nz;
+  phl_status st;
+  for (int v = 0; v < G.nv; ++v)
+    if ((st = copy_field(g, g->U + v * G.plane, nullptr, cons + v * nc, nx, ny, nz, false)) != PHL_OK) return st;
+  if ((st = copy_field(g, g->B, nullptr, bx, nx + 1, ny, nz, false)) != PHL_OK) return st;
+  if ((st = copy_field(g, g->B + G.plane, nullptr, by, nx, ny + 1, nz, false)) != PHL_OK) return st;
+  if ((st = copy_field(g, g->B + 2 * G.plane, nullptr, bz, nx, ny, nz + 1, false)) != PHL_OK) return st;
+  return check_flags(g);
+}
+
+phl_status phl_compute_dt(phl_grid *g, double *dt_out) {
+  if (!g || !dt_out) return fail(PHL_EINVAL, "null argument");
+  int nl = 0;
+  launch_dt_fp64(g->G, g->U, g->B, g->T, g->dmax, g->dt, g->dflag, g->stream, &nl, g->prof.on ? &g->prof : nullptr);
+  CK(cudaGetLastError(), "launch dt");
+  CK(cudaMemcpyAsync(dt_out, g->dt, sizeof(double), cudaMemcpyDeviceToHost, g->stream), "read dt");
+  phl_status st = check_flags(g);
+  if (st != PHL_OK) return st;
+  g->last_dt = *dt_out;
+  return PHL_OK;
+}
+
+phl_status phl_step(phl_grid *g, double dt, int nsteps) {
+  if (!g) return fail(PHL_EINVAL, "null grid");
+  if (nsteps < 0) return fail(PHL_EINVAL, "nsteps < 0");
+  for (int s = 0; s < nsteps; ++s) {
+    int nl = 0;
+    if (dt > 0.0) {
+      launch_set_scalar(g->dt, dt, g->stream, g->prof.on ? &g->prof : nullptr);
+      ++nl;
+    } else {
+      launch_dt_fp64(g->G, g->U, g->B, g->T, g->dmax, g->dt, g->dflag, g->stream, &nl,
+                     g->prof.on ? &g->prof : nullptr);
+    }
+    if (g->desc.rk == 2) {
+      do_stage(g, g->U, g->B, g->U1, g->B1, 0.0, 1.0, &nl);
+      do_stage(g, g->U1, g->B1, g->U, g->B, 0.5, 0.5, &nl);
+    } else {
+      do_stage(g, g->U, g->B, g->U1, g->B1, 0.0, 1.0, &nl);
+      do_stage(g, g->U1, g->B1, g->U1, g->B1, 0.75, 0.25, &nl);
+      do_stage(g, g->U1, g->B1, g->U, g->B, 1.0 / 3.0, 2.0 / 3.0, &nl);
+    }
+    CK(cudaGetLastError(), "launch stage");
+    g->launches_per_step = nl;
+    ++g->steps;
+  }
+  return PHL_OK;
+}
+
+phl_status phl_check(phl_grid *g) {
+  if (!g) return fail(PHL_EINVAL, "null grid");
+  return check_flags(g);
+}
+
+phl_status phl_get_stats(phl_grid *g, phl_stats *st) {
+  if (!g || !st) return fail(PHL_EINVAL, "null argument");
+  memset(st, 0, sizeof(*st));
+  st->steps = g->steps;
+  st->last_dt = g->last_dt;
+  int f = 0;
+  CK(cudaMemcpyAsync(&f, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream), "read flags");
+  CK(cudaStreamSynchronize(g->stream), "sync");
+  st->device_flags = f;
+  st->kernels_per_step = g->launches_per_step;
+  st->device_bytes = g->bytes;
+  return PHL_OK;
+}
+
+phl_status phl_set_timing(phl_grid *g, int on) {
+  if (!g) return fail(PHL_EINVAL, "null grid");
+  g->prof.on = on != 0;
+  return PHL_OK;
+}
+
+phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, int reset) {
+  if (!g || !n || (max > 0 && !out)) return fail(PHL_EINVAL, "null argument");
+  CK(g->prof.fold(), "fold kernel timings");
+  int k = 0;
+  for (int c = 0; c < KC_COUNT; ++c) {
+    if (g->prof.cnt[c] == 0) continue;
+    if (k < max) {
+      memset(&out[k], 0, sizeof(out[k]));
+      strncpy(out[k].name, kclass_name(c), sizeof(out[k].name) - 1);
+      out[k].launches = g->prof.cnt[c];
+      out[k].ms = g->prof.ms[c];
+    }
+    ++k;
+  }
+  *n = k;
+  if (reset)
+    for (int c = 0; c < KC_COUNT; ++c) { g->prof.cnt[c] = 0; g->prof.ms[c] = 0.0; }
+  return PHL_OK;
+}
+
+phl_status phl_dt_device_ptr(phl_grid *g, const double **ptr) {
+  if (!g || !ptr) return fail(PHL_EINVAL, "null argument");
+  *ptr = g->dt;
+  return PHL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// phl_internal.cuh -- device-side geometry, layouts and kernel entry points
+// shared by the library's translation units.
+//
+// Device state layout (one allocation per field group, FP64, no ghosts):
+//   index(i, j, k) = i + sy * j + sz * k,  sy = pitch >= nx + 1 (multiple of 4),
+//   sz = sy * (ny + 1); every array spans (nz + 1) planes so cells (i < nx)
+//   and faces (i <= nx) share one geometry.  Conserved variable v lives at
+//   U + v * plane; face component d (normal B on d-faces) at Bf + d * plane.
+// Ghost cells are never stored for the state: a ghost index is mapped to the
+// interior cell its data comes from (periodic wrap, mirror, or copy) and the
+// reflecting sign flips are applied on the fly.
+//
+// Work layout (per-stage scratch, FP64 path): the same index formula with
+// "ge" ghost layers (2 on active dimensions) and one extra face layer:
+//   windex(i, j, k) = (i + ge0) + wy * (j + ge1) + wz * (k + ge2).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "riemann.cuh"
+
+namespace phl {
+
+constexpr int NGW = 2;               // work-array ghost layers
+constexpr int NW_MAX = 10 + PHL_NSPEC_MAX;
+constexpr int NF_MAX = 8 + PHL_NSPEC_MAX;
+constexpr int BG_NG = 3;             // background-profile ghost layers
+
+// primitive deviation components (cell-centred work arrays)
+enum { W_RHO = 0, W_VX, W_VY, W_VZ, W_BX, W_BY, W_BZ, W_P, W_GE, W_GC, W_X0 };
+// conserved components
+enum { U_RHO = 0, U_MX, U_MY, U_MZ, U_E, U_X0 };
+// global-frame flux components
+enum { F_RHO = 0, F_MX, F_MY, F_MZ, F_E, F_BX, F_BY, F_BZ, F_X0 };
+
+enum { FLAG_NEG = 1, FLAG_NAN = 2, FLAG_NEWTON = 4 };
+
+struct DevGeo {
+  int n[3];
+  int act[3];
+  int bc[3][2];
+  long sy, sz, plane;          // state strides / size per field
+  int ge[3];
+  long wy, wz, wtot;           // work strides / size per field
+  double dx[3], idx[3];
+  int nspec, nv, nw, nf;
+  int eos;
+  double gamma;
+  int has_bg;
+  const double *bg_rho_c, *bg_p_c, *bg_rho_f, *bg_p_f;   // device profiles
+  const double *bg_ge_c, *bg_gc_c, *bg_ge_f, *bg_gc_f;   // may be null
+  const double *heat;          // per z-cell, may be null
+  double g[3];
+  int riemann;
+  double eps_sf, mach_thr, cfl;
+};
+
+__host__ __device__ __forceinline__ long sidx(const DevGeo &G, int i, int j, int k) {
+  return (long)i + G.sy * j + G.sz * k;
+}
+__host__ __device__ __forceinline__ long widx(const DevGeo &G, int i, int j, int k) {
+  return (long)(i + G.ge[0]) + G.wy * (j + G.ge[1]) + G.wz * (k + G.ge[2]);
+}
+
+// Ghost mapping of a cell index along one dimension (Table bcs): returns the
+// interior source index; *flip = true where the reflecting mirror applies.
+__host__ __device__ __forceinline__ int cell_src(int i, int n, int bclo, int bchi, bool &flip) {
+  flip = false;
+  if (i < 0) {
+    if (bclo == 0) { int r = i % n; return r < 0 ? r + n : r; }
+    if (bclo == 1) { flip = true; return -1 - i; }
+    return 0;
+  }
+  if (i >= n) {
+    if (bchi == 0) return i % n;
+    if (bchi == 1) { flip = true; return 2 * n - 1 - i; }
+    return n - 1;
+  }
+  return i;
+}
+
+// Background at cell centre k and at z-face k-1/2 (zero without background).
+struct Bg { double rho, p, ge, gc; };
+__device__ __forceinline__ Bg bg_cell(const DevGeo &G, int k) {
+  Bg b{0.0, 0.0, 0.0, 0.0};
+  if (G.has_bg) {
+    b.rho = G.bg_rho_c[k + BG_NG];
+    b.p = G.bg_p_c[k + BG_NG];
+    b.ge = G.bg_ge_c ? G.bg_ge_c[k + BG_NG] : G.gamma;
+    b.gc = G.bg_gc_c ? G.bg_gc_c[k + BG_NG] : G.gamma;
+  }
+  return b;
+}
+__device__ __forceinline__ Bg bg_zface(const DevGeo &G, int k) {
+  Bg b{0.0, 0.0, 0.0, 0.0};
+  if (G.has_bg) {
+    b.rho = G.bg_rho_f[k + BG_NG];
+    b.p = G.bg_p_f[k + BG_NG];
+    b.ge = G.bg_ge_f ? G.bg_ge_f[k + BG_NG] : G.gamma;
+    b.gc = G.bg_gc_f ? G.bg_gc_f[k + BG_NG] : G.gamma;
+  }
+  return b;
+}
+
+// Kernel classes for the optional per-kernel event timing.
+enum KClass {
+  KC_PRIM = 0, KC_FLAG_RAW, KC_FLAG_DILATE, KC_FLUX_X, KC_FLUX_Y, KC_FLUX_Z, KC_EMF, KC_UPDATE_CELLS,
+  KC_UPDATE_FACES, KC_DT, KC_SCALAR, KC_STAGE_MIXED, KC_COUNT
+};
+const char *kclass_name(int c);
+
+// Records (start, end) event pairs around launches when enabled.
+struct Prof {
+  bool on = false;
+  cudaEvent_t *ev = nullptr;   // pool of 2 * cap events
+  int *cls = nullptr;
+  int cap = 0, used = 0;
+  double ms[KC_COUNT] = {0};
+  long cnt[KC_COUNT] = {0};
+  int cur = -1;
+  cudaError_t begin(int c, cudaStream_t s);
+  cudaError_t end(cudaStream_t s);
+  cudaError_t fold();          // synchronises on the recorded events
+  void release();
+};
+
+// Pointers of one FP64 stage evaluation.
+struct StageBufs {
+  const double *Uin, *Bin;     // stage input state
+  const double *Ubase, *Bbase; // U^n
+  double *Uout, *Bout;
+  double a, b;                 // out = a * base + b * (in - dt * R)
+  const double *dt;            // device scalar
+  double *W;                   // nw work fields
+  double *F[3];                // nf flux fields per direction
+  double *E;                   // 3 edge-EMF fields
+  uint8_t *raw, *flag;         // raw flags (interior), dilated flags (work layout)
+  double *T;                   // temperature (stellar), state layout
+  int *dflag;                  // device error word
+};
+
+// FP64 multi-kernel stage (kernels_fp64.cu)
+void launch_stage_fp64(const DevGeo &G, const StageBufs &B, cudaStream_t s, int *nlaunch, Prof *prof);
+void launch_dt_fp64(const DevGeo &G, const double *U, const double *Bf, double *T, unsigned long long *dmax,
+                    double *dt, int *dflag, cudaStream_t s, int *nlaunch, Prof *prof);
+void launch_set_scalar(double *p, double v, cudaStream_t s, Prof *prof);
+
+}  // namespace phl

@@ -1,0 +1,52 @@
+// unit_kernels.cu -- the stage's device functions exposed for unit testing.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include "phl.h"
+#include "phl_internal.cuh"
+
+using namespace phl;
+
+namespace {
+
+template <typename R>
+__global__ void k_riemann_batch(long n, const double *wl, const double *wr, const double *bn, const double *bg,
+                                int nspec, int solver, double mthr, double *f) {
+  const int nw = 9 + nspec, nf = 7 + nspec;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    R a[9 + PHL_NSPEC_MAX], b[9 + PHL_NSPEC_MAX], out[7 + PHL_NSPEC_MAX];
+    for (int q = 0; q < nw; ++q) { a[q] = (R)wl[t * nw + q]; b[q] = (R)wr[t * nw + q]; }
+    int up;
+    riemann_dev<R>(a, b, (R)bn[t], (R)bg[4 * t], (R)bg[4 * t + 1], (R)bg[4 * t + 2], (R)bg[4 * t + 3], nspec,
+                   solver, (R)mthr, out, up);
+    for (int q = 0; q < nf; ++q) f[t * nf + q] = (double)out[q];
+  }
+}
+
+}  // namespace
+
+extern "C" phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const double *bn,
+                                        const double *bg, int nspec, int solver, double mach_thr,
+                                        int precision, double *f) {
+  if (n < 0 || nspec < 0 || nspec > PHL_MAXSPEC || solver < 0 || solver > 2) return PHL_EINVAL;
+  if (n == 0) return PHL_OK;
+  if (!wl || !wr || !bn || !bg || !f) return PHL_EINVAL;
+  const size_t nw = 9 + nspec, nf = 7 + nspec;
+  double *d = nullptr;
+  const size_t tot = n * (2 * nw + 1 + 4 + nf);
+  if (cudaMalloc(&d, tot * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return PHL_ENOMEM; }
+  double *dwl = d, *dwr = dwl + n * nw, *dbn = dwr + n * nw, *dbg = dbn + n, *df = dbg + 4 * n;
+  cudaMemcpy(dwl, wl, n * nw * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(dwr, wr, n * nw * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(dbn, bn, n * sizeof(double), cudaMemcpyHostToDevice);
+  cudaMemcpy(dbg, bg, 4 * n * sizeof(double), cudaMemcpyHostToDevice);
+  const int blocks = (int)((n + 127) / 128 < 4096 ? (n + 127) / 128 : 4096);
+  if (precision == PHL_FP64)
+    k_riemann_batch<double><<<blocks, 128>>>(n, dwl, dwr, dbn, dbg, nspec, solver, mach_thr, df);
+  else
+    k_riemann_batch<float><<<blocks, 128>>>(n, dwl, dwr, dbn, dbg, nspec, solver, mach_thr, df);
+  cudaError_t e = cudaMemcpy(f, df, n * nf * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) { cudaGetLastError(); return PHL_ECUDA; }
+  return PHL_OK;
+}

@@ -195,6 +195,18 @@ def test_well_balanced_rest(kind):
     assert np.abs(st2["cons"][1:4] / st2["cons"][0]).max() > 1e-5
 
 
+def test_reflecting_walls_keep_normal_field_zero():
+    """Table bcs: B_n = 0 at a reflecting wall.  The wall faces carry no EMF, so
+    the normal field there stays exactly zero while the interior field evolves."""
+    pr = W.stratified_box(12, 10, 16, amp=5e-2)
+    rng = np.random.default_rng(2)
+    pr.cons[1:3] += 1e-3 * rng.standard_normal(pr.cons[1:3].shape)
+    pr.bx[:] = 1e-2
+    st, _, _ = O.Oracle(pr).run(15)
+    assert np.all(st["bz"][0] == 0.0) and np.all(st["bz"][-1] == 0.0)
+    assert np.abs(st["bz"][1:-1]).max() > 1e-9
+
+
 def test_gravity_source_closed_form():
     """Uniform gas in a tall box with reflecting ends and no background: far from
     the walls the only force is rho*g, so m_z = rho*g*t and E gains rho*(g t)^2/2."""
