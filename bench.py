@@ -47,7 +47,7 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (profiling recipe's nominal table)
 BYTES_PER_CELL_STAGE = {1: 128.0, 2: 192.0, 3: 192.0}
 # FP64 flux kernel: FP64 operations per face (DADD + DMUL + 2 DFMA counted from
 # the ncu SASS counters of k_flux on the stratified box).
-FP64_FLOP_PER_FACE = None
+FP64_FLOP_PER_FACE = 807.0
 
 
 def read_peaks():
