@@ -178,6 +178,28 @@ phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const d
                              const double *bg, int nspec, int solver, double mach_thr,
                              int precision, double *f);
 
+/* CFL step (same definition as phl_compute_dt) computed without allocating
+ * any device memory.  No counterpart in the paper: it exists for callers that
+ * cannot let a library call cudaMalloc/cudaFree -- a host program whose own
+ * memory pool owns all device memory, or a driver loop that must not pay the
+ * device-wide synchronisation those calls may imply.
+ *   desc     geometry and physics (n, lo, hi, gamma, cfl; ideal EOS only);
+ *            no other field is read and no grid is needed;
+ *   cons, bx, by, bz  device pointers, ABI layout above (read only);
+ *   dt_out   device pointer to one double that receives cfl / max(...);
+ *   stream   cudaStream_t the two kernels are queued on (asynchronous).
+ * Scratch: a library-owned __device__ array of PHL_DT_NOALLOC_MAX_CELLS / 4096
+ * doubles (128 KiB), present on every GPU that loads the library until the
+ * process exits; grids above PHL_DT_NOALLOC_MAX_CELLS cells are rejected with
+ * PHL_EINVAL ("too many cells").  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call shares the array and leaves its partial
+ * results in it; calls whose kernels overlap on the GPU race on it.
+ * Errors: PHL_EINVAL, PHL_EUNSUPPORTED (stellar EOS), PHL_ECUDA. */
+#define PHL_DT_NOALLOC_MAX_CELLS 67108864L
+phl_status phl_cfl_dt_noalloc(const phl_grid_desc *desc, const double *cons, const double *bx,
+                              const double *by, const double *bz, double *dt_out, void *stream);
+
 void phl_destroy(phl_grid *g);
 
 /* Message describing the calling thread's last failure ("" if none). */

@@ -74,6 +74,8 @@ _SIGS = {
     "phl_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "phl_destroy": (None, [C.c_void_p]),
     "phl_last_error": (C.c_char_p, []),
+    "phl_cfl_dt_noalloc": (C.c_int, [C.POINTER(GridDesc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]),
     "phl_riemann_batch": (C.c_int, [C.c_long, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_int, C.c_double, C.c_int, C.c_void_p]),
 }
@@ -122,6 +124,18 @@ def riemann_batch(wl, wr, bn, bg=None, nspec=0, solver="lhlld", mach_thr=0.6, pr
     _check(lib().phl_riemann_batch(n, wl.ctypes.data, wr.ctypes.data, bn.ctypes.data, bg.ctypes.data, nspec,
                                    RIEMANN[solver], float(mach_thr), PRECISION[precision], f.ctypes.data))
     return f
+
+
+def cfl_dt_noalloc(grid_or_desc, cons, bx, by, bz, dt_out, stream=None):
+    """CFL step without device allocation (phl_cfl_dt_noalloc in include/phl.h).
+
+    For callers that cannot let the library allocate device memory.  All arrays
+    are CUDA tensors in the ABI layout; dt_out is a one-element float64 CUDA
+    tensor.  The call is asynchronous on `stream` (a cudaStream_t handle).
+    """
+    d = grid_or_desc.desc if isinstance(grid_or_desc, Grid) else grid_or_desc
+    ptrs = [_ptr(a)[0] for a in (cons, bx, by, bz, dt_out)]
+    _check(lib().phl_cfl_dt_noalloc(C.byref(d), *ptrs, stream))
 
 
 class Grid:

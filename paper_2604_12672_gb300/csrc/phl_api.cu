@@ -43,6 +43,16 @@ phl_status cuda_fail(cudaError_t e, const char *what) {
 
 }  // namespace
 
+namespace phl {
+int set_error(int st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+}  // namespace phl
+
 struct phl_grid {
   phl_grid_desc desc;
   DevGeo G;

@@ -139,6 +139,10 @@ struct StageBufs {
   int *dflag;                  // device error word
 };
 
+// Records the calling thread's last-error message (phl_last_error) and
+// returns st (phl_api.cu).
+int set_error(int st, const char *fmt, ...);
+
 // FP64 multi-kernel stage (kernels_fp64.cu)
 void launch_stage_fp64(const DevGeo &G, const StageBufs &B, cudaStream_t s, int *nlaunch, Prof *prof);
 void launch_dt_fp64(const DevGeo &G, const double *U, const double *Bf, double *T, unsigned long long *dmax,
