@@ -48,6 +48,11 @@ BYTES_PER_CELL_STAGE = {1: 128.0, 2: 192.0, 3: 192.0}
 # FP64 flux kernel: FP64 operations per face (DADD + DMUL + 2 DFMA counted from
 # the ncu SASS counters of k_flux on the stratified box).
 FP64_FLOP_PER_FACE = 807.0
+# Mixed flux kernel: FP32 operations per face (FADD + FMUL + 2 FFMA from the ncu
+# SASS counters of k_flux<float>); peak = 152 SMs x 128 FP32 lanes x 2 flop x
+# 2.07 GHz (measured FFMA probe: 73.2 TFLOP/s).
+FP32_FLOP_PER_FACE = 590.0
+FP32_NOMINAL_TFLOPS = 80.5
 
 
 def read_peaks():
@@ -65,7 +70,7 @@ class Clocks:
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem")
 
     def __init__(self, gpu_id):
         self.proc = None
@@ -85,7 +90,7 @@ class Clocks:
         except Exception:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
+        sm, mx, mem, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
@@ -99,11 +104,16 @@ class Clocks:
             for n, v in zip(names, parts[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+            if len(parts) > 8:
+                try:
+                    mem.append(float(parts[8]))
+                except ValueError:
+                    pass
         if not sm:
             return None
         load = [s for s in sm if s > 0.5 * max(sm)] or sm
         return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "mem_mhz": statistics.median(mem) if mem else None}
 
 
 def dist_init():
@@ -177,14 +187,17 @@ def roofline(kt, pr, form, hbm_peak, peak_kind):
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None, "peak_kind": f"{peak_kind} HBM copy",
                 "avg_launch_ms": avg_ms, "launches": launches}
-    if name.startswith("flux") and FP64_FLOP_PER_FACE:
+    if name.startswith("flux"):
         n = pr.n[0]
         faces = (n + 1) * (n + 2) * (n + 2)
-        achieved = faces * FP64_FLOP_PER_FACE / (avg_ms * 1e-3) / 1e12
-        peak = FP64_NOMINAL_TFLOPS
+        fp64 = form == "fp64"
+        flop = FP64_FLOP_PER_FACE if fp64 else FP32_FLOP_PER_FACE
+        peak = FP64_NOMINAL_TFLOPS if fp64 else FP32_NOMINAL_TFLOPS
+        achieved = faces * flop / (avg_ms * 1e-3) / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": "nominal FP64 (recipe)",
-                "avg_launch_ms": avg_ms, "launches": launches}
+                "frac": achieved / peak, "traffic": None,
+                "peak_kind": "nominal FP64 (recipe)" if fp64 else "nominal FP32 (152 SM x 128 lanes x 2.07 GHz)",
+                "flop_per_face": flop, "avg_launch_ms": avg_ms, "launches": launches}
     # HBM view of the whole stage for any other dominant kernel
     stage_ms = sum(v[1] for v in kt.values()) / max(kt.get("update_cells", (1, 0))[0], 1)
     per_stage = ncells * sum(BYTES_PER_CELL_STAGE.values()) / 3.0
@@ -192,6 +205,16 @@ def roofline(kt, pr, form, hbm_peak, peak_kind):
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": None, "peak_kind": f"{peak_kind} HBM copy",
             "avg_launch_ms": avg_ms, "launches": launches, "note": "whole-stage algorithmic bytes / stage time"}
+
+
+def stage_hbm(rate, form, hbm_peak, peak_kind):
+    """Whole stage against HBM: algorithmic bytes per cell-stage x rate.
+    FP64 form: read stage input + U^n, write output, FP64 (170.7 B average);
+    mixed form: FP64 U^n + FP32 increments (128 B average)."""
+    b = sum(BYTES_PER_CELL_STAGE.values()) / 3.0 if form == "fp64" else 128.0
+    gbs = rate * b / 1e9
+    return {"bytes_per_cell_stage": b, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+            "peak_kind": f"{peak_kind} HBM copy", "frac_of_8tbs": gbs / 8000.0}
 
 
 def e2e_measure(P, g, pr, steps):
@@ -313,7 +336,7 @@ def main():
         "e2e": e2e,
         "clocks": clk,
         "cpu_baseline": cpu,
-        "hbm_frac_of_8tbs": None if roof.get("unit") != "GB/s" else roof["achieved"] / 8000.0,
+        "stage_hbm": stage_hbm(value / max(ws, 1), args.form, hbm_peak, peak_kind),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -18,6 +18,15 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 
+# Translation units whose FP32 arithmetic uses the fast (approximate, ~2 ulp)
+# division and square root and flushes denormals: the mixed-precision stage
+# (its FP32 work is on well-balanced deviations; FP64 code is unaffected).
+PER_FILE_FLAGS = {
+    "kernels_mixed.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "unit_kernels.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+}
+
+
 def _nvcc():
     for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
         if c and (os.path.exists(c) or c == "nvcc"):
@@ -46,7 +55,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def comp(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + NVCC_FLAGS + PER_FILE_FLAGS.get(os.path.basename(src), []) + list(extra) + \
+            ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

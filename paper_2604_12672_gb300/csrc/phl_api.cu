@@ -61,9 +61,14 @@ struct phl_grid {
   double *U = nullptr, *U1 = nullptr, *B = nullptr, *B1 = nullptr, *T = nullptr;
   // background and heating profiles
   double *bg = nullptr, *heat = nullptr;
+  float *bgf = nullptr, *heatf = nullptr;
   // work
   double *W = nullptr, *F[3] = {nullptr, nullptr, nullptr}, *E = nullptr;
   uint8_t *raw = nullptr, *flag = nullptr;
+  // mixed precision: FP32 increments and work arrays
+  float *dUf = nullptr, *dBf = nullptr, *Wf = nullptr, *Ff[3] = {nullptr, nullptr, nullptr}, *Ef = nullptr;
+  unsigned int *fmax = nullptr;
+  bool mixed = false;
   // scalars
   double *dt = nullptr;
   unsigned long long *dmax = nullptr;
@@ -124,6 +129,14 @@ phl_status check_flags(phl_grid *g) {
   return PHL_OK;
 }
 
+void launch_dt(phl_grid *g, int *nl) {
+  Prof *pf = g->prof.on ? &g->prof : nullptr;
+  if (g->mixed)
+    launch_dt_mixed(g->G, g->U, g->B, g->fmax, g->dt, g->dflag, g->stream, nl, pf);
+  else
+    launch_dt_fp64(g->G, g->U, g->B, g->T, g->dmax, g->dt, g->dflag, g->stream, nl, pf);
+}
+
 void do_stage(phl_grid *g, const double *Uin, const double *Bin, double *Uout, double *Bout, double a,
               double b, int *nl) {
   StageBufs S;
@@ -159,7 +172,7 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   if (!(d->cfl > 0.0)) return fail(PHL_EINVAL, "cfl must be positive");
   if (d->rk != 2 && d->rk != 3) return fail(PHL_EINVAL, "rk must be 2 or 3");
   if (d->riemann < 0 || d->riemann > 2) return fail(PHL_EINVAL, "bad riemann solver");
-  if (d->precision != PHL_FP64) return fail(PHL_EUNSUPPORTED, "precision mode not available in this build");
+  if (d->precision != PHL_FP64 && d->precision != PHL_MIXED) return fail(PHL_EINVAL, "bad precision mode");
   if (d->bg_rho_c && (!d->bg_p_c || !d->bg_rho_f || !d->bg_p_f))
     return fail(PHL_EINVAL, "incomplete background profiles");
   const long ncell = (long)d->n[0] * d->n[1] * d->n[2];
@@ -197,6 +210,11 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   G.eps_sf = d->eps_sf;
   G.mach_thr = d->mach_thr;
   G.cfl = d->cfl;
+  for (int k = 0; k < 3; ++k) { G.idxf[k] = (float)G.idx[k]; G.gf[k] = (float)d->g[k]; }
+  G.gammaf = (float)d->gamma;
+  G.gm1f = (float)(d->gamma - 1.0);
+  G.machf = (float)d->mach_thr;
+  G.epsf = (float)d->eps_sf;
 
   phl_status st = PHL_OK;
 #define AL(p, n)                                  \
@@ -204,22 +222,34 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     st = dalloc(g, p, (size_t)(n));               \
     if (st != PHL_OK) { phl_destroy(g); return st; } \
   } while (0)
+  g->mixed = d->precision == PHL_MIXED;
   AL(&g->U, G.nv * G.plane);
-  AL(&g->U1, G.nv * G.plane);
   AL(&g->B, 3 * G.plane);
-  AL(&g->B1, 3 * G.plane);
-  AL(&g->W, (long)G.nw * G.wtot);
-  for (int k = 0; k < 3; ++k)
-    if (G.act[k]) AL(&g->F[k], (long)(G.nf + 1) * G.wtot);   // + contact direction
-  AL(&g->E, 3 * G.wtot);
-  AL(&g->raw, ncell);
+  if (!g->mixed) {
+    AL(&g->U1, G.nv * G.plane);
+    AL(&g->B1, 3 * G.plane);
+    AL(&g->W, (long)G.nw * G.wtot);
+    for (int k = 0; k < 3; ++k)
+      if (G.act[k]) AL(&g->F[k], (long)(G.nf + 1) * G.wtot);   // + contact direction
+    AL(&g->E, 3 * G.wtot);
+  } else {
+    AL(&g->dUf, G.nv * G.plane);
+    AL(&g->dBf, 3 * G.plane);
+    AL(&g->Wf, (long)G.nw * G.wtot);
+    for (int k = 0; k < 3; ++k)
+      if (G.act[k]) AL(&g->Ff[k], (long)(G.nf + 1) * G.wtot);
+    AL(&g->Ef, 3 * G.wtot);
+    AL(&g->fmax, 1);
+  }
+  AL(&g->raw, 2 * ncell);   // raw flags + one dilation pass buffer
   AL(&g->flag, G.wtot);
   AL(&g->dt, 1);
   AL(&g->dmax, 1);
   AL(&g->dflag, 1);
   const int nz = d->n[2];
-  const long nbg = 8L * (nz + 2 * BG_NG + 1);
+  const long nbg = 9L * (nz + 2 * BG_NG + 1);   // 8 profiles + E_hat at centres
   AL(&g->bg, nbg);
+  AL(&g->bgf, nbg);
   if (d->bg_rho_c) {
     std::vector<double> h(nbg, 0.0);
     const long L = nz + 2 * BG_NG + 1;
@@ -230,8 +260,19 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
       const long cnt = (q == 2 || q == 3 || q == 6 || q == 7) ? L : L - 1;
       memcpy(&h[q * L], src[q], cnt * sizeof(double));
     }
+    for (long q = 0; q < L - 1; ++q) h[8 * L + q] = d->bg_p_c[q] / (d->gamma - 1.0);   // E_hat
+    std::vector<float> hf(nbg);
+    for (long q = 0; q < nbg; ++q) hf[q] = (float)h[q];
     cudaError_t e = cudaMemcpy(g->bg, h.data(), nbg * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { phl_destroy(g); return cuda_fail(e, "copy background"); }
+    e = cudaMemcpy(g->bgf, hf.data(), nbg * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { phl_destroy(g); return cuda_fail(e, "copy background"); }
+    G.bgf_rho_c = g->bgf; G.bgf_p_c = g->bgf + L; G.bgf_rho_f = g->bgf + 2 * L; G.bgf_p_f = g->bgf + 3 * L;
+    G.bgf_ge_c = d->bg_ge_c ? g->bgf + 4 * L : nullptr;
+    G.bgf_gc_c = d->bg_gc_c ? g->bgf + 5 * L : nullptr;
+    G.bgf_ge_f = d->bg_ge_f ? g->bgf + 6 * L : nullptr;
+    G.bgf_gc_f = d->bg_gc_f ? g->bgf + 7 * L : nullptr;
+    G.bg_e_c = g->bg + 8 * L;
     G.has_bg = 1;
     G.bg_rho_c = g->bg; G.bg_p_c = g->bg + L; G.bg_rho_f = g->bg + 2 * L; G.bg_p_f = g->bg + 3 * L;
     G.bg_ge_c = d->bg_ge_c ? g->bg + 4 * L : nullptr;
@@ -241,9 +282,14 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   }
   if (d->heat) {
     AL(&g->heat, nz);
+    AL(&g->heatf, nz);
+    std::vector<float> hf(nz);
+    for (int q = 0; q < nz; ++q) hf[q] = (float)d->heat[q];
     cudaError_t e = cudaMemcpy(g->heat, d->heat, nz * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->heatf, hf.data(), nz * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { phl_destroy(g); return cuda_fail(e, "copy heating"); }
     G.heat = g->heat;
+    G.heatf = g->heatf;
   }
 #undef AL
   *out = g;
@@ -301,7 +347,7 @@ phl_status phl_get_state(phl_grid *g, double *cons, double *bx, double *by, doub
 phl_status phl_compute_dt(phl_grid *g, double *dt_out) {
   if (!g || !dt_out) return fail(PHL_EINVAL, "null argument");
   int nl = 0;
-  launch_dt_fp64(g->G, g->U, g->B, g->T, g->dmax, g->dt, g->dflag, g->stream, &nl, g->prof.on ? &g->prof : nullptr);
+  launch_dt(g, &nl);
   CK(cudaGetLastError(), "launch dt");
   CK(cudaMemcpyAsync(dt_out, g->dt, sizeof(double), cudaMemcpyDeviceToHost, g->stream), "read dt");
   phl_status st = check_flags(g);
@@ -319,10 +365,19 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
       launch_set_scalar(g->dt, dt, g->stream, g->prof.on ? &g->prof : nullptr);
       ++nl;
     } else {
-      launch_dt_fp64(g->G, g->U, g->B, g->T, g->dmax, g->dt, g->dflag, g->stream, &nl,
-                     g->prof.on ? &g->prof : nullptr);
+      launch_dt(g, &nl);
     }
-    if (g->desc.rk == 2) {
+    if (g->mixed) {
+      const double bs3[3] = {1.0, 0.25, 2.0 / 3.0}, bs2[2] = {1.0, 0.5};
+      const int ns = g->desc.rk == 2 ? 2 : 3;
+      MixedBufs M;
+      M.U = g->U; M.B = g->B; M.dU = g->dUf; M.dB = g->dBf; M.W = g->Wf;
+      M.F[0] = g->Ff[0]; M.F[1] = g->Ff[1]; M.F[2] = g->Ff[2]; M.E = g->Ef;
+      M.raw = g->raw; M.flag = g->flag; M.dt = g->dt; M.dflag = g->dflag;
+      for (int st = 0; st < ns; ++st)
+        launch_stage_mixed(g->G, M, st, ns, ns == 2 ? bs2[st] : bs3[st], g->stream, &nl,
+                           g->prof.on ? &g->prof : nullptr);
+    } else if (g->desc.rk == 2) {
       do_stage(g, g->U, g->B, g->U1, g->B1, 0.0, 1.0, &nl);
       do_stage(g, g->U1, g->B1, g->U, g->B, 0.5, 0.5, &nl);
     } else {

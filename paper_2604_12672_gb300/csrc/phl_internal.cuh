@@ -53,6 +53,12 @@ struct DevGeo {
   double g[3];
   int riemann;
   double eps_sf, mach_thr, cfl;
+  // FP32 copies for the mixed-precision kernels (no per-thread conversions)
+  float idxf[3], gf[3], gammaf, gm1f, machf, epsf;
+  const float *bgf_rho_c, *bgf_p_c, *bgf_rho_f, *bgf_p_f;   // null without background
+  const float *bgf_ge_c, *bgf_gc_c, *bgf_ge_f, *bgf_gc_f;
+  const float *heatf;
+  const double *bg_e_c;        // E_hat = P_hat / (gamma - 1) at cell centres (FP64)
 };
 
 __host__ __device__ __forceinline__ long sidx(const DevGeo &G, int i, int j, int k) {
@@ -102,6 +108,78 @@ __device__ __forceinline__ Bg bg_zface(const DevGeo &G, int k) {
   return b;
 }
 
+// The background in the arithmetic type of a kernel: FP64 profiles for double,
+// their FP32 copies for float.
+template <typename R>
+struct BgT { R rho, p, ge, gc; };
+template <typename R>
+__device__ __forceinline__ BgT<R> bg_cell_t(const DevGeo &G, int k);
+template <typename R>
+__device__ __forceinline__ BgT<R> bg_zface_t(const DevGeo &G, int k);
+template <>
+__device__ __forceinline__ BgT<double> bg_cell_t<double>(const DevGeo &G, int k) {
+  const Bg b = bg_cell(G, k);
+  return BgT<double>{b.rho, b.p, b.ge, b.gc};
+}
+template <>
+__device__ __forceinline__ BgT<double> bg_zface_t<double>(const DevGeo &G, int k) {
+  const Bg b = bg_zface(G, k);
+  return BgT<double>{b.rho, b.p, b.ge, b.gc};
+}
+template <>
+__device__ __forceinline__ BgT<float> bg_cell_t<float>(const DevGeo &G, int k) {
+  BgT<float> b{0.0f, 0.0f, 0.0f, 0.0f};
+  if (G.has_bg) {
+    b.rho = G.bgf_rho_c[k + BG_NG];
+    b.p = G.bgf_p_c[k + BG_NG];
+    b.ge = G.bgf_ge_c ? G.bgf_ge_c[k + BG_NG] : G.gammaf;
+    b.gc = G.bgf_gc_c ? G.bgf_gc_c[k + BG_NG] : G.gammaf;
+  }
+  return b;
+}
+template <>
+__device__ __forceinline__ BgT<float> bg_zface_t<float>(const DevGeo &G, int k) {
+  BgT<float> b{0.0f, 0.0f, 0.0f, 0.0f};
+  if (G.has_bg) {
+    b.rho = G.bgf_rho_f[k + BG_NG];
+    b.p = G.bgf_p_f[k + BG_NG];
+    b.ge = G.bgf_ge_f ? G.bgf_ge_f[k + BG_NG] : G.gammaf;
+    b.gc = G.bgf_gc_f ? G.bgf_gc_f[k + BG_NG] : G.gammaf;
+  }
+  return b;
+}
+template <typename R> __device__ __forceinline__ R mach_thr_t(const DevGeo &G);
+template <> __device__ __forceinline__ double mach_thr_t<double>(const DevGeo &G) { return G.mach_thr; }
+template <> __device__ __forceinline__ float mach_thr_t<float>(const DevGeo &G) { return G.machf; }
+template <typename R> __device__ __forceinline__ R eps_sf_t(const DevGeo &G);
+template <> __device__ __forceinline__ double eps_sf_t<double>(const DevGeo &G) { return G.eps_sf; }
+template <> __device__ __forceinline__ float eps_sf_t<float>(const DevGeo &G) { return G.epsf; }
+
+// IEEE binary64 <-> binary32 conversions done on the integer pipe (the FP64
+// pipe, which also executes the conversion instructions, runs at 1/64 of the
+// FP32 rate on this GPU).  d2f_bits rounds to nearest (ties away from zero,
+// vs. ties-to-even of a hardware conversion), flushes |x| < 2^-126 to zero and
+// maps overflow to infinity; f2d_bits is exact for normal floats and zero.
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u, a = hi & 0x7fffffffu;
+  // exponent rebias 1023 -> 127 inside the high word, then 20 + 3 mantissa bits
+  unsigned t = __funnelshift_l(lo, a - (896u << 20), 3);
+  t += (lo >> 28) & 1u;
+  t = (a < (897u << 20)) ? 0u : t;
+  t = (a >= (1151u << 20)) ? (0x7f800000u | ((a > 0x7ff00000u || (a == 0x7ff00000u && lo)) ? 0x400000u : 0u)) : t;
+  return __uint_as_float(t | sign);
+}
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+  unsigned lo = m << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 255u) hi = sign | 0x7ff00000u | (m >> 3);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // Kernel classes for the optional per-kernel event timing.
 enum KClass {
   KC_PRIM = 0, KC_FLAG_RAW, KC_FLAG_DILATE, KC_FLUX_X, KC_FLUX_Y, KC_FLUX_Z, KC_EMF, KC_UPDATE_CELLS,
@@ -138,6 +216,21 @@ struct StageBufs {
   double *T;                   // temperature (stellar), state layout
   int *dflag;                  // device error word
 };
+
+// Buffers of the mixed-precision stage (kernels_mixed.cu): FP64 U^n, FP32
+// stage increments and FP32 work arrays.
+struct MixedBufs {
+  double *U, *B;               // U^n cells / faces (padded state layout)
+  float *dU, *dB;              // stage increments, same layout
+  float *W, *F[3], *E;         // work arrays (work layout)
+  uint8_t *raw, *flag;
+  const double *dt;
+  int *dflag;
+};
+void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
+                        int *nlaunch, Prof *prof);
+void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigned int *fmax_bits, double *dt,
+                     int *dflag, cudaStream_t s, int *nlaunch, Prof *prof);
 
 // Records the calling thread's last-error message (phl_last_error) and
 // returns st (phl_api.cu).

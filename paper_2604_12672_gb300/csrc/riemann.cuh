@@ -140,28 +140,37 @@ __device__ __forceinline__ int contact_dir(R frho, R rhol, R rhor, R SL, R SR) {
 // wl, wr: normal-frame deviation states (RD_* order) with nspec mass fractions.
 // Background at the face: rh, ph, geh, gch (all 0 without a background).
 // f: F - F_hat in RF_* order (7 + nspec values).
-template <typename R>
-__device__ void riemann_dev(const R *wl, const R *wr, R bn, R rh, R ph, R geh, R gch, int nspec,
-                            int solver, R mthr, R *f, int &up) {
+// NS: compile-time capacity for mass fractions (loops unroll; nspec <= NS).
+template <typename R, int NS>
+__device__ __forceinline__ void riemann_dev(const R *wl, const R *wr, R bn, R rh, R ph, R geh, R gch, int nspec,
+                                            int solver, R mthr, R *f, int &up) {
   Side<R> L, R_;
   side_init(L, wl, bn, rh, ph, geh, gch);
   side_init(R_, wr, bn, rh, ph, geh, gch);
   const R SL = fmin(L.un - L.cf, R_.un - R_.cf);
   const R SR = fmax(L.un + L.cf, R_.un + R_.cf);
-  R xl[PHL_NSPEC_MAX], xr[PHL_NSPEC_MAX];
+  R xl[NS > 0 ? NS : 1], xr[NS > 0 ? NS : 1];
   {
     R sl = R(0), sr = R(0);
-    for (int l = 0; l < nspec; ++l) { sl += wl[RD_X0 + l]; sr += wr[RD_X0 + l]; }
-    for (int l = 0; l < nspec; ++l) { xl[l] = wl[RD_X0 + l] / sl; xr[l] = wr[RD_X0 + l] / sr; }
+#pragma unroll
+    for (int l = 0; l < NS; ++l)
+      if (l < nspec) { sl += wl[RD_X0 + l]; sr += wr[RD_X0 + l]; }
+#pragma unroll
+    for (int l = 0; l < NS; ++l)
+      if (l < nspec) { xl[l] = wl[RD_X0 + l] / sl; xr[l] = wr[RD_X0 + l] / sr; }
   }
 
   if (solver == SOLVER_HLL) {
     if (SL >= R(0)) {
       for (int q = 0; q < 7; ++q) f[q] = L.F[q];
-      for (int l = 0; l < nspec; ++l) f[RF_X0 + l] = L.F[RF_RHO] * xl[l];
+#pragma unroll
+      for (int l = 0; l < NS; ++l)
+        if (l < nspec) f[RF_X0 + l] = L.F[RF_RHO] * xl[l];
     } else if (SR <= R(0)) {
       for (int q = 0; q < 7; ++q) f[q] = R_.F[q];
-      for (int l = 0; l < nspec; ++l) f[RF_X0 + l] = R_.F[RF_RHO] * xr[l];
+#pragma unroll
+      for (int l = 0; l < NS; ++l)
+        if (l < nspec) f[RF_X0 + l] = R_.F[RF_RHO] * xr[l];
     } else {
       R dU[7];
       dU[RF_RHO] = wr[RD_RHO] - wl[RD_RHO];
@@ -173,9 +182,11 @@ __device__ void riemann_dev(const R *wl, const R *wr, R bn, R rh, R ph, R geh, R
       dU[RF_BT2] = R_.bt2 - L.bt2;
       const R idn = R(1) / (SR - SL);
       for (int q = 0; q < 7; ++q) f[q] = (SR * L.F[q] - SL * R_.F[q] + SL * SR * dU[q]) * idn;
-      for (int l = 0; l < nspec; ++l)
-        f[RF_X0 + l] = (SR * L.F[RF_RHO] * xl[l] - SL * R_.F[RF_RHO] * xr[l] +
-                        SL * SR * (R_.rho * xr[l] - L.rho * xl[l])) * idn;
+#pragma unroll
+      for (int l = 0; l < NS; ++l)
+        if (l < nspec)
+          f[RF_X0 + l] = (SR * L.F[RF_RHO] * xl[l] - SL * R_.F[RF_RHO] * xr[l] +
+                          SL * SR * (R_.rho * xr[l] - L.rho * xl[l])) * idn;
     }
     up = contact_dir(f[RF_RHO], L.rho, R_.rho, SL, SR);
     return;
@@ -250,7 +261,9 @@ __device__ void riemann_dev(const R *wl, const R *wr, R bn, R rh, R ph, R geh, R
     }
   }
   for (int q = 0; q < 7; ++q) f[q] = F[q];
-  for (int l = 0; l < nspec; ++l) f[RF_X0 + l] = F[RF_RHO] * (left ? xl[l] : xr[l]);
+#pragma unroll
+  for (int l = 0; l < NS; ++l)
+    if (l < nspec) f[RF_X0 + l] = F[RF_RHO] * (left ? xl[l] : xr[l]);
   up = contact_dir(F[RF_RHO], L.rho, R_.rho, SL, SR);
 }
 

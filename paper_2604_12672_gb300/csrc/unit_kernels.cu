@@ -17,7 +17,7 @@ __global__ void k_riemann_batch(long n, const double *wl, const double *wr, cons
     R a[9 + PHL_NSPEC_MAX], b[9 + PHL_NSPEC_MAX], out[7 + PHL_NSPEC_MAX];
     for (int q = 0; q < nw; ++q) { a[q] = (R)wl[t * nw + q]; b[q] = (R)wr[t * nw + q]; }
     int up;
-    riemann_dev<R>(a, b, (R)bn[t], (R)bg[4 * t], (R)bg[4 * t + 1], (R)bg[4 * t + 2], (R)bg[4 * t + 3], nspec,
+    riemann_dev<R, PHL_NSPEC_MAX>(a, b, (R)bn[t], (R)bg[4 * t], (R)bg[4 * t + 1], (R)bg[4 * t + 2], (R)bg[4 * t + 3], nspec,
                    solver, (R)mthr, out, up);
     for (int q = 0; q < nf; ++q) f[t * nf + q] = (double)out[q];
   }
