@@ -200,6 +200,39 @@ phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const d
 phl_status phl_cfl_dt_noalloc(const phl_grid_desc *desc, const double *cons, const double *bx,
                               const double *by, const double *bz, double *dt_out, void *stream);
 
+/* ---------------- stellar equation of state (Sect. 2.2, item ii) --------
+ * Ions (ideal gas), radiation (Eqs. prad, erad) and an electron-positron gas
+ * of arbitrary degeneracy and relativity in pair equilibrium.  The e-/e+ part
+ * is a table of its Helmholtz free-energy density over (ln n_e, ln T),
+ * n_e = rho Y_e N_A, with f_x, f_y, f_xy at each node, computed on the device
+ * from generalised Fermi-Dirac integrals, and interpolated by bicubic
+ * Hermite polynomials; P, e, c_v and the pressure derivatives all derive from
+ * that one interpolant.  CGS units. */
+typedef struct phl_eos_table phl_eos_table;
+
+/* Build the table on the current device: log10(rho Y_e) in [lrhoye_lo,
+ * lrhoye_hi] with nrho nodes, log10 T in [lT_lo, lT_hi] with nT nodes.
+ * Errors: PHL_EINVAL, PHL_ENOMEM, PHL_ENEWTON (a node did not converge). */
+phl_status phl_eos_table_create(double lrhoye_lo, double lrhoye_hi, int nrho, double lT_lo,
+                                double lT_hi, int nT, phl_eos_table **out);
+void phl_eos_table_destroy(phl_eos_table *t);
+/* Copy the node data to host: [nx, ny, x0, dx, y0, dy, (f, f_x, f_y, f_xy)...]
+ * (6 + 4 nx ny doubles); for tests. */
+phl_status phl_eos_table_export(const phl_eos_table *t, double *out, long nout);
+
+/* Batch EOS: for each i, temperature from (rho, e_int) by Newton
+ * T <- T + (e - e_EoS) / c_v until |de|/e < tol, then one more step
+ * (Sect. 2.2); T_inout holds the first guess and receives T.  Outputs (may
+ * be NULL except T_inout): P, gamma_e = P/(rho e) + 1, gamma_c = rho c_s^2 / P,
+ * c_s, Newton iterations (-1: no convergence).  abar, ye: mean mass number
+ * and electron fraction per element.  precision = PHL_FP64: FP64 Newton;
+ * PHL_MIXED: FP32 Newton to 1e-6 then one FP64 step.  where = PHL_HOST (host
+ * arrays, synchronous) or PHL_DEVICE (device arrays, asynchronous on stream). */
+phl_status phl_eos(const phl_eos_table *t, long n, const double *rho, const double *eint,
+                   const double *abar, const double *ye, double *T_inout, double *P,
+                   double *gamma_e, double *gamma_c, double *cs, int *iters, int precision,
+                   double tol, int maxit, int where, void *stream);
+
 void phl_destroy(phl_grid *g);
 
 /* Message describing the calling thread's last failure ("" if none). */

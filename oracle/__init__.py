@@ -53,6 +53,23 @@ def lib():
         L.ora_riemann.argtypes = [_dp, _dp, C.c_double, C.c_int, C.c_int, C.c_double, _dp]
         L.ora_divb.restype = C.c_double
         L.ora_divb.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp]
+        L.ora_eos_table_build.restype = C.c_void_p
+        L.ora_eos_table_build.argtypes = [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int]
+        L.ora_eos_table_free.restype = None
+        L.ora_eos_table_free.argtypes = [C.c_void_p]
+        L.ora_eos_table_size.restype = C.c_long
+        L.ora_eos_table_size.argtypes = [C.c_void_p]
+        L.ora_eos_table_export.restype = C.c_int
+        L.ora_eos_table_export.argtypes = [C.c_void_p, _dp, C.c_long]
+        L.ora_ep_direct.restype = C.c_int
+        L.ora_ep_direct.argtypes = [C.c_double, C.c_double, C.c_double] + [_dp] * 5
+        L.ora_fd.restype = C.c_double
+        L.ora_fd.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.ora_eos_rt.restype = C.c_int
+        L.ora_eos_rt.argtypes = [C.POINTER(OraCfg), C.c_double, C.c_double, _dp] + [_dp] * 7
+        L.ora_eos_invert.restype = C.c_int
+        L.ora_eos_invert.argtypes = [C.POINTER(OraCfg), C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp,
+                                     C.POINTER(C.c_int)]
         L.ora_mlp_forward.restype = None
         L.ora_mlp_forward.argtypes = [_dp, C.c_int, C.c_int, _dp, C.c_long, _dp]
         L.ora_mlp_loss_grad.restype = C.c_double
@@ -162,6 +179,72 @@ class Oracle:
         if rc != 0:
             raise RuntimeError(f"oracle stage failed with code {rc}")
         return dict(cons=cons_o, bx=bo[0], by=bo[1], bz=bo[2], T=T)
+
+
+class EosTable:
+    """The oracle's own e-/e+ free-energy table (its own quadrature)."""
+
+    def __init__(self, lrhoye=(4.0, 8.0), nrho=161, lT=(7.0, 10.0), nT=121):
+        self.h = lib().ora_eos_table_build(lrhoye[0], lrhoye[1], nrho, lT[0], lT[1], nT)
+        if not self.h:
+            raise RuntimeError("oracle EOS table build failed")
+
+    def export(self):
+        n = lib().ora_eos_table_size(self.h)
+        out = np.zeros(n)
+        lib().ora_eos_table_export(self.h, _ptr(out), n)
+        return out
+
+    def __del__(self):
+        try:
+            lib().ora_eos_table_free(self.h)
+        except Exception:
+            pass
+
+
+def stellar_cfg(A, Z, table=None, tol=1e-11, maxit=50):
+    c = OraCfg()
+    c.eos = 1
+    c.nspec = len(A)
+    for l, (a, z) in enumerate(zip(A, Z)):
+        c.A[l], c.Z[l] = a, z
+    c.newton_tol = tol
+    c.newton_maxit = maxit
+    c.eos_table = table.h if table is not None else None
+    return c
+
+
+def eos_rt(cfg, rho, T, X):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    o = [C.c_double() for _ in range(7)]
+    rc = lib().ora_eos_rt(C.byref(cfg), rho, T, _ptr(X), *[C.byref(v) for v in o])
+    if rc:
+        raise RuntimeError(f"oracle EOS failed ({rc})")
+    return dict(zip(("P", "e", "cv", "dPdr", "dPdT", "gamma_e", "gamma_c"), [v.value for v in o]))
+
+
+def eos_invert(cfg, rho, eint, X, T_guess):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    T = C.c_double(T_guess)
+    P, ge, gc = C.c_double(), C.c_double(), C.c_double()
+    it = C.c_int()
+    rc = lib().ora_eos_invert(C.byref(cfg), rho, eint, _ptr(X), C.byref(T), C.byref(P), C.byref(ge), C.byref(gc),
+                              C.byref(it))
+    if rc:
+        raise RuntimeError(f"oracle EOS inversion failed ({rc})")
+    return dict(T=T.value, P=P.value, gamma_e=ge.value, gamma_c=gc.value, iters=it.value)
+
+
+def ep_direct(rho, ye, T):
+    o = [C.c_double() for _ in range(5)]
+    rc = lib().ora_ep_direct(rho, ye, T, *[C.byref(v) for v in o])
+    if rc:
+        raise RuntimeError("oracle e-/e+ evaluation failed")
+    return dict(zip(("P", "e", "s", "eta", "npos"), [v.value for v in o]))
+
+
+def fd(k, eta, beta):
+    return lib().ora_fd(k, eta, beta)
 
 
 def riemann(wl, wr, bn, solver="lhlld", mach_thr=0.6, nspec=0):

@@ -76,6 +76,12 @@ _SIGS = {
     "phl_last_error": (C.c_char_p, []),
     "phl_cfl_dt_noalloc": (C.c_int, [C.POINTER(GridDesc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p]),
+    "phl_eos_table_create": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
+                                       C.POINTER(C.c_void_p)]),
+    "phl_eos_table_destroy": (None, [C.c_void_p]),
+    "phl_eos_table_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long]),
+    "phl_eos": (C.c_int, [C.c_void_p, C.c_long] + [C.c_void_p] * 10 + [C.c_int, C.c_double, C.c_int, C.c_int,
+                                                                          C.c_void_p]),
     "phl_riemann_batch": (C.c_int, [C.c_long, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_int, C.c_double, C.c_int, C.c_void_p]),
 }
@@ -136,6 +142,50 @@ def cfl_dt_noalloc(grid_or_desc, cons, bx, by, bz, dt_out, stream=None):
     d = grid_or_desc.desc if isinstance(grid_or_desc, Grid) else grid_or_desc
     ptrs = [_ptr(a)[0] for a in (cons, bx, by, bz, dt_out)]
     _check(lib().phl_cfl_dt_noalloc(C.byref(d), *ptrs, stream))
+
+
+class EosTable:
+    """Stellar EOS table on the current device (phl_eos_table_create)."""
+
+    def __init__(self, lrhoye=(4.0, 8.0), nrho=161, lT=(7.0, 10.0), nT=121):
+        h = C.c_void_p()
+        _check(lib().phl_eos_table_create(lrhoye[0], lrhoye[1], nrho, lT[0], lT[1], nT, C.byref(h)))
+        self.h = h
+        self.shape = (nrho, nT)
+
+    def export(self):
+        n = 6 + 4 * self.shape[0] * self.shape[1]
+        out = np.zeros(n)
+        _check(lib().phl_eos_table_export(self.h, out.ctypes.data, n))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().phl_eos_table_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def eos(table, rho, eint, abar, ye, T_guess, precision="fp64", tol=1e-11, maxit=50):
+    """Batch stellar EOS on host arrays; returns dict of T, P, gamma_e, gamma_c, cs, iters."""
+    arr = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    rho, eint, abar, ye = arr(rho), arr(eint), arr(abar), arr(ye)
+    T = arr(T_guess).copy()
+    n = rho.size
+    out = {k: np.zeros(n) for k in ("P", "gamma_e", "gamma_c", "cs")}
+    it = np.zeros(n, dtype=np.int32)
+    _check(lib().phl_eos(table.h, n, rho.ctypes.data, eint.ctypes.data, abar.ctypes.data, ye.ctypes.data,
+                         T.ctypes.data, out["P"].ctypes.data, out["gamma_e"].ctypes.data,
+                         out["gamma_c"].ctypes.data, out["cs"].ctypes.data, it.ctypes.data,
+                         PRECISION[precision], tol, maxit, HOST, None))
+    out["T"] = T
+    out["iters"] = it
+    return out
 
 
 class Grid:

@@ -1,0 +1,296 @@
+// eos.cu -- the stellar EOS table, built on the device from Fermi-Dirac
+// integrals, and the batch EOS entry point phl_eos.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "eos_stellar.cuh"
+#include "phl.h"
+#include "phl_internal.cuh"
+
+using namespace phl;
+using namespace phl::eos;
+
+struct phl_eos_table {
+  Table t;
+  double *dv = nullptr;
+  float *dvf = nullptr;
+};
+
+namespace {
+
+constexpr int GLN = 32;   // Gauss-Legendre order of the integral panels
+__constant__ double c_glx[GLN], c_glw[GLN];
+
+// Gauss-Legendre nodes/weights on [-1, 1]: Newton on the Legendre recurrence.
+void gauss_legendre(int n, double *x, double *w) {
+  for (int i = 0; i < n; ++i) {
+    double z = cos(PI_D * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// One species at (eta, b): F_1/2, F_3/2, F_5/2, dF_{1/2,3/2}/deta, dF_{1/2,3/2}/db.
+// Integration variable s with x = s^2; panels refine around the Fermi edge.
+__device__ void fd_integrals(double eta, double b, double *F) {
+  for (int q = 0; q < 7; ++q) F[q] = 0.0;
+  const double se = eta > 0.0 ? sqrt(eta) : 0.0;
+  const double wd = 0.5 / fmax(se, 0.5);      // width of the edge in s
+  const double smax = sqrt(fmax(eta, 0.0) + 100.0);
+  double edge[9] = {0.0, se - 12.0 * wd, se - 4.0 * wd, se - 1.5 * wd, se, se + 1.5 * wd, se + 4.0 * wd,
+                    se + 12.0 * wd, smax};
+  for (int k = 0; k < 9; ++k) edge[k] = fmin(fmax(edge[k], 0.0), smax);
+  for (int k = 1; k < 9; ++k)   // insertion sort (edges already nearly sorted)
+    for (int m = k; m > 0 && edge[m] < edge[m - 1]; --m) { const double t = edge[m]; edge[m] = edge[m - 1]; edge[m - 1] = t; }
+  for (int pnl = 0; pnl < 8; ++pnl) {
+    const double a = edge[pnl], c = edge[pnl + 1];
+    if (!(c > a)) continue;
+    const int nsub = 3;
+    for (int sb = 0; sb < nsub; ++sb) {
+      const double lo = a + (c - a) * sb / nsub, hi = a + (c - a) * (sb + 1) / nsub;
+      const double hm = 0.5 * (hi - lo), cm = 0.5 * (hi + lo);
+      for (int g = 0; g < GLN; ++g) {
+        const double s = cm + hm * c_glx[g];
+        const double wgt = 2.0 * s * hm * c_glw[g];   // dx = 2 s ds
+        const double x = s * s, u = x - eta;
+        const double z = exp(-fabs(u));
+        const double fermi = u > 0.0 ? z / (1.0 + z) : 1.0 / (1.0 + z);
+        const double fder = z / ((1.0 + z) * (1.0 + z));   // f (1 - f)
+        const double S = sqrt(1.0 + 0.5 * b * x);
+        const double x12 = s, x32 = x * s, x52 = x * x * s;
+        F[0] += wgt * x12 * S * fermi;
+        F[1] += wgt * x32 * S * fermi;
+        F[2] += wgt * x52 * S * fermi;
+        F[3] += wgt * x12 * S * fder;
+        F[4] += wgt * x32 * S * fder;
+        F[5] += wgt * x32 * fermi / (4.0 * S);
+        F[6] += wgt * x52 * fermi / (4.0 * S);
+      }
+    }
+  }
+}
+
+struct Species { double n, n_eta, n_b, P, Ek; };
+
+__device__ Species species(double eta, double b, double lam3) {
+  double F[7];
+  fd_integrals(eta, b, F);
+  const double Kn = 8.0 * PI_D * sqrt(2.0) * lam3;
+  const double rb = sqrt(b), b32 = b * rb, b52 = b * b * rb;
+  Species s;
+  s.n = Kn * b32 * (F[0] + b * F[1]);
+  s.n_eta = Kn * b32 * (F[3] + b * F[4]);
+  s.n_b = Kn * (1.5 * rb * (F[0] + b * F[1]) + b32 * (F[5] + F[1] + b * F[6]));
+  s.P = (2.0 / 3.0) * Kn * MEC2 * b52 * (F[1] + 0.5 * b * F[2]);
+  s.Ek = Kn * MEC2 * b52 * (F[1] + b * F[2]);
+  return s;
+}
+
+// Free-energy node of the e-/e+ gas at net density ne and temperature T.
+__global__ void k_table_nodes(int nx, int ny, double x0, double dx, double y0, double dy, double lam3,
+                              double *v, int *fail) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nx * ny) return;
+  const int i = idx % nx, j = idx / nx;
+  const double ne = exp(x0 + i * dx), T = exp(y0 + j * dy);
+  const double b = KB * T / MEC2, kT = KB * T;
+  // charge neutrality n-(eta) - n+(-eta - 2/b) = ne: bracketed Newton
+  const double Kn = 8.0 * PI_D * sqrt(2.0) * lam3;
+  const double xf = cbrt(3.0 * ne / (8.0 * PI_D * lam3));
+  double eta = fmax(log(ne / (Kn * b * sqrt(b) * 0.886226925452758)), (sqrt(1.0 + xf * xf) - 1.0) / b);
+  double lo = -700.0, hi = 1e7;
+  bool ok = false;
+  Species m, p;
+  for (int it = 0; it < 200; ++it) {
+    m = species(eta, b, lam3);
+    p = species(-eta - 2.0 / b, b, lam3);
+    const double r = m.n - p.n - ne;
+    if (r > 0.0) hi = eta; else lo = eta;
+    double en = eta - r / (m.n_eta + p.n_eta);
+    if (!(en > lo && en < hi)) en = 0.5 * (lo + hi);
+    const bool done = fabs(en - eta) <= 1e-15 * (fabs(eta) + 1.0) || hi - lo < 1e-14 * (fabs(eta) + 1.0);
+    eta = en;
+    if (done) { ok = true; break; }
+  }
+  if (!ok) { atomicOr(fail, 1); return; }
+  const double etap = -eta - 2.0 / b;
+  m = species(eta, b, lam3);
+  p = species(etap, b, lam3);
+  const double Ts = (m.Ek + m.P - eta * kT * m.n) + (p.Ek + p.P - etap * kT * p.n);
+  const double deta_db = -(m.n_b - (p.n_b + p.n_eta * 2.0 / (b * b))) / (m.n_eta + p.n_eta);
+  double *o = v + 4L * idx;
+  o[0] = ne * eta * kT - (m.P + p.P);     // f
+  o[1] = ne * eta * kT;                   // f_x
+  o[2] = -Ts;                             // f_y
+  o[3] = ne * kT * (eta + deta_db * b);   // f_xy
+}
+
+template <typename R>
+__global__ void k_eos_batch(Table t, long n, const double *rho, const double *eint, const double *abar,
+                            const double *ye, double *T, double *P, double *ge, double *gc, double *cs, int *iters,
+                            double tol, int maxit, int final64) {
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  EosOut<R> o;
+  R Tr = (R)T[i];
+  int it = eos_invert<R>(t, (R)rho[i], (R)eint[i], (R)abar[i], (R)ye[i], Tr, (R)tol, maxit, o);
+  double Td = (double)Tr;
+  EosOut<double> od;
+  bool ok = it > 0;
+  if (ok && final64) {   // final Newton step in FP64
+    ok = eos_rt<double>(t, rho[i], Td, abar[i], ye[i], od);
+    if (ok) {
+      Td = Td + (eint[i] - od.e) / od.cv;
+      ok = eos_rt<double>(t, rho[i], Td, abar[i], ye[i], od);
+    }
+  } else {
+    od.P = o.P; od.ge = o.ge; od.gc = o.gc;
+  }
+  T[i] = Td;
+  if (P) P[i] = ok ? od.P : NAN;
+  if (ge) ge[i] = od.ge;
+  if (gc) gc[i] = od.gc;
+  if (cs) cs[i] = sqrt(od.gc * od.P / rho[i]);
+  if (iters) iters[i] = ok ? it : -1;
+}
+
+}  // namespace
+
+namespace phl {
+// Table view for the stage kernels (phl_api.cu)
+const Table *eos_table_view(const phl_eos_table *t) { return t ? &t->t : nullptr; }
+}  // namespace phl
+
+extern "C" {
+
+phl_status phl_eos_table_create(double lrhoye_lo, double lrhoye_hi, int nrho, double lT_lo, double lT_hi, int nT,
+                                phl_eos_table **out) {
+  if (!out || nrho < 4 || nT < 4 || !(lrhoye_hi > lrhoye_lo) || !(lT_hi > lT_lo))
+    return (phl_status)set_error(PHL_EINVAL, "phl_eos_table_create: bad arguments");
+  *out = nullptr;
+  double gx[GLN], gw[GLN];
+  gauss_legendre(GLN, gx, gw);
+  cudaError_t e = cudaMemcpyToSymbol(c_glx, gx, sizeof(gx));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_glw, gw, sizeof(gw));
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "eos table: %s", cudaGetErrorString(e));
+  phl_eos_table *t = new phl_eos_table();
+  t->t.nx = nrho;
+  t->t.ny = nT;
+  t->t.x0 = log(pow(10.0, lrhoye_lo) * NAV);
+  t->t.dx = (lrhoye_hi - lrhoye_lo) * log(10.0) / (nrho - 1);
+  t->t.y0 = lT_lo * log(10.0);
+  t->t.dy = (lT_hi - lT_lo) * log(10.0) / (nT - 1);
+  t->t.x0f = (float)t->t.x0; t->t.dxf = (float)t->t.dx; t->t.y0f = (float)t->t.y0; t->t.dyf = (float)t->t.dy;
+  const long nv = 4L * nrho * nT;
+  int *fail = nullptr;
+  e = cudaMalloc(&t->dv, nv * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&t->dvf, nv * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&fail, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(fail, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(t->dv); cudaFree(t->dvf); cudaFree(fail); delete t;
+    return (phl_status)set_error(PHL_ENOMEM, "eos table: %s", cudaGetErrorString(e));
+  }
+  const double me = MEC2 / (CL * CL), l = me * CL / HPL;
+  const int nn = nrho * nT;
+  k_table_nodes<<<(nn + 63) / 64, 64>>>(nrho, nT, t->t.x0, t->t.dx, t->t.y0, t->t.dy, l * l * l, t->dv, fail);
+  std::vector<double> h(nv);
+  int f = 0;
+  e = cudaMemcpy(h.data(), t->dv, nv * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&f, fail, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(fail);
+  if (e != cudaSuccess || f) {
+    cudaFree(t->dv); cudaFree(t->dvf); delete t;
+    return (phl_status)set_error(e != cudaSuccess ? PHL_ECUDA : PHL_ENEWTON, "eos table: node solve failed");
+  }
+  std::vector<float> hf(nv);
+  for (long q = 0; q < nv; ++q) hf[q] = (float)h[q];
+  cudaMemcpy(t->dvf, hf.data(), nv * sizeof(float), cudaMemcpyHostToDevice);
+  t->t.v = t->dv;
+  t->t.vf = t->dvf;
+  *out = t;
+  return PHL_OK;
+}
+
+void phl_eos_table_destroy(phl_eos_table *t) {
+  if (!t) return;
+  cudaFree(t->dv);
+  cudaFree(t->dvf);
+  delete t;
+}
+
+phl_status phl_eos_table_export(const phl_eos_table *t, double *out, long nout) {
+  if (!t || !out) return (phl_status)set_error(PHL_EINVAL, "null argument");
+  const long nv = 4L * t->t.nx * t->t.ny;
+  if (nout < 6 + nv) return (phl_status)set_error(PHL_EINVAL, "phl_eos_table_export: buffer too small");
+  out[0] = t->t.nx; out[1] = t->t.ny; out[2] = t->t.x0; out[3] = t->t.dx; out[4] = t->t.y0; out[5] = t->t.dy;
+  if (cudaMemcpy(out + 6, t->dv, nv * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return (phl_status)set_error(PHL_ECUDA, "phl_eos_table_export: copy failed");
+  return PHL_OK;
+}
+
+phl_status phl_eos(const phl_eos_table *t, long n, const double *rho, const double *eint, const double *abar,
+                   const double *ye, double *T_inout, double *P, double *gamma_e, double *gamma_c, double *cs,
+                   int *iters, int precision, double tol, int maxit, int where, void *stream) {
+  if (!t || n < 0 || !rho || !eint || !abar || !ye || !T_inout)
+    return (phl_status)set_error(PHL_EINVAL, "phl_eos: null argument");
+  if (n == 0) return PHL_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double *drho = rho, *dein = eint, *dab = abar, *dye = ye;
+  double *dT = T_inout, *dP = P, *dge = gamma_e, *dgc = gamma_c, *dcs = cs;
+  int *dit = iters;
+  void *buf = nullptr;
+  if (where == PHL_HOST) {   // stage through one device buffer
+    const size_t nb = (size_t)n * (9 * sizeof(double) + sizeof(int));
+    if (cudaMalloc(&buf, nb) != cudaSuccess) { cudaGetLastError(); return (phl_status)set_error(PHL_ENOMEM, "phl_eos: alloc"); }
+    double *b = (double *)buf;
+    double *a[9];
+    for (int k = 0; k < 9; ++k) a[k] = b + (size_t)k * n;
+    cudaMemcpyAsync(a[0], rho, n * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(a[1], eint, n * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(a[2], abar, n * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(a[3], ye, n * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(a[4], T_inout, n * 8, cudaMemcpyHostToDevice, s);
+    drho = a[0]; dein = a[1]; dab = a[2]; dye = a[3]; dT = a[4];
+    dP = a[5]; dge = a[6]; dgc = a[7]; dcs = a[8];
+    dit = (int *)(b + (size_t)9 * n);
+  }
+  const int blocks = (int)((n + 127) / 128);
+  if (precision == PHL_FP64)
+    k_eos_batch<double><<<blocks, 128, 0, s>>>(t->t, n, drho, dein, dab, dye, dT, dP, dge, dgc, dcs, dit, tol, maxit, 0);
+  else
+    k_eos_batch<float><<<blocks, 128, 0, s>>>(t->t, n, drho, dein, dab, dye, dT, dP, dge, dgc, dcs, dit, 1e-6, maxit, 1);
+  cudaError_t e = cudaGetLastError();
+  if (where == PHL_HOST) {
+    if (e == cudaSuccess) {
+      cudaMemcpyAsync(T_inout, dT, n * 8, cudaMemcpyDeviceToHost, s);
+      if (P) cudaMemcpyAsync(P, dP, n * 8, cudaMemcpyDeviceToHost, s);
+      if (gamma_e) cudaMemcpyAsync(gamma_e, dge, n * 8, cudaMemcpyDeviceToHost, s);
+      if (gamma_c) cudaMemcpyAsync(gamma_c, dgc, n * 8, cudaMemcpyDeviceToHost, s);
+      if (cs) cudaMemcpyAsync(cs, dcs, n * 8, cudaMemcpyDeviceToHost, s);
+      if (iters) cudaMemcpyAsync(iters, dit, n * sizeof(int), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+    }
+    cudaFree(buf);
+  }
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_eos: %s", cudaGetErrorString(e));
+  return PHL_OK;
+}
+
+}  // extern "C"

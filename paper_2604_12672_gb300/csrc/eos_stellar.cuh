@@ -1,0 +1,145 @@
+// eos_stellar.cuh -- stellar equation of state on the device (Sect. 2.2, item ii).
+//
+// Ions (ideal gas), radiation (Eqs. prad, erad) and an electron-positron gas
+// in pair equilibrium.  The e-/e+ part is a table of its Helmholtz
+// free-energy density f over (x, y) = (ln n_e, ln T), n_e = rho Y_e N_A, with
+// the derivatives f_x = n eta k T, f_y = -T s and f_xy at each node, built on
+// the device from the generalised Fermi-Dirac integrals
+//   F_k(eta, b) = int_0^inf x^k sqrt(1 + b x/2) / (exp(x - eta) + 1) dx,
+// b = kT / m_e c^2.  Bicubic Hermite interpolation of f gives P = f_x - f,
+// e = (f - f_y) / rho, c_v = (f_y - f_yy) / (rho T), dP/dT = (f_xy - f_y) / T,
+// dP/drho = (f_xx - f_x) / rho -- all from one interpolant, so the
+// thermodynamic identities hold for the interpolated EOS.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace phl {
+namespace eos {
+
+// CODATA 2018 (CGS)
+constexpr double KB = 1.380649e-16;
+constexpr double MEC2 = 8.1871057769e-7;
+constexpr double HPL = 6.62607015e-27;
+constexpr double CL = 2.99792458e10;
+constexpr double NAV = 6.02214076e23;
+constexpr double ARAD = 7.565733250e-15;
+constexpr double RGAS = KB * NAV;
+constexpr double PI_D = 3.14159265358979323846;
+
+struct Table {
+  int nx, ny;
+  double x0, dx, y0, dy;      // x = ln n_e, y = ln T
+  const double *v;            // [ny][nx][4]: f, f_x, f_y, f_xy (device)
+  const float *vf;            // FP32 copy
+  float x0f, dxf, y0f, dyf;
+};
+
+struct Mix {                   // composition-derived constants of a cell
+  double abar, ye;
+};
+
+template <typename R> struct TV { R f, fx, fy, fxx, fyy, fxy; };
+
+// Bicubic Hermite evaluation of the free energy and its derivatives.
+template <typename R>
+__device__ __forceinline__ bool table_eval(const Table &t, R x, R y, TV<R> &o) {
+  const R x0 = sizeof(R) == 8 ? (R)t.x0 : (R)t.x0f, dx = sizeof(R) == 8 ? (R)t.dx : (R)t.dxf;
+  const R y0 = sizeof(R) == 8 ? (R)t.y0 : (R)t.y0f, dy = sizeof(R) == 8 ? (R)t.dy : (R)t.dyf;
+  const R gx = (x - x0) / dx, gy = (y - y0) / dy;
+  if (!(gx >= R(0) && gx <= R(t.nx - 1) && gy >= R(0) && gy <= R(t.ny - 1))) return false;
+  int i = (int)gx, j = (int)gy;
+  if (i > t.nx - 2) i = t.nx - 2;
+  if (j > t.ny - 2) j = t.ny - 2;
+  const R u = gx - (R)i, v = gy - (R)j;
+  // cubic Hermite basis: value at 0, slope at 0, value at 1, slope at 1
+  const R u2 = u * u, u3 = u2 * u, v2 = v * v, v3 = v2 * v;
+  const R hu[4] = {R(2) * u3 - R(3) * u2 + R(1), u3 - R(2) * u2 + u, R(-2) * u3 + R(3) * u2, u3 - u2};
+  const R du[4] = {R(6) * u2 - R(6) * u, R(3) * u2 - R(4) * u + R(1), R(-6) * u2 + R(6) * u, R(3) * u2 - R(2) * u};
+  const R eu[4] = {R(12) * u - R(6), R(6) * u - R(4), R(-12) * u + R(6), R(6) * u - R(2)};
+  const R hv[4] = {R(2) * v3 - R(3) * v2 + R(1), v3 - R(2) * v2 + v, R(-2) * v3 + R(3) * v2, v3 - v2};
+  const R dv[4] = {R(6) * v2 - R(6) * v, R(3) * v2 - R(4) * v + R(1), R(-6) * v2 + R(6) * v, R(3) * v2 - R(2) * v};
+  const R ev[4] = {R(12) * v - R(6), R(6) * v - R(4), R(-12) * v + R(6), R(6) * v - R(2)};
+  R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+#pragma unroll
+  for (int cb = 0; cb < 2; ++cb)
+#pragma unroll
+    for (int ca = 0; ca < 2; ++ca) {
+      const long k = ((long)(j + cb) * t.nx + (i + ca)) * 4;
+      R q0, q1, q2, q3;
+      if (sizeof(R) == 8) { q0 = (R)t.v[k]; q1 = (R)t.v[k + 1]; q2 = (R)t.v[k + 2]; q3 = (R)t.v[k + 3]; }
+      else { q0 = (R)t.vf[k]; q1 = (R)t.vf[k + 1]; q2 = (R)t.vf[k + 2]; q3 = (R)t.vf[k + 3]; }
+      const R c0 = q0, c1 = q1 * dx, c2 = q2 * dy, c3 = q3 * dx * dy;
+      const int iv = 2 * ca, is = 2 * ca + 1, jv = 2 * cb, js = 2 * cb + 1;
+      a0 += c0 * hu[iv] * hv[jv] + c1 * hu[is] * hv[jv] + c2 * hu[iv] * hv[js] + c3 * hu[is] * hv[js];
+      a1 += c0 * du[iv] * hv[jv] + c1 * du[is] * hv[jv] + c2 * du[iv] * hv[js] + c3 * du[is] * hv[js];
+      a2 += c0 * hu[iv] * dv[jv] + c1 * hu[is] * dv[jv] + c2 * hu[iv] * dv[js] + c3 * hu[is] * dv[js];
+      a3 += c0 * eu[iv] * hv[jv] + c1 * eu[is] * hv[jv] + c2 * eu[iv] * hv[js] + c3 * eu[is] * hv[js];
+      a4 += c0 * hu[iv] * ev[jv] + c1 * hu[is] * ev[jv] + c2 * hu[iv] * ev[js] + c3 * hu[is] * ev[js];
+      a5 += c0 * du[iv] * dv[jv] + c1 * du[is] * dv[jv] + c2 * du[iv] * dv[js] + c3 * du[is] * dv[js];
+    }
+  o.f = a0;
+  o.fx = a1 / dx;
+  o.fy = a2 / dy;
+  o.fxx = a3 / (dx * dx);
+  o.fyy = a4 / (dy * dy);
+  o.fxy = a5 / (dx * dy);
+  return true;
+}
+
+template <typename R> struct EosOut { R P, e, cv, Pr, PT, ge, gc; };
+
+// Full EOS at (rho, T) for a mixture with mean mass number abar and Y_e.
+template <typename R>
+__device__ __forceinline__ bool eos_rt(const Table &t, R rho, R T, R abar, R ye, EosOut<R> &o) {
+  TV<R> q;
+  const R ne = rho * ye * R(NAV);
+  if (!table_eval<R>(t, log(ne), log(T), q)) return false;
+  const R irho = R(1) / rho, iT = R(1) / T;
+  const R Pe = q.fx - q.f;
+  const R ee = (q.f - q.fy) * irho;
+  const R cve = (q.fy - q.fyy) * irho * iT;
+  const R PeT = (q.fxy - q.fy) * iT;
+  const R Per = (q.fxx - q.fx) * irho;
+  const R iab = R(1) / abar;
+  const R T3 = T * T * T, T4 = T3 * T;
+  const R Rg = R(RGAS), ar = R(ARAD);
+  o.P = Pe + rho * Rg * T * iab + ar * T4 / R(3);
+  o.e = ee + R(1.5) * Rg * T * iab + ar * T4 * irho;
+  o.cv = cve + R(1.5) * Rg * iab + R(4) * ar * T3 * irho;
+  o.PT = PeT + rho * Rg * iab + R(4) / R(3) * ar * T3;
+  o.Pr = Per + Rg * T * iab;
+  // auxiliary indices of Sect. 2.6: gamma_e = P / (rho e) + 1, gamma_c = rho c_s^2 / P
+  const R cs2 = o.Pr + T * o.PT * o.PT / (rho * rho * o.cv);
+  o.ge = o.P / (rho * o.e) + R(1);
+  o.gc = rho * cs2 / o.P;
+  return true;
+}
+
+// Newton inversion e_int -> T (Sect. 2.2): T <- T + (e - e_EoS)/c_v until
+// |de|/e < tol, then one more step; bracketed inside the table's T range.
+// Returns iterations (> 0) or -1 on failure.
+template <typename R>
+__device__ __forceinline__ int eos_invert(const Table &t, R rho, R eint, R abar, R ye, R &T, R tol, int maxit,
+                                          EosOut<R> &o) {
+  const R Tlo = exp(R(t.y0)), Thi = exp(R(t.y0 + (t.ny - 1) * t.dy));
+  R lo = Tlo, hi = Thi;
+  if (!(T > Tlo && T < Thi)) T = sqrt(Tlo * Thi);
+  for (int it = 1; it <= maxit; ++it) {
+    if (!eos_rt<R>(t, rho, T, abar, ye, o)) return -1;
+    const R de = eint - o.e;
+    if (fabs(de) < tol * fabs(eint)) {
+      T = T + de / o.cv;
+      if (!eos_rt<R>(t, rho, T, abar, ye, o)) return -1;
+      return it;
+    }
+    if (de > R(0)) lo = T; else hi = T;
+    R Tn = T + de / o.cv;
+    if (!(Tn > lo && Tn < hi)) Tn = R(0.5) * (lo + hi);
+    T = Tn;
+  }
+  return -1;
+}
+
+}  // namespace eos
+}  // namespace phl

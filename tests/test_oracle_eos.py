@@ -1,0 +1,170 @@
+"""Pins of the oracle's stellar EOS and temperature-guess network.
+
+The e-/e+ gas is checked against closed forms (complete Fermi-Dirac integrals
+as polylogarithms, the non-degenerate and completely degenerate limits), an
+independent quadrature library, thermodynamic identities, and round trips of
+the Newton inversion; the network's gradient against finite differences.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+K_B = 1.380649e-16
+ME_C2 = 8.1871057769e-7
+N_A = 6.02214076e23
+H = 6.62607015e-27
+C_L = 2.99792458e10
+A_RAD = 7.565733250e-15
+X = [0.5, 0.5]
+A, Z = [16.0, 28.0], [8.0, 14.0]
+
+
+@pytest.fixture(scope="module")
+def table():
+    return O.EosTable(nrho=321, nT=241)
+
+
+@pytest.mark.parametrize("k", [0.5, 1.5, 2.5])
+@pytest.mark.parametrize("eta", [-30.0, -5.0, 0.0, 3.0, 20.0, 200.0])
+def test_fd_integral_nonrelativistic_polylog(k, eta):
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    exact = float(mpmath.re(-mpmath.gamma(k + 1) * mpmath.polylog(k + 1, -mpmath.exp(mpmath.mpf(eta)))))
+    got = O.fd(k, eta, 1e-14)
+    assert abs(got - exact) <= 1e-12 * abs(exact), (got, exact)
+
+
+@pytest.mark.parametrize("beta", [0.1, 1.0, 5.0])
+@pytest.mark.parametrize("eta", [-3.0, 2.0, 30.0])
+def test_fd_integral_relativistic_vs_quadrature_library(beta, eta):
+    integrate = pytest.importorskip("scipy.integrate")
+    for k in (0.5, 1.5, 2.5):
+        f = lambda x: x ** k * math.sqrt(1 + 0.5 * beta * x) / (math.exp(min(x - eta, 700)) + 1)
+        pts = [max(eta, 0.0)] if eta > 0 else None
+        ref, _ = integrate.quad(f, 0, max(eta, 0) + 200, points=pts, epsabs=0, epsrel=1e-13, limit=500)
+        got = O.fd(k, eta, beta)
+        assert abs(got - ref) <= 1e-11 * ref, (k, got, ref)
+
+
+def test_nondegenerate_limit():
+    # P = n k T for a non-degenerate gas at any temperature (no pairs here)
+    rho, ye, T = 1e-2, 0.5, 1e8
+    r = O.ep_direct(rho, ye, T)
+    n = rho * ye * N_A
+    assert abs(r["P"] / (n * K_B * T) - 1) < 1e-6
+    # kinetic energy 3/2 n k T once k T << m_e c^2 (b = 1.7e-6 here)
+    rho, T = 1e-8, 1e4
+    r = O.ep_direct(rho, ye, T)
+    n = rho * ye * N_A
+    assert abs(r["e"] * rho / (1.5 * n * K_B * T) - 1) < 1e-5
+
+
+def test_complete_degeneracy_chandrasekhar():
+    rho, ye, T = 1e8, 1.0, 1e6
+    n = rho * ye * N_A
+    me = ME_C2 / C_L ** 2
+    x = (3 * n / (8 * math.pi)) ** (1 / 3) * H / (me * C_L)
+    p_chandra = math.pi * me ** 4 * C_L ** 5 / (3 * H ** 3) * (
+        x * (2 * x * x - 3) * math.sqrt(1 + x * x) + 3 * math.asinh(x))
+    r = O.ep_direct(rho, ye, T)
+    assert abs(r["P"] / p_chandra - 1) < 1e-5, (r["P"], p_chandra)
+
+
+def test_table_vs_direct_quadrature(table):
+    cfg = O.stellar_cfg(A, Z, table)
+    cfgd = O.stellar_cfg(A, Z, None)
+    worst = {}
+    for rho in (1e5, 3e5, 1e6, 3e6, 1e7):
+        for T in (1.1e8, 4e8, 1.3e9, 3e9):
+            a, b = O.eos_rt(cfg, rho, T, X), O.eos_rt(cfgd, rho, T, X)
+            for k in ("P", "e", "gamma_e", "gamma_c", "cv"):
+                worst[k] = max(worst.get(k, 0), abs(a[k] - b[k]) / abs(b[k]))
+    # bicubic Hermite of the free energy, 80 nodes per decade: first-derivative
+    # quantities O(h^3), second-derivative quantities O(h^2)
+    assert worst["P"] < 5e-6 and worst["e"] < 5e-5 and worst["gamma_e"] < 1e-5, worst
+    assert worst["cv"] < 2e-3 and worst["gamma_c"] < 2e-3, worst
+
+
+def test_thermodynamic_consistency_of_the_table(table):
+    """(de/drho)_T = (P - T (dP/dT)_rho) / rho^2 holds for the interpolated EOS."""
+    cfg = O.stellar_cfg(A, Z, table)
+    for rho, T in ((2e5, 3.3e8), (5e6, 2.1e9), (1e7, 1.2e9)):
+        h = 1e-5
+        ep = O.eos_rt(cfg, rho * (1 + h), T, X)["e"]
+        em = O.eos_rt(cfg, rho * (1 - h), T, X)["e"]
+        r = O.eos_rt(cfg, rho, T, X)
+        lhs = (ep - em) / (2 * h * rho)
+        rhs = (r["P"] - T * r["dPdT"]) / rho ** 2
+        assert abs(lhs - rhs) <= 1e-5 * abs(r["P"] / rho ** 2), (lhs, rhs)
+
+
+def test_gamma_c_is_the_adiabatic_sound_speed(table):
+    """c_s^2 = (dP/drho)_s from an explicit adiabat de = P / rho^2 drho."""
+    cfg = O.stellar_cfg(A, Z, table)
+    for rho, T in ((3e5, 5e8), (4e6, 2.5e9)):
+        r0 = O.eos_rt(cfg, rho, T, X)
+        d = 1e-5 * rho
+        target = r0["e"] + r0["P"] / rho ** 2 * d
+        r1 = O.eos_invert(cfg, rho + d, target, X, T)
+        cs2_fd = (r1["P"] - r0["P"]) / d
+        cs2 = r0["gamma_c"] * r0["P"] / rho
+        assert abs(cs2_fd / cs2 - 1) < 1e-4, (cs2_fd, cs2)
+
+
+def test_newton_round_trip_and_guess_independence(table):
+    """T -> e -> T; the attainable accuracy is the rounding of e amplified by
+    the condition number e / (c_v T) (large for degenerate electrons)."""
+    cfg = O.stellar_cfg(A, Z, table)
+    for rho in (1e5, 1e6, 1e7):
+        for T in (1.2e8, 7e8, 2.9e9):
+            r = O.eos_rt(cfg, rho, T, X)
+            cond = max(1.0, r["e"] / (r["cv"] * T))
+            tol = max(1e-12, 1e-15 * cond) * T
+            ts = [O.eos_invert(cfg, rho, r["e"], X, g)["T"] for g in (1.05e8, 1e9, 8e9)]
+            for t in ts:
+                assert abs(t - T) <= tol, (rho, T, t, cond)
+            assert max(ts) - min(ts) <= tol
+
+
+def test_radiation_dominated_limit(table):
+    cfg = O.stellar_cfg(A, Z, table)
+    rho, T = 1e4 * 2, 9e9     # rho Y_e = 1e4, radiation- and pair-dominated
+    r = O.eos_rt(cfg, rho, T, X)
+    assert r["P"] > A_RAD * T ** 4 / 3
+
+
+# ---------------------------------------------------------------------------
+# temperature-guess network (3 -> 64 -> 64 -> 1, tanh)
+# ---------------------------------------------------------------------------
+
+def _nparams(nin, nh):
+    return nh * nin + nh + nh * nh + nh + nh + 1
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    nin, nh = 3, 8
+    w = rng.normal(scale=0.5, size=_nparams(nin, nh))
+    x = rng.normal(size=(20, nin))
+    t = rng.normal(size=20)
+    loss, g = O.mlp_loss_grad(w, nin, nh, x, t)
+    for i in rng.choice(len(w), 25, replace=False):
+        e = np.zeros_like(w)
+        e[i] = 1e-6
+        lp, _ = O.mlp_loss_grad(w + e, nin, nh, x, t)
+        lm, _ = O.mlp_loss_grad(w - e, nin, nh, x, t)
+        fdg = (lp - lm) / 2e-6
+        assert abs(fdg - g[i]) <= 1e-7 * max(1.0, abs(g[i])), (i, fdg, g[i])
+
+
+def test_mlp_forward_hand_computed():
+    nin, nh = 1, 1
+    # W1, b1, W2, b2, W3, b3
+    w = np.array([2.0, -0.5, 1.5, 0.25, -3.0, 0.1])
+    x = np.array([[0.3]])
+    h1 = math.tanh(2.0 * 0.3 - 0.5)
+    h2 = math.tanh(1.5 * h1 + 0.25)
+    assert abs(O.mlp_forward(w, nin, nh, x)[0] - (-3.0 * h2 + 0.1)) < 1e-15
