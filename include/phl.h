@@ -94,6 +94,8 @@ typedef struct {
   int newton_maxit;
   int use_mlp;              /* stellar EOS: MLP first guess                     */
   void *stream;             /* cudaStream_t                                     */
+  const struct phl_eos_table *eos_table;  /* stellar EOS table (not owned)      */
+  double bg_X[PHL_MAXSPEC]; /* stellar: mass fractions of the background        */
 } phl_grid_desc;
 
 typedef struct {
@@ -117,6 +119,14 @@ phl_status phl_create_grid(const phl_grid_desc *desc, phl_grid **out);
 phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx,
                          const double *by, const double *bz, const double *T,
                          int where);
+
+/* Load the state from primitive fields: prim[(5 + nspec)][nz][ny][nx] =
+ * rho, u_x, u_y, u_z, P, X_l (mass fractions), plus the face fields.  The
+ * conserved energy is rho e(rho, T) + rho u^2/2 + B^2/2 with T from
+ * P_EoS(rho, T, X) = P (stellar EOS: Newton on P; ideal gas: direct);
+ * the temperatures become the Newton first guesses.  Host or device arrays. */
+phl_status phl_set_state_prim(phl_grid *g, const double *prim, const double *bx, const double *by,
+                              const double *bz, int where);
 
 /* Store the state into caller arrays (layout above); T may be NULL.
  * Synchronises the grid's stream and reports device flags. */
@@ -226,7 +236,8 @@ phl_status phl_eos_table_export(const phl_eos_table *t, double *out, long nout);
  * be NULL except T_inout): P, gamma_e = P/(rho e) + 1, gamma_c = rho c_s^2 / P,
  * c_s, Newton iterations (-1: no convergence).  abar, ye: mean mass number
  * and electron fraction per element.  precision = PHL_FP64: FP64 Newton;
- * PHL_MIXED: FP32 Newton to 1e-6 then one FP64 step.  where = PHL_HOST (host
+ * PHL_MIXED: FP32 Newton to about 1e-5, finished by FP64 Newton to tol (the
+ * iteration count then sums both phases).  where = PHL_HOST (host
  * arrays, synchronous) or PHL_DEVICE (device arrays, asynchronous on stream). */
 phl_status phl_eos(const phl_eos_table *t, long n, const double *rho, const double *eint,
                    const double *abar, const double *ye, double *T_inout, double *P,

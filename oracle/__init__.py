@@ -235,6 +235,66 @@ def eos_invert(cfg, rho, eint, X, T_guess):
     return dict(T=T.value, P=P.value, gamma_e=ge.value, gamma_c=gc.value, iters=it.value)
 
 
+def p_to_T(cfg, rho, P, X, T0=1e9, tol=1e-14, maxit=100):
+    """Temperature with P_EoS(rho, T, X) = P: Newton on P (bracketed)."""
+    T, lo, hi = T0, 1e7, 1e10
+    for _ in range(maxit):
+        r = eos_rt(cfg, rho, T, X)
+        dp = P - r["P"]
+        if dp > 0:
+            lo = T
+        else:
+            hi = T
+        if abs(dp) <= tol * P:
+            return T
+        Tn = T + dp / r["dPdT"]
+        T = Tn if lo < Tn < hi else 0.5 * (lo + hi)
+    raise RuntimeError("P -> T inversion did not converge")
+
+
+def prepare_stellar(pr, table):
+    """The oracle's own completion of a stellar problem given in primitives:
+    background gamma_e, gamma_c (centres and faces) and the cell temperature
+    and total energy, all from the oracle EOS with P -> T inversions."""
+    q = pr.copy()
+    cfg = stellar_cfg(pr.meta["A"], pr.meta["Z"], table)
+    bX = pr.meta["bg_X"]
+    bg = dict(pr.bg)
+    for loc in ("c", "f"):
+        rho, P = bg["rho_" + loc], bg["p_" + loc]
+        ge, gc = np.zeros_like(rho), np.zeros_like(rho)
+        T = 1e9
+        for i in range(rho.size):
+            T = p_to_T(cfg, rho[i], P[i], bX, T)
+            r = eos_rt(cfg, rho[i], T, bX)
+            ge[i], gc[i] = r["gamma_e"], r["gamma_c"]
+        bg["ge_" + loc], bg["gc_" + loc] = ge, gc
+    q.bg = bg
+    prim = pr.meta["prim"]
+    nz, ny, nx = prim["rho"].shape
+    Tc = np.zeros((nz, ny, nx))
+    bcx = 0.5 * (pr.bx[:, :, :-1] + pr.bx[:, :, 1:])
+    bcy = 0.5 * (pr.by[:, :-1, :] + pr.by[:, 1:, :])
+    bcz = 0.5 * (pr.bz[:-1, :, :] + pr.bz[1:, :, :])
+    E = np.zeros((nz, ny, nx))
+    for k in range(nz):
+        T = 1e9
+        for j in range(ny):
+            for i in range(nx):
+                rho = prim["rho"][k, j, i]
+                Xc = prim["X"][:, k, j, i]
+                T = p_to_T(cfg, rho, prim["p"][k, j, i], Xc, T)
+                e = eos_rt(cfg, rho, T, Xc)["e"]
+                v = prim["vel"][:, k, j, i]
+                Tc[k, j, i] = T
+                E[k, j, i] = rho * e + 0.5 * rho * (v ** 2).sum() + 0.5 * (
+                    bcx[k, j, i] ** 2 + bcy[k, j, i] ** 2 + bcz[k, j, i] ** 2)
+    q.cons = pr.cons.copy()
+    q.cons[4] = E
+    q.T = Tc
+    return q
+
+
 def ep_direct(rho, ye, T):
     o = [C.c_double() for _ in range(5)]
     rc = lib().ora_ep_direct(rho, ye, T, *[C.byref(v) for v in o])

@@ -69,26 +69,32 @@ static void gl_init(void) {
 }
 
 /* Integrals of one species at (eta, b), by x = t^2 and composite
- * Gauss-Legendre panels clustered around the Fermi edge t = sqrt(eta):
+ * Gauss-Legendre panels.  The panel edges sit at fixed distances (in units
+ * of kT) from the Fermi edge x = max(eta, 0), so the Fermi function varies by
+ * at most a factor e^3 ... e^24 across a panel and is below e^-48 where the
+ * first panel ends: the quadrature error stays at rounding level for every
+ * degeneracy (a panel ending only a few kT before the edge leaves the
+ * exponential tail unresolved, an O(e^-8) relative error at strong
+ * degeneracy).
  *   out[0..2] = F_1/2, F_3/2, F_5/2
  *   out[3..4] = dF_1/2/deta, dF_3/2/deta
  *   out[5..6] = dF_1/2/db,   dF_3/2/db */
 static void fd_set(double eta, double b, double *out) {
   gl_init();
   for (int q = 0; q < 7; ++q) out[q] = 0.0;
-  double te = eta > 0.0 ? sqrt(eta) : 0.0;
-  double w = 0.5 / (te > 0.5 ? te : 0.5);
-  double tmax = sqrt((eta > 0.0 ? eta : 0.0) + 90.0);
-  double e[8] = {0.0, te - 8 * w, te - 3 * w, te - w, te + w, te + 3 * w, te + 8 * w, tmax};
-  int ne = 8;
-  /* sort and clamp */
-  for (int i = 0; i < ne; ++i) { if (e[i] < 0.0) e[i] = 0.0; if (e[i] > tmax) e[i] = tmax; }
-  for (int i = 1; i < ne; ++i)
-    for (int j = i; j > 0 && e[j] < e[j - 1]; --j) { double t = e[j]; e[j] = e[j - 1]; e[j - 1] = t; }
+  static const double off[12] = {-48.0, -24.0, -12.0, -6.0, -3.0, 0.0, 3.0, 6.0, 12.0, 24.0, 48.0, 100.0};
+  const double base = eta > 0.0 ? eta : 0.0;
+  double e[13];
+  int ne = 0;
+  e[ne++] = 0.0;
+  for (int q = 0; q < 12; ++q) {
+    double x = base + off[q];
+    if (x > 0.0) e[ne++] = sqrt(x);   /* t-space edge */
+  }
   for (int pnl = 0; pnl + 1 < ne; ++pnl) {
     double a = e[pnl], c = e[pnl + 1];
     if (c - a <= 0.0) continue;
-    int nsub = 4;
+    int nsub = 2;
     for (int s = 0; s < nsub; ++s) {
       double lo = a + (c - a) * s / nsub, hi = a + (c - a) * (s + 1) / nsub;
       double hm = 0.5 * (hi - lo), cm = 0.5 * (hi + lo);

@@ -793,7 +793,8 @@ double ora_dt(const ora_cfg *cfg, const double *cons, const double *bx,
         bc[0] = 0.5 * (bx[AF(&G, 0, i, j, k)] + bx[AF(&G, 0, i + 1, j, k)]);
         bc[1] = 0.5 * (by[AF(&G, 1, i, j, k)] + by[AF(&G, 1, i, j + 1, k)]);
         bc[2] = 0.5 * (bz[AF(&G, 2, i, j, k)] + bz[AF(&G, 2, i, j, k + 1)]);
-        if (cell_prims(&G, u, bc, k, T ? &T[a] : NULL, w)) return -1.0;
+        double Tl = T ? T[a] : 0.0;    /* the step's Newton guesses are left untouched */
+        if (cell_prims(&G, u, bc, k, T ? &Tl : NULL, w)) return -1.0;
         bgstate b = bg_cell(&G, k);
         double rho = w[W_RHO] + b.rho, P = w[W_P] + b.p, gc = w[W_GC] + b.gc;
         double a2 = gc * P / rho;

@@ -45,6 +45,7 @@ class GridDesc(C.Structure):
         ("eps_sf", C.c_double), ("mach_thr", C.c_double), ("precision", C.c_int),
         ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("use_mlp", C.c_int),
         ("stream", C.c_void_p),
+        ("eos_table", C.c_void_p), ("bg_X", C.c_double * PHL_MAXSPEC),
     ]
 
 
@@ -64,6 +65,7 @@ _SIGS = {
     "phl_create_grid": (C.c_int, [C.POINTER(GridDesc), C.POINTER(C.c_void_p)]),
     "phl_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "phl_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_set_state_prim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "phl_compute_dt": (C.c_int, [C.c_void_p, _dp]),
     "phl_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "phl_check": (C.c_int, [C.c_void_p]),
@@ -192,8 +194,9 @@ class Grid:
     """One simulation box on the current CUDA device (see include/phl.h)."""
 
     def __init__(self, pr, precision="fp64", riemann=None, eps_sf=None, cfl=None, rk=3, wb=True,
-                 stream=None, mach_thr=None):
+                 stream=None, mach_thr=None, eos_table=None, newton_tol=1e-11, newton_maxit=50):
         self.pr = pr
+        self.eos_table = eos_table
         d = GridDesc()
         for k in range(3):
             d.n[k] = pr.n[k]
@@ -204,6 +207,13 @@ class Grid:
         d.eos = EOS[pr.eos]
         d.gamma = pr.gamma
         d.nspec = pr.nspec
+        if pr.eos == "stellar":
+            if eos_table is None:
+                raise ValueError("stellar problems need an EosTable")
+            d.eos_table = eos_table.h
+            for l in range(pr.nspec):
+                d.A[l], d.Z[l] = pr.meta["A"][l], pr.meta["Z"][l]
+                d.bg_X[l] = pr.meta["bg_X"][l]
         self._keep = []
         if pr.bg is not None and wb:
             for key in ("rho_c", "p_c", "rho_f", "p_f", "ge_c", "gc_c", "ge_f", "gc_f"):
@@ -221,8 +231,8 @@ class Grid:
         d.eps_sf = pr.eps_sf if eps_sf is None else eps_sf
         d.mach_thr = pr.mach_thr if mach_thr is None else mach_thr
         d.precision = PRECISION[precision]
-        d.newton_tol = 1e-11
-        d.newton_maxit = 50
+        d.newton_tol = newton_tol
+        d.newton_maxit = newton_maxit
         d.use_mlp = 0
         d.stream = stream
         self.desc = d
@@ -247,10 +257,24 @@ class Grid:
         where = ptrs[0][1]
         _check(lib().phl_set_state(self.h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[4][0], where))
 
+    def set_state_prim(self, prim, bx, by, bz):
+        ptrs = [_ptr(a) for a in (prim, bx, by, bz)]
+        _check(lib().phl_set_state_prim(self.h, ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], ptrs[0][1]))
+
     def load(self, st=None):
-        st = st or dict(cons=self.pr.cons, bx=self.pr.bx, by=self.pr.by, bz=self.pr.bz, T=self.pr.T)
+        pr = self.pr
+        if st is None and pr.eos == "stellar" and np.isnan(pr.cons[4]).any():
+            pm = pr.meta["prim"]
+            prim = np.ascontiguousarray(np.concatenate(
+                [pm["rho"][None], pm["vel"], pm["p"][None], pm["X"]], axis=0), dtype=np.float64)
+            self.set_state_prim(prim, np.ascontiguousarray(pr.bx), np.ascontiguousarray(pr.by),
+                                np.ascontiguousarray(pr.bz))
+            return
+        st = st or dict(cons=pr.cons, bx=pr.bx, by=pr.by, bz=pr.bz, T=pr.T)
+        T = st.get("T")
         self.set_state(np.ascontiguousarray(st["cons"]), np.ascontiguousarray(st["bx"]),
-                       np.ascontiguousarray(st["by"]), np.ascontiguousarray(st["bz"]), st.get("T"))
+                       np.ascontiguousarray(st["by"]), np.ascontiguousarray(st["bz"]),
+                       None if T is None else np.ascontiguousarray(T))
 
     def get_state_into(self, cons, bx, by, bz, T=None):
         ptrs = [_ptr(a) for a in (cons, bx, by, bz, T)]
@@ -260,8 +284,9 @@ class Grid:
         pr = self.pr
         cons = np.empty_like(pr.cons)
         bx, by, bz = np.empty_like(pr.bx), np.empty_like(pr.by), np.empty_like(pr.bz)
-        self.get_state_into(cons, bx, by, bz)
-        return dict(cons=cons, bx=bx, by=by, bz=bz, T=None)
+        T = np.empty(cons.shape[1:]) if pr.eos == "stellar" else None
+        self.get_state_into(cons, bx, by, bz, T)
+        return dict(cons=cons, bx=bx, by=by, bz=bz, T=T)
 
     def step(self, nsteps=1, dt=0.0):
         _check(lib().phl_step(self.h, float(dt), int(nsteps)))

@@ -47,42 +47,40 @@ void gauss_legendre(int n, double *x, double *w) {
 }
 
 // One species at (eta, b): F_1/2, F_3/2, F_5/2, dF_{1/2,3/2}/deta, dF_{1/2,3/2}/db.
-// Integration variable s with x = s^2; panels refine around the Fermi edge.
+// Integration variable s with x = s^2.  Panel edges at fixed offsets (in kT)
+// from the Fermi edge x = max(eta, 0): the Fermi factor changes by at most
+// e^20 across a panel and is below e^-50 before the first edge, so the
+// exponential tails are resolved at every degeneracy.
 __device__ void fd_integrals(double eta, double b, double *F) {
   for (int q = 0; q < 7; ++q) F[q] = 0.0;
-  const double se = eta > 0.0 ? sqrt(eta) : 0.0;
-  const double wd = 0.5 / fmax(se, 0.5);      // width of the edge in s
-  const double smax = sqrt(fmax(eta, 0.0) + 100.0);
-  double edge[9] = {0.0, se - 12.0 * wd, se - 4.0 * wd, se - 1.5 * wd, se, se + 1.5 * wd, se + 4.0 * wd,
-                    se + 12.0 * wd, smax};
-  for (int k = 0; k < 9; ++k) edge[k] = fmin(fmax(edge[k], 0.0), smax);
-  for (int k = 1; k < 9; ++k)   // insertion sort (edges already nearly sorted)
-    for (int m = k; m > 0 && edge[m] < edge[m - 1]; --m) { const double t = edge[m]; edge[m] = edge[m - 1]; edge[m - 1] = t; }
-  for (int pnl = 0; pnl < 8; ++pnl) {
-    const double a = edge[pnl], c = edge[pnl + 1];
+  constexpr int NOFF = 14;
+  const double off[NOFF] = {-50.0, -30.0, -16.0, -8.0, -4.0, -1.5, 0.0, 1.5, 4.0, 8.0, 16.0, 30.0, 50.0, 110.0};
+  const double base = fmax(eta, 0.0);
+  double a = 0.0;
+  for (int k = 0; k < NOFF; ++k) {
+    const double xe = base + off[k];
+    if (!(xe > 0.0)) continue;
+    const double c = sqrt(xe);
     if (!(c > a)) continue;
-    const int nsub = 3;
-    for (int sb = 0; sb < nsub; ++sb) {
-      const double lo = a + (c - a) * sb / nsub, hi = a + (c - a) * (sb + 1) / nsub;
-      const double hm = 0.5 * (hi - lo), cm = 0.5 * (hi + lo);
-      for (int g = 0; g < GLN; ++g) {
-        const double s = cm + hm * c_glx[g];
-        const double wgt = 2.0 * s * hm * c_glw[g];   // dx = 2 s ds
-        const double x = s * s, u = x - eta;
-        const double z = exp(-fabs(u));
-        const double fermi = u > 0.0 ? z / (1.0 + z) : 1.0 / (1.0 + z);
-        const double fder = z / ((1.0 + z) * (1.0 + z));   // f (1 - f)
-        const double S = sqrt(1.0 + 0.5 * b * x);
-        const double x12 = s, x32 = x * s, x52 = x * x * s;
-        F[0] += wgt * x12 * S * fermi;
-        F[1] += wgt * x32 * S * fermi;
-        F[2] += wgt * x52 * S * fermi;
-        F[3] += wgt * x12 * S * fder;
-        F[4] += wgt * x32 * S * fder;
-        F[5] += wgt * x32 * fermi / (4.0 * S);
-        F[6] += wgt * x52 * fermi / (4.0 * S);
-      }
+    const double hm = 0.5 * (c - a), cm = 0.5 * (c + a);
+    for (int g = 0; g < GLN; ++g) {
+      const double s = cm + hm * c_glx[g];
+      const double wgt = 2.0 * s * hm * c_glw[g];   // dx = 2 s ds
+      const double x = s * s, u = x - eta;
+      const double z = exp(-fabs(u));
+      const double fermi = u > 0.0 ? z / (1.0 + z) : 1.0 / (1.0 + z);
+      const double fder = z / ((1.0 + z) * (1.0 + z));   // f (1 - f)
+      const double S = sqrt(1.0 + 0.5 * b * x);
+      const double x12 = s, x32 = x * s, x52 = x * x * s;
+      F[0] += wgt * x12 * S * fermi;
+      F[1] += wgt * x32 * S * fermi;
+      F[2] += wgt * x52 * S * fermi;
+      F[3] += wgt * x12 * S * fder;
+      F[4] += wgt * x32 * S * fder;
+      F[5] += wgt * x32 * fermi / (4.0 * S);
+      F[6] += wgt * x52 * fermi / (4.0 * S);
     }
+    a = c;
   }
 }
 
@@ -144,29 +142,20 @@ __global__ void k_table_nodes(int nx, int ny, double x0, double dx, double y0, d
 template <typename R>
 __global__ void k_eos_batch(Table t, long n, const double *rho, const double *eint, const double *abar,
                             const double *ye, double *T, double *P, double *ge, double *gc, double *cs, int *iters,
-                            double tol, int maxit, int final64) {
+                            double tol, int maxit) {
   const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  EosOut<R> o;
-  R Tr = (R)T[i];
-  int it = eos_invert<R>(t, (R)rho[i], (R)eint[i], (R)abar[i], (R)ye[i], Tr, (R)tol, maxit, o);
-  double Td = (double)Tr;
-  EosOut<double> od;
-  bool ok = it > 0;
-  if (ok && final64) {   // final Newton step in FP64
-    ok = eos_rt<double>(t, rho[i], Td, abar[i], ye[i], od);
-    if (ok) {
-      Td = Td + (eint[i] - od.e) / od.cv;
-      ok = eos_rt<double>(t, rho[i], Td, abar[i], ye[i], od);
-    }
-  } else {
-    od.P = o.P; od.ge = o.ge; od.gc = o.gc;
-  }
+  EosOut<double> o;
+  double Td = T[i];
+  int it;
+  if (sizeof(R) == 8) it = eos_invert<double>(t, rho[i], eint[i], abar[i], ye[i], Td, tol, maxit, o);
+  else it = eos_invert_mixed(t, rho[i], eint[i], abar[i], ye[i], Td, tol, maxit, o);
+  const bool ok = it > 0;
   T[i] = Td;
-  if (P) P[i] = ok ? od.P : NAN;
-  if (ge) ge[i] = od.ge;
-  if (gc) gc[i] = od.gc;
-  if (cs) cs[i] = sqrt(od.gc * od.P / rho[i]);
+  if (P) P[i] = ok ? o.P : NAN;
+  if (ge) ge[i] = o.ge;
+  if (gc) gc[i] = o.gc;
+  if (cs) cs[i] = sqrt(o.gc * o.P / rho[i]);
   if (iters) iters[i] = ok ? it : -1;
 }
 
@@ -273,9 +262,9 @@ phl_status phl_eos(const phl_eos_table *t, long n, const double *rho, const doub
   }
   const int blocks = (int)((n + 127) / 128);
   if (precision == PHL_FP64)
-    k_eos_batch<double><<<blocks, 128, 0, s>>>(t->t, n, drho, dein, dab, dye, dT, dP, dge, dgc, dcs, dit, tol, maxit, 0);
+    k_eos_batch<double><<<blocks, 128, 0, s>>>(t->t, n, drho, dein, dab, dye, dT, dP, dge, dgc, dcs, dit, tol, maxit);
   else
-    k_eos_batch<float><<<blocks, 128, 0, s>>>(t->t, n, drho, dein, dab, dye, dT, dP, dge, dgc, dcs, dit, 1e-6, maxit, 1);
+    k_eos_batch<float><<<blocks, 128, 0, s>>>(t->t, n, drho, dein, dab, dye, dT, dP, dge, dgc, dcs, dit, tol, maxit);
   cudaError_t e = cudaGetLastError();
   if (where == PHL_HOST) {
     if (e == cudaSuccess) {

@@ -24,6 +24,7 @@ constexpr double HPL = 6.62607015e-27;
 constexpr double CL = 2.99792458e10;
 constexpr double NAV = 6.02214076e23;
 constexpr double ARAD = 7.565733250e-15;
+constexpr double ARAD_QUARTER = 2.9492579329135276e-04;   // ARAD^(1/4)
 constexpr double RGAS = KB * NAV;
 constexpr double PI_D = 3.14159265358979323846;
 
@@ -102,15 +103,25 @@ __device__ __forceinline__ bool eos_rt(const Table &t, R rho, R T, R abar, R ye,
   const R PeT = (q.fxy - q.fy) * iT;
   const R Per = (q.fxx - q.fx) * irho;
   const R iab = R(1) / abar;
-  const R T3 = T * T * T, T4 = T3 * T;
-  const R Rg = R(RGAS), ar = R(ARAD);
-  o.P = Pe + rho * Rg * T * iab + ar * T4 / R(3);
-  o.e = ee + R(1.5) * Rg * T * iab + ar * T4 * irho;
-  o.cv = cve + R(1.5) * Rg * iab + R(4) * ar * T3 * irho;
-  o.PT = PeT + rho * Rg * iab + R(4) / R(3) * ar * T3;
+  const R Rg = R(RGAS);
+  R aT4, aT3;   // radiation a T^4 and a T^3
+  if (sizeof(R) == 8) {
+    const R T3 = T * T * T;
+    aT3 = R(ARAD) * T3;
+    aT4 = aT3 * T;
+  } else {   // T^4 overflows FP32 above 2^32 K: form (a^(1/4) T)^4 instead
+    const R t = R(ARAD_QUARTER) * T, t2 = t * t;
+    aT4 = t2 * t2;
+    aT3 = aT4 * iT;
+  }
+  o.P = Pe + rho * Rg * T * iab + aT4 / R(3);
+  o.e = ee + R(1.5) * Rg * T * iab + aT4 * irho;
+  o.cv = cve + R(1.5) * Rg * iab + R(4) * aT3 * irho;
+  o.PT = PeT + rho * Rg * iab + R(4) / R(3) * aT3;
   o.Pr = Per + Rg * T * iab;
-  // auxiliary indices of Sect. 2.6: gamma_e = P / (rho e) + 1, gamma_c = rho c_s^2 / P
-  const R cs2 = o.Pr + T * o.PT * o.PT / (rho * rho * o.cv);
+  // auxiliary indices of Sect. 2.6: gamma_e = P / (rho e) + 1, gamma_c = rho c_s^2 / P;
+  // c_s^2 = P_rho + T P_T^2 / (rho^2 c_v), grouped so no product leaves the FP32 range
+  const R cs2 = o.Pr + (T * o.PT * irho) * (o.PT * irho / o.cv);
   o.ge = o.P / (rho * o.e) + R(1);
   o.gc = rho * cs2 / o.P;
   return true;
@@ -139,6 +150,24 @@ __device__ __forceinline__ int eos_invert(const Table &t, R rho, R eint, R abar,
     T = Tn;
   }
   return -1;
+}
+
+// Mixed-precision inversion: FP32 Newton iterations bring T within about
+// 1e-5 of the root (|de| / e; FP32 holds ln n_e ~ 70 and ln T ~ 20 only to
+// ~1e-6, the floor of an FP32 table lookup), then FP64 Newton finishes to tol
+// with the same stopping rule as the FP64 path (converged, then one more
+// step).  The FP32 phase only supplies the starting point: if it stalls, its
+// last bracketed iterate is used.
+// Returns the total iteration count, or -1 if the FP64 phase fails.
+__device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, double eint, double abar, double ye,
+                                                double &T, double tol, int maxit, EosOut<double> &o) {
+  float Tf = (float)T;
+  EosOut<float> of;
+  const int it32 = eos_invert<float>(t, (float)rho, (float)eint, (float)abar, (float)ye, Tf, 1e-5f,
+                                     maxit < 12 ? maxit : 12, of);
+  if (isfinite(Tf) && Tf > 0.0f) T = (double)Tf;
+  const int it64 = eos_invert<double>(t, rho, eint, abar, ye, T, tol, maxit, o);
+  return it64 < 0 ? -1 : it64 + (it32 > 0 ? it32 : 12);
 }
 
 }  // namespace eos

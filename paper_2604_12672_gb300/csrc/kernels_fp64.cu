@@ -205,8 +205,12 @@ void launch_stage_fp64(const DevGeo &G, const StageBufs &S, cudaStream_t s, int 
     int l[3], h[3];
     for (int d = 0; d < 3; ++d) rng(d, NGW, NGW, l[d], h[d]);
     Box b = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
-    PHL_LAUNCH(KC_PRIM, prof, s, k_prim<<<grid3(b), block3(b), 0, s>>>(G, b, S.Uin, S.Bin, S.W, S.dflag));
-    ++nl;
+    if (G.eos == 1) {
+      launch_eos_cells<double>(G, S.Uin, S.Bin, nullptr, nullptr, S.Tin, S.Tout, S.W, S.dflag, s, &nl, prof);
+    } else {
+      PHL_LAUNCH(KC_PRIM, prof, s, k_prim<<<grid3(b), block3(b), 0, s>>>(G, b, S.Uin, S.Bin, S.W, S.dflag));
+      ++nl;
+    }
   }
   // (2) shock flags
   if (G.eps_sf > 0.0) {

@@ -25,12 +25,13 @@ __device__ __forceinline__ void cell_prims_mx(const DevGeo &G, const double *__r
   const long pl = G.plane;
   const Bg b = bg_cell(G, k);                       // FP64 background for the deviations
   const double ehat = G.has_bg ? G.bg_e_c[k + BG_NG] : 0.0;
-  float drho = d2f_bits(U[p] - b.rho);
-  float m0 = d2f_bits(U[pl + p]), m1 = d2f_bits(U[2 * pl + p]), m2 = d2f_bits(U[3 * pl + p]);
-  float dE = d2f_bits(U[4 * pl + p] - ehat);
-  float bxl = d2f_bits(Bf[p]), bxh = d2f_bits(Bf[p + 1]);
-  float byl = d2f_bits(Bf[pl + p]), byh = d2f_bits(Bf[pl + p + G.sy]);
-  float bzl = d2f_bits(Bf[2 * pl + p]), bzh = d2f_bits(Bf[2 * pl + p + G.sz]);
+  const double sr = G.isc_rho, sm = G.isc_m, se = G.isc_e, sb = G.isc_b;   // to scaled units (exact)
+  float drho = d2f_bits((U[p] - b.rho) * sr);
+  float m0 = d2f_bits(U[pl + p] * sm), m1 = d2f_bits(U[2 * pl + p] * sm), m2 = d2f_bits(U[3 * pl + p] * sm);
+  float dE = d2f_bits((U[4 * pl + p] - ehat) * se);
+  float bxl = d2f_bits(Bf[p] * sb), bxh = d2f_bits(Bf[p + 1] * sb);
+  float byl = d2f_bits(Bf[pl + p] * sb), byh = d2f_bits(Bf[pl + p + G.sy] * sb);
+  float bzl = d2f_bits(Bf[2 * pl + p] * sb), bzh = d2f_bits(Bf[2 * pl + p + G.sz] * sb);
   if (dU) {
     drho += dU[p];
     m0 += dU[pl + p]; m1 += dU[2 * pl + p]; m2 += dU[3 * pl + p];
@@ -57,7 +58,7 @@ __device__ __forceinline__ void cell_prims_mx(const DevGeo &G, const double *__r
 #pragma unroll
   for (int l = 0; l < PHL_NSPEC_MAX; ++l) {
     if (l >= G.nspec) continue;
-    float rx = d2f_bits(U[(U_X0 + l) * pl + p]);
+    float rx = d2f_bits(U[(U_X0 + l) * pl + p] * sr);
     if (dU) rx += dU[(U_X0 + l) * pl + p];
     w[W_X0 + l] = rx * ir;
   }
@@ -98,7 +99,7 @@ struct StageMx {
 };
 
 __global__ void k_update_cells_mx(DevGeo G, Box box, StageMx S) {
-  const float dt = (float)*S.dt;
+  const float dt = (float)(*S.dt * G.isc_t);
   {
     int c[3];
     if (!cell3(box, c)) return;
@@ -135,7 +136,7 @@ __global__ void k_update_cells_mx(DevGeo G, Box box, StageMx S) {
       const long q = v * pl + ps;
       const float din = S.first ? 0.0f : S.dU[q];
       const float dout = S.b * (din - dt * r[v]);
-      if (S.last) S.U[q] += f2d_bits(dout);
+      if (S.last) S.U[q] += f2d_bits(dout) * usc(G, v);
       else S.dU[q] = dout;
     }
   }
@@ -144,7 +145,7 @@ __global__ void k_update_cells_mx(DevGeo G, Box box, StageMx S) {
 template <int D>
 __global__ void k_update_faces_mx(DevGeo G, Box box, StageMx S) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
-  const float dt = (float)*S.dt;
+  const float dt = (float)(*S.dt * G.isc_t);
   {
     int c[3];
     if (!cell3(box, c)) return;
@@ -158,7 +159,7 @@ __global__ void k_update_faces_mx(DevGeo G, Box box, StageMx S) {
     const long q = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
     const float din = S.first ? 0.0f : S.dB[q];
     const float dout = S.b * (din - dt * r);
-    if (S.last) S.B[q] += f2d_bits(dout);
+    if (S.last) S.B[q] += f2d_bits(dout) * G.sc_b;
     else S.dB[q] = dout;
   }
 }
@@ -200,8 +201,8 @@ __global__ void k_dt_mx(DevGeo G, Box box, const double *__restrict__ U, const d
   }
 }
 
-__global__ void k_dt_mx_finalize(double cfl, unsigned int *fmax_bits, double *dt) {
-  *dt = cfl / (double)__uint_as_float(*fmax_bits);
+__global__ void k_dt_mx_finalize(double cfl, double t_s, unsigned int *fmax_bits, double *dt) {
+  *dt = cfl * t_s / (double)__uint_as_float(*fmax_bits);
   *fmax_bits = 0u;
 }
 
@@ -211,7 +212,7 @@ void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigne
                      int *dflag, cudaStream_t s, int *nlaunch, Prof *prof) {
   Box b = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
   PHL_LAUNCH(KC_DT, prof, s, k_dt_mx<<<nblocks(b.n), TPB, 0, s>>>(G, b, U, Bf, fmax_bits, dflag));
-  PHL_LAUNCH(KC_DT, prof, s, k_dt_mx_finalize<<<1, 1, 0, s>>>(G.cfl, fmax_bits, dt));
+  PHL_LAUNCH(KC_DT, prof, s, k_dt_mx_finalize<<<1, 1, 0, s>>>(G.cfl, G.sc_t, fmax_bits, dt));
   if (nlaunch) *nlaunch += 2;
 }
 
@@ -229,8 +230,12 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
     int l[3], h[3];
     for (int d = 0; d < 3; ++d) rng(d, NGW, NGW, l[d], h[d]);
     Box bx = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
-    PHL_LAUNCH(KC_PRIM, prof, s, k_prim_mx<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, dU, dB, M.W, M.dflag));
-    ++nl;
+    if (G.eos == 1) {
+      launch_eos_cells<float>(G, M.U, M.B, dU, dB, M.Tin, M.Tout, M.W, M.dflag, s, &nl, prof);
+    } else {
+      PHL_LAUNCH(KC_PRIM, prof, s, k_prim_mx<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, dU, dB, M.W, M.dflag));
+      ++nl;
+    }
   }
   if (G.eps_sf > 0.0) {
     Box bx = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);

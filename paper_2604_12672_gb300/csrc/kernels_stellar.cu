@@ -1,0 +1,311 @@
+// kernels_stellar.cu -- stage steps of the stellar EOS path (Sect. 2.2):
+// the Newton inversion e_int -> T once per interior cell, ghost cells filled
+// from their source cells, the background's auxiliary indices, the CFL step,
+// and the primitive -> conserved conversion used to load a state.
+#include <math.h>
+
+#include "eos_stellar.cuh"
+#include "phl_internal.cuh"
+#include "stage_common.cuh"
+
+namespace phl {
+using namespace stage;
+namespace {
+
+// Mean mass number and electron fraction of normalised mass fractions.
+template <typename R>
+__device__ __forceinline__ void mixture(const DevGeo &G, const R *X, R &abar, R &ye) {
+  R sx = R(0), sa = R(0), sz = R(0);
+#pragma unroll
+  for (int l = 0; l < PHL_NSPEC_MAX; ++l)
+    if (l < G.nspec) sx += X[l];
+#pragma unroll
+  for (int l = 0; l < PHL_NSPEC_MAX; ++l)
+    if (l < G.nspec) {
+      const R x = X[l] / sx;
+      sa += x / (R)G.Acomp[l];
+      sz += (R)G.Zcomp[l] * x / (R)G.Acomp[l];
+    }
+  abar = R(1) / sa;
+  ye = sz;
+}
+
+// Interior cells: conserved -> primitives with the EOS.  FP64 path (R = double):
+// FP64 Newton.  Mixed path (R = float): FP32 Newton iterations to about 1e-6,
+// finished in FP64 to the same tolerance.  Writes the deviations W and T_out.
+template <typename R>
+__global__ void k_eos_cells(DevGeo G, Box box, const double *__restrict__ U, const double *__restrict__ Bf,
+                            const float *__restrict__ dU, const float *__restrict__ dB,
+                            const double *__restrict__ Tin, double *__restrict__ Tout, R *__restrict__ W,
+                            int *dflag) {
+  int c[3];
+  if (!cell3(box, c)) return;
+  const long p = sidx(G, c[0], c[1], c[2]);
+  const long pl = G.plane;
+  double u[5 + PHL_NSPEC_MAX];
+#pragma unroll
+  for (int v = 0; v < 5 + PHL_NSPEC_MAX; ++v) {
+    if (v >= G.nv) continue;
+    u[v] = U[v * pl + p];
+    if (dU) u[v] += (double)dU[v * pl + p] * usc(G, v);
+  }
+  double bl[3] = {Bf[p], Bf[pl + p], Bf[2 * pl + p]};
+  double bh[3] = {Bf[p + 1], Bf[pl + p + G.sy], Bf[2 * pl + p + G.sz]};
+  if (dB) {
+    const double s = G.sc_b;
+    bl[0] += dB[p] * s; bl[1] += dB[pl + p] * s; bl[2] += dB[2 * pl + p] * s;
+    bh[0] += dB[p + 1] * s; bh[1] += dB[pl + p + G.sy] * s; bh[2] += dB[2 * pl + p + G.sz] * s;
+  }
+  const double rho = u[0];
+  const double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
+  const double bx = 0.5 * (bl[0] + bh[0]), by = 0.5 * (bl[1] + bh[1]), bz = 0.5 * (bl[2] + bh[2]);
+  const double eint = u[4] / rho - 0.5 * (vx * vx + vy * vy + vz * vz) - 0.5 * (bx * bx + by * by + bz * bz) / rho;
+  double X[PHL_NSPEC_MAX];
+#pragma unroll
+  for (int l = 0; l < PHL_NSPEC_MAX; ++l)
+    if (l < G.nspec) X[l] = u[5 + l] / rho;
+  double abar, ye;
+  mixture<double>(G, X, abar, ye);
+  double T = Tin[p];
+  eos::EosOut<double> o;
+  int it;
+  if (sizeof(R) == 8)
+    it = eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
+  else
+    it = eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
+  if (it < 0 || !(o.P > 0.0) || !(rho > 0.0)) atomicOr(dflag, it < 0 ? FLAG_NEWTON : FLAG_NEG);
+  Tout[p] = T;
+  const Bg b = bg_cell(G, c[2]);
+  const long q = widx(G, c[0], c[1], c[2]);
+  const long wt = G.wtot;
+  // FP32 deviations are held in the mixed form's power-of-two units
+  const bool f32 = sizeof(R) == 4;
+  const double sr = f32 ? G.isc_rho : 1.0, sv = f32 ? G.isc_v : 1.0, sb = f32 ? G.isc_b : 1.0,
+               sp = f32 ? G.isc_e : 1.0;
+  W[W_RHO * wt + q] = (R)((rho - b.rho) * sr);
+  W[W_VX * wt + q] = (R)(vx * sv); W[W_VY * wt + q] = (R)(vy * sv); W[W_VZ * wt + q] = (R)(vz * sv);
+  W[W_BX * wt + q] = (R)(bx * sb); W[W_BY * wt + q] = (R)(by * sb); W[W_BZ * wt + q] = (R)(bz * sb);
+  W[W_P * wt + q] = (R)((o.P - b.p) * sp);
+  W[W_GE * wt + q] = (R)(o.ge - b.ge);
+  W[W_GC * wt + q] = (R)(o.gc - b.gc);
+#pragma unroll
+  for (int l = 0; l < PHL_NSPEC_MAX; ++l)
+    if (l < G.nspec) W[(W_X0 + l) * wt + q] = (R)X[l];
+}
+
+// Cells of the work layout outside the interior take the deviations of the
+// interior cell their data comes from (Table bcs), with the reflecting flips.
+template <typename R>
+__global__ void k_ghost_fill(DevGeo G, Box box, R *__restrict__ W) {
+  int c[3];
+  if (!cell3(box, c)) return;
+  int s[3];
+  bool fl[3], ghost = false;
+  for (int d = 0; d < 3; ++d) {
+    fl[d] = false;
+    s[d] = G.act[d] ? cell_src(c[d], G.n[d], G.bc[d][0], G.bc[d][1], fl[d]) : 0;
+    ghost |= s[d] != c[d];
+  }
+  if (!ghost) return;
+  const long qd = widx(G, c[0], c[1], c[2]), qs = widx(G, s[0], s[1], s[2]);
+  const long wt = G.wtot;
+#pragma unroll
+  for (int v = 0; v < NW_MAX; ++v) {
+    if (v >= G.nw) continue;
+    R x = W[v * wt + qs];
+    const bool flip = (v >= W_VX && v <= W_VZ && fl[v - W_VX]) || (v >= W_BX && v <= W_BZ && fl[v - W_BX]);
+    W[v * wt + qd] = flip ? -x : x;
+  }
+}
+
+// CFL condition with the stellar EOS (T guesses read, not written).
+template <typename R>
+__global__ void k_dt_stellar(DevGeo G, Box box, const double *__restrict__ U, const double *__restrict__ Bf,
+                             const double *__restrict__ Tin, unsigned long long *dmax, int *dflag) {
+  int c[3];
+  double m = 0.0;
+  if (cell3(box, c)) {
+    const long p = sidx(G, c[0], c[1], c[2]);
+    const long pl = G.plane;
+    const double rho = U[p];
+    const double v[3] = {U[pl + p] / rho, U[2 * pl + p] / rho, U[3 * pl + p] / rho};
+    const double bc[3] = {0.5 * (Bf[p] + Bf[p + 1]), 0.5 * (Bf[pl + p] + Bf[pl + p + G.sy]),
+                          0.5 * (Bf[2 * pl + p] + Bf[2 * pl + p + G.sz])};
+    const double b2 = bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2];
+    const double eint = U[4 * pl + p] / rho - 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) - 0.5 * b2 / rho;
+    double X[PHL_NSPEC_MAX];
+#pragma unroll
+    for (int l = 0; l < PHL_NSPEC_MAX; ++l)
+      if (l < G.nspec) X[l] = U[(5 + l) * pl + p] / rho;
+    double abar, ye;
+    mixture<double>(G, X, abar, ye);
+    R T = (R)Tin[p];
+    eos::EosOut<R> o;
+    if (sizeof(R) == 8) {
+      if (eos::eos_invert<R>(G.tab, (R)rho, (R)eint, (R)abar, (R)ye, T, (R)G.newton_tol, G.newton_maxit, o) < 0)
+        atomicOr(dflag, FLAG_NEWTON);
+    } else {
+      // the CFL step needs c_s to a few digits: FP32 Newton to 1e-5 (FP32's own
+      // floor for ln n, ln T is ~1e-6); a stalled iteration keeps its last,
+      // bracketed iterate
+      if (eos::eos_invert<R>(G.tab, (R)rho, (R)eint, (R)abar, (R)ye, T, (R)1e-5, 16, o) < 0 &&
+          !eos::eos_rt<R>(G.tab, (R)rho, T, (R)abar, (R)ye, o))
+        atomicOr(dflag, FLAG_NEWTON);
+    }
+    const double a2 = (double)o.gc * (double)o.P / rho, bb = b2 / rho;
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      if (!G.act[d]) continue;
+      const double bd2 = bc[d] * bc[d] / rho;
+      const double disc = fmax((a2 + bb) * (a2 + bb) - 4.0 * a2 * bd2, 0.0);
+      s += (fabs(v[d]) + sqrt(0.5 * (a2 + bb + sqrt(disc)))) / G.dx[d];
+    }
+    m = (s == s) ? s : INFINITY;
+  }
+  for (int o2 = 16; o2 > 0; o2 >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o2));
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+    atomicMax(dmax, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+__global__ void k_dt_finalize_st(double cfl, unsigned long long *dmax, double *dt) {
+  *dt = cfl / __longlong_as_double((long long)*dmax);
+  *dmax = 0ull;
+}
+
+// P -> T at fixed rho (Newton on P, bracketed in the table's range).
+__device__ bool p_to_T(const DevGeo &G, double rho, double P, double abar, double ye, double &T,
+                       eos::EosOut<double> &o) {
+  double lo = exp(G.tab.y0), hi = exp(G.tab.y0 + (G.tab.ny - 1) * G.tab.dy);
+  if (!(T > lo && T < hi)) T = sqrt(lo * hi);
+  for (int it = 0; it < 200; ++it) {
+    if (!eos::eos_rt<double>(G.tab, rho, T, abar, ye, o)) return false;
+    const double dp = P - o.P;
+    if (fabs(dp) <= 1e-14 * P) return true;
+    if (dp > 0.0) lo = T; else hi = T;
+    double Tn = T + dp / o.PT;
+    if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+    T = Tn;
+  }
+  return false;
+}
+
+// Background of the stellar path: T_hat, gamma_e, gamma_c at centres and
+// z-faces and E_hat = rho_hat e(rho_hat, T_hat) at centres, from rho_hat, P_hat.
+__global__ void k_bg_stellar(DevGeo G, int L, double *bg, double *bgX, int *fail) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * L) return;
+  const bool face = i >= L;
+  const int q = face ? i - L : i;
+  if (!face && q == L - 1) return;          // centres have one value fewer
+  const double rho = bg[(face ? 2 : 0) * L + q], P = bg[(face ? 3 : 1) * L + q];
+  double abar, ye;
+  mixture<double>(G, bgX, abar, ye);
+  double T = 1e9;
+  eos::EosOut<double> o;
+  if (!p_to_T(G, rho, P, abar, ye, T, o)) { atomicOr(fail, 1); return; }
+  bg[(face ? 6 : 4) * L + q] = o.ge;
+  bg[(face ? 7 : 5) * L + q] = o.gc;
+  if (!face) bg[8 * L + q] = rho * o.e;
+}
+
+// Primitive state (rho, v, P, X) -> conserved state and temperature.
+__global__ void k_prim_to_cons(DevGeo G, Box box, const double *__restrict__ prim, long np_,
+                               double *__restrict__ U, const double *__restrict__ Bf, double *__restrict__ T,
+                               int *dflag) {
+  int c[3];
+  if (!cell3(box, c)) return;
+  const long a = c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2]);   // ABI index
+  const long p = sidx(G, c[0], c[1], c[2]);
+  const long pl = G.plane;
+  const double rho = prim[a], P = prim[4 * np_ + a];
+  const double v[3] = {prim[np_ + a], prim[2 * np_ + a], prim[3 * np_ + a]};
+  double X[PHL_NSPEC_MAX];
+#pragma unroll
+  for (int l = 0; l < PHL_NSPEC_MAX; ++l)
+    if (l < G.nspec) X[l] = prim[(5 + l) * np_ + a];
+  const double bc[3] = {0.5 * (Bf[p] + Bf[p + 1]), 0.5 * (Bf[pl + p] + Bf[pl + p + G.sy]),
+                        0.5 * (Bf[2 * pl + p] + Bf[2 * pl + p + G.sz])};
+  double e;
+  double Tc = 0.0;
+  if (G.eos == 0) {
+    e = P / ((G.gamma - 1.0) * rho);
+  } else {
+    double abar, ye;
+    mixture<double>(G, X, abar, ye);
+    Tc = 1e9;
+    eos::EosOut<double> o;
+    if (!p_to_T(G, rho, P, abar, ye, Tc, o)) atomicOr(dflag, FLAG_NEWTON);
+    e = o.e;
+  }
+  U[p] = rho;
+  for (int d = 0; d < 3; ++d) U[(1 + d) * pl + p] = rho * v[d];
+  U[4 * pl + p] = rho * e + 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) +
+                  0.5 * (bc[0] * bc[0] + bc[1] * bc[1] + bc[2] * bc[2]);
+#pragma unroll
+  for (int l = 0; l < PHL_NSPEC_MAX; ++l)
+    if (l < G.nspec) U[(5 + l) * pl + p] = rho * X[l];
+  if (T) T[p] = Tc;
+}
+
+}  // namespace
+
+template <typename R>
+void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
+                      const double *Tin, double *Tout, R *W, int *dflag, cudaStream_t s, int *nl, Prof *prof) {
+  Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
+  PHL_LAUNCH(KC_PRIM, prof, s, k_eos_cells<R><<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout, W, dflag));
+  int l[3], h[3];
+  for (int d = 0; d < 3; ++d) {
+    if (G.act[d]) { l[d] = -NGW; h[d] = G.n[d] + NGW; } else { l[d] = 0; h[d] = 1; }
+  }
+  Box be = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
+  PHL_LAUNCH(KC_PRIM, prof, s, k_ghost_fill<R><<<grid3(be), block3(be), 0, s>>>(G, be, W));
+  if (nl) *nl += 2;
+}
+template void launch_eos_cells<double>(const DevGeo &, const double *, const double *, const float *, const float *,
+                                       const double *, double *, double *, int *, cudaStream_t, int *, Prof *);
+template void launch_eos_cells<float>(const DevGeo &, const double *, const double *, const float *, const float *,
+                                      const double *, double *, float *, int *, cudaStream_t, int *, Prof *);
+
+void launch_dt_stellar(const DevGeo &G, bool fp32, const double *U, const double *Bf, const double *T,
+                       unsigned long long *dmax, double *dt, int *dflag, cudaStream_t s, int *nl, Prof *prof) {
+  Box b = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
+  if (fp32)
+    PHL_LAUNCH(KC_DT, prof, s, k_dt_stellar<float><<<grid3(b), block3(b), 0, s>>>(G, b, U, Bf, T, dmax, dflag));
+  else
+    PHL_LAUNCH(KC_DT, prof, s, k_dt_stellar<double><<<grid3(b), block3(b), 0, s>>>(G, b, U, Bf, T, dmax, dflag));
+  PHL_LAUNCH(KC_DT, prof, s, k_dt_finalize_st<<<1, 1, 0, s>>>(G.cfl, dmax, dt));
+  if (nl) *nl += 2;
+}
+
+cudaError_t stellar_background(const DevGeo &G, int L, double *bg, const double *bgX_host) {
+  double *dX = nullptr;
+  int *fail = nullptr;
+  cudaError_t e = cudaMalloc(&dX, PHL_NSPEC_MAX * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&fail, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(dX, bgX_host, PHL_NSPEC_MAX * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(fail, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    k_bg_stellar<<<(2 * L + 63) / 64, 64>>>(G, L, bg, dX, fail);
+    int f = 0;
+    e = cudaMemcpy(&f, fail, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && f) e = cudaErrorInvalidValue;
+  }
+  cudaFree(dX);
+  cudaFree(fail);
+  return e;
+}
+
+void launch_prim_to_cons(const DevGeo &G, const double *prim, double *U, const double *Bf, double *T, int *dflag,
+                         cudaStream_t s) {
+  Box b = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
+  k_prim_to_cons<<<grid3(b), block3(b), 0, s>>>(G, b, prim, b.n, U, Bf, T, dflag);
+}
+
+}  // namespace phl

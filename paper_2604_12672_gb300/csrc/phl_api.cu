@@ -11,6 +11,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
+
+#include <utility>
 #include <vector>
 
 #include "phl.h"
@@ -58,7 +62,7 @@ struct phl_grid {
   DevGeo G;
   cudaStream_t stream;
   // state
-  double *U = nullptr, *U1 = nullptr, *B = nullptr, *B1 = nullptr, *T = nullptr;
+  double *U = nullptr, *U1 = nullptr, *B = nullptr, *B1 = nullptr, *T = nullptr, *T2 = nullptr;
   // background and heating profiles
   double *bg = nullptr, *heat = nullptr;
   float *bgf = nullptr, *heatf = nullptr;
@@ -131,7 +135,9 @@ phl_status check_flags(phl_grid *g) {
 
 void launch_dt(phl_grid *g, int *nl) {
   Prof *pf = g->prof.on ? &g->prof : nullptr;
-  if (g->mixed)
+  if (g->G.eos == PHL_EOS_STELLAR)
+    launch_dt_stellar(g->G, g->mixed, g->U, g->B, g->T, g->dmax, g->dt, g->dflag, g->stream, nl, pf);
+  else if (g->mixed)
     launch_dt_mixed(g->G, g->U, g->B, g->fmax, g->dt, g->dflag, g->stream, nl, pf);
   else
     launch_dt_fp64(g->G, g->U, g->B, g->T, g->dmax, g->dt, g->dflag, g->stream, nl, pf);
@@ -143,8 +149,9 @@ void do_stage(phl_grid *g, const double *Uin, const double *Bin, double *Uout, d
   S.Uin = Uin; S.Bin = Bin; S.Ubase = g->U; S.Bbase = g->B;
   S.Uout = Uout; S.Bout = Bout; S.a = a; S.b = b; S.dt = g->dt;
   S.W = g->W; S.F[0] = g->F[0]; S.F[1] = g->F[1]; S.F[2] = g->F[2]; S.E = g->E;
-  S.raw = g->raw; S.flag = g->flag; S.T = g->T; S.dflag = g->dflag;
+  S.raw = g->raw; S.flag = g->flag; S.Tin = g->T; S.Tout = g->T2; S.dflag = g->dflag;
   launch_stage_fp64(g->G, S, g->stream, nl, g->prof.on ? &g->prof : nullptr);
+  if (g->T) std::swap(g->T, g->T2);   // this stage's temperatures are the next guesses
 }
 
 }  // namespace
@@ -167,7 +174,13 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
       return fail(PHL_EINVAL, "periodic boundaries must be periodic on both sides");
   }
   if (d->nspec < 0 || d->nspec > PHL_MAXSPEC) return fail(PHL_EINVAL, "nspec out of range");
-  if (d->eos != PHL_EOS_IDEAL) return fail(PHL_EUNSUPPORTED, "stellar EOS not available in this build");
+  if (d->eos != PHL_EOS_IDEAL && d->eos != PHL_EOS_STELLAR) return fail(PHL_EINVAL, "bad eos");
+  if (d->eos == PHL_EOS_STELLAR) {
+    if (!d->eos_table) return fail(PHL_EINVAL, "stellar EOS needs an eos_table");
+    if (d->nspec < 1) return fail(PHL_EINVAL, "stellar EOS needs mass fractions (nspec >= 1)");
+    for (int l = 0; l < d->nspec; ++l)
+      if (!(d->A[l] > 0.0) || !(d->Z[l] > 0.0)) return fail(PHL_EINVAL, "species A, Z must be positive");
+  }
   if (!(d->gamma > 1.0)) return fail(PHL_EINVAL, "gamma must exceed 1");
   if (!(d->cfl > 0.0)) return fail(PHL_EINVAL, "cfl must be positive");
   if (d->rk != 2 && d->rk != 3) return fail(PHL_EINVAL, "rk must be 2 or 3");
@@ -210,11 +223,40 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   G.eps_sf = d->eps_sf;
   G.mach_thr = d->mach_thr;
   G.cfl = d->cfl;
-  for (int k = 0; k < 3; ++k) { G.idxf[k] = (float)G.idx[k]; G.gf[k] = (float)d->g[k]; }
+  {   // power-of-two unit scales of the mixed form's FP32 quantities
+    double rho_ref = 1.0, p_ref = 1.0, dx_min = 0.0;
+    if (d->bg_rho_c && d->bg_p_c) {
+      rho_ref = p_ref = 0.0;
+      for (int k = 0; k < d->n[2] + 2 * BG_NG; ++k) {
+        rho_ref = std::max(rho_ref, std::fabs(d->bg_rho_c[k]));
+        p_ref = std::max(p_ref, std::fabs(d->bg_p_c[k]));
+      }
+      if (!(rho_ref > 0.0) || !(p_ref > 0.0)) rho_ref = p_ref = 1.0;
+    }
+    for (int k = 0; k < 3; ++k)
+      if (G.act[k]) dx_min = dx_min > 0.0 ? std::min(dx_min, G.dx[k]) : G.dx[k];
+    if (!(dx_min > 0.0)) dx_min = 1.0;
+    const int ea = (int)std::lround(0.5 * std::log2(p_ref)), eb = (int)std::lround(0.5 * std::log2(rho_ref));
+    const double P_s = std::ldexp(1.0, 2 * ea), rho_s = std::ldexp(1.0, 2 * eb);
+    const double v_s = std::ldexp(1.0, ea - eb), B_s = std::ldexp(1.0, ea);
+    const double L_s = std::ldexp(1.0, (int)std::lround(std::log2(dx_min)));
+    const double t_s = L_s / v_s;
+    G.sc_rho = rho_s; G.sc_m = rho_s * v_s; G.sc_e = P_s; G.sc_b = B_s; G.sc_t = t_s;
+    G.isc_rho = 1.0 / rho_s; G.isc_m = 1.0 / (rho_s * v_s); G.isc_e = 1.0 / P_s; G.isc_b = 1.0 / B_s;
+    G.isc_t = 1.0 / t_s; G.isc_v = 1.0 / v_s;
+    for (int k = 0; k < 3; ++k) {
+      G.idxf[k] = (float)(G.idx[k] * L_s);
+      G.gf[k] = (float)(d->g[k] * t_s * t_s / L_s);
+    }
+  }
   G.gammaf = (float)d->gamma;
   G.gm1f = (float)(d->gamma - 1.0);
   G.machf = (float)d->mach_thr;
   G.epsf = (float)d->eps_sf;
+  G.newton_tol = d->newton_tol > 0.0 ? d->newton_tol : 1e-11;
+  G.newton_maxit = d->newton_maxit > 0 ? d->newton_maxit : 50;
+  for (int l = 0; l < PHL_NSPEC_MAX; ++l) { G.Acomp[l] = d->A[l]; G.Zcomp[l] = d->Z[l]; }
+  if (d->eos == PHL_EOS_STELLAR) G.tab = *eos_table_view(d->eos_table);
 
   phl_status st = PHL_OK;
 #define AL(p, n)                                  \
@@ -242,6 +284,10 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     AL(&g->fmax, 1);
   }
   AL(&g->raw, 2 * ncell);   // raw flags + one dilation pass buffer
+  if (d->eos == PHL_EOS_STELLAR) {
+    AL(&g->T, G.plane);
+    AL(&g->T2, G.plane);
+  }
   AL(&g->flag, G.wtot);
   AL(&g->dt, 1);
   AL(&g->dmax, 1);
@@ -261,30 +307,42 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
       memcpy(&h[q * L], src[q], cnt * sizeof(double));
     }
     for (long q = 0; q < L - 1; ++q) h[8 * L + q] = d->bg_p_c[q] / (d->gamma - 1.0);   // E_hat
+    const bool stellar_bg = d->eos == PHL_EOS_STELLAR && !d->bg_ge_c;
+    const bool gam = d->bg_ge_c || stellar_bg;
+    if (stellar_bg) {   // gamma_e, gamma_c, E_hat of the background from the device EOS
+      cudaError_t e0 = cudaMemcpy(g->bg, h.data(), nbg * sizeof(double), cudaMemcpyHostToDevice);
+      if (e0 == cudaSuccess) e0 = stellar_background(G, (int)L, g->bg, d->bg_X);
+      if (e0 == cudaSuccess) e0 = cudaMemcpy(h.data(), g->bg, nbg * sizeof(double), cudaMemcpyDeviceToHost);
+      if (e0 != cudaSuccess) { phl_destroy(g); return cuda_fail(e0, "stellar background"); }
+    }
     std::vector<float> hf(nbg);
-    for (long q = 0; q < nbg; ++q) hf[q] = (float)h[q];
+    for (long q = 0; q < nbg; ++q) {   // rho rows 0, 2; pressure rows 1, 3, 8 scaled
+      const long row = q / L;
+      const double sc = (row == 0 || row == 2) ? G.isc_rho : ((row == 1 || row == 3 || row == 8) ? G.isc_e : 1.0);
+      hf[q] = (float)(h[q] * sc);
+    }
     cudaError_t e = cudaMemcpy(g->bg, h.data(), nbg * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { phl_destroy(g); return cuda_fail(e, "copy background"); }
     e = cudaMemcpy(g->bgf, hf.data(), nbg * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { phl_destroy(g); return cuda_fail(e, "copy background"); }
     G.bgf_rho_c = g->bgf; G.bgf_p_c = g->bgf + L; G.bgf_rho_f = g->bgf + 2 * L; G.bgf_p_f = g->bgf + 3 * L;
-    G.bgf_ge_c = d->bg_ge_c ? g->bgf + 4 * L : nullptr;
-    G.bgf_gc_c = d->bg_gc_c ? g->bgf + 5 * L : nullptr;
-    G.bgf_ge_f = d->bg_ge_f ? g->bgf + 6 * L : nullptr;
-    G.bgf_gc_f = d->bg_gc_f ? g->bgf + 7 * L : nullptr;
+    G.bgf_ge_c = gam ? g->bgf + 4 * L : nullptr;
+    G.bgf_gc_c = gam ? g->bgf + 5 * L : nullptr;
+    G.bgf_ge_f = gam ? g->bgf + 6 * L : nullptr;
+    G.bgf_gc_f = gam ? g->bgf + 7 * L : nullptr;
     G.bg_e_c = g->bg + 8 * L;
     G.has_bg = 1;
     G.bg_rho_c = g->bg; G.bg_p_c = g->bg + L; G.bg_rho_f = g->bg + 2 * L; G.bg_p_f = g->bg + 3 * L;
-    G.bg_ge_c = d->bg_ge_c ? g->bg + 4 * L : nullptr;
-    G.bg_gc_c = d->bg_gc_c ? g->bg + 5 * L : nullptr;
-    G.bg_ge_f = d->bg_ge_f ? g->bg + 6 * L : nullptr;
-    G.bg_gc_f = d->bg_gc_f ? g->bg + 7 * L : nullptr;
+    G.bg_ge_c = gam ? g->bg + 4 * L : nullptr;
+    G.bg_gc_c = gam ? g->bg + 5 * L : nullptr;
+    G.bg_ge_f = gam ? g->bg + 6 * L : nullptr;
+    G.bg_gc_f = gam ? g->bg + 7 * L : nullptr;
   }
   if (d->heat) {
     AL(&g->heat, nz);
     AL(&g->heatf, nz);
     std::vector<float> hf(nz);
-    for (int q = 0; q < nz; ++q) hf[q] = (float)d->heat[q];
+    for (int q = 0; q < nz; ++q) hf[q] = (float)(d->heat[q] * G.sc_t * G.isc_e);   // scaled units
     cudaError_t e = cudaMemcpy(g->heat, d->heat, nz * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->heatf, hf.data(), nz * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { phl_destroy(g); return cuda_fail(e, "copy heating"); }
@@ -313,7 +371,8 @@ phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx, cons
                          const double *bz, const double *T, int where) {
   if (!g || !cons || !bx || !by || !bz) return fail(PHL_EINVAL, "null argument");
   if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
-  (void)T;
+  if (g->G.eos == PHL_EOS_STELLAR && !T)
+    return fail(PHL_EINVAL, "stellar EOS: give T (Newton guesses) or use phl_set_state_prim");
   const DevGeo &G = g->G;
   const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
   const long nc = (long)nx * ny * nz;
@@ -323,6 +382,8 @@ phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx, cons
   if ((st = copy_field(g, g->B, bx, nullptr, nx + 1, ny, nz, true)) != PHL_OK) return st;
   if ((st = copy_field(g, g->B + G.plane, by, nullptr, nx, ny + 1, nz, true)) != PHL_OK) return st;
   if ((st = copy_field(g, g->B + 2 * G.plane, bz, nullptr, nx, ny, nz + 1, true)) != PHL_OK) return st;
+  if (g->T && T)
+    if ((st = copy_field(g, g->T, T, nullptr, nx, ny, nz, true)) != PHL_OK) return st;
   CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream), "reset flags");
   if (where == PHL_HOST) CK(cudaStreamSynchronize(g->stream), "sync");
   return PHL_OK;
@@ -331,7 +392,6 @@ phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx, cons
 phl_status phl_get_state(phl_grid *g, double *cons, double *bx, double *by, double *bz, double *T, int where) {
   if (!g || !cons || !bx || !by || !bz) return fail(PHL_EINVAL, "null argument");
   if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
-  (void)T;
   const DevGeo &G = g->G;
   const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
   const long nc = (long)nx * ny * nz;
@@ -341,6 +401,39 @@ phl_status phl_get_state(phl_grid *g, double *cons, double *bx, double *by, doub
   if ((st = copy_field(g, g->B, nullptr, bx, nx + 1, ny, nz, false)) != PHL_OK) return st;
   if ((st = copy_field(g, g->B + G.plane, nullptr, by, nx, ny + 1, nz, false)) != PHL_OK) return st;
   if ((st = copy_field(g, g->B + 2 * G.plane, nullptr, bz, nx, ny, nz + 1, false)) != PHL_OK) return st;
+  if (g->T && T)
+    if ((st = copy_field(g, g->T, nullptr, T, nx, ny, nz, false)) != PHL_OK) return st;
+  return check_flags(g);
+}
+
+phl_status phl_set_state_prim(phl_grid *g, const double *prim, const double *bx, const double *by,
+                              const double *bz, int where) {
+  if (!g || !prim || !bx || !by || !bz) return fail(PHL_EINVAL, "null argument");
+  if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
+  const DevGeo &G = g->G;
+  const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+  const long nc = (long)nx * ny * nz;
+  phl_status st;
+  if ((st = copy_field(g, g->B, bx, nullptr, nx + 1, ny, nz, true)) != PHL_OK) return st;
+  if ((st = copy_field(g, g->B + G.plane, by, nullptr, nx, ny + 1, nz, true)) != PHL_OK) return st;
+  if ((st = copy_field(g, g->B + 2 * G.plane, bz, nullptr, nx, ny, nz + 1, true)) != PHL_OK) return st;
+  const double *dprim = prim;
+  double *tmp = nullptr;
+  if (where == PHL_HOST) {
+    CK(cudaMalloc(&tmp, (size_t)(5 + G.nspec) * nc * sizeof(double)), "alloc primitive staging");
+    cudaError_t e = cudaMemcpyAsync(tmp, prim, (size_t)(5 + G.nspec) * nc * sizeof(double), cudaMemcpyHostToDevice,
+                                    g->stream);
+    if (e != cudaSuccess) { cudaFree(tmp); return cuda_fail(e, "copy primitives"); }
+    dprim = tmp;
+  }
+  CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream), "reset flags");
+  launch_prim_to_cons(G, dprim, g->U, g->B, g->T, g->dflag, g->stream);
+  cudaError_t e = cudaGetLastError();
+  if (tmp) {
+    cudaStreamSynchronize(g->stream);
+    cudaFree(tmp);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "primitive -> conserved");
   return check_flags(g);
 }
 
@@ -374,9 +467,13 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
       M.U = g->U; M.B = g->B; M.dU = g->dUf; M.dB = g->dBf; M.W = g->Wf;
       M.F[0] = g->Ff[0]; M.F[1] = g->Ff[1]; M.F[2] = g->Ff[2]; M.E = g->Ef;
       M.raw = g->raw; M.flag = g->flag; M.dt = g->dt; M.dflag = g->dflag;
-      for (int st = 0; st < ns; ++st)
+      for (int st = 0; st < ns; ++st) {
+        M.Tin = g->T;
+        M.Tout = g->T2;
         launch_stage_mixed(g->G, M, st, ns, ns == 2 ? bs2[st] : bs3[st], g->stream, &nl,
                            g->prof.on ? &g->prof : nullptr);
+        if (g->T) std::swap(g->T, g->T2);
+      }
     } else if (g->desc.rk == 2) {
       do_stage(g, g->U, g->B, g->U1, g->B1, 0.0, 1.0, &nl);
       do_stage(g, g->U1, g->B1, g->U, g->B, 0.5, 0.5, &nl);

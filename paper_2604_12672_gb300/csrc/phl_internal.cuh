@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "eos_stellar.cuh"
 #include "riemann.cuh"
 
 namespace phl {
@@ -54,11 +55,23 @@ struct DevGeo {
   int riemann;
   double eps_sf, mach_thr, cfl;
   // FP32 copies for the mixed-precision kernels (no per-thread conversions)
-  float idxf[3], gf[3], gammaf, gm1f, machf, epsf;
+  // Mixed form: the FP32 quantities are held in units of powers of two
+  // (rho_s, P_s, v_s = sqrt(P_s / rho_s), B_s = sqrt(P_s), L_s, t_s = L_s / v_s)
+  // near the background's scales, so stellar CGS magnitudes (P ~ 1e24) stay
+  // far inside the FP32 range.  Multiplying by a power of two is exact, so the
+  // scaling changes no rounding.  sc_* turn scaled values into physical ones.
+  double sc_rho, sc_m, sc_e, sc_b, sc_t;
+  double isc_rho, isc_m, isc_e, isc_b, isc_t, isc_v;
+  float idxf[3], gf[3], gammaf, gm1f, machf, epsf;   // idxf, gf in scaled units
   const float *bgf_rho_c, *bgf_p_c, *bgf_rho_f, *bgf_p_f;   // null without background
   const float *bgf_ge_c, *bgf_gc_c, *bgf_ge_f, *bgf_gc_f;
   const float *heatf;
   const double *bg_e_c;        // E_hat = P_hat / (gamma - 1) at cell centres (FP64)
+  // stellar EOS
+  eos::Table tab;
+  double Acomp[PHL_NSPEC_MAX], Zcomp[PHL_NSPEC_MAX];
+  double newton_tol;
+  int newton_maxit;
 };
 
 __host__ __device__ __forceinline__ long sidx(const DevGeo &G, int i, int j, int k) {
@@ -213,7 +226,8 @@ struct StageBufs {
   double *F[3];                // nf flux fields per direction
   double *E;                   // 3 edge-EMF fields
   uint8_t *raw, *flag;         // raw flags (interior), dilated flags (work layout)
-  double *T;                   // temperature (stellar), state layout
+  const double *Tin;           // temperature guesses (stellar), state layout
+  double *Tout;                // temperatures found by this stage
   int *dflag;                  // device error word
 };
 
@@ -226,11 +240,32 @@ struct MixedBufs {
   uint8_t *raw, *flag;
   const double *dt;
   int *dflag;
+  const double *Tin;           // stellar EOS: guesses in, temperatures out
+  double *Tout;
 };
 void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
                         int *nlaunch, Prof *prof);
 void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigned int *fmax_bits, double *dt,
                      int *dflag, cudaStream_t s, int *nlaunch, Prof *prof);
+
+// Stellar EOS path (kernels_stellar.cu)
+template <typename R>
+void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
+                      const double *Tin, double *Tout, R *W, int *dflag, cudaStream_t s, int *nl, Prof *prof);
+void launch_dt_stellar(const DevGeo &G, bool fp32, const double *U, const double *Bf, const double *T,
+                       unsigned long long *dmax, double *dt, int *dflag, cudaStream_t s, int *nl, Prof *prof);
+cudaError_t stellar_background(const DevGeo &G, int L, double *bg, const double *bgX_host);
+void launch_prim_to_cons(const DevGeo &G, const double *prim, double *U, const double *Bf, double *T, int *dflag,
+                         cudaStream_t s);
+const eos::Table *eos_table_view(const struct phl_eos_table *t);
+
+// Scale of conserved variable v of the mixed form (rho, m, E, rho X).
+__host__ __device__ __forceinline__ double usc(const DevGeo &G, int v) {
+  return (v >= 1 && v <= 3) ? G.sc_m : (v == 4 ? G.sc_e : G.sc_rho);
+}
+__host__ __device__ __forceinline__ double iusc(const DevGeo &G, int v) {
+  return (v >= 1 && v <= 3) ? G.isc_m : (v == 4 ? G.isc_e : G.isc_rho);
+}
 
 // Records the calling thread's last-error message (phl_last_error) and
 // returns st (phl_api.cu).

@@ -224,7 +224,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_flux(DevGeo G, 
     }
     const long qb = (long)D * G.plane + sidx(G, s[0], s[1], s[2]);
     R bn;
-    if constexpr (sizeof(R) == 4) bn = dB ? d2f_bits(Bf[qb]) + dB[qb] : d2f_bits(Bf[qb]);   // B^n + dB
+    if constexpr (sizeof(R) == 4) {   // B^n + dB in scaled units
+      const float b0 = d2f_bits(Bf[qb] * G.isc_b);
+      bn = dB ? b0 + dB[qb] : b0;
+    }
     else bn = (R)Bf[qb];
     const int solver = (flag[pL] | flag[pR]) ? SOLVER_HLL : G.riemann;
     R f[7 + NS];

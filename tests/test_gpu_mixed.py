@@ -146,3 +146,39 @@ def test_mixed_mass_conservation_periodic(P):
     for v_ in (0, 4):
         t0 = pr.cons[v_].sum()
         assert abs(out["cons"][v_].sum() - t0) <= 1e-10 * abs(t0), v_
+
+
+def test_mixed_form_is_unit_invariant(P):
+    """The FP32 quantities are held in power-of-two units near the
+    background's scales: the same box in units where P ~ 2^80 (stellar CGS
+    magnitudes, whose squares overflow FP32) steps to the exactly rescaled
+    result of the unit box."""
+    pr = W.stratified_box(16, 16, 32, amp=3e-2, beta=1e3, mach_heat=3e-2)
+    s_rho, s_p, s_l = 2.0 ** 24, 2.0 ** 80, 2.0 ** 27
+    s_v = 2.0 ** 28                      # sqrt(s_p / s_rho)
+    s_b, s_t = 2.0 ** 40, s_l / s_v
+    q = pr.copy()
+    q.lo = tuple(x * s_l for x in pr.lo)
+    q.hi = tuple(x * s_l for x in pr.hi)
+    q.g = tuple(x * s_v * s_v / s_l for x in pr.g)
+    q.cons = pr.cons.copy()
+    q.cons[0] *= s_rho
+    q.cons[1:4] *= s_rho * s_v
+    q.cons[4] *= s_p
+    q.bx, q.by, q.bz = pr.bx * s_b, pr.by * s_b, pr.bz * s_b
+    q.bg = dict(rho_c=pr.bg["rho_c"] * s_rho, rho_f=pr.bg["rho_f"] * s_rho,
+                p_c=pr.bg["p_c"] * s_p, p_f=pr.bg["p_f"] * s_p)
+    q.heat = pr.heat * s_p / s_t
+    out = []
+    for prob in (pr, q):
+        g = P.Grid(prob, precision="mixed")
+        g.load()
+        g.step(6)
+        out.append(g.get_state())
+        g.close()
+    a, b = out
+    assert np.array_equal(b["cons"][0], a["cons"][0] * s_rho)
+    assert np.array_equal(b["cons"][1:4], a["cons"][1:4] * (s_rho * s_v))
+    assert np.array_equal(b["cons"][4], a["cons"][4] * s_p)
+    for k in ("bx", "by", "bz"):
+        assert np.array_equal(b[k], a[k] * s_b)

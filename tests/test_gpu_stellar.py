@@ -1,0 +1,181 @@
+"""Stellar EOS on the device vs the CPU oracle.
+
+The device builds its own free-energy table with its own quadrature and runs
+its own Newton inversions; the oracle does the same on the CPU.  Compared:
+the table nodes, batch inversions, the primitive -> conserved loading, and
+whole RK steps of the stratified stellar box (FP64 to 1e-11 relative
+L-infinity per field; the mixed form to the L1 bar of 1e-5 per field).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+A, Z = W.STELLAR_A, W.STELLAR_Z
+X = W.STELLAR_X
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2604_12672_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def tables(P):
+    return P.EosTable(), O.EosTable()
+
+
+def mixture(Xs):
+    abar = 1.0 / sum(x / a for x, a in zip(Xs, A))
+    ye = sum(x * z / a for x, z, a in zip(Xs, Z, A))
+    return abar, ye
+
+
+def rel_linf(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_table_nodes_match_oracle(tables):
+    """Both quadratures converge to rounding, so the nodes agree to 1e-12
+    where nothing cancels.  f = n mu - P (hot pairs), f_x = n eta k T (eta
+    crossing 0), f_y = -T s and f_xy = n k T (eta + b d eta/d b) (strongly
+    degenerate electrons, T s / (n mu) ~ (pi / eta)^2) are small differences of
+    terms of size |f| + |f_x| in parts of the table: there each side's
+    rounding of those terms bounds the agreement (2e-13 of |f| + |f_x|)."""
+    dt, ot = tables
+    a, b = dt.export(), ot.export()
+    assert a.shape == b.shape
+    assert np.array_equal(a[:6], b[:6])
+    n = (a.size - 6) // 4
+    va, vb = a[6:].reshape(n, 4), b[6:].reshape(n, 4)
+    big = np.abs(vb[:, 0]) + np.abs(vb[:, 1])
+    for c in range(4):
+        err = np.abs(va[:, c] - vb[:, c])
+        bound = 1e-12 * np.abs(vb[:, c]) + 2e-13 * big
+        worst = int(np.argmax(err / bound))
+        assert (err <= bound).all(), (c, worst, va[worst, c], vb[worst, c])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_inversion_vs_oracle(P, tables, precision):
+    dt, ot = tables
+    rng = np.random.Generator(np.random.PCG64(77))
+    n = 400
+    rho = 10 ** rng.uniform(4.5, 7.5, n)
+    T = 10 ** rng.uniform(7.7, 9.7, n)
+    Xo = rng.uniform(0.05, 0.95, n)
+    cfg = O.stellar_cfg(A, Z, ot)
+    e = np.empty(n)
+    Tref = np.empty(n)
+    Pref, ge, gc = np.empty(n), np.empty(n), np.empty(n)
+    abar, ye = np.empty(n), np.empty(n)
+    guess = T * 10 ** rng.uniform(-0.3, 0.3, n)
+    for i in range(n):
+        Xs = [Xo[i], 1 - Xo[i]]
+        e[i] = O.eos_rt(cfg, rho[i], T[i], Xs)["e"]
+        r = O.eos_invert(cfg, rho[i], e[i], Xs, guess[i])
+        Tref[i], Pref[i], ge[i], gc[i] = r["T"], r["P"], r["gamma_e"], r["gamma_c"]
+        abar[i], ye[i] = mixture(Xs)
+    out = P.eos(dt, rho, e, abar, ye, guess, precision=precision)
+    # the oracle's own inversion reproduces the temperature it started from
+    assert np.abs(Tref / T - 1).max() < 1e-9
+    # T, P, gamma_e use first derivatives of f, which the two tables hold to
+    # ~1e-13; gamma_c also uses f_xx, f_yy, f_xy, whose node values agree only
+    # to ~1e-13 of |f| + |f_x| (the cancellations of the strongly degenerate
+    # corner), so its bar is wider.
+    tol = 1e-11
+    assert np.abs(out["T"] / Tref - 1).max() <= tol, np.abs(out["T"] / Tref - 1).max()
+    for k, ref, t in (("P", Pref, tol), ("gamma_e", ge, tol), ("gamma_c", gc, 1e-9)):
+        assert np.abs(out[k] / ref - 1).max() <= t, (k, np.abs(out[k] / ref - 1).max())
+    cs = np.sqrt(gc * Pref / rho)
+    assert np.abs(out["cs"] / cs - 1).max() <= 1e-9
+    assert (out["iters"] >= 1).all() and (out["iters"] <= 62).all()
+
+
+def _stellar(nx, ny, nz, **kw):
+    return W.stellar_box(nx, ny, nz, **kw)
+
+
+def test_prim_to_cons_and_background_vs_oracle(P, tables):
+    dt, ot = tables
+    pr = _stellar(8, 8, 24)
+    ref = O.prepare_stellar(pr, ot)
+    g = P.Grid(pr, eos_table=dt)
+    g.load()
+    st = g.get_state()
+    g.close()
+    assert rel_linf(st["cons"][4], ref.cons[4]) <= 1e-12
+    assert rel_linf(st["T"], ref.T) <= 1e-11
+    for v in (0, 5, 6):
+        assert np.array_equal(st["cons"][v], pr.cons[v])
+
+
+@pytest.mark.parametrize("riemann", ["lhlld", "hll"])
+def test_stellar_box_fp64_parity(P, tables, riemann):
+    """Relative L-infinity per field <= 1e-11 after 8 RK3 steps.  The box
+    starts with Mach ~1e-2 velocities: from rest in pressure equilibrium the
+    first horizontal momenta would be driven by pressure differences at the
+    level of the two tables' ~1e-13 disagreement and measure only that."""
+    dt, ot = tables
+    pr = _stellar(16, 16, 32, amp=3e-2, beta=1e3, mach_heat=3e-2, vel_amp=1e-2)
+    ref = O.prepare_stellar(pr, ot)
+    g = P.Grid(pr, eos_table=dt, riemann=riemann)
+    g.load()
+    nsteps = 8
+    g.step(nsteps)
+    st = g.get_state()
+    g.close()
+    out, _, _ = O.Oracle(ref, eos_table=ot.h, riemann=riemann).run(nsteps)
+    for v in range(st["cons"].shape[0]):
+        e = rel_linf(st["cons"][v], out["cons"][v])
+        assert e <= 1e-11, (v, e)
+    for k in ("bx", "by", "bz"):
+        e = rel_linf(st[k], out[k])
+        assert e <= 1e-11, (k, e)
+    assert rel_linf(st["T"], out["T"]) <= 1e-10
+
+
+def test_stellar_box_mixed_l1(P, tables):
+    dt, ot = tables
+    pr = _stellar(16, 16, 32, amp=3e-2, beta=1e3, mach_heat=3e-2, vel_amp=1e-2)
+    ref = O.prepare_stellar(pr, ot)
+    g = P.Grid(pr, eos_table=dt, precision="mixed")
+    g.load()
+    nsteps = 8
+    g.step(nsteps)
+    st = g.get_state()
+    g.close()
+    out, _, _ = O.Oracle(ref, eos_table=ot.h).run(nsteps)
+    for v in range(st["cons"].shape[0]):
+        if v in (1, 2, 3):
+            scale = np.abs(out["cons"][0]).sum() * np.sqrt(np.abs(out["cons"][4] / out["cons"][0]).mean())
+        else:
+            scale = np.abs(out["cons"][v]).sum()
+        l1 = np.abs(st["cons"][v] - out["cons"][v]).sum() / scale
+        assert l1 <= 1e-5, (v, l1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stellar_hydrostatic_rest(P, tables, precision):
+    """Unperturbed, unheated, field-free stellar atmosphere: the well-balanced
+    scheme keeps it at rest (velocities at rounding level of the sound speed)."""
+    dt, _ = tables
+    pr = _stellar(8, 8, 32, amp=0.0, heat=False, beta=1e30)
+    g = P.Grid(pr, eos_table=dt, precision=precision)
+    g.load()
+    g.step(20)
+    st = g.get_state()
+    g.close()
+    rho = st["cons"][0]
+    v = np.abs(st["cons"][1:4] / rho).max()
+    cs = np.sqrt(5.0 / 3.0 * W.STELLAR_P_BASE / W.STELLAR_RHO_BASE)
+    lim = 1e-12 if precision == "fp64" else 1e-6
+    assert v <= lim * cs, v / cs

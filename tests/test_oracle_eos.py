@@ -28,13 +28,15 @@ def table():
 
 
 @pytest.mark.parametrize("k", [0.5, 1.5, 2.5])
-@pytest.mark.parametrize("eta", [-30.0, -5.0, 0.0, 3.0, 20.0, 200.0])
+@pytest.mark.parametrize("eta", [-30.0, -5.0, 0.0, 3.0, 20.0, 200.0, 1000.0, 2500.0])
 def test_fd_integral_nonrelativistic_polylog(k, eta):
+    """b -> 0: F_k(eta) = -Gamma(k + 1) Li_{k+1}(-e^eta), up to the strongly
+    degenerate electrons at the cold, dense corner of the table (eta ~ 2000)."""
     mpmath = pytest.importorskip("mpmath")
-    mpmath.mp.dps = 30
+    mpmath.mp.dps = 40
     exact = float(mpmath.re(-mpmath.gamma(k + 1) * mpmath.polylog(k + 1, -mpmath.exp(mpmath.mpf(eta)))))
-    got = O.fd(k, eta, 1e-14)
-    assert abs(got - exact) <= 1e-12 * abs(exact), (got, exact)
+    got = O.fd(k, eta, 1e-22)
+    assert abs(got - exact) <= 1e-13 * abs(exact), (got, exact)
 
 
 @pytest.mark.parametrize("beta", [0.1, 1.0, 5.0])
@@ -60,6 +62,21 @@ def test_nondegenerate_limit():
     r = O.ep_direct(rho, ye, T)
     n = rho * ye * N_A
     assert abs(r["e"] * rho / (1.5 * n * K_B * T) - 1) < 1e-5
+
+
+@pytest.mark.parametrize("rho,T", [(1e8, 1e7), (3e7, 1e7), (1e8, 3e7)])
+def test_degenerate_entropy_sommerfeld(rho, T):
+    """Strong degeneracy: s = (pi^2 / 3) k^2 T g(E_F), g = 8 pi p_F E_F / (c^2 h^3)
+    the density of states at the Fermi surface; the next term of the
+    expansion is O((pi / eta)^2) relative."""
+    n = rho * N_A
+    pf = H * (3 * n / (8 * math.pi)) ** (1 / 3)
+    ef = math.sqrt((pf * C_L) ** 2 + ME_C2 ** 2)
+    g = 8 * math.pi * pf * ef / (C_L ** 2 * H ** 3)
+    s_vol = math.pi ** 2 / 3 * K_B ** 2 * T * g
+    r = O.ep_direct(rho, 1.0, T)
+    assert r["eta"] > 500
+    assert abs(r["s"] * rho / s_vol - 1) <= 10 * (math.pi / r["eta"]) ** 2, (r["s"] * rho, s_vol)
 
 
 def test_complete_degeneracy_chandrasekhar():

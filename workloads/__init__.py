@@ -350,6 +350,84 @@ def isothermal_atmosphere(nx, nz, c2=1.0, g0=1.0, ndim=2, cfl=0.4, b0=0.0):
                      g=(0.0, 0.0, -g0), bg=bg, cfl=cfl)
 
 
+# Stellar box (configuration C3 shape): CGS units, O/Si mixture.
+STELLAR_A = (16.0, 28.0)
+STELLAR_Z = (8.0, 14.0)
+STELLAR_X = (0.5, 0.5)
+# Base pressure of the polytrope: close to the stellar EOS at rho = 1e7 g/cc,
+# T = 3e9 K for this mixture (ions + radiation + e-/e+ = 1.8e24 dyn/cm^2).
+STELLAR_P_BASE = 1.8e24
+STELLAR_RHO_BASE = 1.0e7
+STELLAR_RHO_TOP = 1.0e5
+STELLAR_L = 1.0e8          # box edge, cm
+
+
+def stellar_box(nx, ny, nz, seed=1234, amp=1e-3, beta=1e6, mach_heat=1e-3, cfl=0.4, heat=True, name=None,
+                vel_amp=0.0):
+    """3D stratified box with the stellar EOS (configuration C3 shape).
+
+    Given as primitive fields: the conserved energy and the temperature
+    depend on the equation of state, so each implementation builds them from
+    (rho, P, v, X, B) with its own EOS.  Background: n = 1.5 polytrope
+    P = K rho^(5/3) under constant g from rho = 1e7 g/cc at z = 0, reaching
+    1e5 g/cc at z = L (1 + 4/nz), K = P_base / rho_base^(5/3).  Isobaric density noise amp * U(-1, 1) from
+    PCG64(seed); X(16O) = X(28Si) = 0.5; uniform B_x with beta = 2 P_hat(L/2)/B^2.
+    vel_amp > 0 adds velocities vel_amp * c_s0 * U(-1, 1) per component (drawn
+    after the density noise), c_s0 = sqrt(5/3 P_base / rho_base).
+    """
+    n_poly = 1.5
+    K = STELLAR_P_BASE / STELLAR_RHO_BASE ** (1.0 + 1.0 / n_poly)
+    # rho = rho_top is reached at z = L (1 + 4/nz), so the three ghost layers
+    # above the box keep rho inside [rho_top, rho_base]
+    z_end = STELLAR_L * (1.0 + 4.0 / nz)
+    g0 = K * (n_poly + 1.0) * (STELLAR_RHO_BASE ** (1.0 / n_poly) - STELLAR_RHO_TOP ** (1.0 / n_poly)) / z_end
+
+    def fn(z):
+        base = STELLAR_RHO_BASE ** (1.0 / n_poly) - g0 * z / (K * (n_poly + 1.0))
+        rho = base ** n_poly
+        return rho, K * rho ** (1.0 + 1.0 / n_poly)
+
+    L = STELLAR_L
+    bg = background_profiles(nz, 0.0, L, fn)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    noise = rng.uniform(-1.0, 1.0, size=(nz, ny, nx))
+    rho_c = bg["rho_c"][NG_BG:NG_BG + nz][:, None, None]
+    p_c = bg["p_c"][NG_BG:NG_BG + nz][:, None, None]
+    rho = rho_c * (1.0 + amp * noise)
+    p = np.broadcast_to(p_c, (nz, ny, nx)).copy()
+    _, p_mid = fn(np.array([0.5 * L]))
+    b0 = math.sqrt(2.0 * float(p_mid[0]) / beta)
+    bx = np.full((nz, ny, nx + 1), b0)
+    by = np.zeros((nz, ny + 1, nx))
+    bz = np.zeros((nz + 1, ny, nx))
+    q = None
+    if heat:
+        cs_b = math.sqrt(1.4 * STELLAR_P_BASE / STELLAR_RHO_BASE)
+        qv = (mach_heat * cs_b) ** 3 * STELLAR_RHO_BASE / (0.1 * L)
+        zc = (np.arange(nz) + 0.5) / nz
+        q = np.where(zc < 0.1, qv, 0.0)
+    nspec = 2
+    cons = np.full((5 + nspec, nz, ny, nx), np.nan)
+    cons[0] = rho
+    cons[1:4] = 0.0
+    for l in range(nspec):
+        cons[5 + l] = rho * STELLAR_X[l]
+    vel = np.zeros((3, nz, ny, nx))
+    if vel_amp > 0.0:
+        cs0 = math.sqrt(5.0 / 3.0 * STELLAR_P_BASE / STELLAR_RHO_BASE)
+        vel = vel_amp * cs0 * rng.uniform(-1.0, 1.0, size=(3, nz, ny, nx))
+        cons[1:4] = rho * vel
+    prim = dict(rho=rho, vel=vel, p=p,
+                X=np.stack([np.full((nz, ny, nx), x) for x in STELLAR_X]))
+    pr = Problem(name=name or f"stellar{nx}x{ny}x{nz}", ndim=3, n=(nx, ny, nz), lo=(0.0, 0.0, 0.0),
+                 hi=(L, L, L), bc=((PERIODIC, PERIODIC), (PERIODIC, PERIODIC), (REFLECT, REFLECT)),
+                 gamma=5.0 / 3.0, cons=cons, bx=bx, by=by, bz=bz, g=(0.0, 0.0, -g0), bg=bg, heat=q, cfl=cfl,
+                 nspec=nspec, eos="stellar")
+    pr.meta.update(seed=seed, amp=amp, beta=beta, b0=b0, A=list(STELLAR_A), Z=list(STELLAR_Z),
+                   X=list(STELLAR_X), prim=prim, bg_X=list(STELLAR_X))
+    return pr
+
+
 def ensemble_dims(nbox=24, seed=2024, choices=(64, 96, 128, 160, 192)):
     """Box edge lengths of the batched ensemble (configuration C4)."""
     rng = np.random.Generator(np.random.PCG64(seed))
