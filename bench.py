@@ -7,9 +7,12 @@ isobaric density noise 1e-3 (seed 1234), uniform B_x with beta 1e6, periodic
 x/y and reflecting z (workloads.stratified_box).  One "step" is one SSP-RK3
 step: the CFL reduction plus three stage evaluations (primitives/EOS, shock
 flags, PLM, LHLLD/HLL fluxes, Contact-CT, sources, RK update).  The metric is
-cell-updates per second per stage: cells x 3 stages x steps / time.
+cell-updates per second per stage: cells x 3 stages x steps / time.  By
+default both forms are timed one after the other: the plain FP64 form and the
+mixed form (FP32 deviations, FP64 state); the line's value is the mixed form's,
+with the FP64 form, their ratio and the per-field L1 of mixed vs FP64 beside it.
 
-  python bench.py [--gpus N --steps K --warmup W] [--form fp64|mixed]
+  python bench.py [--gpus N --steps K --warmup W] [--form both|fp64|mixed]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
 Timing: W untimed steps, then K steps bracketed by a barrier and device
@@ -49,9 +52,10 @@ BYTES_PER_CELL_STAGE = {1: 128.0, 2: 192.0, 3: 192.0}
 # the ncu SASS counters of k_flux on the stratified box).
 FP64_FLOP_PER_FACE = 807.0
 # Mixed flux kernel: FP32 operations per face (FADD + FMUL + 2 FFMA from the ncu
-# SASS counters of k_flux<float>); peak = 152 SMs x 128 FP32 lanes x 2 flop x
-# 2.07 GHz (measured FFMA probe: 73.2 TFLOP/s).
-FP32_FLOP_PER_FACE = 590.0
+# SASS counters of k_flux<0/1/2, float> on the stratified box at 64^3, per sweep
+# direction); peak = 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (measured FFMA
+# probe: 73.2 TFLOP/s).
+FP32_FLOP_PER_FACE = {"flux_x": 372.8, "flux_y": 316.0, "flux_z": 315.7}
 FP32_NOMINAL_TFLOPS = 80.5
 
 
@@ -191,7 +195,7 @@ def roofline(kt, pr, form, hbm_peak, peak_kind):
         n = pr.n[0]
         faces = (n + 1) * (n + 2) * (n + 2)
         fp64 = form == "fp64"
-        flop = FP64_FLOP_PER_FACE if fp64 else FP32_FLOP_PER_FACE
+        flop = FP64_FLOP_PER_FACE if fp64 else FP32_FLOP_PER_FACE[name]
         peak = FP64_NOMINAL_TFLOPS if fp64 else FP32_NOMINAL_TFLOPS
         achieved = faces * flop / (avg_ms * 1e-3) / 1e12
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -282,15 +286,45 @@ def run_reference(args):
     return 0
 
 
+def l1_mixed_vs_fp64(P, pr, steps=3):
+    """Per-field L1 of the mixed form against the FP64 form on the benchmark
+    box after a few steps at the same fixed dt (deviations from the initial
+    state for rho, m, E and the face field): ||q_mix - q_64||_1 / ||q_64 - q_0||_1."""
+    import numpy as np
+    g64 = P.Grid(pr, precision="fp64")
+    g64.load()
+    dt = g64.compute_dt()
+    g64.step(steps, dt)
+    a = g64.get_state()
+    g64.close()
+    gm = P.Grid(pr, precision="mixed")
+    gm.load()
+    gm.step(steps, dt)
+    b = gm.get_state()
+    gm.close()
+    out = {}
+    names = {0: "rho", 1: "mx", 2: "my", 3: "mz", 4: "E"}
+    for v, nm in names.items():
+        d0 = np.abs(a["cons"][v] - pr.cons[v]).sum()
+        out[nm] = float(np.abs(b["cons"][v] - a["cons"][v]).sum() / max(d0, 1e-300))
+    for k in ("bx", "by", "bz"):
+        d0 = np.abs(a[k] - getattr(pr, k)).sum()
+        out[k] = float(np.abs(b[k] - a[k]).sum() / max(d0, 1e-300)) if d0 > 0 else 0.0
+    return {"steps": steps, "dt": dt, "l1_rel_of_change": out,
+            "note": "||mixed - fp64||_1 / ||fp64 - initial||_1 per field at the same fixed dt"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--form", default="both", choices=["fp64", "mixed", "both"],
+                    help="both: time the plain FP64 form and the mixed form; the value is the mixed form's")
     ap.add_argument("--n", type=int, default=256, help="box edge (256 is the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -309,34 +343,55 @@ def main():
     props = torch.cuda.get_device_properties(local)
     gpu_id = getattr(props, "uuid", None)
     gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else (gpu_id or local)
-    clocks = Clocks(gpu_id)
-    g, ms, kt, st = time_form(P, pr, args.form, args.steps, args.warmup, stream, ws)
-    clk = clocks.stop()
-    ms_max = allreduce_max(ms, ws)
-    value = pr.ncells * STAGES * args.steps * ws / (ms_max * 1e-3)
-    roof = roofline(kt, pr, args.form, hbm_peak, peak_kind)
+    forms = ["fp64", "mixed"] if args.form == "both" else [args.form]
+    head = forms[-1]
+    res = {}
+    clk = None
+    for form in forms:
+        clocks = Clocks(gpu_id) if form == head else None
+        g, ms, kt, st = time_form(P, pr, form, args.steps, args.warmup, stream, ws)
+        if clocks is not None:
+            clk = clocks.stop()
+        ms_max = allreduce_max(ms, ws)
+        value = pr.ncells * STAGES * args.steps * ws / (ms_max * 1e-3)
+        res[form] = dict(g=g, ms=ms_max, kt=kt, value=value)
+        if form != head:
+            g.close()
+    h = res[head]
+    g = h["g"]
+    roof = roofline(h["kt"], pr, head, hbm_peak, peak_kind)
     e2e = e2e_measure(P, g, pr, args.e2e_steps)
     g.close()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample()
-    launches = sum(v[0] for v in kt.values())
+    l1 = None
+    if rank == 0 and len(forms) == 2 and not args.no_l1:
+        l1 = l1_mixed_vs_fp64(P, pr)
+    launches = sum(v[0] for v in h["kt"].values())
+    forms_out = {f: {"value": r["value"], "ms_per_step": r["ms"] / args.steps,
+                     "stage_hbm": stage_hbm(r["value"] / max(ws, 1), f, hbm_peak, peak_kind),
+                     "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in r["kt"].items()}}
+                 for f, r in res.items()}
+    if len(forms) == 2:
+        forms_out["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.form == "fp64" else "f32+f64",
+        "dtype": "f64" if head == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": pr.ncells, "n": list(pr.n), "form": args.form,
-                   "stages_per_step": STAGES, "parallelism": f"replicas x{ws}",
+        "config": {"workload": WORKLOAD, "cells": pr.ncells, "n": list(pr.n), "form": head,
+                   "forms_timed": forms, "stages_per_step": STAGES, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (state 1.07 GB per copy, no flush)"},
         "roofline": roof,
-        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
+        "forms": forms_out,
+        "l1_mixed_vs_fp64": l1,
         "gpu_launches": launches,
         "e2e": e2e,
         "clocks": clk,
         "cpu_baseline": cpu,
-        "stage_hbm": stage_hbm(value / max(ws, 1), args.form, hbm_peak, peak_kind),
+        "stage_hbm": stage_hbm(h["value"] / max(ws, 1), head, hbm_peak, peak_kind),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
