@@ -314,6 +314,75 @@ def l1_mixed_vs_fp64(P, pr, steps=3):
             "note": "||mixed - fp64||_1 / ||fp64 - initial||_1 per field at the same fixed dt"}
 
 
+def stellar_c3(P, n, steps, warmup, stream, ws):
+    """The same box with the stellar EOS (ions + radiation + e-/e+ pairs, 16O/28Si
+    0.5/0.5, rho 1e5-1e7 g/cc): plain FP64 form (Newton from the previous T)
+    vs the mixed form with the network's first guess, trained here on 1e7
+    seeded EOS samples by the project's own kernels."""
+    import numpy as np
+    import workloads as W
+    table = P.EosTable()
+    net = P.Mlp(seed=7)
+    train = net.train(table, nsamples=10_000_000, epochs=8, batch=4096, lr=1e-2, seed=2026)
+    pr = W.stellar_box(n, n, n)
+    out = {"workload": f"stellar box {n}^3 (ions + radiation + e-/e+ table EOS, 16O/28Si 0.5/0.5, "
+                       f"rho 1e7 -> 1e5 g/cc polytrope, CGS), SSP-RK3",
+           "mlp_training": train, "forms": {}}
+    runs = (("fp64", "fp64", None, 0), ("mixed", "mixed", None, 0), ("mixed+mlp", "mixed", net, 1),
+            ("mixed+mlp_cold_only", "mixed", net, 2))
+    for name, prec, mlp, mode in runs:
+        import torch
+        g = P.Grid(pr, precision=prec, stream=stream.cuda_stream, eos_table=table, mlp=mlp, mlp_mode=mode)
+        g.load()
+        for _ in range(warmup):
+            g.step(1)
+        g.check()
+        it0 = g.stats()["newton_iters"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(ws)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            g.step(steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = allreduce_max(e0.elapsed_time(e1), ws)
+        g.check()
+        it = g.stats()["newton_iters"] - it0
+        g.close()
+        out["forms"][name] = {"value": pr.ncells * STAGES * steps * ws / (ms * 1e-3), "unit": UNIT,
+                              "ms_per_step": ms / steps,
+                              "newton_iters_per_cell_stage": it / (pr.ncells * STAGES * steps)}
+    f = out["forms"]
+    out["mixed_mlp_over_fp64"] = f["mixed+mlp"]["value"] / f["fp64"]["value"]
+    # per-field L1 of the mixed + network form against the FP64 form, 3 steps at a fixed dt
+    g64 = P.Grid(pr, precision="fp64", eos_table=table)
+    g64.load()
+    dt = g64.compute_dt()
+    g64.step(3, dt)
+    a = g64.get_state()
+    g64.close()
+    gm = P.Grid(pr, precision="mixed", eos_table=table, mlp=net, mlp_mode=1)
+    gm.load()
+    gm.step(3, dt)
+    b = gm.get_state()
+    gm.close()
+    l1 = {}
+    ref0 = P.Grid(pr, precision="fp64", eos_table=table)
+    ref0.load()
+    s0 = ref0.get_state()
+    ref0.close()
+    for v, nm in {0: "rho", 1: "mx", 2: "my", 3: "mz", 4: "E"}.items():
+        d0 = np.abs(a["cons"][v] - s0["cons"][v]).sum()
+        l1[nm] = float(np.abs(b["cons"][v] - a["cons"][v]).sum() / max(d0, 1e-300))
+    l1["T"] = float(np.abs(b["T"] - a["T"]).sum() / max(np.abs(a["T"] - s0["T"]).sum(), 1e-300))
+    out["l1_mixed_mlp_vs_fp64"] = {"steps": 3, "l1_rel_of_change": l1}
+    net.close()
+    table.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,6 +395,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-c3", action="store_true", help="skip the stellar-EOS box (mixed + network vs FP64)")
+    ap.add_argument("--c3-steps", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -368,6 +439,9 @@ def main():
     l1 = None
     if rank == 0 and len(forms) == 2 and not args.no_l1:
         l1 = l1_mixed_vs_fp64(P, pr)
+    c3 = None
+    if not args.no_c3 and len(forms) == 2:
+        c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws)
     launches = sum(v[0] for v in h["kt"].values())
     forms_out = {f: {"value": r["value"], "ms_per_step": r["ms"] / args.steps,
                      "stage_hbm": stage_hbm(r["value"] / max(ws, 1), f, hbm_peak, peak_kind),
@@ -387,6 +461,7 @@ def main():
         "roofline": roof,
         "forms": forms_out,
         "l1_mixed_vs_fp64": l1,
+        "stellar_eos_box": c3,
         "gpu_launches": launches,
         "e2e": e2e,
         "clocks": clk,

@@ -92,9 +92,12 @@ typedef struct {
   int precision;            /* PHL_FP64 / PHL_MIXED                             */
   double newton_tol;        /* stellar EOS Newton tolerance (1e-11)             */
   int newton_maxit;
-  int use_mlp;              /* stellar EOS: MLP first guess                     */
+  int use_mlp;              /* stellar EOS, Newton first guess from desc.mlp:   */
+                            /* 1: always (previous T as fallback); 2: only where */
+                            /* no previous T exists (cold start); 0: never       */
   void *stream;             /* cudaStream_t                                     */
   const struct phl_eos_table *eos_table;  /* stellar EOS table (not owned)      */
+  const struct phl_mlp *mlp;  /* temperature-guess network when use_mlp (not owned) */
   double bg_X[PHL_MAXSPEC]; /* stellar: mass fractions of the background        */
 } phl_grid_desc;
 
@@ -105,6 +108,7 @@ typedef struct {
   int device_flags;         /* bit 0: rho/P <= 0, bit 1: NaN, bit 2: Newton     */
   int kernels_per_step;     /* CUDA kernel launches per RK step                 */
   size_t device_bytes;      /* device memory owned by the grid                  */
+  long newton_iters;        /* stellar EOS: Newton iterations summed over cells */
 } phl_stats;
 
 /* Create a grid: validates the description, allocates the state (padded SoA
@@ -113,8 +117,9 @@ typedef struct {
  * PHL_EUNSUPPORTED, PHL_ECUDA. */
 phl_status phl_create_grid(const phl_grid_desc *desc, phl_grid **out);
 
-/* Load the state (layout above).  T may be NULL (stellar EOS: T is then
- * initialised by a Newton solve from 1e8 K).  where = PHL_HOST or
+/* Load the state (layout above).  T (stellar EOS: Newton first guesses) may
+ * be NULL: the first inversion then starts from the network's guess
+ * (use_mlp) or from the table's mid-range temperature.  where = PHL_HOST or
  * PHL_DEVICE.  Stream-ordered; host sources are copied before return. */
 phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx,
                          const double *by, const double *bz, const double *T,
@@ -237,12 +242,72 @@ phl_status phl_eos_table_export(const phl_eos_table *t, double *out, long nout);
  * c_s, Newton iterations (-1: no convergence).  abar, ye: mean mass number
  * and electron fraction per element.  precision = PHL_FP64: FP64 Newton;
  * PHL_MIXED: FP32 Newton to about 1e-5, finished by FP64 Newton to tol (the
- * iteration count then sums both phases).  where = PHL_HOST (host
+ * iteration count sums both phases).  The iterations evaluate e and c_v
+ * only; P, gamma_e, gamma_c once, at the final T.  where = PHL_HOST (host
  * arrays, synchronous) or PHL_DEVICE (device arrays, asynchronous on stream). */
 phl_status phl_eos(const phl_eos_table *t, long n, const double *rho, const double *eint,
                    const double *abar, const double *ye, double *T_inout, double *P,
                    double *gamma_e, double *gamma_c, double *cs, int *iters, int precision,
                    double tol, int maxit, int where, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Temperature-guess network for the EOS inversion (not in the paper; the
+ * Newton iteration of Sect. 2.2 stays the judge of the converged T).
+ * y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3 with 3 inputs, two hidden layers
+ * of PHL_MLP_HIDDEN units, one output.  Inputs x = ((log10 rho - c0) s0,
+ * (log10 e_int - c1) s1, (X_0 - c2) s2), X_0 the first species' mass
+ * fraction; output log10 T = c3 + y / s3.  Training runs on the device in
+ * FP32 (master weights, Adam); inference uses BF16 weights on the tensor
+ * cores with FP32 accumulation, fused into the grid's EOS kernel when
+ * desc.use_mlp is set.  Flat FP32 weight layout (PHL_MLP_NPARAM values):
+ * W1[64][3], b1[64], W2[64][64], b2[64], W3[64], b3. */
+#define PHL_MLP_HIDDEN 64
+#define PHL_MLP_NPARAM 4481
+typedef struct phl_mlp phl_mlp;
+
+typedef struct {
+  long nsamples;            /* EOS samples (5% held out for validation)         */
+  int epochs;
+  long batch;               /* minibatch size                                  */
+  double lr;                /* peak Adam step (cosine decay to 0)              */
+  unsigned long long seed;  /* SplitMix64 counter-based sample generator       */
+  double lrho[2], lT[2];    /* log10 rho and log10 T ranges (uniform)          */
+  double A[2], Z[2];        /* the two species; X_0 uniform in [0, 1]          */
+} phl_mlp_train_cfg;
+
+typedef struct {
+  double final_loss;        /* last minibatch MSE (normalised target)          */
+  double val_rms_log10T;    /* held-out error of the BF16 network, in log10 T   */
+  double val_max_log10T;
+  long steps;
+  double seconds;
+} phl_mlp_train_stats;
+
+/* Glorot-uniform weights from seed, zero biases.  Errors: PHL_ENOMEM. */
+phl_status phl_mlp_create(unsigned long long seed, phl_mlp **out);
+void phl_mlp_destroy(phl_mlp *m);
+/* Host FP32 weights in the layout above (set also rebuilds the BF16 copy and
+ * resets the optimiser state). */
+phl_status phl_mlp_set_weights(phl_mlp *m, const float *w);
+phl_status phl_mlp_get_weights(const phl_mlp *m, float *w);
+/* Affine input/output maps c[4], s[4] (host arrays). */
+phl_status phl_mlp_set_norm(phl_mlp *m, const double *c, const double *s);
+phl_status phl_mlp_get_norm(const phl_mlp *m, double *c, double *s);
+/* Mean squared error over n samples (x[n][3] normalised inputs, t[n] targets)
+ * and its gradient (PHL_MLP_NPARAM floats) from the FP32 forward and backward
+ * kernels.  where: PHL_HOST or PHL_DEVICE for x, t, grad; loss is host. */
+phl_status phl_mlp_loss_grad(phl_mlp *m, long n, const float *x, const float *t, double *loss,
+                             float *grad, int where);
+/* BF16 tensor-core forward pass on normalised inputs x[n][3] -> y[n]. */
+phl_status phl_mlp_forward(const phl_mlp *m, long n, const float *x, float *y, int where);
+/* Temperature guesses T[n] (clamped to the table's range) for (rho, e_int, X_0). */
+phl_status phl_mlp_guess_temperature(const phl_mlp *m, const phl_eos_table *t, long n, const double *rho,
+                           const double *eint, const double *X0, double *T, int where);
+/* Generate cfg->nsamples (rho, T, X_0) -> e_int samples with the device EOS
+ * on table t, set the affine maps from their ranges, and train.  st may be
+ * NULL.  Errors: PHL_EINVAL (arguments, ranges outside the table). */
+phl_status phl_mlp_train(phl_mlp *m, const phl_eos_table *t, const phl_mlp_train_cfg *cfg,
+                         phl_mlp_train_stats *st);
 
 void phl_destroy(phl_grid *g);
 

@@ -45,13 +45,29 @@ class GridDesc(C.Structure):
         ("eps_sf", C.c_double), ("mach_thr", C.c_double), ("precision", C.c_int),
         ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("use_mlp", C.c_int),
         ("stream", C.c_void_p),
-        ("eos_table", C.c_void_p), ("bg_X", C.c_double * PHL_MAXSPEC),
+        ("eos_table", C.c_void_p), ("mlp", C.c_void_p), ("bg_X", C.c_double * PHL_MAXSPEC),
     ]
 
 
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_long), ("t", C.c_double), ("last_dt", C.c_double),
-                ("device_flags", C.c_int), ("kernels_per_step", C.c_int), ("device_bytes", C.c_size_t)]
+                ("device_flags", C.c_int), ("kernels_per_step", C.c_int), ("device_bytes", C.c_size_t),
+                ("newton_iters", C.c_long)]
+
+
+MLP_NPARAM = 4481
+MLP_HIDDEN = 64
+
+
+class MlpTrainCfg(C.Structure):
+    _fields_ = [("nsamples", C.c_long), ("epochs", C.c_int), ("batch", C.c_long), ("lr", C.c_double),
+                ("seed", C.c_ulonglong), ("lrho", C.c_double * 2), ("lT", C.c_double * 2),
+                ("A", C.c_double * 2), ("Z", C.c_double * 2)]
+
+
+class MlpTrainStats(C.Structure):
+    _fields_ = [("final_loss", C.c_double), ("val_rms_log10T", C.c_double), ("val_max_log10T", C.c_double),
+                ("steps", C.c_long), ("seconds", C.c_double)]
 
 
 class KernelTime(C.Structure):
@@ -81,6 +97,18 @@ _SIGS = {
     "phl_eos_table_create": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
                                        C.POINTER(C.c_void_p)]),
     "phl_eos_table_destroy": (None, [C.c_void_p]),
+    "phl_mlp_create": (C.c_int, [C.c_ulonglong, C.POINTER(C.c_void_p)]),
+    "phl_mlp_destroy": (None, [C.c_void_p]),
+    "phl_mlp_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "phl_mlp_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "phl_mlp_set_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phl_mlp_get_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "phl_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_long, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                    C.c_void_p, C.c_int]),
+    "phl_mlp_forward": (C.c_int, [C.c_void_p, C.c_long, C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_mlp_guess_temperature": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_int]),
+    "phl_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(MlpTrainCfg), C.POINTER(MlpTrainStats)]),
     "phl_eos_table_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long]),
     "phl_eos": (C.c_int, [C.c_void_p, C.c_long] + [C.c_void_p] * 10 + [C.c_int, C.c_double, C.c_int, C.c_int,
                                                                           C.c_void_p]),
@@ -190,13 +218,90 @@ def eos(table, rho, eint, abar, ye, T_guess, precision="fp64", tol=1e-11, maxit=
     return out
 
 
+class Mlp:
+    """Temperature-guess network on the current device (phl_mlp_* in include/phl.h)."""
+
+    def __init__(self, seed=1):
+        h = C.c_void_p()
+        _check(lib().phl_mlp_create(int(seed), C.byref(h)))
+        self.h = h
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == MLP_NPARAM
+        _check(lib().phl_mlp_set_weights(self.h, w.ctypes.data))
+
+    def get_weights(self):
+        w = np.zeros(MLP_NPARAM, dtype=np.float32)
+        _check(lib().phl_mlp_get_weights(self.h, w.ctypes.data))
+        return w
+
+    def set_norm(self, c, s):
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        _check(lib().phl_mlp_set_norm(self.h, c.ctypes.data, s.ctypes.data))
+
+    def get_norm(self):
+        c, s = np.zeros(4), np.zeros(4)
+        _check(lib().phl_mlp_get_norm(self.h, c.ctypes.data, s.ctypes.data))
+        return c, s
+
+    def loss_grad(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(MLP_NPARAM, dtype=np.float32)
+        loss = C.c_double()
+        _check(lib().phl_mlp_loss_grad(self.h, t.size, x.ctypes.data, t.ctypes.data, C.byref(loss),
+                                       g.ctypes.data, HOST))
+        return loss.value, g
+
+    def forward(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros(x.shape[0], dtype=np.float32)
+        _check(lib().phl_mlp_forward(self.h, x.shape[0], x.ctypes.data, y.ctypes.data, HOST))
+        return y
+
+    def guess_T(self, table, rho, eint, X0):
+        arr = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        rho, eint, X0 = arr(rho), arr(eint), arr(X0)
+        T = np.zeros(rho.size)
+        _check(lib().phl_mlp_guess_temperature(self.h, table.h, rho.size, rho.ctypes.data, eint.ctypes.data,
+                                     X0.ctypes.data, T.ctypes.data, HOST))
+        return T
+
+    def train(self, table, nsamples=10_000_000, epochs=8, batch=8192, lr=3e-3, seed=2026,
+              lrho=(5.0, 7.0), lT=(8.0, 9.477121254719663), A=(16.0, 28.0), Z=(8.0, 14.0)):
+        c = MlpTrainCfg()
+        c.nsamples, c.epochs, c.batch, c.lr, c.seed = int(nsamples), int(epochs), int(batch), float(lr), int(seed)
+        c.lrho[0], c.lrho[1] = lrho
+        c.lT[0], c.lT[1] = lT
+        c.A[0], c.A[1] = A
+        c.Z[0], c.Z[1] = Z
+        st = MlpTrainStats()
+        _check(lib().phl_mlp_train(self.h, table.h, C.byref(c), C.byref(st)))
+        return {k: getattr(st, k) for k, _ in MlpTrainStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().phl_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Grid:
     """One simulation box on the current CUDA device (see include/phl.h)."""
 
     def __init__(self, pr, precision="fp64", riemann=None, eps_sf=None, cfl=None, rk=3, wb=True,
-                 stream=None, mach_thr=None, eos_table=None, newton_tol=1e-11, newton_maxit=50):
+                 stream=None, mach_thr=None, eos_table=None, newton_tol=1e-11, newton_maxit=50, mlp=None,
+                 mlp_mode=1):
         self.pr = pr
         self.eos_table = eos_table
+        self.mlp = mlp
         d = GridDesc()
         for k in range(3):
             d.n[k] = pr.n[k]
@@ -233,7 +338,8 @@ class Grid:
         d.precision = PRECISION[precision]
         d.newton_tol = newton_tol
         d.newton_maxit = newton_maxit
-        d.use_mlp = 0
+        d.use_mlp = int(mlp_mode) if mlp is not None else 0
+        d.mlp = mlp.h if mlp is not None else None
         d.stream = stream
         self.desc = d
         h = C.c_void_p()

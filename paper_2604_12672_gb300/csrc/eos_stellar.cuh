@@ -42,8 +42,9 @@ struct Mix {                   // composition-derived constants of a cell
 
 template <typename R> struct TV { R f, fx, fy, fxx, fyy, fxy; };
 
-// Bicubic Hermite evaluation of the free energy and its derivatives.
-template <typename R>
+// Bicubic Hermite evaluation of the free energy and its derivatives (FULL =
+// false: only f, f_y, f_yy, which is what e and c_v need).
+template <typename R, bool FULL = true>
 __device__ __forceinline__ bool table_eval(const Table &t, R x, R y, TV<R> &o) {
   const R x0 = sizeof(R) == 8 ? (R)t.x0 : (R)t.x0f, dx = sizeof(R) == 8 ? (R)t.dx : (R)t.dxf;
   const R y0 = sizeof(R) == 8 ? (R)t.y0 : (R)t.y0f, dy = sizeof(R) == 8 ? (R)t.dy : (R)t.dyf;
@@ -73,11 +74,13 @@ __device__ __forceinline__ bool table_eval(const Table &t, R x, R y, TV<R> &o) {
       const R c0 = q0, c1 = q1 * dx, c2 = q2 * dy, c3 = q3 * dx * dy;
       const int iv = 2 * ca, is = 2 * ca + 1, jv = 2 * cb, js = 2 * cb + 1;
       a0 += c0 * hu[iv] * hv[jv] + c1 * hu[is] * hv[jv] + c2 * hu[iv] * hv[js] + c3 * hu[is] * hv[js];
-      a1 += c0 * du[iv] * hv[jv] + c1 * du[is] * hv[jv] + c2 * du[iv] * hv[js] + c3 * du[is] * hv[js];
       a2 += c0 * hu[iv] * dv[jv] + c1 * hu[is] * dv[jv] + c2 * hu[iv] * dv[js] + c3 * hu[is] * dv[js];
-      a3 += c0 * eu[iv] * hv[jv] + c1 * eu[is] * hv[jv] + c2 * eu[iv] * hv[js] + c3 * eu[is] * hv[js];
       a4 += c0 * hu[iv] * ev[jv] + c1 * hu[is] * ev[jv] + c2 * hu[iv] * ev[js] + c3 * hu[is] * ev[js];
-      a5 += c0 * du[iv] * dv[jv] + c1 * du[is] * dv[jv] + c2 * du[iv] * dv[js] + c3 * du[is] * dv[js];
+      if (FULL) {
+        a1 += c0 * du[iv] * hv[jv] + c1 * du[is] * hv[jv] + c2 * du[iv] * hv[js] + c3 * du[is] * hv[js];
+        a3 += c0 * eu[iv] * hv[jv] + c1 * eu[is] * hv[jv] + c2 * eu[iv] * hv[js] + c3 * eu[is] * hv[js];
+        a5 += c0 * du[iv] * dv[jv] + c1 * du[is] * dv[jv] + c2 * du[iv] * dv[js] + c3 * du[is] * dv[js];
+      }
     }
   o.f = a0;
   o.fx = a1 / dx;
@@ -127,9 +130,33 @@ __device__ __forceinline__ bool eos_rt(const Table &t, R rho, R T, R abar, R ye,
   return true;
 }
 
+// Specific internal energy and c_v at (rho, T): what a Newton iteration needs.
+template <typename R>
+__device__ __forceinline__ bool eos_ecv(const Table &t, R rho, R T, R abar, R ye, R &e, R &cv) {
+  TV<R> q;
+  const R ne = rho * ye * R(NAV);
+  if (!table_eval<R, false>(t, log(ne), log(T), q)) return false;
+  const R irho = R(1) / rho, iT = R(1) / T;
+  const R iab = R(1) / abar;
+  const R Rg = R(RGAS);
+  R aT4, aT3;
+  if (sizeof(R) == 8) {
+    aT3 = R(ARAD) * T * T * T;
+    aT4 = aT3 * T;
+  } else {
+    const R tt = R(ARAD_QUARTER) * T, t2 = tt * tt;
+    aT4 = t2 * t2;
+    aT3 = aT4 * iT;
+  }
+  e = (q.f - q.fy) * irho + R(1.5) * Rg * T * iab + aT4 * irho;
+  cv = (q.fy - q.fyy) * irho * iT + R(1.5) * Rg * iab + R(4) * aT3 * irho;
+  return true;
+}
+
 // Newton inversion e_int -> T (Sect. 2.2): T <- T + (e - e_EoS)/c_v until
 // |de|/e < tol, then one more step; bracketed inside the table's T range.
-// Returns iterations (> 0) or -1 on failure.
+// The iterations evaluate only e and c_v; the full EOS (P, gamma_e, gamma_c)
+// is evaluated once, at the final T.  Returns the iteration count or -1.
 template <typename R>
 __device__ __forceinline__ int eos_invert(const Table &t, R rho, R eint, R abar, R ye, R &T, R tol, int maxit,
                                           EosOut<R> &o) {
@@ -137,34 +164,53 @@ __device__ __forceinline__ int eos_invert(const Table &t, R rho, R eint, R abar,
   R lo = Tlo, hi = Thi;
   if (!(T > Tlo && T < Thi)) T = sqrt(Tlo * Thi);
   for (int it = 1; it <= maxit; ++it) {
-    if (!eos_rt<R>(t, rho, T, abar, ye, o)) return -1;
-    const R de = eint - o.e;
+    R e, cv;
+    if (!eos_ecv<R>(t, rho, T, abar, ye, e, cv)) return -1;
+    const R de = eint - e;
     if (fabs(de) < tol * fabs(eint)) {
-      T = T + de / o.cv;
+      T = T + de / cv;
       if (!eos_rt<R>(t, rho, T, abar, ye, o)) return -1;
       return it;
     }
     if (de > R(0)) lo = T; else hi = T;
-    R Tn = T + de / o.cv;
+    R Tn = T + de / cv;
     if (!(Tn > lo && Tn < hi)) Tn = R(0.5) * (lo + hi);
     T = Tn;
   }
   return -1;
 }
 
-// Mixed-precision inversion: FP32 Newton iterations bring T within about
-// 1e-5 of the root (|de| / e; FP32 holds ln n_e ~ 70 and ln T ~ 20 only to
-// ~1e-6, the floor of an FP32 table lookup), then FP64 Newton finishes to tol
-// with the same stopping rule as the FP64 path (converged, then one more
-// step).  The FP32 phase only supplies the starting point: if it stalls, its
-// last bracketed iterate is used.
-// Returns the total iteration count, or -1 if the FP64 phase fails.
+// The FP32 phase of the mixed inversion: Newton on e and c_v only, until
+// |de|/e < tol or maxit; T keeps the last bracketed iterate.
+__device__ __forceinline__ int newton_fp32(const Table &t, float rho, float eint, float abar, float ye, float &T,
+                                           float tol, int maxit) {
+  const float Tlo = expf((float)t.y0), Thi = expf((float)(t.y0 + (t.ny - 1) * t.dy));
+  float lo = Tlo, hi = Thi;
+  if (!(T > Tlo && T < Thi)) T = sqrtf(Tlo * Thi);
+  for (int it = 1; it <= maxit; ++it) {
+    float e, cv;
+    if (!eos_ecv<float>(t, rho, T, abar, ye, e, cv)) return -1;
+    const float de = eint - e;
+    if (de > 0.0f) lo = T; else hi = T;
+    float Tn = T + de / cv;
+    if (!(Tn > lo && Tn < hi)) Tn = 0.5f * (lo + hi);
+    T = Tn;
+    if (fabsf(de) < tol * fabsf(eint)) return it;
+  }
+  return -1;
+}
+
+// Mixed-precision inversion: FP32 Newton iterations (e and c_v only) bring T
+// within about 1e-5 of the root (|de| / e; FP32 holds ln n_e ~ 70 and
+// ln T ~ 20 only to ~1e-6, the floor of an FP32 table lookup); FP64 Newton
+// then finishes with the FP64 path's stopping rule (|de|/e < tol, one more
+// step, the full evaluation at the final T).  The low-Mach deviations need
+// P to ~1e-12, so a single FP64 step from 1e-5 is not enough.  Returns the
+// total iteration count, or -1 if the FP64 phase fails.
 __device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, double eint, double abar, double ye,
                                                 double &T, double tol, int maxit, EosOut<double> &o) {
   float Tf = (float)T;
-  EosOut<float> of;
-  const int it32 = eos_invert<float>(t, (float)rho, (float)eint, (float)abar, (float)ye, Tf, 1e-5f,
-                                     maxit < 12 ? maxit : 12, of);
+  const int it32 = newton_fp32(t, (float)rho, (float)eint, (float)abar, (float)ye, Tf, 1e-5f, maxit < 12 ? maxit : 12);
   if (isfinite(Tf) && Tf > 0.0f) T = (double)Tf;
   const int it64 = eos_invert<double>(t, rho, eint, abar, ye, T, tol, maxit, o);
   return it64 < 0 ? -1 : it64 + (it32 > 0 ? it32 : 12);

@@ -39,7 +39,8 @@ __global__ void k_eos_cells(DevGeo G, Box box, const double *__restrict__ U, con
                             const double *__restrict__ Tin, double *__restrict__ Tout, R *__restrict__ W,
                             int *dflag) {
   int c[3];
-  if (!cell3(box, c)) return;
+  const bool in = cell3(box, c);
+  if (!in) { c[0] = box.lo[0]; c[1] = box.lo[1]; c[2] = box.lo[2]; }   // harmless stand-in for the warp's MLP
   const long p = sidx(G, c[0], c[1], c[2]);
   const long pl = G.plane;
   double u[5 + PHL_NSPEC_MAX];
@@ -69,10 +70,39 @@ __global__ void k_eos_cells(DevGeo G, Box box, const double *__restrict__ U, con
   double T = Tin[p];
   eos::EosOut<double> o;
   int it;
-  if (sizeof(R) == 8)
-    it = eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
-  else
-    it = eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
+  // use_mlp = 1: the network's guess first, the previous temperature as the
+  // fallback; use_mlp = 2: the network only where no previous temperature exists
+  const bool need = G.use_mlp == 1 || !(T > 0.0);
+  if (G.use_mlp && __any_sync(0xffffffffu, in && need)) {
+    // warp-collective BF16 tensor-core guess; the Newton iteration judges it and
+    // falls back to the previous temperature if it does not converge from it
+    const bool ok_in = in && rho > 0.0 && eint > 0.0;
+    const float lr = ok_in ? (float)log10(rho) : G.mlp.c[0];
+    const float le = ok_in ? (float)log10(eint) : G.mlp.c[1];
+    const float x0 = ok_in ? (float)(X[0] / (X[0] + (G.nspec > 1 ? X[1] : 0.0))) : G.mlp.c[2];
+    const float lt = mlp::guess_log10T(G.mlp, lr, le, x0);
+    if (!in) return;
+    double Tg = need ? exp10((double)lt) : T;
+    it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, Tg, G.newton_tol, G.newton_maxit, o)
+                        : eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, Tg, G.newton_tol, G.newton_maxit, o);
+    if (it > 0) {
+      T = Tg;
+    } else {
+      it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o)
+                          : eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
+    }
+  } else {
+    if (!in) return;
+    if (sizeof(R) == 8)
+      it = eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
+    else
+      it = eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
+  }
+  if (G.niter) {   // warp sum, one atomic per warp
+    const unsigned m = __activemask();
+    const unsigned tot = __reduce_add_sync(m, it > 0 ? (unsigned)it : 0u);
+    if ((int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(G.niter, (unsigned long long)tot);
+  }
   if (it < 0 || !(o.P > 0.0) || !(rho > 0.0)) atomicOr(dflag, it < 0 ? FLAG_NEWTON : FLAG_NEG);
   Tout[p] = T;
   const Bg b = bg_cell(G, c[2]);

@@ -63,6 +63,7 @@ struct phl_grid {
   cudaStream_t stream;
   // state
   double *U = nullptr, *U1 = nullptr, *B = nullptr, *B1 = nullptr, *T = nullptr, *T2 = nullptr;
+  unsigned long long *niter = nullptr;   // Newton iteration counter (stellar EOS)
   // background and heating profiles
   double *bg = nullptr, *heat = nullptr;
   float *bgf = nullptr, *heatf = nullptr;
@@ -181,6 +182,9 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     for (int l = 0; l < d->nspec; ++l)
       if (!(d->A[l] > 0.0) || !(d->Z[l] > 0.0)) return fail(PHL_EINVAL, "species A, Z must be positive");
   }
+  if (d->use_mlp < 0 || d->use_mlp > 2) return fail(PHL_EINVAL, "use_mlp must be 0, 1 or 2");
+  if (d->use_mlp && (d->eos != PHL_EOS_STELLAR || !d->mlp))
+    return fail(PHL_EINVAL, "use_mlp needs the stellar EOS and desc.mlp");
   if (!(d->gamma > 1.0)) return fail(PHL_EINVAL, "gamma must exceed 1");
   if (!(d->cfl > 0.0)) return fail(PHL_EINVAL, "cfl must be positive");
   if (d->rk != 2 && d->rk != 3) return fail(PHL_EINVAL, "rk must be 2 or 3");
@@ -257,6 +261,10 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   G.newton_maxit = d->newton_maxit > 0 ? d->newton_maxit : 50;
   for (int l = 0; l < PHL_NSPEC_MAX; ++l) { G.Acomp[l] = d->A[l]; G.Zcomp[l] = d->Z[l]; }
   if (d->eos == PHL_EOS_STELLAR) G.tab = *eos_table_view(d->eos_table);
+  if (d->use_mlp) {
+    G.use_mlp = d->use_mlp;
+    G.mlp = mlp_view(d->mlp);
+  }
 
   phl_status st = PHL_OK;
 #define AL(p, n)                                  \
@@ -287,6 +295,8 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   if (d->eos == PHL_EOS_STELLAR) {
     AL(&g->T, G.plane);
     AL(&g->T2, G.plane);
+    AL(&g->niter, 1);
+    G.niter = g->niter;
   }
   AL(&g->flag, G.wtot);
   AL(&g->dt, 1);
@@ -371,8 +381,6 @@ phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx, cons
                          const double *bz, const double *T, int where) {
   if (!g || !cons || !bx || !by || !bz) return fail(PHL_EINVAL, "null argument");
   if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
-  if (g->G.eos == PHL_EOS_STELLAR && !T)
-    return fail(PHL_EINVAL, "stellar EOS: give T (Newton guesses) or use phl_set_state_prim");
   const DevGeo &G = g->G;
   const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
   const long nc = (long)nx * ny * nz;
@@ -382,8 +390,13 @@ phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx, cons
   if ((st = copy_field(g, g->B, bx, nullptr, nx + 1, ny, nz, true)) != PHL_OK) return st;
   if ((st = copy_field(g, g->B + G.plane, by, nullptr, nx, ny + 1, nz, true)) != PHL_OK) return st;
   if ((st = copy_field(g, g->B + 2 * G.plane, bz, nullptr, nx, ny, nz + 1, true)) != PHL_OK) return st;
-  if (g->T && T)
-    if ((st = copy_field(g, g->T, T, nullptr, nx, ny, nz, true)) != PHL_OK) return st;
+  if (g->T) {
+    if (T) {
+      if ((st = copy_field(g, g->T, T, nullptr, nx, ny, nz, true)) != PHL_OK) return st;
+    } else {   // no guesses: the network's (use_mlp) or the table's mid-range temperature
+      CK(cudaMemsetAsync(g->T, 0, G.plane * sizeof(double), g->stream), "clear T");
+    }
+  }
   CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream), "reset flags");
   if (where == PHL_HOST) CK(cudaStreamSynchronize(g->stream), "sync");
   return PHL_OK;
@@ -505,6 +518,11 @@ phl_status phl_get_stats(phl_grid *g, phl_stats *st) {
   st->device_flags = f;
   st->kernels_per_step = g->launches_per_step;
   st->device_bytes = g->bytes;
+  if (g->niter) {
+    unsigned long long it = 0;
+    CK(cudaMemcpy(&it, g->niter, sizeof(it), cudaMemcpyDeviceToHost), "read Newton iterations");
+    st->newton_iters = (long)it;
+  }
   return PHL_OK;
 }
 

@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "eos_stellar.cuh"
+#include "mlp_dev.cuh"
 #include "riemann.cuh"
 
 namespace phl {
@@ -72,6 +73,9 @@ struct DevGeo {
   double Acomp[PHL_NSPEC_MAX], Zcomp[PHL_NSPEC_MAX];
   double newton_tol;
   int newton_maxit;
+  int use_mlp;                 // first Newton guess from the network
+  mlp::Dev mlp;
+  unsigned long long *niter;   // Newton iterations summed over cells (device)
 };
 
 __host__ __device__ __forceinline__ long sidx(const DevGeo &G, int i, int j, int k) {
@@ -258,6 +262,7 @@ cudaError_t stellar_background(const DevGeo &G, int L, double *bg, const double 
 void launch_prim_to_cons(const DevGeo &G, const double *prim, double *U, const double *Bf, double *T, int *dflag,
                          cudaStream_t s);
 const eos::Table *eos_table_view(const struct phl_eos_table *t);
+mlp::Dev mlp_view(const struct phl_mlp *m);
 
 // Scale of conserved variable v of the mixed form (rho, m, E, rho X).
 __host__ __device__ __forceinline__ double usc(const DevGeo &G, int v) {
