@@ -309,6 +309,49 @@ phl_status phl_mlp_guess_temperature(const phl_mlp *m, const phl_eos_table *t, l
 phl_status phl_mlp_train(phl_mlp *m, const phl_eos_table *t, const phl_mlp_train_cfg *cfg,
                          phl_mlp_train_stats *st);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles of independent boxes of uneven sizes (mixed form, ideal gas, no
+ * species, SSP-RK3).  Each box is a grid of its own (state I/O through
+ * phl_ensemble_grid + phl_set_state / phl_get_state; each box keeps its own
+ * CFL step).  phl_ensemble_step runs one persistent cooperative launch per RK
+ * stage covering every box and every step of the stage (phases separated by
+ * grid-wide barriers); the step's three launches are captured as one CUDA
+ * graph and replayed.  The launch shape (threads per block, blocks per SM)
+ * is chosen by phl_ensemble_autotune or set explicitly. */
+typedef struct phl_ensemble phl_ensemble;
+
+typedef struct {
+  int block;                /* threads per block (128 or 256)                   */
+  int blocks_per_sm;        /* persistent blocks per SM (<= co-resident limit)  */
+  double ms_per_step;       /* measured (autotune)                              */
+} phl_tune_entry;
+
+typedef struct {
+  int nbox;
+  long cells;               /* total cells of all boxes                         */
+  int block, blocks_per_sm; /* current launch shape                             */
+  int graph;                /* 1 when the step runs as a captured CUDA graph    */
+  int launches_per_step;
+} phl_ensemble_info;
+
+/* descs[nbox]: one description per box (precision PHL_MIXED, PHL_EOS_IDEAL,
+ * nspec 0, rk 3, one shared stream; NULL: the ensemble creates a blocking
+ * stream of its own, which the default stream's work is ordered with).
+ * use_graph != 0 captures the step.
+ * Errors: PHL_EINVAL, PHL_EUNSUPPORTED, PHL_ENOMEM, PHL_ECUDA. */
+phl_status phl_ensemble_create(const phl_grid_desc *descs, int nbox, int use_graph, phl_ensemble **out);
+/* Grid handle of box `box` (owned by the ensemble; do not destroy). */
+phl_status phl_ensemble_grid(phl_ensemble *e, int box, phl_grid **g);
+phl_status phl_ensemble_step(phl_ensemble *e, int nsteps);
+/* Device flags of every box (as phl_check). */
+phl_status phl_ensemble_check(phl_ensemble *e);
+phl_status phl_ensemble_set_shape(phl_ensemble *e, int block, int blocks_per_sm);
+/* Time every launch shape for trial_steps steps (state saved and restored)
+ * and keep the fastest; out[max] receives the timings (*n entries). */
+phl_status phl_ensemble_autotune(phl_ensemble *e, int trial_steps, phl_tune_entry *out, int max, int *n);
+phl_status phl_ensemble_get_info(const phl_ensemble *e, phl_ensemble_info *info);
+void phl_ensemble_destroy(phl_ensemble *e);
+
 void phl_destroy(phl_grid *g);
 
 /* Message describing the calling thread's last failure ("" if none). */

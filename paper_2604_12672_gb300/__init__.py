@@ -109,6 +109,14 @@ _SIGS = {
     "phl_mlp_guess_temperature": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_int]),
     "phl_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(MlpTrainCfg), C.POINTER(MlpTrainStats)]),
+    "phl_ensemble_create": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "phl_ensemble_grid": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "phl_ensemble_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "phl_ensemble_check": (C.c_int, [C.c_void_p]),
+    "phl_ensemble_set_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "phl_ensemble_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "phl_ensemble_get_info": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "phl_ensemble_destroy": (None, [C.c_void_p]),
     "phl_eos_table_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_long]),
     "phl_eos": (C.c_int, [C.c_void_p, C.c_long] + [C.c_void_p] * 10 + [C.c_int, C.c_double, C.c_int, C.c_int,
                                                                           C.c_void_p]),
@@ -293,62 +301,144 @@ class Mlp:
             pass
 
 
+def make_desc(pr, precision="fp64", riemann=None, eps_sf=None, cfl=None, rk=3, wb=True, stream=None,
+              mach_thr=None, eos_table=None, newton_tol=1e-11, newton_maxit=50, mlp=None, mlp_mode=1):
+    """phl_grid_desc of a problem; returns (desc, arrays the desc points into)."""
+    d = GridDesc()
+    for k in range(3):
+        d.n[k] = pr.n[k]
+        d.lo[k] = pr.lo[k]
+        d.hi[k] = pr.hi[k]
+        d.bc[k][0], d.bc[k][1] = pr.bc[k]
+        d.g[k] = pr.g[k]
+    d.eos = EOS[pr.eos]
+    d.gamma = pr.gamma
+    d.nspec = pr.nspec
+    if pr.eos == "stellar":
+        if eos_table is None:
+            raise ValueError("stellar problems need an EosTable")
+        d.eos_table = eos_table.h
+        for l in range(pr.nspec):
+            d.A[l], d.Z[l] = pr.meta["A"][l], pr.meta["Z"][l]
+            d.bg_X[l] = pr.meta["bg_X"][l]
+    keep = []
+    if pr.bg is not None and wb:
+        for key in ("rho_c", "p_c", "rho_f", "p_f", "ge_c", "gc_c", "ge_f", "gc_f"):
+            if key in pr.bg:
+                arr = np.ascontiguousarray(pr.bg[key], dtype=np.float64)
+                keep.append(arr)
+                setattr(d, "bg_" + key, arr.ctypes.data_as(_dp))
+    if pr.heat is not None:
+        h = np.ascontiguousarray(pr.heat, dtype=np.float64)
+        keep.append(h)
+        d.heat = h.ctypes.data_as(_dp)
+    d.cfl = pr.cfl if cfl is None else cfl
+    d.rk = rk
+    d.riemann = RIEMANN[riemann or pr.riemann]
+    d.eps_sf = pr.eps_sf if eps_sf is None else eps_sf
+    d.mach_thr = pr.mach_thr if mach_thr is None else mach_thr
+    d.precision = PRECISION[precision]
+    d.newton_tol = newton_tol
+    d.newton_maxit = newton_maxit
+    d.use_mlp = int(mlp_mode) if mlp is not None else 0
+    d.mlp = mlp.h if mlp is not None else None
+    d.stream = stream
+    return d, keep
+
+
+class TuneEntry(C.Structure):
+    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("ms_per_step", C.c_double)]
+
+
+class EnsembleInfo(C.Structure):
+    _fields_ = [("nbox", C.c_int), ("cells", C.c_long), ("block", C.c_int), ("blocks_per_sm", C.c_int),
+                ("graph", C.c_int), ("launches_per_step", C.c_int)]
+
+
+class Ensemble:
+    """Independent boxes of uneven sizes stepped together (phl_ensemble_* in
+    include/phl.h): one persistent launch per RK stage, graph-captured step."""
+
+    def __init__(self, problems, use_graph=True, stream=None):
+        self.problems = list(problems)
+        descs = (GridDesc * len(self.problems))()
+        self._keep = []
+        for i, pr in enumerate(self.problems):
+            d, keep = make_desc(pr, precision="mixed", stream=stream)
+            descs[i] = d
+            self._keep += keep
+        h = C.c_void_p()
+        _check(lib().phl_ensemble_create(descs, len(self.problems), int(bool(use_graph)), C.byref(h)))
+        self.h = h
+        self.grids = []
+        for i, pr in enumerate(self.problems):
+            gh = C.c_void_p()
+            _check(lib().phl_ensemble_grid(self.h, i, C.byref(gh)))
+            self.grids.append(Grid(pr, _handle=gh))
+
+    def load(self):
+        for g in self.grids:
+            g.load()
+
+    def step(self, nsteps=1):
+        _check(lib().phl_ensemble_step(self.h, int(nsteps)))
+
+    def check(self):
+        _check(lib().phl_ensemble_check(self.h))
+
+    def set_shape(self, block, blocks_per_sm):
+        _check(lib().phl_ensemble_set_shape(self.h, int(block), int(blocks_per_sm)))
+
+    def autotune(self, trial_steps=2):
+        out = (TuneEntry * 64)()
+        n = C.c_int()
+        _check(lib().phl_ensemble_autotune(self.h, int(trial_steps), out, 64, C.byref(n)))
+        return [{"block": out[i].block, "blocks_per_sm": out[i].blocks_per_sm, "ms_per_step": out[i].ms_per_step}
+                for i in range(min(n.value, 64))]
+
+    def info(self):
+        i = EnsembleInfo()
+        _check(lib().phl_ensemble_get_info(self.h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in EnsembleInfo._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            for g in self.grids:
+                g.h = None
+            lib().phl_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Grid:
     """One simulation box on the current CUDA device (see include/phl.h)."""
 
     def __init__(self, pr, precision="fp64", riemann=None, eps_sf=None, cfl=None, rk=3, wb=True,
                  stream=None, mach_thr=None, eos_table=None, newton_tol=1e-11, newton_maxit=50, mlp=None,
-                 mlp_mode=1):
+                 mlp_mode=1, _handle=None):
         self.pr = pr
         self.eos_table = eos_table
         self.mlp = mlp
-        d = GridDesc()
-        for k in range(3):
-            d.n[k] = pr.n[k]
-            d.lo[k] = pr.lo[k]
-            d.hi[k] = pr.hi[k]
-            d.bc[k][0], d.bc[k][1] = pr.bc[k]
-            d.g[k] = pr.g[k]
-        d.eos = EOS[pr.eos]
-        d.gamma = pr.gamma
-        d.nspec = pr.nspec
-        if pr.eos == "stellar":
-            if eos_table is None:
-                raise ValueError("stellar problems need an EosTable")
-            d.eos_table = eos_table.h
-            for l in range(pr.nspec):
-                d.A[l], d.Z[l] = pr.meta["A"][l], pr.meta["Z"][l]
-                d.bg_X[l] = pr.meta["bg_X"][l]
-        self._keep = []
-        if pr.bg is not None and wb:
-            for key in ("rho_c", "p_c", "rho_f", "p_f", "ge_c", "gc_c", "ge_f", "gc_f"):
-                if key in pr.bg:
-                    arr = np.ascontiguousarray(pr.bg[key], dtype=np.float64)
-                    self._keep.append(arr)
-                    setattr(d, "bg_" + key, arr.ctypes.data_as(_dp))
-        if pr.heat is not None:
-            h = np.ascontiguousarray(pr.heat, dtype=np.float64)
-            self._keep.append(h)
-            d.heat = h.ctypes.data_as(_dp)
-        d.cfl = pr.cfl if cfl is None else cfl
-        d.rk = rk
-        d.riemann = RIEMANN[riemann or pr.riemann]
-        d.eps_sf = pr.eps_sf if eps_sf is None else eps_sf
-        d.mach_thr = pr.mach_thr if mach_thr is None else mach_thr
-        d.precision = PRECISION[precision]
-        d.newton_tol = newton_tol
-        d.newton_maxit = newton_maxit
-        d.use_mlp = int(mlp_mode) if mlp is not None else 0
-        d.mlp = mlp.h if mlp is not None else None
-        d.stream = stream
+        if _handle is not None:          # a box owned by an Ensemble
+            self.h, self._owned, self._keep = _handle, False, []
+            return
+        d, self._keep = make_desc(pr, precision, riemann, eps_sf, cfl, rk, wb, stream, mach_thr, eos_table,
+                                  newton_tol, newton_maxit, mlp, mlp_mode)
         self.desc = d
         h = C.c_void_p()
         _check(lib().phl_create_grid(C.byref(d), C.byref(h)))
         self.h = h
+        self._owned = True
 
     def close(self):
         if getattr(self, "h", None):
-            lib().phl_destroy(self.h)
+            if getattr(self, "_owned", True):
+                lib().phl_destroy(self.h)
             self.h = None
 
     def __del__(self):

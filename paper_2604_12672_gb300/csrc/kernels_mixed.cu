@@ -1,167 +1,26 @@
-// kernels_mixed.cu -- mixed-precision stage: FP32 arithmetic on the
-// well-balanced deviations, FP64 for the background and the RK accumulation.
-//
-// State during a step: U^n in FP64 (cells and faces) and the stage increment
-// dU = U^(s) - U^n in FP32.  SSP-RK stages (Sect. 2.9) with a + b = 1 give
-//   U^(s) - U^n = b (U^(s-1) - U^n) - b dt R   =>   dU_out = b (dU_in - dt R),
-// so every stage works on FP32 increments and only the last stage adds its
-// increment into U^n in FP64.  Primitive deviations (Sect. 2.8) are formed
-// from U^n - U_hat in FP64 (one subtraction each for rho and E) plus dU.
+// kernels_mixed.cu -- mixed-precision stage, one kernel per step of the
+// stage (device bodies in mixed_common.cuh).
 #include <math.h>
 
-#include "phl_internal.cuh"
-#include "stage_common.cuh"
+#include "mixed_common.cuh"
 
 namespace phl {
 using namespace stage;
 namespace {
 
-// Deviations of the stage-input state at interior cell (i, j, k), in FP32.
-__device__ __forceinline__ void cell_prims_mx(const DevGeo &G, const double *__restrict__ U,
-                                              const double *__restrict__ Bf, const float *__restrict__ dU,
-                                              const float *__restrict__ dB, int i, int j, int k, float *w,
-                                              int *dflag) {
-  const long p = sidx(G, i, j, k);
-  const long pl = G.plane;
-  const Bg b = bg_cell(G, k);                       // FP64 background for the deviations
-  const double ehat = G.has_bg ? G.bg_e_c[k + BG_NG] : 0.0;
-  const double sr = G.isc_rho, sm = G.isc_m, se = G.isc_e, sb = G.isc_b;   // to scaled units (exact)
-  float drho = d2f_bits((U[p] - b.rho) * sr);
-  float m0 = d2f_bits(U[pl + p] * sm), m1 = d2f_bits(U[2 * pl + p] * sm), m2 = d2f_bits(U[3 * pl + p] * sm);
-  float dE = d2f_bits((U[4 * pl + p] - ehat) * se);
-  float bxl = d2f_bits(Bf[p] * sb), bxh = d2f_bits(Bf[p + 1] * sb);
-  float byl = d2f_bits(Bf[pl + p] * sb), byh = d2f_bits(Bf[pl + p + G.sy] * sb);
-  float bzl = d2f_bits(Bf[2 * pl + p] * sb), bzh = d2f_bits(Bf[2 * pl + p + G.sz] * sb);
-  if (dU) {
-    drho += dU[p];
-    m0 += dU[pl + p]; m1 += dU[2 * pl + p]; m2 += dU[3 * pl + p];
-    dE += dU[4 * pl + p];
-  }
-  if (dB) {
-    bxl += dB[p]; bxh += dB[p + 1];
-    byl += dB[pl + p]; byh += dB[pl + p + G.sy];
-    bzl += dB[2 * pl + p]; bzh += dB[2 * pl + p + G.sz];
-  }
-  const BgT<float> bf = bg_cell_t<float>(G, k);
-  const float rho = bf.rho + drho;
-  const float ir = 1.0f / rho;
-  const float vx = m0 * ir, vy = m1 * ir, vz = m2 * ir;
-  const float bx = 0.5f * (bxl + bxh), by = 0.5f * (byl + byh), bz = 0.5f * (bzl + bzh);
-  const float gm1 = G.gm1f;
-  const float dP = gm1 * (dE - 0.5f * rho * (vx * vx + vy * vy + vz * vz) - 0.5f * (bx * bx + by * by + bz * bz));
-  w[W_RHO] = drho;
-  w[W_VX] = vx; w[W_VY] = vy; w[W_VZ] = vz;
-  w[W_BX] = bx; w[W_BY] = by; w[W_BZ] = bz;
-  w[W_P] = dP;
-  w[W_GE] = G.gammaf - bf.ge;
-  w[W_GC] = G.gammaf - bf.gc;
-#pragma unroll
-  for (int l = 0; l < PHL_NSPEC_MAX; ++l) {
-    if (l >= G.nspec) continue;
-    float rx = d2f_bits(U[(U_X0 + l) * pl + p] * sr);
-    if (dU) rx += dU[(U_X0 + l) * pl + p];
-    w[W_X0 + l] = rx * ir;
-  }
-  const float P = bf.p + dP;
-  if (!(rho > 0.0f) || !(P > 0.0f)) atomicOr(dflag, FLAG_NEG);
-  if (!isfinite(P) || !isfinite(rho)) atomicOr(dflag, FLAG_NAN);
-}
-
 __global__ void k_prim_mx(DevGeo G, Box box, const double *__restrict__ U, const double *__restrict__ Bf,
                           const float *__restrict__ dU, const float *__restrict__ dB, float *__restrict__ W,
                           int *dflag) {
-  {
-    int c[3], s[3];
-    bool fl[3];
-    if (!cell3(box, c)) return;
-    for (int d = 0; d < 3; ++d) {
-      fl[d] = false;
-      s[d] = G.act[d] ? cell_src(c[d], G.n[d], G.bc[d][0], G.bc[d][1], fl[d]) : 0;
-    }
-    float w[NW_MAX];
-    cell_prims_mx(G, U, Bf, dU, dB, s[0], s[1], s[2], w, dflag);
-    for (int d = 0; d < 3; ++d)
-      if (fl[d]) { w[W_VX + d] = -w[W_VX + d]; w[W_BX + d] = -w[W_BX + d]; }
-    const long q = widx(G, c[0], c[1], c[2]);
-#pragma unroll
-    for (int v = 0; v < NW_MAX; ++v)
-      if (v < G.nw) W[v * G.wtot + q] = w[v];
-  }
+  k_prim_mx_at(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, U, Bf, dU, dB, W, dflag);
 }
 
-struct StageMx {
-  double *U, *B;          // U^n (updated in place by the last stage)
-  float *dU, *dB;         // stage increments (in place)
-  bool first, last;       // first stage: dU_in = 0; last: fold into U^n
-  float b;                // RK coefficient of the stage
-  const double *dt;
-  const float *W, *F[3], *E;
-};
-
 __global__ void k_update_cells_mx(DevGeo G, Box box, StageMx S) {
-  const float dt = (float)(*S.dt * G.isc_t);
-  {
-    int c[3];
-    if (!cell3(box, c)) return;
-    const long p = widx(G, c[0], c[1], c[2]);
-    const long ps = sidx(G, c[0], c[1], c[2]);
-    const long wt = G.wtot, pl = G.plane;
-    float r[5 + PHL_NSPEC_MAX];
-#pragma unroll
-    for (int v = 0; v < 5 + PHL_NSPEC_MAX; ++v) {
-      if (v >= G.nv) continue;
-      const int fc = v < 5 ? v : F_X0 + (v - U_X0);
-      float s = 0.0f;
-      for (int d = 0; d < 3; ++d) {
-        if (!G.act[d]) continue;
-        const float *f = S.F[d] + fc * wt;
-        s += (f[p + (d == 0 ? 1L : (d == 1 ? G.wy : G.wz))] - f[p]) * G.idxf[d];
-      }
-      r[v] = s;
-    }
-    // sources S - S_hat: (rho - rho_hat) g on momentum, rho u . g (+ heating) on energy
-    const float drho = S.W[W_RHO * wt + p];
-    const float rho = bg_cell_t<float>(G, c[2]).rho + drho;
-    float se = 0.0f;
-    for (int d = 0; d < 3; ++d) {
-      const float gd = G.gf[d];
-      r[U_MX + d] -= drho * gd;
-      se += rho * S.W[(W_VX + d) * wt + p] * gd;
-    }
-    if (G.heatf) se += G.heatf[c[2]];
-    r[U_E] -= se;
-#pragma unroll
-    for (int v = 0; v < 5 + PHL_NSPEC_MAX; ++v) {
-      if (v >= G.nv) continue;
-      const long q = v * pl + ps;
-      const float din = S.first ? 0.0f : S.dU[q];
-      const float dout = S.b * (din - dt * r[v]);
-      if (S.last) S.U[q] += f2d_bits(dout) * usc(G, v);
-      else S.dU[q] = dout;
-    }
-  }
+  k_update_cells_mx_at(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, S);
 }
 
 template <int D>
 __global__ void k_update_faces_mx(DevGeo G, Box box, StageMx S) {
-  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
-  const float dt = (float)(*S.dt * G.isc_t);
-  {
-    int c[3];
-    if (!cell3(box, c)) return;
-    int e[3] = {c[0], c[1], c[2]};
-    if (!G.act[D]) e[D] = 0;
-    const long p = widx(G, e[0], e[1], e[2]);
-    const long wt = G.wtot;
-    float r = 0.0f;
-    if (G.act[A]) r += (S.E[(long)B * wt + p + wstride(G, A)] - S.E[(long)B * wt + p]) * G.idxf[A];
-    if (G.act[B]) r -= (S.E[(long)A * wt + p + wstride(G, B)] - S.E[(long)A * wt + p]) * G.idxf[B];
-    const long q = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
-    const float din = S.first ? 0.0f : S.dB[q];
-    const float dout = S.b * (din - dt * r);
-    if (S.last) S.B[q] += f2d_bits(dout) * G.sc_b;
-    else S.dB[q] = dout;
-  }
+  k_update_faces_mx_at<D>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, S);
 }
 
 // CFL condition in FP32 from U^n (Eq. cfl); non-negative floats order like
@@ -172,23 +31,7 @@ __global__ void k_dt_mx(DevGeo G, Box box, const double *__restrict__ U, const d
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < box.n; t += (long)gridDim.x * blockDim.x) {
     int c[3];
     unflat(box, t, c);
-    float w[NW_MAX];
-    cell_prims_mx(G, U, Bf, nullptr, nullptr, c[0], c[1], c[2], w, dflag);
-    const BgT<float> b = bg_cell_t<float>(G, c[2]);
-    const float rho = b.rho + w[W_RHO], P = b.p + w[W_P], gc = b.gc + w[W_GC];
-    const float ir = 1.0f / rho;
-    const float a2 = gc * P * ir;
-    const float b2 = (w[W_BX] * w[W_BX] + w[W_BY] * w[W_BY] + w[W_BZ] * w[W_BZ]) * ir;
-    float s = 0.0f;
-    for (int d = 0; d < 3; ++d) {
-      if (!G.act[d]) continue;
-      const float bd2 = w[W_BX + d] * w[W_BX + d] * ir;
-      float disc = (a2 + b2) * (a2 + b2) - 4.0f * a2 * bd2;
-      disc = fmaxf(disc, 0.0f);
-      const float cf = sqrtf(0.5f * (a2 + b2 + sqrtf(disc)));
-      s += (fabsf(w[W_VX + d]) + cf) * G.idxf[d];
-    }
-    m = (s == s) ? fmaxf(m, s) : INFINITY;
+    m = fmaxf(m, dt_rate_mx(G, U, Bf, c, dflag));
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   __shared__ float red[TPB / 32];

@@ -157,6 +157,23 @@ void do_stage(phl_grid *g, const double *Uin, const double *Bin, double *Uout, d
 
 }  // namespace
 
+namespace phl {
+GridView grid_view(phl_grid *g) {
+  GridView v;
+  v.G = &g->G;
+  v.U = g->U; v.B = g->B;
+  v.dU = g->dUf; v.dB = g->dBf; v.W = g->Wf;
+  for (int k = 0; k < 3; ++k) v.F[k] = g->Ff[k];
+  v.E = g->Ef;
+  v.raw = g->raw; v.flag = g->flag;
+  v.dt = g->dt; v.fmax = g->fmax; v.dflag = g->dflag;
+  v.stream = g->stream;
+  v.steps = &g->steps;
+  v.mixed = g->mixed;
+  return v;
+}
+}  // namespace phl
+
 extern "C" {
 
 const char *phl_last_error(void) { return g_err; }
@@ -506,6 +523,7 @@ phl_status phl_check(phl_grid *g) {
   if (!g) return fail(PHL_EINVAL, "null grid");
   return check_flags(g);
 }
+
 
 phl_status phl_get_stats(phl_grid *g, phl_stats *st) {
   if (!g || !st) return fail(PHL_EINVAL, "null argument");

@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "eos_stellar.cuh"
+#include "phl.h"
 #include "mlp_dev.cuh"
 #include "riemann.cuh"
 
@@ -251,6 +252,21 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
                         int *nlaunch, Prof *prof);
 void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigned int *fmax_bits, double *dt,
                      int *dflag, cudaStream_t s, int *nlaunch, Prof *prof);
+
+// Buffers of a grid for the ensemble path (ensemble.cu); mixed grids only.
+struct GridView {
+  const DevGeo *G;
+  double *U, *B;
+  float *dU, *dB, *W, *F[3], *E;
+  uint8_t *raw, *flag;
+  double *dt;
+  unsigned int *fmax;
+  int *dflag;
+  cudaStream_t stream;
+  long *steps;
+  bool mixed;
+};
+GridView grid_view(::phl_grid *g);
 
 // Stellar EOS path (kernels_stellar.cu)
 template <typename R>

@@ -55,15 +55,19 @@ inline Box make_box(int lx, int hx, int ly, int hy, int lz, int hz) {
 // One thread per box element, 1D launch; the (i, j, k) decode uses FastDiv.
 inline dim3 block3(const Box &) { return dim3(256, 1, 1); }
 inline dim3 grid3(const Box &b) { return dim3((unsigned)((b.n + 255) / 256), 1, 1); }
-__device__ __forceinline__ bool cell3(const Box &b, int *c) {
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if ((long)t >= b.n) return false;
+// Cell of linear index tl in the box (x fastest); false beyond the box.
+__device__ __forceinline__ bool cell_at(const Box &b, long tl, int *c) {
+  if (tl >= b.n) return false;
+  const unsigned t = (unsigned)tl;
   const unsigned q1 = fastdiv(t, b.fx);
   const unsigned q2 = fastdiv(q1, b.fy);
   c[0] = b.lo[0] + (int)(t - q1 * b.fx.d);
   c[1] = b.lo[1] + (int)(q1 - q2 * b.fy.d);
   c[2] = b.lo[2] + (int)q2;
   return true;
+}
+__device__ __forceinline__ bool cell3(const Box &b, int *c) {
+  return cell_at(b, blockIdx.x * (long)blockDim.x + threadIdx.x, c);
 }
 
 __device__ __forceinline__ void unflat(const Box &b, long t, int *c) {
@@ -92,10 +96,10 @@ __device__ __forceinline__ R vl_slope(R a, R b, R c) {
 __device__ __forceinline__ long wstride(const DevGeo &G, int d) { return d == 0 ? 1L : (d == 1 ? G.wy : G.wz); }
 
 template <typename R>
-__global__ void k_flag_raw(DevGeo G, Box box, const R *__restrict__ W, uint8_t *__restrict__ raw) {
+__device__ __forceinline__ void k_flag_raw_at(long tl, const DevGeo &G, const Box &box, const R *__restrict__ W, uint8_t *__restrict__ raw) {
   {
     int c[3];
-    if (!cell3(box, c)) return;
+    if (!cell_at(box, tl, c)) return;
     const long q = widx(G, c[0], c[1], c[2]);
     const R *P = W + (long)W_P * G.wtot;
     const R P0 = P[q] + bg_cell_t<R>(G, c[2]).p;
@@ -111,15 +115,19 @@ __global__ void k_flag_raw(DevGeo G, Box box, const R *__restrict__ W, uint8_t *
     raw[c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2])] = (sum / (eps_sf_t<R>(G) * P0) > R(1)) ? 1 : 0;
   }
 }
+template <typename R>
+__global__ void k_flag_raw(DevGeo G, Box box, const R *__restrict__ W, uint8_t *__restrict__ raw) {
+  k_flag_raw_at<R>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, W, raw);
+}
 
 // 5^d dilation of the raw shock flags (Sect. 2.7), done as one 5-wide OR per
 // active axis: OR over a box equals the nested ORs over its axes.  Neighbours
 // beyond a periodic boundary wrap, beyond any other boundary are skipped.
 template <int D>
-__global__ void k_dilate_axis(DevGeo G, Box box, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
+__device__ __forceinline__ void k_dilate_axis_at(long tl, const DevGeo &G, const Box &box, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
   {
     int c[3];
-    if (!cell3(box, c)) return;
+    if (!cell_at(box, tl, c)) return;
     const int n = G.n[D];
     const bool per = G.bc[D][0] == 0;
     uint8_t f = 0;
@@ -136,19 +144,26 @@ __global__ void k_dilate_axis(DevGeo G, Box box, const uint8_t *__restrict__ in,
     out[c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2])] = f;
   }
 }
+template <int D>
+__global__ void k_dilate_axis(DevGeo G, Box box, const uint8_t *__restrict__ in, uint8_t *__restrict__ out) {
+  k_dilate_axis_at<D>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, in, out);
+}
 
 // Flags of the cells the face stencils touch ([-1, n] on active axes): a ghost
 // cell carries the flag of the interior cell its data comes from.
-__global__ void k_flag_expand(DevGeo G, Box box, const uint8_t *__restrict__ dil, uint8_t *__restrict__ flag) {
+__device__ __forceinline__ void k_flag_expand_at(long tl, const DevGeo &G, const Box &box, const uint8_t *__restrict__ dil, uint8_t *__restrict__ flag) {
   {
     int c[3], s[3];
-    if (!cell3(box, c)) return;
+    if (!cell_at(box, tl, c)) return;
     for (int d = 0; d < 3; ++d) {
       bool fl;
       s[d] = G.act[d] ? cell_src(c[d], G.n[d], G.bc[d][0], G.bc[d][1], fl) : 0;
     }
     flag[widx(G, c[0], c[1], c[2])] = dil[s[0] + (long)G.n[0] * (s[1] + (long)G.n[1] * s[2])];
   }
+}
+__global__ void k_flag_expand(DevGeo G, Box box, const uint8_t *__restrict__ dil, uint8_t *__restrict__ flag) {
+  k_flag_expand_at(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, dil, flag);
 }
 
 // raw -> dilated (interior) -> flags on the work layout; tmp: one interior byte field.
@@ -174,12 +189,12 @@ inline int launch_flags(const DevGeo &G, uint8_t *raw, uint8_t *tmp, uint8_t *fl
 }
 
 template <int D, typename R, int NS>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_flux(DevGeo G, Box box, const R *__restrict__ W, const double *__restrict__ Bf,
+__device__ __forceinline__ void k_flux_at(long tl, const DevGeo &G, const Box &box, const R *__restrict__ W, const double *__restrict__ Bf,
                        const R *__restrict__ dB, const uint8_t *__restrict__ flag, R *__restrict__ F, int *dflag) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   {
     int c[3];
-    if (!cell3(box, c)) return;
+    if (!cell_at(box, tl, c)) return;
     const long sd = wstride(G, D);
     const long pR = widx(G, c[0], c[1], c[2]), pL = pR - sd;
     constexpr int NWC = W_X0 + NS;   // components this instantiation can hold
@@ -256,15 +271,20 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_flux(DevGeo G, 
     F[(long)G.nf * wt + pR] = (R)up;   // contact direction for Contact-CT
   }
 }
+template <int D, typename R, int NS>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_flux(DevGeo G, Box box, const R *__restrict__ W, const double *__restrict__ Bf,
+                       const R *__restrict__ dB, const uint8_t *__restrict__ flag, R *__restrict__ F, int *dflag) {
+  k_flux_at<D, R, NS>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, W, Bf, dB, flag, F, dflag);
+}
 
 // Edge EMF along D at the lower corner (a-1/2, b-1/2), (D, A, B) cyclic.
 template <int D, typename R>
-__global__ void k_emf(DevGeo G, Box box, const R *__restrict__ W, const R *__restrict__ FA,
+__device__ __forceinline__ void k_emf_at(long tl, const DevGeo &G, const Box &box, const R *__restrict__ W, const R *__restrict__ FA,
                       const R *__restrict__ FB, R *__restrict__ E) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
   {
     int c[3];
-    if (!cell3(box, c)) return;
+    if (!cell_at(box, tl, c)) return;
     const long p = widx(G, c[0], c[1], c[2]);
     const long wt = G.wtot;
     R e;
@@ -304,6 +324,11 @@ __global__ void k_emf(DevGeo G, Box box, const R *__restrict__ W, const R *__res
       e = R(0);
     E[(long)D * wt + p] = e;
   }
+}
+template <int D, typename R>
+__global__ void k_emf(DevGeo G, Box box, const R *__restrict__ W, const R *__restrict__ FA,
+                      const R *__restrict__ FB, R *__restrict__ E) {
+  k_emf_at<D, R>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, W, FA, FB, E);
 }
 
 
