@@ -383,6 +383,64 @@ def stellar_c3(P, n, steps, warmup, stream, ws):
     return out
 
 
+def ensemble_c4(P, steps, warmup, stream, ws):
+    """24 independent boxes of the stratified-box physics with edges drawn
+    from {64, 96, 128, 160, 192} per axis (seed 2024), mixed form: one
+    persistent launch per stage over all boxes, graph-captured step, launch
+    shape from the autotuner.  Beside it, the same boxes stepped one after
+    another with the per-kernel path."""
+    import torch
+    import workloads as W
+    probs = W.ensemble()
+    cells = sum(p.ncells for p in probs)
+    E = P.Ensemble(probs, use_graph=True)
+    E.load()
+    tune = E.autotune(trial_steps=1)
+    E.load()
+    for _ in range(warmup):
+        E.step(1)
+    E.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0.record()
+    E.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = allreduce_max(e0.elapsed_time(e1), ws)
+    E.check()
+    info = E.info()
+    E.close()
+    # the same boxes, one grid after another (per-kernel launches, no graph)
+    grids = [P.Grid(p, precision="mixed") for p in probs]
+    for g in grids:
+        g.load()
+        g.step(1)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        for g in grids:
+            g.step(1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    launches_seq = sum(g.stats()["kernels_per_step"] for g in grids)
+    for g in grids:
+        g.close()
+    return {"workload": "24 stratified boxes (C2 physics), edges from {64,96,128,160,192} per axis, seed 2024, "
+                        "mixed form", "boxes": [list(p.n) for p in probs], "cells": cells,
+            "value": cells * STAGES * steps * ws / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "launch_shape": {"mode": ["persistent stage kernel", "one launch per phase",
+                                      "per-box kernel chains on concurrent streams"][info["mode"]],
+                             "block": info["block"], "blocks_per_sm": info["blocks_per_sm"],
+                             "streams": info["streams"]},
+            "graph": info["graph"], "launches_per_step": info["launches_per_step"],
+            "autotune": tune,
+            "sequential_grids": {"value": cells * STAGES * steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / steps,
+                                 "launches_per_step": launches_seq}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,6 +455,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-c3", action="store_true", help="skip the stellar-EOS box (mixed + network vs FP64)")
     ap.add_argument("--c3-steps", type=int, default=4)
+    ap.add_argument("--no-c4", action="store_true", help="skip the 24-box ensemble")
+    ap.add_argument("--c4-steps", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -442,6 +502,9 @@ def main():
     c3 = None
     if not args.no_c3 and len(forms) == 2:
         c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws)
+    c4 = None
+    if not args.no_c4 and len(forms) == 2:
+        c4 = ensemble_c4(P, args.c4_steps, 2, stream, ws)
     launches = sum(v[0] for v in h["kt"].values())
     forms_out = {f: {"value": r["value"], "ms_per_step": r["ms"] / args.steps,
                      "stage_hbm": stage_hbm(r["value"] / max(ws, 1), f, hbm_peak, peak_kind),
@@ -462,6 +525,7 @@ def main():
         "forms": forms_out,
         "l1_mixed_vs_fp64": l1,
         "stellar_eos_box": c3,
+        "ensemble_24_boxes": c4,
         "gpu_launches": launches,
         "e2e": e2e,
         "clocks": clk,

@@ -316,22 +316,29 @@ phl_status phl_mlp_train(phl_mlp *m, const phl_eos_table *t, const phl_mlp_train
  * CFL step).  phl_ensemble_step runs one persistent cooperative launch per RK
  * stage covering every box and every step of the stage (phases separated by
  * grid-wide barriers); the step's three launches are captured as one CUDA
- * graph and replayed.  The launch shape (threads per block, blocks per SM)
- * is chosen by phl_ensemble_autotune or set explicitly. */
+ * graph and replayed.  Alternatively each phase of a stage is its own launch
+ * over all boxes (mode 1), or each box runs its own chain of per-kernel
+ * launches on one of several concurrent streams (mode 2); the step is one
+ * graph in every mode.  The mode and launch shape are chosen by
+ * phl_ensemble_autotune or set explicitly. */
 typedef struct phl_ensemble phl_ensemble;
 
 typedef struct {
-  int block;                /* threads per block (128 or 256)                   */
-  int blocks_per_sm;        /* persistent blocks per SM (<= co-resident limit)  */
+  int mode;                 /* 0: persistent stage kernel; 1: one launch per     */
+                            /* phase of the stage (all boxes per launch); 2:     */
+                            /* each box's own kernel chain, concurrent streams  */
+  int block;                /* threads per block (128 or 256; modes 0, 1)       */
+  int blocks_per_sm;        /* mode 0: persistent blocks per SM                 */
+  int streams;              /* mode 2: concurrent streams                       */
   double ms_per_step;       /* measured (autotune)                              */
 } phl_tune_entry;
 
 typedef struct {
   int nbox;
   long cells;               /* total cells of all boxes                         */
-  int block, blocks_per_sm; /* current launch shape                             */
+  int mode, block, blocks_per_sm, streams;   /* current launch shape            */
   int graph;                /* 1 when the step runs as a captured CUDA graph    */
-  int launches_per_step;
+  int launches_per_step;    /* kernel launches per step (inside the graph)      */
 } phl_ensemble_info;
 
 /* descs[nbox]: one description per box (precision PHL_MIXED, PHL_EOS_IDEAL,
@@ -345,7 +352,7 @@ phl_status phl_ensemble_grid(phl_ensemble *e, int box, phl_grid **g);
 phl_status phl_ensemble_step(phl_ensemble *e, int nsteps);
 /* Device flags of every box (as phl_check). */
 phl_status phl_ensemble_check(phl_ensemble *e);
-phl_status phl_ensemble_set_shape(phl_ensemble *e, int block, int blocks_per_sm);
+phl_status phl_ensemble_set_shape(phl_ensemble *e, int mode, int block, int blocks_per_sm, int streams);
 /* Time every launch shape for trial_steps steps (state saved and restored)
  * and keep the fastest; out[max] receives the timings (*n entries). */
 phl_status phl_ensemble_autotune(phl_ensemble *e, int trial_steps, phl_tune_entry *out, int max, int *n);

@@ -113,7 +113,7 @@ _SIGS = {
     "phl_ensemble_grid": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "phl_ensemble_step": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_ensemble_check": (C.c_int, [C.c_void_p]),
-    "phl_ensemble_set_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "phl_ensemble_set_shape": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]),
     "phl_ensemble_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "phl_ensemble_get_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "phl_ensemble_destroy": (None, [C.c_void_p]),
@@ -347,12 +347,14 @@ def make_desc(pr, precision="fp64", riemann=None, eps_sf=None, cfl=None, rk=3, w
 
 
 class TuneEntry(C.Structure):
-    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("ms_per_step", C.c_double)]
+    _fields_ = [("mode", C.c_int), ("block", C.c_int), ("blocks_per_sm", C.c_int), ("streams", C.c_int),
+                ("ms_per_step", C.c_double)]
 
 
 class EnsembleInfo(C.Structure):
-    _fields_ = [("nbox", C.c_int), ("cells", C.c_long), ("block", C.c_int), ("blocks_per_sm", C.c_int),
-                ("graph", C.c_int), ("launches_per_step", C.c_int)]
+    _fields_ = [("nbox", C.c_int), ("cells", C.c_long), ("mode", C.c_int), ("block", C.c_int),
+                ("blocks_per_sm", C.c_int), ("streams", C.c_int), ("graph", C.c_int),
+                ("launches_per_step", C.c_int)]
 
 
 class Ensemble:
@@ -386,15 +388,15 @@ class Ensemble:
     def check(self):
         _check(lib().phl_ensemble_check(self.h))
 
-    def set_shape(self, block, blocks_per_sm):
-        _check(lib().phl_ensemble_set_shape(self.h, int(block), int(blocks_per_sm)))
+    def set_shape(self, block=256, blocks_per_sm=0, mode=0, streams=0):
+        _check(lib().phl_ensemble_set_shape(self.h, int(mode), int(block), int(blocks_per_sm), int(streams)))
 
     def autotune(self, trial_steps=2):
         out = (TuneEntry * 64)()
         n = C.c_int()
         _check(lib().phl_ensemble_autotune(self.h, int(trial_steps), out, 64, C.byref(n)))
-        return [{"block": out[i].block, "blocks_per_sm": out[i].blocks_per_sm, "ms_per_step": out[i].ms_per_step}
-                for i in range(min(n.value, 64))]
+        return [{"mode": out[i].mode, "block": out[i].block, "blocks_per_sm": out[i].blocks_per_sm,
+                 "streams": out[i].streams, "ms_per_step": out[i].ms_per_step} for i in range(min(n.value, 64))]
 
     def info(self):
         i = EnsembleInfo()

@@ -9,7 +9,11 @@
 // strides through them and finds an item's box by binary search over the
 // phase's prefix sums.  The step (3 launches) is captured once as a CUDA graph
 // and replayed; the launch shape (block size, blocks per SM) is picked by
-// timing the candidates (phl_ensemble_autotune).
+// timing the candidates (phl_ensemble_autotune).  A second mode launches each
+// phase on its own (all boxes per launch, each phase with its own register
+// allocation); a third gives every box its own chain of per-kernel launches
+// on concurrent streams (fork/join).  The step is one graph in every mode;
+// the autotuner times all of them.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <string.h>
@@ -167,6 +171,13 @@ __global__ void __launch_bounds__(BS) k_ens_stage(EnsArgs a) {
   run_phase(a, PH_UPD, t0, nth);
 }
 
+// One phase over all boxes (the phase-batched mode: each phase its own
+// launch, with its own register allocation, all launches in the step's graph).
+template <int PH, int BS>
+__global__ void __launch_bounds__(BS) k_ens_phase(EnsArgs a) {
+  run_phase(a, PH, (long)blockIdx.x * BS + threadIdx.x, (long)gridDim.x * BS);
+}
+
 }  // namespace
 }  // namespace phl
 
@@ -181,6 +192,12 @@ struct phl_ensemble {
   int nbox = 0;
   long cells = 0;
   cudaStream_t stream = nullptr;
+  int mode = 0;                      // 0: persistent cooperative stage kernel, 1: one launch per phase,
+                                     // 2: each box's own kernel chain, boxes on concurrent streams
+  int nstreams = 0;                  // mode 2
+  int chain_launches = 0;            // mode 2: kernel launches per step
+  std::vector<cudaStream_t> aux;     // mode 2 streams
+  std::vector<cudaEvent_t> ev;       // fork / join events (aux.size() + 1)
   int block = 256, bps = 0;          // launch shape
   int max_bps[2] = {0, 0};           // occupancy limits for 128 / 256 threads
   cudaStream_t own_stream = nullptr;
@@ -213,10 +230,87 @@ cudaError_t launch_stage(phl_ensemble *E, int stage, int nstages, float b) {
   return cudaLaunchCooperativeKernel((void *)k_ens_stage<256>, grid, block, args, 0, E->stream);
 }
 
+template <int BS>
+cudaError_t launch_phase(phl_ensemble *E, int ph, const EnsArgs &a) {
+  const long total = E->hpref[(size_t)ph * (E->nbox + 1) + E->nbox];
+  if (total == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<long>((total + BS - 1) / BS, 152L * 16);
+  switch (ph) {
+#define PHL_PH(P) case P: k_ens_phase<P, BS><<<blocks, BS, 0, E->stream>>>(a); break;
+    PHL_PH(PH_DT) PHL_PH(PH_DTFIN) PHL_PH(PH_PRIM) PHL_PH(PH_RAW) PHL_PH(PH_DIL0) PHL_PH(PH_DIL1)
+    PHL_PH(PH_DIL2) PHL_PH(PH_EXP) PHL_PH(PH_FLUX) PHL_PH(PH_EMF) PHL_PH(PH_UPD)
+#undef PHL_PH
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage_phases(phl_ensemble *E, int stage, int nstages, float b) {
+  EnsArgs a;
+  a.rec = E->drec;
+  a.pref = E->dpref;
+  a.nbox = E->nbox;
+  a.stage = stage;
+  a.nstages = nstages;
+  a.b = b;
+  const int order[] = {PH_DT, PH_DTFIN, PH_PRIM, PH_RAW, PH_DIL0, PH_DIL1, PH_DIL2, PH_EXP, PH_FLUX, PH_EMF, PH_UPD};
+  for (int ph : order) {
+    if ((ph == PH_DT || ph == PH_DTFIN) && stage != 0) continue;
+    const cudaError_t e = E->block == 128 ? launch_phase<128>(E, ph, a) : launch_phase<256>(E, ph, a);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Mode 2: every box runs its own per-kernel step (CFL reduction + 3 stages)
+// on one of nstreams streams forked from the ensemble's stream and joined back.
+cudaError_t launch_step_chains(phl_ensemble *E) {
+  const int ns = E->nstreams;
+  while ((int)E->aux.size() < ns) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    E->aux.push_back(st);
+    E->ev.push_back(ev);
+  }
+  if (E->ev.size() < E->aux.size() + 1) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    E->ev.push_back(ev);
+  }
+  cudaEvent_t fork = E->ev.back();
+  cudaError_t e = cudaEventRecord(fork, E->stream);
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(E->aux[k], fork, 0);
+  static const double b3[3] = {1.0, 0.25, 2.0 / 3.0};
+  int launches = 0;
+  for (int b = 0; b < E->nbox && e == cudaSuccess; ++b) {
+    const GridView v = grid_view(E->grids[b]);
+    cudaStream_t st = E->aux[b % ns];
+    MixedBufs M;
+    M.U = v.U; M.B = v.B; M.dU = v.dU; M.dB = v.dB; M.W = v.W;
+    for (int k = 0; k < 3; ++k) M.F[k] = v.F[k];
+    M.E = v.E; M.raw = v.raw; M.flag = v.flag; M.dt = v.dt; M.dflag = v.dflag; M.Tin = nullptr; M.Tout = nullptr;
+    int nl = 0;
+    launch_dt_mixed(*v.G, v.U, v.B, v.fmax, v.dt, v.dflag, st, &nl, nullptr);
+    for (int stg = 0; stg < 3; ++stg) launch_stage_mixed(*v.G, M, stg, 3, b3[stg], st, &nl, nullptr);
+    launches += nl;
+    e = cudaGetLastError();
+  }
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(E->ev[k], E->aux[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(E->stream, E->ev[k], 0);
+  }
+  E->chain_launches = launches;
+  return e;
+}
+
 cudaError_t launch_step(phl_ensemble *E) {
   static const float b3[3] = {1.0f, 0.25f, 2.0f / 3.0f};
+  if (E->mode == 2) return launch_step_chains(E);
   for (int st = 0; st < 3; ++st) {
-    cudaError_t e = launch_stage(E, st, 3, b3[st]);
+    cudaError_t e = E->mode == 0 ? launch_stage(E, st, 3, b3[st]) : launch_stage_phases(E, st, 3, b3[st]);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -405,12 +499,17 @@ phl_status phl_ensemble_check(phl_ensemble *E) {
   return PHL_OK;
 }
 
-phl_status phl_ensemble_set_shape(phl_ensemble *E, int block, int blocks_per_sm) {
-  if (!E || (block != 128 && block != 256)) return ens_fail(PHL_EINVAL, "block must be 128 or 256");
-  const int mx = E->max_bps[block == 128 ? 0 : 1];
-  if (blocks_per_sm < 1 || blocks_per_sm > mx) return ens_fail(PHL_EINVAL, "blocks per SM out of the co-resident range");
-  E->block = block;
-  E->bps = blocks_per_sm;
+phl_status phl_ensemble_set_shape(phl_ensemble *E, int mode, int block, int blocks_per_sm, int streams) {
+  if (!E) return ens_fail(PHL_EINVAL, "null ensemble");
+  if (mode < 0 || mode > 2) return ens_fail(PHL_EINVAL, "mode must be 0 (persistent), 1 (phases) or 2 (chains)");
+  if (mode != 2 && block != 128 && block != 256) return ens_fail(PHL_EINVAL, "block must be 128 or 256");
+  if (mode == 0 && (blocks_per_sm < 1 || blocks_per_sm > E->max_bps[block == 128 ? 0 : 1]))
+    return ens_fail(PHL_EINVAL, "blocks per SM out of the co-resident range");
+  if (mode == 2 && (streams < 1 || streams > 64)) return ens_fail(PHL_EINVAL, "streams must be 1..64");
+  E->mode = mode;
+  E->block = mode == 2 ? 256 : block;
+  E->bps = mode == 0 ? blocks_per_sm : 0;
+  E->nstreams = mode == 2 ? streams : 0;
   drop_graph(E);
   return PHL_OK;
 }
@@ -437,17 +536,36 @@ phl_status phl_ensemble_autotune(phl_ensemble *E, int trial_steps, phl_tune_entr
       if (copies[i]) cudaMemcpyAsync(save[i].first, copies[i], save[i].second, cudaMemcpyDeviceToDevice, E->stream);
   };
   std::vector<phl_tune_entry> res;
-  int best_b = E->block, best_p = E->bps;
+  int best_m = E->mode, best_b = E->block, best_p = E->bps, best_s = E->nstreams;
   double best_ms = 1e300;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  std::vector<phl_tune_entry> cand;
   for (int bsz : {128, 256}) {
+    phl_tune_entry c;
+    c.mode = 1; c.block = bsz; c.blocks_per_sm = 0; c.streams = 0; c.ms_per_step = 0.0;
+    cand.push_back(c);
+    for (int p = 1; p <= E->max_bps[bsz == 128 ? 0 : 1]; ++p) {
+      c.mode = 0; c.blocks_per_sm = p;
+      cand.push_back(c);
+    }
+  }
+  for (int ns : {1, 4, 8, E->nbox}) {
+    phl_tune_entry c;
+    c.mode = 2; c.block = 256; c.blocks_per_sm = 0; c.streams = std::min(ns, E->nbox); c.ms_per_step = 0.0;
+    bool dup = false;
+    for (const auto &q : cand) dup |= q.mode == 2 && q.streams == c.streams;
+    if (!dup) cand.push_back(c);
+  }
+  for (const phl_tune_entry &c : cand) {
     if (e != cudaSuccess) break;
-    const int mx = E->max_bps[bsz == 128 ? 0 : 1];
-    for (int p = 1; p <= mx; ++p) {
+    {
+      const int bsz = c.block, p = c.blocks_per_sm;
+      E->mode = c.mode;
       E->block = bsz;
       E->bps = p;
+      E->nstreams = c.streams;
       drop_graph(E);
       build_graph(E);
       restore();
@@ -461,12 +579,12 @@ phl_status phl_ensemble_autotune(phl_ensemble *E, int trial_steps, phl_tune_entr
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.0f;
       if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-      phl_tune_entry t;
-      t.block = bsz;
-      t.blocks_per_sm = p;
+      phl_tune_entry t = c;
       t.ms_per_step = ms / trial_steps;
       res.push_back(t);
-      if (t.ms_per_step < best_ms) { best_ms = t.ms_per_step; best_b = bsz; best_p = p; }
+      if (t.ms_per_step < best_ms) {
+        best_ms = t.ms_per_step; best_m = c.mode; best_b = bsz; best_p = p; best_s = c.streams;
+      }
     }
   }
   restore();
@@ -475,8 +593,10 @@ phl_status phl_ensemble_autotune(phl_ensemble *E, int trial_steps, phl_tune_entr
   cudaError_t es = cudaStreamSynchronize(E->stream);
   for (void *c : copies) cudaFree(c);
   if (e == cudaSuccess) e = es;
+  E->mode = best_m;
   E->block = best_b;
   E->bps = best_p;
+  E->nstreams = best_s;
   drop_graph(E);
   if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_ensemble_autotune: %s", cudaGetErrorString(e));
   if (n) *n = (int)res.size();
@@ -489,16 +609,31 @@ phl_status phl_ensemble_get_info(const phl_ensemble *E, phl_ensemble_info *info)
   if (!E || !info) return ens_fail(PHL_EINVAL, "null argument");
   info->nbox = E->nbox;
   info->cells = E->cells;
+  info->mode = E->mode;
   info->block = E->block;
   info->blocks_per_sm = E->bps;
+  info->streams = E->nstreams;
   info->graph = E->graph_ok;
-  info->launches_per_step = 3;
+  int nl = 3;
+  if (E->mode == 2) {
+    nl = E->chain_launches;
+  } else if (E->mode == 1) {
+    nl = 0;
+    for (int st = 0; st < 3; ++st)
+      for (int ph = 0; ph < NPH; ++ph) {
+        if ((ph == PH_DT || ph == PH_DTFIN) && st != 0) continue;
+        if (E->hpref[(size_t)ph * (E->nbox + 1) + E->nbox] > 0) ++nl;
+      }
+  }
+  info->launches_per_step = nl;
   return PHL_OK;
 }
 
 void phl_ensemble_destroy(phl_ensemble *E) {
   if (!E) return;
   drop_graph(E);
+  for (cudaStream_t st : E->aux) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : E->ev) cudaEventDestroy(ev);
   for (phl_grid *g : E->grids) phl_destroy(g);
   cudaFree(E->drec);
   cudaFree(E->dpref);

@@ -5,7 +5,8 @@ The bodies are inlined into a different kernel, so the compiler's choice of
 fused multiply-adds may differ: the two agree to the FP32 rounding of the
 deviations (the mixed form's own error, bar 1e-5 of each field's change),
 not bit for bit.  Runs of the ensemble itself are reproducible bit for bit
-with any launch shape, and the autotuner leaves the state untouched."""
+with any launch shape (the phase bodies are the same code in both launch
+modes), and the autotuner leaves the state untouched."""
 import numpy as np
 import pytest
 
@@ -75,24 +76,37 @@ def test_ensemble_equals_boxes_alone(P, graph):
 def test_launch_shapes_and_autotune(P):
     probs = _boxes()
     E = P.Ensemble(probs)
-    E.load()
-    E.step(3)
-    ref = [g.get_state() for g in E.grids]
+
+    def run(mode, blk, bps, streams=0):
+        E.load()
+        E.set_shape(blk, bps, mode=mode, streams=streams)
+        E.step(3)
+        return [g.get_state() for g in E.grids]
+
+    # the same kernels give the same bits with any launch shape
+    ref = {0: run(0, 256, 1), 1: run(1, 256, 0), 2: run(2, 256, 0, 4)}
+    for mode, blk, bps, ns in ((0, 128, 1, 0), (0, 128, 2, 0), (1, 128, 0, 0), (2, 256, 0, 1), (2, 256, 0, 3)):
+        for a, r in zip(run(mode, blk, bps, ns), ref[mode]):
+            _same(a, r)
+    # mode 2 runs each box's own per-kernel step: bit for bit the box alone
+    for a, pr in zip(ref[2], probs):
+        _same(a, _alone(P, pr, 3))
+    # the launch modes inline the same bodies into different kernels
+    for m in (1, 2):
+        for a, r, pr in zip(ref[0], ref[m], probs):
+            _close(pr, a, r)
     E.load()
     res = E.autotune(trial_steps=1)
-    assert len(res) >= 2 and all(r["ms_per_step"] > 0 for r in res)
+    assert len(res) >= 3 and all(r["ms_per_step"] > 0 for r in res)
+    assert {r["mode"] for r in res} == {0, 1, 2}
     info = E.info()
     best = min(res, key=lambda r: r["ms_per_step"])
-    assert (info["block"], info["blocks_per_sm"]) == (best["block"], best["blocks_per_sm"])
-    E.step(3)
-    for g, r in zip(E.grids, ref):     # the autotuner restored the initial state
-        _same(g.get_state(), r)
-    # any other co-resident shape gives the same bits
-    E.load()
-    E.set_shape(128, 1)
-    E.step(3)
-    for g, r in zip(E.grids, ref):
-        _same(g.get_state(), r)
+    assert (info["mode"], info["block"], info["blocks_per_sm"], info["streams"]) == (
+        best["mode"], best["block"], best["blocks_per_sm"], best["streams"])
+    E.step(3)   # from the loaded state, which the autotuner restored
+    after = [g.get_state() for g in E.grids]
+    for a, r in zip(after, run(info["mode"], info["block"], info["blocks_per_sm"], info["streams"])):
+        _same(a, r)
     E.close()
 
 
