@@ -105,19 +105,16 @@ __device__ __forceinline__ void star_diff(const Side<R> &s, R S, R SM, R dpts, R
   rhos = s.rho * su * iq;
   const R den = s.rho * su * q - bn * bn;
   const R scale = s.rho * su * su + bn * bn;
-  R dbf;                            // (B*_t - B_t) / B_t
-  if (fabs(den) < R(1e-12) * scale) {
-    vs1 = s.ut1; vs2 = s.ut2; bs1 = s.bt1; bs2 = s.bt2;
-    dbf = R(0);
-  } else {
-    const R iden = R(1) / den;
-    const R fv = bn * smu * iden;
-    dbf = s.rho * su * smu * iden;
-    vs1 = s.ut1 - s.bt1 * fv;
-    vs2 = s.ut2 - s.bt2 * fv;
-    bs1 = s.bt1 + s.bt1 * dbf;
-    bs2 = s.bt2 + s.bt2 * dbf;
-  }
+  // degenerate case (den ~ 0): the transverse values stay those of the side;
+  // selected rather than branched so that a warp's faces take one path
+  const bool deg = fabs(den) < R(1e-12) * scale;
+  const R iden = R(1) / den;
+  const R fv = deg ? R(0) : bn * smu * iden;
+  const R dbf = deg ? R(0) : s.rho * su * smu * iden;   // (B*_t - B_t) / B_t
+  vs1 = s.ut1 - s.bt1 * fv;
+  vs2 = s.ut2 - s.bt2 * fv;
+  bs1 = s.bt1 + s.bt1 * dbf;
+  bs2 = s.bt2 + s.bt2 * dbf;
   const R vbs = SM * bn + vs1 * bs1 + vs2 * bs2;
   dU[RF_RHO] = s.rho * smu * iq;                         // rho* - rho
   dU[RF_MN] = rhos * SM - s.rho * s.un;
@@ -206,59 +203,50 @@ __device__ __forceinline__ void riemann_dev(const R *wl, const R *wr, R bn, R rh
   const R pdis = L.rho * R_.rho * sR * sL * (R_.un - L.un) * iD;
   const R dpts = (sR * R_.rho * L.dpt - sL * L.rho * R_.dpt) * iD + pdis;   // p_T* - P_hat
 
+  // Region of the face (Eq. flux-hlld): outside the fan (S_L >= 0 or S_R < 0),
+  // single-star (S*_L >= 0 or S*_R < 0) or double-star.  The flux is always
+  // F_X + [fan] S_X (U*_X - U_X) + [double star] S*_X (U**_X - U*_X) with X the
+  // side the region belongs to; every region's terms are computed and the
+  // face's are selected, so the faces of a warp follow one instruction path.
+  R dUL[7], dUR[7], rhosL, rhosR, vL1, vL2, bL1, bL2, vR1, vR2, bR1, bR2;
+  star_diff(L, SL, SM, dpts, bn, dUL, rhosL, vL1, vL2, bL1, bL2);
+  star_diff(R_, SR, SM, dpts, bn, dUR, rhosR, vR1, vR2, bR1, bR2);
+  const R sqL = rsqrt_t(rhosL), sqR = rsqrt_t(rhosR);
+  const R abn = fabs(bn);
+  const R SsL = SM - abn / sqL, SsR = SM + abn / sqR;
+  const bool outL = SL >= R(0), outR = !outL && SR < R(0), fan = !outL && !outR;
+  const bool starL = SsL >= R(0), starR = !starL && SsR < R(0), dbl = fan && !starL && !starR;
+  const bool left = outL || (fan && (starL || (!starR && SM >= R(0))));
+  const R sgn = bn >= R(0) ? R(1) : R(-1);
+  const R isum = R(1) / (sqL + sqR);
+  const R vss1 = (sqL * vL1 + sqR * vR1 + (bR1 - bL1) * sgn) * isum;
+  const R vss2 = (sqL * vL2 + sqR * vR2 + (bR2 - bL2) * sgn) * isum;
+  const R bss1 = (sqL * bR1 + sqR * bL1 + sqL * sqR * (vR1 - vL1) * sgn) * isum;
+  const R bss2 = (sqL * bR2 + sqR * bL2 + sqL * sqR * (vR2 - vL2) * sgn) * isum;
+  const R vbss = SM * bn + vss1 * bss1 + vss2 * bss2;
+  // the chosen side's quantities
+  const R S = left ? SL : SR, Ss = left ? SsL : SsR, rhos = left ? rhosL : rhosR;
+  const R sqs = left ? -sqL : sqR;
+  const R v1 = left ? vL1 : vR1, v2 = left ? vL2 : vR2, b1 = left ? bL1 : bR1, b2 = left ? bL2 : bR2;
+  const R vbs = SM * bn + v1 * b1 + v2 * b2;
+  R d2[7];
+  d2[RF_RHO] = R(0); d2[RF_MN] = R(0);
+  d2[RF_MT1] = rhos * (vss1 - v1); d2[RF_MT2] = rhos * (vss2 - v2);
+  d2[RF_E] = sqs * (vbs - vbss) * sgn;
+  d2[RF_BT1] = bss1 - b1; d2[RF_BT2] = bss2 - b2;
   R F[7];
-  bool left;
-  if (SL >= R(0)) {
-    for (int q = 0; q < 7; ++q) F[q] = L.F[q];
-    left = true;
-  } else if (SR < R(0)) {
-    for (int q = 0; q < 7; ++q) F[q] = R_.F[q];
-    left = false;
-  } else {
-    R dUL[7], dUR[7], rhosL, rhosR, vL1, vL2, bL1, bL2, vR1, vR2, bR1, bR2;
-    star_diff(L, SL, SM, dpts, bn, dUL, rhosL, vL1, vL2, bL1, bL2);
-    star_diff(R_, SR, SM, dpts, bn, dUR, rhosR, vR1, vR2, bR1, bR2);
-    const R sqL = rsqrt_t(rhosL), sqR = rsqrt_t(rhosR);
-    const R abn = fabs(bn);
-    const R SsL = SM - abn / sqL, SsR = SM + abn / sqR;
-    if (SsL >= R(0)) {
-      for (int q = 0; q < 7; ++q) F[q] = L.F[q] + SL * dUL[q];
-      left = true;
-    } else if (SsR < R(0)) {
-      for (int q = 0; q < 7; ++q) F[q] = R_.F[q] + SR * dUR[q];
-      left = false;
-    } else {
-      const R sgn = bn >= R(0) ? R(1) : R(-1);
-      const R isum = R(1) / (sqL + sqR);
-      const R vss1 = (sqL * vL1 + sqR * vR1 + (bR1 - bL1) * sgn) * isum;
-      const R vss2 = (sqL * vL2 + sqR * vR2 + (bR2 - bL2) * sgn) * isum;
-      const R bss1 = (sqL * bR1 + sqR * bL1 + sqL * sqR * (vR1 - vL1) * sgn) * isum;
-      const R bss2 = (sqL * bR2 + sqR * bL2 + sqL * sqR * (vR2 - vL2) * sgn) * isum;
-      const R vbss = SM * bn + vss1 * bss1 + vss2 * bss2;
-      if (SM >= R(0)) {
-        const R vbs = SM * bn + vL1 * bL1 + vL2 * bL2;
-        R d2[7];
-        d2[RF_RHO] = R(0); d2[RF_MN] = R(0);
-        d2[RF_MT1] = rhosL * (vss1 - vL1); d2[RF_MT2] = rhosL * (vss2 - vL2);
-        d2[RF_E] = -sqL * (vbs - vbss) * sgn;
-        d2[RF_BT1] = bss1 - bL1; d2[RF_BT2] = bss2 - bL2;
-        for (int q = 0; q < 7; ++q) F[q] = L.F[q] + SL * dUL[q] + SsL * d2[q];
-        left = true;
-      } else {
-        const R vbs = SM * bn + vR1 * bR1 + vR2 * bR2;
-        R d2[7];
-        d2[RF_RHO] = R(0); d2[RF_MN] = R(0);
-        d2[RF_MT1] = rhosR * (vss1 - vR1); d2[RF_MT2] = rhosR * (vss2 - vR2);
-        d2[RF_E] = sqR * (vbs - vbss) * sgn;
-        d2[RF_BT1] = bss1 - bR1; d2[RF_BT2] = bss2 - bR2;
-        for (int q = 0; q < 7; ++q) F[q] = R_.F[q] + SR * dUR[q] + SsR * d2[q];
-        left = false;
-      }
-    }
-    if (xi != R(1) && SR > R(0)) {
-      F[RF_MN] += (xi - R(1)) * pdis;
-      F[RF_E] += (xi - R(1)) * pdis * SM;
-    }
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const R fx = left ? L.F[q] : R_.F[q];
+    const R dux = left ? dUL[q] : dUR[q];
+    const R t1 = fan ? S * dux : R(0);
+    const R t2 = dbl ? Ss * d2[q] : R(0);
+    F[q] = fx + t1 + t2;
+  }
+  // LHLLD: inside the fan the dissipative part of p_T* is scaled by xi
+  if (fan && xi != R(1) && SR > R(0)) {
+    F[RF_MN] += (xi - R(1)) * pdis;
+    F[RF_E] += (xi - R(1)) * pdis * SM;
   }
   for (int q = 0; q < 7; ++q) f[q] = F[q];
 #pragma unroll

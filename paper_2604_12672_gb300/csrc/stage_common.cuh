@@ -272,7 +272,7 @@ __device__ __forceinline__ void k_flux_at(long tl, const DevGeo &G, const Box &b
   }
 }
 template <int D, typename R, int NS>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_flux(DevGeo G, Box box, const R *__restrict__ W, const double *__restrict__ Bf,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_flux(DevGeo G, Box box, const R *__restrict__ W, const double *__restrict__ Bf,
                        const R *__restrict__ dB, const uint8_t *__restrict__ flag, R *__restrict__ F, int *dflag) {
   k_flux_at<D, R, NS>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, W, Bf, dB, flag, F, dflag);
 }
