@@ -47,42 +47,58 @@ struct Side {
   R dpt;    // p_T - P_hat
   R enth;   // E + p_T (full)
   R de;     // E - E_hat
-  R cf, cs;
+  R cf;
+  R m2;     // |u|^2 / c_s^2
   R vb;     // u . B
   R F[7];   // physical flux minus background flux
 };
 
+// Ideal-gas constants of the flux (gamma, 1/(gamma-1), gamma/(gamma-1)); with
+// IDEAL the indices are these constants instead of reconstructed values.
 template <typename R>
-__device__ __forceinline__ void side_init(Side<R> &s, const R *w, R bn, R rh, R ph, R geh, R gch) {
+struct GasK { R g, igm1, ggm1; };
+
+template <typename R, bool IDEAL>
+__device__ __forceinline__ void side_init(Side<R> &s, const R *w, R bn, R rh, R ph, R geh, R gch, const GasK<R> &K) {
   s.rho = rh + w[RD_RHO];
   s.un = w[RD_UN]; s.ut1 = w[RD_UT1]; s.ut2 = w[RD_UT2];
   s.bt1 = w[RD_BT1]; s.bt2 = w[RD_BT2];
   const R dp = w[RD_P];
   s.p = ph + dp;
-  s.ge = geh + w[RD_GE];
-  const R gc = gch + w[RD_GC];
+  const R irho = R(1) / s.rho;
   const R b2 = bn * bn + s.bt1 * s.bt1 + s.bt2 * s.bt2;
   const R u2 = s.un * s.un + s.ut1 * s.ut1 + s.ut2 * s.ut2;
   const R half = R(0.5);
   s.dpt = dp + half * b2;
-  const R gem1 = s.ge - R(1);
-  // internal energy density P / (gamma_e - 1) relative to P_hat / (gamma_hat_e - 1)
-  R deint;
-  if (ph == R(0)) {
-    deint = s.p / gem1;
-  } else {
-    const R gehm1 = geh - R(1);
-    deint = (dp * gehm1 - ph * w[RD_GE]) / (gem1 * gehm1);
-  }
   const R kin = half * s.rho * u2;
-  s.de = deint + kin + half * b2;
-  s.enth = s.ge / gem1 * s.p + kin + b2;
-  const R a2 = gc * s.p / s.rho;
-  const R bb = b2 / s.rho, bnn = bn * bn / s.rho;
+  R gc;
+  if (IDEAL) {
+    // P / (gamma - 1) relative to P_hat / (gamma - 1)
+    s.ge = K.g;
+    gc = K.g;
+    s.de = dp * K.igm1 + kin + half * b2;
+    s.enth = K.ggm1 * s.p + kin + b2;
+  } else {
+    s.ge = geh + w[RD_GE];
+    gc = gch + w[RD_GC];
+    const R gem1 = s.ge - R(1);
+    // internal energy density P / (gamma_e - 1) relative to P_hat / (gamma_hat_e - 1)
+    R deint;
+    if (ph == R(0)) {
+      deint = s.p / gem1;
+    } else {
+      const R gehm1 = geh - R(1);
+      deint = (dp * gehm1 - ph * w[RD_GE]) / (gem1 * gehm1);
+    }
+    s.de = deint + kin + half * b2;
+    s.enth = s.ge / gem1 * s.p + kin + b2;
+  }
+  const R a2 = gc * s.p * irho;
+  const R bb = b2 * irho, bnn = bn * bn * irho;
   R disc = (a2 + bb) * (a2 + bb) - R(4) * a2 * bnn;
   if (disc < R(0)) disc = R(0);
   s.cf = rsqrt_t(half * (a2 + bb + rsqrt_t(disc)));
-  s.cs = rsqrt_t(a2);
+  s.m2 = u2 / a2;
   s.vb = s.un * bn + s.ut1 * s.bt1 + s.ut2 * s.bt2;
   s.F[RF_RHO] = s.rho * s.un;
   s.F[RF_MN] = s.rho * s.un * s.un + s.dpt - bn * bn;
@@ -138,12 +154,12 @@ __device__ __forceinline__ int contact_dir(R frho, R rhol, R rhor, R SL, R SR) {
 // Background at the face: rh, ph, geh, gch (all 0 without a background).
 // f: F - F_hat in RF_* order (7 + nspec values).
 // NS: compile-time capacity for mass fractions (loops unroll; nspec <= NS).
-template <typename R, int NS>
+template <typename R, int NS, bool IDEAL = false>
 __device__ __forceinline__ void riemann_dev(const R *wl, const R *wr, R bn, R rh, R ph, R geh, R gch, int nspec,
-                                            int solver, R mthr, R *f, int &up) {
+                                            int solver, R mthr, R *f, int &up, const GasK<R> &K = GasK<R>{}) {
   Side<R> L, R_;
-  side_init(L, wl, bn, rh, ph, geh, gch);
-  side_init(R_, wr, bn, rh, ph, geh, gch);
+  side_init<R, IDEAL>(L, wl, bn, rh, ph, geh, gch, K);
+  side_init<R, IDEAL>(R_, wr, bn, rh, ph, geh, gch, K);
   const R SL = fmin(L.un - L.cf, R_.un - R_.cf);
   const R SR = fmax(L.un + L.cf, R_.un + R_.cf);
   R xl[NS > 0 ? NS : 1], xr[NS > 0 ? NS : 1];
@@ -190,11 +206,9 @@ __device__ __forceinline__ void riemann_dev(const R *wl, const R *wr, R bn, R rh
   }
 
   R xi = R(1);
-  if (solver == SOLVER_LHLLD) {
-    const R ml = rsqrt_t(L.un * L.un + L.ut1 * L.ut1 + L.ut2 * L.ut2) / L.cs;
-    const R mr = rsqrt_t(R_.un * R_.un + R_.ut1 * R_.ut1 + R_.ut2 * R_.ut2) / R_.cs;
-    const R m = ml > mr ? ml : mr;
-    xi = m < mthr ? m : R(1);
+  if (solver == SOLVER_LHLLD) {   // xi = max(M_L, M_R) below the threshold, M = |u| / c_s
+    const R m2 = L.m2 > R_.m2 ? L.m2 : R_.m2;
+    xi = m2 < mthr * mthr ? rsqrt_t(m2) : R(1);
   }
   const R sR = SR - R_.un, sL = SL - L.un;
   const R D = sR * R_.rho - sL * L.rho;

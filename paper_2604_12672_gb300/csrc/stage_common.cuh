@@ -188,89 +188,110 @@ inline int launch_flags(const DevGeo &G, uint8_t *raw, uint8_t *tmp, uint8_t *fl
   return nl + 1;
 }
 
-template <int D, typename R, int NS>
-__device__ __forceinline__ void k_flux_at(long tl, const DevGeo &G, const Box &box, const R *__restrict__ W, const double *__restrict__ Bf,
-                       const R *__restrict__ dB, const uint8_t *__restrict__ flag, R *__restrict__ F, int *dflag) {
+// Flux at the D-face of work cell c (index pR, left neighbour pR - sd).
+// fetch(v, k) returns component v of W at stencil cell k = 0..3 (pL - sd, pL,
+// pR, pR + sd).  Stores F - F_hat and the contact direction.
+template <int D, typename R, int NS, typename Fetch>
+__device__ __forceinline__ void flux_face(const DevGeo &G, const int *c, long pR, Fetch fetch,
+                                          const double *__restrict__ Bf, const R *__restrict__ dB,
+                                          const uint8_t *__restrict__ flag, R *__restrict__ F, int *dflag) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-  {
-    int c[3];
-    if (!cell_at(box, tl, c)) return;
-    const long sd = wstride(G, D);
-    const long pR = widx(G, c[0], c[1], c[2]), pL = pR - sd;
-    constexpr int NWC = W_X0 + NS;   // components this instantiation can hold
-    R wl[NWC], wr[NWC];
-    const bool ideal = G.eos == 0;   // ideal gas: gamma_e = gamma_c = gamma (not reconstructed)
-    R ql[NWC], qr[NWC];
+  const long sd = wstride(G, D);
+  const long pL = pR - sd;
+  constexpr int NWC = W_X0 + NS;   // components this instantiation can hold
+  R wl[NWC], wr[NWC];
+  const bool ideal = G.eos == 0;   // ideal gas: gamma_e = gamma_c = gamma (not reconstructed)
+  R ql[NWC], qr[NWC];
 #pragma unroll
-    for (int v = 0; v < NWC; ++v) {
-      if (v >= G.nw || (ideal && (v == W_GE || v == W_GC))) continue;
-      const R *a = W + v * G.wtot;
-      const R w0 = a[pL - sd], w1 = a[pL], w2 = a[pR], w3 = a[pR + sd];
-      ql[v] = w1 + R(0.5) * vl_slope(w0, w1, w2);
-      qr[v] = w2 - R(0.5) * vl_slope(w1, w2, w3);
-    }
-    if (ideal) {
-      ql[W_GE] = qr[W_GE] = W[W_GE * G.wtot + pR];
-      ql[W_GC] = qr[W_GC] = W[W_GC * G.wtot + pR];
-    }
-    wl[RD_RHO] = ql[W_RHO];        wr[RD_RHO] = qr[W_RHO];
-    wl[RD_UN] = ql[W_VX + D];      wr[RD_UN] = qr[W_VX + D];
-    wl[RD_UT1] = ql[W_VX + T1];    wr[RD_UT1] = qr[W_VX + T1];
-    wl[RD_UT2] = ql[W_VX + T2];    wr[RD_UT2] = qr[W_VX + T2];
-    wl[RD_BT1] = ql[W_BX + T1];    wr[RD_BT1] = qr[W_BX + T1];
-    wl[RD_BT2] = ql[W_BX + T2];    wr[RD_BT2] = qr[W_BX + T2];
-    wl[RD_P] = ql[W_P];            wr[RD_P] = qr[W_P];
-    wl[RD_GE] = ql[W_GE];          wr[RD_GE] = qr[W_GE];
-    wl[RD_GC] = ql[W_GC];          wr[RD_GC] = qr[W_GC];
-#pragma unroll
-    for (int l = 0; l < NS; ++l)
-      if (l < G.nspec) { wl[RD_X0 + l] = ql[W_X0 + l]; wr[RD_X0 + l] = qr[W_X0 + l]; }
-    const BgT<R> bf = (D == 2) ? bg_zface_t<R>(G, c[2]) : bg_cell_t<R>(G, c[2]);
-    if (!(bf.rho + wl[RD_RHO] > R(0) && bf.rho + wr[RD_RHO] > R(0) && bf.p + wl[RD_P] > R(0) &&
-          bf.p + wr[RD_P] > R(0)))
-      atomicOr(dflag, FLAG_NEG);
-    // normal field on this face; transverse ghost rows map to their source rows
-    int s[3];
-    s[D] = c[D];
-    {
-      bool fl;
-      s[T1] = G.act[T1] ? cell_src(c[T1], G.n[T1], G.bc[T1][0], G.bc[T1][1], fl) : 0;
-      s[T2] = G.act[T2] ? cell_src(c[T2], G.n[T2], G.bc[T2][0], G.bc[T2][1], fl) : 0;
-    }
-    const long qb = (long)D * G.plane + sidx(G, s[0], s[1], s[2]);
-    R bn;
-    if constexpr (sizeof(R) == 4) {   // B^n + dB in scaled units
-      const float b0 = d2f_bits(Bf[qb] * G.isc_b);
-      bn = dB ? b0 + dB[qb] : b0;
-    }
-    else bn = (R)Bf[qb];
-    const int solver = (flag[pL] | flag[pR]) ? SOLVER_HLL : G.riemann;
-    R f[7 + NS];
-    int up;
-    riemann_dev<R, NS>(wl, wr, bn, bf.rho, bf.p, bf.ge, bf.gc, G.nspec, solver, mach_thr_t<R>(G), f, up);
-    // reflecting wall face: a symmetry plane (Table bcs, u_n = 0, B_n = 0); only
-    // the normal-momentum flux survives, the others are exactly zero
-    if ((c[D] == 0 && G.bc[D][0] == 1) || (c[D] == G.n[D] && G.bc[D][1] == 1)) {
-#pragma unroll
-      for (int q = 0; q < 7 + NS; ++q)
-        if (q != RF_MN) f[q] = R(0);
-      up = 0;
-    }
-    const long wt = G.wtot;
-    F[F_RHO * wt + pR] = f[RF_RHO];
-    F[(F_MX + D) * wt + pR] = f[RF_MN];
-    F[(F_MX + T1) * wt + pR] = f[RF_MT1];
-    F[(F_MX + T2) * wt + pR] = f[RF_MT2];
-    F[F_E * wt + pR] = f[RF_E];
-    F[(F_BX + D) * wt + pR] = R(0);
-    F[(F_BX + T1) * wt + pR] = f[RF_BT1];
-    F[(F_BX + T2) * wt + pR] = f[RF_BT2];
-#pragma unroll
-    for (int l = 0; l < NS; ++l)
-      if (l < G.nspec) F[(F_X0 + l) * wt + pR] = f[RF_X0 + l];
-    F[(long)G.nf * wt + pR] = (R)up;   // contact direction for Contact-CT
+  for (int v = 0; v < NWC; ++v) {
+    if (v >= G.nw || (ideal && (v == W_GE || v == W_GC))) continue;
+    const R w0 = fetch(v, 0), w1 = fetch(v, 1), w2 = fetch(v, 2), w3 = fetch(v, 3);
+    ql[v] = w1 + R(0.5) * vl_slope(w0, w1, w2);
+    qr[v] = w2 - R(0.5) * vl_slope(w1, w2, w3);
   }
+  if (ideal) {
+    ql[W_GE] = qr[W_GE] = fetch(W_GE, 2);
+    ql[W_GC] = qr[W_GC] = fetch(W_GC, 2);
+  }
+  wl[RD_RHO] = ql[W_RHO];        wr[RD_RHO] = qr[W_RHO];
+  wl[RD_UN] = ql[W_VX + D];      wr[RD_UN] = qr[W_VX + D];
+  wl[RD_UT1] = ql[W_VX + T1];    wr[RD_UT1] = qr[W_VX + T1];
+  wl[RD_UT2] = ql[W_VX + T2];    wr[RD_UT2] = qr[W_VX + T2];
+  wl[RD_BT1] = ql[W_BX + T1];    wr[RD_BT1] = qr[W_BX + T1];
+  wl[RD_BT2] = ql[W_BX + T2];    wr[RD_BT2] = qr[W_BX + T2];
+  wl[RD_P] = ql[W_P];            wr[RD_P] = qr[W_P];
+  wl[RD_GE] = ql[W_GE];          wr[RD_GE] = qr[W_GE];
+  wl[RD_GC] = ql[W_GC];          wr[RD_GC] = qr[W_GC];
+#pragma unroll
+  for (int l = 0; l < NS; ++l)
+    if (l < G.nspec) { wl[RD_X0 + l] = ql[W_X0 + l]; wr[RD_X0 + l] = qr[W_X0 + l]; }
+  const BgT<R> bf = (D == 2) ? bg_zface_t<R>(G, c[2]) : bg_cell_t<R>(G, c[2]);
+  if (!(bf.rho + wl[RD_RHO] > R(0) && bf.rho + wr[RD_RHO] > R(0) && bf.p + wl[RD_P] > R(0) &&
+        bf.p + wr[RD_P] > R(0)))
+    atomicOr(dflag, FLAG_NEG);
+  // normal field on this face; transverse ghost rows map to their source rows
+  int s[3];
+  s[D] = c[D];
+  {
+    bool fl;
+    s[T1] = G.act[T1] ? cell_src(c[T1], G.n[T1], G.bc[T1][0], G.bc[T1][1], fl) : 0;
+    s[T2] = G.act[T2] ? cell_src(c[T2], G.n[T2], G.bc[T2][0], G.bc[T2][1], fl) : 0;
+  }
+  const long qb = (long)D * G.plane + sidx(G, s[0], s[1], s[2]);
+  R bn;
+  if constexpr (sizeof(R) == 4) {   // B^n + dB in scaled units
+    const float b0 = d2f_bits(Bf[qb] * G.isc_b);
+    bn = dB ? b0 + dB[qb] : b0;
+  }
+  else bn = (R)Bf[qb];
+  const int solver = (flag[pL] | flag[pR]) ? SOLVER_HLL : G.riemann;
+  R f[7 + NS];
+  int up;
+  if (G.eos == 0) {   // ideal gas: gamma constant
+    GasK<R> K;
+    K.g = sizeof(R) == 4 ? (R)G.gammaf : (R)G.gamma;
+    K.igm1 = R(1) / (K.g - R(1));
+    K.ggm1 = K.g * K.igm1;
+    riemann_dev<R, NS, true>(wl, wr, bn, bf.rho, bf.p, bf.ge, bf.gc, G.nspec, solver, mach_thr_t<R>(G), f, up, K);
+  } else {
+    riemann_dev<R, NS, false>(wl, wr, bn, bf.rho, bf.p, bf.ge, bf.gc, G.nspec, solver, mach_thr_t<R>(G), f, up);
+  }
+  // reflecting wall face: a symmetry plane (Table bcs, u_n = 0, B_n = 0); only
+  // the normal-momentum flux survives, the others are exactly zero
+  if ((c[D] == 0 && G.bc[D][0] == 1) || (c[D] == G.n[D] && G.bc[D][1] == 1)) {
+#pragma unroll
+    for (int q = 0; q < 7 + NS; ++q)
+      if (q != RF_MN) f[q] = R(0);
+    up = 0;
+  }
+  const long wt = G.wtot;
+  F[F_RHO * wt + pR] = f[RF_RHO];
+  F[(F_MX + D) * wt + pR] = f[RF_MN];
+  F[(F_MX + T1) * wt + pR] = f[RF_MT1];
+  F[(F_MX + T2) * wt + pR] = f[RF_MT2];
+  F[F_E * wt + pR] = f[RF_E];
+  F[(F_BX + D) * wt + pR] = R(0);
+  F[(F_BX + T1) * wt + pR] = f[RF_BT1];
+  F[(F_BX + T2) * wt + pR] = f[RF_BT2];
+#pragma unroll
+  for (int l = 0; l < NS; ++l)
+    if (l < G.nspec) F[(F_X0 + l) * wt + pR] = f[RF_X0 + l];
+  F[(long)G.nf * wt + pR] = (R)up;   // contact direction for Contact-CT
 }
+
+template <int D, typename R, int NS>
+__device__ __forceinline__ void k_flux_at(long tl, const DevGeo &G, const Box &box, const R *__restrict__ W,
+                                          const double *__restrict__ Bf, const R *__restrict__ dB,
+                                          const uint8_t *__restrict__ flag, R *__restrict__ F, int *dflag) {
+  int c[3];
+  if (!cell_at(box, tl, c)) return;
+  const long sd = wstride(G, D);
+  const long pR = widx(G, c[0], c[1], c[2]);
+  const long base = pR - 2 * sd;
+  auto fetch = [&](int v, int k) -> R { return W[v * G.wtot + base + k * sd]; };
+  flux_face<D, R, NS>(G, c, pR, fetch, Bf, dB, flag, F, dflag);
+}
+
 template <int D, typename R, int NS>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_flux(DevGeo G, Box box, const R *__restrict__ W, const double *__restrict__ Bf,
                        const R *__restrict__ dB, const uint8_t *__restrict__ flag, R *__restrict__ F, int *dflag) {
