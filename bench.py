@@ -139,13 +139,22 @@ def barrier(ws):
 
 
 def allreduce_max(x, ws):
+    """Maximum of x over the ranks (the slowest rank's time)."""
     if ws <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms_local, ws):
+    """Whole-job throughput: every rank's units over the slowest rank's time
+    (independent replicas, weak scaling).  Returns (rate, ms_max)."""
+    ms_max = allreduce_max(ms_local, ws)
+    return units_per_rank * ws / (ms_max * 1e-3), ms_max
 
 
 def make_problem(n):
@@ -483,8 +492,7 @@ def main():
         g, ms, kt, st = time_form(P, pr, form, args.steps, args.warmup, stream, ws)
         if clocks is not None:
             clk = clocks.stop()
-        ms_max = allreduce_max(ms, ws)
-        value = pr.ncells * STAGES * args.steps * ws / (ms_max * 1e-3)
+        value, ms_max = whole_job_rate(pr.ncells * STAGES * args.steps, ms, ws)
         res[form] = dict(g=g, ms=ms_max, kt=kt, value=value)
         if form != head:
             g.close()
