@@ -112,15 +112,21 @@ __global__ void k_eos_cells(DevGeo G, Box box, const double *__restrict__ U, con
   const bool f32 = sizeof(R) == 4;
   const double sr = f32 ? G.isc_rho : 1.0, sv = f32 ? G.isc_v : 1.0, sb = f32 ? G.isc_b : 1.0,
                sp = f32 ? G.isc_e : 1.0;
-  W[W_RHO * wt + q] = (R)((rho - b.rho) * sr);
-  W[W_VX * wt + q] = (R)(vx * sv); W[W_VY * wt + q] = (R)(vy * sv); W[W_VZ * wt + q] = (R)(vz * sv);
-  W[W_BX * wt + q] = (R)(bx * sb); W[W_BY * wt + q] = (R)(by * sb); W[W_BZ * wt + q] = (R)(bz * sb);
-  W[W_P * wt + q] = (R)((o.P - b.p) * sp);
-  W[W_GE * wt + q] = (R)(o.ge - b.ge);
-  W[W_GC * wt + q] = (R)(o.gc - b.gc);
+  W[wix<R>(G, W_RHO, q)] = (R)((rho - b.rho) * sr);
+  W[wix<R>(G, W_VX, q)] = (R)(vx * sv); W[wix<R>(G, W_VY, q)] = (R)(vy * sv); W[wix<R>(G, W_VZ, q)] = (R)(vz * sv);
+  W[wix<R>(G, W_BX, q)] = (R)(bx * sb); W[wix<R>(G, W_BY, q)] = (R)(by * sb); W[wix<R>(G, W_BZ, q)] = (R)(bz * sb);
+  W[wix<R>(G, W_P, q)] = (R)((o.P - b.p) * sp);
+  W[wix<R>(G, W_GE, q)] = (R)(o.ge - b.ge);
+  W[wix<R>(G, W_GC, q)] = (R)(o.gc - b.gc);
 #pragma unroll
   for (int l = 0; l < PHL_NSPEC_MAX; ++l)
-    if (l < G.nspec) W[(W_X0 + l) * wt + q] = (R)X[l];
+    if (l < G.nspec) W[wix<R>(G, W_X0 + l, q)] = (R)X[l];
+  if constexpr (sizeof(R) == 4) {
+    float w[W_P + 1];
+#pragma unroll
+    for (int v = 0; v <= W_P; ++v) w[v] = W[wix<float>(G, v, q)];
+    write_aux(G, W, q, w);
+  }
 }
 
 // Cells of the work layout outside the interior take the deviations of the
@@ -142,9 +148,15 @@ __global__ void k_ghost_fill(DevGeo G, Box box, R *__restrict__ W) {
 #pragma unroll
   for (int v = 0; v < NW_MAX; ++v) {
     if (v >= G.nw) continue;
-    R x = W[v * wt + qs];
+    R x = W[wix<R>(G, v, qs)];
     const bool flip = (v >= W_VX && v <= W_VZ && fl[v - W_VX]) || (v >= W_BX && v <= W_BZ && fl[v - W_BX]);
-    W[v * wt + qd] = flip ? -x : x;
+    W[wix<R>(G, v, qd)] = flip ? -x : x;
+  }
+  if constexpr (sizeof(R) == 4) {   // the ghost's auxiliaries from its (flipped) values
+    float w[W_P + 1];
+#pragma unroll
+    for (int v = 0; v <= W_P; ++v) w[v] = W[wix<float>(G, v, qd)];
+    write_aux(G, W, qd, w);
   }
 }
 

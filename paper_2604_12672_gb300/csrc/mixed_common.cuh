@@ -87,7 +87,8 @@ __device__ __forceinline__ void k_prim_mx_at(long tl, const DevGeo &G, const Box
     const long q = widx(G, c[0], c[1], c[2]);
 #pragma unroll
     for (int v = 0; v < NW_MAX; ++v)
-      if (v < G.nw) W[v * G.wtot + q] = w[v];
+      if (v < G.nw && v < G.wstr) W[wix<float>(G, v, q)] = w[v];
+    write_aux(G, W, q, w);
   }
 }
 
@@ -122,13 +123,13 @@ __device__ __forceinline__ void k_update_cells_mx_at(long tl, const DevGeo &G, c
       r[v] = s;
     }
     // sources S - S_hat: (rho - rho_hat) g on momentum, rho u . g (+ heating) on energy
-    const float drho = S.W[W_RHO * wt + p];
+    const float drho = S.W[wix<float>(G, W_RHO, p)];
     const float rho = bg_cell_t<float>(G, c[2]).rho + drho;
     float se = 0.0f;
     for (int d = 0; d < 3; ++d) {
       const float gd = G.gf[d];
       r[U_MX + d] -= drho * gd;
-      se += rho * S.W[(W_VX + d) * wt + p] * gd;
+      se += rho * S.W[wix<float>(G, W_VX + d, p)] * gd;
     }
     if (G.heatf) se += G.heatf[c[2]];
     r[U_E] -= se;

@@ -234,6 +234,10 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   G.wy = d->n[0] + 2L * G.ge[0] + 1;
   G.wz = G.wy * (d->n[1] + 2L * G.ge[1] + 1);
   G.wtot = G.wz * (d->n[2] + 2L * G.ge[2] + 1);
+  // FP32 W interleaving: 8 values per cell for an ideal gas without species
+  // (rho, u, B, P deviations), else the padded component count (gamma_e,
+  // gamma_c, mass fractions)
+  G.wstr = (d->eos == PHL_EOS_IDEAL && d->nspec == 0) ? 8 : (d->nspec == 0 ? 12 : 16);
   G.nspec = d->nspec;
   G.nv = 5 + d->nspec;
   G.nw = 10 + d->nspec;
@@ -302,7 +306,7 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   } else {
     AL(&g->dUf, G.nv * G.plane);
     AL(&g->dBf, 3 * G.plane);
-    AL(&g->Wf, (long)G.nw * G.wtot);
+    AL(&g->Wf, (long)(G.wstr + NAUX) * G.wtot);   // interleaved W + auxiliary planes
     for (int k = 0; k < 3; ++k)
       if (G.act[k]) AL(&g->Ff[k], (long)(G.nf + 1) * G.wtot);
     AL(&g->Ef, 3 * G.wtot);

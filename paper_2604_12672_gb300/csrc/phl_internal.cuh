@@ -45,6 +45,7 @@ struct DevGeo {
   long sy, sz, plane;          // state strides / size per field
   int ge[3];
   long wy, wz, wtot;           // work strides / size per field
+  int wstr;                    // FP32 W: values per cell (components interleaved)
   double dx[3], idx[3];
   int nspec, nv, nw, nf;
   int eos;
@@ -279,6 +280,32 @@ void launch_prim_to_cons(const DevGeo &G, const double *prim, double *U, const d
                          cudaStream_t s);
 const eos::Table *eos_table_view(const struct phl_eos_table *t);
 mlp::Dev mlp_view(const struct phl_mlp *m);
+
+// Index of component v of work cell q in W.  FP64 path: one plane of wtot
+// values per component.  FP32 path: the components of a cell are contiguous
+// (wstr floats, a multiple of 4), so one cell's deviations are two to four
+// 16-byte loads and a face's stencil touches 4 cells instead of 4 x nw lines.
+template <typename R>
+__host__ __device__ __forceinline__ long wix(const DevGeo &G, int v, long q) {
+  if constexpr (sizeof(R) == 4) return q * (long)G.wstr + v;
+  else return (long)v * G.wtot + q;
+}
+
+// FP32 path: after the interleaved W, four planes of per-cell auxiliaries for
+// the kernels that need one value per cell: the pressure deviation (shock
+// flags) and the cell-centred EMF E = -u x B (Contact-CT), written with W.
+enum { AUX_P = 0, AUX_E = 1, NAUX = 4 };
+__host__ __device__ __forceinline__ long waux(const DevGeo &G, int a, long q) {
+  return (long)G.wstr * G.wtot + (long)a * G.wtot + q;
+}
+__device__ __forceinline__ void write_aux(const DevGeo &G, float *W, long q, const float *w) {
+  W[waux(G, AUX_P, q)] = w[W_P];
+#pragma unroll
+  for (int D = 0; D < 3; ++D) {
+    const int A = (D + 1) % 3, B = (D + 2) % 3;
+    W[waux(G, AUX_E + D, q)] = -(w[W_VX + A] * w[W_BX + B] - w[W_VX + B] * w[W_BX + A]);
+  }
+}
 
 // Scale of conserved variable v of the mixed form (rho, m, E, rho X).
 __host__ __device__ __forceinline__ double usc(const DevGeo &G, int v) {

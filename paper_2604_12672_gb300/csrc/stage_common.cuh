@@ -101,15 +101,18 @@ __device__ __forceinline__ void k_flag_raw_at(long tl, const DevGeo &G, const Bo
     int c[3];
     if (!cell_at(box, tl, c)) return;
     const long q = widx(G, c[0], c[1], c[2]);
-    const R *P = W + (long)W_P * G.wtot;
-    const R P0 = P[q] + bg_cell_t<R>(G, c[2]).p;
+    auto P = [&](long r) {
+      if constexpr (sizeof(R) == 4) return W[waux(G, AUX_P, r)];
+      else return W[wix<R>(G, W_P, r)];
+    };
+    const R P0 = P(q) + bg_cell_t<R>(G, c[2]).p;
     R sum = R(0);
     for (int d = 0; d < 3; ++d) {
       if (!G.act[d]) continue;
       const long sd = wstride(G, d);
       const int kp = c[2] + (d == 2), km = c[2] - (d == 2);
-      const R Pp = P[q + sd] + bg_cell_t<R>(G, kp).p;
-      const R Pm = P[q - sd] + bg_cell_t<R>(G, km).p;
+      const R Pp = P(q + sd) + bg_cell_t<R>(G, kp).p;
+      const R Pm = P(q - sd) + bg_cell_t<R>(G, km).p;
       sum += fabs(Pp - Pm);
     }
     raw[c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2])] = (sum / (eps_sf_t<R>(G) * P0) > R(1)) ? 1 : 0;
@@ -209,9 +212,9 @@ __device__ __forceinline__ void flux_face(const DevGeo &G, const int *c, long pR
     ql[v] = w1 + R(0.5) * vl_slope(w0, w1, w2);
     qr[v] = w2 - R(0.5) * vl_slope(w1, w2, w3);
   }
-  if (ideal) {
-    ql[W_GE] = qr[W_GE] = fetch(W_GE, 2);
-    ql[W_GC] = qr[W_GC] = fetch(W_GC, 2);
+  if (ideal) {   // not used by the ideal-gas solver (constant gamma)
+    ql[W_GE] = qr[W_GE] = R(0);
+    ql[W_GC] = qr[W_GC] = R(0);
   }
   wl[RD_RHO] = ql[W_RHO];        wr[RD_RHO] = qr[W_RHO];
   wl[RD_UN] = ql[W_VX + D];      wr[RD_UN] = qr[W_VX + D];
@@ -288,7 +291,7 @@ __device__ __forceinline__ void k_flux_at(long tl, const DevGeo &G, const Box &b
   const long sd = wstride(G, D);
   const long pR = widx(G, c[0], c[1], c[2]);
   const long base = pR - 2 * sd;
-  auto fetch = [&](int v, int k) -> R { return W[v * G.wtot + base + k * sd]; };
+  auto fetch = [&](int v, int k) -> R { return W[wix<R>(G, v, base + k * sd)]; };
   flux_face<D, R, NS>(G, c, pR, fetch, Bf, dB, flag, F, dflag);
 }
 
@@ -319,9 +322,12 @@ __device__ __forceinline__ void k_emf_at(long tl, const DevGeo &G, const Box &bo
       const R *ua = FA + (long)G.nf * wt, *ub = FB + (long)G.nf * wt;
       const R ma1 = ua[p], ma0 = ua[p - sb];
       const R mb1 = ub[p], mb0 = ub[p - sa];
-      const R *va = W + (W_VX + A) * wt, *vb = W + (W_VX + B) * wt;
-      const R *ba = W + (W_BX + A) * wt, *bb = W + (W_BX + B) * wt;
-      auto ec = [&](long q) { return -(va[q] * bb[q] - vb[q] * ba[q]); };
+      auto ec = [&](long q) -> R {
+        if constexpr (sizeof(R) == 4) return W[waux(G, AUX_E + D, q)];
+        else
+          return -(W[wix<R>(G, W_VX + A, q)] * W[wix<R>(G, W_BX + B, q)] -
+                   W[wix<R>(G, W_VX + B, q)] * W[wix<R>(G, W_BX + A, q)]);
+      };
       const R E00 = ec(p - sa - sb), E10 = ec(p - sb), E01 = ec(p - sa), E11 = ec(p);
       const R lo_l = Eb0 - E00, lo_r = Eb1 - E10;
       const R up_l = E01 - Eb0, up_r = E11 - Eb1;
