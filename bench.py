@@ -52,10 +52,13 @@ BYTES_PER_CELL_STAGE = {1: 128.0, 2: 192.0, 3: 192.0}
 # the ncu SASS counters of k_flux on the stratified box).
 FP64_FLOP_PER_FACE = 807.0
 # Mixed flux kernel: FP32 operations per face (FADD + FMUL + 2 FFMA from the ncu
-# SASS counters of k_flux<0/1/2, float> on the stratified box at 64^3, per sweep
-# direction); peak = 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (measured FFMA
-# probe: 73.2 TFLOP/s).
-FP32_FLOP_PER_FACE = {"flux_x": 372.8, "flux_y": 316.0, "flux_z": 315.7}
+# SASS counters of k_flux<0/1/2, float> on the stratified box at 160^3, per sweep
+# direction), and its DRAM bytes per face (dram__bytes_read + write, same capture;
+# W is larger than L2 at 160^3, so the per-face traffic carries over to 256^3);
+# peak = 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (measured FFMA probe:
+# 73.2 TFLOP/s).
+FP32_FLOP_PER_FACE = {"flux_x": 381.1, "flux_y": 381.1, "flux_z": 380.1}
+FP32_DRAM_BYTES_PER_FACE = {"flux_x": 74.4, "flux_y": 75.8, "flux_z": 76.1}
 FP32_NOMINAL_TFLOPS = 80.5
 
 
@@ -207,8 +210,10 @@ def roofline(kt, pr, form, hbm_peak, peak_kind):
         flop = FP64_FLOP_PER_FACE if fp64 else FP32_FLOP_PER_FACE[name]
         peak = FP64_NOMINAL_TFLOPS if fp64 else FP32_NOMINAL_TFLOPS
         achieved = faces * flop / (avg_ms * 1e-3) / 1e12
+        traffic = None if fp64 else faces * FP32_DRAM_BYTES_PER_FACE[name]
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_note": None if fp64 else "bytes per launch: ncu DRAM bytes per face at 160^3 x faces",
                 "peak_kind": "nominal FP64 (recipe)" if fp64 else "nominal FP32 (152 SM x 128 lanes x 2.07 GHz)",
                 "flop_per_face": flop, "avg_launch_ms": avg_ms, "launches": launches}
     # HBM view of the whole stage for any other dominant kernel
