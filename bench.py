@@ -370,6 +370,7 @@ def stellar_c3(P, n, steps, warmup, stream, ws):
                               "newton_iters_per_cell_stage": it / (pr.ncells * STAGES * steps)}
     f = out["forms"]
     out["mixed_mlp_over_fp64"] = f["mixed+mlp"]["value"] / f["fp64"]["value"]
+    out["mixed_mlp_cold_only_over_fp64"] = f["mixed+mlp_cold_only"]["value"] / f["fp64"]["value"]
     # per-field L1 of the mixed + network form against the FP64 form, 3 steps at a fixed dt
     g64 = P.Grid(pr, precision="fp64", eos_table=table)
     g64.load()

@@ -42,26 +42,54 @@ struct Mix {                   // composition-derived constants of a cell
 
 template <typename R> struct TV { R f, fx, fy, fxx, fyy, fxy; };
 
-// Bicubic Hermite evaluation of the free energy and its derivatives (FULL =
-// false: only f, f_y, f_yy, which is what e and c_v need).
-template <typename R, bool FULL = true>
-__device__ __forceinline__ bool table_eval(const Table &t, R x, R y, TV<R> &o) {
+// x-part of the bicubic Hermite evaluation (x = ln n_e): cell, fraction and
+// the cubic Hermite basis (value at 0, slope at 0, value at 1, slope at 1)
+// with its first and second derivatives.  Constant during a Newton inversion
+// (rho and the composition are fixed), so it is computed once per cell.
+template <typename R> struct XB {
+  int i;
+  bool ok;
+  R hu[4], du[4], eu[4];
+};
+
+template <typename R>
+__device__ __forceinline__ XB<R> xbasis(const Table &t, R x) {
+  XB<R> X;
   const R x0 = sizeof(R) == 8 ? (R)t.x0 : (R)t.x0f, dx = sizeof(R) == 8 ? (R)t.dx : (R)t.dxf;
-  const R y0 = sizeof(R) == 8 ? (R)t.y0 : (R)t.y0f, dy = sizeof(R) == 8 ? (R)t.dy : (R)t.dyf;
-  const R gx = (x - x0) / dx, gy = (y - y0) / dy;
-  if (!(gx >= R(0) && gx <= R(t.nx - 1) && gy >= R(0) && gy <= R(t.ny - 1))) return false;
-  int i = (int)gx, j = (int)gy;
+  const R gx = (x - x0) / dx;
+  X.ok = gx >= R(0) && gx <= R(t.nx - 1);
+  int i = X.ok ? (int)gx : 0;
   if (i > t.nx - 2) i = t.nx - 2;
+  X.i = i;
+  const R u = gx - (R)i;
+  const R u2 = u * u, u3 = u2 * u;
+  X.hu[0] = R(2) * u3 - R(3) * u2 + R(1); X.hu[1] = u3 - R(2) * u2 + u;
+  X.hu[2] = R(-2) * u3 + R(3) * u2;       X.hu[3] = u3 - u2;
+  X.du[0] = R(6) * u2 - R(6) * u;          X.du[1] = R(3) * u2 - R(4) * u + R(1);
+  X.du[2] = R(-6) * u2 + R(6) * u;         X.du[3] = R(3) * u2 - R(2) * u;
+  X.eu[0] = R(12) * u - R(6);              X.eu[1] = R(6) * u - R(4);
+  X.eu[2] = R(-12) * u + R(6);             X.eu[3] = R(6) * u - R(2);
+  return X;
+}
+
+// Bicubic Hermite evaluation of the free energy and its derivatives at
+// (x, y = ln T) given the x-part (FULL = false: only f, f_y, f_yy, which is
+// what e and c_v need).
+template <typename R, bool FULL = true>
+__device__ __forceinline__ bool table_eval_xb(const Table &t, const XB<R> &X, R y, TV<R> &o) {
+  const R dx = sizeof(R) == 8 ? (R)t.dx : (R)t.dxf;
+  const R y0 = sizeof(R) == 8 ? (R)t.y0 : (R)t.y0f, dy = sizeof(R) == 8 ? (R)t.dy : (R)t.dyf;
+  const R gy = (y - y0) / dy;
+  if (!(X.ok && gy >= R(0) && gy <= R(t.ny - 1))) return false;
+  const int i = X.i;
+  int j = (int)gy;
   if (j > t.ny - 2) j = t.ny - 2;
-  const R u = gx - (R)i, v = gy - (R)j;
-  // cubic Hermite basis: value at 0, slope at 0, value at 1, slope at 1
-  const R u2 = u * u, u3 = u2 * u, v2 = v * v, v3 = v2 * v;
-  const R hu[4] = {R(2) * u3 - R(3) * u2 + R(1), u3 - R(2) * u2 + u, R(-2) * u3 + R(3) * u2, u3 - u2};
-  const R du[4] = {R(6) * u2 - R(6) * u, R(3) * u2 - R(4) * u + R(1), R(-6) * u2 + R(6) * u, R(3) * u2 - R(2) * u};
-  const R eu[4] = {R(12) * u - R(6), R(6) * u - R(4), R(-12) * u + R(6), R(6) * u - R(2)};
+  const R v = gy - (R)j;
+  const R v2 = v * v, v3 = v2 * v;
   const R hv[4] = {R(2) * v3 - R(3) * v2 + R(1), v3 - R(2) * v2 + v, R(-2) * v3 + R(3) * v2, v3 - v2};
   const R dv[4] = {R(6) * v2 - R(6) * v, R(3) * v2 - R(4) * v + R(1), R(-6) * v2 + R(6) * v, R(3) * v2 - R(2) * v};
   const R ev[4] = {R(12) * v - R(6), R(6) * v - R(4), R(-12) * v + R(6), R(6) * v - R(2)};
+  const R *hu = X.hu, *du = X.du, *eu = X.eu;
   R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
 #pragma unroll
   for (int cb = 0; cb < 2; ++cb)
@@ -91,14 +119,18 @@ __device__ __forceinline__ bool table_eval(const Table &t, R x, R y, TV<R> &o) {
   return true;
 }
 
+template <typename R, bool FULL = true>
+__device__ __forceinline__ bool table_eval(const Table &t, R x, R y, TV<R> &o) {
+  return table_eval_xb<R, FULL>(t, xbasis<R>(t, x), y, o);
+}
+
 template <typename R> struct EosOut { R P, e, cv, Pr, PT, ge, gc; };
 
 // Full EOS at (rho, T) for a mixture with mean mass number abar and Y_e.
 template <typename R>
-__device__ __forceinline__ bool eos_rt(const Table &t, R rho, R T, R abar, R ye, EosOut<R> &o) {
+__device__ __forceinline__ bool eos_rt_xb(const Table &t, const XB<R> &X, R rho, R T, R abar, EosOut<R> &o) {
   TV<R> q;
-  const R ne = rho * ye * R(NAV);
-  if (!table_eval<R>(t, log(ne), log(T), q)) return false;
+  if (!table_eval_xb<R>(t, X, log(T), q)) return false;
   const R irho = R(1) / rho, iT = R(1) / T;
   const R Pe = q.fx - q.f;
   const R ee = (q.f - q.fy) * irho;
@@ -130,12 +162,16 @@ __device__ __forceinline__ bool eos_rt(const Table &t, R rho, R T, R abar, R ye,
   return true;
 }
 
+template <typename R>
+__device__ __forceinline__ bool eos_rt(const Table &t, R rho, R T, R abar, R ye, EosOut<R> &o) {
+  return eos_rt_xb<R>(t, xbasis<R>(t, log(rho * ye * R(NAV))), rho, T, abar, o);
+}
+
 // Specific internal energy and c_v at (rho, T): what a Newton iteration needs.
 template <typename R>
-__device__ __forceinline__ bool eos_ecv(const Table &t, R rho, R T, R abar, R ye, R &e, R &cv) {
+__device__ __forceinline__ bool eos_ecv_xb(const Table &t, const XB<R> &X, R rho, R T, R abar, R &e, R &cv) {
   TV<R> q;
-  const R ne = rho * ye * R(NAV);
-  if (!table_eval<R, false>(t, log(ne), log(T), q)) return false;
+  if (!table_eval_xb<R, false>(t, X, log(T), q)) return false;
   const R irho = R(1) / rho, iT = R(1) / T;
   const R iab = R(1) / abar;
   const R Rg = R(RGAS);
@@ -153,23 +189,28 @@ __device__ __forceinline__ bool eos_ecv(const Table &t, R rho, R T, R abar, R ye
   return true;
 }
 
+template <typename R>
+__device__ __forceinline__ bool eos_ecv(const Table &t, R rho, R T, R abar, R ye, R &e, R &cv) {
+  return eos_ecv_xb<R>(t, xbasis<R>(t, log(rho * ye * R(NAV))), rho, T, abar, e, cv);
+}
+
 // Newton inversion e_int -> T (Sect. 2.2): T <- T + (e - e_EoS)/c_v until
 // |de|/e < tol, then one more step; bracketed inside the table's T range.
 // The iterations evaluate only e and c_v; the full EOS (P, gamma_e, gamma_c)
 // is evaluated once, at the final T.  Returns the iteration count or -1.
 template <typename R>
-__device__ __forceinline__ int eos_invert(const Table &t, R rho, R eint, R abar, R ye, R &T, R tol, int maxit,
-                                          EosOut<R> &o) {
+__device__ __forceinline__ int newton_loop(const Table &t, const XB<R> &X, R rho, R eint, R abar, R &T, R tol,
+                                           int maxit, EosOut<R> &o, bool have, R e0, R cv0) {
   const R Tlo = exp(R(t.y0)), Thi = exp(R(t.y0 + (t.ny - 1) * t.dy));
   R lo = Tlo, hi = Thi;
-  if (!(T > Tlo && T < Thi)) T = sqrt(Tlo * Thi);
+  if (!(T > Tlo && T < Thi)) { T = sqrt(Tlo * Thi); have = false; }
   for (int it = 1; it <= maxit; ++it) {
-    R e, cv;
-    if (!eos_ecv<R>(t, rho, T, abar, ye, e, cv)) return -1;
+    R e = e0, cv = cv0;   // the first iteration may come evaluated
+    if (!(have && it == 1) && !eos_ecv_xb<R>(t, X, rho, T, abar, e, cv)) return -1;
     const R de = eint - e;
     if (fabs(de) < tol * fabs(eint)) {
       T = T + de / cv;
-      if (!eos_rt<R>(t, rho, T, abar, ye, o)) return -1;
+      if (!eos_rt_xb<R>(t, X, rho, T, abar, o)) return -1;
       return it;
     }
     if (de > R(0)) lo = T; else hi = T;
@@ -180,6 +221,13 @@ __device__ __forceinline__ int eos_invert(const Table &t, R rho, R eint, R abar,
   return -1;
 }
 
+template <typename R>
+__device__ __forceinline__ int eos_invert(const Table &t, R rho, R eint, R abar, R ye, R &T, R tol, int maxit,
+                                          EosOut<R> &o) {
+  const XB<R> X = xbasis<R>(t, log(rho * ye * R(NAV)));   // rho and Y_e fixed
+  return newton_loop<R>(t, X, rho, eint, abar, T, tol, maxit, o, false, R(0), R(0));
+}
+
 // The FP32 phase of the mixed inversion: Newton on e and c_v only, until
 // |de|/e < tol or maxit; T keeps the last bracketed iterate.
 __device__ __forceinline__ int newton_fp32(const Table &t, float rho, float eint, float abar, float ye, float &T,
@@ -187,9 +235,10 @@ __device__ __forceinline__ int newton_fp32(const Table &t, float rho, float eint
   const float Tlo = expf((float)t.y0), Thi = expf((float)(t.y0 + (t.ny - 1) * t.dy));
   float lo = Tlo, hi = Thi;
   if (!(T > Tlo && T < Thi)) T = sqrtf(Tlo * Thi);
+  const XB<float> X = xbasis<float>(t, logf(rho * ye * float(NAV)));
   for (int it = 1; it <= maxit; ++it) {
     float e, cv;
-    if (!eos_ecv<float>(t, rho, T, abar, ye, e, cv)) return -1;
+    if (!eos_ecv_xb<float>(t, X, rho, T, abar, e, cv)) return -1;
     const float de = eint - e;
     if (de > 0.0f) lo = T; else hi = T;
     float Tn = T + de / cv;
@@ -200,8 +249,8 @@ __device__ __forceinline__ int newton_fp32(const Table &t, float rho, float eint
   return -1;
 }
 
-// Mixed-precision inversion: FP32 Newton iterations (e and c_v only) bring T
-// within about 1e-5 of the root (|de| / e; FP32 holds ln n_e ~ 70 and
+// Mixed-precision inversion: from a guess farther than 1e-4 from the root,
+// FP32 Newton iterations (e and c_v only) bring T within about 1e-5 of it (|de| / e; FP32 holds ln n_e ~ 70 and
 // ln T ~ 20 only to ~1e-6, the floor of an FP32 table lookup); FP64 Newton
 // then finishes with the FP64 path's stopping rule (|de|/e < tol, one more
 // step, the full evaluation at the final T).  The low-Mach deviations need
@@ -209,10 +258,20 @@ __device__ __forceinline__ int newton_fp32(const Table &t, float rho, float eint
 // total iteration count, or -1 if the FP64 phase fails.
 __device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, double eint, double abar, double ye,
                                                 double &T, double tol, int maxit, EosOut<double> &o) {
+  // a first guess already within 1e-4 of the root (the previous step's T in
+  // a time step) goes straight to the FP64 iteration: the FP32 phase could
+  // only degrade it to FP32's ~1e-6
+  const XB<double> X = xbasis<double>(t, log(rho * ye * NAV));
+  {
+    const double Tlo = exp(t.y0), Thi = exp(t.y0 + (t.ny - 1) * t.dy);
+    double e, cv;
+    if (T > Tlo && T < Thi && eos_ecv_xb<double>(t, X, rho, T, abar, e, cv) && fabs(eint - e) < 1e-4 * fabs(eint))
+      return newton_loop<double>(t, X, rho, eint, abar, T, tol, maxit, o, true, e, cv);
+  }
   float Tf = (float)T;
   const int it32 = newton_fp32(t, (float)rho, (float)eint, (float)abar, (float)ye, Tf, 1e-5f, maxit < 12 ? maxit : 12);
   if (isfinite(Tf) && Tf > 0.0f) T = (double)Tf;
-  const int it64 = eos_invert<double>(t, rho, eint, abar, ye, T, tol, maxit, o);
+  const int it64 = newton_loop<double>(t, X, rho, eint, abar, T, tol, maxit, o, false, 0.0, 0.0);
   return it64 < 0 ? -1 : it64 + (it32 > 0 ? it32 : 12);
 }
 

@@ -30,18 +30,15 @@ __device__ __forceinline__ void mixture(const DevGeo &G, const R *X, R &abar, R 
   ye = sz;
 }
 
-// Interior cells: conserved -> primitives with the EOS.  FP64 path (R = double):
-// FP64 Newton.  Mixed path (R = float): FP32 Newton iterations to about 1e-6,
-// finished in FP64 to the same tolerance.  Writes the deviations W and T_out.
-template <typename R>
-__global__ void k_eos_cells(DevGeo G, Box box, const double *__restrict__ U, const double *__restrict__ Bf,
-                            const float *__restrict__ dU, const float *__restrict__ dB,
-                            const double *__restrict__ Tin, double *__restrict__ Tout, R *__restrict__ W,
-                            int *dflag) {
-  int c[3];
-  const bool in = cell3(box, c);
-  if (!in) { c[0] = box.lo[0]; c[1] = box.lo[1]; c[2] = box.lo[2]; }   // harmless stand-in for the warp's MLP
-  const long p = sidx(G, c[0], c[1], c[2]);
+// Stage-input state of interior cell p: density, velocity, cell-centred B,
+// specific internal energy, mass fractions.
+struct CellState {
+  double rho, v[3], b[3], eint, X[PHL_NSPEC_MAX];
+};
+__device__ __forceinline__ CellState cell_state(const DevGeo &G, long p, const double *__restrict__ U,
+                                                const double *__restrict__ Bf, const float *__restrict__ dU,
+                                                const float *__restrict__ dB) {
+  CellState c;
   const long pl = G.plane;
   double u[5 + PHL_NSPEC_MAX];
 #pragma unroll
@@ -57,46 +54,72 @@ __global__ void k_eos_cells(DevGeo G, Box box, const double *__restrict__ U, con
     bl[0] += dB[p] * s; bl[1] += dB[pl + p] * s; bl[2] += dB[2 * pl + p] * s;
     bh[0] += dB[p + 1] * s; bh[1] += dB[pl + p + G.sy] * s; bh[2] += dB[2 * pl + p + G.sz] * s;
   }
-  const double rho = u[0];
-  const double vx = u[1] / rho, vy = u[2] / rho, vz = u[3] / rho;
-  const double bx = 0.5 * (bl[0] + bh[0]), by = 0.5 * (bl[1] + bh[1]), bz = 0.5 * (bl[2] + bh[2]);
-  const double eint = u[4] / rho - 0.5 * (vx * vx + vy * vy + vz * vz) - 0.5 * (bx * bx + by * by + bz * bz) / rho;
-  double X[PHL_NSPEC_MAX];
+  c.rho = u[0];
+  c.v[0] = u[1] / c.rho; c.v[1] = u[2] / c.rho; c.v[2] = u[3] / c.rho;
+  c.b[0] = 0.5 * (bl[0] + bh[0]); c.b[1] = 0.5 * (bl[1] + bh[1]); c.b[2] = 0.5 * (bl[2] + bh[2]);
+  c.eint = u[4] / c.rho - 0.5 * (c.v[0] * c.v[0] + c.v[1] * c.v[1] + c.v[2] * c.v[2]) -
+           0.5 * (c.b[0] * c.b[0] + c.b[1] * c.b[1] + c.b[2] * c.b[2]) / c.rho;
 #pragma unroll
   for (int l = 0; l < PHL_NSPEC_MAX; ++l)
-    if (l < G.nspec) X[l] = u[5 + l] / rho;
+    if (l < G.nspec) c.X[l] = u[5 + l] / c.rho;
+  return c;
+}
+
+// First guesses from the temperature-guess network (use_mlp = 1: every cell;
+// 2: cells without a previous temperature, Tin <= 0), written to Tg; the other
+// cells get their previous temperature.  Warp-collective BF16 tensor-core
+// inference; kept out of the Newton kernel so that one keeps few registers.
+__global__ void k_mlp_guess(DevGeo G, Box box, const double *__restrict__ U, const double *__restrict__ Bf,
+                            const float *__restrict__ dU, const float *__restrict__ dB,
+                            const double *__restrict__ Tin, double *__restrict__ Tg) {
+  int c[3];
+  const bool in = cell3(box, c);
+  if (!in) { c[0] = box.lo[0]; c[1] = box.lo[1]; c[2] = box.lo[2]; }   // harmless stand-in for the warp
+  const long p = sidx(G, c[0], c[1], c[2]);
+  const double T = Tin[p];
+  const bool need = G.use_mlp == 1 || !(T > 0.0);
+  if (!__any_sync(0xffffffffu, in && need)) {
+    if (in) Tg[p] = T;
+    return;
+  }
+  const CellState s = cell_state(G, p, U, Bf, dU, dB);
+  const bool ok_in = in && s.rho > 0.0 && s.eint > 0.0;
+  const float lr = ok_in ? (float)log10(s.rho) : G.mlp.c[0];
+  const float le = ok_in ? (float)log10(s.eint) : G.mlp.c[1];
+  const float x0 = ok_in ? (float)(s.X[0] / (s.X[0] + (G.nspec > 1 ? s.X[1] : 0.0))) : G.mlp.c[2];
+  const float lt = mlp::guess_log10T(G.mlp, lr, le, x0);
+  if (in) Tg[p] = need ? exp10((double)lt) : T;
+}
+
+// Interior cells: conserved -> primitives with the EOS.  FP64 path (R = double):
+// FP64 Newton.  Mixed path (R = float): FP64 Newton from a guess within 1e-4,
+// else FP32 Newton iterations to about 1e-5 finished in FP64 to the same
+// tolerance.  First guess: Tg (the network's, with use_mlp) or Tin; with the
+// network the previous temperature is the fallback.  Writes W and T_out.
+template <typename R>
+__global__ void __launch_bounds__(256, 2) k_eos_cells(DevGeo G, Box box, const double *__restrict__ U,
+                                                       const double *__restrict__ Bf, const float *__restrict__ dU,
+                                                       const float *__restrict__ dB, const double *__restrict__ Tin,
+                                                       double *__restrict__ Tout, R *__restrict__ W, int *dflag) {
+  int c[3];
+  if (!cell3(box, c)) return;
+  const long p = sidx(G, c[0], c[1], c[2]);
+  const CellState cs = cell_state(G, p, U, Bf, dU, dB);
+  const double rho = cs.rho, eint = cs.eint;
+  const double vx = cs.v[0], vy = cs.v[1], vz = cs.v[2], bx = cs.b[0], by = cs.b[1], bz = cs.b[2];
+  double X[PHL_NSPEC_MAX];
+#pragma unroll
+  for (int l = 0; l < PHL_NSPEC_MAX; ++l) X[l] = cs.X[l];
   double abar, ye;
   mixture<double>(G, X, abar, ye);
-  double T = Tin[p];
+  double T = G.use_mlp ? Tout[p] : Tin[p];   // Tout holds the network's guesses (k_mlp_guess)
   eos::EosOut<double> o;
-  int it;
-  // use_mlp = 1: the network's guess first, the previous temperature as the
-  // fallback; use_mlp = 2: the network only where no previous temperature exists
-  const bool need = G.use_mlp == 1 || !(T > 0.0);
-  if (G.use_mlp && __any_sync(0xffffffffu, in && need)) {
-    // warp-collective BF16 tensor-core guess; the Newton iteration judges it and
-    // falls back to the previous temperature if it does not converge from it
-    const bool ok_in = in && rho > 0.0 && eint > 0.0;
-    const float lr = ok_in ? (float)log10(rho) : G.mlp.c[0];
-    const float le = ok_in ? (float)log10(eint) : G.mlp.c[1];
-    const float x0 = ok_in ? (float)(X[0] / (X[0] + (G.nspec > 1 ? X[1] : 0.0))) : G.mlp.c[2];
-    const float lt = mlp::guess_log10T(G.mlp, lr, le, x0);
-    if (!in) return;
-    double Tg = need ? exp10((double)lt) : T;
-    it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, Tg, G.newton_tol, G.newton_maxit, o)
-                        : eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, Tg, G.newton_tol, G.newton_maxit, o);
-    if (it > 0) {
-      T = Tg;
-    } else {
-      it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o)
+  int it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o)
                           : eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
-    }
-  } else {
-    if (!in) return;
-    if (sizeof(R) == 8)
-      it = eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
-    else
-      it = eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
+  if (it < 0 && G.use_mlp) {   // the plain Newton from the previous temperature is the fallback
+    T = Tin[p];
+    it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o)
+                        : eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
   }
   if (G.niter) {   // warp sum, one atomic per warp
     const unsigned m = __activemask();
@@ -301,6 +324,10 @@ template <typename R>
 void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
                       const double *Tin, double *Tout, R *W, int *dflag, cudaStream_t s, int *nl, Prof *prof) {
   Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
+  if (G.use_mlp) {
+    PHL_LAUNCH(KC_PRIM, prof, s, k_mlp_guess<<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout));
+    if (nl) *nl += 1;
+  }
   PHL_LAUNCH(KC_PRIM, prof, s, k_eos_cells<R><<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout, W, dflag));
   int l[3], h[3];
   for (int d = 0; d < 3; ++d) {
