@@ -60,6 +60,9 @@ FP64_FLOP_PER_FACE = 807.0
 FP32_FLOP_PER_FACE = {"flux_x": 381.1, "flux_y": 381.1, "flux_z": 380.1}
 FP32_DRAM_BYTES_PER_FACE = {"flux_x": 74.4, "flux_y": 75.8, "flux_z": 76.1}
 FP32_NOMINAL_TFLOPS = 80.5
+# Fused tile kernel (k_flux_update_mx): DRAM bytes per cell from an ncu capture
+# (None until measured for the current kernel).
+FUSED_DRAM_BYTES_PER_CELL = None
 
 
 def read_peaks():
@@ -165,10 +168,13 @@ def make_problem(n):
     return W.stratified_box(n, n, n)
 
 
-def time_form(P, pr, form, steps, warmup, stream, ws):
-    """Device-timed K steps of one precision form; returns dict of measurements."""
+def time_form(P, pr, form, steps, warmup, stream, ws, fused=-1):
+    """Device-timed K steps of one precision form; returns dict of measurements.
+    fused >= 0 picks the mixed stage's kernel decomposition (phl_set_fused)."""
     import torch
     g = P.Grid(pr, precision=form, stream=stream.cuda_stream)
+    if form == "mixed" and fused >= 0:
+        g.set_fused(fused)
     g.load()
     for _ in range(warmup):
         g.step(1)
@@ -203,6 +209,18 @@ def roofline(kt, pr, form, hbm_peak, peak_kind):
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None, "peak_kind": f"{peak_kind} HBM copy",
                 "avg_launch_ms": avg_ms, "launches": launches}
+    if name == "flux_update":
+        # fused tile kernel: the faces of all three directions + the cell update;
+        # algorithmic work = 3 faces per cell x the flux arithmetic per face
+        # (the same device code as the per-direction kernels)
+        flop = 3.0 * FP32_FLOP_PER_FACE["flux_x"]
+        achieved = ncells * flop / (avg_ms * 1e-3) / 1e12
+        traffic = ncells * FUSED_DRAM_BYTES_PER_CELL if FUSED_DRAM_BYTES_PER_CELL else None
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_NOMINAL_TFLOPS, "traffic": traffic,
+                "traffic_note": "bytes per launch: ncu DRAM bytes per cell x cells" if traffic else None,
+                "peak_kind": "nominal FP32 (152 SM x 128 lanes x 2 x 2.07 GHz)",
+                "flop_per_cell": flop, "avg_launch_ms": avg_ms, "launches": launches}
     if name.startswith("flux"):
         n = pr.n[0]
         faces = (n + 1) * (n + 2) * (n + 2)
@@ -465,6 +483,9 @@ def main():
     ap.add_argument("--form", default="both", choices=["fp64", "mixed", "both"],
                     help="both: time the plain FP64 form and the mixed form; the value is the mixed form's")
     ap.add_argument("--n", type=int, default=256, help="box edge (256 is the benchmark workload)")
+    ap.add_argument("--fused", type=int, default=-1,
+                    help="mixed stage: 0 = per-direction face kernels, 1..4 = fused tile kernel launch shape "
+                         "(default: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -495,7 +516,7 @@ def main():
     clk = None
     for form in forms:
         clocks = Clocks(gpu_id) if form == head else None
-        g, ms, kt, st = time_form(P, pr, form, args.steps, args.warmup, stream, ws)
+        g, ms, kt, st = time_form(P, pr, form, args.steps, args.warmup, stream, ws, args.fused)
         if clocks is not None:
             clk = clocks.stop()
         value, ms_max = whole_job_rate(pr.ncells * STAGES * args.steps, ms, ws)

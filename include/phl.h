@@ -172,6 +172,24 @@ phl_status phl_set_timing(phl_grid *g, int on);
  * reset != 0 clears the totals afterwards. */
 phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, int reset);
 
+/* Selects how a mixed-precision grid evaluates a stage (Sects. 2.4-2.9; the
+ * arithmetic is the same, only the kernel decomposition differs).
+ *   on = 1: the fused tile kernel -- each CTA stages an 8x8x8 tile of the
+ *           primitive deviations with two ghost layers by TMA, computes the
+ *           faces of all three directions in shared memory and applies the
+ *           cell update; shock flags before it and the Contact-CT EMFs and
+ *           face updates after it run as one kernel each.  Needs
+ *           precision = PHL_MIXED, an ideal gas, nspec = 0 and three active
+ *           dimensions (PHL_EUNSUPPORTED otherwise).  Default where eligible.
+ *   on = 2..4: the same kernel in other launch shapes (threads per CTA,
+ *           CTAs per SM, faces of one direction at a time through a smaller
+ *           shared buffer), for tuning; 1 selects the default shape.
+ *   on = 0: one kernel per direction for the faces, then EMFs and updates.
+ * Results of all of these agree to FP32 rounding of the deviations.  Call
+ * between steps only (no stage of the grid in flight on its stream).
+ * PHL_EINVAL for on outside 0..4. */
+phl_status phl_set_fused(phl_grid *g, int on);
+
 /* Device pointer of the last computed dt (double), valid for the grid's
  * lifetime; lets callers enqueue reads without a synchronisation. */
 phl_status phl_dt_device_ptr(phl_grid *g, const double **ptr);

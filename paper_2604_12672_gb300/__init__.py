@@ -89,6 +89,7 @@ _SIGS = {
     "phl_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "phl_dt_device_ptr": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "phl_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "phl_set_fused": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "phl_destroy": (None, [C.c_void_p]),
     "phl_last_error": (C.c_char_p, []),
@@ -507,6 +508,12 @@ class Grid:
 
     def set_timing(self, on=True):
         _check(lib().phl_set_timing(self.h, int(bool(on))))
+
+    def set_fused(self, on=1):
+        """Mixed-precision stage decomposition (phl_set_fused): 0/False = one
+        face kernel per direction, 1/True = the fused tile kernel in its
+        default launch shape, 2..4 = other launch shapes of it."""
+        _check(lib().phl_set_fused(self.h, int(on)))
 
     def kernel_times(self, reset=True):
         """{kernel class: (launches, total ms)} since the last reset (synchronises)."""

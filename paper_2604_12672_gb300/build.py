@@ -24,6 +24,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
 PER_FILE_FLAGS = {
     "kernels_mixed.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "unit_kernels.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "stage_fused.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
 }
 
 

@@ -80,12 +80,14 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
       ++nl;
     }
   }
-  if (G.eps_sf > 0.0) {
+  const bool fused = M.tmapW && fused_stage_ok(G);
+  if (G.eps_sf > 0.0 && !fused) {
     Box bx = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
     PHL_LAUNCH(KC_FLAG_RAW, prof, s, k_flag_raw<float><<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.W, M.raw));
     nl += 1 + launch_flags(G, M.raw, M.raw + (long)G.n[0] * G.n[1] * G.n[2], M.flag, s, prof);
   }
-  for (int D = 0; D < 3; ++D) {
+  if (fused) launch_fused_tail(G, M, first, last, b, s, &nl, prof);   // flags, faces, cells, EMFs, faces B
+  for (int D = 0; D < 3 && !fused; ++D) {
     if (!G.act[D]) continue;
     int l[3], h[3];
     for (int d = 0; d < 3; ++d) {
@@ -96,7 +98,7 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
     launch_flux<float>(D, G, bx, M.W, M.B, dB, M.flag, M.F[D], M.dflag, s, prof);
     ++nl;
   }
-  for (int D = 0; D < 3; ++D) {
+  for (int D = 0; D < 3 && !fused; ++D) {
     const int A = (D + 1) % 3, B = (D + 2) % 3;
     if (!G.act[A] && !G.act[B]) continue;
     int l[3] = {0, 0, 0}, h[3];
@@ -113,12 +115,12 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
   S.U = M.U; S.B = M.B; S.dU = M.dU; S.dB = M.dB;
   S.first = first; S.last = last; S.b = (float)b; S.dt = M.dt;
   S.W = M.W; S.F[0] = M.F[0]; S.F[1] = M.F[1]; S.F[2] = M.F[2]; S.E = M.E;
-  {
+  if (!fused) {
     Box bx = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
     PHL_LAUNCH(KC_UPDATE_CELLS, prof, s, k_update_cells_mx<<<grid3(bx), block3(bx), 0, s>>>(G, bx, S));
     ++nl;
   }
-  for (int D = 0; D < 3; ++D) {
+  for (int D = 0; D < 3 && !fused; ++D) {
     int h[3] = {G.n[0], G.n[1], G.n[2]};
     h[D] += 1;
     Box bx = make_box(0, h[0], 0, h[1], 0, h[2]);

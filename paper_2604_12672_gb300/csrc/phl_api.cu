@@ -84,6 +84,8 @@ struct phl_grid {
   double last_dt = 0.0;
   int launches_per_step = 0;
   Prof prof;
+  int fused = 0;                        // mixed stage on the fused tile kernel: launch shape, 0 = off
+  alignas(64) unsigned char tmapW[128]; // its TMA descriptor of W
 };
 
 namespace {
@@ -131,6 +133,7 @@ phl_status check_flags(phl_grid *g) {
   if (f & FLAG_NAN) return fail(PHL_ENAN, "non-finite value in the state");
   if (f & FLAG_NEG) return fail(PHL_ENEGATIVE, "non-positive density or pressure");
   if (f & FLAG_NEWTON) return fail(PHL_ENEWTON, "EOS Newton iteration did not converge");
+  if (f & FLAG_TIMEOUT) return fail(PHL_ETIMEOUT, "a bounded device wait (tile copy) gave up");
   return PHL_OK;
 }
 
@@ -311,6 +314,10 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
       if (G.act[k]) AL(&g->Ff[k], (long)(G.nf + 1) * G.wtot);
     AL(&g->Ef, 3 * G.wtot);
     AL(&g->fmax, 1);
+    if (fused_stage_ok(G)) {
+      if (make_fused_tmap(G, g->Wf, g->tmapW) != PHL_OK) { phl_destroy(g); return PHL_ECUDA; }
+      g->fused = PHL_FUSED_DEFAULT;
+    }
   }
   AL(&g->raw, 2 * ncell);   // raw flags + one dilation pass buffer
   if (d->eos == PHL_EOS_STELLAR) {
@@ -501,6 +508,8 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
       M.U = g->U; M.B = g->B; M.dU = g->dUf; M.dB = g->dBf; M.W = g->Wf;
       M.F[0] = g->Ff[0]; M.F[1] = g->Ff[1]; M.F[2] = g->Ff[2]; M.E = g->Ef;
       M.raw = g->raw; M.flag = g->flag; M.dt = g->dt; M.dflag = g->dflag;
+      M.tmapW = g->fused ? g->tmapW : nullptr;
+      M.fused_variant = g->fused;
       for (int st = 0; st < ns; ++st) {
         M.Tin = g->T;
         M.Tout = g->T2;
@@ -571,6 +580,17 @@ phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, 
   *n = k;
   if (reset)
     for (int c = 0; c < KC_COUNT; ++c) { g->prof.cnt[c] = 0; g->prof.ms[c] = 0.0; }
+  return PHL_OK;
+}
+
+phl_status phl_set_fused(phl_grid *g, int on) {
+  if (!g) return fail(PHL_EINVAL, "null grid");
+  if (on < 0 || on > PHL_FUSED_SHAPES) return fail(PHL_EINVAL, "fused launch shape must be 0..%d", PHL_FUSED_SHAPES);
+  if (!on) { g->fused = 0; return PHL_OK; }
+  if (!g->mixed || !fused_stage_ok(g->G))
+    return fail(PHL_EUNSUPPORTED, "the fused stage needs the mixed form, an ideal gas without species and 3 active dimensions");
+  if (make_fused_tmap(g->G, g->Wf, g->tmapW) != PHL_OK) return PHL_ECUDA;
+  g->fused = on == 1 ? PHL_FUSED_DEFAULT : on;
   return PHL_OK;
 }
 

@@ -36,7 +36,7 @@ enum { U_RHO = 0, U_MX, U_MY, U_MZ, U_E, U_X0 };
 // global-frame flux components
 enum { F_RHO = 0, F_MX, F_MY, F_MZ, F_E, F_BX, F_BY, F_BZ, F_X0 };
 
-enum { FLAG_NEG = 1, FLAG_NAN = 2, FLAG_NEWTON = 4 };
+enum { FLAG_NEG = 1, FLAG_NAN = 2, FLAG_NEWTON = 4, FLAG_TIMEOUT = 8 };
 
 struct DevGeo {
   int n[3];
@@ -45,7 +45,7 @@ struct DevGeo {
   long sy, sz, plane;          // state strides / size per field
   int ge[3];
   long wy, wz, wtot;           // work strides / size per field
-  int wstr;                    // FP32 W: values per cell (components interleaved)
+  int wstr;                    // FP32 W: values per cell (wstr / 4 planes of float4)
   double dx[3], idx[3];
   int nspec, nv, nw, nf;
   int eos;
@@ -202,7 +202,7 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // Kernel classes for the optional per-kernel event timing.
 enum KClass {
   KC_PRIM = 0, KC_FLAG_RAW, KC_FLAG_DILATE, KC_FLUX_X, KC_FLUX_Y, KC_FLUX_Z, KC_EMF, KC_UPDATE_CELLS,
-  KC_UPDATE_FACES, KC_DT, KC_SCALAR, KC_STAGE_MIXED, KC_COUNT
+  KC_UPDATE_FACES, KC_DT, KC_SCALAR, KC_STAGE_MIXED, KC_FLUX_UPDATE, KC_COUNT
 };
 const char *kclass_name(int c);
 
@@ -248,11 +248,22 @@ struct MixedBufs {
   int *dflag;
   const double *Tin;           // stellar EOS: guesses in, temperatures out
   double *Tout;
+  const void *tmapW = nullptr; // TMA descriptor of W (fused path), or null
+  int fused_variant = 1;       // launch shape of the fused tile kernel (phl_set_fused)
 };
 void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
                         int *nlaunch, Prof *prof);
 void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigned int *fmax_bits, double *dt,
                      int *dflag, cudaStream_t s, int *nlaunch, Prof *prof);
+
+// Fused mixed stage (stage_fused.cu): faces of all three directions and the
+// cell update in one tiled kernel; ideal gas, no species, 3-D grids.
+bool fused_stage_ok(const DevGeo &G);
+constexpr int PHL_FUSED_SHAPES = 4;    // launch shapes of the tile kernel
+constexpr int PHL_FUSED_DEFAULT = 2;   // the shape used unless phl_set_fused picks another (288 threads, 3 CTAs/SM, phased)
+int make_fused_tmap(const DevGeo &G, const float *W, void *tmap128);
+void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool last, double b, cudaStream_t s,
+                       int *nl, Prof *prof);
 
 // Buffers of a grid for the ensemble path (ensemble.cu); mixed grids only.
 struct GridView {
@@ -282,12 +293,14 @@ const eos::Table *eos_table_view(const struct phl_eos_table *t);
 mlp::Dev mlp_view(const struct phl_mlp *m);
 
 // Index of component v of work cell q in W.  FP64 path: one plane of wtot
-// values per component.  FP32 path: the components of a cell are contiguous
-// (wstr floats, a multiple of 4), so one cell's deviations are two to four
-// 16-byte loads and a face's stencil touches 4 cells instead of 4 x nw lines.
+// values per component.  FP32 path: planes of float4, components 4h..4h+3 of
+// every cell in plane h (wstr / 4 planes), so one cell's deviations are two to
+// four 16-byte loads, a face's stencil touches 4 cells instead of 4 x nw
+// lines, and a tile staged in shared memory keeps the float4 rows of
+// consecutive cells contiguous (no bank conflicts between neighbouring lanes).
 template <typename R>
 __host__ __device__ __forceinline__ long wix(const DevGeo &G, int v, long q) {
-  if constexpr (sizeof(R) == 4) return q * (long)G.wstr + v;
+  if constexpr (sizeof(R) == 4) return (((long)(v >> 2) * G.wtot + q) << 2) + (v & 3);
   else return (long)v * G.wtot + q;
 }
 

@@ -8,7 +8,8 @@ namespace phl {
 const char *kclass_name(int c) {
   static const char *names[KC_COUNT] = {"prim",         "flag_raw",     "flag_dilate", "flux_x",
                                         "flux_y",       "flux_z",       "emf",         "update_cells",
-                                        "update_faces", "dt",           "set_scalar",  "stage_mixed"};
+                                        "update_faces", "dt",           "set_scalar",  "stage_mixed",
+                                        "flux_update"};
   return (c >= 0 && c < KC_COUNT) ? names[c] : "?";
 }
 

@@ -1,0 +1,568 @@
+// stage_fused.cu -- fused face-flux + cell-update kernel of the mixed-precision
+// stage (ideal gas, no mass fractions, three active dimensions) and the
+// Contact-CT EMF kernel that reads the interior-only face fluxes it leaves.
+//
+// One CTA owns a tile of FX x FY x FZ cells.  A single 4-D TMA copy
+// (cp.async.bulk.tensor, completion on an mbarrier) stages the tile's
+// primitive deviations W with NGW = 2 ghost layers on every side, both float4
+// planes, in shared memory.  The CTA then evaluates every face of the tile in
+// all three directions from shared memory -- van Leer PLM on the deviations
+// (Sect. 2.5), LHLLD / HLL flux in deviation form with the background flux
+// removed (Sects. 2.6-2.8, Eq. wb1) -- keeps the five fluid flux components
+// of each face in shared memory, and finishes with the residual, the gravity
+// and heating sources and the SSP-RK increment of its own cells (Sect. 2.9,
+// Eq. spatres).  Only the tangential-B fluxes and the contact direction of
+// each owned face go to global memory, for the edge EMFs (Sect. 2.4).
+//
+// Compared with one kernel per direction plus a separate update, the face
+// fluxes never round-trip through HBM, each face costs shared-memory loads
+// instead of global gathers with ghost remapping, and the only per-face global
+// traffic left is the normal field, two flag bytes and three EMF inputs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+
+#include "mixed_common.cuh"
+
+namespace phl {
+using namespace stage;
+namespace {
+
+constexpr int FX = 8, FY = 8, FZ = 8;                                  // cells per tile
+constexpr int HX = FX + 2 * NGW, HY = FY + 2 * NGW, HZ = FZ + 2 * NGW;   // staged extent
+constexpr int NHC = HX * HY * HZ;                                      // staged cells
+constexpr int NXF = (FX + 1) * FY * FZ, NYF = FX * (FY + 1) * FZ, NZF = FX * FY * (FZ + 1);
+constexpr int NFACE = NXF + NYF + NZF;
+constexpr int FTPB = 256;
+constexpr unsigned W_TILE_BYTES = 2u * NHC * 16u;
+
+// Shared memory of a tile: the barrier first, then the staged W (128-byte
+// aligned for the TMA destination), then the face buffer, which the phased
+// variant sizes for one direction's faces only (its launch requests less).
+struct FusedSmem {
+  unsigned long long bar;  // TMA completion barrier
+  unsigned long long pad[15];
+  float4 w[2][NHC];        // staged W: (drho, vx, vy, vz) and (Bx, By, Bz, dP) per cell
+  float f[5][NFACE];       // face fluxes, normal frame (rho, m_n, m_t1, m_t2, E); the
+                           // kernel indexes it flat with row stride NXF (phased) or NFACE
+};
+static_assert(offsetof(FusedSmem, w) % 128 == 0, "TMA destination alignment");
+constexpr size_t smem_bytes(bool phased) {
+  return offsetof(FusedSmem, f) + sizeof(float) * 5 * (phased ? NXF : NFACE) + 128;   // + alignment slack
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the barrier phase with a wall-clock limit; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, unsigned long long limit_ns) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > limit_ns) return false;
+  return true;
+}
+
+// Flux of the D-face at the lower side of staged cell s2 (its right cell),
+// global cell c.  Returns the five fluid components in out[] and stores the
+// EMF inputs when the tile owns the face.
+__device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int D, int s2,
+                                           const int *c, int cD, bool own, const uint8_t *__restrict__ flag,
+                                           float *__restrict__ Fd, const GasK<float> &K, float *out, int *dflag) {
+  const int sD = D == 0 ? 1 : (D == 1 ? HX : HX * HY);
+  float ql[8], qr[8];
+  {
+    float4 a[4], b[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      a[m] = sm.w[0][s2 + (m - 2) * sD];
+      b[m] = sm.w[1][s2 + (m - 2) * sD];
+    }
+    auto plm = [&](int v, float w0, float w1, float w2, float w3) {
+      ql[v] = w1 + 0.5f * vl_slope(w0, w1, w2);
+      qr[v] = w2 - 0.5f * vl_slope(w1, w2, w3);
+    };
+    plm(W_RHO, a[0].x, a[1].x, a[2].x, a[3].x);
+    plm(W_VX, a[0].y, a[1].y, a[2].y, a[3].y);
+    plm(W_VY, a[0].z, a[1].z, a[2].z, a[3].z);
+    plm(W_VZ, a[0].w, a[1].w, a[2].w, a[3].w);
+    plm(W_BX, b[0].x, b[1].x, b[2].x, b[3].x);
+    plm(W_BY, b[0].y, b[1].y, b[2].y, b[3].y);
+    plm(W_BZ, b[0].z, b[1].z, b[2].z, b[3].z);
+    plm(W_P, b[0].w, b[1].w, b[2].w, b[3].w);
+  }
+  // normal frame (n, t1, t2) = (D, D+1, D+2 mod 3)
+  float wl[W_X0], wr[W_X0];
+  auto frame = [&](const float *q, float *w) {
+    w[RD_RHO] = q[W_RHO];
+    w[RD_UN] = D == 0 ? q[W_VX] : (D == 1 ? q[W_VY] : q[W_VZ]);
+    w[RD_UT1] = D == 0 ? q[W_VY] : (D == 1 ? q[W_VZ] : q[W_VX]);
+    w[RD_UT2] = D == 0 ? q[W_VZ] : (D == 1 ? q[W_VX] : q[W_VY]);
+    w[RD_BT1] = D == 0 ? q[W_BY] : (D == 1 ? q[W_BZ] : q[W_BX]);
+    w[RD_BT2] = D == 0 ? q[W_BZ] : (D == 1 ? q[W_BX] : q[W_BY]);
+    w[RD_P] = q[W_P];
+    w[RD_GE] = 0.0f;
+    w[RD_GC] = 0.0f;
+  };
+  frame(ql, wl);
+  frame(qr, wr);
+  const BgT<float> bf = D == 2 ? bg_zface_t<float>(G, c[2]) : bg_cell_t<float>(G, c[2]);
+  if (!(bf.rho + wl[RD_RHO] > 0.0f && bf.rho + wr[RD_RHO] > 0.0f && bf.p + wl[RD_P] > 0.0f &&
+        bf.p + wr[RD_P] > 0.0f))
+    atomicOr(dflag, FLAG_NEG);
+  const long qb = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
+  const float b0 = d2f_bits(S.B[qb] * G.isc_b);
+  const float bn = S.first ? b0 : b0 + S.dB[qb];
+  const long pR = widx(G, c[0], c[1], c[2]);
+  int solver = G.riemann;
+  if (flag) {   // dilated shock flags of the two cells (interior layout; a ghost cell carries its source's)
+    bool fl;
+    const int nD = G.n[D];
+    const int cl = cell_src(cD - 1, nD, G.bc[D][0], G.bc[D][1], fl);
+    const int cr = cell_src(cD, nD, G.bc[D][0], G.bc[D][1], fl);
+    const long base = (long)c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2]);
+    const long sD = D == 0 ? 1L : (D == 1 ? (long)G.n[0] : (long)G.n[0] * G.n[1]);
+    if (flag[base + (cl - cD) * sD] | flag[base + (cr - cD) * sD]) solver = SOLVER_HLL;
+  }
+  float fl[7];
+  int up;
+  riemann_dev<float, 0, true>(wl, wr, bn, bf.rho, bf.p, bf.ge, bf.gc, 0, solver, G.machf, fl, up, K);
+  // reflecting wall face: a symmetry plane; only the normal-momentum flux survives
+  if ((cD == 0 && G.bc[D][0] == 1) || (cD == G.n[D] && G.bc[D][1] == 1)) {
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+      if (q != RF_MN) fl[q] = 0.0f;
+    up = 0;
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) out[q] = fl[q];
+  if (own) {
+    const long wt = G.wtot;
+    const int T1 = D == 2 ? 0 : D + 1, T2 = D == 0 ? 2 : D - 1;
+    Fd[(F_BX + T1) * wt + pR] = fl[RF_BT1];
+    Fd[(F_BX + T2) * wt + pR] = fl[RF_BT2];
+    Fd[(long)G.nf * wt + pR] = (float)up;
+  }
+}
+
+// Face index of the D-face at the lower side of tile cell (i, j, k) within the
+// faces of direction D (x fastest; the extent along D is one longer).
+__device__ __forceinline__ int dface(int D, int i, int j, int k) {
+  return D == 0 ? (k * FY + j) * (FX + 1) + i : (D == 1 ? (k * (FY + 1) + j) * FX + i : (k * FY + j) * FX + i);
+}
+__device__ __forceinline__ int dface_step(int D) { return D == 0 ? 1 : (D == 1 ? FX : FX * FY); }
+
+// Evaluates face f of direction D (its index among the tile's D-faces) and
+// returns the five fluid flux components (zeros outside the domain).
+__device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int D, int f,
+                                          int x0, int y0, int z0, const uint8_t *__restrict__ flag, float *F0,
+                                          float *F1, float *F2, const GasK<float> &K, float *out, int *dflag) {
+  int i, j, k;
+  if (D == 0) { i = f % (FX + 1); const int r = f / (FX + 1); j = r % FY; k = r / FY; }
+  else if (D == 1) { i = f % FX; const int r = f / FX; j = r % (FY + 1); k = r / (FY + 1); }
+  else { i = f % FX; const int r = f / FX; j = r % FY; k = r / FY; }
+  const int c[3] = {x0 + i, y0 + j, z0 + k};
+  const bool valid = c[0] <= G.n[0] - (D != 0) && c[1] <= G.n[1] - (D != 1) && c[2] <= G.n[2] - (D != 2);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) out[q] = 0.0f;
+  if (!valid) return;
+  const int s2 = ((k + NGW) * HY + (j + NGW)) * HX + (i + NGW);
+  const int loc = D == 0 ? i : (D == 1 ? j : k);
+  const int ext = D == 0 ? FX : (D == 1 ? FY : FZ);
+  const int cD = D == 0 ? c[0] : (D == 1 ? c[1] : c[2]);
+  const bool own = loc < ext || cD == G.n[D];
+  float *Fd = D == 0 ? F0 : (D == 1 ? F1 : F2);
+  fused_face(G, S, sm, D, s2, c, cD, own, flag, Fd, K, out, dflag);
+}
+
+// Tile kernel.  PHASED = false: all faces of the tile are evaluated in one
+// loop and kept in shared memory (5 x NFACE floats), then every cell sums its
+// six faces.  PHASED = true: one direction at a time through a buffer of one
+// direction's faces; each thread keeps the running residuals of its cells in
+// registers (same summation order x, y, z), so the CTA needs ~1/3 of the
+// shared memory and more CTAs fit on an SM.
+template <int NT, int MINB, bool PHASED>
+__global__ void __launch_bounds__(NT, MINB)
+    k_flux_update_mx(const __grid_constant__ CUtensorMap tmW, DevGeo G, StageMx S, const uint8_t *__restrict__ flag,
+                     float *__restrict__ F0, float *__restrict__ F1, float *__restrict__ F2, int ntx, int nty,
+                     int *dflag) {
+  extern __shared__ unsigned char smraw[];
+  FusedSmem &sm = *reinterpret_cast<FusedSmem *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
+  const int tid = threadIdx.x;
+  int t = blockIdx.x;
+  const int tx = t % ntx;
+  t /= ntx;
+  const int ty = t % nty, tz = t / nty;
+  const int x0 = tx * FX, y0 = ty * FY, z0 = tz * FZ;
+  const unsigned bar = smem_u32(&sm.bar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(W_TILE_BYTES) : "memory");
+    // work-layout coordinates of staged cell (-NGW, -NGW, -NGW): (x0 - NGW + ge) = x0
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(&sm.w[0][0])),
+        "l"((unsigned long long)&tmW), "r"(4 * x0), "r"(y0), "r"(z0), "r"(0), "r"(bar)
+        : "memory");
+  }
+  const bool ok = mbar_wait_bounded(bar, 0u, 1000000000ull);
+  if (__syncthreads_or(!ok)) {   // the copy did not land in 1 s: report, let it finish, leave
+    if (tid == 0) atomicOr(dflag, FLAG_TIMEOUT);
+    mbar_wait_bounded(bar, 0u, 1000000000ull);
+    return;
+  }
+
+  GasK<float> K;
+  K.g = G.gammaf;
+  K.igm1 = 1.0f / (K.g - 1.0f);
+  K.ggm1 = K.g * K.igm1;
+  // face buffer: component q of buffered face f at fb[q * FS + f]
+  constexpr int FS = PHASED ? NXF : NFACE;
+  float *fb = &sm.f[0][0];
+  // normal-frame component that carries global component v on d-faces
+  constexpr int qm[5][3] = {{0, 0, 0}, {1, 3, 2}, {2, 1, 3}, {3, 2, 1}, {4, 4, 4}};
+  constexpr int NC = FX * FY * FZ, CPT = (NC + NT - 1) / NT;   // cells per thread
+  float racc[CPT][5];
+#pragma unroll
+  for (int m = 0; m < CPT; ++m)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) racc[m][v] = 0.0f;
+
+  if constexpr (PHASED) {
+    static_assert(NXF == NYF && NYF == NZF, "phased tiles need equal face counts per direction");
+#pragma unroll 1
+    for (int D = 0; D < 3; ++D) {
+      for (int f = tid; f < NXF; f += NT) {
+        float out[5];
+        tile_face(G, S, sm, D, f, x0, y0, z0, flag, F0, F1, F2, K, out, dflag);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
+      }
+      __syncthreads();
+      const int st = dface_step(D);
+      const float idd = G.idxf[D];
+#pragma unroll
+      for (int m = 0; m < CPT; ++m) {
+        const int cc = tid + m * NT;
+        if (cc < NC) {
+          const int f0 = dface(D, cc % FX, (cc / FX) % FY, cc / (FX * FY));
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const int q = D == 0 ? qm[v][0] : (D == 1 ? qm[v][1] : qm[v][2]);
+            racc[m][v] += (fb[q * FS + f0 + st] - fb[q * FS + f0]) * idd;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int f = tid; f < NFACE; f += NT) {
+      const int D = f < NXF ? 0 : (f < NXF + NYF ? 1 : 2);
+      const int fd = f - (D == 0 ? 0 : (D == 1 ? NXF : NXF + NYF));
+      float out[5];
+      tile_face(G, S, sm, D, fd, x0, y0, z0, flag, F0, F1, F2, K, out, dflag);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int cc = tid + m * NT;
+      if (cc < NC) {
+        const int i = cc % FX, j = (cc / FX) % FY, k = cc / (FX * FY);
+        const int fx = dface(0, i, j, k), fy = NXF + dface(1, i, j, k), fz = NXF + NYF + dface(2, i, j, k);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          racc[m][v] += (fb[qm[v][0] * FS + fx + 1] - fb[qm[v][0] * FS + fx]) * G.idxf[0];
+          racc[m][v] += (fb[qm[v][1] * FS + fy + FX] - fb[qm[v][1] * FS + fy]) * G.idxf[1];
+          racc[m][v] += (fb[qm[v][2] * FS + fz + FX * FY] - fb[qm[v][2] * FS + fz]) * G.idxf[2];
+        }
+      }
+    }
+  }
+
+  // R = sum_d (F_d(+) - F_d(-)) / dx_d - (S - S_hat), then the RK increment
+  const float dt = (float)(*S.dt * G.isc_t);
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) {
+    const int cc = tid + m * NT;
+    if (cc >= NC) continue;
+    const int i = cc % FX, j = (cc / FX) % FY, k = cc / (FX * FY);
+    const int c0 = x0 + i, c1 = y0 + j, c2 = z0 + k;
+    if (c0 >= G.n[0] || c1 >= G.n[1] || c2 >= G.n[2]) continue;
+    float *r = racc[m];
+    // sources S - S_hat: (rho - rho_hat) g on momentum, rho u . g (+ heating) on energy
+    const float4 wa = sm.w[0][((k + NGW) * HY + (j + NGW)) * HX + (i + NGW)];
+    const float drho = wa.x;
+    const float rho = bg_cell_t<float>(G, c2).rho + drho;
+    const float vel[3] = {wa.y, wa.z, wa.w};
+    float se = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float gd = G.gf[d];
+      r[U_MX + d] -= drho * gd;
+      se += rho * vel[d] * gd;
+    }
+    if (G.heatf) se += G.heatf[c2];
+    r[U_E] -= se;
+    const long ps = sidx(G, c0, c1, c2);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const long q = v * G.plane + ps;
+      const float din = S.first ? 0.0f : S.dU[q];
+      const float dout = S.b * (din - dt * r[v]);
+      if (S.last) S.U[q] += f2d_bits(dout) * usc(G, v);
+      else S.dU[q] = dout;
+    }
+  }
+}
+
+// 5^3 dilation of the raw shock flags (Sect. 2.7) for one 8^3 tile of
+// interior cells in one pass: the raw flags of the tile and two neighbours on
+// every side are staged in shared memory (beyond a periodic boundary they
+// wrap, beyond any other boundary they count as unflagged), then ORed along x,
+// y and z in turn (the OR over a box is the nested ORs over its axes).
+__global__ void __launch_bounds__(256) k_flag_dilate3(DevGeo G, const uint8_t *__restrict__ raw,
+                                                     uint8_t *__restrict__ dil, int ntx, int nty) {
+  __shared__ uint8_t r0[HZ][HY][HX], r1[HZ][HY][FX], r2[HZ][FY][FX];
+  int t = blockIdx.x;
+  const int tx = t % ntx;
+  t /= ntx;
+  const int ty = t % nty, tz = t / nty;
+  const int o[3] = {tx * FX - NGW, ty * FY - NGW, tz * FZ - NGW};
+  for (int q = threadIdx.x; q < NHC; q += blockDim.x) {
+    const int l[3] = {q % HX, (q / HX) % HY, q / (HX * HY)};
+    int g[3];
+    bool in = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      int x = o[d] + l[d];
+      if (x < 0 || x >= G.n[d]) {
+        if (G.bc[d][0] == 0) x = ((x % G.n[d]) + G.n[d]) % G.n[d];
+        else in = false;
+      }
+      g[d] = x;
+    }
+    r0[l[2]][l[1]][l[0]] = in ? raw[g[0] + (long)G.n[0] * (g[1] + (long)G.n[1] * g[2])] : (uint8_t)0;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < HZ * HY * FX; q += blockDim.x) {
+    const int x = q % FX, y = (q / FX) % HY, z = q / (FX * HY);
+    r1[z][y][x] = r0[z][y][x] | r0[z][y][x + 1] | r0[z][y][x + 2] | r0[z][y][x + 3] | r0[z][y][x + 4];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < HZ * FY * FX; q += blockDim.x) {
+    const int x = q % FX, y = (q / FX) % FY, z = q / (FX * FY);
+    r2[z][y][x] = r1[z][y][x] | r1[z][y + 1][x] | r1[z][y + 2][x] | r1[z][y + 3][x] | r1[z][y + 4][x];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < FX * FY * FZ; q += blockDim.x) {
+    const int x = q % FX, y = (q / FX) % FY, z = q / (FX * FY);
+    const int c0 = o[0] + NGW + x, c1 = o[1] + NGW + y, c2 = o[2] + NGW + z;
+    if (c0 >= G.n[0] || c1 >= G.n[1] || c2 >= G.n[2]) continue;
+    dil[c0 + (long)G.n[0] * (c1 + (long)G.n[1] * c2)] =
+        r2[z][y][x] | r2[z + 1][y][x] | r2[z + 2][y][x] | r2[z + 3][y][x] | r2[z + 4][y][x];
+  }
+}
+
+// Contact-CT edge EMF along D at the lower corner (a-1/2, b-1/2) of cell c,
+// (D, A, B) cyclic (Sect. 2.4): the mean of the four face EMFs plus the
+// upwinded half-derivatives towards the cell-centred E = -u x B.  The face
+// fluxes are stored for interior faces only: a face in a ghost row reads the
+// interior row its data comes from (periodic wrap, outflow copy).  Ghost rows
+// behind a reflecting wall feed only wall edges, whose EMF is zero (u_n = B_n
+// = 0 there), so no mirror signs are needed.
+template <int D>
+__device__ __forceinline__ float emf_edge(const DevGeo &G, const int *c, const float *__restrict__ W,
+                                          const float *__restrict__ FA, const float *__restrict__ FB) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  bool fl;
+  const int bm = cell_src(c[B] - 1, G.n[B], G.bc[B][0], G.bc[B][1], fl);
+  const int b0 = cell_src(c[B], G.n[B], G.bc[B][0], G.bc[B][1], fl);
+  const int am = cell_src(c[A] - 1, G.n[A], G.bc[A][0], G.bc[A][1], fl);
+  const int a0 = cell_src(c[A], G.n[A], G.bc[A][0], G.bc[A][1], fl);
+  int e[3] = {c[0], c[1], c[2]};
+  e[B] = b0;
+  const long pa1 = widx(G, e[0], e[1], e[2]);
+  e[B] = bm;
+  const long pa0 = widx(G, e[0], e[1], e[2]);
+  e[B] = c[B];
+  e[A] = a0;
+  const long pb1 = widx(G, e[0], e[1], e[2]);
+  e[A] = am;
+  const long pb0 = widx(G, e[0], e[1], e[2]);
+  const long p = widx(G, c[0], c[1], c[2]);
+  const long wt = G.wtot;
+  const long sa = wstride(G, A), sb = wstride(G, B);
+  const float *fab = FA + (F_BX + B) * wt;
+  const float *fba = FB + (F_BX + A) * wt;
+  const float *ua = FA + (long)G.nf * wt, *ub = FB + (long)G.nf * wt;
+  const float Ea1 = -fab[pa1], Ea0 = -fab[pa0];
+  const float Eb1 = fba[pb1], Eb0 = fba[pb0];
+  const float ma1 = ua[pa1], ma0 = ua[pa0];
+  const float mb1 = ub[pb1], mb0 = ub[pb0];
+  auto ec = [&](long q) -> float { return W[waux(G, AUX_E + D, q)]; };
+  const float E00 = ec(p - sa - sb), E10 = ec(p - sb), E01 = ec(p - sa), E11 = ec(p);
+  const float lo_l = Eb0 - E00, lo_r = Eb1 - E10;
+  const float up_l = E01 - Eb0, up_r = E11 - Eb1;
+  const float h = 0.5f, q4 = 0.25f;
+  const float dlo = ma0 > 0.0f ? lo_l : (ma0 < 0.0f ? lo_r : h * (lo_l + lo_r));
+  const float dup = ma1 > 0.0f ? up_l : (ma1 < 0.0f ? up_r : h * (up_l + up_r));
+  const float le_d = Ea0 - E00, le_u = Ea1 - E01;
+  const float ri_d = E10 - Ea0, ri_u = E11 - Ea1;
+  const float dle = mb0 > 0.0f ? le_d : (mb0 < 0.0f ? le_u : h * (le_d + le_u));
+  const float dri = mb1 > 0.0f ? ri_d : (mb1 < 0.0f ? ri_u : h * (ri_d + ri_u));
+  float v = q4 * (Ea1 + Ea0 + Eb1 + Eb0) + q4 * (dlo - dup) + q4 * (dle - dri);
+  if ((c[A] == 0 && G.bc[A][0] == 1) || (c[A] == G.n[A] && G.bc[A][1] == 1) || (c[B] == 0 && G.bc[B][0] == 1) ||
+      (c[B] == G.n[B] && G.bc[B][1] == 1))
+    v = 0.0f;
+  return v;
+}
+
+// All three edge EMFs at the lower corners of site c in [0, n0] x [0, n1] x
+// [0, n2] (an edge along D exists for c_D < n_D).
+__global__ void k_emf3(DevGeo G, Box box, const float *__restrict__ W, const float *__restrict__ F0,
+                       const float *__restrict__ F1, const float *__restrict__ F2, float *__restrict__ E) {
+  int c[3];
+  if (!cell3(box, c)) return;
+  const long p = widx(G, c[0], c[1], c[2]);
+  const long wt = G.wtot;
+  if (c[0] < G.n[0]) E[p] = emf_edge<0>(G, c, W, F1, F2);
+  if (c[1] < G.n[1]) E[wt + p] = emf_edge<1>(G, c, W, F2, F0);
+  if (c[2] < G.n[2]) E[2 * wt + p] = emf_edge<2>(G, c, W, F0, F1);
+}
+
+// Face update of the normal field on the D-face at site c from the curl of
+// the edge EMFs (Eq. induction in discrete form), as k_update_faces_mx.
+template <int D>
+__device__ __forceinline__ void face_update(const DevGeo &G, const int *c, const StageMx &S, float dt) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  const long p = widx(G, c[0], c[1], c[2]);
+  const long wt = G.wtot;
+  float r = 0.0f;
+  r += (S.E[(long)B * wt + p + wstride(G, A)] - S.E[(long)B * wt + p]) * G.idxf[A];
+  r -= (S.E[(long)A * wt + p + wstride(G, B)] - S.E[(long)A * wt + p]) * G.idxf[B];
+  const long q = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
+  const float din = S.first ? 0.0f : S.dB[q];
+  const float dout = S.b * (din - dt * r);
+  if (S.last) S.B[q] += f2d_bits(dout) * G.sc_b;
+  else S.dB[q] = dout;
+}
+
+__global__ void k_update_faces3(DevGeo G, Box box, StageMx S) {
+  int c[3];
+  if (!cell3(box, c)) return;
+  const float dt = (float)(*S.dt * G.isc_t);
+  if (c[1] < G.n[1] && c[2] < G.n[2]) face_update<0>(G, c, S, dt);
+  if (c[0] < G.n[0] && c[2] < G.n[2]) face_update<1>(G, c, S, dt);
+  if (c[0] < G.n[0] && c[1] < G.n[1]) face_update<2>(G, c, S, dt);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    else
+      cudaGetLastError();
+  }
+  return enc;
+}
+
+}  // namespace
+
+bool fused_stage_ok(const DevGeo &G) {
+  return G.eos == PHL_EOS_IDEAL && G.nspec == 0 && G.wstr == 8 && G.act[0] && G.act[1] && G.act[2];
+}
+
+// TMA descriptor of W's two float4 planes as a 4-D tensor (x * 4 floats, y, z,
+// plane); the box is one staged tile.  Strides are multiples of 16 bytes
+// (float4 rows) and the allocation is 256-byte aligned.
+int make_fused_tmap(const DevGeo &G, const float *W, void *tmap128) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+  if (!enc) return set_error(PHL_ECUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[4] = {(cuuint64_t)(4 * G.wy), (cuuint64_t)(G.wz / G.wy), (cuuint64_t)(G.wtot / G.wz), 2};
+  cuuint64_t strides[3] = {(cuuint64_t)(G.wy * 16), (cuuint64_t)(G.wz * 16), (cuuint64_t)(G.wtot * 16)};
+  cuuint32_t box[4] = {4 * HX, HY, HZ, 2};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc((CUtensorMap *)tmap128, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)W, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(PHL_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return PHL_OK;
+}
+
+// Faces, EMFs and updates of one mixed stage on the fused path (prim and
+// flags already done): k_flux_update_mx, three EMF launches, three face
+// updates.
+void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool last, double b, cudaStream_t s,
+                       int *nl, Prof *prof) {
+  StageMx S;
+  S.U = M.U; S.B = M.B; S.dU = M.dU; S.dB = M.dB;
+  S.first = first; S.last = last; S.b = (float)b; S.dt = M.dt;
+  S.W = M.W; S.F[0] = M.F[0]; S.F[1] = M.F[1]; S.F[2] = M.F[2]; S.E = M.E;
+  const int ntx = (G.n[0] + FX - 1) / FX, nty = (G.n[1] + FY - 1) / FY, ntz = (G.n[2] + FZ - 1) / FZ;
+  const int nb = ntx * nty * ntz;
+  const long ncell = (long)G.n[0] * G.n[1] * G.n[2];
+  const uint8_t *dil = nullptr;
+  if (G.eps_sf > 0.0) {   // raw flags, then their 5^3 dilation, both on the interior layout
+    Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
+    PHL_LAUNCH(KC_FLAG_RAW, prof, s, k_flag_raw<float><<<grid3(bi), block3(bi), 0, s>>>(G, bi, M.W, M.raw));
+    PHL_LAUNCH(KC_FLAG_DILATE, prof, s, k_flag_dilate3<<<nb, 256, 0, s>>>(G, M.raw, M.raw + ncell, ntx, nty));
+    dil = M.raw + ncell;
+    *nl += 2;
+  }
+  const CUtensorMap *tm = (const CUtensorMap *)M.tmapW;
+  // launch shapes: (threads, min CTAs per SM, phased)
+#define PHL_FUSED(NT, MB, PH)                                                                                   \
+  do {                                                                                                         \
+    static bool attr = false;                                                                                  \
+    if (!attr) {                                                                                               \
+      cudaFuncSetAttribute(k_flux_update_mx<NT, MB, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                           (int)smem_bytes(PH));                                                               \
+      attr = true;                                                                                             \
+    }                                                                                                          \
+    PHL_LAUNCH(KC_FLUX_UPDATE, prof, s,                                                                        \
+               (k_flux_update_mx<NT, MB, PH><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0], M.F[1],     \
+                                                                             M.F[2], ntx, nty, M.dflag)));     \
+  } while (0)
+  switch (M.fused_variant) {
+    case 2: PHL_FUSED(288, 3, true); break;
+    case 3: PHL_FUSED(256, 3, true); break;
+    case 4: PHL_FUSED(384, 2, true); break;
+    default: PHL_FUSED(256, 2, false); break;
+  }
+#undef PHL_FUSED
+  ++*nl;
+  Box bs = make_box(0, G.n[0] + 1, 0, G.n[1] + 1, 0, G.n[2] + 1);
+  PHL_LAUNCH(KC_EMF, prof, s, k_emf3<<<grid3(bs), block3(bs), 0, s>>>(G, bs, M.W, M.F[0], M.F[1], M.F[2], M.E));
+  PHL_LAUNCH(KC_UPDATE_FACES, prof, s, k_update_faces3<<<grid3(bs), block3(bs), 0, s>>>(G, bs, S));
+  *nl += 2;
+}
+
+}  // namespace phl
