@@ -194,6 +194,14 @@ phl_status phl_set_fused(phl_grid *g, int on);
  * lifetime; lets callers enqueue reads without a synchronisation. */
 phl_status phl_dt_device_ptr(phl_grid *g, const double **ptr);
 
+/* The mixed form's FP64 <-> FP32 boundary conversions, for unit tests: for
+ * each x[i], f[i] = x[i] * 2^k rounded to the nearest FP32 (ties away from
+ * zero; magnitudes below 2^-126 flush to zero, above the FP32 range give
+ * +-inf; NaN stays NaN) and back[i] = f[i] * 2^-k in FP64 (exact).  The
+ * kernels apply their power-of-two unit scales this way, on the integer
+ * pipe.  Host arrays of n values; |k| < 800 (PHL_EINVAL otherwise). */
+phl_status phl_convert_batch(long n, const double *x, int k, float *f, double *back);
+
 /* Evaluate the library's face flux (the device Riemann solver of the stage)
  * for n independent faces -- for unit tests of the solver itself.
  *   wl, wr  [n][9 + nspec] normal-frame primitive deviations, in order

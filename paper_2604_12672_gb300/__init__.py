@@ -90,6 +90,7 @@ _SIGS = {
     "phl_dt_device_ptr": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "phl_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_set_fused": (C.c_int, [C.c_void_p, C.c_int]),
+    "phl_convert_batch": (C.c_int, [C.c_long, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "phl_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "phl_destroy": (None, [C.c_void_p]),
     "phl_last_error": (C.c_char_p, []),
@@ -156,6 +157,16 @@ def _ptr(a):
     # torch tensor
     assert a.is_contiguous(), "contiguous tensor expected"
     return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
+
+
+def convert_batch(x, k):
+    """Device FP64 -> FP32 conversion of x * 2^k and its exact way back
+    (phl_convert_batch); returns (float32 array, float64 array)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    f = np.empty(x.shape, np.float32)
+    back = np.empty(x.shape, np.float64)
+    _check(lib().phl_convert_batch(x.size, x.ctypes.data, int(k), f.ctypes.data, back.ctypes.data))
+    return f, back
 
 
 def riemann_batch(wl, wr, bn, bg=None, nspec=0, solver="lhlld", mach_thr=0.6, precision="fp64"):

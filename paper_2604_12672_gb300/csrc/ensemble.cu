@@ -292,6 +292,7 @@ cudaError_t launch_step_chains(phl_ensemble *E) {
     M.U = v.U; M.B = v.B; M.dU = v.dU; M.dB = v.dB; M.W = v.W;
     for (int k = 0; k < 3; ++k) M.F[k] = v.F[k];
     M.E = v.E; M.raw = v.raw; M.flag = v.flag; M.dt = v.dt; M.dflag = v.dflag; M.Tin = nullptr; M.Tout = nullptr;
+    M.tmapW = v.tmapW; M.fused_variant = v.fused;   // the box's own stage decomposition
     int nl = 0;
     launch_dt_mixed(*v.G, v.U, v.B, v.fmax, v.dt, v.dflag, st, &nl, nullptr);
     for (int stg = 0; stg < 3; ++stg) launch_stage_mixed(*v.G, M, stg, 3, b3[stg], st, &nl, nullptr);

@@ -27,13 +27,14 @@ __device__ __forceinline__ void cell_prims_mx(const DevGeo &G, const double *__r
   const long pl = G.plane;
   const Bg b = bg_cell(G, k);                       // FP64 background for the deviations
   const double ehat = G.has_bg ? G.bg_e_c[k + BG_NG] : 0.0;
-  const double sr = G.isc_rho, sm = G.isc_m, se = G.isc_e, sb = G.isc_b;   // to scaled units (exact)
-  float drho = d2f_bits((U[p] - b.rho) * sr);
-  float m0 = d2f_bits(U[pl + p] * sm), m1 = d2f_bits(U[2 * pl + p] * sm), m2 = d2f_bits(U[3 * pl + p] * sm);
-  float dE = d2f_bits((U[4 * pl + p] - ehat) * se);
-  float bxl = d2f_bits(Bf[p] * sb), bxh = d2f_bits(Bf[p + 1] * sb);
-  float byl = d2f_bits(Bf[pl + p] * sb), byh = d2f_bits(Bf[pl + p + G.sy] * sb);
-  float bzl = d2f_bits(Bf[2 * pl + p] * sb), bzh = d2f_bits(Bf[2 * pl + p + G.sz] * sb);
+  // to scaled units: powers of two folded into the conversion (exact)
+  const int kr = -G.e_rho, km = -G.e_m, ke = -G.e_e, kb = -G.e_b;
+  float drho = d2f_scaled(U[p] - b.rho, kr);
+  float m0 = d2f_scaled(U[pl + p], km), m1 = d2f_scaled(U[2 * pl + p], km), m2 = d2f_scaled(U[3 * pl + p], km);
+  float dE = d2f_scaled(U[4 * pl + p] - ehat, ke);
+  float bxl = d2f_scaled(Bf[p], kb), bxh = d2f_scaled(Bf[p + 1], kb);
+  float byl = d2f_scaled(Bf[pl + p], kb), byh = d2f_scaled(Bf[pl + p + G.sy], kb);
+  float bzl = d2f_scaled(Bf[2 * pl + p], kb), bzh = d2f_scaled(Bf[2 * pl + p + G.sz], kb);
   if (dU) {
     drho += dU[p];
     m0 += dU[pl + p]; m1 += dU[2 * pl + p]; m2 += dU[3 * pl + p];
@@ -60,7 +61,7 @@ __device__ __forceinline__ void cell_prims_mx(const DevGeo &G, const double *__r
 #pragma unroll
   for (int l = 0; l < PHL_NSPEC_MAX; ++l) {
     if (l >= G.nspec) continue;
-    float rx = d2f_bits(U[(U_X0 + l) * pl + p] * sr);
+    float rx = d2f_scaled(U[(U_X0 + l) * pl + p], kr);
     if (dU) rx += dU[(U_X0 + l) * pl + p];
     w[W_X0 + l] = rx * ir;
   }
@@ -102,7 +103,7 @@ struct StageMx {
 };
 
 __device__ __forceinline__ void k_update_cells_mx_at(long tl, const DevGeo &G, const Box &box, StageMx S) {
-  const float dt = (float)(*S.dt * G.isc_t);
+  const float dt = d2f_scaled(*S.dt, -G.e_t);
   {
     int c[3];
     if (!cell_at(box, tl, c)) return;
@@ -139,7 +140,7 @@ __device__ __forceinline__ void k_update_cells_mx_at(long tl, const DevGeo &G, c
       const long q = v * pl + ps;
       const float din = S.first ? 0.0f : S.dU[q];
       const float dout = S.b * (din - dt * r[v]);
-      if (S.last) S.U[q] += f2d_bits(dout) * usc(G, v);
+      if (S.last) S.U[q] += f2d_scaled(dout, uexp(G, v));
       else S.dU[q] = dout;
     }
   }
@@ -148,7 +149,7 @@ __device__ __forceinline__ void k_update_cells_mx_at(long tl, const DevGeo &G, c
 template <int D>
 __device__ __forceinline__ void k_update_faces_mx_at(long tl, const DevGeo &G, const Box &box, StageMx S) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
-  const float dt = (float)(*S.dt * G.isc_t);
+  const float dt = d2f_scaled(*S.dt, -G.e_t);
   {
     int c[3];
     if (!cell_at(box, tl, c)) return;
@@ -162,7 +163,7 @@ __device__ __forceinline__ void k_update_faces_mx_at(long tl, const DevGeo &G, c
     const long q = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
     const float din = S.first ? 0.0f : S.dB[q];
     const float dout = S.b * (din - dt * r);
-    if (S.last) S.B[q] += f2d_bits(dout) * G.sc_b;
+    if (S.last) S.B[q] += f2d_scaled(dout, G.e_b);
     else S.dB[q] = dout;
   }
 }

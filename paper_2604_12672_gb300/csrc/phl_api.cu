@@ -173,6 +173,8 @@ GridView grid_view(phl_grid *g) {
   v.stream = g->stream;
   v.steps = &g->steps;
   v.mixed = g->mixed;
+  v.tmapW = g->fused ? g->tmapW : nullptr;
+  v.fused = g->fused;
   return v;
 }
 }  // namespace phl
@@ -270,6 +272,8 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     const double L_s = std::ldexp(1.0, (int)std::lround(std::log2(dx_min)));
     const double t_s = L_s / v_s;
     G.sc_rho = rho_s; G.sc_m = rho_s * v_s; G.sc_e = P_s; G.sc_b = B_s; G.sc_t = t_s;
+    G.e_rho = 2 * eb; G.e_m = ea + eb; G.e_e = 2 * ea; G.e_b = ea;
+    G.e_t = (int)std::lround(std::log2(dx_min)) - (ea - eb);
     G.isc_rho = 1.0 / rho_s; G.isc_m = 1.0 / (rho_s * v_s); G.isc_e = 1.0 / P_s; G.isc_b = 1.0 / B_s;
     G.isc_t = 1.0 / t_s; G.isc_v = 1.0 / v_s;
     for (int k = 0; k < 3; ++k) {
@@ -316,6 +320,8 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     AL(&g->fmax, 1);
     if (fused_stage_ok(G)) {
       if (make_fused_tmap(G, g->Wf, g->tmapW) != PHL_OK) { phl_destroy(g); return PHL_ECUDA; }
+      const cudaError_t e = fused_init();
+      if (e != cudaSuccess) { phl_destroy(g); return cuda_fail(e, "fused stage set-up"); }
       g->fused = PHL_FUSED_DEFAULT;
     }
   }

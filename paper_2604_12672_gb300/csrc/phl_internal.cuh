@@ -64,6 +64,7 @@ struct DevGeo {
   // far inside the FP32 range.  Multiplying by a power of two is exact, so the
   // scaling changes no rounding.  sc_* turn scaled values into physical ones.
   double sc_rho, sc_m, sc_e, sc_b, sc_t;
+  int e_rho, e_m, e_e, e_b, e_t;   // sc_x = 2^e_x (applied to the exponent field by d2f_scaled / f2d_scaled)
   double isc_rho, isc_m, isc_e, isc_b, isc_t, isc_v;
   float idxf[3], gf[3], gammaf, gm1f, machf, epsf;   // idxf, gf in scaled units
   const float *bgf_rho_c, *bgf_p_c, *bgf_rho_f, *bgf_p_f;   // null without background
@@ -199,6 +200,33 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// The same conversions with an exact power-of-two scale folded into the
+// exponent rebias: d2f_scaled(x, k) == d2f_bits(x * 2^k) and f2d_scaled(f, k)
+// == f2d_bits(f) * 2^k bit for bit (for |k| < 800 and results inside the
+// FP64 range), without the FP64 multiply.  The mixed form's unit scales are
+// powers of two, so its FP64 <-> FP32 boundary costs no FP64 arithmetic.
+__device__ __forceinline__ float d2f_scaled(double x, int k) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u, a = hi & 0x7fffffffu;
+  const unsigned rb = (unsigned)(896 - k) << 20;
+  unsigned t = __funnelshift_l(lo, a - rb, 3);
+  t += (lo >> 28) & 1u;
+  t = (a < rb + (1u << 20)) ? 0u : t;
+  t = (a >= rb + (255u << 20))
+          ? (0x7f800000u | ((a > 0x7ff00000u || (a == 0x7ff00000u && lo)) ? 0x400000u : 0u))
+          : t;
+  return __uint_as_float(t | sign);
+}
+__device__ __forceinline__ double f2d_scaled(float f, int k) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi = sign | ((e + (unsigned)(896 + k)) << 20) | (m >> 3);
+  unsigned lo = m << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 255u) hi = sign | 0x7ff00000u | (m >> 3);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // Kernel classes for the optional per-kernel event timing.
 enum KClass {
   KC_PRIM = 0, KC_FLAG_RAW, KC_FLAG_DILATE, KC_FLUX_X, KC_FLUX_Y, KC_FLUX_Z, KC_EMF, KC_UPDATE_CELLS,
@@ -262,6 +290,7 @@ bool fused_stage_ok(const DevGeo &G);
 constexpr int PHL_FUSED_SHAPES = 4;    // launch shapes of the tile kernel
 constexpr int PHL_FUSED_DEFAULT = 2;   // the shape used unless phl_set_fused picks another (288 threads, 3 CTAs/SM, phased)
 int make_fused_tmap(const DevGeo &G, const float *W, void *tmap128);
+cudaError_t fused_init();   // shared-memory limits of the tile kernels (once per process)
 void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool last, double b, cudaStream_t s,
                        int *nl, Prof *prof);
 
@@ -277,6 +306,8 @@ struct GridView {
   cudaStream_t stream;
   long *steps;
   bool mixed;
+  const void *tmapW;           // TMA descriptor of W when the grid runs the fused stage
+  int fused;                   // its launch shape (0: per-direction kernels)
 };
 GridView grid_view(::phl_grid *g);
 
@@ -323,6 +354,9 @@ __device__ __forceinline__ void write_aux(const DevGeo &G, float *W, long q, con
 // Scale of conserved variable v of the mixed form (rho, m, E, rho X).
 __host__ __device__ __forceinline__ double usc(const DevGeo &G, int v) {
   return (v >= 1 && v <= 3) ? G.sc_m : (v == 4 ? G.sc_e : G.sc_rho);
+}
+__host__ __device__ __forceinline__ int uexp(const DevGeo &G, int v) {
+  return (v >= 1 && v <= 3) ? G.e_m : (v == 4 ? G.e_e : G.e_rho);
 }
 __host__ __device__ __forceinline__ double iusc(const DevGeo &G, int v) {
   return (v >= 1 && v <= 3) ? G.isc_m : (v == 4 ? G.isc_e : G.isc_rho);

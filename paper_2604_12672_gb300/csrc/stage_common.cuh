@@ -243,7 +243,7 @@ __device__ __forceinline__ void flux_face(const DevGeo &G, const int *c, long pR
   const long qb = (long)D * G.plane + sidx(G, s[0], s[1], s[2]);
   R bn;
   if constexpr (sizeof(R) == 4) {   // B^n + dB in scaled units
-    const float b0 = d2f_bits(Bf[qb] * G.isc_b);
+    const float b0 = d2f_scaled(Bf[qb], -G.e_b);
     bn = dB ? b0 + dB[qb] : b0;
   }
   else bn = (R)Bf[qb];

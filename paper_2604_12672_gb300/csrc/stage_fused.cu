@@ -128,7 +128,7 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
         bf.p + wr[RD_P] > 0.0f))
     atomicOr(dflag, FLAG_NEG);
   const long qb = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
-  const float b0 = d2f_bits(S.B[qb] * G.isc_b);
+  const float b0 = d2f_scaled(S.B[qb], -G.e_b);
   const float bn = S.first ? b0 : b0 + S.dB[qb];
   const long pR = widx(G, c[0], c[1], c[2]);
   int solver = G.riemann;
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(NT, MINB)
   }
 
   // R = sum_d (F_d(+) - F_d(-)) / dx_d - (S - S_hat), then the RK increment
-  const float dt = (float)(*S.dt * G.isc_t);
+  const float dt = d2f_scaled(*S.dt, -G.e_t);
 #pragma unroll
   for (int m = 0; m < CPT; ++m) {
     const int cc = tid + m * NT;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(NT, MINB)
       const long q = v * G.plane + ps;
       const float din = S.first ? 0.0f : S.dU[q];
       const float dout = S.b * (din - dt * r[v]);
-      if (S.last) S.U[q] += f2d_bits(dout) * usc(G, v);
+      if (S.last) S.U[q] += f2d_scaled(dout, uexp(G, v));
       else S.dU[q] = dout;
     }
   }
@@ -466,14 +466,14 @@ __device__ __forceinline__ void face_update(const DevGeo &G, const int *c, const
   const long q = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
   const float din = S.first ? 0.0f : S.dB[q];
   const float dout = S.b * (din - dt * r);
-  if (S.last) S.B[q] += f2d_bits(dout) * G.sc_b;
+  if (S.last) S.B[q] += f2d_scaled(dout, G.e_b);
   else S.dB[q] = dout;
 }
 
 __global__ void k_update_faces3(DevGeo G, Box box, StageMx S) {
   int c[3];
   if (!cell3(box, c)) return;
-  const float dt = (float)(*S.dt * G.isc_t);
+  const float dt = d2f_scaled(*S.dt, -G.e_t);
   if (c[1] < G.n[1] && c[2] < G.n[2]) face_update<0>(G, c, S, dt);
   if (c[0] < G.n[0] && c[2] < G.n[2]) face_update<1>(G, c, S, dt);
   if (c[0] < G.n[0] && c[1] < G.n[1]) face_update<2>(G, c, S, dt);
@@ -495,6 +495,24 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 }
 
 }  // namespace
+
+cudaError_t fused_init() {
+  static cudaError_t done = cudaErrorNotReady;
+  if (done == cudaSuccess) return done;
+  cudaError_t e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes(false));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<288, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<256, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<384, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(true));
+  done = e;
+  return e;
+}
 
 bool fused_stage_ok(const DevGeo &G) {
   return G.eos == PHL_EOS_IDEAL && G.nspec == 0 && G.wstr == 8 && G.act[0] && G.act[1] && G.act[2];
@@ -541,12 +559,6 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   // launch shapes: (threads, min CTAs per SM, phased)
 #define PHL_FUSED(NT, MB, PH)                                                                                   \
   do {                                                                                                         \
-    static bool attr = false;                                                                                  \
-    if (!attr) {                                                                                               \
-      cudaFuncSetAttribute(k_flux_update_mx<NT, MB, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
-                           (int)smem_bytes(PH));                                                               \
-      attr = true;                                                                                             \
-    }                                                                                                          \
     PHL_LAUNCH(KC_FLUX_UPDATE, prof, s,                                                                        \
                (k_flux_update_mx<NT, MB, PH><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0], M.F[1],     \
                                                                              M.F[2], ntx, nty, M.dflag)));     \

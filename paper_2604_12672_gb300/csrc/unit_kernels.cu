@@ -23,7 +23,33 @@ __global__ void k_riemann_batch(long n, const double *wl, const double *wr, cons
   }
 }
 
+__global__ void k_convert_batch(long n, const double *x, int k, float *f, double *back) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const float v = d2f_scaled(x[t], k);
+    f[t] = v;
+    back[t] = f2d_scaled(v, -k);
+  }
+}
+
 }  // namespace
+
+extern "C" phl_status phl_convert_batch(long n, const double *x, int k, float *f, double *back) {
+  if (n < 0 || k <= -800 || k >= 800) return PHL_EINVAL;
+  if (n == 0) return PHL_OK;
+  if (!x || !f || !back) return PHL_EINVAL;
+  char *d = nullptr;
+  if (cudaMalloc(&d, n * (2 * sizeof(double) + sizeof(float))) != cudaSuccess) { cudaGetLastError(); return PHL_ENOMEM; }
+  double *dx = (double *)d, *db = dx + n;
+  float *df = (float *)(db + n);
+  cudaMemcpy(dx, x, n * sizeof(double), cudaMemcpyHostToDevice);
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_convert_batch<<<blocks, 256>>>(n, dx, k, df, db);
+  cudaError_t e = cudaMemcpy(f, df, n * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(back, db, n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) { cudaGetLastError(); return PHL_ECUDA; }
+  return PHL_OK;
+}
 
 extern "C" phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const double *bn,
                                         const double *bg, int nspec, int solver, double mach_thr,

@@ -104,3 +104,31 @@ def test_periodic_3d_box_one_step(P):
     for k in ("bx", "by", "bz"):
         d = np.abs(st[k] - ref[k]).max()
         assert d <= 1e-15, (k, d)
+
+
+@pytest.mark.parametrize("k", [0, -20, 37, -80])
+def test_scaled_conversions_match_ieee(P, k):
+    """d2f_scaled / f2d_scaled, the mixed form's FP64 <-> FP32 boundary with a
+    power-of-two unit folded into the exponent: x * 2^k rounded to nearest
+    FP32 (IEEE ties-to-even and the kernel's ties-away agree off exact ties,
+    which random doubles never hit), subnormal results flushed to zero,
+    overflow to inf, NaN kept; the way back is exact."""
+    rng = np.random.default_rng(100 + k)
+    scale = 2.0 ** -k
+    x = np.concatenate([
+        rng.standard_normal(20000) * scale * 10.0 ** rng.uniform(-30, 30, 20000),
+        np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan]) * scale,
+        np.array([1e-50, -1e-45, 2.0 ** -130, 2.0 ** 129, -2.0 ** 200]) * scale,
+    ])
+    f, back = P.convert_batch(x, k)
+    with np.errstate(over="ignore", under="ignore", invalid="ignore"):
+        ref = (x * 2.0 ** k).astype(np.float32)
+    tiny = np.abs(ref) < np.float32(2.0 ** -126)
+    ref = np.where(tiny, np.copysign(np.float32(0.0), ref), ref)
+    nan = np.isnan(x)
+    assert np.all(np.isnan(f[nan]))
+    assert np.array_equal(f[~nan], ref[~nan])
+    assert np.array_equal(np.signbit(f[~nan]), np.signbit(ref[~nan]))
+    with np.errstate(over="ignore"):
+        expect_back = f.astype(np.float64) * 2.0 ** -k
+    assert np.array_equal(back[~nan], expect_back[~nan])
