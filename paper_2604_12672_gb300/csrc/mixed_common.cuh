@@ -86,9 +86,15 @@ __device__ __forceinline__ void k_prim_mx_at(long tl, const DevGeo &G, const Box
     for (int d = 0; d < 3; ++d)
       if (fl[d]) { w[W_VX + d] = -w[W_VX + d]; w[W_BX + d] = -w[W_BX + d]; }
     const long q = widx(G, c[0], c[1], c[2]);
+    if (G.wstr == 8) {   // ideal gas without species: the two float4 planes, one 16-byte store each
+      float4 *W4 = reinterpret_cast<float4 *>(W);
+      W4[q] = make_float4(w[W_RHO], w[W_VX], w[W_VY], w[W_VZ]);
+      W4[G.wtot + q] = make_float4(w[W_BX], w[W_BY], w[W_BZ], w[W_P]);
+    } else {
 #pragma unroll
-    for (int v = 0; v < NW_MAX; ++v)
-      if (v < G.nw && v < G.wstr) W[wix<float>(G, v, q)] = w[v];
+      for (int v = 0; v < NW_MAX; ++v)
+        if (v < G.nw && v < G.wstr) W[wix<float>(G, v, q)] = w[v];
+    }
     write_aux(G, W, q, w);
   }
 }

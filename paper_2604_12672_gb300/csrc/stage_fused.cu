@@ -339,50 +339,75 @@ __global__ void __launch_bounds__(NT, MINB)
 }
 
 // 5^3 dilation of the raw shock flags (Sect. 2.7) for one 8^3 tile of
-// interior cells in one pass: the raw flags of the tile and two neighbours on
-// every side are staged in shared memory (beyond a periodic boundary they
-// wrap, beyond any other boundary they count as unflagged), then ORed along x,
-// y and z in turn (the OR over a box is the nested ORs over its axes).
+// interior cells in one pass, eight flags (one byte each) per 64-bit word: the
+// raw flags of x0-4 .. x0+11 for every row of the tile and its two neighbour
+// rows on each side are staged in shared memory as two words, then ORed along
+// x (byte shifts of the 16-byte window), y and z (word ORs) in turn -- the OR
+// over a box is the nested ORs over its axes.  Beyond a periodic boundary the
+// flags wrap; beyond any other boundary they count as unflagged.
 __global__ void __launch_bounds__(256) k_flag_dilate3(DevGeo G, const uint8_t *__restrict__ raw,
                                                      uint8_t *__restrict__ dil, int ntx, int nty) {
-  __shared__ uint8_t r0[HZ][HY][HX], r1[HZ][HY][FX], r2[HZ][FY][FX];
+  __shared__ unsigned long long r0[HZ * HY][2];
+  __shared__ unsigned long long r1[HZ * HY], r2[HZ * FY];
   int t = blockIdx.x;
   const int tx = t % ntx;
   t /= ntx;
   const int ty = t % nty, tz = t / nty;
-  const int o[3] = {tx * FX - NGW, ty * FY - NGW, tz * FZ - NGW};
-  for (int q = threadIdx.x; q < NHC; q += blockDim.x) {
-    const int l[3] = {q % HX, (q / HX) % HY, q / (HX * HY)};
-    int g[3];
+  const int x0 = tx * FX, y0 = ty * FY, z0 = tz * FZ;
+  const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+  const int xs = x0 - 4;
+  const bool wide = (nx % 8) == 0 && xs >= 0 && xs + 16 <= nx;   // aligned window inside the row
+  const bool px = G.bc[0][0] == 0, py = G.bc[1][0] == 0, pz = G.bc[2][0] == 0;
+  for (int q = threadIdx.x; q < HZ * HY * 4; q += blockDim.x) {
+    const int w = q & 3, row = q >> 2;
+    int y = y0 - NGW + row % HY, z = z0 - NGW + row / HY;
     bool in = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      int x = o[d] + l[d];
-      if (x < 0 || x >= G.n[d]) {
-        if (G.bc[d][0] == 0) x = ((x % G.n[d]) + G.n[d]) % G.n[d];
-        else in = false;
+    if (y < 0 || y >= ny) { if (py) y = (y % ny + ny) % ny; else in = false; }
+    if (z < 0 || z >= nz) { if (pz) z = (z % nz + nz) % nz; else in = false; }
+    unsigned v = 0u;
+    if (in) {
+      const uint8_t *rr = raw + (long)nx * (y + (long)ny * z);
+      if (wide) {
+        v = *reinterpret_cast<const unsigned *>(rr + xs + 4 * w);
+      } else {
+        for (int bb = 0; bb < 4; ++bb) {
+          int x = xs + 4 * w + bb;
+          bool ok = true;
+          if (x < 0 || x >= nx) { if (px) x = (x % nx + nx) % nx; else ok = false; }
+          if (ok) v |= (unsigned)rr[x] << (8 * bb);
+        }
       }
-      g[d] = x;
     }
-    r0[l[2]][l[1]][l[0]] = in ? raw[g[0] + (long)G.n[0] * (g[1] + (long)G.n[1] * g[2])] : (uint8_t)0;
+    reinterpret_cast<unsigned *>(&r0[row][0])[w] = v;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < HZ * HY * FX; q += blockDim.x) {
-    const int x = q % FX, y = (q / FX) % HY, z = q / (FX * HY);
-    r1[z][y][x] = r0[z][y][x] | r0[z][y][x + 1] | r0[z][y][x + 2] | r0[z][y][x + 3] | r0[z][y][x + 4];
+  for (int row = threadIdx.x; row < HZ * HY; row += blockDim.x) {
+    // output byte j (x = x0 + j) ORs window bytes j+2 .. j+6
+    const unsigned long long lo = r0[row][0], hi = r0[row][1];
+    unsigned long long o = 0ull;
+#pragma unroll
+    for (int sh = 2; sh <= 6; ++sh) o |= (lo >> (8 * sh)) | (hi << (64 - 8 * sh));
+    r1[row] = o;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < HZ * FY * FX; q += blockDim.x) {
-    const int x = q % FX, y = (q / FX) % FY, z = q / (FX * FY);
-    r2[z][y][x] = r1[z][y][x] | r1[z][y + 1][x] | r1[z][y + 2][x] | r1[z][y + 3][x] | r1[z][y + 4][x];
+  for (int q = threadIdx.x; q < HZ * FY; q += blockDim.x) {
+    const int y = q % FY, z = q / FY;
+    const unsigned long long *c = &r1[z * HY + y];
+    r2[q] = c[0] | c[1] | c[2] | c[3] | c[4];
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < FX * FY * FZ; q += blockDim.x) {
-    const int x = q % FX, y = (q / FX) % FY, z = q / (FX * FY);
-    const int c0 = o[0] + NGW + x, c1 = o[1] + NGW + y, c2 = o[2] + NGW + z;
-    if (c0 >= G.n[0] || c1 >= G.n[1] || c2 >= G.n[2]) continue;
-    dil[c0 + (long)G.n[0] * (c1 + (long)G.n[1] * c2)] =
-        r2[z][y][x] | r2[z + 1][y][x] | r2[z + 2][y][x] | r2[z + 3][y][x] | r2[z + 4][y][x];
+  for (int q = threadIdx.x; q < FZ * FY; q += blockDim.x) {
+    const int y = q % FY, z = q / FY;
+    const int c1 = y0 + y, c2 = z0 + z;
+    if (c1 >= ny || c2 >= nz) continue;
+    const unsigned long long o = r2[z * FY + y] | r2[(z + 1) * FY + y] | r2[(z + 2) * FY + y] |
+                                 r2[(z + 3) * FY + y] | r2[(z + 4) * FY + y];
+    uint8_t *d = dil + x0 + (long)nx * (c1 + (long)ny * c2);
+    if ((nx % 8) == 0 && x0 + 8 <= nx) {
+      *reinterpret_cast<unsigned long long *>(d) = o;
+    } else {
+      for (int j = 0; j < 8 && x0 + j < nx; ++j) d[j] = (uint8_t)(o >> (8 * j));
+    }
   }
 }
 
@@ -394,36 +419,33 @@ __global__ void __launch_bounds__(256) k_flag_dilate3(DevGeo G, const uint8_t *_
 // behind a reflecting wall feed only wall edges, whose EMF is zero (u_n = B_n
 // = 0 there), so no mirror signs are needed.
 template <int D>
-__device__ __forceinline__ float emf_edge(const DevGeo &G, const int *c, const float *__restrict__ W,
-                                          const float *__restrict__ FA, const float *__restrict__ FB) {
+__device__ __forceinline__ float emf_edge(const DevGeo &G, const int *c, bool interior, long p,
+                                          const float *__restrict__ W, const float *__restrict__ FA,
+                                          const float *__restrict__ FB) {
   constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
-  bool fl;
-  const int bm = cell_src(c[B] - 1, G.n[B], G.bc[B][0], G.bc[B][1], fl);
-  const int b0 = cell_src(c[B], G.n[B], G.bc[B][0], G.bc[B][1], fl);
-  const int am = cell_src(c[A] - 1, G.n[A], G.bc[A][0], G.bc[A][1], fl);
-  const int a0 = cell_src(c[A], G.n[A], G.bc[A][0], G.bc[A][1], fl);
-  int e[3] = {c[0], c[1], c[2]};
-  e[B] = b0;
-  const long pa1 = widx(G, e[0], e[1], e[2]);
-  e[B] = bm;
-  const long pa0 = widx(G, e[0], e[1], e[2]);
-  e[B] = c[B];
-  e[A] = a0;
-  const long pb1 = widx(G, e[0], e[1], e[2]);
-  e[A] = am;
-  const long pb0 = widx(G, e[0], e[1], e[2]);
-  const long p = widx(G, c[0], c[1], c[2]);
-  const long wt = G.wtot;
   const long sa = wstride(G, A), sb = wstride(G, B);
-  const float *fab = FA + (F_BX + B) * wt;
-  const float *fba = FB + (F_BX + A) * wt;
+  long pa1 = p, pa0 = p - sb, pb1 = p, pb0 = p - sa;   // faces of an interior site
+  if (!interior) {   // rows beyond the boundary read the interior rows their data come from
+    bool fl;
+    const int bm = cell_src(c[B] - 1, G.n[B], G.bc[B][0], G.bc[B][1], fl);
+    const int b0 = cell_src(c[B], G.n[B], G.bc[B][0], G.bc[B][1], fl);
+    const int am = cell_src(c[A] - 1, G.n[A], G.bc[A][0], G.bc[A][1], fl);
+    const int a0 = cell_src(c[A], G.n[A], G.bc[A][0], G.bc[A][1], fl);
+    pa1 = p + (b0 - c[B]) * sb;
+    pa0 = p + (bm - c[B]) * sb;
+    pb1 = p + (a0 - c[A]) * sa;
+    pb0 = p + (am - c[A]) * sa;
+  }
+  const long wt = G.wtot;
+  const float *fab = FA + (F_BX + B) * wt;   // F_a(B_b) on a-faces
+  const float *fba = FB + (F_BX + A) * wt;   // F_b(B_a) on b-faces
   const float *ua = FA + (long)G.nf * wt, *ub = FB + (long)G.nf * wt;
   const float Ea1 = -fab[pa1], Ea0 = -fab[pa0];
   const float Eb1 = fba[pb1], Eb0 = fba[pb0];
   const float ma1 = ua[pa1], ma0 = ua[pa0];
   const float mb1 = ub[pb1], mb0 = ub[pb0];
-  auto ec = [&](long q) -> float { return W[waux(G, AUX_E + D, q)]; };
-  const float E00 = ec(p - sa - sb), E10 = ec(p - sb), E01 = ec(p - sa), E11 = ec(p);
+  const float *ecell = W + waux(G, AUX_E + D, 0);
+  const float E00 = ecell[p - sa - sb], E10 = ecell[p - sb], E01 = ecell[p - sa], E11 = ecell[p];
   const float lo_l = Eb0 - E00, lo_r = Eb1 - E10;
   const float up_l = E01 - Eb0, up_r = E11 - Eb1;
   const float h = 0.5f, q4 = 0.25f;
@@ -434,23 +456,26 @@ __device__ __forceinline__ float emf_edge(const DevGeo &G, const int *c, const f
   const float dle = mb0 > 0.0f ? le_d : (mb0 < 0.0f ? le_u : h * (le_d + le_u));
   const float dri = mb1 > 0.0f ? ri_d : (mb1 < 0.0f ? ri_u : h * (ri_d + ri_u));
   float v = q4 * (Ea1 + Ea0 + Eb1 + Eb0) + q4 * (dlo - dup) + q4 * (dle - dri);
-  if ((c[A] == 0 && G.bc[A][0] == 1) || (c[A] == G.n[A] && G.bc[A][1] == 1) || (c[B] == 0 && G.bc[B][0] == 1) ||
-      (c[B] == G.n[B] && G.bc[B][1] == 1))
+  if (!interior && ((c[A] == 0 && G.bc[A][0] == 1) || (c[A] == G.n[A] && G.bc[A][1] == 1) ||
+                    (c[B] == 0 && G.bc[B][0] == 1) || (c[B] == G.n[B] && G.bc[B][1] == 1)))
     v = 0.0f;
   return v;
 }
 
 // All three edge EMFs at the lower corners of site c in [0, n0] x [0, n1] x
-// [0, n2] (an edge along D exists for c_D < n_D).
+// [0, n2] (an edge along D exists for c_D < n_D).  Sites away from every
+// boundary (all faces and cells they touch are interior) skip the ghost
+// mapping.
 __global__ void k_emf3(DevGeo G, Box box, const float *__restrict__ W, const float *__restrict__ F0,
                        const float *__restrict__ F1, const float *__restrict__ F2, float *__restrict__ E) {
   int c[3];
   if (!cell3(box, c)) return;
   const long p = widx(G, c[0], c[1], c[2]);
   const long wt = G.wtot;
-  if (c[0] < G.n[0]) E[p] = emf_edge<0>(G, c, W, F1, F2);
-  if (c[1] < G.n[1]) E[wt + p] = emf_edge<1>(G, c, W, F2, F0);
-  if (c[2] < G.n[2]) E[2 * wt + p] = emf_edge<2>(G, c, W, F0, F1);
+  const bool interior = c[0] >= 1 && c[0] < G.n[0] && c[1] >= 1 && c[1] < G.n[1] && c[2] >= 1 && c[2] < G.n[2];
+  if (c[0] < G.n[0]) E[p] = emf_edge<0>(G, c, interior, p, W, F1, F2);
+  if (c[1] < G.n[1]) E[wt + p] = emf_edge<1>(G, c, interior, p, W, F2, F0);
+  if (c[2] < G.n[2]) E[2 * wt + p] = emf_edge<2>(G, c, interior, p, W, F0, F1);
 }
 
 // Face update of the normal field on the D-face at site c from the curl of
