@@ -35,16 +35,20 @@ constexpr int NXF = (FX + 1) * FY * FZ, NYF = FX * (FY + 1) * FZ, NZF = FX * FY 
 constexpr int NFACE = NXF + NYF + NZF;
 constexpr int FTPB = 256;
 constexpr unsigned W_TILE_BYTES = 2u * NHC * 16u;
+static_assert(NXF % 32 == 0 && NYF % 32 == 0, "a warp's faces must share one direction");
 
-// Shared memory of a tile: the barrier first, then the staged W (128-byte
-// aligned for the TMA destination), then the face buffer, which the phased
-// variant sizes for one direction's faces only (its launch requests less).
+// Shared memory of a tile: the barrier, the tile's background profiles and
+// shock flags, then the staged W (128-byte aligned for the TMA destination),
+// then the face buffer, which the phased variant sizes for one direction's
+// faces only (its launch requests less).
 struct FusedSmem {
-  unsigned long long bar;  // TMA completion barrier
-  unsigned long long pad[15];
-  float4 w[2][NHC];        // staged W: (drho, vx, vy, vz) and (Bx, By, Bz, dP) per cell
-  float f[5][NFACE];       // face fluxes, normal frame (rho, m_n, m_t1, m_t2, E); the
-                           // kernel indexes it flat with row stride NXF (phased) or NFACE
+  unsigned long long bar;              // TMA completion barrier
+  float bgc[2][FZ];                    // background rho, P at the tile's cell centres (scaled units)
+  float bgf[2][FZ + 1];                // the same at its z-faces
+  uint8_t flg[FZ + 2][FY + 2][FX + 2]; // dilated shock flags of cells -1 .. F (a ghost carries its source's)
+  alignas(128) float4 w[2][NHC];       // staged W: (drho, vx, vy, vz) and (Bx, By, Bz, dP) per cell
+  float f[5][NFACE];                   // face fluxes, normal frame (rho, m_n, m_t1, m_t2, E); the
+                                       // kernel indexes it flat with row stride NXF (phased) or NFACE
 };
 static_assert(offsetof(FusedSmem, w) % 128 == 0, "TMA destination alignment");
 constexpr size_t smem_bytes(bool phased) {
@@ -81,12 +85,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
 }
 
 // Flux of the D-face at the lower side of staged cell s2 (its right cell),
-// global cell c.  Returns the five fluid components in out[] and stores the
-// EMF inputs when the tile owns the face.
-__device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int D, int s2,
-                                           const int *c, int cD, bool own, const uint8_t *__restrict__ flag,
-                                           float *__restrict__ Fd, const GasK<float> &K, float *out, int *dflag) {
-  const int sD = D == 0 ? 1 : (D == 1 ? HX : HX * HY);
+// tile cell (i, j, k), global cell c.  Returns the five fluid components in
+// out[] and stores the EMF inputs when the tile owns the face.
+template <int D>
+__device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int s2, int i,
+                                           int j, int k, const int *c, bool own, float *__restrict__ Fd,
+                                           const GasK<float> &K, float *out, int *dflag) {
+  constexpr int sD = D == 0 ? 1 : (D == 1 ? HX : HX * HY);
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
   float ql[8], qr[8];
   {
     float4 a[4], b[4];
@@ -103,49 +109,41 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
     plm(W_VX, a[0].y, a[1].y, a[2].y, a[3].y);
     plm(W_VY, a[0].z, a[1].z, a[2].z, a[3].z);
     plm(W_VZ, a[0].w, a[1].w, a[2].w, a[3].w);
-    plm(W_BX, b[0].x, b[1].x, b[2].x, b[3].x);
-    plm(W_BY, b[0].y, b[1].y, b[2].y, b[3].y);
-    plm(W_BZ, b[0].z, b[1].z, b[2].z, b[3].z);
+    if (D != 0) plm(W_BX, b[0].x, b[1].x, b[2].x, b[3].x);   // the normal field is not reconstructed
+    if (D != 1) plm(W_BY, b[0].y, b[1].y, b[2].y, b[3].y);
+    if (D != 2) plm(W_BZ, b[0].z, b[1].z, b[2].z, b[3].z);
     plm(W_P, b[0].w, b[1].w, b[2].w, b[3].w);
   }
   // normal frame (n, t1, t2) = (D, D+1, D+2 mod 3)
   float wl[W_X0], wr[W_X0];
   auto frame = [&](const float *q, float *w) {
     w[RD_RHO] = q[W_RHO];
-    w[RD_UN] = D == 0 ? q[W_VX] : (D == 1 ? q[W_VY] : q[W_VZ]);
-    w[RD_UT1] = D == 0 ? q[W_VY] : (D == 1 ? q[W_VZ] : q[W_VX]);
-    w[RD_UT2] = D == 0 ? q[W_VZ] : (D == 1 ? q[W_VX] : q[W_VY]);
-    w[RD_BT1] = D == 0 ? q[W_BY] : (D == 1 ? q[W_BZ] : q[W_BX]);
-    w[RD_BT2] = D == 0 ? q[W_BZ] : (D == 1 ? q[W_BX] : q[W_BY]);
+    w[RD_UN] = q[W_VX + D];
+    w[RD_UT1] = q[W_VX + T1];
+    w[RD_UT2] = q[W_VX + T2];
+    w[RD_BT1] = q[W_BX + T1];
+    w[RD_BT2] = q[W_BX + T2];
     w[RD_P] = q[W_P];
     w[RD_GE] = 0.0f;
     w[RD_GC] = 0.0f;
   };
   frame(ql, wl);
   frame(qr, wr);
-  const BgT<float> bf = D == 2 ? bg_zface_t<float>(G, c[2]) : bg_cell_t<float>(G, c[2]);
-  if (!(bf.rho + wl[RD_RHO] > 0.0f && bf.rho + wr[RD_RHO] > 0.0f && bf.p + wl[RD_P] > 0.0f &&
-        bf.p + wr[RD_P] > 0.0f))
+  const float brho = D == 2 ? sm.bgf[0][k] : sm.bgc[0][k], bp = D == 2 ? sm.bgf[1][k] : sm.bgc[1][k];
+  if (!(brho + wl[RD_RHO] > 0.0f && brho + wr[RD_RHO] > 0.0f && bp + wl[RD_P] > 0.0f && bp + wr[RD_P] > 0.0f))
     atomicOr(dflag, FLAG_NEG);
   const long qb = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
   const float b0 = d2f_scaled(S.B[qb], -G.e_b);
   const float bn = S.first ? b0 : b0 + S.dB[qb];
-  const long pR = widx(G, c[0], c[1], c[2]);
-  int solver = G.riemann;
-  if (flag) {   // dilated shock flags of the two cells (interior layout; a ghost cell carries its source's)
-    bool fl;
-    const int nD = G.n[D];
-    const int cl = cell_src(cD - 1, nD, G.bc[D][0], G.bc[D][1], fl);
-    const int cr = cell_src(cD, nD, G.bc[D][0], G.bc[D][1], fl);
-    const long base = (long)c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2]);
-    const long sD = D == 0 ? 1L : (D == 1 ? (long)G.n[0] : (long)G.n[0] * G.n[1]);
-    if (flag[base + (cl - cD) * sD] | flag[base + (cr - cD) * sD]) solver = SOLVER_HLL;
-  }
+  // dilated shock flags of the two cells; local cell (i, j, k) sits at flg[k+1][j+1][i+1]
+  const uint8_t *fr = &sm.flg[k + 1][j + 1][i + 1];
+  constexpr int fs = D == 0 ? 1 : (D == 1 ? FX + 2 : (FX + 2) * (FY + 2));
+  const int solver = (fr[0] | fr[-fs]) ? SOLVER_HLL : G.riemann;
   float fl[7];
   int up;
-  riemann_dev<float, 0, true>(wl, wr, bn, bf.rho, bf.p, bf.ge, bf.gc, 0, solver, G.machf, fl, up, K);
+  riemann_dev<float, 0, true>(wl, wr, bn, brho, bp, 0.0f, 0.0f, 0, solver, G.machf, fl, up, K);
   // reflecting wall face: a symmetry plane; only the normal-momentum flux survives
-  if ((cD == 0 && G.bc[D][0] == 1) || (cD == G.n[D] && G.bc[D][1] == 1)) {
+  if ((c[D] == 0 && G.bc[D][0] == 1) || (c[D] == G.n[D] && G.bc[D][1] == 1)) {
 #pragma unroll
     for (int q = 0; q < 7; ++q)
       if (q != RF_MN) fl[q] = 0.0f;
@@ -155,25 +153,19 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
   for (int q = 0; q < 5; ++q) out[q] = fl[q];
   if (own) {
     const long wt = G.wtot;
-    const int T1 = D == 2 ? 0 : D + 1, T2 = D == 0 ? 2 : D - 1;
+    const long pR = widx(G, c[0], c[1], c[2]);
     Fd[(F_BX + T1) * wt + pR] = fl[RF_BT1];
     Fd[(F_BX + T2) * wt + pR] = fl[RF_BT2];
     Fd[(long)G.nf * wt + pR] = (float)up;
   }
 }
 
-// Face index of the D-face at the lower side of tile cell (i, j, k) within the
-// faces of direction D (x fastest; the extent along D is one longer).
-__device__ __forceinline__ int dface(int D, int i, int j, int k) {
-  return D == 0 ? (k * FY + j) * (FX + 1) + i : (D == 1 ? (k * (FY + 1) + j) * FX + i : (k * FY + j) * FX + i);
-}
-__device__ __forceinline__ int dface_step(int D) { return D == 0 ? 1 : (D == 1 ? FX : FX * FY); }
-
 // Evaluates face f of direction D (its index among the tile's D-faces) and
 // returns the five fluid flux components (zeros outside the domain).
-__device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int D, int f,
-                                          int x0, int y0, int z0, const uint8_t *__restrict__ flag, float *F0,
-                                          float *F1, float *F2, const GasK<float> &K, float *out, int *dflag) {
+template <int D>
+__device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int f, int x0,
+                                          int y0, int z0, float *F0, float *F1, float *F2, const GasK<float> &K,
+                                          float *out, int *dflag) {
   int i, j, k;
   if (D == 0) { i = f % (FX + 1); const int r = f / (FX + 1); j = r % FY; k = r / FY; }
   else if (D == 1) { i = f % FX; const int r = f / FX; j = r % (FY + 1); k = r / (FY + 1); }
@@ -184,12 +176,44 @@ __device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, con
   for (int q = 0; q < 5; ++q) out[q] = 0.0f;
   if (!valid) return;
   const int s2 = ((k + NGW) * HY + (j + NGW)) * HX + (i + NGW);
+  constexpr int ext = D == 0 ? FX : (D == 1 ? FY : FZ);
   const int loc = D == 0 ? i : (D == 1 ? j : k);
-  const int ext = D == 0 ? FX : (D == 1 ? FY : FZ);
-  const int cD = D == 0 ? c[0] : (D == 1 ? c[1] : c[2]);
-  const bool own = loc < ext || cD == G.n[D];
+  const bool own = loc < ext || c[D] == G.n[D];
   float *Fd = D == 0 ? F0 : (D == 1 ? F1 : F2);
-  fused_face(G, S, sm, D, s2, c, cD, own, flag, Fd, K, out, dflag);
+  fused_face<D>(G, S, sm, s2, i, j, k, c, own, Fd, K, out, dflag);
+}
+
+// One direction's faces of the tile through the face buffer, then each
+// thread's running residuals of its cells (phased variant).
+template <int D, int NT, int CPT, int FS>
+__device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, FusedSmem &sm, float *fb, int tid,
+                                           int x0, int y0, int z0, float *F0, float *F1, float *F2,
+                                           const GasK<float> &K, float (*racc)[5], int *dflag) {
+  constexpr int qm[5][3] = {{0, 0, 0}, {1, 3, 2}, {2, 1, 3}, {3, 2, 1}, {4, 4, 4}};
+  constexpr int NC = FX * FY * FZ;
+  for (int f = tid; f < NXF; f += NT) {
+    float out[5];
+    tile_face<D>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
+  }
+  __syncthreads();
+  constexpr int st = D == 0 ? 1 : (D == 1 ? FX : FX * FY);
+  const float idd = G.idxf[D];
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) {
+    const int cc = tid + m * NT;
+    if (cc < NC) {
+      const int i = cc % FX, j = (cc / FX) % FY, k = cc / (FX * FY);
+      const int f0 = D == 0 ? (k * FY + j) * (FX + 1) + i : (D == 1 ? (k * (FY + 1) + j) * FX + i : (k * FY + j) * FX + i);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const int q = qm[v][D];
+        racc[m][v] += (fb[q * FS + f0 + st] - fb[q * FS + f0]) * idd;
+      }
+    }
+  }
+  __syncthreads();
 }
 
 // Tile kernel.  PHASED = false: all faces of the tile are evaluated in one
@@ -226,6 +250,42 @@ __global__ void __launch_bounds__(NT, MINB)
         "l"((unsigned long long)&tmW), "r"(4 * x0), "r"(y0), "r"(z0), "r"(0), "r"(bar)
         : "memory");
   }
+  // while the copy is in flight: the tile's background profiles and the
+  // dilated shock flags of cells -1 .. F along each axis (a ghost cell carries
+  // the flag of the interior cell its data comes from; cells further out feed
+  // no face and stay unflagged)
+  if (tid < FZ + 1) {
+    const int z = z0 + tid;
+    const bool in = G.has_bg && z <= G.n[2];
+    sm.bgf[0][tid] = in ? G.bgf_rho_f[z + BG_NG] : 0.0f;
+    sm.bgf[1][tid] = in ? G.bgf_p_f[z + BG_NG] : 0.0f;
+    if (tid < FZ) {
+      const bool inc = G.has_bg && z < G.n[2];
+      sm.bgc[0][tid] = inc ? G.bgf_rho_c[z + BG_NG] : 0.0f;
+      sm.bgc[1][tid] = inc ? G.bgf_p_c[z + BG_NG] : 0.0f;
+    }
+  }
+  for (int q = tid; q < (FX + 2) * (FY + 2) * (FZ + 2); q += NT) {
+    const int l[3] = {q % (FX + 2), (q / (FX + 2)) % (FY + 2), q / ((FX + 2) * (FY + 2))};
+    const int o[3] = {x0, y0, z0};
+    uint8_t v = 0;
+    if (flag) {
+      int g[3];
+      bool in = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        int x = o[d] - 1 + l[d];
+        if (x < -1 || x > G.n[d]) in = false;
+        else if (x == -1 || x == G.n[d]) {
+          bool fl;
+          x = cell_src(x, G.n[d], G.bc[d][0], G.bc[d][1], fl);
+        }
+        g[d] = x;
+      }
+      if (in) v = flag[g[0] + (long)G.n[0] * (g[1] + (long)G.n[1] * g[2])];
+    }
+    (&sm.flg[0][0][0])[q] = v;
+  }
   const bool ok = mbar_wait_bounded(bar, 0u, 1000000000ull);
   if (__syncthreads_or(!ok)) {   // the copy did not land in 1 s: report, let it finish, leave
     if (tid == 0) atomicOr(dflag, FLAG_TIMEOUT);
@@ -251,37 +311,16 @@ __global__ void __launch_bounds__(NT, MINB)
 
   if constexpr (PHASED) {
     static_assert(NXF == NYF && NYF == NZF, "phased tiles need equal face counts per direction");
-#pragma unroll 1
-    for (int D = 0; D < 3; ++D) {
-      for (int f = tid; f < NXF; f += NT) {
-        float out[5];
-        tile_face(G, S, sm, D, f, x0, y0, z0, flag, F0, F1, F2, K, out, dflag);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
-      }
-      __syncthreads();
-      const int st = dface_step(D);
-      const float idd = G.idxf[D];
-#pragma unroll
-      for (int m = 0; m < CPT; ++m) {
-        const int cc = tid + m * NT;
-        if (cc < NC) {
-          const int f0 = dface(D, cc % FX, (cc / FX) % FY, cc / (FX * FY));
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const int q = D == 0 ? qm[v][0] : (D == 1 ? qm[v][1] : qm[v][2]);
-            racc[m][v] += (fb[q * FS + f0 + st] - fb[q * FS + f0]) * idd;
-          }
-        }
-      }
-      __syncthreads();
-    }
+    tile_phase<0, NT, CPT, FS>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<1, NT, CPT, FS>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<2, NT, CPT, FS>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
   } else {
+    // NXF and NXF + NYF are multiples of 32: the direction is uniform in a warp
     for (int f = tid; f < NFACE; f += NT) {
-      const int D = f < NXF ? 0 : (f < NXF + NYF ? 1 : 2);
-      const int fd = f - (D == 0 ? 0 : (D == 1 ? NXF : NXF + NYF));
       float out[5];
-      tile_face(G, S, sm, D, fd, x0, y0, z0, flag, F0, F1, F2, K, out, dflag);
+      if (f < NXF) tile_face<0>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      else if (f < NXF + NYF) tile_face<1>(G, S, sm, f - NXF, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      else tile_face<2>(G, S, sm, f - NXF - NYF, x0, y0, z0, F0, F1, F2, K, out, dflag);
 #pragma unroll
       for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
     }
@@ -291,7 +330,8 @@ __global__ void __launch_bounds__(NT, MINB)
       const int cc = tid + m * NT;
       if (cc < NC) {
         const int i = cc % FX, j = (cc / FX) % FY, k = cc / (FX * FY);
-        const int fx = dface(0, i, j, k), fy = NXF + dface(1, i, j, k), fz = NXF + NYF + dface(2, i, j, k);
+        const int fx = (k * FY + j) * (FX + 1) + i, fy = NXF + (k * (FY + 1) + j) * FX + i,
+                  fz = NXF + NYF + (k * FY + j) * FX + i;
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           racc[m][v] += (fb[qm[v][0] * FS + fx + 1] - fb[qm[v][0] * FS + fx]) * G.idxf[0];
@@ -315,7 +355,7 @@ __global__ void __launch_bounds__(NT, MINB)
     // sources S - S_hat: (rho - rho_hat) g on momentum, rho u . g (+ heating) on energy
     const float4 wa = sm.w[0][((k + NGW) * HY + (j + NGW)) * HX + (i + NGW)];
     const float drho = wa.x;
-    const float rho = bg_cell_t<float>(G, c2).rho + drho;
+    const float rho = sm.bgc[0][k] + drho;
     const float vel[3] = {wa.y, wa.z, wa.w};
     float se = 0.0f;
 #pragma unroll
