@@ -181,13 +181,14 @@ phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, 
  *           face updates after it run as one kernel each.  Needs
  *           precision = PHL_MIXED, an ideal gas, nspec = 0 and three active
  *           dimensions (PHL_EUNSUPPORTED otherwise).  Default where eligible.
- *   on = 2..4: the same kernel in other launch shapes (threads per CTA,
+ *   on = 2..7: the same kernel in other launch shapes (threads per CTA,
  *           CTAs per SM, faces of one direction at a time through a smaller
- *           shared buffer), for tuning; 1 selects the default shape.
+ *           shared buffer; 5 to 7 evaluate two faces per thread on packed
+ *           FP32x2 arithmetic), for tuning; 1 selects the default shape.
  *   on = 0: one kernel per direction for the faces, then EMFs and updates.
  * Results of all of these agree to FP32 rounding of the deviations.  Call
  * between steps only (no stage of the grid in flight on its stream).
- * PHL_EINVAL for on outside 0..4. */
+ * PHL_EINVAL for on outside 0..7. */
 phl_status phl_set_fused(phl_grid *g, int on);
 
 /* Device pointer of the last computed dt (double), valid for the grid's
@@ -213,8 +214,12 @@ phl_status phl_convert_batch(long n, const double *x, int k, float *f, double *b
  *   f       [n][7 + nspec] output F - F_hat: rho, m_n, m_t1, m_t2, E, B_t1,
  *           B_t2, rho*X_l...
  * solver = PHL_LHLLD / PHL_HLLD / PHL_HLL; precision = PHL_FP64 evaluates in
- * double, PHL_MIXED in float (inputs rounded to float).  All pointers are host
- * memory; the call is synchronous on the legacy default stream. */
+ * double, PHL_MIXED in float (inputs rounded to float), 2 in float with the
+ * ideal-gas solver of the fused stage kernel, two faces per thread on packed
+ * FP32x2 arithmetic (nspec = 0 only; gamma taken from bg[.][2] of the first
+ * face of each pair, so all faces must share one gamma; gamma_e and gamma_c
+ * deviations are ignored).  All pointers are host memory; the call is
+ * synchronous on the legacy default stream. */
 phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const double *bn,
                              const double *bg, int nspec, int solver, double mach_thr,
                              int precision, double *f);

@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include "mixed_common.cuh"
+#include "riemann_x2.cuh"
 
 namespace phl {
 using namespace stage;
@@ -183,19 +184,162 @@ __device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, con
   fused_face<D>(G, S, sm, s2, i, j, k, c, own, Fd, K, out, dflag);
 }
 
+// Two D-faces of the tile (fa, fb: indices among its D-faces) evaluated
+// together on packed FP32x2 arithmetic: PLM and the ideal-gas LHLLD / HLL flux
+// of riemann_x2.cuh, lane x = face fa, lane y = face fb.  With hasb false the
+// second lane repeats fa and its results are dropped.  Faces outside the
+// domain give zeros, as in tile_face.
+template <int D>
+__device__ __forceinline__ void tile_face2(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int fa, int fb,
+                                           bool hasb, int x0, int y0, int z0, float *F0, float *F1, float *F2,
+                                           const GasK<float> &K, float *oa, float *ob, int *dflag) {
+  using namespace x2;
+  constexpr int sD = D == 0 ? 1 : (D == 1 ? HX : HX * HY);
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  constexpr int ext = D == 0 ? FX : (D == 1 ? FY : FZ);
+  constexpr int fs = D == 0 ? 1 : (D == 1 ? FX + 2 : (FX + 2) * (FY + 2));
+  int l[2][3];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int f = h == 0 ? fa : fb;
+    if (D == 0) { l[h][0] = f % (FX + 1); const int r = f / (FX + 1); l[h][1] = r % FY; l[h][2] = r / FY; }
+    else if (D == 1) { l[h][0] = f % FX; const int r = f / FX; l[h][1] = r % (FY + 1); l[h][2] = r / (FY + 1); }
+    else { l[h][0] = f % FX; const int r = f / FX; l[h][1] = r % FY; l[h][2] = r / FY; }
+  }
+  const int ca[3] = {x0 + l[0][0], y0 + l[0][1], z0 + l[0][2]};
+  const int cb[3] = {x0 + l[1][0], y0 + l[1][1], z0 + l[1][2]};
+  auto inside = [&](const int *c) {
+    return c[0] <= G.n[0] - (D != 0) && c[1] <= G.n[1] - (D != 1) && c[2] <= G.n[2] - (D != 2);
+  };
+  const bool va = inside(ca), vb = hasb && inside(cb);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) { oa[q] = 0.0f; ob[q] = 0.0f; }
+  if (!va && !vb) return;
+  const int s2a = ((l[0][2] + NGW) * HY + (l[0][1] + NGW)) * HX + (l[0][0] + NGW);
+  const int s2b = ((l[1][2] + NGW) * HY + (l[1][1] + NGW)) * HX + (l[1][0] + NGW);
+  V ql[8], qr[8];
+  {
+    const V half = vv(0.5f), zero = vv(0.0f);
+    auto slope = [&](V w0, V w1, V w2) -> V {   // van Leer harmonic slope (Sect. 2.5, item i)
+      const V dm = w1 - w0, dp = w2 - w1;
+      const V pr = dm * dp;
+      return sel(pr > zero, (pr + pr) * rcp(dm + dp), zero);
+    };
+#pragma unroll
+    for (int hw = 0; hw < 2; ++hw) {
+      float4 A[4], Bv[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        A[m] = sm.w[hw][s2a + (m - 2) * sD];
+        Bv[m] = sm.w[hw][s2b + (m - 2) * sD];
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int v = 4 * hw + e;
+        if (v == W_BX + D) continue;   // the normal field is not reconstructed
+        auto comp = [&](const float4 &u) { return e == 0 ? u.x : (e == 1 ? u.y : (e == 2 ? u.z : u.w)); };
+        const V w0 = vv(comp(A[0]), comp(Bv[0])), w1 = vv(comp(A[1]), comp(Bv[1]));
+        const V w2 = vv(comp(A[2]), comp(Bv[2])), w3 = vv(comp(A[3]), comp(Bv[3]));
+        ql[v] = fma(half, slope(w0, w1, w2), w1);
+        qr[v] = fma(neg(half), slope(w1, w2, w3), w2);
+      }
+    }
+  }
+  V wl[W_X0], wr[W_X0];
+  auto frame = [&](const V *q, V *w) {
+    w[RD_RHO] = q[W_RHO];
+    w[RD_UN] = q[W_VX + D];
+    w[RD_UT1] = q[W_VX + T1];
+    w[RD_UT2] = q[W_VX + T2];
+    w[RD_BT1] = q[W_BX + T1];
+    w[RD_BT2] = q[W_BX + T2];
+    w[RD_P] = q[W_P];
+  };
+  frame(ql, wl);
+  frame(qr, wr);
+  const int ka = l[0][2], kb = l[1][2];
+  const V brho = D == 2 ? vv(sm.bgf[0][ka], sm.bgf[0][kb]) : vv(sm.bgc[0][ka], sm.bgc[0][kb]);
+  const V bp = D == 2 ? vv(sm.bgf[1][ka], sm.bgf[1][kb]) : vv(sm.bgc[1][ka], sm.bgc[1][kb]);
+  {
+    const V rl = brho + wl[RD_RHO], rr = brho + wr[RD_RHO], pl = bp + wl[RD_P], pr = bp + wr[RD_P];
+    const bool na = !(rl.x > 0.0f && rr.x > 0.0f && pl.x > 0.0f && pr.x > 0.0f);
+    const bool nb = !(rl.y > 0.0f && rr.y > 0.0f && pl.y > 0.0f && pr.y > 0.0f);
+    if ((va && na) || (vb && nb)) atomicOr(dflag, FLAG_NEG);
+  }
+  const long qba = (long)D * G.plane + sidx(G, ca[0], ca[1], ca[2]);
+  const long qbb = (long)D * G.plane + sidx(G, cb[0], cb[1], cb[2]);
+  float bna = d2f_scaled(S.B[qba], -G.e_b), bnb = d2f_scaled(S.B[qbb], -G.e_b);
+  if (!S.first) { bna += S.dB[qba]; bnb += S.dB[qbb]; }
+  const uint8_t *fra = &sm.flg[l[0][2] + 1][l[0][1] + 1][l[0][0] + 1];
+  const uint8_t *frb = &sm.flg[l[1][2] + 1][l[1][1] + 1][l[1][0] + 1];
+  const bool hla = (fra[0] | fra[-fs]) != 0, hlb = (frb[0] | frb[-fs]) != 0;
+  V fl[7];
+  int upa, upb;
+  const bool any_hll_solver = G.riemann == SOLVER_HLL;
+  riemann_ideal_x2(wl, wr, vv(bna, bnb), brho, bp, B2{hla || any_hll_solver, hlb || any_hll_solver},
+                   any_hll_solver ? SOLVER_LHLLD : G.riemann, G.machf, fl, upa, upb, K);
+  const bool wa = (ca[D] == 0 && G.bc[D][0] == 1) || (ca[D] == G.n[D] && G.bc[D][1] == 1);
+  const bool wb = (cb[D] == 0 && G.bc[D][0] == 1) || (cb[D] == G.n[D] && G.bc[D][1] == 1);
+  float fa7[7], fb7[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {   // reflecting wall face: only the normal-momentum flux survives
+    fa7[q] = (wa && q != RF_MN) ? 0.0f : fl[q].x;
+    fb7[q] = (wb && q != RF_MN) ? 0.0f : fl[q].y;
+  }
+  if (wa) upa = 0;
+  if (wb) upb = 0;
+  float *Fd = D == 0 ? F0 : (D == 1 ? F1 : F2);
+  const long wt = G.wtot;
+  if (va) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) oa[q] = fa7[q];
+    if (l[0][D] < ext || ca[D] == G.n[D]) {
+      const long pR = widx(G, ca[0], ca[1], ca[2]);
+      Fd[(F_BX + T1) * wt + pR] = fa7[RF_BT1];
+      Fd[(F_BX + T2) * wt + pR] = fa7[RF_BT2];
+      Fd[(long)G.nf * wt + pR] = (float)upa;
+    }
+  }
+  if (vb) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) ob[q] = fb7[q];
+    if (l[1][D] < ext || cb[D] == G.n[D]) {
+      const long pR = widx(G, cb[0], cb[1], cb[2]);
+      Fd[(F_BX + T1) * wt + pR] = fb7[RF_BT1];
+      Fd[(F_BX + T2) * wt + pR] = fb7[RF_BT2];
+      Fd[(long)G.nf * wt + pR] = (float)upb;
+    }
+  }
+}
+
 // One direction's faces of the tile through the face buffer, then each
 // thread's running residuals of its cells (phased variant).
-template <int D, int NT, int CPT, int FS>
+template <int D, int NT, int CPT, int FS, bool PAIRED>
 __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, FusedSmem &sm, float *fb, int tid,
                                            int x0, int y0, int z0, float *F0, float *F1, float *F2,
                                            const GasK<float> &K, float (*racc)[5], int *dflag) {
   constexpr int qm[5][3] = {{0, 0, 0}, {1, 3, 2}, {2, 1, 3}, {3, 2, 1}, {4, 4, 4}};
   constexpr int NC = FX * FY * FZ;
-  for (int f = tid; f < NXF; f += NT) {
-    float out[5];
-    tile_face<D>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
+  if constexpr (PAIRED) {   // faces f and f + NT together
+    for (int f = tid; f < NXF; f += 2 * NT) {
+      const int g2 = f + NT;
+      const bool hasb = g2 < NXF;
+      float oa[5], ob[5];
+      tile_face2<D>(G, S, sm, f, hasb ? g2 : f, hasb, x0, y0, z0, F0, F1, F2, K, oa, ob, dflag);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
+      for (int q = 0; q < 5; ++q) fb[q * FS + f] = oa[q];
+      if (hasb) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) fb[q * FS + g2] = ob[q];
+      }
+    }
+  } else {
+    for (int f = tid; f < NXF; f += NT) {
+      float out[5];
+      tile_face<D>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
+    }
   }
   __syncthreads();
   constexpr int st = D == 0 ? 1 : (D == 1 ? FX : FX * FY);
@@ -222,7 +366,7 @@ __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, Fu
 // direction's faces; each thread keeps the running residuals of its cells in
 // registers (same summation order x, y, z), so the CTA needs ~1/3 of the
 // shared memory and more CTAs fit on an SM.
-template <int NT, int MINB, bool PHASED>
+template <int NT, int MINB, bool PHASED, bool PAIRED = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_flux_update_mx(const __grid_constant__ CUtensorMap tmW, DevGeo G, StageMx S, const uint8_t *__restrict__ flag,
                      float *__restrict__ F0, float *__restrict__ F1, float *__restrict__ F2, int ntx, int nty,
@@ -311,9 +455,9 @@ __global__ void __launch_bounds__(NT, MINB)
 
   if constexpr (PHASED) {
     static_assert(NXF == NYF && NYF == NZF, "phased tiles need equal face counts per direction");
-    tile_phase<0, NT, CPT, FS>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
-    tile_phase<1, NT, CPT, FS>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
-    tile_phase<2, NT, CPT, FS>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<0, NT, CPT, FS, PAIRED>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<1, NT, CPT, FS, PAIRED>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<2, NT, CPT, FS, PAIRED>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
   } else {
     // NXF and NXF + NYF are multiples of 32: the direction is uniform in a warp
     for (int f = tid; f < NFACE; f += NT) {
@@ -575,6 +719,15 @@ cudaError_t fused_init() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_flux_update_mx<384, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<288, 2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<288, 1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(true));
   done = e;
   return e;
 }
@@ -622,17 +775,21 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   }
   const CUtensorMap *tm = (const CUtensorMap *)M.tmapW;
   // launch shapes: (threads, min CTAs per SM, phased)
-#define PHL_FUSED(NT, MB, PH)                                                                                   \
+#define PHL_FUSED(NT, MB, PH, PA)                                                                               \
   do {                                                                                                         \
     PHL_LAUNCH(KC_FLUX_UPDATE, prof, s,                                                                        \
-               (k_flux_update_mx<NT, MB, PH><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0], M.F[1],     \
-                                                                             M.F[2], ntx, nty, M.dflag)));     \
+               (k_flux_update_mx<NT, MB, PH, PA><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0],        \
+                                                                                 M.F[1], M.F[2], ntx, nty,     \
+                                                                                 M.dflag)));                   \
   } while (0)
   switch (M.fused_variant) {
-    case 2: PHL_FUSED(288, 3, true); break;
-    case 3: PHL_FUSED(256, 3, true); break;
-    case 4: PHL_FUSED(384, 2, true); break;
-    default: PHL_FUSED(256, 2, false); break;
+    case 2: PHL_FUSED(288, 3, true, false); break;
+    case 3: PHL_FUSED(256, 3, true, false); break;
+    case 4: PHL_FUSED(384, 2, true, false); break;
+    case 5: PHL_FUSED(288, 1, true, true); break;
+    case 6: PHL_FUSED(256, 2, true, true); break;
+    case 7: PHL_FUSED(288, 2, true, true); break;
+    default: PHL_FUSED(256, 2, false, false); break;
   }
 #undef PHL_FUSED
   ++*nl;

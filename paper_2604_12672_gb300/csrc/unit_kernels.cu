@@ -4,6 +4,7 @@
 
 #include "phl.h"
 #include "phl_internal.cuh"
+#include "riemann_x2.cuh"
 
 using namespace phl;
 
@@ -20,6 +21,35 @@ __global__ void k_riemann_batch(long n, const double *wl, const double *wr, cons
     riemann_dev<R, PHL_NSPEC_MAX>(a, b, (R)bn[t], (R)bg[4 * t], (R)bg[4 * t + 1], (R)bg[4 * t + 2], (R)bg[4 * t + 3], nspec,
                    solver, (R)mthr, out, up);
     for (int q = 0; q < nf; ++q) f[t * nf + q] = (double)out[q];
+  }
+}
+
+// Pairs of faces through the packed FP32x2 ideal-gas solver; gamma from the
+// background's gamma_e column (bg[4t + 2]) of the pair's first face.
+__global__ void k_riemann_batch_x2(long n, const double *wl, const double *wr, const double *bn, const double *bg,
+                                   int solver, double mthr, double *f) {
+  const long np = (n + 1) / 2;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < np; t += (long)gridDim.x * blockDim.x) {
+    const long a = 2 * t, b = (2 * t + 1 < n) ? 2 * t + 1 : 2 * t;
+    x2::V l[9], r[9];
+    for (int q = 0; q < 9; ++q) {
+      l[q] = x2::vv((float)wl[a * 9 + q], (float)wl[b * 9 + q]);
+      r[q] = x2::vv((float)wr[a * 9 + q], (float)wr[b * 9 + q]);
+    }
+    GasK<float> K;
+    K.g = (float)bg[4 * a + 2];
+    K.igm1 = 1.0f / (K.g - 1.0f);
+    K.ggm1 = K.g * K.igm1;
+    const x2::B2 hll{solver == SOLVER_HLL, solver == SOLVER_HLL};
+    x2::V out[7];
+    int ua, ub;
+    x2::riemann_ideal_x2(l, r, x2::vv((float)bn[a], (float)bn[b]), x2::vv((float)bg[4 * a], (float)bg[4 * b]),
+                         x2::vv((float)bg[4 * a + 1], (float)bg[4 * b + 1]), hll,
+                         solver == SOLVER_HLL ? SOLVER_LHLLD : solver, (float)mthr, out, ua, ub, K);
+    for (int q = 0; q < 7; ++q) {
+      f[a * 7 + q] = (double)out[q].x;
+      if (b != a) f[b * 7 + q] = (double)out[q].y;
+    }
   }
 }
 
@@ -55,6 +85,7 @@ extern "C" phl_status phl_riemann_batch(long n, const double *wl, const double *
                                         const double *bg, int nspec, int solver, double mach_thr,
                                         int precision, double *f) {
   if (n < 0 || nspec < 0 || nspec > PHL_MAXSPEC || solver < 0 || solver > 2) return PHL_EINVAL;
+  if (precision == 2 && nspec != 0) return PHL_EINVAL;
   if (n == 0) return PHL_OK;
   if (!wl || !wr || !bn || !bg || !f) return PHL_EINVAL;
   const size_t nw = 9 + nspec, nf = 7 + nspec;
@@ -69,6 +100,8 @@ extern "C" phl_status phl_riemann_batch(long n, const double *wl, const double *
   const int blocks = (int)((n + 127) / 128 < 4096 ? (n + 127) / 128 : 4096);
   if (precision == PHL_FP64)
     k_riemann_batch<double><<<blocks, 128>>>(n, dwl, dwr, dbn, dbg, nspec, solver, mach_thr, df);
+  else if (precision == 2)
+    k_riemann_batch_x2<<<blocks, 128>>>(n, dwl, dwr, dbn, dbg, solver, mach_thr, df);
   else
     k_riemann_batch<float><<<blocks, 128>>>(n, dwl, dwr, dbn, dbg, nspec, solver, mach_thr, df);
   cudaError_t e = cudaMemcpy(f, df, n * nf * sizeof(double), cudaMemcpyDeviceToHost);

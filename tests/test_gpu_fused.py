@@ -64,17 +64,21 @@ def test_fused_matches_per_direction_and_oracle(P, bc):
         assert l_fo[k] <= 1e-5, ("fused vs oracle", k, l_fo[k])
 
 
-@pytest.mark.parametrize("shape", [2, 3, 4])
+@pytest.mark.parametrize("shape", [2, 3, 4, 5, 6, 7])
 def test_fused_launch_shapes_agree(P, shape):
-    """Every launch shape of the tile kernel (phased faces, other CTA sizes)
-    gives the per-direction result to FP32 rounding."""
+    """Every launch shape of the tile kernel (phased faces, other CTA sizes,
+    two faces per thread on FP32x2 arithmetic) gives the per-direction result
+    to FP32 rounding: shapes 2-4 run the same scalar face code (agreement to
+    1e-6 relative L1 of the deviations), shapes 5-7 the paired solver, whose
+    explicit FMAs round differently (held to the mixed form's bar, 1e-5)."""
     pr = W.stratified_box(19, 13, 21, amp=3e-2, beta=1e3, mach_heat=3e-2)
     pr.bc = BCS["outflow_x_reflect_y"]
     dt = 0.5 * O.Oracle(pr).dt(dict(cons=pr.cons, bx=pr.bx, by=pr.by, bz=pr.bz))
     a = run(P, pr, shape, 4, dt)
     b = run(P, pr, 0, 4, dt)
+    tol = 1e-6 if shape <= 4 else 1e-5
     for k, v in deviation_l1(pr, a, b).items():
-        assert v <= 1e-6, (shape, k, v)
+        assert v <= tol, (shape, k, v)
 
 
 def blast(nx, ny, nz, seed=5):
