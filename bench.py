@@ -60,9 +60,15 @@ FP64_FLOP_PER_FACE = 807.0
 FP32_FLOP_PER_FACE = {"flux_x": 381.1, "flux_y": 381.1, "flux_z": 380.1}
 FP32_DRAM_BYTES_PER_FACE = {"flux_x": 74.4, "flux_y": 75.8, "flux_z": 76.1}
 FP32_NOMINAL_TFLOPS = 80.5
-# Fused tile kernel (k_flux_update_mx): DRAM bytes per cell from an ncu capture
-# (None until measured for the current kernel).
-FUSED_DRAM_BYTES_PER_CELL = None
+# Fused tile kernel (k_flux_update_mx, default launch shape): from the ncu
+# counters of the stratified box at 160^3 (W larger than L2), one launch of
+# stage 1 and one of stage 2: FP32 operations (FADD + FMUL + 2 FFMA) 1398 per
+# cell as executed, i.e. 414 per face over the 3.375 faces per cell an 8^3
+# tile evaluates; the algorithmic count is 3 faces per cell x 414 = 1243.
+# DRAM bytes per cell: 113.2 (stage 1, no increment to read) and 145.7
+# (stages 2-3), 134.9 on average over an RK3 step.
+FUSED_FLOP_PER_CELL = 3.0 * 414.3
+FUSED_DRAM_BYTES_PER_CELL = (113.2 + 2.0 * 145.7) / 3.0
 
 
 def read_peaks():
@@ -179,8 +185,6 @@ def time_form(P, pr, form, steps, warmup, stream, ws, fused=-1):
     for _ in range(warmup):
         g.step(1)
     g.check()
-    g.set_timing(True)
-    g.kernel_times(reset=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     barrier(ws)
@@ -191,6 +195,12 @@ def time_form(P, pr, form, steps, warmup, stream, ws, fused=-1):
     torch.cuda.synchronize()
     barrier(ws)
     ms = e0.elapsed_time(e1)
+    g.check()
+    # per-kernel breakdown: the same number of steps again with an event pair
+    # around every launch (kept out of the timed region above)
+    g.set_timing(True)
+    g.kernel_times(reset=True)
+    g.step(steps)
     kt = g.kernel_times(reset=True)
     g.set_timing(False)
     g.check()
@@ -211,14 +221,13 @@ def roofline(kt, pr, form, hbm_peak, peak_kind):
                 "avg_launch_ms": avg_ms, "launches": launches}
     if name == "flux_update":
         # fused tile kernel: the faces of all three directions + the cell update;
-        # algorithmic work = 3 faces per cell x the flux arithmetic per face
-        # (the same device code as the per-direction kernels)
-        flop = 3.0 * FP32_FLOP_PER_FACE["flux_x"]
+        # algorithmic work = 3 faces per cell x the FP32 operations per face
+        flop = FUSED_FLOP_PER_CELL
         achieved = ncells * flop / (avg_ms * 1e-3) / 1e12
-        traffic = ncells * FUSED_DRAM_BYTES_PER_CELL if FUSED_DRAM_BYTES_PER_CELL else None
+        traffic = ncells * FUSED_DRAM_BYTES_PER_CELL
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_NOMINAL_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_NOMINAL_TFLOPS, "traffic": traffic,
-                "traffic_note": "bytes per launch: ncu DRAM bytes per cell x cells" if traffic else None,
+                "traffic_note": "bytes per launch: ncu DRAM bytes per cell at 160^3 (RK3 mean) x cells",
                 "peak_kind": "nominal FP32 (152 SM x 128 lanes x 2 x 2.07 GHz)",
                 "flop_per_cell": flop, "avg_launch_ms": avg_ms, "launches": launches}
     if name.startswith("flux"):
