@@ -85,6 +85,8 @@ struct phl_grid {
   int launches_per_step = 0;
   Prof prof;
   int fused = 0;                        // mixed stage on the fused tile kernel: launch shape, 0 = off
+  double *stage_a = nullptr, *stage_b = nullptr;   // work arrays reused as host-transfer staging
+  size_t stage_a_bytes = 0, stage_b_bytes = 0;
   alignas(64) unsigned char tmapW[128]; // its TMA descriptor of W
 };
 
@@ -123,6 +125,77 @@ phl_status copy_field(phl_grid *g, double *dev, const double *abi_src, double *a
   p.extent = make_cudaExtent((size_t)ex * sizeof(double), (size_t)ey, (size_t)ez);
   p.kind = cudaMemcpyDefault;
   CK(cudaMemcpy3DAsync(&p, g->stream), "cudaMemcpy3DAsync");
+  return PHL_OK;
+}
+
+// Dense (ABI) <-> padded device layout of one field with extents (ex, ey, ez):
+// one CTA per x-row, consecutive threads on consecutive elements.
+__global__ void k_repitch(const double *__restrict__ src, double *__restrict__ dst, int ex, int ey, long sy, long sz,
+                          int to_dev) {
+  const long row = blockIdx.x;   // j + ey * k
+  const long j = row % ey, k = row / ey;
+  const long dense = row * ex, padded = j * sy + k * sz;
+  for (int i = threadIdx.x; i < ex; i += blockDim.x) {
+    if (to_dev) dst[padded + i] = src[dense + i];
+    else dst[dense + i] = src[padded + i];
+  }
+}
+
+// The state (nv cell fields and three face fields) between ABI arrays and the
+// device layout.  Device arrays: one repitch kernel per field, straight from
+// or into the caller's buffers.  Host arrays: one linear copy per array
+// through the grid's work arrays (dead between steps), at full link bandwidth,
+// plus the repitch kernels; pitched 3-D copies only when the work arrays are
+// too small to hold the dense state.
+phl_status state_io(phl_grid *g, double *cons, double *bx, double *by, double *bz, bool to_dev, bool host) {
+  const DevGeo &G = g->G;
+  const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
+  const long nc = (long)nx * ny * nz;
+  const long nf[3] = {(long)(nx + 1) * ny * nz, (long)nx * (ny + 1) * nz, (long)nx * ny * (nz + 1)};
+  const int ext[3][3] = {{nx + 1, ny, nz}, {nx, ny + 1, nz}, {nx, ny, nz + 1}};
+  double *face_abi[3] = {bx, by, bz};
+  const size_t cons_bytes = (size_t)G.nv * nc * sizeof(double);
+  const size_t face_bytes = (size_t)(nf[0] + nf[1] + nf[2]) * sizeof(double);
+  const bool staged = host && g->stage_a && g->stage_b && cons_bytes <= g->stage_a_bytes && face_bytes <= g->stage_b_bytes;
+  if (host && !staged) {   // pitched copies
+    phl_status st;
+    for (int v = 0; v < G.nv; ++v)
+      if ((st = copy_field(g, g->U + v * G.plane, to_dev ? cons + v * nc : nullptr, to_dev ? nullptr : cons + v * nc,
+                           nx, ny, nz, to_dev)) != PHL_OK)
+        return st;
+    for (int d = 0; d < 3; ++d)
+      if ((st = copy_field(g, g->B + d * G.plane, to_dev ? face_abi[d] : nullptr, to_dev ? nullptr : face_abi[d],
+                           ext[d][0], ext[d][1], ext[d][2], to_dev)) != PHL_OK)
+        return st;
+    return PHL_OK;
+  }
+  double *ca = staged ? g->stage_a : cons;
+  double *fa[3];
+  fa[0] = staged ? g->stage_b : bx;
+  fa[1] = staged ? g->stage_b + nf[0] : by;
+  fa[2] = staged ? g->stage_b + nf[0] + nf[1] : bz;
+  if (staged && to_dev) {
+    CK(cudaMemcpyAsync(ca, cons, cons_bytes, cudaMemcpyHostToDevice, g->stream), "copy state");
+    for (int d = 0; d < 3; ++d)
+      CK(cudaMemcpyAsync(fa[d], face_abi[d], nf[d] * sizeof(double), cudaMemcpyHostToDevice, g->stream), "copy B");
+  }
+  for (int v = 0; v < G.nv; ++v) {
+    double *dev = g->U + v * G.plane;
+    if (to_dev) k_repitch<<<(unsigned)((long)ny * nz), 256, 0, g->stream>>>(ca + v * nc, dev, nx, ny, G.sy, G.sz, 1);
+    else k_repitch<<<(unsigned)((long)ny * nz), 256, 0, g->stream>>>(dev, ca + v * nc, nx, ny, G.sy, G.sz, 0);
+  }
+  for (int d = 0; d < 3; ++d) {
+    double *dev = g->B + d * G.plane;
+    const unsigned rows = (unsigned)((long)ext[d][1] * ext[d][2]);
+    if (to_dev) k_repitch<<<rows, 256, 0, g->stream>>>(fa[d], dev, ext[d][0], ext[d][1], G.sy, G.sz, 1);
+    else k_repitch<<<rows, 256, 0, g->stream>>>(dev, fa[d], ext[d][0], ext[d][1], G.sy, G.sz, 0);
+  }
+  CK(cudaGetLastError(), "repitch");
+  if (staged && !to_dev) {
+    CK(cudaMemcpyAsync(cons, ca, cons_bytes, cudaMemcpyDeviceToHost, g->stream), "copy state");
+    for (int d = 0; d < 3; ++d)
+      CK(cudaMemcpyAsync(face_abi[d], fa[d], nf[d] * sizeof(double), cudaMemcpyDeviceToHost, g->stream), "copy B");
+  }
   return PHL_OK;
 }
 
@@ -310,6 +383,10 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     for (int k = 0; k < 3; ++k)
       if (G.act[k]) AL(&g->F[k], (long)(G.nf + 1) * G.wtot);   // + contact direction
     AL(&g->E, 3 * G.wtot);
+    g->stage_a = g->W;
+    g->stage_a_bytes = (size_t)G.nw * G.wtot * sizeof(double);
+    g->stage_b = g->F[0];
+    g->stage_b_bytes = g->F[0] ? (size_t)(G.nf + 1) * G.wtot * sizeof(double) : 0;
   } else {
     AL(&g->dUf, G.nv * G.plane);
     AL(&g->dBf, 3 * G.plane);
@@ -318,6 +395,10 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
       if (G.act[k]) AL(&g->Ff[k], (long)(G.nf + 1) * G.wtot);
     AL(&g->Ef, 3 * G.wtot);
     AL(&g->fmax, 1);
+    g->stage_a = (double *)g->Wf;
+    g->stage_a_bytes = (size_t)(G.wstr + NAUX) * G.wtot * sizeof(float);
+    g->stage_b = (double *)g->Ff[0];
+    g->stage_b_bytes = g->Ff[0] ? (size_t)(G.nf + 1) * G.wtot * sizeof(float) : 0;
     if (fused_stage_ok(G)) {
       if (make_fused_tmap(G, g->Wf, g->tmapW) != PHL_OK) { phl_destroy(g); return PHL_ECUDA; }
       const cudaError_t e = fused_init();
@@ -419,11 +500,10 @@ phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx, cons
   const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
   const long nc = (long)nx * ny * nz;
   phl_status st;
-  for (int v = 0; v < G.nv; ++v)
-    if ((st = copy_field(g, g->U + v * G.plane, cons + v * nc, nullptr, nx, ny, nz, true)) != PHL_OK) return st;
-  if ((st = copy_field(g, g->B, bx, nullptr, nx + 1, ny, nz, true)) != PHL_OK) return st;
-  if ((st = copy_field(g, g->B + G.plane, by, nullptr, nx, ny + 1, nz, true)) != PHL_OK) return st;
-  if ((st = copy_field(g, g->B + 2 * G.plane, bz, nullptr, nx, ny, nz + 1, true)) != PHL_OK) return st;
+  (void)nc;
+  if ((st = state_io(g, const_cast<double *>(cons), const_cast<double *>(bx), const_cast<double *>(by),
+                     const_cast<double *>(bz), true, where == PHL_HOST)) != PHL_OK)
+    return st;
   if (g->T) {
     if (T) {
       if ((st = copy_field(g, g->T, T, nullptr, nx, ny, nz, true)) != PHL_OK) return st;
@@ -443,11 +523,8 @@ phl_status phl_get_state(phl_grid *g, double *cons, double *bx, double *by, doub
   const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
   const long nc = (long)nx * ny * nz;
   phl_status st;
-  for (int v = 0; v < G.nv; ++v)
-    if ((st = copy_field(g, g->U + v * G.plane, nullptr, cons + v * nc, nx, ny, nz, false)) != PHL_OK) return st;
-  if ((st = copy_field(g, g->B, nullptr, bx, nx + 1, ny, nz, false)) != PHL_OK) return st;
-  if ((st = copy_field(g, g->B + G.plane, nullptr, by, nx, ny + 1, nz, false)) != PHL_OK) return st;
-  if ((st = copy_field(g, g->B + 2 * G.plane, nullptr, bz, nx, ny, nz + 1, false)) != PHL_OK) return st;
+  (void)nc;
+  if ((st = state_io(g, cons, bx, by, bz, false, where == PHL_HOST)) != PHL_OK) return st;
   if (g->T && T)
     if ((st = copy_field(g, g->T, nullptr, T, nx, ny, nz, false)) != PHL_OK) return st;
   return check_flags(g);
