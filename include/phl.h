@@ -191,6 +191,18 @@ phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, 
  * PHL_EINVAL for on outside 0..7. */
 phl_status phl_set_fused(phl_grid *g, int on);
 
+/* Test of the failure path of the fused tile kernel's bounded wait.  With
+ * on != 0, each tile announces 16 bytes more to its TMA completion barrier than
+ * its copy delivers: the copy itself completes (nothing is left in flight),
+ * the barrier's phase never does, every CTA gives up after its bounded waits
+ * (1 s each), sets the timeout bit and returns without writing its cells, and
+ * the next synchronising call (phl_check, phl_compute_dt, phl_get_state)
+ * returns PHL_ETIMEOUT.  The context stays usable: with on = 0 and the state
+ * reloaded (phl_set_state clears the error bits) the grid steps normally.
+ * Meant for tiny grids (each affected stage waits ~2 s per wave of CTAs).
+ * PHL_EUNSUPPORTED if the grid does not run the fused kernel. */
+phl_status phl_test_tile_wait_timeout(phl_grid *g, int on);
+
 /* Device pointer of the last computed dt (double), valid for the grid's
  * lifetime; lets callers enqueue reads without a synchronisation. */
 phl_status phl_dt_device_ptr(phl_grid *g, const double **ptr);

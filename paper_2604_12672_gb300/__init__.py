@@ -90,6 +90,7 @@ _SIGS = {
     "phl_dt_device_ptr": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "phl_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_set_fused": (C.c_int, [C.c_void_p, C.c_int]),
+    "phl_test_tile_wait_timeout": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_convert_batch": (C.c_int, [C.c_long, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "phl_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "phl_destroy": (None, [C.c_void_p]),
@@ -520,10 +521,15 @@ class Grid:
     def set_timing(self, on=True):
         _check(lib().phl_set_timing(self.h, int(bool(on))))
 
+    def test_tile_wait_timeout(self, on=True):
+        """Make the fused tile kernel's bounded TMA wait run out (a test of the
+        failure path; see phl_test_tile_wait_timeout)."""
+        _check(lib().phl_test_tile_wait_timeout(self.h, int(bool(on))))
+
     def set_fused(self, on=1):
         """Mixed-precision stage decomposition (phl_set_fused): 0/False = one
         face kernel per direction, 1/True = the fused tile kernel in its
-        default launch shape, 2..4 = other launch shapes of it."""
+        default launch shape, 2..7 = other launch shapes of it."""
         _check(lib().phl_set_fused(self.h, int(on)))
 
     def kernel_times(self, reset=True):

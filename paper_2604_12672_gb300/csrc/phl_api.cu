@@ -85,6 +85,7 @@ struct phl_grid {
   int launches_per_step = 0;
   Prof prof;
   int fused = 0;                        // mixed stage on the fused tile kernel: launch shape, 0 = off
+  unsigned test_extra_tx = 0;           // phl_test_tile_wait_timeout
   double *stage_a = nullptr, *stage_b = nullptr;   // work arrays reused as host-transfer staging
   size_t stage_a_bytes = 0, stage_b_bytes = 0;
   alignas(64) unsigned char tmapW[128]; // its TMA descriptor of W
@@ -203,10 +204,11 @@ phl_status check_flags(phl_grid *g) {
   int f = 0;
   CK(cudaMemcpyAsync(&f, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream), "read flags");
   CK(cudaStreamSynchronize(g->stream), "sync");
+  // a timeout is reported first: the tiles that gave up left their cells unwritten
+  if (f & FLAG_TIMEOUT) return fail(PHL_ETIMEOUT, "a bounded device wait (tile copy) gave up");
   if (f & FLAG_NAN) return fail(PHL_ENAN, "non-finite value in the state");
   if (f & FLAG_NEG) return fail(PHL_ENEGATIVE, "non-positive density or pressure");
   if (f & FLAG_NEWTON) return fail(PHL_ENEWTON, "EOS Newton iteration did not converge");
-  if (f & FLAG_TIMEOUT) return fail(PHL_ETIMEOUT, "a bounded device wait (tile copy) gave up");
   return PHL_OK;
 }
 
@@ -593,6 +595,7 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
       M.raw = g->raw; M.flag = g->flag; M.dt = g->dt; M.dflag = g->dflag;
       M.tmapW = g->fused ? g->tmapW : nullptr;
       M.fused_variant = g->fused;
+      M.test_extra_tx = g->test_extra_tx;
       for (int st = 0; st < ns; ++st) {
         M.Tin = g->T;
         M.Tout = g->T2;
@@ -674,6 +677,13 @@ phl_status phl_set_fused(phl_grid *g, int on) {
     return fail(PHL_EUNSUPPORTED, "the fused stage needs the mixed form, an ideal gas without species and 3 active dimensions");
   if (make_fused_tmap(g->G, g->Wf, g->tmapW) != PHL_OK) return PHL_ECUDA;
   g->fused = on == 1 ? PHL_FUSED_DEFAULT : on;
+  return PHL_OK;
+}
+
+phl_status phl_test_tile_wait_timeout(phl_grid *g, int on) {
+  if (!g) return fail(PHL_EINVAL, "null grid");
+  if (on && !g->fused) return fail(PHL_EUNSUPPORTED, "the grid does not run the fused tile kernel");
+  g->test_extra_tx = on ? 16u : 0u;
   return PHL_OK;
 }
 

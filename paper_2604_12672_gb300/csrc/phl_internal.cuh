@@ -278,6 +278,7 @@ struct MixedBufs {
   double *Tout;
   const void *tmapW = nullptr; // TMA descriptor of W (fused path), or null
   int fused_variant = 1;       // launch shape of the fused tile kernel (phl_set_fused)
+  unsigned test_extra_tx = 0;  // timeout test: bytes announced to the tile barrier that never arrive
 };
 void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
                         int *nlaunch, Prof *prof);

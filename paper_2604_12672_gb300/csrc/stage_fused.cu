@@ -370,7 +370,7 @@ template <int NT, int MINB, bool PHASED, bool PAIRED = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_flux_update_mx(const __grid_constant__ CUtensorMap tmW, DevGeo G, StageMx S, const uint8_t *__restrict__ flag,
                      float *__restrict__ F0, float *__restrict__ F1, float *__restrict__ F2, int ntx, int nty,
-                     int *dflag) {
+                     int *dflag, unsigned extra_tx) {
   extern __shared__ unsigned char smraw[];
   FusedSmem &sm = *reinterpret_cast<FusedSmem *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
   const int tid = threadIdx.x;
@@ -386,7 +386,9 @@ __global__ void __launch_bounds__(NT, MINB)
   }
   __syncthreads();
   if (tid == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(W_TILE_BYTES) : "memory");
+    // extra_tx is 0 except in the timeout test (bytes that never arrive)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(W_TILE_BYTES + extra_tx)
+                 : "memory");
     // work-layout coordinates of staged cell (-NGW, -NGW, -NGW): (x0 - NGW + ge) = x0
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -780,7 +782,7 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
     PHL_LAUNCH(KC_FLUX_UPDATE, prof, s,                                                                        \
                (k_flux_update_mx<NT, MB, PH, PA><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0],        \
                                                                                  M.F[1], M.F[2], ntx, nty,     \
-                                                                                 M.dflag)));                   \
+                                                                                 M.dflag, M.test_extra_tx)));  \
   } while (0)
   switch (M.fused_variant) {
     case 2: PHL_FUSED(288, 3, true, false); break;
