@@ -181,14 +181,16 @@ phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, 
  *           face updates after it run as one kernel each.  Needs
  *           precision = PHL_MIXED, an ideal gas, nspec = 0 and three active
  *           dimensions (PHL_EUNSUPPORTED otherwise).  Default where eligible.
- *   on = 2..7: the same kernel in other launch shapes (threads per CTA,
+ *   on = 2..9: the same kernel in other launch shapes (threads per CTA,
  *           CTAs per SM, faces of one direction at a time through a smaller
  *           shared buffer; 5 to 7 evaluate two faces per thread on packed
- *           FP32x2 arithmetic), for tuning; 1 selects the default shape.
+ *           FP32x2 arithmetic; 8 and 9 pair the left and right states of
+ *           each face on FP32x2 arithmetic), for tuning; 1 selects the
+ *           default shape.
  *   on = 0: one kernel per direction for the faces, then EMFs and updates.
  * Results of all of these agree to FP32 rounding of the deviations.  Call
  * between steps only (no stage of the grid in flight on its stream).
- * PHL_EINVAL for on outside 0..7. */
+ * PHL_EINVAL for on outside 0..9. */
 phl_status phl_set_fused(phl_grid *g, int on);
 
 /* Test of the failure path of the fused tile kernel's bounded wait.  With
@@ -228,9 +230,11 @@ phl_status phl_convert_batch(long n, const double *x, int k, float *f, double *b
  * solver = PHL_LHLLD / PHL_HLLD / PHL_HLL; precision = PHL_FP64 evaluates in
  * double, PHL_MIXED in float (inputs rounded to float), 2 in float with the
  * ideal-gas solver of the fused stage kernel, two faces per thread on packed
- * FP32x2 arithmetic (nspec = 0 only; gamma taken from bg[.][2] of the first
- * face of each pair, so all faces must share one gamma; gamma_e and gamma_c
- * deviations are ignored).  All pointers are host memory; the call is
+ * FP32x2 arithmetic, 3 in float with the ideal-gas solver that pairs the left
+ * and right states of each face on FP32x2 arithmetic (2 and 3: nspec = 0
+ * only; gamma taken from bg[.][2] (of the first face of each pair for 2), so
+ * all faces must share one gamma; gamma_e and gamma_c deviations are
+ * ignored).  All pointers are host memory; the call is
  * synchronous on the legacy default stream. */
 phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const double *bn,
                              const double *bg, int nspec, int solver, double mach_thr,

@@ -19,7 +19,7 @@ PHL_MAXSPEC = 4
 PERIODIC, REFLECT, OUTFLOW = 0, 1, 2
 EOS = {"ideal": 0, "stellar": 1}
 RIEMANN = {"lhlld": 0, "hlld": 1, "hll": 2}
-PRECISION = {"fp64": 0, "mixed": 1, "mixed_x2": 2}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_x2": 2, "mixed_lr": 3}
 HOST, DEVICE = 0, 1
 STATUS = {0: "PHL_OK", 1: "PHL_EINVAL", 2: "PHL_ECUDA", 3: "PHL_ENOMEM", 4: "PHL_ENEGATIVE",
           5: "PHL_ENAN", 6: "PHL_ENEWTON", 7: "PHL_ETIMEOUT", 8: "PHL_EUNSUPPORTED"}
@@ -529,7 +529,7 @@ class Grid:
     def set_fused(self, on=1):
         """Mixed-precision stage decomposition (phl_set_fused): 0/False = one
         face kernel per direction, 1/True = the fused tile kernel in its
-        default launch shape, 2..7 = other launch shapes of it."""
+        default launch shape, 2..9 = other launch shapes of it."""
         _check(lib().phl_set_fused(self.h, int(on)))
 
     def kernel_times(self, reset=True):

@@ -288,8 +288,8 @@ void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigne
 // Fused mixed stage (stage_fused.cu): faces of all three directions and the
 // cell update in one tiled kernel; ideal gas, no species, 3-D grids.
 bool fused_stage_ok(const DevGeo &G);
-constexpr int PHL_FUSED_SHAPES = 7;    // launch shapes of the tile kernel
-constexpr int PHL_FUSED_DEFAULT = 2;   // the shape used unless phl_set_fused picks another (288 threads, 3 CTAs/SM, phased)
+constexpr int PHL_FUSED_SHAPES = 9;    // launch shapes of the tile kernel
+constexpr int PHL_FUSED_DEFAULT = 8;   // the shape used unless phl_set_fused picks another (288 threads, 3 CTAs/SM, phased, left/right-paired solver)
 int make_fused_tmap(const DevGeo &G, const float *W, void *tmap128);
 cudaError_t fused_init();   // shared-memory limits of the tile kernels (once per process)
 void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool last, double b, cudaStream_t s,

@@ -253,3 +253,137 @@ __device__ __forceinline__ void riemann_ideal_x2(const V *wl, const V *wr, V bn,
 
 }  // namespace x2
 }  // namespace phl
+
+namespace phl {
+namespace x2 {
+
+// ---------------------------------------------------------------------------
+// One face, its left and right states as the two lanes (lane x = L, lane y =
+// R).  The side quantities, the fast speeds, the physical fluxes and both
+// HLLD intermediate states are the same arithmetic on each side, so they run
+// as packed pairs without doubling the live state; everything that mixes the
+// sides (wave speeds, S_M, p_T*, the double-star states, the region choice)
+// stays scalar.  Same method and formulas as riemann_dev with IDEAL = true.
+
+__device__ __forceinline__ void sides_init_lr(SideV &s, const float *wl, const float *wr, float bn, float rh, float ph,
+                                              const GasK<float> &K) {
+  const float w2[RD_P + 1][2] = {{wl[RD_RHO], wr[RD_RHO]}, {wl[RD_UN], wr[RD_UN]}, {wl[RD_UT1], wr[RD_UT1]},
+                                 {wl[RD_UT2], wr[RD_UT2]}, {wl[RD_BT1], wr[RD_BT1]}, {wl[RD_BT2], wr[RD_BT2]},
+                                 {wl[RD_P], wr[RD_P]}};
+  V w[RD_P + 1];
+#pragma unroll
+  for (int q = 0; q <= RD_P; ++q) w[q] = vv(w2[q][0], w2[q][1]);
+  side_init_v(s, w, vv(bn), vv(rh), vv(ph), K);
+}
+
+__device__ __forceinline__ void riemann_ideal_lr(const float *wl, const float *wr, float bn, float rh, float ph,
+                                                 int solver, float mthr, float *f, int &up, const GasK<float> &K) {
+  SideV s;   // lane x: left side, lane y: right side
+  sides_init_lr(s, wl, wr, bn, rh, ph, K);
+  const V lo = s.un - s.cf, hi = s.un + s.cf;
+  const float SL = fminf(lo.x, lo.y), SR = fmaxf(hi.x, hi.y);
+  if (solver == SOLVER_HLL) {
+    if (SL >= 0.0f) {
+#pragma unroll
+      for (int q = 0; q < 7; ++q) f[q] = s.F[q].x;
+    } else if (SR <= 0.0f) {
+#pragma unroll
+      for (int q = 0; q < 7; ++q) f[q] = s.F[q].y;
+    } else {
+      const V m = s.rho * s.un, m1 = s.rho * s.ut1, m2 = s.rho * s.ut2;
+      float dU[7];
+      dU[RF_RHO] = wr[RD_RHO] - wl[RD_RHO];
+      dU[RF_MN] = m.y - m.x;
+      dU[RF_MT1] = m1.y - m1.x;
+      dU[RF_MT2] = m2.y - m2.x;
+      dU[RF_E] = s.de.y - s.de.x;
+      dU[RF_BT1] = s.bt1.y - s.bt1.x;
+      dU[RF_BT2] = s.bt2.y - s.bt2.x;
+      const float idn = 1.0f / (SR - SL);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) f[q] = (SR * s.F[q].x - SL * s.F[q].y + SL * SR * dU[q]) * idn;
+    }
+    const float scale = 1e-12f * fmaxf(s.rho.x, s.rho.y) * fmaxf(fabsf(SL), fabsf(SR));
+    up = f[RF_RHO] > scale ? 1 : (f[RF_RHO] < -scale ? -1 : 0);
+    return;
+  }
+  float xi = 1.0f;
+  if (solver == SOLVER_LHLLD) {
+    const float m2 = fmaxf(s.m2.x, s.m2.y);
+    xi = m2 < mthr * mthr ? sqrtf(m2) : 1.0f;
+  }
+  const V S2 = vv(SL, SR);
+  const V sv = S2 - s.un;            // (S_L - u_L, S_R - u_R)
+  const V rs = sv * s.rho;
+  const float iD = 1.0f / (rs.y - rs.x);
+  const V rsu = rs * s.un;
+  const float SM = (rsu.y - rsu.x - s.dpt.y + s.dpt.x) * iD;
+  const float pdis = s.rho.x * s.rho.y * sv.y * sv.x * (s.un.y - s.un.x) * iD;
+  const float dpts = (rs.y * s.dpt.x - rs.x * s.dpt.y) * iD + pdis;   // p_T* - P_hat
+  // both sides' HLLD intermediate states (star_diff of riemann.cuh, paired)
+  const V SMv = vv(SM), bnv = vv(bn);
+  const V qv = S2 - SMv;
+  const V iq = rcp(qv);
+  const V smu = SMv - s.un;
+  const V rhos = rs * iq;
+  const float bn2 = bn * bn;
+  const V den = fma(rs, qv, vv(-bn2));
+  const V scl = fma(rs, sv, vv(bn2));
+  const B2 deg = vabs(den) < vv(1e-12f) * scl;
+  const V iden = rcp(den);
+  const V fv = sel(deg, vv(0.0f), bnv * smu * iden);
+  const V dbf = sel(deg, vv(0.0f), rs * smu * iden);
+  const V vs1 = fma(neg(s.bt1), fv, s.ut1), vs2 = fma(neg(s.bt2), fv, s.ut2);
+  const V bs1 = fma(s.bt1, dbf, s.bt1), bs2 = fma(s.bt2, dbf, s.bt2);
+  const V vbs = fma(vs2, bs2, fma(vs1, bs1, SMv * bnv));
+  V dU[7];
+  dU[RF_RHO] = s.rho * smu * iq;
+  dU[RF_MN] = fma(rhos, SMv, neg(s.rho * s.un));
+  dU[RF_MT1] = fma(rhos, vs1, neg(s.rho * s.ut1));
+  dU[RF_MT2] = fma(rhos, vs2, neg(s.rho * s.ut2));
+  dU[RF_E] = fma(bnv, s.vb - vbs, fma(vv(dpts) - s.dpt, SMv, smu * s.enth)) * iq;
+  dU[RF_BT1] = s.bt1 * dbf;
+  dU[RF_BT2] = s.bt2 * dbf;
+  const V sq = sqrt2(rhos);
+  const float abn = fabsf(bn);
+  const V Ss = fma(vv(-abn, abn), rcp(sq), SMv);   // (S*_L, S*_R)
+  const bool outL = SL >= 0.0f, outR = !outL && SR < 0.0f, fan = !outL && !outR;
+  const bool starL = Ss.x >= 0.0f, starR = !starL && Ss.y < 0.0f, dbl = fan && !starL && !starR;
+  const bool left = outL || (fan && (starL || (!starR && SM >= 0.0f)));
+  const float sgn = bn >= 0.0f ? 1.0f : -1.0f;
+  const float isum = 1.0f / (sq.x + sq.y);
+  const V sqv1 = sq * vs1, sqv2 = sq * vs2;
+  const float vss1 = (sqv1.x + sqv1.y + (bs1.y - bs1.x) * sgn) * isum;
+  const float vss2 = (sqv2.x + sqv2.y + (bs2.y - bs2.x) * sgn) * isum;
+  const float sqLR = sq.x * sq.y;
+  const float bss1 = (sq.x * bs1.y + sq.y * bs1.x + sqLR * (vs1.y - vs1.x) * sgn) * isum;
+  const float bss2 = (sq.x * bs2.y + sq.y * bs2.x + sqLR * (vs2.y - vs2.x) * sgn) * isum;
+  const float vbss = SM * bn + vss1 * bss1 + vss2 * bss2;
+  auto pick = [&](const V &v) { return left ? v.x : v.y; };
+  const float S = left ? SL : SR, Ssx = pick(Ss), rhosx = pick(rhos);
+  const float sqs = left ? -sq.x : sq.y;
+  const float v1 = pick(vs1), v2 = pick(vs2), b1 = pick(bs1), b2 = pick(bs2);
+  const float vbsx = SM * bn + v1 * b1 + v2 * b2;
+  float d2[7];
+  d2[RF_RHO] = 0.0f; d2[RF_MN] = 0.0f;
+  d2[RF_MT1] = rhosx * (vss1 - v1); d2[RF_MT2] = rhosx * (vss2 - v2);
+  d2[RF_E] = sqs * (vbsx - vbss) * sgn;
+  d2[RF_BT1] = bss1 - b1; d2[RF_BT2] = bss2 - b2;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const float fx = pick(s.F[q]);
+    const float t1 = fan ? S * pick(dU[q]) : 0.0f;
+    const float t2 = dbl ? Ssx * d2[q] : 0.0f;
+    f[q] = fx + t1 + t2;
+  }
+  // LHLLD: inside the fan the dissipative part of p_T* is scaled by xi
+  if (fan && xi != 1.0f && SR > 0.0f) {
+    f[RF_MN] += (xi - 1.0f) * pdis;
+    f[RF_E] += (xi - 1.0f) * pdis * SM;
+  }
+  const float scale = 1e-12f * fmaxf(s.rho.x, s.rho.y) * fmaxf(fabsf(SL), fabsf(SR));
+  up = f[RF_RHO] > scale ? 1 : (f[RF_RHO] < -scale ? -1 : 0);
+}
+
+}  // namespace x2
+}  // namespace phl

@@ -88,7 +88,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
 // Flux of the D-face at the lower side of staged cell s2 (its right cell),
 // tile cell (i, j, k), global cell c.  Returns the five fluid components in
 // out[] and stores the EMF inputs when the tile owns the face.
-template <int D>
+template <int D, bool LR>
 __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int s2, int i,
                                            int j, int k, const int *c, bool own, float *__restrict__ Fd,
                                            const GasK<float> &K, float *out, int *dflag) {
@@ -142,7 +142,8 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
   const int solver = (fr[0] | fr[-fs]) ? SOLVER_HLL : G.riemann;
   float fl[7];
   int up;
-  riemann_dev<float, 0, true>(wl, wr, bn, brho, bp, 0.0f, 0.0f, 0, solver, G.machf, fl, up, K);
+  if constexpr (LR) x2::riemann_ideal_lr(wl, wr, bn, brho, bp, solver, G.machf, fl, up, K);
+  else riemann_dev<float, 0, true>(wl, wr, bn, brho, bp, 0.0f, 0.0f, 0, solver, G.machf, fl, up, K);
   // reflecting wall face: a symmetry plane; only the normal-momentum flux survives
   if ((c[D] == 0 && G.bc[D][0] == 1) || (c[D] == G.n[D] && G.bc[D][1] == 1)) {
 #pragma unroll
@@ -163,7 +164,7 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
 
 // Evaluates face f of direction D (its index among the tile's D-faces) and
 // returns the five fluid flux components (zeros outside the domain).
-template <int D>
+template <int D, bool LR>
 __device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int f, int x0,
                                           int y0, int z0, float *F0, float *F1, float *F2, const GasK<float> &K,
                                           float *out, int *dflag) {
@@ -181,7 +182,7 @@ __device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, con
   const int loc = D == 0 ? i : (D == 1 ? j : k);
   const bool own = loc < ext || c[D] == G.n[D];
   float *Fd = D == 0 ? F0 : (D == 1 ? F1 : F2);
-  fused_face<D>(G, S, sm, s2, i, j, k, c, own, Fd, K, out, dflag);
+  fused_face<D, LR>(G, S, sm, s2, i, j, k, c, own, Fd, K, out, dflag);
 }
 
 // Two D-faces of the tile (fa, fb: indices among its D-faces) evaluated
@@ -314,7 +315,7 @@ __device__ __forceinline__ void tile_face2(const DevGeo &G, const StageMx &S, co
 
 // One direction's faces of the tile through the face buffer, then each
 // thread's running residuals of its cells (phased variant).
-template <int D, int NT, int CPT, int FS, bool PAIRED>
+template <int D, int NT, int CPT, int FS, bool PAIRED, bool LR>
 __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, FusedSmem &sm, float *fb, int tid,
                                            int x0, int y0, int z0, float *F0, float *F1, float *F2,
                                            const GasK<float> &K, float (*racc)[5], int *dflag) {
@@ -336,7 +337,7 @@ __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, Fu
   } else {
     for (int f = tid; f < NXF; f += NT) {
       float out[5];
-      tile_face<D>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      tile_face<D, LR>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
 #pragma unroll
       for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
     }
@@ -366,7 +367,7 @@ __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, Fu
 // direction's faces; each thread keeps the running residuals of its cells in
 // registers (same summation order x, y, z), so the CTA needs ~1/3 of the
 // shared memory and more CTAs fit on an SM.
-template <int NT, int MINB, bool PHASED, bool PAIRED = false>
+template <int NT, int MINB, bool PHASED, bool PAIRED = false, bool LR = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_flux_update_mx(const __grid_constant__ CUtensorMap tmW, DevGeo G, StageMx S, const uint8_t *__restrict__ flag,
                      float *__restrict__ F0, float *__restrict__ F1, float *__restrict__ F2, int ntx, int nty,
@@ -457,16 +458,16 @@ __global__ void __launch_bounds__(NT, MINB)
 
   if constexpr (PHASED) {
     static_assert(NXF == NYF && NYF == NZF, "phased tiles need equal face counts per direction");
-    tile_phase<0, NT, CPT, FS, PAIRED>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
-    tile_phase<1, NT, CPT, FS, PAIRED>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
-    tile_phase<2, NT, CPT, FS, PAIRED>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<0, NT, CPT, FS, PAIRED, LR>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<1, NT, CPT, FS, PAIRED, LR>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<2, NT, CPT, FS, PAIRED, LR>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
   } else {
     // NXF and NXF + NYF are multiples of 32: the direction is uniform in a warp
     for (int f = tid; f < NFACE; f += NT) {
       float out[5];
-      if (f < NXF) tile_face<0>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
-      else if (f < NXF + NYF) tile_face<1>(G, S, sm, f - NXF, x0, y0, z0, F0, F1, F2, K, out, dflag);
-      else tile_face<2>(G, S, sm, f - NXF - NYF, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      if (f < NXF) tile_face<0, LR>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      else if (f < NXF + NYF) tile_face<1, LR>(G, S, sm, f - NXF, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      else tile_face<2, LR>(G, S, sm, f - NXF - NYF, x0, y0, z0, F0, F1, F2, K, out, dflag);
 #pragma unroll
       for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
     }
@@ -728,6 +729,12 @@ cudaError_t fused_init() {
     e = cudaFuncSetAttribute(k_flux_update_mx<288, 1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes(true));
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<288, 3, true, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, false, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false));
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes(true));
   done = e;
@@ -777,21 +784,23 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   }
   const CUtensorMap *tm = (const CUtensorMap *)M.tmapW;
   // launch shapes: (threads, min CTAs per SM, phased)
-#define PHL_FUSED(NT, MB, PH, PA)                                                                               \
+#define PHL_FUSED(NT, MB, PH, PA, LRS)                                                                          \
   do {                                                                                                         \
     PHL_LAUNCH(KC_FLUX_UPDATE, prof, s,                                                                        \
-               (k_flux_update_mx<NT, MB, PH, PA><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0],        \
+               (k_flux_update_mx<NT, MB, PH, PA, LRS><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0],   \
                                                                                  M.F[1], M.F[2], ntx, nty,     \
                                                                                  M.dflag, M.test_extra_tx)));  \
   } while (0)
   switch (M.fused_variant) {
-    case 2: PHL_FUSED(288, 3, true, false); break;
-    case 3: PHL_FUSED(256, 3, true, false); break;
-    case 4: PHL_FUSED(384, 2, true, false); break;
-    case 5: PHL_FUSED(288, 1, true, true); break;
-    case 6: PHL_FUSED(256, 2, true, true); break;
-    case 7: PHL_FUSED(288, 2, true, true); break;
-    default: PHL_FUSED(256, 2, false, false); break;
+    case 2: PHL_FUSED(288, 3, true, false, false); break;
+    case 3: PHL_FUSED(256, 3, true, false, false); break;
+    case 4: PHL_FUSED(384, 2, true, false, false); break;
+    case 5: PHL_FUSED(288, 1, true, true, false); break;
+    case 6: PHL_FUSED(256, 2, true, true, false); break;
+    case 7: PHL_FUSED(288, 2, true, true, false); break;
+    case 8: PHL_FUSED(288, 3, true, false, true); break;
+    case 9: PHL_FUSED(256, 2, false, false, true); break;
+    default: PHL_FUSED(256, 2, false, false, false); break;
   }
 #undef PHL_FUSED
   ++*nl;

@@ -53,6 +53,22 @@ __global__ void k_riemann_batch_x2(long n, const double *wl, const double *wr, c
   }
 }
 
+// One face per thread through the left/right-paired ideal-gas solver.
+__global__ void k_riemann_batch_lr(long n, const double *wl, const double *wr, const double *bn, const double *bg,
+                                   int solver, double mthr, double *f) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    float l[9], r[9], out[7];
+    for (int q = 0; q < 9; ++q) { l[q] = (float)wl[t * 9 + q]; r[q] = (float)wr[t * 9 + q]; }
+    GasK<float> K;
+    K.g = (float)bg[4 * t + 2];
+    K.igm1 = 1.0f / (K.g - 1.0f);
+    K.ggm1 = K.g * K.igm1;
+    int up;
+    x2::riemann_ideal_lr(l, r, (float)bn[t], (float)bg[4 * t], (float)bg[4 * t + 1], solver, (float)mthr, out, up, K);
+    for (int q = 0; q < 7; ++q) f[t * 7 + q] = (double)out[q];
+  }
+}
+
 __global__ void k_convert_batch(long n, const double *x, int k, float *f, double *back) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
     const float v = d2f_scaled(x[t], k);
@@ -85,7 +101,7 @@ extern "C" phl_status phl_riemann_batch(long n, const double *wl, const double *
                                         const double *bg, int nspec, int solver, double mach_thr,
                                         int precision, double *f) {
   if (n < 0 || nspec < 0 || nspec > PHL_MAXSPEC || solver < 0 || solver > 2) return PHL_EINVAL;
-  if (precision == 2 && nspec != 0) return PHL_EINVAL;
+  if ((precision == 2 || precision == 3) && nspec != 0) return PHL_EINVAL;
   if (n == 0) return PHL_OK;
   if (!wl || !wr || !bn || !bg || !f) return PHL_EINVAL;
   const size_t nw = 9 + nspec, nf = 7 + nspec;
@@ -102,6 +118,8 @@ extern "C" phl_status phl_riemann_batch(long n, const double *wl, const double *
     k_riemann_batch<double><<<blocks, 128>>>(n, dwl, dwr, dbn, dbg, nspec, solver, mach_thr, df);
   else if (precision == 2)
     k_riemann_batch_x2<<<blocks, 128>>>(n, dwl, dwr, dbn, dbg, solver, mach_thr, df);
+  else if (precision == 3)
+    k_riemann_batch_lr<<<blocks, 128>>>(n, dwl, dwr, dbn, dbg, solver, mach_thr, df);
   else
     k_riemann_batch<float><<<blocks, 128>>>(n, dwl, dwr, dbn, dbg, nspec, solver, mach_thr, df);
   cudaError_t e = cudaMemcpy(f, df, n * nf * sizeof(double), cudaMemcpyDeviceToHost);

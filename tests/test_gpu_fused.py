@@ -64,7 +64,7 @@ def test_fused_matches_per_direction_and_oracle(P, bc):
         assert l_fo[k] <= 1e-5, ("fused vs oracle", k, l_fo[k])
 
 
-@pytest.mark.parametrize("shape", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("shape", [2, 3, 4, 5, 6, 7, 8, 9])
 def test_fused_launch_shapes_agree(P, shape):
     """Every launch shape of the tile kernel (phased faces, other CTA sizes,
     two faces per thread on FP32x2 arithmetic) gives the per-direction result
@@ -76,7 +76,7 @@ def test_fused_launch_shapes_agree(P, shape):
     dt = 0.5 * O.Oracle(pr).dt(dict(cons=pr.cons, bx=pr.bx, by=pr.by, bz=pr.bz))
     a = run(P, pr, shape, 4, dt)
     b = run(P, pr, 0, 4, dt)
-    tol = 1e-6 if shape <= 4 else 1e-5
+    tol = 1e-6 if shape <= 4 else 1e-5   # paired shapes round their explicit FMAs differently
     for k, v in deviation_l1(pr, a, b).items():
         assert v <= tol, (shape, k, v)
 

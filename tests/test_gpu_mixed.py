@@ -215,14 +215,16 @@ def test_riemann_fp32x2_pairs(P, solver, regime):
             d[:, 6] = rng.uniform(0.1, 2.0, n)
         bn = rng.normal(size=n) * rng.choice([0.0, 1e-3, 1.0], size=n)
     kw = dict(bg=bg, solver=solver)
-    fx2 = P.riemann_batch(dl, dr, bn, precision="mixed_x2", **kw)
     f32 = P.riemann_batch(dl, dr, bn, precision="mixed", **kw)
     f64 = P.riemann_batch(dl, dr, bn, precision="fp64", **kw)
-    assert np.all(np.isfinite(fx2))
     scale = np.abs(f64).max(axis=0) + 1e-300
-    err = (np.abs(fx2 - f64) / scale).max(axis=0)
     err32 = (np.abs(f32 - f64) / scale).max(axis=0)
-    # the pair solver is as accurate as the scalar FP32 one (a few FP32 ulps
-    # of each component's scale; the deviation form keeps low-Mach fluxes
-    # free of cancellation)
-    assert np.all(err < np.maximum(4.0 * err32, 1e-5)), (err, err32)
+    # both paired solvers (two faces per thread; left/right states of one face)
+    # are as accurate as the scalar FP32 one (a few FP32 ulps of each
+    # component's scale; the deviation form keeps low-Mach fluxes free of
+    # cancellation)
+    for prec in ("mixed_x2", "mixed_lr"):
+        fp = P.riemann_batch(dl, dr, bn, precision=prec, **kw)
+        assert np.all(np.isfinite(fp)), prec
+        err = (np.abs(fp - f64) / scale).max(axis=0)
+        assert np.all(err < np.maximum(4.0 * err32, 1e-5)), (prec, err, err32)
