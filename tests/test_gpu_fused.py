@@ -2,12 +2,12 @@
 all three directions and the cell update) against the per-direction kernels
 and against the FP64 CPU oracle.
 
-Both GPU paths evaluate the same FP32 arithmetic on the same deviations; they
-may differ only in how the compiler contracts products into FMAs, so they are
-compared with a bound of a few FP32 roundings per step, and each is held to
-the mixed form's accuracy bar against the oracle (relative L1 of the
-deviations <= 1e-5 per field).  Grid sizes are not multiples of the 8^3 tile,
-so ragged tiles are exercised on every face.
+Both GPU paths evaluate the same method in FP32 on the same deviations; the
+default tile shape pairs the left and right states of a face on FP32x2
+arithmetic with explicit FMAs, so the two agree to FP32 rounding (relative L1
+of the deviations <= 1e-5, the mixed form's bar; the scalar tile shapes to
+1e-6), and each is held to the same bar against the oracle.  Grid sizes are
+not multiples of the 8^3 tile, so ragged tiles are exercised on every face.
 """
 import numpy as np
 import pytest
@@ -59,7 +59,7 @@ def test_fused_matches_per_direction_and_oracle(P, bc):
     print(bc, "fused vs per-direction", {k: f"{v:.1e}" for k, v in l_fp.items()})
     print(bc, "fused vs oracle", {k: f"{v:.1e}" for k, v in l_fo.items()})
     for k, v in l_fp.items():
-        assert v <= 1e-6, ("fused vs per-direction", k, v)
+        assert v <= 1e-5, ("fused vs per-direction", k, v)
     for k in ("rho", "mx", "my", "mz", "E", "bx"):
         assert l_fo[k] <= 1e-5, ("fused vs oracle", k, l_fo[k])
 
