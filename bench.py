@@ -60,13 +60,15 @@ FP64_FLOP_PER_FACE = 807.0
 FP32_FLOP_PER_FACE = {"flux_x": 381.1, "flux_y": 381.1, "flux_z": 380.1}
 FP32_DRAM_BYTES_PER_FACE = {"flux_x": 74.4, "flux_y": 75.8, "flux_z": 76.1}
 FP32_NOMINAL_TFLOPS = 80.5
-# Fused tile kernel (k_flux_update_mx, default launch shape): from the ncu
-# counters of the stratified box at 160^3 (W larger than L2), one launch of
-# stage 1 and one of stage 2: FP32 operations (FADD + FMUL + 2 FFMA) 1398 per
-# cell as executed, i.e. 414 per face over the 3.375 faces per cell an 8^3
-# tile evaluates; the algorithmic count is 3 faces per cell x 414 = 1243.
-# DRAM bytes per cell: 113.2 (stage 1, no increment to read) and 145.7
-# (stages 2-3), 134.9 on average over an RK3 step.
+# Fused tile kernel (k_flux_update_mx): from the ncu counters of the
+# stratified box at 160^3 (W larger than L2), one launch of stage 1 and one of
+# stage 2 of the scalar launch shape (2): FP32 operations (FADD + FMUL + 2 FFMA)
+# 1398 per cell as executed, i.e. 414 per face over the 3.375 faces per cell
+# an 8^3 tile evaluates; the algorithmic count is 3 faces per cell x 414 =
+# 1243.  The default shape evaluates the same operations, partly as packed
+# FP32x2 instructions that those per-opcode counters do not include.  DRAM
+# bytes per cell (both shapes): 113.2 (stage 1, no increment to read) and
+# 145.6 (stages 2-3), 134.9 on average over an RK3 step.
 FUSED_FLOP_PER_CELL = 3.0 * 414.3
 FUSED_DRAM_BYTES_PER_CELL = (113.2 + 2.0 * 145.7) / 3.0
 
