@@ -16,6 +16,7 @@ from . import build as _build
 ORA_MAXSPEC = 4
 _RIEMANN = {"lhlld": 0, "hlld": 1, "hll": 2}
 _EOS = {"ideal": 0, "stellar": 1}
+_RECON = {"vanleer": 0, "pph": 1}
 
 _dp = C.POINTER(C.c_double)
 
@@ -30,7 +31,7 @@ class OraCfg(C.Structure):
         ("bg_ge_c", _dp), ("bg_gc_c", _dp), ("bg_ge_f", _dp), ("bg_gc_f", _dp),
         ("heat", _dp), ("cfl", C.c_double), ("rk", C.c_int), ("riemann", C.c_int),
         ("eps_sf", C.c_double), ("mach_thr", C.c_double), ("newton_tol", C.c_double),
-        ("newton_maxit", C.c_int), ("eos_table", C.c_void_p),
+        ("newton_maxit", C.c_int), ("eos_table", C.c_void_p), ("recon", C.c_int),
     ]
 
 
@@ -123,6 +124,7 @@ class Oracle:
         c.newton_tol = newton_tol
         c.newton_maxit = newton_maxit
         c.eos_table = eos_table
+        c.recon = _RECON[pr.recon]
         self.cfg = c
 
     # ------------------------------------------------------------------

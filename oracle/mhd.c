@@ -228,6 +228,33 @@ static inline double vl_slope(double a, double b, double c) {
   return 0.0;
 }
 
+/* ---------------- PPH reconstruction (Sect. 2.5, item ii) ----------------
+ * Third order on the three-cell stencil: the parabola whose averages over
+ * cells i-1, i, i+1 are the three cell values, evaluated at the cell's faces.
+ * Its right-face value is (-W_{i-1} + 5 W_i + 2 W_{i+1}) / 6 and its
+ * left-face value (2 W_{i-1} + 5 W_i - W_{i+1}) / 6.  Unlimited for every
+ * primitive variable except the mass fractions.  Those take the limited
+ * parabola (reading: the monotonicity constraints of the piecewise parabolic
+ * method of Colella & Woodward 1984 -- each face value clipped to the range
+ * of the two cells sharing the face; a cell that is a local extremum stays
+ * constant; a parabola that would overshoot inside the cell has its far face
+ * value pulled back so that it is monotone there). */
+static inline double pph_right(double a, double b, double c) { return (-a + 5.0 * b + 2.0 * c) / 6.0; }
+static inline double pph_left(double a, double b, double c) { return (2.0 * a + 5.0 * b - c) / 6.0; }
+static inline double clip(double v, double x, double y) {
+  double lo = x < y ? x : y, hi = x < y ? y : x;
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+/* limited left and right face values of the cell with value b between a and c */
+static inline void pph_limited(double a, double b, double c, double *fl, double *fr) {
+  if ((b - a) * (c - b) <= 0.0) { *fl = b; *fr = b; return; }
+  double l = clip(pph_left(a, b, c), a, b), r = clip(pph_right(a, b, c), b, c);
+  const double d = r - l, a6 = 6.0 * (b - 0.5 * (l + r));
+  if (d * a6 > d * d) l = 3.0 * b - 2.0 * r;
+  else if (d * a6 < -d * d) r = 3.0 * b - 2.0 * l;
+  *fl = l; *fr = r;
+}
+
 /* ---------------- Riemann solvers (Sect. 2.6) ---------------- */
 /* Normal-frame state: rho, un, ut1, ut2, Bt1, Bt2, P, ge, gc, X.. */
 enum { R_RHO = 0, R_UN, R_UT1, R_UT2, R_BT1, R_BT2, R_P, R_GE, R_GC, R_X0 };
@@ -588,10 +615,22 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
           long sd = G->s[d];
           double wl[10 + ORA_MAXSPEC], wr[10 + ORA_MAXSPEC];
           for (int q = 0; q < G->nw; ++q) {
-            double sL = vl_slope(w->W[q][pL - sd], w->W[q][pL], w->W[q][pR]);
-            double sR = vl_slope(w->W[q][pL], w->W[q][pR], w->W[q][pR + sd]);
-            wl[q] = w->W[q][pL] + 0.5 * sL;
-            wr[q] = w->W[q][pR] - 0.5 * sR;
+            const double a = w->W[q][pL - sd], b = w->W[q][pL], cc = w->W[q][pR], e = w->W[q][pR + sd];
+            if (c->recon == ORA_RECON_PPH) {   /* left state: cell pL's right face; right state: pR's left face */
+              if (q < W_X0) { wl[q] = pph_right(a, b, cc); wr[q] = pph_left(b, cc, e); }
+              else {
+                double fl_, fr_;
+                pph_limited(a, b, cc, &fl_, &fr_);
+                wl[q] = fr_;
+                pph_limited(b, cc, e, &fl_, &fr_);
+                wr[q] = fl_;
+              }
+            } else {
+              double sL = vl_slope(a, b, cc);
+              double sR = vl_slope(b, cc, e);
+              wl[q] = b + 0.5 * sL;
+              wr[q] = cc - 0.5 * sR;
+            }
           }
           int k = c3[2];
           bgstate bf = (d == 2) ? bg_zface(G, k) : bg_cell(G, k);

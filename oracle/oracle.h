@@ -26,6 +26,7 @@ extern "C" {
 enum { ORA_PERIODIC = 0, ORA_REFLECT = 1, ORA_OUTFLOW = 2 };
 enum { ORA_EOS_IDEAL = 0, ORA_EOS_STELLAR = 1 };
 enum { ORA_LHLLD = 0, ORA_HLLD = 1, ORA_HLL = 2 };
+enum { ORA_RECON_VANLEER = 0, ORA_RECON_PPH = 1 };
 #define ORA_MAXSPEC 4
 
 typedef struct {
@@ -50,6 +51,7 @@ typedef struct {
   double newton_tol;        /* stellar EOS */
   int newton_maxit;
   const void *eos_table;    /* stellar EOS table (ora_eos_table_build) */
+  int recon;                /* ORA_RECON_VANLEER (limited linear) or ORA_RECON_PPH */
 } ora_cfg;
 
 /* Advance nsteps SSP-RK steps in place.  dt_fixed > 0 uses that step;

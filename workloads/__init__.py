@@ -51,6 +51,7 @@ class Problem:
     heat: Optional[np.ndarray] = None   # volumetric heating rate per z-cell (nz,)
     cfl: float = 0.4
     riemann: str = "lhlld"        # lhlld | hlld | hll
+    recon: str = "vanleer"        # vanleer (limited linear) | pph (third-order parabolic)
     eps_sf: float = 0.2           # shock-flattening threshold; 0 switches it off
     mach_thr: float = 0.6
     nspec: int = 0
