@@ -60,6 +60,7 @@ typedef enum {
 enum { PHL_PERIODIC = 0, PHL_REFLECT = 1, PHL_OUTFLOW = 2 };
 enum { PHL_EOS_IDEAL = 0, PHL_EOS_STELLAR = 1 };
 enum { PHL_LHLLD = 0, PHL_HLLD = 1, PHL_HLL = 2 };
+enum { PHL_RECON_VANLEER = 0, PHL_RECON_PPH = 1 };
 enum { PHL_FP64 = 0, PHL_MIXED = 1 };
 enum { PHL_HOST = 0, PHL_DEVICE = 1 };
 #define PHL_MAXSPEC 4
@@ -99,6 +100,12 @@ typedef struct {
   const struct phl_eos_table *eos_table;  /* stellar EOS table (not owned)      */
   const struct phl_mlp *mlp;  /* temperature-guess network when use_mlp (not owned) */
   double bg_X[PHL_MAXSPEC]; /* stellar: mass fractions of the background        */
+  /* Reconstruction (Sect. 2.5): PHL_RECON_VANLEER, limited linear (van Leer
+   * slope, item i; the default, 0); PHL_RECON_PPH, the three-cell parabola of
+   * item ii -- unlimited for the primitive variables, limited for the mass
+   * fractions (the piecewise-parabolic method's monotonicity constraints).
+   * Both use the same three-cell stencil per face side. */
+  int recon;
 } phl_grid_desc;
 
 typedef struct {

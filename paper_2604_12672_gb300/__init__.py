@@ -20,6 +20,7 @@ PERIODIC, REFLECT, OUTFLOW = 0, 1, 2
 EOS = {"ideal": 0, "stellar": 1}
 RIEMANN = {"lhlld": 0, "hlld": 1, "hll": 2}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_x2": 2, "mixed_lr": 3}
+RECON = {"vanleer": 0, "pph": 1}
 HOST, DEVICE = 0, 1
 STATUS = {0: "PHL_OK", 1: "PHL_EINVAL", 2: "PHL_ECUDA", 3: "PHL_ENOMEM", 4: "PHL_ENEGATIVE",
           5: "PHL_ENAN", 6: "PHL_ENEWTON", 7: "PHL_ETIMEOUT", 8: "PHL_EUNSUPPORTED"}
@@ -46,6 +47,7 @@ class GridDesc(C.Structure):
         ("newton_tol", C.c_double), ("newton_maxit", C.c_int), ("use_mlp", C.c_int),
         ("stream", C.c_void_p),
         ("eos_table", C.c_void_p), ("mlp", C.c_void_p), ("bg_X", C.c_double * PHL_MAXSPEC),
+        ("recon", C.c_int),
     ]
 
 
@@ -353,6 +355,7 @@ def make_desc(pr, precision="fp64", riemann=None, eps_sf=None, cfl=None, rk=3, w
     d.precision = PRECISION[precision]
     d.newton_tol = newton_tol
     d.newton_maxit = newton_maxit
+    d.recon = RECON[getattr(pr, "recon", "vanleer")]
     d.use_mlp = int(mlp_mode) if mlp is not None else 0
     d.mlp = mlp.h if mlp is not None else None
     d.stream = stream

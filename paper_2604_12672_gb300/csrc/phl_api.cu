@@ -286,6 +286,7 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   if (!(d->cfl > 0.0)) return fail(PHL_EINVAL, "cfl must be positive");
   if (d->rk != 2 && d->rk != 3) return fail(PHL_EINVAL, "rk must be 2 or 3");
   if (d->riemann < 0 || d->riemann > 2) return fail(PHL_EINVAL, "bad riemann solver");
+  if (d->recon != PHL_RECON_VANLEER && d->recon != PHL_RECON_PPH) return fail(PHL_EINVAL, "bad reconstruction");
   if (d->precision != PHL_FP64 && d->precision != PHL_MIXED) return fail(PHL_EINVAL, "bad precision mode");
   if (d->bg_rho_c && (!d->bg_p_c || !d->bg_rho_f || !d->bg_p_f))
     return fail(PHL_EINVAL, "incomplete background profiles");
@@ -325,6 +326,7 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   G.eos = d->eos;
   G.gamma = d->gamma;
   G.riemann = d->riemann;
+  G.recon = d->recon;
   G.eps_sf = d->eps_sf;
   G.mach_thr = d->mach_thr;
   G.cfl = d->cfl;

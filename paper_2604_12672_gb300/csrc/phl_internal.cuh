@@ -56,6 +56,7 @@ struct DevGeo {
   const double *heat;          // per z-cell, may be null
   double g[3];
   int riemann;
+  int recon;                   // PHL_RECON_VANLEER / PHL_RECON_PPH
   double eps_sf, mach_thr, cfl;
   // FP32 copies for the mixed-precision kernels (no per-thread conversions)
   // Mixed form: the FP32 quantities are held in units of powers of two

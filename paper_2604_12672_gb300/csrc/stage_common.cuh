@@ -93,6 +93,30 @@ __device__ __forceinline__ R vl_slope(R a, R b, R c) {
   return (dm * dp > R(0)) ? R(2) * dm * dp / (dm + dp) : R(0);
 }
 
+// PPH (Sect. 2.5, item ii): the parabola whose averages over cells i-1, i,
+// i+1 are (a, b, c), at the cell's right and left faces; unlimited.
+template <typename R>
+__device__ __forceinline__ R pph_right(R a, R b, R c) { return (-a + R(5) * b + R(2) * c) / R(6); }
+template <typename R>
+__device__ __forceinline__ R pph_left(R a, R b, R c) { return (R(2) * a + R(5) * b - c) / R(6); }
+// Limited parabola for mass fractions: face values clipped to the range of the
+// two cells sharing the face, a local extremum stays constant, and the far
+// face value is pulled back where the parabola would overshoot inside the
+// cell (the piecewise parabolic method's monotonicity constraints, Colella &
+// Woodward 1984).  Returns the cell's left and right face values.
+template <typename R>
+__device__ __forceinline__ void pph_limited(R a, R b, R c, R &fl, R &fr) {
+  if ((b - a) * (c - b) <= R(0)) { fl = b; fr = b; return; }
+  R l = pph_left(a, b, c), r = pph_right(a, b, c);
+  l = fmin(fmax(l, fmin(a, b)), fmax(a, b));
+  r = fmin(fmax(r, fmin(b, c)), fmax(b, c));
+  const R d = r - l, a6 = R(6) * (b - R(0.5) * (l + r));
+  if (d * a6 > d * d) l = R(3) * b - R(2) * r;
+  else if (d * a6 < -d * d) r = R(3) * b - R(2) * l;
+  fl = l;
+  fr = r;
+}
+
 __device__ __forceinline__ long wstride(const DevGeo &G, int d) { return d == 0 ? 1L : (d == 1 ? G.wy : G.wz); }
 
 template <typename R>
@@ -209,8 +233,21 @@ __device__ __forceinline__ void flux_face(const DevGeo &G, const int *c, long pR
   for (int v = 0; v < NWC; ++v) {
     if (v >= G.nw || (ideal && (v == W_GE || v == W_GC))) continue;
     const R w0 = fetch(v, 0), w1 = fetch(v, 1), w2 = fetch(v, 2), w3 = fetch(v, 3);
-    ql[v] = w1 + R(0.5) * vl_slope(w0, w1, w2);
-    qr[v] = w2 - R(0.5) * vl_slope(w1, w2, w3);
+    if (G.recon == PHL_RECON_PPH) {   // left state: cell pL's right face; right state: pR's left face
+      if (v < W_X0) {
+        ql[v] = pph_right(w0, w1, w2);
+        qr[v] = pph_left(w1, w2, w3);
+      } else {
+        R fl, fr;
+        pph_limited(w0, w1, w2, fl, fr);
+        ql[v] = fr;
+        pph_limited(w1, w2, w3, fl, fr);
+        qr[v] = fl;
+      }
+    } else {
+      ql[v] = w1 + R(0.5) * vl_slope(w0, w1, w2);
+      qr[v] = w2 - R(0.5) * vl_slope(w1, w2, w3);
+    }
   }
   if (ideal) {   // not used by the ideal-gas solver (constant gamma)
     ql[W_GE] = qr[W_GE] = R(0);

@@ -102,9 +102,15 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
       a[m] = sm.w[0][s2 + (m - 2) * sD];
       b[m] = sm.w[1][s2 + (m - 2) * sD];
     }
+    const bool pph = G.recon == PHL_RECON_PPH;
     auto plm = [&](int v, float w0, float w1, float w2, float w3) {
-      ql[v] = w1 + 0.5f * vl_slope(w0, w1, w2);
-      qr[v] = w2 - 0.5f * vl_slope(w1, w2, w3);
+      if (pph) {   // unlimited parabola (no mass fractions on this path)
+        ql[v] = pph_right(w0, w1, w2);
+        qr[v] = pph_left(w1, w2, w3);
+      } else {
+        ql[v] = w1 + 0.5f * vl_slope(w0, w1, w2);
+        qr[v] = w2 - 0.5f * vl_slope(w1, w2, w3);
+      }
     };
     plm(W_RHO, a[0].x, a[1].x, a[2].x, a[3].x);
     plm(W_VX, a[0].y, a[1].y, a[2].y, a[3].y);
@@ -241,8 +247,14 @@ __device__ __forceinline__ void tile_face2(const DevGeo &G, const StageMx &S, co
         auto comp = [&](const float4 &u) { return e == 0 ? u.x : (e == 1 ? u.y : (e == 2 ? u.z : u.w)); };
         const V w0 = vv(comp(A[0]), comp(Bv[0])), w1 = vv(comp(A[1]), comp(Bv[1]));
         const V w2 = vv(comp(A[2]), comp(Bv[2])), w3 = vv(comp(A[3]), comp(Bv[3]));
-        ql[v] = fma(half, slope(w0, w1, w2), w1);
-        qr[v] = fma(neg(half), slope(w1, w2, w3), w2);
+        if (G.recon == PHL_RECON_PPH) {   // unlimited parabola: (-w0 + 5 w1 + 2 w2) / 6, (2 w1 + 5 w2 - w3) / 6
+          const V s6 = vv(1.0f / 6.0f), five = vv(5.0f), two = vv(2.0f);
+          ql[v] = fma(two, w2, fma(five, w1, neg(w0))) * s6;
+          qr[v] = (fma(two, w1, five * w2) - w3) * s6;
+        } else {
+          ql[v] = fma(half, slope(w0, w1, w2), w1);
+          qr[v] = fma(neg(half), slope(w1, w2, w3), w2);
+        }
       }
     }
   }
