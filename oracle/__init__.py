@@ -35,6 +35,10 @@ class OraCfg(C.Structure):
     ]
 
 
+class OraDiff(C.Structure):
+    _fields_ = [("k0", C.c_double), ("nT", C.c_int), ("nR", C.c_int), ("cv", C.c_double)]
+
+
 _lib = None
 
 
@@ -54,6 +58,13 @@ def lib():
         L.ora_riemann.argtypes = [_dp, _dp, C.c_double, C.c_int, C.c_int, C.c_double, _dp]
         L.ora_divb.restype = C.c_double
         L.ora_divb.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp]
+        L.ora_diffuse.restype = C.c_int
+        L.ora_diffuse.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp, _dp, C.POINTER(OraDiff), C.c_double, C.c_int,
+                                  C.POINTER(C.c_int)]
+        L.ora_rkl2_amp.restype = C.c_double
+        L.ora_rkl2_amp.argtypes = [C.c_int, C.c_double]
+        L.ora_sts_stages.restype = C.c_int
+        L.ora_sts_stages.argtypes = [C.c_double, C.c_double]
         L.ora_eos_table_build.restype = C.c_void_p
         L.ora_eos_table_build.argtypes = [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int]
         L.ora_eos_table_free.restype = None
@@ -166,6 +177,22 @@ class Oracle:
         return lib().ora_dt(C.byref(self.cfg), _ptr(np.ascontiguousarray(st["cons"])),
                             _ptr(np.ascontiguousarray(st["bx"])), _ptr(np.ascontiguousarray(st["by"])),
                             _ptr(np.ascontiguousarray(st["bz"])), _ptr(T))
+
+    def diffuse(self, dt, k0, nT=0, nR=0, cv=1.5, state=None, max_stages=100000):
+        """One RKL2 thermal-diffusion super step (diffusion.c); returns
+        (state dict with the new total energy, number of stages)."""
+        pr = self.pr
+        st = state or dict(cons=pr.cons, bx=pr.bx, by=pr.by, bz=pr.bz)
+        cons = np.ascontiguousarray(st["cons"], dtype=np.float64).copy()
+        p = OraDiff(k0=float(k0), nT=int(nT), nR=int(nR), cv=float(cv))
+        ns = C.c_int(0)
+        rc = lib().ora_diffuse(C.byref(self.cfg), _ptr(cons), *[_ptr(np.ascontiguousarray(st[k])) for k in ("bx", "by", "bz")],
+                               C.byref(p), float(dt), int(max_stages), C.byref(ns))
+        if rc != 0:
+            raise RuntimeError(f"oracle diffusion failed with code {rc}")
+        out = dict(st)
+        out["cons"] = cons
+        return out, ns.value
 
     def divb(self, state):
         return lib().ora_divb(C.byref(self.cfg), _ptr(np.ascontiguousarray(state["bx"])),

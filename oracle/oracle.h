@@ -54,6 +54,28 @@ typedef struct {
   int recon;                /* ORA_RECON_VANLEER (limited linear) or ORA_RECON_PPH */
 } ora_cfg;
 
+/* Thermal diffusion (Sect. 2.10): conductivity K = k0 T^nT / rho^nR with
+ * T = e_int / cv (ideal gas, code units). */
+typedef struct {
+  double k0;
+  int nT, nR;
+  double cv;
+} ora_diff;
+
+/* RKL2 coefficients mu_j, nu_j, mu~_j, gamma~_j (j = 1..s; arrays of s + 1),
+ * the amplification factor of an s-stage step at z = lambda dt, and the
+ * paper's stage count for a step dt against the parabolic limit dt_p. */
+void ora_rkl2_coeffs(int s, double *mu, double *nu, double *mut, double *gat);
+double ora_rkl2_amp(int s, double z);
+int ora_sts_stages(double dt, double dt_p);
+
+/* One RKL2 super step of length dt of rho d(e_int)/dt = div(K grad T) with
+ * rho, u, B fixed, on the ABI-layout state (cons updated in place: E only).
+ * *nsts_out receives the stage count.  Returns 0, -1 (bad input), -2
+ * (non-positive rho or e_int) or -4 (more than max_stages stages needed). */
+int ora_diffuse(const ora_cfg *cfg, double *cons, const double *bx, const double *by, const double *bz,
+                const ora_diff *p, double dt, int max_stages, int *nsts_out);
+
 /* Advance nsteps SSP-RK steps in place.  dt_fixed > 0 uses that step;
  * otherwise each step's dt comes from the CFL condition on U^n.
  * t (nullable) accumulates time; dt_last (nullable) receives the last dt.
