@@ -179,6 +179,34 @@ phl_status phl_set_timing(phl_grid *g, int on);
  * reset != 0 clears the totals afterwards. */
 phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, int reset);
 
+/* Thermal diffusion (Sect. 2.10): ideal gas with T = e_int / cv (code
+ * units) and conductivity K = k0 T^nT / rho^nR (nT = 0..4, nR = 0..2; a
+ * constant K: nT = nR = 0; radiative diffusion with a constant opacity,
+ * K = 4acT^3 / (3 kappa rho): nT = 3, nR = 1, k0 = 4ac / (3 kappa)). */
+typedef struct {
+  double k0;
+  int nT, nR;
+  double cv;
+} phl_diffusion;
+
+/* Advance rho d(e_int)/dt = div(K grad T) over dt with the density,
+ * velocity, magnetic field and mass fractions held fixed, by one RKL2 super
+ * step (Meyer, Balsara & Aslam 2012; Sect. 2.10 items i-iv) in FP64, and add
+ * rho times the change of e_int to the total energy.  The stage count is the
+ * paper's N_STS = max(1 + floor((sqrt(9 + 16 dt/dt_p) - 1)/2), 3) with the
+ * parabolic limit dt_p = 1/2 [max sum_s D/dx_s^2]^-1, D = K/(rho cv), of the
+ * state at the start of the step: the call reads that maximum back (one
+ * synchronisation of the grid's stream) and then enqueues N_STS + 1 kernels.
+ * Space: conservative seven-point operator, face conductivity the mean of
+ * the two cells', no flux through sides that are not periodic.  Call between
+ * MHD steps (e.g. Strang splitting: half dt, phl_step, half dt).  The first
+ * call allocates the grid's diffusion arrays (seven doubles per cell).
+ *   max_stages: PHL_EINVAL when N_STS would exceed it; *nsts_out (nullable)
+ *   receives N_STS.  PHL_EUNSUPPORTED for the stellar EOS.  A cell with
+ *   rho <= 0 or e_int <= 0 sets the device flag (PHL_ENEGATIVE at the next
+ *   synchronising call). */
+phl_status phl_diffuse(phl_grid *g, const phl_diffusion *p, double dt, int max_stages, int *nsts_out);
+
 /* Selects how a mixed-precision grid evaluates a stage (Sects. 2.4-2.9; the
  * arithmetic is the same, only the kernel decomposition differs).
  *   on = 1: the fused tile kernel -- each CTA stages an 8x8x8 tile of the

@@ -51,6 +51,10 @@ class GridDesc(C.Structure):
     ]
 
 
+class Diffusion(C.Structure):
+    _fields_ = [("k0", C.c_double), ("nT", C.c_int), ("nR", C.c_int), ("cv", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_long), ("t", C.c_double), ("last_dt", C.c_double),
                 ("device_flags", C.c_int), ("kernels_per_step", C.c_int), ("device_bytes", C.c_size_t),
@@ -92,6 +96,7 @@ _SIGS = {
     "phl_dt_device_ptr": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
     "phl_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_set_fused": (C.c_int, [C.c_void_p, C.c_int]),
+    "phl_diffuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     "phl_test_tile_wait_timeout": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_convert_batch": (C.c_int, [C.c_long, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "phl_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
@@ -523,6 +528,14 @@ class Grid:
 
     def set_timing(self, on=True):
         _check(lib().phl_set_timing(self.h, int(bool(on))))
+
+    def diffuse(self, dt, k0, nT=0, nR=0, cv=1.5, max_stages=100000):
+        """One RKL2 thermal-diffusion super step of length dt (phl_diffuse);
+        returns the number of stages."""
+        p = Diffusion(k0=float(k0), nT=int(nT), nR=int(nR), cv=float(cv))
+        ns = C.c_int(0)
+        _check(lib().phl_diffuse(self.h, C.byref(p), float(dt), int(max_stages), C.byref(ns)))
+        return ns.value
 
     def test_tile_wait_timeout(self, on=True):
         """Make the fused tile kernel's bounded TMA wait run out (a test of the

@@ -87,6 +87,7 @@ struct phl_grid {
   int fused = 0;                        // mixed stage on the fused tile kernel: launch shape, 0 = off
   unsigned test_extra_tx = 0;           // phl_test_tile_wait_timeout
   double *stage_a = nullptr, *stage_b = nullptr;   // work arrays reused as host-transfer staging
+  double *diff = nullptr;               // thermal-diffusion arrays (7 per cell), allocated on first use
   size_t stage_a_bytes = 0, stage_b_bytes = 0;
   alignas(64) unsigned char tmapW[128]; // its TMA descriptor of W
 };
@@ -679,6 +680,29 @@ phl_status phl_set_fused(phl_grid *g, int on) {
     return fail(PHL_EUNSUPPORTED, "the fused stage needs the mixed form, an ideal gas without species and 3 active dimensions");
   if (make_fused_tmap(g->G, g->Wf, g->tmapW) != PHL_OK) return PHL_ECUDA;
   g->fused = on == 1 ? PHL_FUSED_DEFAULT : on;
+  return PHL_OK;
+}
+
+phl_status phl_diffuse(phl_grid *g, const phl_diffusion *p, double dt, int max_stages, int *nsts_out) {
+  if (!g || !p) return fail(PHL_EINVAL, "null argument");
+  if (g->G.eos != PHL_EOS_IDEAL) return fail(PHL_EUNSUPPORTED, "thermal diffusion is built for the ideal gas");
+  if (!(p->k0 >= 0.0) || !(p->cv > 0.0) || p->nT < 0 || p->nT > 4 || p->nR < 0 || p->nR > 2 || !(dt > 0.0) ||
+      max_stages < 3)
+    return fail(PHL_EINVAL, "bad diffusion parameters");
+  if (!g->diff) {
+    const long nc = (long)g->G.n[0] * g->G.n[1] * g->G.n[2];
+    phl_status st = dalloc(g, &g->diff, (size_t)7 * nc);
+    if (st != PHL_OK) return st;
+  }
+  int ns = 0, nl = 0;
+  const cudaError_t e = launch_diffuse(g->G, g->U, g->B, *p, dt, max_stages, g->diff, g->dmax, g->dflag, g->stream,
+                                       &ns, &nl);
+  if (nsts_out) *nsts_out = ns;
+  if (e == cudaErrorInvalidValue && ns > max_stages) {
+    cudaGetLastError();
+    return fail(PHL_EINVAL, "thermal diffusion needs %d stages, more than max_stages = %d", ns, max_stages);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "thermal diffusion");
   return PHL_OK;
 }
 

@@ -42,7 +42,7 @@ def pulse(n, k0=1e-2, cv=1.5, T0=1.0, A=0.5, sigma=0.1, bc=0):
     T = T0 + A * np.exp(-(xx ** 2 + yy ** 2) / sigma ** 2)
     z = np.zeros((1, n, n))
     pr = W._assemble("pulse", 2, (n, n, 1), (-0.5, -0.5, 0.0), (0.5, 0.5, 1.0), ((bc, bc), (bc, bc), (0, 0)),
-                     1.0 + 1.0 / cv, np.ones((1, n, n)), [z, z, z], T[None] / cv * (1.0 / cv) * cv,
+                     1.0 + 1.0 / cv, np.ones((1, n, n)), [z, z, z], T[None],
                      np.zeros((1, n, n + 1)), np.zeros((1, n + 1, n)), np.zeros((2, n, n)),
                      eint_density=cv * T[None])
     return pr, xx, yy
