@@ -427,6 +427,47 @@ def stellar_c3(P, n, steps, warmup, stream, ws):
     return out
 
 
+def diffusion_sts(P, n, stream, hbm_peak, peak_kind, reps=3):
+    """Thermal diffusion by RKL2 super-time-stepping (phl_diffuse) on the same
+    box: radiative conductivity K = k0 T^3 / rho sized so that the box's MHD
+    step is ~100 parabolic limits (CFL_p ~ 100: ~20 stages, the paper's middle
+    case).  Times whole super steps (one read-back of the parabolic rate, then
+    the stage kernels) with CUDA events; algorithmic bytes per cell-stage: the
+    stage reads e_int^(j-1), e_int^(j-2), e_int^(0), the operator at e_int^(0),
+    1/rho and k0/rho^nR and writes e_int^(j): 7 x 8 = 56 B."""
+    import torch
+    import workloads as W
+    pr = make_problem(n)
+    cv = 1.0 / (pr.gamma - 1.0)
+    g = P.Grid(pr, precision="mixed", stream=stream.cuda_stream)
+    g.load()
+    dt_h = g.compute_dt()
+    # parabolic rate of K = k0 T^3/rho at the hottest, thinnest cell: D / dx^2 summed over 3 axes
+    rho = pr.cons[0]
+    T = (pr.cons[4] - 0.5 * (pr.cons[1] ** 2 + pr.cons[2] ** 2 + pr.cons[3] ** 2) / rho) / rho / cv
+    rate1 = (T ** 3 / rho / (rho * cv)).max() * 3 * n * n     # for k0 = 1
+    k0 = 100.0 / (2.0 * rate1 * dt_h)                          # dt_h / dt_p = 100
+    ns = g.diffuse(dt_h, k0, nT=3, nR=1, cv=cv)                # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            ns = g.diffuse(dt_h, k0, nT=3, nR=1, cv=cv)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    g.check()
+    g.close()
+    rate = pr.ncells * ns / (ms * 1e-3)
+    gbs = rate * 56.0 / 1e9
+    return {"workload": f"RKL2 thermal diffusion on the {n}^3 box, K = k0 T^3 / rho, dt = the MHD CFL step, "
+                        f"CFL_p = 100", "stages": ns, "ms_per_super_step": ms,
+            "value": rate, "unit": "cell-stages/s", "bytes_per_cell_stage": 56.0,
+            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "peak_kind": f"{peak_kind} HBM copy"}}
+
+
 def ensemble_c4(P, steps, warmup, stream, ws):
     """24 independent boxes of the stratified-box physics with edges drawn
     from {64, 96, 128, 160, 192} per axis (seed 2024), mixed form: one
@@ -498,6 +539,7 @@ def main():
                     help="mixed stage: 0 = per-direction face kernels, 1..4 = fused tile kernel launch shape "
                          "(default: the library's choice)")
     ap.add_argument("--no-pph", action="store_true", help="skip the mixed form with PPH reconstruction")
+    ap.add_argument("--no-sts", action="store_true", help="skip the RKL2 thermal-diffusion super step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -552,6 +594,9 @@ def main():
     c4 = None
     if not args.no_c4 and len(forms) == 2:
         c4 = ensemble_c4(P, args.c4_steps, 2, stream, ws)
+    sts = None
+    if not args.no_sts and len(forms) == 2:
+        sts = diffusion_sts(P, args.n, stream, hbm_peak, peak_kind)
     launches = sum(v[0] for v in h["kt"].values())
     forms_out = {f: {"value": r["value"], "ms_per_step": r["ms"] / args.steps,
                      "stage_hbm": stage_hbm(r["value"] / max(ws, 1), f, hbm_peak, peak_kind),
@@ -582,6 +627,7 @@ def main():
         "l1_mixed_vs_fp64": l1,
         "stellar_eos_box": c3,
         "ensemble_24_boxes": c4,
+        "thermal_diffusion_sts": sts,
         "gpu_launches": launches,
         "e2e": e2e,
         "clocks": clk,
