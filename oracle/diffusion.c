@@ -10,11 +10,12 @@
  * nT = nR = 0; radiative diffusion with a constant opacity, K = 4acT^3 / (3
  * kappa rho), has nT = 3, nR = 1).
  *
- * Space (reading; the paper states the operator, not its stencil): the
- * conservative seven-point form, face flux -K_f (T_R - T_L) / dx with K_f
- * the arithmetic mean of the two cells' K; a side that is not periodic carries
- * no flux (the reflecting mirror and the outflow copy both give the ghost the
- * cell's own temperature).
+ * Space (Sect. 2.10): the face flux is the centred difference
+ * -K_f (T_R - T_L) / dx with K_f the harmonic mean 2 K_L K_R / (K_L + K_R) of
+ * the two cells' conductivities (zero where both vanish); summed over the six
+ * faces this is the conservative seven-point form.  Reading: a side that is not
+ * periodic carries no flux (the reflecting mirror and the outflow copy both
+ * give the ghost the cell's own temperature).
  *
  * Time: RKL2 (Meyer, Balsara & Aslam 2012) over the whole step dt, in the
  * paper's stage form (items i-iv of Sect. 2.10), with the paper's count
@@ -110,7 +111,8 @@ static void diff_op(const dgrid *g, const ora_diff *p, const double *rho, const 
               cc[d] = (cc[d] + g->n[d]) % g->n[d];
             }
             const long qn = cidx(g, cc[0], cc[1], cc[2]);
-            const double Kf = 0.5 * (K[q] + K[qn]);
+            const double Ks = K[q] + K[qn];
+            const double Kf = Ks > 0.0 ? 2.0 * K[q] * K[qn] / Ks : 0.0;   /* harmonic mean */
             const double gradT = (Y[qn] / p->cv - Tc) / g->dx[d];   /* toward the neighbour */
             flux_sum += Kf * gradT;
           }

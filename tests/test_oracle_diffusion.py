@@ -88,3 +88,29 @@ def test_diffusion_conserves_energy(bc, nT, nR):
     assert ns >= 3
     assert abs(st["cons"][4].sum() - E0) <= 1e-13 * abs(E0)
     assert np.array_equal(st["cons"][:4], pr.cons[:4])     # rho and momentum untouched
+
+
+def test_insulating_cells_block_the_flux():
+    """The face conductivity is the harmonic mean of the two cells' (Sect.
+    2.10), which is the series conductance of two half cells: a face next to
+    a cell of vanishing conductivity carries (almost) no heat.  Two columns of
+    such cells (K = k0 / rho^2 with rho = 1e9) split a periodic box into two
+    compartments at different temperatures; each compartment keeps its own
+    energy while heat still spreads inside it.  (An arithmetic face mean
+    would leak half the neighbour's conductance through those faces.)"""
+    n, cv, k0 = 32, 1.5, 1e-2
+    pr, xx, yy = pulse(n, k0, cv)
+    ix = np.arange(n)
+    inner = (ix > 8) & (ix < 24)
+    T = np.where(inner[None, :], 2.0 + 0.5 * np.exp(-(xx ** 2 + yy ** 2) / 0.01), 1.0)
+    rho = np.ones((n, n))
+    rho[:, [8, 24]] = 1e9
+    pr.cons[0][0] = rho
+    pr.cons[4][0] = rho * cv * T
+    st, ns = O.Oracle(pr).diffuse(0.2, k0, nT=0, nR=2, cv=cv)
+    assert ns >= 4
+    E0, E1 = pr.cons[4][0], st["cons"][4][0]
+    for part in (inner, ~inner & (ix != 8) & (ix != 24)):
+        a, b = E0[:, part].sum(), E1[:, part].sum()
+        assert abs(b - a) <= 1e-12 * abs(a), (a, b)
+    assert np.abs(E1[:, inner] - E0[:, inner]).max() > 1e-2     # heat does spread inside
