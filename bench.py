@@ -431,12 +431,15 @@ def diffusion_sts(P, n, stream, hbm_peak, peak_kind, reps=3):
     """Thermal diffusion by RKL2 super-time-stepping (phl_diffuse) on the same
     box: radiative conductivity K = k0 T^3 / rho sized so that the box's MHD
     step is ~100 parabolic limits (CFL_p ~ 100: ~20 stages, the paper's middle
-    case).  Times whole super steps (one read-back of the parabolic rate, then
-    the stage kernels) with CUDA events; algorithmic bytes per cell-stage: the
-    stage reads e_int^(j-1), e_int^(j-2), e_int^(0), the operator at e_int^(0),
-    1/rho and k0/rho^nR and writes e_int^(j): 7 x 8 = 56 B."""
+    case).  Times whole super steps (one read-back of the parabolic rate, the
+    set-up kernels, the stage kernels) with CUDA events, in the mixed form
+    (float stages on the change of e_int) on the mixed grid and in the FP64
+    form.  Algorithmic bytes per cell-stage of the stage kernel: mixed, it
+    reads d^(m-1), d^(m-2), y0, the conductivity factor, 1/(rho c_v), the
+    operator at d = 0 and three face differences and writes d^(m): 10 x 4 =
+    40 B; FP64, it reads e_int^(m-1), e_int^(m-2), e_int^(0), the operator at
+    e_int^(0), 1/rho and k0/rho^nR and writes e_int^(m): 7 x 8 = 56 B."""
     import torch
-    import workloads as W
     pr = make_problem(n)
     cv = 1.0 / (pr.gamma - 1.0)
     g = P.Grid(pr, precision="mixed", stream=stream.cuda_stream)
@@ -447,25 +450,34 @@ def diffusion_sts(P, n, stream, hbm_peak, peak_kind, reps=3):
     T = (pr.cons[4] - 0.5 * (pr.cons[1] ** 2 + pr.cons[2] ** 2 + pr.cons[3] ** 2) / rho) / rho / cv
     rate1 = (T ** 3 / rho / (rho * cv)).max() * 3 * n * n     # for k0 = 1
     k0 = 100.0 / (2.0 * rate1 * dt_h)                          # dt_h / dt_p = 100
-    ns = g.diffuse(dt_h, k0, nT=3, nR=1, cv=cv)                # warm-up
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(reps):
-            ns = g.diffuse(dt_h, k0, nT=3, nR=1, cv=cv)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    g.check()
+    out = {}
+    for form, nbytes in (("mixed", 40.0), ("fp64", 56.0)):
+        g.load()
+        ns = g.diffuse(dt_h, k0, nT=3, nR=1, cv=cv, precision=form)    # warm-up
+        g.load()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                ns = g.diffuse(dt_h, k0, nT=3, nR=1, cv=cv, precision=form)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        g.check()
+        rate = pr.ncells * ns / (ms * 1e-3)
+        gbs = rate * nbytes / 1e9
+        out[form] = {"stages": ns, "ms_per_super_step": ms, "value": rate, "unit": "cell-stages/s",
+                     "bytes_per_cell_stage": nbytes,
+                     "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                             "peak_kind": f"{peak_kind} HBM copy", "note": "whole super step incl. set-up"}}
     g.close()
-    rate = pr.ncells * ns / (ms * 1e-3)
-    gbs = rate * 56.0 / 1e9
-    return {"workload": f"RKL2 thermal diffusion on the {n}^3 box, K = k0 T^3 / rho, dt = the MHD CFL step, "
-                        f"CFL_p = 100", "stages": ns, "ms_per_super_step": ms,
-            "value": rate, "unit": "cell-stages/s", "bytes_per_cell_stage": 56.0,
-            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                    "peak_kind": f"{peak_kind} HBM copy"}}
+    res = {"workload": f"RKL2 thermal diffusion on the {n}^3 box, K = k0 T^3 / rho, dt = the MHD CFL step, "
+                       f"CFL_p = 100"}
+    res.update(out["mixed"])
+    res["form"] = "mixed"
+    res["fp64"] = out["fp64"]
+    return res
 
 
 def ensemble_c4(P, steps, warmup, stream, ws):

@@ -183,24 +183,33 @@ phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, 
  * units) and conductivity K = k0 T^nT / rho^nR (nT = 0..4, nR = 0..2; a
  * constant K: nT = nR = 0; radiative diffusion with a constant opacity,
  * K = 4acT^3 / (3 kappa rho): nT = 3, nR = 1, k0 = 4ac / (3 kappa)). */
+enum { PHL_DIFF_GRID = 0, PHL_DIFF_FP64 = 1, PHL_DIFF_MIXED = 2 };
 typedef struct {
   double k0;
   int nT, nR;
   double cv;
+  int precision;            /* PHL_DIFF_GRID: the grid's precision mode;       */
+                            /* PHL_DIFF_FP64: stages in double;                */
+                            /* PHL_DIFF_MIXED: stages in float on the change   */
+                            /* of e_int (face differences of e_int^(0) taken   */
+                            /* in double), either grid                         */
+  int tile_z;               /* mixed stage kernel: planes per CTA (0: 16), a    */
+                            /* tuning knob; results do not depend on it        */
 } phl_diffusion;
 
 /* Advance rho d(e_int)/dt = div(K grad T) over dt with the density,
  * velocity, magnetic field and mass fractions held fixed, by one RKL2 super
- * step (Meyer, Balsara & Aslam 2012; Sect. 2.10 items i-iv) in FP64, and add
+ * step (Meyer, Balsara & Aslam 2012; Sect. 2.10 items i-iv), and add
  * rho times the change of e_int to the total energy.  The stage count is the
  * paper's N_STS = max(1 + floor((sqrt(9 + 16 dt/dt_p) - 1)/2), 3) with the
  * parabolic limit dt_p = 1/2 [max sum_s D/dx_s^2]^-1, D = K/(rho cv), of the
  * state at the start of the step: the call reads that maximum back (one
- * synchronisation of the grid's stream) and then enqueues N_STS + 1 kernels.
- * Space: conservative seven-point operator, face conductivity the mean of
- * the two cells', no flux through sides that are not periodic.  Call between
- * MHD steps (e.g. Strang splitting: half dt, phl_step, half dt).  The first
- * call allocates the grid's diffusion arrays (seven doubles per cell).
+ * synchronisation of the grid's stream) and then enqueues the stage kernels
+ * (N_STS + 1 in FP64, N_STS + 2 mixed).  Space: conservative seven-point
+ * operator, face conductivity the harmonic mean of the two cells' (Sect.
+ * 2.10), no flux through sides that are not periodic.  Call between MHD
+ * steps (e.g. Strang splitting: half dt, phl_step, half dt).  The first call
+ * allocates the grid's diffusion arrays (seven doubles per cell).
  *   max_stages: PHL_EINVAL when N_STS would exceed it; *nsts_out (nullable)
  *   receives N_STS.  PHL_EUNSUPPORTED for the stellar EOS.  A cell with
  *   rho <= 0 or e_int <= 0 sets the device flag (PHL_ENEGATIVE at the next

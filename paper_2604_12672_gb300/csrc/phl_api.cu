@@ -687,15 +687,19 @@ phl_status phl_diffuse(phl_grid *g, const phl_diffusion *p, double dt, int max_s
   if (!g || !p) return fail(PHL_EINVAL, "null argument");
   if (g->G.eos != PHL_EOS_IDEAL) return fail(PHL_EUNSUPPORTED, "thermal diffusion is built for the ideal gas");
   if (!(p->k0 >= 0.0) || !(p->cv > 0.0) || p->nT < 0 || p->nT > 4 || p->nR < 0 || p->nR > 2 || !(dt > 0.0) ||
-      max_stages < 3)
+      max_stages < 3 || p->precision < PHL_DIFF_GRID || p->precision > PHL_DIFF_MIXED || p->tile_z < 0 ||
+      p->tile_z > 4096)
     return fail(PHL_EINVAL, "bad diffusion parameters");
   if (!g->diff) {
     const long nc = (long)g->G.n[0] * g->G.n[1] * g->G.n[2];
-    phl_status st = dalloc(g, &g->diff, (size_t)7 * nc);
+    phl_status st = dalloc(g, &g->diff, (size_t)7 * nc + 8);
     if (st != PHL_OK) return st;
   }
+  const bool mixed = p->precision == PHL_DIFF_MIXED || (p->precision == PHL_DIFF_GRID && g->mixed);
+  if (mixed && (double)g->G.n[0] * g->G.n[1] * g->G.n[2] >= 4294967295.0)
+    return fail(PHL_EUNSUPPORTED, "mixed thermal diffusion indexes cells with 32 bits (fewer than 2^32 - 1 cells)");
   int ns = 0, nl = 0;
-  const cudaError_t e = launch_diffuse(g->G, g->U, g->B, *p, dt, max_stages, g->diff, g->dmax, g->dflag, g->stream,
+  const cudaError_t e = launch_diffuse(g->G, g->U, g->B, *p, dt, max_stages, mixed, g->diff, g->dflag, g->stream,
                                        &ns, &nl);
   if (nsts_out) *nsts_out = ns;
   if (e == cudaErrorInvalidValue && ns > max_stages) {

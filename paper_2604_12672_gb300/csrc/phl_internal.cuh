@@ -288,8 +288,8 @@ void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigne
 
 // Thermal diffusion by RKL2 super-time-stepping (diffusion.cu).
 cudaError_t launch_diffuse(const DevGeo &G, double *U, const double *Bf, const phl_diffusion &p, double dt,
-                           int max_stages, double *scratch, unsigned long long *dmax, int *dflag, cudaStream_t s,
-                           int *nsts, int *nlaunch);
+                           int max_stages, bool mixed, double *scratch, int *dflag, cudaStream_t s, int *nsts,
+                           int *nlaunch);
 
 // Fused mixed stage (stage_fused.cu): faces of all three directions and the
 // cell update in one tiled kernel; ideal gas, no species, 3-D grids.
