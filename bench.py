@@ -450,27 +450,38 @@ def diffusion_sts(P, n, stream, hbm_peak, peak_kind, reps=3):
     T = (pr.cons[4] - 0.5 * (pr.cons[1] ** 2 + pr.cons[2] ** 2 + pr.cons[3] ** 2) / rho) / rho / cv
     rate1 = (T ** 3 / rho / (rho * cv)).max() * 3 * n * n     # for k0 = 1
     k0 = 100.0 / (2.0 * rate1 * dt_h)                          # dt_h / dt_p = 100
-    out = {}
-    for form, nbytes in (("mixed", 40.0), ("fp64", 56.0)):
+    def timed(form, dt):
         g.load()
-        ns = g.diffuse(dt_h, k0, nT=3, nR=1, cv=cv, precision=form)    # warm-up
+        g.diffuse(dt, k0, nT=3, nR=1, cv=cv, precision=form)    # warm-up
         g.load()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             e0.record(stream)
             for _ in range(reps):
-                ns = g.diffuse(dt_h, k0, nT=3, nR=1, cv=cv, precision=form)
+                ns = g.diffuse(dt, k0, nT=3, nR=1, cv=cv, precision=form)
             e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
         g.check()
+        return ns, e0.elapsed_time(e1) / reps
+
+    out = {}
+    for form, nbytes in (("mixed", 40.0), ("fp64", 56.0)):
+        ns, ms = timed(form, dt_h)
+        # the stage kernel alone: two super steps with different stage counts
+        ns2, ms2 = timed(form, dt_h / 8.0)
+        ms_stage = (ms - ms2) / (ns - ns2)
         rate = pr.ncells * ns / (ms * 1e-3)
         gbs = rate * nbytes / 1e9
+        gbs_k = pr.ncells * nbytes / (ms_stage * 1e-3) / 1e9
         out[form] = {"stages": ns, "ms_per_super_step": ms, "value": rate, "unit": "cell-stages/s",
                      "bytes_per_cell_stage": nbytes,
                      "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                             "peak_kind": f"{peak_kind} HBM copy", "note": "whole super step incl. set-up"}}
+                             "peak_kind": f"{peak_kind} HBM copy", "note": "whole super step incl. set-up"},
+                     "stage_kernel": {"ms": ms_stage, "set_up_ms": ms - ns * ms_stage,
+                                      "achieved": gbs_k, "peak": hbm_peak, "unit": "GB/s",
+                                      "frac": gbs_k / hbm_peak,
+                                      "method": f"(t({ns} stages) - t({ns2} stages)) / {ns - ns2}"}}
     g.close()
     res = {"workload": f"RKL2 thermal diffusion on the {n}^3 box, K = k0 T^3 / rho, dt = the MHD CFL step, "
                        f"CFL_p = 100"}
@@ -552,6 +563,8 @@ def main():
                          "(default: the library's choice)")
     ap.add_argument("--no-pph", action="store_true", help="skip the mixed form with PPH reconstruction")
     ap.add_argument("--no-sts", action="store_true", help="skip the RKL2 thermal-diffusion super step")
+    ap.add_argument("--sts-only", action="store_true",
+                    help="time only the RKL2 thermal-diffusion super step (print its object; for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -571,8 +584,12 @@ def main():
     import paper_2604_12672_gb300 as P
 
     hbm_peak, peak_kind = read_peaks()
-    pr = make_problem(args.n)
     stream = torch.cuda.Stream()
+    if args.sts_only:
+        if rank == 0:
+            print(json.dumps(diffusion_sts(P, args.n, stream, hbm_peak, peak_kind)))
+        return 0
+    pr = make_problem(args.n)
     props = torch.cuda.get_device_properties(local)
     gpu_id = getattr(props, "uuid", None)
     gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else (gpu_id or local)

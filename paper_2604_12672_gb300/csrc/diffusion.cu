@@ -69,15 +69,28 @@ __device__ __forceinline__ long dense(const DevGeo &G, const int *c) {
   return c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2]);
 }
 
-// Non-negative doubles compare as their bit patterns.
-__device__ __forceinline__ void block_max(double v, unsigned long long *dst, double *red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+// Block maximum of a non-negative double into *dst.  Non-negative doubles
+// order as their bit patterns, so the reduction runs on the integer pipe
+// (GB300's FP64 pipe is 1/64 of the FP32 rate); a negative input counts as
+// zero (a NaN wins, and the host then treats the maximum as absent).
+__device__ __forceinline__ unsigned long long dbits(double v) {
+  const long long b = __double_as_longlong(v);
+  return b > 0 ? (unsigned long long)b : 0ull;
+}
+__device__ __forceinline__ void block_max(unsigned long long v, unsigned long long *dst, unsigned long long *red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double u = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
-    if (threadIdx.x == 0) atomicMax(dst, (unsigned long long)__double_as_longlong(u));
+    unsigned long long w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, w, o);
+      w = u > w ? u : w;
+    }
+    if (threadIdx.x == 0) atomicMax(dst, w);
   }
   __syncthreads();
 }
@@ -89,7 +102,7 @@ template <bool MX>
 __global__ void k_diff_init(DevGeo G, Box box, const double *__restrict__ U, const double *__restrict__ Bf,
                             phl_diffusion p, double icv, DiffArrays A, DiffMx M, unsigned long long *red,
                             int *dflag) {
-  double rate = 0.0, emax = 0.0, kmax = 0.0, imax = 0.0;
+  unsigned long long rate = 0, emax = 0, kmax = 0, imax = 0;
   int c[3];
   if (cell3(box, c)) {
     const long ps = sidx(G, c[0], c[1], c[2]);
@@ -117,12 +130,12 @@ __global__ void k_diff_init(DevGeo G, Box box, const double *__restrict__ U, con
     double s2 = 0.0;
     for (int d = 0; d < 3; ++d)
       if (G.act[d]) s2 += G.idx[d] * G.idx[d];
-    rate = fmax(D * s2, 0.0);
-    emax = fmax(e, 0.0);
-    kmax = fmax(kr, 0.0);
-    imax = fmax(ir, 0.0);
+    rate = dbits(D * s2);
+    emax = dbits(e);
+    kmax = dbits(kr);
+    imax = dbits(ir);
   }
-  __shared__ double red_s[TPB / 32];
+  __shared__ unsigned long long red_s[TPB / 32];
   block_max(rate, red + 0, red_s);
   if (MX) {
     block_max(emax, red + 1, red_s);
@@ -469,7 +482,9 @@ void rkl2_coeffs(int s, double *mu, double *nu, double *mut, double *gat) {
 }
 
 int sts_stage_count(double dt, double dt_p) {
-  const int n = 1 + (int)std::floor(0.5 * (std::sqrt(9.0 + 16.0 * dt / dt_p) - 1.0));
+  const double f = 1.0 + std::floor(0.5 * (std::sqrt(9.0 + 16.0 * dt / dt_p) - 1.0));
+  if (!(f < 1e9)) return 1000000000;   // beyond any stage limit
+  const int n = (int)f;
   return n < 3 ? 3 : n;
 }
 
@@ -511,7 +526,9 @@ cudaError_t launch_diffuse(const DevGeo &G, double *U, const double *Bf, const p
   double mx[NRED];
   memcpy(mx, bits, sizeof(mx));
   const double rate = mx[0];
-  const int ns = rate > 0.0 ? sts_stage_count(dt, 0.5 / rate) : 3;
+  // a NaN maximum comes with a flagged cell (reported at the next check); an
+  // infinite parabolic rate needs more stages than any limit
+  const int ns = !(rate > 0.0) ? 3 : std::isfinite(rate * dt) ? sts_stage_count(dt, 0.5 / rate) : max_stages + 1;
   *nsts = ns;
   if (ns > max_stages) return cudaErrorInvalidValue;
   std::vector<double> mu((size_t)ns + 1), nu((size_t)ns + 1), mut((size_t)ns + 1), gat((size_t)ns + 1);
