@@ -39,6 +39,14 @@ class OraDiff(C.Structure):
     _fields_ = [("k0", C.c_double), ("nT", C.c_int), ("nR", C.c_int), ("cv", C.c_double)]
 
 
+class OraPoisson(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("xf", _dp * 3), ("G", C.c_double), ("lmax", C.c_int),
+                ("criterion", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int)]
+
+
+_CRITERION = {"relative": 0, "absolute": 1}
+
+
 _lib = None
 
 
@@ -61,6 +69,21 @@ def lib():
         L.ora_diffuse.restype = C.c_int
         L.ora_diffuse.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp, _dp, C.POINTER(OraDiff), C.c_double, C.c_int,
                                   C.POINTER(C.c_int)]
+        L.ora_poisson_nghost.restype = C.c_long
+        L.ora_poisson_nghost.argtypes = [C.POINTER(C.c_int)]
+        L.ora_multipole_moments.restype = C.c_int
+        L.ora_multipole_moments.argtypes = [C.POINTER(OraPoisson), _dp, _dp, _dp, _dp, _dp]
+        L.ora_multipole_phi.restype = C.c_double
+        L.ora_multipole_phi.argtypes = [C.c_double, C.c_int, C.c_double, _dp, _dp, _dp,
+                                        C.c_double, C.c_double, C.c_double]
+        L.ora_poisson_boundary.restype = C.c_int
+        L.ora_poisson_boundary.argtypes = [C.POINTER(OraPoisson), _dp, _dp]
+        L.ora_poisson_apply.restype = C.c_int
+        L.ora_poisson_apply.argtypes = [C.POINTER(OraPoisson), _dp, _dp, _dp]
+        L.ora_gravity.restype = C.c_int
+        L.ora_gravity.argtypes = [C.POINTER(OraPoisson), _dp, _dp, _dp, _dp, _dp]
+        L.ora_poisson_solve.restype = C.c_int
+        L.ora_poisson_solve.argtypes = [C.POINTER(OraPoisson), _dp, _dp, _dp, C.POINTER(C.c_int), _dp]
         L.ora_rkl2_amp.restype = C.c_double
         L.ora_rkl2_amp.argtypes = [C.c_int, C.c_double]
         L.ora_sts_stages.restype = C.c_int
@@ -360,3 +383,66 @@ def mlp_loss_grad(w, nin, nh, x, t):
     g = np.zeros_like(w)
     loss = lib().ora_mlp_loss_grad(_ptr(w), nin, nh, _ptr(x), _ptr(t), x.shape[0], _ptr(g))
     return loss, g
+
+
+class Poisson:
+    """The oracle's Poisson solver (Sect. 2.12) on a grid given by its face
+    coordinates xf = (xf_x, xf_y, xf_z), each n_d + 1 increasing values.
+    Cell arrays are [nz][ny][nx]; ghost potentials are one flat array (x
+    faces [2][nz][ny], y faces [2][nz][nx], z faces [2][ny][nx])."""
+
+    def __init__(self, xf, G=1.0, lmax=0, criterion="relative", tol=1e-4, max_iter=10000):
+        self.xf = [np.ascontiguousarray(a, dtype=np.float64) for a in xf]
+        self.n = tuple(len(a) - 1 for a in self.xf)
+        self.p = OraPoisson()
+        for d in range(3):
+            self.p.n[d] = self.n[d]
+            self.p.xf[d] = _ptr(self.xf[d])
+        self.p.G, self.p.lmax = float(G), int(lmax)
+        self.p.criterion, self.p.tol, self.p.max_iter = _CRITERION[criterion], float(tol), int(max_iter)
+        self.nghost = lib().ora_poisson_nghost(self.p.n)
+
+    def _cells(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        assert a.shape == self.n[::-1], (a.shape, self.n)
+        return a
+
+    def moments(self, rho):
+        rho = self._cells(rho)
+        M, X, Q, O = C.c_double(), np.zeros(3), np.zeros(9), np.zeros(27)
+        assert lib().ora_multipole_moments(C.byref(self.p), _ptr(rho), C.byref(M), _ptr(X), _ptr(Q), _ptr(O)) == 0
+        return M.value, X, Q.reshape(3, 3), O.reshape(3, 3, 3)
+
+    def multipole_phi(self, moments, pts, lmax=None):
+        M, X, Q, O = moments
+        X, Q, O = (np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (X, Q, O))
+        lm = self.p.lmax if lmax is None else lmax
+        return np.array([lib().ora_multipole_phi(self.p.G, lm, M, _ptr(X), _ptr(Q), _ptr(O), *map(float, r))
+                         for r in pts])
+
+    def boundary(self, rho):
+        gh = np.zeros(self.nghost)
+        assert lib().ora_poisson_boundary(C.byref(self.p), _ptr(self._cells(rho)), _ptr(gh)) == 0
+        return gh
+
+    def apply(self, phi, ghost=None):
+        out = np.zeros(self.n[::-1])
+        gh = None if ghost is None else np.ascontiguousarray(ghost, dtype=np.float64)
+        assert lib().ora_poisson_apply(C.byref(self.p), _ptr(self._cells(phi)),
+                                       _ptr(gh) if gh is not None else None, _ptr(out)) == 0
+        return out
+
+    def gravity(self, phi, ghost):
+        g = [np.zeros(self.n[::-1]) for _ in range(3)]
+        gh = np.ascontiguousarray(ghost, dtype=np.float64)
+        assert lib().ora_gravity(C.byref(self.p), _ptr(self._cells(phi)), _ptr(gh), *map(_ptr, g)) == 0
+        return g
+
+    def solve(self, rho, phi0=None):
+        """Returns (phi, ghost, iterations, final residual RMS, status)."""
+        rho = self._cells(rho)
+        phi = np.zeros(self.n[::-1]) if phi0 is None else self._cells(phi0).copy()
+        gh = np.zeros(self.nghost)
+        it, res = C.c_int(), C.c_double()
+        st = lib().ora_poisson_solve(C.byref(self.p), _ptr(rho), _ptr(phi), _ptr(gh), C.byref(it), C.byref(res))
+        return phi, gh, it.value, res.value, st

@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["mhd.c", "eos.c", "mlp.c", "diffusion.c"]
+SOURCES = ["mhd.c", "eos.c", "mlp.c", "diffusion.c", "poisson.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

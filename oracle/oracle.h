@@ -5,7 +5,9 @@
  * update of PHLEGETHON (arXiv 2604.12672, Sect. 2): primitive recovery and EOS
  * (Sect. 2.2), deviation well-balancing (Sect. 2.8), van Leer PLM (Sect. 2.5),
  * LHLLD / HLL Riemann fluxes (Sect. 2.6), shock flattening (Sect. 2.7),
- * Contact-CT (Sect. 2.4), SSP-RK stages and the CFL step (Sect. 2.9).
+ * Contact-CT (Sect. 2.4), SSP-RK stages and the CFL step (Sect. 2.9); thermal
+ * diffusion by RKL2 super-time-stepping (Sect. 2.10); the Poisson solver for
+ * the gravitational potential (Sect. 2.12).
  *
  * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load
  * it.  It shares no code, header, table or helper with the CUDA library; both
@@ -75,6 +77,31 @@ int ora_sts_stages(double dt, double dt_p);
  * (non-positive rho or e_int) or -4 (more than max_stages stages needed). */
 int ora_diffuse(const ora_cfg *cfg, double *cons, const double *bx, const double *by, const double *bz,
                 const ora_diff *p, double dt, int max_stages, int *nsts_out);
+
+/* Poisson solver for the gravitational potential (poisson.c, Sect. 2.12).
+ * xf[d]: the n[d] + 1 increasing face coordinates of axis d; rho, phi: cell
+ * arrays [nz][ny][nx]; ghost potentials: x faces [2][nz][ny], then y faces
+ * [2][nz][nx], then z faces [2][ny][nx] (lower side first). */
+enum { ORA_POISSON_RELATIVE = 0, ORA_POISSON_ABSOLUTE = 1 };
+typedef struct {
+  int n[3];
+  const double *xf[3];
+  double G;
+  int lmax;                 /* 0: monopole; 2: + quadrupole; 3: + octupole */
+  int criterion;            /* ORA_POISSON_RELATIVE (Eq. poisson-eps) / _ABSOLUTE */
+  double tol;
+  int max_iter;
+} ora_poisson;
+
+long ora_poisson_nghost(const int *n);
+int ora_multipole_moments(const ora_poisson *p, const double *rho, double *M, double *X, double *Q, double *O);
+double ora_multipole_phi(double G, int lmax, double M, const double *X, const double *Q, const double *O, double x,
+                         double y, double z);
+int ora_poisson_boundary(const ora_poisson *p, const double *rho, double *ghost);
+int ora_poisson_apply(const ora_poisson *p, const double *phi, const double *ghost, double *out);
+int ora_gravity(const ora_poisson *p, const double *phi, const double *ghost, double *gx, double *gy, double *gz);
+int ora_poisson_solve(const ora_poisson *p, const double *rho, double *phi, double *ghost_out, int *iters,
+                      double *resid);
 
 /* Advance nsteps SSP-RK steps in place.  dt_fixed > 0 uses that step;
  * otherwise each step's dt comes from the CFL condition on U^n.

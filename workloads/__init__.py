@@ -472,3 +472,54 @@ def permute_axes(pr: Problem, perm) -> Problem:
     q.ndim = 3 if min(n) > 1 else pr.ndim
     q.meta = dict(pr.meta, perm=tuple(perm), inv=tuple(inv))
     return q
+
+
+# ---------------------------------------------------------------- Poisson
+# Inputs of the Poisson solver (Sect. 2.12): face coordinates per axis and a
+# cell density.  No solver arithmetic lives here.
+
+def stretched_faces(n, lo=-0.5, hi=0.5):
+    """n + 1 face coordinates of the paper's stretched axis for its Poisson
+    test: x = (eta + eta^5) / 4 at eta = -1 + 2 i / n, i = 0..n, mapped onto
+    [lo, hi] (the paper's domain is [-1/2, 1/2]): twice the uniform
+    resolution at the origin."""
+    eta = -1.0 + 2.0 * np.arange(n + 1) / n
+    x = 0.25 * (eta + eta ** 5)
+    return lo + (x + 0.5) * (hi - lo)
+
+
+def random_faces(n, seed, lo=-0.5, hi=0.5, spread=0.5):
+    """n + 1 increasing face coordinates on [lo, hi] with cell widths varying
+    by up to a factor (1 + spread) / (1 - spread), smoothly (a random sum of
+    a few sines), seeded."""
+    rng = np.random.default_rng(seed)
+    s = np.linspace(0.0, 1.0, n)
+    w = np.ones(n)
+    for k in range(1, 4):
+        w += spread / 3.0 * np.sin(2 * np.pi * k * s + rng.uniform(0, 2 * np.pi))
+    w = np.clip(w, 1.0 - spread, 1.0 + spread)
+    f = np.concatenate([[0.0], np.cumsum(w)])
+    return lo + (hi - lo) * f / f[-1]
+
+
+def sphere_density(xf, rho0=1.0, r0=0.25):
+    """The paper's Poisson test density rho0 (1 - r^2/r0^2)^2 inside r0, zero
+    outside, at the cell centres (midpoints of the faces)."""
+    xc = [0.5 * (a[1:] + a[:-1]) for a in xf]
+    z, y, x = np.meshgrid(xc[2], xc[1], xc[0], indexing="ij")
+    r2 = x * x + y * y + z * z
+    return np.where(r2 <= r0 * r0, rho0 * (1.0 - r2 / (r0 * r0)) ** 2, 0.0)
+
+
+def lumpy_density(xf, seed, nblob=5, floor=1e-3):
+    """A positive density: a floor plus a few seeded Gaussian blobs of random
+    centre, width and mass (off-centre, so every multipole is present)."""
+    rng = np.random.default_rng(seed)
+    xc = [0.5 * (a[1:] + a[:-1]) for a in xf]
+    z, y, x = np.meshgrid(xc[2], xc[1], xc[0], indexing="ij")
+    rho = np.full(x.shape, floor)
+    for _ in range(nblob):
+        c = rng.uniform(-0.25, 0.25, 3)
+        w = rng.uniform(0.04, 0.12)
+        rho += rng.uniform(0.2, 1.0) * np.exp(-((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) / w ** 2)
+    return rho
