@@ -54,7 +54,8 @@ typedef enum {
   PHL_ENAN = 5,          /* non-finite value                              */
   PHL_ENEWTON = 6,       /* EOS temperature inversion did not converge    */
   PHL_ETIMEOUT = 7,      /* a bounded device wait gave up                 */
-  PHL_EUNSUPPORTED = 8   /* option combination not built                  */
+  PHL_EUNSUPPORTED = 8,  /* option combination not built                  */
+  PHL_ENOCONV = 9        /* iterative solver did not converge / broke down */
 } phl_status;
 
 enum { PHL_PERIODIC = 0, PHL_REFLECT = 1, PHL_OUTFLOW = 2 };
@@ -454,6 +455,61 @@ void phl_destroy(phl_grid *g);
 
 /* Message describing the calling thread's last failure ("" if none). */
 const char *phl_last_error(void);
+
+/* ---------------------------------------------------------------------
+ * Poisson solver for the gravitational potential (Sect. 2.12).
+ *
+ * Solves sum_axes (L1 phi_{i-1} + L2 phi_i + L3 phi_{i+1}) = 4 pi G rho_i on a
+ * Cartesian grid whose axes are stretched independently (Eq. poisson-FD:
+ * L1 = 2/(dm (dm+dp)), L2 = -2/(dm dp), L3 = 2/(dp (dm+dp)) with dm, dp the
+ * spacings to the neighbouring cell centres), by BiCGSTAB with the Jacobi
+ * preconditioner (Sect. 2.12), in FP64 on the device.  Cell centres are the
+ * midpoints of the given faces; the ghost centre beyond a side is the mirror
+ * image of the first (last) centre in that side.  Boundary values: the
+ * multipole expansion of the cell masses rho V about their centre of mass
+ * (monopole always; quadrupole for lmax >= 2; octupole for lmax = 3).
+ * Convergence: the RMS over cells of the residual weighted by 1/(4 pi G rho)
+ * (PHL_POISSON_RELATIVE, Eq. poisson-eps; needs rho > 0 everywhere) or
+ * unweighted (PHL_POISSON_ABSOLUTE) below tol, checked after each half and
+ * full BiCGSTAB step.
+ *
+ * Arrays: rho, phi, gx, gy, gz are cell arrays [nz][ny][nx] (x fastest) of
+ * doubles in host or device memory as `where` says (PHL_HOST / PHL_DEVICE);
+ * the library copies them, never keeps the caller's pointers.  Ghost
+ * potentials: x sides [2][nz][ny], then y sides [2][nz][nx], then z sides
+ * [2][ny][nx], the lower side first: 2 (ny nz + nx nz + nx ny) doubles. */
+enum { PHL_POISSON_RELATIVE = 0, PHL_POISSON_ABSOLUTE = 1 };
+typedef struct {
+  int n[3];                 /* cells per axis, >= 2 each; fewer than 2^32 cells  */
+  const double *xf[3];      /* host: n[d] + 1 increasing face coordinates (read */
+                            /* at creation only)                               */
+  double G;                 /* gravitational constant, > 0                      */
+  int lmax;                 /* 0, 2 or 3                                       */
+  int criterion;            /* PHL_POISSON_RELATIVE / PHL_POISSON_ABSOLUTE      */
+  double tol;               /* > 0 (the paper's default: 1e-4, relative)        */
+  int max_iter;             /* >= 1                                            */
+  void *stream;             /* cudaStream_t (null: the legacy default stream)   */
+} phl_poisson_desc;
+typedef struct phl_poisson phl_poisson;
+
+/* Allocates the solver (12 doubles per cell plus the ghost potentials).
+ * PHL_EINVAL (dimensions, faces, lmax, criterion, tol, max_iter, G),
+ * PHL_EUNSUPPORTED (2^32 cells or more), PHL_ENOMEM. */
+phl_status phl_poisson_create(const phl_poisson_desc *d, phl_poisson **out);
+phl_status phl_poisson_destroy(phl_poisson *p);
+/* phi: in, the initial guess; out, the solution.  *iters (nullable): the
+ * BiCGSTAB iterations taken; *resid (nullable): the last residual RMS.
+ * Synchronous on the solver's stream (it reads the convergence state back
+ * once per 16 iterations).  PHL_ENOCONV: max_iter reached (phi holds the
+ * last iterate) or a breakdown; PHL_EINVAL: relative criterion with a cell
+ * rho <= 0. */
+phl_status phl_poisson_solve(phl_poisson *p, const double *rho, double *phi, int where, int *iters, double *resid);
+/* The ghost potentials of the last solve (PHL_EINVAL before any solve). */
+phl_status phl_poisson_ghost(phl_poisson *p, double *ghost, int where);
+/* g = -grad phi at the cell centres by the non-uniform central difference
+ * (Eqs. grav_x..grav_z), with the last solve's ghost potentials at the
+ * sides.  Synchronous. */
+phl_status phl_poisson_gravity(phl_poisson *p, const double *phi, double *gx, double *gy, double *gz, int where);
 
 #ifdef __cplusplus
 }

@@ -136,6 +136,12 @@ _SIGS = {
                                                                           C.c_void_p]),
     "phl_riemann_batch": (C.c_int, [C.c_long, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_int, C.c_double, C.c_int, C.c_void_p]),
+    "phl_poisson_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "phl_poisson_destroy": (C.c_int, [C.c_void_p]),
+    "phl_poisson_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_double)]),
+    "phl_poisson_ghost": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_poisson_gravity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
 }
 
 
@@ -566,3 +572,69 @@ class Grid:
         p = C.c_void_p()
         _check(lib().phl_dt_device_ptr(self.h, C.byref(p)))
         return p.value
+
+
+class PoissonDesc(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("xf", C.c_void_p * 3), ("G", C.c_double), ("lmax", C.c_int),
+                ("criterion", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("stream", C.c_void_p)]
+
+
+POISSON_CRITERION = {"relative": 0, "absolute": 1}
+
+
+class Poisson:
+    """The device Poisson solver (phl_poisson_*, Sect. 2.12) on a grid given
+    by its face coordinates xf = (xf_x, xf_y, xf_z).  Cell arrays are
+    [nz][ny][nx] numpy float64 (host) or CUDA tensors (device)."""
+
+    def __init__(self, xf, G=1.0, lmax=0, criterion="relative", tol=1e-4, max_iter=10000, stream=None):
+        self._xf = [np.ascontiguousarray(a, dtype=np.float64) for a in xf]
+        self.n = tuple(len(a) - 1 for a in self._xf)
+        d = PoissonDesc()
+        for a in range(3):
+            d.n[a] = self.n[a]
+            d.xf[a] = self._xf[a].ctypes.data
+        d.G, d.lmax, d.criterion = float(G), int(lmax), POISSON_CRITERION[criterion]
+        d.tol, d.max_iter, d.stream = float(tol), int(max_iter), stream
+        h = C.c_void_p()
+        _check(lib().phl_poisson_create(C.byref(d), C.byref(h)))
+        self.h = h
+        nx, ny, nz = self.n
+        self.nghost = 2 * (ny * nz + nx * nz + nx * ny)
+
+    def solve(self, rho, phi=None):
+        """Returns (phi, iterations, residual); phi (optional) is the initial
+        guess and, as an array of the same kind as rho, receives the result."""
+        if phi is None:
+            phi = np.zeros(self.n[::-1]) if isinstance(rho, np.ndarray) else rho.new_zeros(rho.shape)
+        pr, wr = _ptr(rho)
+        pp, wp = _ptr(phi)
+        assert wr == wp, "rho and phi must live in the same memory"
+        it, res = C.c_int(), C.c_double()
+        _check(lib().phl_poisson_solve(self.h, pr, pp, wr, C.byref(it), C.byref(res)))
+        return phi, it.value, res.value
+
+    def ghost(self):
+        g = np.zeros(self.nghost)
+        _check(lib().phl_poisson_ghost(self.h, g.ctypes.data, HOST))
+        return g
+
+    def gravity(self, phi):
+        if isinstance(phi, np.ndarray):
+            g = [np.zeros(self.n[::-1]) for _ in range(3)]
+        else:
+            g = [phi.new_zeros(phi.shape) for _ in range(3)]
+        pp, w = _ptr(phi)
+        _check(lib().phl_poisson_gravity(self.h, pp, _ptr(g[0])[0], _ptr(g[1])[0], _ptr(g[2])[0], w))
+        return g
+
+    def close(self):
+        if self.h:
+            lib().phl_poisson_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
