@@ -491,6 +491,51 @@ def diffusion_sts(P, n, stream, hbm_peak, peak_kind, reps=3):
     return res
 
 
+POISSON_FLOP_PER_CELL_IT = 62.0     # FP64 flops per cell and BiCGSTAB iteration (FMA = 2), absolute criterion
+POISSON_BYTES_PER_CELL_IT = 200.0   # algorithmic bytes per cell and iteration (25 vector reads/writes of 8 B)
+FP64_NOMINAL_TFLOPS = 1.25          # GB300 dense FP64 (nominal)
+
+
+def poisson_sphere(P, n, stream, hbm_peak, peak_kind, reps=2):
+    """The paper's Poisson accuracy test at n^3: the (1 - r^2/r0^2)^2 sphere
+    (r0 = 1/4, rho0 = 1, G = 1) on the (eta + eta^5)/4 stretched grid,
+    monopole boundary values, absolute RMS residual below 1e-10, zero
+    initial guess; FP64 BiCGSTAB with the Jacobi preconditioner
+    (phl_poisson_solve).  Inputs resident on the device; CUDA-event time per
+    solve, iterations, and the iteration against the FP64 and HBM rooflines
+    (62 FP64 flops and 200 algorithmic bytes per cell and iteration)."""
+    import torch
+    import workloads as W
+    xf = [W.stretched_faces(n)] * 3
+    rho = torch.from_numpy(W.sphere_density(xf)).cuda()
+    S = P.Poisson(xf, G=1.0, lmax=0, criterion="absolute", tol=1e-10, max_iter=20000,
+                  stream=stream.cuda_stream)
+    phi = torch.zeros_like(rho)
+    with torch.cuda.stream(stream):
+        S.solve(rho, phi)                                   # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            phi.zero_()
+            _, it, res = S.solve(rho, phi)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    S.close()
+    cells = n ** 3
+    ms_it = ms / it
+    tfl = cells * POISSON_FLOP_PER_CELL_IT / (ms_it * 1e-3) / 1e12
+    gbs = cells * POISSON_BYTES_PER_CELL_IT / (ms_it * 1e-3) / 1e9
+    return {"workload": f"Poisson sphere test on the stretched {n}^3 grid (monopole, |r| < 1e-10, phi0 = 0)",
+            "iterations": it, "residual": res, "ms_per_solve": ms, "ms_per_iteration": ms_it,
+            "value": cells * it / (ms * 1e-3), "unit": "cell-iterations/s",
+            "fp64": {"achieved": tfl, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tfl / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64"},
+            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "peak_kind": f"{peak_kind} HBM copy"}}
+
+
 def ensemble_c4(P, steps, warmup, stream, ws):
     """24 independent boxes of the stratified-box physics with edges drawn
     from {64, 96, 128, 160, 192} per axis (seed 2024), mixed form: one
@@ -565,6 +610,9 @@ def main():
     ap.add_argument("--no-sts", action="store_true", help="skip the RKL2 thermal-diffusion super step")
     ap.add_argument("--sts-only", action="store_true",
                     help="time only the RKL2 thermal-diffusion super step (print its object; for profiling)")
+    ap.add_argument("--no-poisson", action="store_true", help="skip the Poisson solve")
+    ap.add_argument("--poisson-only", action="store_true",
+                    help="time only the Poisson solve (print its object; for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -588,6 +636,10 @@ def main():
     if args.sts_only:
         if rank == 0:
             print(json.dumps(diffusion_sts(P, args.n, stream, hbm_peak, peak_kind)))
+        return 0
+    if args.poisson_only:
+        if rank == 0:
+            print(json.dumps(poisson_sphere(P, args.n, stream, hbm_peak, peak_kind)))
         return 0
     pr = make_problem(args.n)
     props = torch.cuda.get_device_properties(local)
@@ -626,6 +678,9 @@ def main():
     sts = None
     if not args.no_sts and len(forms) == 2:
         sts = diffusion_sts(P, args.n, stream, hbm_peak, peak_kind)
+    poisson = None
+    if not args.no_poisson and len(forms) == 2:
+        poisson = poisson_sphere(P, args.n, stream, hbm_peak, peak_kind)
     launches = sum(v[0] for v in h["kt"].values())
     forms_out = {f: {"value": r["value"], "ms_per_step": r["ms"] / args.steps,
                      "stage_hbm": stage_hbm(r["value"] / max(ws, 1), f, hbm_peak, peak_kind),
@@ -657,6 +712,7 @@ def main():
         "stellar_eos_box": c3,
         "ensemble_24_boxes": c4,
         "thermal_diffusion_sts": sts,
+        "poisson_sphere": poisson,
         "gpu_launches": launches,
         "e2e": e2e,
         "clocks": clk,
