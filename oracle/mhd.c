@@ -614,17 +614,23 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
           long pR = IXv(G, c3), pL = pR - G->s[d];
           long sd = G->s[d];
           double wl[10 + ORA_MAXSPEC], wr[10 + ORA_MAXSPEC];
+          /* shock flattening (Sect. 2.7): a flagged cell reconstructs with van Leer */
+          const int vlL = c->recon == ORA_RECON_VANLEER || w->flag[pL];
+          const int vlR = c->recon == ORA_RECON_VANLEER || w->flag[pR];
           for (int q = 0; q < G->nw; ++q) {
             const double a = w->W[q][pL - sd], b = w->W[q][pL], cc = w->W[q][pR], e = w->W[q][pR + sd];
-            if (c->recon == ORA_RECON_PPH) {   /* left state: cell pL's right face; right state: pR's left face */
-              if (q < W_X0) { wl[q] = pph_right(a, b, cc); wr[q] = pph_left(b, cc, e); }
+            if (!vlL || !vlR) {   /* PPH: left state from cell pL's right face, right state from pR's left face */
+              double pl, pr;
+              if (q < W_X0) { pl = pph_right(a, b, cc); pr = pph_left(b, cc, e); }
               else {
                 double fl_, fr_;
                 pph_limited(a, b, cc, &fl_, &fr_);
-                wl[q] = fr_;
+                pl = fr_;
                 pph_limited(b, cc, e, &fl_, &fr_);
-                wr[q] = fl_;
+                pr = fl_;
               }
+              wl[q] = vlL ? b + 0.5 * vl_slope(a, b, cc) : pl;
+              wr[q] = vlR ? cc - 0.5 * vl_slope(b, cc, e) : pr;
             } else {
               double sL = vl_slope(a, b, cc);
               double sR = vl_slope(b, cc, e);
