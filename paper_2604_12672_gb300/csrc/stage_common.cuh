@@ -228,22 +228,27 @@ __device__ __forceinline__ void flux_face(const DevGeo &G, const int *c, long pR
   constexpr int NWC = W_X0 + NS;   // components this instantiation can hold
   R wl[NWC], wr[NWC];
   const bool ideal = G.eos == 0;   // ideal gas: gamma_e = gamma_c = gamma (not reconstructed)
+  // shock flattening (Sect. 2.7): a flagged cell reconstructs with van Leer
+  const bool vlL = G.recon == PHL_RECON_VANLEER || flag[pL], vlR = G.recon == PHL_RECON_VANLEER || flag[pR];
   R ql[NWC], qr[NWC];
 #pragma unroll
   for (int v = 0; v < NWC; ++v) {
     if (v >= G.nw || (ideal && (v == W_GE || v == W_GC))) continue;
     const R w0 = fetch(v, 0), w1 = fetch(v, 1), w2 = fetch(v, 2), w3 = fetch(v, 3);
-    if (G.recon == PHL_RECON_PPH) {   // left state: cell pL's right face; right state: pR's left face
+    if (!vlL || !vlR) {   // PPH: left state from cell pL's right face, right state from pR's left face
+      R pl, pr;
       if (v < W_X0) {
-        ql[v] = pph_right(w0, w1, w2);
-        qr[v] = pph_left(w1, w2, w3);
+        pl = pph_right(w0, w1, w2);
+        pr = pph_left(w1, w2, w3);
       } else {
         R fl, fr;
         pph_limited(w0, w1, w2, fl, fr);
-        ql[v] = fr;
+        pl = fr;
         pph_limited(w1, w2, w3, fl, fr);
-        qr[v] = fl;
+        pr = fl;
       }
+      ql[v] = vlL ? w1 + R(0.5) * vl_slope(w0, w1, w2) : pl;
+      qr[v] = vlR ? w2 - R(0.5) * vl_slope(w1, w2, w3) : pr;
     } else {
       ql[v] = w1 + R(0.5) * vl_slope(w0, w1, w2);
       qr[v] = w2 - R(0.5) * vl_slope(w1, w2, w3);

@@ -102,15 +102,15 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
       a[m] = sm.w[0][s2 + (m - 2) * sD];
       b[m] = sm.w[1][s2 + (m - 2) * sD];
     }
+    // PPH: unlimited parabola (no mass fractions on this path); a cell flagged
+    // by the shock flattener reconstructs with van Leer (Sect. 2.7)
+    const uint8_t *fc = &sm.flg[k + 1][j + 1][i + 1];
+    constexpr int fsD = D == 0 ? 1 : (D == 1 ? FX + 2 : (FX + 2) * (FY + 2));
     const bool pph = G.recon == PHL_RECON_PPH;
+    const bool pphL = pph && !fc[-fsD], pphR = pph && !fc[0];
     auto plm = [&](int v, float w0, float w1, float w2, float w3) {
-      if (pph) {   // unlimited parabola (no mass fractions on this path)
-        ql[v] = pph_right(w0, w1, w2);
-        qr[v] = pph_left(w1, w2, w3);
-      } else {
-        ql[v] = w1 + 0.5f * vl_slope(w0, w1, w2);
-        qr[v] = w2 - 0.5f * vl_slope(w1, w2, w3);
-      }
+      ql[v] = pphL ? pph_right(w0, w1, w2) : w1 + 0.5f * vl_slope(w0, w1, w2);
+      qr[v] = pphR ? pph_left(w1, w2, w3) : w2 - 0.5f * vl_slope(w1, w2, w3);
     };
     plm(W_RHO, a[0].x, a[1].x, a[2].x, a[3].x);
     plm(W_VX, a[0].y, a[1].y, a[2].y, a[3].y);
@@ -224,6 +224,11 @@ __device__ __forceinline__ void tile_face2(const DevGeo &G, const StageMx &S, co
   if (!va && !vb) return;
   const int s2a = ((l[0][2] + NGW) * HY + (l[0][1] + NGW)) * HX + (l[0][0] + NGW);
   const int s2b = ((l[1][2] + NGW) * HY + (l[1][1] + NGW)) * HX + (l[1][0] + NGW);
+  // cells flagged by the shock flattener (left / right of each face)
+  const uint8_t *fla = &sm.flg[l[0][2] + 1][l[0][1] + 1][l[0][0] + 1];
+  const uint8_t *flb = &sm.flg[l[1][2] + 1][l[1][1] + 1][l[1][0] + 1];
+  const B2 vlL{fla[-fs] != 0, flb[-fs] != 0}, vlR{fla[0] != 0, flb[0] != 0};
+  const bool vlAny = vlL.x || vlL.y || vlR.x || vlR.y;
   V ql[8], qr[8];
   {
     const V half = vv(0.5f), zero = vv(0.0f);
@@ -251,6 +256,10 @@ __device__ __forceinline__ void tile_face2(const DevGeo &G, const StageMx &S, co
           const V s6 = vv(1.0f / 6.0f), five = vv(5.0f), two = vv(2.0f);
           ql[v] = fma(two, w2, fma(five, w1, neg(w0))) * s6;
           qr[v] = (fma(two, w1, five * w2) - w3) * s6;
+          if (vlAny) {   // cells flagged by the shock flattener reconstruct with van Leer (Sect. 2.7)
+            ql[v] = sel(vlL, fma(half, slope(w0, w1, w2), w1), ql[v]);
+            qr[v] = sel(vlR, fma(neg(half), slope(w1, w2, w3), w2), qr[v]);
+          }
         } else {
           ql[v] = fma(half, slope(w0, w1, w2), w1);
           qr[v] = fma(neg(half), slope(w1, w2, w3), w2);
