@@ -16,7 +16,7 @@ from . import build as _build
 ORA_MAXSPEC = 4
 _RIEMANN = {"lhlld": 0, "hlld": 1, "hll": 2}
 _EOS = {"ideal": 0, "stellar": 1}
-_RECON = {"vanleer": 0, "pph": 1}
+_RECON = {"vanleer": 0, "pph": 1, "pqh": 2}
 
 _dp = C.POINTER(C.c_double)
 
@@ -69,6 +69,8 @@ def lib():
         L.ora_diffuse.restype = C.c_int
         L.ora_diffuse.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp, _dp, C.POINTER(OraDiff), C.c_double, C.c_int,
                                   C.POINTER(C.c_int)]
+        L.ora_recon_cell.restype = None
+        L.ora_recon_cell.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
         L.ora_poisson_nghost.restype = C.c_long
         L.ora_poisson_nghost.argtypes = [C.POINTER(C.c_int)]
         L.ora_multipole_moments.restype = C.c_int
@@ -446,3 +448,11 @@ class Poisson:
         it, res = C.c_int(), C.c_double()
         st = lib().ora_poisson_solve(C.byref(self.p), _ptr(rho), _ptr(phi), _ptr(gh), C.byref(it), C.byref(res))
         return phi, gh, it.value, res.value, st
+
+
+def recon_cell(recon, w5, species=False):
+    """(left, right) face values of the centre of five cell values."""
+    w = np.ascontiguousarray(w5, dtype=np.float64)
+    fl, fr = C.c_double(), C.c_double()
+    lib().ora_recon_cell(_RECON[recon], int(bool(species)), _ptr(w), C.byref(fl), C.byref(fr))
+    return fl.value, fr.value

@@ -255,6 +255,62 @@ static inline void pph_limited(double a, double b, double c, double *fl, double 
   *fl = l; *fr = r;
 }
 
+/* Limited fifth-order reconstruction (Sect. 2.5, item iii: a limited
+ * fifth-order polynomial reconstruction following the PQH method of the cited
+ * Leidi et al. 2024, applied to every variable; that method is not printed,
+ * reading): the face value of the degree-4 polynomial whose averages over the
+ * five cells i-2..i+2 are the cell values,
+ *   right face (2a - 13b + 47c + 27d - 3e) / 60 (the left face mirrored),
+ * limited by the monotonicity-preserving bounds of Suresh & Huynh (1997):
+ * kept where it lies between the cell value and the monotone bound
+ * c + minmod(d - c, 4 (c - b)); otherwise moved to the nearest point of an
+ * interval built from the neighbouring values and curvature estimates, which
+ * contains the smooth extrema a plain clip would flatten. */
+static inline double minmod2(double x, double y) {
+  return (x > 0.0 && y > 0.0) ? (x < y ? x : y) : ((x < 0.0 && y < 0.0) ? (x > y ? x : y) : 0.0);
+}
+static inline double minmod4(double w, double x, double y, double z) {
+  return minmod2(minmod2(w, x), minmod2(y, z));
+}
+static inline double mn3(double x, double y, double z) { double m = x < y ? x : y; return m < z ? m : z; }
+static inline double mx3(double x, double y, double z) { double m = x > y ? x : y; return m > z ? m : z; }
+/* the limited value at the face between c and d of the cells a b c d e */
+static double mp5_face(double a, double b, double c, double d, double e) {
+  const double vor = (2.0 * a - 13.0 * b + 47.0 * c + 27.0 * d - 3.0 * e) / 60.0;
+  const double vmp = c + minmod2(d - c, 4.0 * (c - b));
+  if ((vor - c) * (vor - vmp) <= 0.0) return vor;
+  const double djm1 = a - 2.0 * b + c, dj = b - 2.0 * c + d, djp1 = c - 2.0 * d + e;
+  const double dm4p = minmod4(4.0 * dj - djp1, 4.0 * djp1 - dj, dj, djp1);
+  const double dm4m = minmod4(4.0 * dj - djm1, 4.0 * djm1 - dj, dj, djm1);
+  const double vul = c + 4.0 * (c - b);
+  const double vav = 0.5 * (c + d);
+  const double vmd = vav - 0.5 * dm4p;
+  const double vlc = c + 0.5 * (c - b) + 4.0 / 3.0 * dm4m;
+  const double lo = fmax(mn3(c, d, vmd), mn3(c, vul, vlc));
+  const double hi = fmin(mx3(c, d, vmd), mx3(c, vul, vlc));
+  return vor + minmod2(lo - vor, hi - vor);
+}
+/* left and right face values of cell c (stencil a b c d e) */
+static inline void pqh_limited(double a, double b, double c, double d, double e, double *fl, double *fr) {
+  *fr = mp5_face(a, b, c, d, e);
+  *fl = mp5_face(e, d, c, b, a);
+}
+
+/* Face values of the centre cell w[2] of five cells, for tests: recon, and
+ * species != 0 for a mass fraction (PPH limits only those). */
+void ora_recon_cell(int recon, int species, const double *w, double *fl, double *fr) {
+  if (recon == ORA_RECON_PQH) { pqh_limited(w[0], w[1], w[2], w[3], w[4], fl, fr); return; }
+  if (recon == ORA_RECON_PPH) {
+    if (species) { pph_limited(w[1], w[2], w[3], fl, fr); return; }
+    *fl = pph_left(w[1], w[2], w[3]);
+    *fr = pph_right(w[1], w[2], w[3]);
+    return;
+  }
+  const double sl = vl_slope(w[1], w[2], w[3]);
+  *fl = w[2] - 0.5 * sl;
+  *fr = w[2] + 0.5 * sl;
+}
+
 /* ---------------- Riemann solvers (Sect. 2.6) ---------------- */
 /* Normal-frame state: rho, un, ut1, ut2, Bt1, Bt2, P, ge, gc, X.. */
 enum { R_RHO = 0, R_UN, R_UT1, R_UT2, R_BT1, R_BT2, R_P, R_GE, R_GC, R_X0 };
@@ -619,7 +675,16 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
           const int vlR = c->recon == ORA_RECON_VANLEER || w->flag[pR];
           for (int q = 0; q < G->nw; ++q) {
             const double a = w->W[q][pL - sd], b = w->W[q][pL], cc = w->W[q][pR], e = w->W[q][pR + sd];
-            if (!vlL || !vlR) {   /* PPH: left state from cell pL's right face, right state from pR's left face */
+            if (c->recon == ORA_RECON_PQH && (!vlL || !vlR)) {
+              double fl_, fr_, pl, pr;
+              const double a2 = w->W[q][pL - 2 * sd], e2 = w->W[q][pR + 2 * sd];
+              pqh_limited(a2, a, b, cc, e, &fl_, &fr_);   /* cell pL */
+              pl = fr_;
+              pqh_limited(a, b, cc, e, e2, &fl_, &fr_);   /* cell pR */
+              pr = fl_;
+              wl[q] = vlL ? b + 0.5 * vl_slope(a, b, cc) : pl;
+              wr[q] = vlR ? cc - 0.5 * vl_slope(b, cc, e) : pr;
+            } else if (!vlL || !vlR) {   /* PPH: left state from cell pL's right face, right state from pR's left face */
               double pl, pr;
               if (q < W_X0) { pl = pph_right(a, b, cc); pr = pph_left(b, cc, e); }
               else {

@@ -28,7 +28,7 @@ extern "C" {
 enum { ORA_PERIODIC = 0, ORA_REFLECT = 1, ORA_OUTFLOW = 2 };
 enum { ORA_EOS_IDEAL = 0, ORA_EOS_STELLAR = 1 };
 enum { ORA_LHLLD = 0, ORA_HLLD = 1, ORA_HLL = 2 };
-enum { ORA_RECON_VANLEER = 0, ORA_RECON_PPH = 1 };
+enum { ORA_RECON_VANLEER = 0, ORA_RECON_PPH = 1, ORA_RECON_PQH = 2 };
 #define ORA_MAXSPEC 4
 
 typedef struct {
@@ -53,7 +53,7 @@ typedef struct {
   double newton_tol;        /* stellar EOS */
   int newton_maxit;
   const void *eos_table;    /* stellar EOS table (ora_eos_table_build) */
-  int recon;                /* ORA_RECON_VANLEER (limited linear) or ORA_RECON_PPH */
+  int recon;                /* ORA_RECON_VANLEER (limited linear), _PPH, _PQH (limited fifth order) */
 } ora_cfg;
 
 /* Thermal diffusion (Sect. 2.10): conductivity K = k0 T^nT / rho^nR with
@@ -77,6 +77,10 @@ int ora_sts_stages(double dt, double dt_p);
  * (non-positive rho or e_int) or -4 (more than max_stages stages needed). */
 int ora_diffuse(const ora_cfg *cfg, double *cons, const double *bx, const double *by, const double *bz,
                 const ora_diff *p, double dt, int max_stages, int *nsts_out);
+
+/* Face values (left, right) of the centre cell w[2] of five cells under a
+ * reconstruction; species != 0: a mass fraction. */
+void ora_recon_cell(int recon, int species, const double *w, double *fl, double *fr);
 
 /* Poisson solver for the gravitational potential (poisson.c, Sect. 2.12).
  * xf[d]: the n[d] + 1 increasing face coordinates of axis d; rho, phi: cell
