@@ -61,7 +61,7 @@ typedef enum {
 enum { PHL_PERIODIC = 0, PHL_REFLECT = 1, PHL_OUTFLOW = 2 };
 enum { PHL_EOS_IDEAL = 0, PHL_EOS_STELLAR = 1 };
 enum { PHL_LHLLD = 0, PHL_HLLD = 1, PHL_HLL = 2 };
-enum { PHL_RECON_VANLEER = 0, PHL_RECON_PPH = 1 };
+enum { PHL_RECON_VANLEER = 0, PHL_RECON_PPH = 1, PHL_RECON_PQH = 2 };
 enum { PHL_FP64 = 0, PHL_MIXED = 1 };
 enum { PHL_HOST = 0, PHL_DEVICE = 1 };
 #define PHL_MAXSPEC 4
@@ -105,7 +105,13 @@ typedef struct {
    * slope, item i; the default, 0); PHL_RECON_PPH, the three-cell parabola of
    * item ii -- unlimited for the primitive variables, limited for the mass
    * fractions (the piecewise-parabolic method's monotonicity constraints).
-   * Both use the same three-cell stencil per face side. */
+   * Both use the same three-cell stencil per face side.  PHL_RECON_PQH, the
+   * limited fifth-order reconstruction of item iii for every variable: the
+   * face value of the degree-4 polynomial through five cell averages, limited
+   * by the monotonicity-preserving bounds of Suresh & Huynh (1997); five-cell
+   * stencil, three ghost layers, not on the fused tile kernel (phl_set_fused
+   * declines it).  Under every scheme, cells flagged by the shock flattener
+   * reconstruct with van Leer (Sect. 2.7). */
   int recon;
 } phl_grid_desc;
 

@@ -20,7 +20,7 @@ PERIODIC, REFLECT, OUTFLOW = 0, 1, 2
 EOS = {"ideal": 0, "stellar": 1}
 RIEMANN = {"lhlld": 0, "hlld": 1, "hll": 2}
 PRECISION = {"fp64": 0, "mixed": 1, "mixed_x2": 2, "mixed_lr": 3}
-RECON = {"vanleer": 0, "pph": 1}
+RECON = {"vanleer": 0, "pph": 1, "pqh": 2}
 HOST, DEVICE = 0, 1
 STATUS = {0: "PHL_OK", 1: "PHL_EINVAL", 2: "PHL_ECUDA", 3: "PHL_ENOMEM", 4: "PHL_ENEGATIVE",
           5: "PHL_ENAN", 6: "PHL_ENEWTON", 7: "PHL_ETIMEOUT", 8: "PHL_EUNSUPPORTED"}

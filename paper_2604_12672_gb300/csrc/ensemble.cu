@@ -409,7 +409,7 @@ phl_status phl_ensemble_create(const phl_grid_desc *descs, int nbox, int use_gra
     R.b_int = make_box(0, nx, 0, ny, 0, nz);
     int l[3], h[3];
     for (int d = 0; d < 3; ++d) {
-      if (G.act[d]) { l[d] = -NGW; h[d] = G.n[d] + NGW; } else { l[d] = 0; h[d] = 1; }
+      if (G.act[d]) { l[d] = -G.ge[d]; h[d] = G.n[d] + G.ge[d]; } else { l[d] = 0; h[d] = 1; }
     }
     R.b_work = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
     for (int d = 0; d < 3; ++d) {

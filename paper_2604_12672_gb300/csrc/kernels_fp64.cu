@@ -200,10 +200,10 @@ void launch_stage_fp64(const DevGeo &G, const StageBufs &S, cudaStream_t s, int 
     if (G.act[d]) { lo = -lo_g; hi = G.n[d] + hi_extra; }
     else { lo = 0; hi = 1; }
   };
-  // (1) primitives on cells [-2, n+2) of every active dimension
+  // (1) primitives on cells [-ge, n+ge) of every active dimension (ge: the work layout's ghost layers)
   {
     int l[3], h[3];
-    for (int d = 0; d < 3; ++d) rng(d, NGW, NGW, l[d], h[d]);
+    for (int d = 0; d < 3; ++d) rng(d, G.ge[d], G.ge[d], l[d], h[d]);
     Box b = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
     if (G.eos == 1) {
       launch_eos_cells<double>(G, S.Uin, S.Bin, nullptr, nullptr, S.Tin, S.Tout, S.W, S.dflag, s, &nl, prof);

@@ -71,7 +71,7 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
   };
   {
     int l[3], h[3];
-    for (int d = 0; d < 3; ++d) rng(d, NGW, NGW, l[d], h[d]);
+    for (int d = 0; d < 3; ++d) rng(d, G.ge[d], G.ge[d], l[d], h[d]);
     Box bx = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
     if (G.eos == 1) {
       launch_eos_cells<float>(G, M.U, M.B, dU, dB, M.Tin, M.Tout, M.W, M.dflag, s, &nl, prof);

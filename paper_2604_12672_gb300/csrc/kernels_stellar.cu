@@ -331,7 +331,7 @@ void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const 
   PHL_LAUNCH(KC_PRIM, prof, s, k_eos_cells<R><<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout, W, dflag));
   int l[3], h[3];
   for (int d = 0; d < 3; ++d) {
-    if (G.act[d]) { l[d] = -NGW; h[d] = G.n[d] + NGW; } else { l[d] = 0; h[d] = 1; }
+    if (G.act[d]) { l[d] = -G.ge[d]; h[d] = G.n[d] + G.ge[d]; } else { l[d] = 0; h[d] = 1; }
   }
   Box be = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
   PHL_LAUNCH(KC_PRIM, prof, s, k_ghost_fill<R><<<grid3(be), block3(be), 0, s>>>(G, be, W));

@@ -287,7 +287,8 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   if (!(d->cfl > 0.0)) return fail(PHL_EINVAL, "cfl must be positive");
   if (d->rk != 2 && d->rk != 3) return fail(PHL_EINVAL, "rk must be 2 or 3");
   if (d->riemann < 0 || d->riemann > 2) return fail(PHL_EINVAL, "bad riemann solver");
-  if (d->recon != PHL_RECON_VANLEER && d->recon != PHL_RECON_PPH) return fail(PHL_EINVAL, "bad reconstruction");
+  if (d->recon != PHL_RECON_VANLEER && d->recon != PHL_RECON_PPH && d->recon != PHL_RECON_PQH)
+    return fail(PHL_EINVAL, "bad reconstruction");
   if (d->precision != PHL_FP64 && d->precision != PHL_MIXED) return fail(PHL_EINVAL, "bad precision mode");
   if (d->bg_rho_c && (!d->bg_p_c || !d->bg_rho_f || !d->bg_p_f))
     return fail(PHL_EINVAL, "incomplete background profiles");
@@ -306,7 +307,7 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     G.bc[k][1] = d->bc[k][1];
     G.dx[k] = (d->hi[k] - d->lo[k]) / d->n[k];
     G.idx[k] = 1.0 / G.dx[k];
-    G.ge[k] = G.act[k] ? NGW : 0;
+    G.ge[k] = G.act[k] ? (d->recon == PHL_RECON_PQH ? NGW + 1 : NGW) : 0;   // PQH: five-cell stencil
     G.g[k] = d->g[k];
   }
   const long pitch = ((long)d->n[0] + 1 + 3) / 4 * 4;

@@ -117,6 +117,32 @@ __device__ __forceinline__ void pph_limited(R a, R b, R c, R &fl, R &fr) {
   fr = r;
 }
 
+// Limited fifth-order reconstruction (Sect. 2.5, item iii; the cited PQH
+// method is not printed): the face value of the degree-4 polynomial whose
+// averages over five cells are the cell values, limited by the
+// monotonicity-preserving bounds of Suresh & Huynh (1997).  mp5_face(a..e):
+// the value at the face between c and d; the left face of c is
+// mp5_face(e, d, c, b, a).
+template <typename R>
+__device__ __forceinline__ R mm2(R x, R y) {
+  return (x > R(0) && y > R(0)) ? fmin(x, y) : ((x < R(0) && y < R(0)) ? fmax(x, y) : R(0));
+}
+template <typename R>
+__device__ __forceinline__ R mp5_face(R a, R b, R c, R d, R e) {
+  const R vor = (R(2) * a - R(13) * b + R(47) * c + R(27) * d - R(3) * e) / R(60);
+  const R vmp = c + mm2(d - c, R(4) * (c - b));
+  if ((vor - c) * (vor - vmp) <= R(0)) return vor;
+  const R djm1 = a - R(2) * b + c, dj = b - R(2) * c + d, djp1 = c - R(2) * d + e;
+  const R dm4p = mm2(mm2(R(4) * dj - djp1, R(4) * djp1 - dj), mm2(dj, djp1));
+  const R dm4m = mm2(mm2(R(4) * dj - djm1, R(4) * djm1 - dj), mm2(dj, djm1));
+  const R vul = c + R(4) * (c - b);
+  const R vmd = R(0.5) * (c + d) - R(0.5) * dm4p;
+  const R vlc = c + R(0.5) * (c - b) + R(4.0 / 3.0) * dm4m;
+  const R lo = fmax(fmin(fmin(c, d), vmd), fmin(fmin(c, vul), vlc));
+  const R hi = fmin(fmax(fmax(c, d), vmd), fmax(fmax(c, vul), vlc));
+  return vor + mm2(lo - vor, hi - vor);
+}
+
 __device__ __forceinline__ long wstride(const DevGeo &G, int d) { return d == 0 ? 1L : (d == 1 ? G.wy : G.wz); }
 
 template <typename R>
@@ -235,7 +261,11 @@ __device__ __forceinline__ void flux_face(const DevGeo &G, const int *c, long pR
   for (int v = 0; v < NWC; ++v) {
     if (v >= G.nw || (ideal && (v == W_GE || v == W_GC))) continue;
     const R w0 = fetch(v, 0), w1 = fetch(v, 1), w2 = fetch(v, 2), w3 = fetch(v, 3);
-    if (!vlL || !vlR) {   // PPH: left state from cell pL's right face, right state from pR's left face
+    if (G.recon == PHL_RECON_PQH && (!vlL || !vlR)) {   // cells pL-2..pR+2 (three ghost layers)
+      const R wm = fetch(v, -1), w4 = fetch(v, 4);
+      ql[v] = vlL ? w1 + R(0.5) * vl_slope(w0, w1, w2) : mp5_face(wm, w0, w1, w2, w3);
+      qr[v] = vlR ? w2 - R(0.5) * vl_slope(w1, w2, w3) : mp5_face(w4, w3, w2, w1, w0);
+    } else if (!vlL || !vlR) {   // PPH: left state from cell pL's right face, right state from pR's left face
       R pl, pr;
       if (v < W_X0) {
         pl = pph_right(w0, w1, w2);

@@ -763,7 +763,8 @@ cudaError_t fused_init() {
 }
 
 bool fused_stage_ok(const DevGeo &G) {
-  return G.eos == PHL_EOS_IDEAL && G.nspec == 0 && G.wstr == 8 && G.act[0] && G.act[1] && G.act[2];
+  return G.eos == PHL_EOS_IDEAL && G.nspec == 0 && G.wstr == 8 && G.act[0] && G.act[1] && G.act[2] &&
+         G.recon != PHL_RECON_PQH;   // the tile stages two ghost layers; PQH needs three
 }
 
 // TMA descriptor of W's two float4 planes as a 4-D tensor (x * 4 floats, y, z,
