@@ -701,6 +701,14 @@ def main():
         gp.close()
         vp, msp = whole_job_rate(pr.ncells * STAGES * args.steps, msp, ws)
         forms_out["mixed_pph"] = {"value": vp, "ms_per_step": msp / args.steps}
+        # the limited fifth-order reconstruction (item iii): per-direction mixed
+        # kernels (the fused tile stages two ghost layers; PQH needs three)
+        q = pr.copy()
+        q.recon = "pqh"
+        gq, msq, _, _ = time_form(P, q, "mixed", args.steps, args.warmup, stream, ws, 0)
+        gq.close()
+        vq, msq = whole_job_rate(pr.ncells * STAGES * args.steps, msq, ws)
+        forms_out["mixed_pqh"] = {"value": vq, "ms_per_step": msq / args.steps, "path": "per-direction kernels"}
     line = {
         "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True,

@@ -88,7 +88,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity,
 // Flux of the D-face at the lower side of staged cell s2 (its right cell),
 // tile cell (i, j, k), global cell c.  Returns the five fluid components in
 // out[] and stores the EMF inputs when the tile owns the face.
-template <int D, bool LR>
+template <int D, bool LR, bool PPH>
 __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int s2, int i,
                                            int j, int k, const int *c, bool own, float *__restrict__ Fd,
                                            const GasK<float> &K, float *out, int *dflag) {
@@ -106,11 +106,15 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
     // by the shock flattener reconstructs with van Leer (Sect. 2.7)
     const uint8_t *fc = &sm.flg[k + 1][j + 1][i + 1];
     constexpr int fsD = D == 0 ? 1 : (D == 1 ? FX + 2 : (FX + 2) * (FY + 2));
-    const bool pph = G.recon == PHL_RECON_PPH;
-    const bool pphL = pph && !fc[-fsD], pphR = pph && !fc[0];
+    const bool pphL = PPH && !fc[-fsD], pphR = PPH && !fc[0];
     auto plm = [&](int v, float w0, float w1, float w2, float w3) {
-      ql[v] = pphL ? pph_right(w0, w1, w2) : w1 + 0.5f * vl_slope(w0, w1, w2);
-      qr[v] = pphR ? pph_left(w1, w2, w3) : w2 - 0.5f * vl_slope(w1, w2, w3);
+      if constexpr (PPH) {   // the per-cell choice only in the PPH instantiation
+        ql[v] = pphL ? pph_right(w0, w1, w2) : w1 + 0.5f * vl_slope(w0, w1, w2);
+        qr[v] = pphR ? pph_left(w1, w2, w3) : w2 - 0.5f * vl_slope(w1, w2, w3);
+      } else {
+        ql[v] = w1 + 0.5f * vl_slope(w0, w1, w2);
+        qr[v] = w2 - 0.5f * vl_slope(w1, w2, w3);
+      }
     };
     plm(W_RHO, a[0].x, a[1].x, a[2].x, a[3].x);
     plm(W_VX, a[0].y, a[1].y, a[2].y, a[3].y);
@@ -170,7 +174,7 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
 
 // Evaluates face f of direction D (its index among the tile's D-faces) and
 // returns the five fluid flux components (zeros outside the domain).
-template <int D, bool LR>
+template <int D, bool LR, bool PPH>
 __device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int f, int x0,
                                           int y0, int z0, float *F0, float *F1, float *F2, const GasK<float> &K,
                                           float *out, int *dflag) {
@@ -188,7 +192,7 @@ __device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, con
   const int loc = D == 0 ? i : (D == 1 ? j : k);
   const bool own = loc < ext || c[D] == G.n[D];
   float *Fd = D == 0 ? F0 : (D == 1 ? F1 : F2);
-  fused_face<D, LR>(G, S, sm, s2, i, j, k, c, own, Fd, K, out, dflag);
+  fused_face<D, LR, PPH>(G, S, sm, s2, i, j, k, c, own, Fd, K, out, dflag);
 }
 
 // Two D-faces of the tile (fa, fb: indices among its D-faces) evaluated
@@ -196,7 +200,7 @@ __device__ __forceinline__ void tile_face(const DevGeo &G, const StageMx &S, con
 // of riemann_x2.cuh, lane x = face fa, lane y = face fb.  With hasb false the
 // second lane repeats fa and its results are dropped.  Faces outside the
 // domain give zeros, as in tile_face.
-template <int D>
+template <int D, bool PPH>
 __device__ __forceinline__ void tile_face2(const DevGeo &G, const StageMx &S, const FusedSmem &sm, int fa, int fb,
                                            bool hasb, int x0, int y0, int z0, float *F0, float *F1, float *F2,
                                            const GasK<float> &K, float *oa, float *ob, int *dflag) {
@@ -252,7 +256,7 @@ __device__ __forceinline__ void tile_face2(const DevGeo &G, const StageMx &S, co
         auto comp = [&](const float4 &u) { return e == 0 ? u.x : (e == 1 ? u.y : (e == 2 ? u.z : u.w)); };
         const V w0 = vv(comp(A[0]), comp(Bv[0])), w1 = vv(comp(A[1]), comp(Bv[1]));
         const V w2 = vv(comp(A[2]), comp(Bv[2])), w3 = vv(comp(A[3]), comp(Bv[3]));
-        if (G.recon == PHL_RECON_PPH) {   // unlimited parabola: (-w0 + 5 w1 + 2 w2) / 6, (2 w1 + 5 w2 - w3) / 6
+        if constexpr (PPH) {   // unlimited parabola: (-w0 + 5 w1 + 2 w2) / 6, (2 w1 + 5 w2 - w3) / 6
           const V s6 = vv(1.0f / 6.0f), five = vv(5.0f), two = vv(2.0f);
           ql[v] = fma(two, w2, fma(five, w1, neg(w0))) * s6;
           qr[v] = (fma(two, w1, five * w2) - w3) * s6;
@@ -336,7 +340,7 @@ __device__ __forceinline__ void tile_face2(const DevGeo &G, const StageMx &S, co
 
 // One direction's faces of the tile through the face buffer, then each
 // thread's running residuals of its cells (phased variant).
-template <int D, int NT, int CPT, int FS, bool PAIRED, bool LR>
+template <int D, int NT, int CPT, int FS, bool PAIRED, bool LR, bool PPH>
 __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, FusedSmem &sm, float *fb, int tid,
                                            int x0, int y0, int z0, float *F0, float *F1, float *F2,
                                            const GasK<float> &K, float (*racc)[5], int *dflag) {
@@ -347,7 +351,7 @@ __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, Fu
       const int g2 = f + NT;
       const bool hasb = g2 < NXF;
       float oa[5], ob[5];
-      tile_face2<D>(G, S, sm, f, hasb ? g2 : f, hasb, x0, y0, z0, F0, F1, F2, K, oa, ob, dflag);
+      tile_face2<D, PPH>(G, S, sm, f, hasb ? g2 : f, hasb, x0, y0, z0, F0, F1, F2, K, oa, ob, dflag);
 #pragma unroll
       for (int q = 0; q < 5; ++q) fb[q * FS + f] = oa[q];
       if (hasb) {
@@ -358,7 +362,7 @@ __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, Fu
   } else {
     for (int f = tid; f < NXF; f += NT) {
       float out[5];
-      tile_face<D, LR>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      tile_face<D, LR, PPH>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
 #pragma unroll
       for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
     }
@@ -388,7 +392,7 @@ __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, Fu
 // direction's faces; each thread keeps the running residuals of its cells in
 // registers (same summation order x, y, z), so the CTA needs ~1/3 of the
 // shared memory and more CTAs fit on an SM.
-template <int NT, int MINB, bool PHASED, bool PAIRED = false, bool LR = false>
+template <int NT, int MINB, bool PHASED, bool PAIRED = false, bool LR = false, bool PPH = false>
 __global__ void __launch_bounds__(NT, MINB)
     k_flux_update_mx(const __grid_constant__ CUtensorMap tmW, DevGeo G, StageMx S, const uint8_t *__restrict__ flag,
                      float *__restrict__ F0, float *__restrict__ F1, float *__restrict__ F2, int ntx, int nty,
@@ -479,16 +483,16 @@ __global__ void __launch_bounds__(NT, MINB)
 
   if constexpr (PHASED) {
     static_assert(NXF == NYF && NYF == NZF, "phased tiles need equal face counts per direction");
-    tile_phase<0, NT, CPT, FS, PAIRED, LR>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
-    tile_phase<1, NT, CPT, FS, PAIRED, LR>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
-    tile_phase<2, NT, CPT, FS, PAIRED, LR>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<0, NT, CPT, FS, PAIRED, LR, PPH>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<1, NT, CPT, FS, PAIRED, LR, PPH>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
+    tile_phase<2, NT, CPT, FS, PAIRED, LR, PPH>(G, S, sm, fb, tid, x0, y0, z0, F0, F1, F2, K, racc, dflag);
   } else {
     // NXF and NXF + NYF are multiples of 32: the direction is uniform in a warp
     for (int f = tid; f < NFACE; f += NT) {
       float out[5];
-      if (f < NXF) tile_face<0, LR>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
-      else if (f < NXF + NYF) tile_face<1, LR>(G, S, sm, f - NXF, x0, y0, z0, F0, F1, F2, K, out, dflag);
-      else tile_face<2, LR>(G, S, sm, f - NXF - NYF, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      if (f < NXF) tile_face<0, LR, PPH>(G, S, sm, f, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      else if (f < NXF + NYF) tile_face<1, LR, PPH>(G, S, sm, f - NXF, x0, y0, z0, F0, F1, F2, K, out, dflag);
+      else tile_face<2, LR, PPH>(G, S, sm, f - NXF - NYF, x0, y0, z0, F0, F1, F2, K, out, dflag);
 #pragma unroll
       for (int q = 0; q < 5; ++q) fb[q * FS + f] = out[q];
     }
@@ -758,6 +762,34 @@ cudaError_t fused_init() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes(true));
+  // the PPH instantiations
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, false, false, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<288, 3, true, false, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<256, 3, true, false, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<384, 2, true, false, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<288, 2, true, true, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<288, 1, true, true, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<288, 3, true, false, true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, false, false, true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, true, true, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true));
   done = e;
   return e;
 }
@@ -806,12 +838,16 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   }
   const CUtensorMap *tm = (const CUtensorMap *)M.tmapW;
   // launch shapes: (threads, min CTAs per SM, phased)
-#define PHL_FUSED(NT, MB, PH, PA, LRS)                                                                          \
-  do {                                                                                                         \
-    PHL_LAUNCH(KC_FLUX_UPDATE, prof, s,                                                                        \
-               (k_flux_update_mx<NT, MB, PH, PA, LRS><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0],   \
-                                                                                 M.F[1], M.F[2], ntx, nty,     \
-                                                                                 M.dflag, M.test_extra_tx)));  \
+#define PHL_FUSED1(NT, MB, PH, PA, LRS, PP)                                                                     \
+  PHL_LAUNCH(KC_FLUX_UPDATE, prof, s,                                                                          \
+             (k_flux_update_mx<NT, MB, PH, PA, LRS, PP><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0],   \
+                                                                                   M.F[1], M.F[2], ntx, nty,     \
+                                                                                   M.dflag, M.test_extra_tx)))
+  // the reconstruction is a template parameter: the van Leer kernels carry no PPH code
+#define PHL_FUSED(NT, MB, PH, PA, LRS)                      \
+  do {                                                     \
+    if (G.recon == PHL_RECON_PPH) PHL_FUSED1(NT, MB, PH, PA, LRS, true); \
+    else PHL_FUSED1(NT, MB, PH, PA, LRS, false);           \
   } while (0)
   switch (M.fused_variant) {
     case 2: PHL_FUSED(288, 3, true, false, false); break;
@@ -825,6 +861,7 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
     default: PHL_FUSED(256, 2, false, false, false); break;
   }
 #undef PHL_FUSED
+#undef PHL_FUSED1
   ++*nl;
   Box bs = make_box(0, G.n[0] + 1, 0, G.n[1] + 1, 0, G.n[2] + 1);
   PHL_LAUNCH(KC_EMF, prof, s, k_emf3<<<grid3(bs), block3(bs), 0, s>>>(G, bs, M.W, M.F[0], M.F[1], M.F[2], M.E));
