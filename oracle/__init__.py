@@ -36,7 +36,7 @@ class OraCfg(C.Structure):
 
 
 class OraDiff(C.Structure):
-    _fields_ = [("k0", C.c_double), ("nT", C.c_int), ("nR", C.c_int), ("cv", C.c_double)]
+    _fields_ = [("k0", C.c_double), ("nT", C.c_int), ("nR", C.c_int), ("cv", C.c_double), ("delta_T", C.c_int)]
 
 
 class OraPoisson(C.Structure):
@@ -203,13 +203,13 @@ class Oracle:
                             _ptr(np.ascontiguousarray(st["bx"])), _ptr(np.ascontiguousarray(st["by"])),
                             _ptr(np.ascontiguousarray(st["bz"])), _ptr(T))
 
-    def diffuse(self, dt, k0, nT=0, nR=0, cv=1.5, state=None, max_stages=100000):
+    def diffuse(self, dt, k0, nT=0, nR=0, cv=1.5, state=None, max_stages=100000, delta_T=False):
         """One RKL2 thermal-diffusion super step (diffusion.c); returns
         (state dict with the new total energy, number of stages)."""
         pr = self.pr
         st = state or dict(cons=pr.cons, bx=pr.bx, by=pr.by, bz=pr.bz)
         cons = np.ascontiguousarray(st["cons"], dtype=np.float64).copy()
-        p = OraDiff(k0=float(k0), nT=int(nT), nR=int(nR), cv=float(cv))
+        p = OraDiff(k0=float(k0), nT=int(nT), nR=int(nR), cv=float(cv), delta_T=int(bool(delta_T)))
         ns = C.c_int(0)
         rc = lib().ora_diffuse(C.byref(self.cfg), _ptr(cons), *[_ptr(np.ascontiguousarray(st[k])) for k in ("bx", "by", "bz")],
                                C.byref(p), float(dt), int(max_stages), C.byref(ns))

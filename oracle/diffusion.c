@@ -17,6 +17,11 @@
  * periodic carries no flux (the reflecting mirror and the outflow copy both
  * give the ghost the cell's own temperature).
  *
+ * Option (Sect. 2.10, last paragraph): with delta_T the operator acts on the
+ * deviation from the background temperature, div(K grad (T - T_hat)), T_hat =
+ * P_hat / ((gamma - 1) rho_hat c_v) of the well-balancing background at the
+ * cell centres; K stays that of the full temperature.
+ *
  * Time: RKL2 (Meyer, Balsara & Aslam 2012) over the whole step dt, in the
  * paper's stage form (items i-iv of Sect. 2.10), with the paper's count
  *     N_STS = max(1 + floor((sqrt(9 + 16 dt / dt_p) - 1) / 2), 3),
@@ -28,6 +33,8 @@
 #include <stdlib.h>
 
 #include "oracle.h"
+
+#define BG_GHOST 3   /* the background profiles carry nz + 6 values: three ghost layers per side */
 
 /* RKL2 coefficients of an s-stage step (Meyer, Balsara & Aslam 2012), index
  * j = 1..s: b_0 = b_1 = b_2 = 1/3, b_j = (j^2 + j - 2) / (2 j (j + 1)),
@@ -76,6 +83,7 @@ typedef struct {
   int n[3], act[3], per[3];
   double dx[3];
   long nc;
+  const double *That;   /* background temperature per z layer (NULL: none subtracted) */
 } dgrid;
 
 static long cidx(const dgrid *g, int i, int j, int k) { return i + (long)g->n[0] * (j + (long)g->n[1] * k); }
@@ -113,7 +121,9 @@ static void diff_op(const dgrid *g, const ora_diff *p, const double *rho, const 
             const long qn = cidx(g, cc[0], cc[1], cc[2]);
             const double Ks = K[q] + K[qn];
             const double Kf = Ks > 0.0 ? 2.0 * K[q] * K[qn] / Ks : 0.0;   /* harmonic mean */
-            const double gradT = (Y[qn] / p->cv - Tc) / g->dx[d];   /* toward the neighbour */
+            double dT = Y[qn] / p->cv - Tc;
+            if (g->That) dT -= g->That[cc[2]] - g->That[k];   /* the deviation T - T_hat */
+            const double gradT = dT / g->dx[d];   /* toward the neighbour */
             flux_sum += Kf * gradT;
           }
           s += flux_sum / g->dx[d];
@@ -134,10 +144,19 @@ int ora_diffuse(const ora_cfg *cfg, double *cons, const double *bx, const double
     g.nc *= g.n[d];
   }
   if (!(p->cv > 0.0) || !(p->k0 >= 0.0) || p->nT < 0 || p->nR < 0 || !(dt > 0.0)) return -1;
+  if (p->delta_T && !cfg->bg_rho_c) return -1;
+  g.That = NULL;
+  double *That = NULL;
+  if (p->delta_T) {
+    That = (double *)malloc((size_t)g.n[2] * sizeof(double));
+    for (int k = 0; k < g.n[2]; ++k)
+      That[k] = cfg->bg_p_c[k + BG_GHOST] / ((cfg->gamma - 1.0) * cfg->bg_rho_c[k + BG_GHOST] * p->cv);
+    g.That = That;
+  }
   const long nc = g.nc;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   double *buf = (double *)malloc(8 * (size_t)nc * sizeof(double));
-  if (!buf) return -1;
+  if (!buf) { free(That); return -1; }
   double *rho = buf, *Y0 = buf + nc, *L0 = buf + 2 * nc, *Ym2 = buf + 3 * nc, *Ym1 = buf + 4 * nc,
          *Y = buf + 5 * nc, *L = buf + 6 * nc, *K = buf + 7 * nc;
   /* e_int of the state, with rho, u and the cell-centred field fixed */
@@ -154,7 +173,7 @@ int ora_diffuse(const ora_cfg *cfg, double *cons, const double *bx, const double
         const double bcz = 0.5 * (bz[i + (long)nx * (j + (long)ny * k)] + bz[i + (long)nx * (j + (long)ny * (k + 1))]);
         rho[q] = r;
         Y0[q] = cons[4 * nc + q] / r - 0.5 * (ux * ux + uy * uy + uz * uz) - 0.5 * (bcx * bcx + bcy * bcy + bcz * bcz) / r;
-        if (!(r > 0.0) || !(Y0[q] > 0.0)) { free(buf); return -2; }
+        if (!(r > 0.0) || !(Y0[q] > 0.0)) { free(buf); free(That); return -2; }
       }
   /* parabolic step limit and the number of stages */
   double dmax = 0.0;
@@ -168,7 +187,7 @@ int ora_diffuse(const ora_cfg *cfg, double *cons, const double *bx, const double
   int s = 3;
   if (dmax > 0.0) s = ora_sts_stages(dt, 0.5 / dmax);
   if (nsts_out) *nsts_out = s;
-  if (s > max_stages) { free(buf); return -4; }
+  if (s > max_stages) { free(buf); free(That); return -4; }
   double *co = (double *)malloc(4 * (size_t)(s + 1) * sizeof(double));
   double *mu = co, *nu = co + s + 1, *mut = nu + s + 1, *gat = mut + s + 1;
   ora_rkl2_coeffs(s, mu, nu, mut, gat);
@@ -185,5 +204,6 @@ int ora_diffuse(const ora_cfg *cfg, double *cons, const double *bx, const double
   for (long q = 0; q < nc; ++q) cons[4 * nc + q] += rho[q] * (Ym1[q] - Y0[q]);
   free(co);
   free(buf);
+  free(That);
   return 0;
 }

@@ -62,6 +62,8 @@ typedef struct {
   double k0;
   int nT, nR;
   double cv;
+  int delta_T;              /* 1: diffuse only T - T_hat, the deviation from the */
+                            /* background temperature P_hat / ((gamma-1) rho_hat cv) */
 } ora_diff;
 
 /* RKL2 coefficients mu_j, nu_j, mu~_j, gamma~_j (j = 1..s; arrays of s + 1),

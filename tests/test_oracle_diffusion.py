@@ -114,3 +114,31 @@ def test_insulating_cells_block_the_flux():
         a, b = E0[:, part].sum(), E1[:, part].sum()
         assert abs(b - a) <= 1e-12 * abs(a), (a, b)
     assert np.abs(E1[:, inner] - E0[:, inner]).max() > 1e-2     # heat does spread inside
+
+
+def test_delta_T_option_leaves_the_background_alone():
+    """Sect. 2.10's option: diffusing T - T_hat (the deviation from the
+    hydrostatic background) leaves the background at rest untouched, whereas
+    the full operator conducts heat down the background's temperature
+    gradient; with a constant conductivity the option is the full operator
+    minus its action on the background (linearity)."""
+    rest = W.stratified_box(6, 5, 24, amp=0.0, heat=False)
+    cv = 1.0 / (rest.gamma - 1.0)
+    kw = dict(k0=3e-3, nT=0, nR=0, cv=cv)
+    o = O.Oracle(rest)
+    st_d, ns_d = o.diffuse(5e-3, delta_T=True, **kw)
+    st_f, ns_f = o.diffuse(5e-3, **kw)
+    assert ns_d == ns_f >= 3
+    # at rest e_int = (E - B^2/2)/rho equals the background's P/((gamma-1) rho) up to rounding
+    assert np.array_equal(st_d["cons"][:4], rest.cons[:4])
+    assert np.abs(st_d["cons"][4] - rest.cons[4]).max() <= 1e-13 * np.abs(rest.cons[4]).max()
+    assert np.abs(st_f["cons"][4] - rest.cons[4]).max() > 1e-6 * np.abs(rest.cons[4]).max()
+    pert = rest.copy()                                  # a temperature perturbation, the same rho
+    pert.cons = rest.cons.copy()
+    rng = np.random.default_rng(4)
+    pert.cons[4] = rest.cons[4] * (1.0 + 3e-2 * rng.uniform(-1, 1, rest.cons[4].shape))
+    op = O.Oracle(pert)
+    d_opt = op.diffuse(5e-3, delta_T=True, **kw)[0]["cons"][4] - pert.cons[4]
+    d_full = op.diffuse(5e-3, **kw)[0]["cons"][4] - pert.cons[4]
+    d_bg = st_f["cons"][4] - rest.cons[4]
+    assert np.abs(d_opt - (d_full - d_bg)).max() <= 1e-9 * np.abs(d_full).max()
