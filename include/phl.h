@@ -202,6 +202,10 @@ typedef struct {
                             /* in double), either grid                         */
   int tile_z;               /* mixed stage kernel: planes per CTA (0: 16), a    */
                             /* tuning knob; results do not depend on it        */
+  int delta_T;              /* 1: diffuse only T - T_hat, the deviation from the */
+                            /* well-balancing background's temperature         */
+                            /* P_hat / ((gamma-1) rho_hat cv) (Sect. 2.10); K  */
+                            /* stays that of the full T; needs a background    */
 } phl_diffusion;
 
 /* Advance rho d(e_int)/dt = div(K grad T) over dt with the density,

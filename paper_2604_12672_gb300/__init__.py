@@ -53,7 +53,7 @@ class GridDesc(C.Structure):
 
 class Diffusion(C.Structure):
     _fields_ = [("k0", C.c_double), ("nT", C.c_int), ("nR", C.c_int), ("cv", C.c_double),
-                ("precision", C.c_int), ("tile_z", C.c_int)]
+                ("precision", C.c_int), ("tile_z", C.c_int), ("delta_T", C.c_int)]
 
 
 DIFF_PRECISION = {"grid": 0, "fp64": 1, "mixed": 2}
@@ -539,13 +539,13 @@ class Grid:
     def set_timing(self, on=True):
         _check(lib().phl_set_timing(self.h, int(bool(on))))
 
-    def diffuse(self, dt, k0, nT=0, nR=0, cv=1.5, max_stages=100000, precision="grid", tile_z=0):
+    def diffuse(self, dt, k0, nT=0, nR=0, cv=1.5, max_stages=100000, precision="grid", tile_z=0, delta_T=False):
         """One RKL2 thermal-diffusion super step of length dt (phl_diffuse);
         precision "grid" (the grid's mode), "fp64" or "mixed"; tile_z: planes
         per CTA of the mixed stage kernel (0: default); returns the number of
         stages."""
         p = Diffusion(k0=float(k0), nT=int(nT), nR=int(nR), cv=float(cv),
-                      precision=DIFF_PRECISION[precision], tile_z=int(tile_z))
+                      precision=DIFF_PRECISION[precision], tile_z=int(tile_z), delta_T=int(bool(delta_T)))
         ns = C.c_int(0)
         _check(lib().phl_diffuse(self.h, C.byref(p), float(dt), int(max_stages), C.byref(ns)))
         return ns.value

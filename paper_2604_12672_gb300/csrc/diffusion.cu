@@ -45,12 +45,20 @@ constexpr int NRED = 4;   // reductions: parabolic rate, max e_int, max k0/rho^n
 
 struct DiffArrays {       // FP64 form
   double *irho, *krho, *Y0, *L0, *Y[3];
+  const double *That;     // background temperature per z layer (null: the full temperature)
 };
 
 struct DiffMx {           // mixed form
   double *Y0d;            // e_int^(0) (set-up only)
   float *y0, *kp, *a, *l0, *g[3], *d[3];
+  const double *That;
 };
+
+// the background temperature P_hat / ((gamma - 1) rho_hat c_v) of each z layer
+__global__ void k_diff_that(DevGeo G, double cv, double *That) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < G.n[2]; k += gridDim.x * blockDim.x)
+    That[k] = G.bg_p_c[k + BG_NG] / ((G.gamma - 1.0) * G.bg_rho_c[k + BG_NG] * cv);
+}
 
 struct Stencil {          // interior cells, dense, x fastest
   int n[3], act[3], per[3];
@@ -174,7 +182,9 @@ __device__ __forceinline__ double diff_op(const DevGeo &G, const phl_diffusion &
       const long qn = q + (long)(x - c[d]) * st[d];
       const double Tn = Y[qn] * icv;
       const double Kn = A.krho[qn] * powi_dev(Tn, p.nT);
-      fsum += hmean(Kc, Kn) * ((Tn - Tc) * G.idx[d]);
+      double dT = Tn - Tc;
+      if (d == 2 && A.That) dT -= A.That[x] - A.That[c[2]];   // the deviation from the background
+      fsum += hmean(Kc, Kn) * (dT * G.idx[d]);
     }
     s += fsum * G.idx[d];
   }
@@ -218,7 +228,8 @@ __global__ void k_diff_finish(DevGeo G, Box box, DiffArrays A, const double *__r
 // kp = k0/rho^nR (2^eY / c_v)^nT 2^-eK (so K = 2^eK kp y^nT), a = 1/(rho c_v)
 // 2^-ea, and the upper-face differences of y0 (FP64 difference, then
 // rounded; zero on a non-periodic upper side, where no flux passes).
-__global__ void k_dmx_prep(DevGeo G, Box box, Stencil S, DiffMx M, double kt, int eK, int eY, float asc) {
+__global__ void k_dmx_prep(DevGeo G, Box box, Stencil S, DiffMx M, double kt, int eK, int eY, float asc,
+                           double cv) {
   int c[3];
   if (!cell3(box, c)) return;
   const long q = dense(G, c);
@@ -227,8 +238,14 @@ __global__ void k_dmx_prep(DevGeo G, Box box, Stencil S, DiffMx M, double kt, in
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (!S.act[d]) continue;
-    if (c[d] + 1 < S.n[d]) gd[d] = d2f_scaled(M.Y0d[q + S.st[d]] - Y, -eY);
-    else if (S.per[d]) gd[d] = d2f_scaled(M.Y0d[q - (long)(S.n[d] - 1) * S.st[d]] - Y, -eY);
+    int up = -1;
+    if (c[d] + 1 < S.n[d]) up = c[d] + 1;
+    else if (S.per[d]) up = 0;
+    if (up < 0) continue;
+    double dY = M.Y0d[q + (long)(up - c[d]) * S.st[d]] - Y;
+    // diffusing the deviation from the background: its (fixed) step moves into g
+    if (d == 2 && M.That) dY -= cv * (M.That[up] - M.That[c[2]]);
+    gd[d] = d2f_scaled(dY, -eY);
   }
   M.y0[q] = d2f_scaled(Y, -eY);
   M.kp[q] = d2f_scaled((double)M.kp[q] * kt, -eK);
@@ -495,6 +512,8 @@ cudaError_t launch_diffuse(const DevGeo &G, double *U, const double *Bf, const p
   unsigned long long *red = (unsigned long long *)(scratch + 7 * nc);
   DiffArrays A{};
   DiffMx M{};
+  A.That = nullptr;
+  M.That = nullptr;
   if (mixed) {   // e_int^(0) in double, then ten float arrays: 6 doubles per cell
     M.Y0d = scratch;
     float *f = (float *)(scratch + nc);
@@ -515,6 +534,12 @@ cudaError_t launch_diffuse(const DevGeo &G, double *U, const double *Bf, const p
   Box b = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
   cudaError_t e = cudaMemsetAsync(red, 0, NRED * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  if (p.delta_T) {   // the background temperature per layer, after the reduction words
+    double *That = scratch + 7 * nc + 8;
+    k_diff_that<<<(G.n[2] + 255) / 256, 256, 0, s>>>(G, p.cv, That);
+    A.That = That;
+    M.That = That;
+  }
   if (mixed)
     k_diff_init<true><<<grid3(b), block3(b), 0, s>>>(G, b, U, Bf, p, icv, A, M, red, dflag);
   else
@@ -571,7 +596,7 @@ cudaError_t launch_diffuse(const DevGeo &G, double *U, const double *Bf, const p
   S.st[0] = 1;
   S.st[1] = G.n[0];
   S.st[2] = (long)G.n[0] * G.n[1];
-  k_dmx_prep<<<grid3(b), block3(b), 0, s>>>(G, b, S, M, kt, eK, eY, (float)std::ldexp(1.0, -ea));
+  k_dmx_prep<<<grid3(b), block3(b), 0, s>>>(G, b, S, M, kt, eK, eY, (float)std::ldexp(1.0, -ea), p.cv);
   // dt M = 2^(eY + eK + ea + ew) dt lambda: the stage factors carry the scales
   const double sc = std::ldexp(dt, eK + ea + ew);
   const int tz = p.tile_z > 0 ? p.tile_z : DTZ_DEFAULT;

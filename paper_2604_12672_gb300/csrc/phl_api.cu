@@ -689,11 +689,13 @@ phl_status phl_diffuse(phl_grid *g, const phl_diffusion *p, double dt, int max_s
   if (g->G.eos != PHL_EOS_IDEAL) return fail(PHL_EUNSUPPORTED, "thermal diffusion is built for the ideal gas");
   if (!(p->k0 >= 0.0) || !(p->cv > 0.0) || p->nT < 0 || p->nT > 4 || p->nR < 0 || p->nR > 2 || !(dt > 0.0) ||
       max_stages < 3 || p->precision < PHL_DIFF_GRID || p->precision > PHL_DIFF_MIXED || p->tile_z < 0 ||
-      p->tile_z > 4096)
+      p->tile_z > 4096 || (p->delta_T != 0 && p->delta_T != 1))
     return fail(PHL_EINVAL, "bad diffusion parameters");
+  if (p->delta_T && !g->G.bg_rho_c)
+    return fail(PHL_EINVAL, "diffusing the deviation from the background temperature needs a background");
   if (!g->diff) {
     const long nc = (long)g->G.n[0] * g->G.n[1] * g->G.n[2];
-    phl_status st = dalloc(g, &g->diff, (size_t)7 * nc + 8);
+    phl_status st = dalloc(g, &g->diff, (size_t)7 * nc + 8 + (size_t)g->G.n[2]);
     if (st != PHL_OK) return st;
   }
   const bool mixed = p->precision == PHL_DIFF_MIXED || (p->precision == PHL_DIFF_GRID && g->mixed);

@@ -165,3 +165,28 @@ def test_full_size_mixed_against_oracle(P):
     ref, no = run_oracle(pr, 1, dt, k0=k0, nT=3, nR=1, cv=cv, max_stages=1000)
     assert [ns] == no and ns >= 15
     check_mixed(pr, st, ref)
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_delta_T_option_matches_oracle(P, form):
+    """Sect. 2.10's option: diffusing only the deviation from the background
+    temperature (radiative K of the full temperature) on the stratified box;
+    a grid without a background rejects it."""
+    pr = W.stratified_box(20, 17, 24, amp=3e-2, beta=1e3, mach_heat=3e-2)
+    kw = dict(k0=2e-3, nT=3, nR=1, cv=1.0 / (pr.gamma - 1.0), delta_T=True)
+    st, ng = run_gpu(P, pr, 2, 1e-3, form, "grid", **kw)
+    ref, no = run_oracle(pr, 2, 1e-3, **kw)
+    assert ng == no
+    dE, dR = st["cons"][4] - pr.cons[4], ref["cons"][4] - pr.cons[4]
+    assert np.abs(dR).max() > 1e-7 * np.abs(pr.cons[4]).max()
+    if form == "fp64":
+        check_fp64(pr, st, ref)
+        assert np.abs(dE - dR).max() <= 1e-9 * np.abs(dR).max()
+    else:
+        check_mixed(pr, st, ref)
+    q, _, _ = pulse(16)
+    g = P.Grid(q)
+    g.load()
+    with pytest.raises(P.PhlError):
+        g.diffuse(0.1, 1e-2, cv=1.5, delta_T=True)
+    g.close()
