@@ -44,12 +44,12 @@ STAGES = 3
 HBM_FALLBACK_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (profiling recipe's nominal table)
 
-# Algorithmic work per unit, stated in DESIGN.md (section "Roofline figures").
+# Algorithmic work per unit.
 # Bytes of one stage per cell that any implementation must move: read the stage
 # input (5 cell + 3 face doubles), read U^n for stages 2-3, write the output.
 BYTES_PER_CELL_STAGE = {1: 128.0, 2: 192.0, 3: 192.0}
 # FP64 flux kernel: FP64 operations per face (DADD + DMUL + 2 DFMA counted from
-# the ncu SASS counters of k_flux on the stratified box; see DESIGN.md).
+# the ncu SASS counters of k_flux on the stratified box).
 FP64_FLOP_PER_FACE = 807.0
 # Mixed flux kernel: FP32 operations per face (FADD + FMUL + 2 FFMA from the ncu
 # SASS counters of k_flux<0/1/2, float> on the stratified box at 160^3, per sweep

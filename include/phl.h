@@ -354,7 +354,7 @@ phl_status phl_eos(const phl_eos_table *t, long n, const double *rho, const doub
 
 /* ---------------------------------------------------------------------------
  * Temperature-guess network for the EOS inversion (not in the paper; the
- * Newton iteration of Sect. 2.2 stays the judge of the converged T).
+ * Newton iteration of Sect. 2.2 alone decides the converged T).
  * y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3 with 3 inputs, two hidden layers
  * of PHL_MLP_HIDDEN units, one output.  Inputs x = ((log10 rho - c0) s0,
  * (log10 e_int - c1) s1, (X_0 - c2) s2), X_0 the first species' mass

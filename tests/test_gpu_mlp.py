@@ -134,7 +134,7 @@ def test_network_guess_saves_newton_iterations(P, table, trained):
     r_mlp = P.eos(table, rho, e, abar, ye, g_mlp)
     r_cold = P.eos(table, rho, e, abar, ye, cold)
     assert (r_mlp["iters"] > 0).all() and (r_cold["iters"] > 0).all()
-    # the judge: the converged temperature does not depend on the guess, to
+    # the criterion: the converged temperature does not depend on the guess, to
     # 1e-12 or the rounding floor of e amplified by e / (c_v T) (degenerate
     # electrons), whichever is larger
     assert (np.abs(r_mlp["T"] / r_cold["T"] - 1) <= np.maximum(1e-12, 2e-14 * cond)).all()

@@ -1,6 +1,6 @@
 """FP64 CUDA path vs the CPU oracle, element by element.
 
-Bar (benchmark spec): relative L-infinity error per field <= 1e-11,
+Bar: relative L-infinity error per field <= 1e-11,
     max |gpu - oracle| / max |oracle|
 for every conserved variable and every face-field component, after the
 stated number of steps.  Both sides compute their own CFL steps from their own
