@@ -17,8 +17,8 @@
  * f_xy (x = ln n, y = ln T), and interpolated with bicubic Hermite
  * polynomials; P, e, c_v and dP/drho, dP/dT all follow from that one
  * interpolant, so the thermodynamic identities hold to round-off (the paper's
- * Helmholtz table uses biquintic Hermite of the free energy; this
- * table is the build's own, from the integrals above).
+ * Helmholtz table interpolates the free energy biquintically, Sect. 2.2; this
+ * table is computed here from the integrals above).
  *
  * Temperature from e_int: Newton T <- T + (e - e_EoS) / c_v until
  * |de|/e < tol (Sect. 2.2), then one more Newton step; steps are kept inside
