@@ -222,9 +222,11 @@ typedef struct {
  * steps (e.g. Strang splitting: half dt, phl_step, half dt).  The first call
  * allocates the grid's diffusion arrays (seven doubles per cell).
  *   max_stages: PHL_EINVAL when N_STS would exceed it; *nsts_out (nullable)
- *   receives N_STS.  PHL_EUNSUPPORTED for the stellar EOS.  A cell with
- *   rho <= 0 or e_int <= 0 sets the device flag (PHL_ENEGATIVE at the next
- *   synchronising call). */
+ *   receives N_STS.  PHL_EINVAL also for bad parameters and for delta_T on a
+ *   grid without a background; PHL_EUNSUPPORTED for the stellar EOS and for
+ *   the mixed form on 2^32 cells or more.  A cell with rho <= 0 or
+ *   e_int <= 0 sets the device flag (PHL_ENEGATIVE at the next synchronising
+ *   call). */
 phl_status phl_diffuse(phl_grid *g, const phl_diffusion *p, double dt, int max_stages, int *nsts_out);
 
 /* Selects how a mixed-precision grid evaluates a stage (Sects. 2.4-2.9; the

@@ -16,13 +16,17 @@
 // rounded) and, for K, as a float; since e_int^(m) = e_int^(0) + d^(m) 2^eY
 // the paper's stage formula becomes
 //   d^(m) = mu_m d^(m-1) + nu_m d^(m-2) + mu~_m dt M[.] + gamma~_m dt M[0]
-// (the (1 - mu - nu) e_int^(0) term cancels).  Power-of-two scales (eY for
+// (the (1 - mu - nu) e_int^(0) term cancels).  With delta_T the operator acts
+// on T - T_hat (Sect. 2.10's option): the FP64 form subtracts T_hat's step on
+// z faces, the mixed form folds it into the face differences of e_int^(0).
+// Power-of-two scales (eY for
 // e_int, eK for K, ea for 1/(rho c_v), ew for 1/dx^2, from maxima reduced at
 // the start) keep every float O(1); the stage factors absorb them.  The
 // stage kernel then moves 40 bytes per cell and does no FP64 arithmetic.
 //
 // Layout: the grid's own diffusion arrays, dense over the interior cells (x
-// fastest), 7 doubles per cell plus a tail of 8 for the reductions.  FP64:
+// fastest), 7 doubles per cell, then 8 words for the reductions and one
+// double per z layer (the background temperature of the delta_T option).  FP64:
 // 1/rho, k0/rho^nR, e_int^(0), the operator at e_int^(0), three stage
 // buffers.  Mixed: e_int^(0) in double (set-up only), then as floats
 // y0 = e_int^(0)/2^eY, the scaled conductivity factor, 1/(rho c_v), the
