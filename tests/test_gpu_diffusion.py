@@ -190,3 +190,25 @@ def test_delta_T_option_matches_oracle(P, form):
     with pytest.raises(P.PhlError):
         g.diffuse(0.1, 1e-2, cv=1.5, delta_T=True)
     g.close()
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_one_dimensional_row(P, form, bc):
+    """Edge case: a 1-D row (ny = nz = 1; the mixed stage kernel's 32 x 8 tile
+    keeps one active row), periodic or walled, against the oracle."""
+    n, cv, k0 = 77, 1.5, 1e-2
+    x = (np.arange(n) + 0.5) / n - 0.5
+    T = 1.0 + 0.5 * np.exp(-x ** 2 / 0.01)
+    z = np.zeros((1, 1, n))
+    pr = W._assemble("row", 1, (n, 1, 1), (-0.5, 0.0, 0.0), (0.5, 1.0, 1.0), ((bc, bc), (0, 0), (0, 0)),
+                     1.0 + 1.0 / cv, np.ones((1, 1, n)), [z, z, z], T[None, None, :],
+                     np.zeros((1, 1, n + 1)), np.zeros((1, 2, n)), np.zeros((2, 1, n)),
+                     eint_density=cv * T[None, None, :])
+    st, ng = run_gpu(P, pr, 2, 2e-3, form, "grid", k0=k0, cv=cv)
+    ref, no = run_oracle(pr, 2, 2e-3, k0=k0, cv=cv)
+    assert ng == no and min(ng) > 3
+    if form == "fp64":
+        check_fp64(pr, st, ref)
+    else:
+        check_mixed(pr, st, ref)

@@ -154,3 +154,20 @@ def test_full_size_sphere(P):
         x, y, z = cell_grid(xf)
         errs.append(np.abs(phi - sphere_phi(np.sqrt(x * x + y * y + z * z))).mean())
     assert np.log2(errs[0] / errs[1]) > 1.8, errs
+
+
+@pytest.mark.parametrize("n", [(2, 2, 2), (3, 2, 5), (40, 3, 2)])
+def test_small_and_anisotropic_grids(P, n):
+    """Edge cases: the smallest grid (two cells per axis) and flat or needle
+    shapes, stretched, octupole boundary values, against the oracle."""
+    xf = [W.random_faces(m, 40 + i) for i, m in enumerate(n)]
+    rho = W.lumpy_density(xf, seed=41)
+    kw = dict(G=1.0, lmax=3, criterion="relative", tol=1e-12, max_iter=500)
+    ref, gh_ref, _, _, st = O.Poisson(xf, **kw).solve(rho)
+    assert st == 0
+    S = P.Poisson(xf, **kw)
+    phi, it, res = S.solve(rho)
+    assert res < 1e-12
+    assert np.abs(phi - ref).max() <= 1e-9 * np.abs(ref).max()
+    assert np.abs(S.ghost() - gh_ref).max() <= 1e-13 * np.abs(gh_ref).max()
+    S.close()
