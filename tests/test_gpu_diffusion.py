@@ -205,8 +205,8 @@ def test_one_dimensional_row(P, form, bc):
                      1.0 + 1.0 / cv, np.ones((1, 1, n)), [z, z, z], T[None, None, :],
                      np.zeros((1, 1, n + 1)), np.zeros((1, 2, n)), np.zeros((2, 1, n)),
                      eint_density=cv * T[None, None, :])
-    st, ng = run_gpu(P, pr, 2, 2e-3, form, "grid", k0=k0, cv=cv)
-    ref, no = run_oracle(pr, 2, 2e-3, k0=k0, cv=cv)
+    st, ng = run_gpu(P, pr, 2, 0.1, form, "grid", k0=k0, cv=cv)     # 6 stages per step
+    ref, no = run_oracle(pr, 2, 0.1, k0=k0, cv=cv)
     assert ng == no and min(ng) > 3
     if form == "fp64":
         check_fp64(pr, st, ref)
