@@ -187,3 +187,20 @@ def test_sphere_potential_converges_at_second_order():
     gorder = np.log2(np.array(gerrs[:-1]) / np.array(gerrs[1:]))
     assert order[-1] > 1.8 and gorder[-1] > 1.5, (errs, order, gerrs, gorder)
     assert errs[-1] < 1e-3 * abs(sphere_phi(np.array(0.0)))
+
+
+def test_sphere_mass_converges_to_the_printed_closed_form():
+    """The monopole of the paper's sphere: the cell masses rho V sum to
+    M = 32 pi rho0 r0^3 / 105 (the closed form the paper prints with Eq.
+    coll1), at second order on the stretched grid (midpoint rule), with the
+    centre of mass at the origin and vanishing octupole by symmetry."""
+    M_exact = 32 * np.pi * 1.0 * 0.25 ** 3 / 105
+    errs = []
+    for n in (16, 32, 64):
+        xf = [W.stretched_faces(n)] * 3
+        M, X, Q, Oc = O.Poisson(xf).moments(W.sphere_density(xf))
+        errs.append(abs(M - M_exact) / M_exact)
+        assert np.abs(X).max() < 1e-15
+        assert np.abs(Oc).max() < 1e-15 * M
+    order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[-1] < 2e-3 and np.all(order > 1.8), (errs, order)
