@@ -216,11 +216,11 @@ typedef struct {
  * parabolic limit dt_p = 1/2 [max sum_s D/dx_s^2]^-1, D = K/(rho cv), of the
  * state at the start of the step: the call reads that maximum back (one
  * synchronisation of the grid's stream) and then enqueues the stage kernels
- * (N_STS + 1 in FP64, N_STS + 2 mixed).  Space: conservative seven-point
+ * (3 N_STS + 2 in FP64, N_STS + 2 mixed).  Space: conservative seven-point
  * operator, face conductivity the harmonic mean of the two cells' (Sect.
  * 2.10), no flux through sides that are not periodic.  Call between MHD
  * steps (e.g. Strang splitting: half dt, phl_step, half dt).  The first call
- * allocates the grid's diffusion arrays (seven doubles per cell).
+ * allocates the grid's diffusion arrays (eleven doubles per cell).
  *   max_stages: PHL_EINVAL when N_STS would exceed it; *nsts_out (nullable)
  *   receives N_STS.  PHL_EINVAL also for bad parameters and for delta_T on a
  *   grid without a background; PHL_EUNSUPPORTED for the stellar EOS and for

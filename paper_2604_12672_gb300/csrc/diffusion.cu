@@ -25,8 +25,9 @@
 // stage kernel then moves 40 bytes per cell and does no FP64 arithmetic.
 //
 // Layout: the grid's own diffusion arrays, dense over the interior cells (x
-// fastest), 7 doubles per cell, then 8 words for the reductions and one
-// double per z layer (the background temperature of the delta_T option).  FP64:
+// fastest), 7 doubles per cell, then 8 words for the reductions, one double
+// per z layer (the background temperature of the delta_T option), and 4
+// doubles per cell for the FP64 form's K and face fluxes.  FP64:
 // 1/rho, k0/rho^nR, e_int^(0), the operator at e_int^(0), three stage
 // buffers.  Mixed: e_int^(0) in double (set-up only), then as floats
 // y0 = e_int^(0)/2^eY, the scaled conductivity factor, 1/(rho c_v), the
@@ -163,58 +164,75 @@ __device__ __forceinline__ double hmean(double a, double b) {
   return s > 0.0 ? 2.0 * a * b / s : 0.0;
 }
 
-// div(K grad T(Y)) / rho at interior cell c from the seven-point stencil.
-__device__ __forceinline__ double diff_op(const DevGeo &G, const phl_diffusion &p, double icv,
-                                          const DiffArrays &A, const double *__restrict__ Y, const int *c,
-                                          long q) {
-  const double Tc = Y[q] * icv;
-  const double Kc = A.krho[q] * powi_dev(Tc, p.nT);
+// The FP64 operator in three passes per stage, so that each cell's K and
+// each face's harmonic mean (an FP64 division) are evaluated once: the FP64
+// pipe (1/64 of the FP32 rate on GB300) bounds this form.
+//   k_diff_k:     K = k0/rho^nR (Y / c_v)^nT of every cell
+//   k_diff_faces: F_d = hm(K_c, K_up) (T_up - T_c [- the background step]) / dx_d
+//                 at the upper d-face of every cell (zero on a non-periodic side)
+//   k_diff_comb:  L = sum_d (F_d(upper) - F_d(lower)) / dx_d / rho, then the
+//                 RKL2 stage combination
+__global__ void k_diff_k(DevGeo G, Box box, phl_diffusion p, double icv, DiffArrays A, const double *__restrict__ Y,
+                         double *__restrict__ K) {
+  int c[3];
+  if (!cell3(box, c)) return;
+  const long q = dense(G, c);
+  K[q] = A.krho[q] * powi_dev(Y[q] * icv, p.nT);
+}
+
+__global__ void k_diff_faces(DevGeo G, Box box, double icv, DiffArrays A, const double *__restrict__ Y,
+                             const double *__restrict__ K, double *__restrict__ F0, double *__restrict__ F1,
+                             double *__restrict__ F2) {
+  int c[3];
+  if (!cell3(box, c)) return;
+  const long q = dense(G, c);
   const long st[3] = {1L, (long)G.n[0], (long)G.n[0] * G.n[1]};
+  double *F[3] = {F0, F1, F2};
+  const double Tc = Y[q] * icv, Kc = K[q];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (!G.act[d]) continue;
+    int x = c[d] + 1;
+    double f = 0.0;   // no flux through a wall or an outflow side
+    if (x < G.n[d] || G.bc[d][0] == PHL_PERIODIC) {
+      if (x == G.n[d]) x = 0;
+      const long qn = q + (long)(x - c[d]) * st[d];
+      double dT = Y[qn] * icv - Tc;
+      if (d == 2 && A.That) dT -= A.That[x] - A.That[c[2]];   // the deviation from the background
+      f = hmean(Kc, K[qn]) * (dT * G.idx[d]);
+    }
+    F[d][q] = f;
+  }
+}
+
+// FIRST: L0 = the operator at e_int^(0) (stored), Y1 = Y0 + mu~_1 dt L0;
+// else Y_j = mu Y_{j-1} + nu Y_{j-2} + (1 - mu - nu) Y0 + mu~ dt L(Y_{j-1}) + gamma~ dt L0
+template <bool FIRST>
+__global__ void k_diff_comb(DevGeo G, Box box, DiffArrays A, const double *__restrict__ F0,
+                            const double *__restrict__ F1, const double *__restrict__ F2, double mu, double nu,
+                            double mdt, double gdt, const double *__restrict__ Ym1, const double *__restrict__ Ym2,
+                            double *__restrict__ Yj) {
+  int c[3];
+  if (!cell3(box, c)) return;
+  const long q = dense(G, c);
+  const long st[3] = {1L, (long)G.n[0], (long)G.n[0] * G.n[1]};
+  const double *F[3] = {F0, F1, F2};
   double s = 0.0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (!G.act[d]) continue;
-    const bool per = G.bc[d][0] == PHL_PERIODIC;
-    double fsum = 0.0;   // (K grad T) at the upper face minus at the lower face
-#pragma unroll
-    for (int side = -1; side <= 1; side += 2) {
-      int x = c[d] + side;
-      if (x < 0 || x >= G.n[d]) {
-        if (!per) continue;   // no flux through a wall or an outflow side
-        x = x < 0 ? x + G.n[d] : x - G.n[d];
-      }
-      const long qn = q + (long)(x - c[d]) * st[d];
-      const double Tn = Y[qn] * icv;
-      const double Kn = A.krho[qn] * powi_dev(Tn, p.nT);
-      double dT = Tn - Tc;
-      if (d == 2 && A.That) dT -= A.That[x] - A.That[c[2]];   // the deviation from the background
-      fsum += hmean(Kc, Kn) * (dT * G.idx[d]);
-    }
-    s += fsum * G.idx[d];
+    double low = 0.0;   // the lower face's flux (zero on a non-periodic side)
+    if (c[d] > 0) low = F[d][q - st[d]];
+    else if (G.bc[d][0] == PHL_PERIODIC) low = F[d][q + (long)(G.n[d] - 1) * st[d]];
+    s += (-low + F[d][q]) * G.idx[d];
   }
-  return s * A.irho[q];
-}
-
-// L0 = operator at e_int^(0); stage 1: Y1 = Y0 + mu~_1 dt L0
-__global__ void k_diff_first(DevGeo G, Box box, phl_diffusion p, double icv, DiffArrays A, double mdt,
-                             double *__restrict__ Y1) {
-  int c[3];
-  if (!cell3(box, c)) return;
-  const long q = dense(G, c);
-  const double L0 = diff_op(G, p, icv, A, A.Y0, c, q);
-  A.L0[q] = L0;
-  Y1[q] = A.Y0[q] + mdt * L0;
-}
-
-// stage j: Y_j = mu Y_{j-1} + nu Y_{j-2} + (1 - mu - nu) Y0 + mu~ dt L(Y_{j-1}) + gamma~ dt L0
-__global__ void k_diff_stage(DevGeo G, Box box, phl_diffusion p, double icv, DiffArrays A, double mu, double nu,
-                             double mdt, double gdt, const double *__restrict__ Ym1, const double *__restrict__ Ym2,
-                             double *__restrict__ Yj) {
-  int c[3];
-  if (!cell3(box, c)) return;
-  const long q = dense(G, c);
-  const double L = diff_op(G, p, icv, A, Ym1, c, q);
-  Yj[q] = mu * Ym1[q] + nu * Ym2[q] + (1.0 - mu - nu) * A.Y0[q] + mdt * L + gdt * A.L0[q];
+  const double L = s * A.irho[q];
+  if (FIRST) {
+    A.L0[q] = L;
+    Yj[q] = A.Y0[q] + mdt * L;
+  } else {
+    Yj[q] = mu * Ym1[q] + nu * Ym2[q] + (1.0 - mu - nu) * A.Y0[q] + mdt * L + gdt * A.L0[q];
+  }
 }
 
 // E += rho (e_int^(N) - e_int^(0))
@@ -564,20 +582,30 @@ cudaError_t launch_diffuse(const DevGeo &G, double *U, const double *Bf, const p
   rkl2_coeffs(ns, mu.data(), nu.data(), mut.data(), gat.data());
 
   if (!mixed) {
-    k_diff_first<<<grid3(b), block3(b), 0, s>>>(G, b, p, icv, A, mut[1] * dt, A.Y[1]);
+    // K and the three face-flux arrays after the background temperatures
+    double *K = scratch + 7 * nc + 8 + G.n[2];
+    double *F0 = K + nc, *F1 = K + 2 * nc, *F2 = K + 3 * nc;
+    auto op = [&](const double *Y) {
+      k_diff_k<<<grid3(b), block3(b), 0, s>>>(G, b, p, icv, A, Y, K);
+      k_diff_faces<<<grid3(b), block3(b), 0, s>>>(G, b, icv, A, Y, K, F0, F1, F2);
+    };
+    op(A.Y0);
+    k_diff_comb<true><<<grid3(b), block3(b), 0, s>>>(G, b, A, F0, F1, F2, 0.0, 0.0, mut[1] * dt, 0.0, nullptr, nullptr,
+                                                      A.Y[1]);
     const double *ym2 = A.Y0, *ym1 = A.Y[1];
     int slot = 2;
     for (int j = 2; j <= ns; ++j) {
       double *yj = A.Y[slot];
-      k_diff_stage<<<grid3(b), block3(b), 0, s>>>(G, b, p, icv, A, mu[j], nu[j], mut[j] * dt, gat[j] * dt, ym1, ym2,
-                                                  yj);
+      op(ym1);
+      k_diff_comb<false><<<grid3(b), block3(b), 0, s>>>(G, b, A, F0, F1, F2, mu[j], nu[j], mut[j] * dt, gat[j] * dt,
+                                                         ym1, ym2, yj);
       ym2 = ym1;
       ym1 = yj;
       slot = (slot + 1) % 3;
       if (A.Y[slot] == ym1 || A.Y[slot] == ym2) slot = (slot + 1) % 3;
     }
     k_diff_finish<<<grid3(b), block3(b), 0, s>>>(G, b, A, ym1, U);
-    if (nlaunch) *nlaunch = ns + 2;
+    if (nlaunch) *nlaunch = 3 * ns + 2;
     return cudaGetLastError();
   }
 

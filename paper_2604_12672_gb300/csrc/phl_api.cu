@@ -695,7 +695,7 @@ phl_status phl_diffuse(phl_grid *g, const phl_diffusion *p, double dt, int max_s
     return fail(PHL_EINVAL, "diffusing the deviation from the background temperature needs a background");
   if (!g->diff) {
     const long nc = (long)g->G.n[0] * g->G.n[1] * g->G.n[2];
-    phl_status st = dalloc(g, &g->diff, (size_t)7 * nc + 8 + (size_t)g->G.n[2]);
+    phl_status st = dalloc(g, &g->diff, (size_t)11 * nc + 8 + (size_t)g->G.n[2]);
     if (st != PHL_OK) return st;
   }
   const bool mixed = p->precision == PHL_DIFF_MIXED || (p->precision == PHL_DIFF_GRID && g->mixed);
