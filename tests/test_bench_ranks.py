@@ -50,3 +50,24 @@ def test_reference_arm_nonzero_rank_exits_without_work(monkeypatch):
     class Args:
         gpus, steps, warmup, n = 2, 1, 0, 8
     assert bench.run_reference(Args()) == 0
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """Rank 0 of the reference arm times the oracle on a bounded sample and
+    prints one JSON line with the contract's keys."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+
+    class Args:
+        gpus, steps, warmup, n = 1, 1, 0, 8
+    assert bench.run_reference(Args()) in (0, None)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    for k in ("metric", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "config"):
+        assert k in line, k
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["e2e"]["value"] == line["value"]
