@@ -330,11 +330,12 @@ __device__ __forceinline__ int wrap_or_out(int x, int n, int per) {
 
 // One stage of the mixed form.  A CTA owns a 32 x 8 column of cells and
 // marches up tz planes of it.  Per plane, (d, k) of the tile and its x/y
-// halo go to shared memory; each face quantity
+// halo go to shared memory (two buffers by plane parity, so one barrier per
+// plane suffices); each cell forms its faces' quantities
 //   G = hm(k_L, k_R) (g_L + d_R - d_L)     (hm: half the harmonic mean)
-// is formed once (the upper x and y faces by their lower cell, the tile's
-// lower boundary faces by the edge threads; z faces in registers, the lower
-// one carried from the plane below), and the cell takes
+// -- a lower face with the same operands in the same order as the
+// neighbour's upper face, so both see the same value (z faces in registers,
+// the lower one carried from the plane below), and takes
 //   lambda = a sum_d w_d (G_upper - G_lower).
 // A face on a non-periodic side is zero.  The loads are software-pipelined:
 // the own slot two planes ahead, everything else one plane ahead, so the
@@ -346,8 +347,7 @@ template <int NT, bool FIRST>
 __global__ void __launch_bounds__(DTX * DTY) k_dmx_stage(Stencil S, DiffMx M, float mu, float nu, float mt, float gt,
                                                         const float *__restrict__ dm1, const float *__restrict__ dm2,
                                                         float *__restrict__ dj, int tz) {
-  __shared__ float sd[DTY + 2][DTX + 2], sk[DTY + 2][DTX + 2];
-  __shared__ float Fx[DTY][DTX + 1], Fy[DTY + 1][DTX];
+  __shared__ float sdb[2][DTY + 2][DTX + 2], skb[2][DTY + 2][DTX + 2];   // double-buffered by plane parity
   const int tx = threadIdx.x % DTX, ty = threadIdx.x / DTX;
   const int nx = S.n[0], ny = S.n[1], nz = S.n[2];
   const int x0 = blockIdx.x * DTX, y0 = blockIdx.y * DTY, z0 = blockIdx.z * tz;
@@ -375,11 +375,11 @@ __global__ void __launch_bounds__(DTX * DTY) k_dmx_stage(Stencil S, DiffMx M, fl
   }
   // in-plane cells below the tile's lower boundary faces (their g), or NOSRC
   unsigned lxsrc = NOSRC, lysrc = NOSRC;
-  if (own && tx == 0 && S.act[0]) {
+  if (own && S.act[0]) {
     const int lx = wrap_or_out(gx - 1, nx, S.per[0]);
     if (lx >= 0) lxsrc = (unsigned)(lx + nx * gy);
   }
-  if (own && ty == 0 && S.act[1]) {
+  if (own && S.act[1]) {
     const int ly = wrap_or_out(gy - 1, ny, S.per[1]);
     if (ly >= 0) lysrc = (unsigned)(gx + nx * ly);
   }
@@ -427,32 +427,31 @@ __global__ void __launch_bounds__(DTX * DTY) k_dmx_stage(Stencil S, DiffMx M, fl
       an = aux_load(z + 1);
     }
     const float cd = oc.d, ck = kval<NT>(oc);
+    float(*sd)[DTX + 2] = sdb[z & 1];
+    float(*sk)[DTX + 2] = skb[z & 1];
     sd[ty + 1][tx + 1] = cd;
     sk[ty + 1][tx + 1] = ck;
     if (threadIdx.x < DHALO) {
       sd[hr][hc] = ac.h.d;
       sk[hr][hc] = kval<NT>(ac.h);
     }
-    __syncthreads();
-    if (own) {
-      if (S.act[0]) {
-        float G = 0.0f;
-        if (gx + 1 < nx || S.per[0]) G = hmean_f(ck, sk[ty + 1][tx + 2]) * (ac.gx + (sd[ty + 1][tx + 2] - cd));
-        Fx[ty][tx + 1] = G;
-        if (tx == 0) Fx[ty][0] = lxsrc != NOSRC ? hmean_f(sk[ty + 1][0], ck) * (ac.glx + (cd - sd[ty + 1][0])) : 0.0f;
-      }
-      if (S.act[1]) {
-        float G = 0.0f;
-        if (gy + 1 < ny || S.per[1]) G = hmean_f(ck, sk[ty + 2][tx + 1]) * (ac.gy + (sd[ty + 2][tx + 1] - cd));
-        Fy[ty + 1][tx] = G;
-        if (ty == 0) Fy[0][tx] = lysrc != NOSRC ? hmean_f(sk[0][tx + 1], ck) * (ac.gly + (cd - sd[0][tx + 1])) : 0.0f;
-      }
-    }
+    // one barrier per plane: the slots alternate between two buffers, and a
+    // thread two planes ahead has passed the barrier every reader reached
     __syncthreads();
     if (own) {
       float s = 0.0f;
-      if (S.act[0]) s += S.w[0] * (Fx[ty][tx + 1] - Fx[ty][tx]);
-      if (S.act[1]) s += S.w[1] * (Fy[ty + 1][tx] - Fy[ty][tx]);
+      if (S.act[0]) {   // each cell forms both its faces (the lower one as its neighbour does)
+        const float up = (gx + 1 < nx || S.per[0])
+                             ? hmean_f(ck, sk[ty + 1][tx + 2]) * (ac.gx + (sd[ty + 1][tx + 2] - cd)) : 0.0f;
+        const float lo = lxsrc != NOSRC ? hmean_f(sk[ty + 1][tx], ck) * (ac.glx + (cd - sd[ty + 1][tx])) : 0.0f;
+        s += S.w[0] * (up - lo);
+      }
+      if (S.act[1]) {
+        const float up = (gy + 1 < ny || S.per[1])
+                             ? hmean_f(ck, sk[ty + 2][tx + 1]) * (ac.gy + (sd[ty + 2][tx + 1] - cd)) : 0.0f;
+        const float lo = lysrc != NOSRC ? hmean_f(sk[ty][tx + 1], ck) * (ac.gly + (cd - sd[ty][tx + 1])) : 0.0f;
+        s += S.w[1] * (up - lo);
+      }
       if (hasz) {
         const bool up = z + 1 < nz || S.per[2];
         const float gzu = up ? hmean_f(ck, kval<NT>(on)) * (ac.gz + (on.d - cd)) : 0.0f;
