@@ -657,7 +657,7 @@ def main():
                     help="time only the Poisson solve (print its object; for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-l1", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-c3", action="store_true", help="skip the stellar-EOS box (mixed + network vs FP64)")
     ap.add_argument("--c3-steps", type=int, default=4)
     ap.add_argument("--no-c4", action="store_true", help="skip the 24-box ensemble")
