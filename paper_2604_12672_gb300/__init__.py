@@ -23,7 +23,7 @@ PRECISION = {"fp64": 0, "mixed": 1, "mixed_x2": 2, "mixed_lr": 3}
 RECON = {"vanleer": 0, "pph": 1, "pqh": 2}
 HOST, DEVICE = 0, 1
 STATUS = {0: "PHL_OK", 1: "PHL_EINVAL", 2: "PHL_ECUDA", 3: "PHL_ENOMEM", 4: "PHL_ENEGATIVE",
-          5: "PHL_ENAN", 6: "PHL_ENEWTON", 7: "PHL_ETIMEOUT", 8: "PHL_EUNSUPPORTED"}
+          5: "PHL_ENAN", 6: "PHL_ENEWTON", 7: "PHL_ETIMEOUT", 8: "PHL_EUNSUPPORTED", 9: "PHL_ENOCONV"}
 
 _dp = C.POINTER(C.c_double)
 
