@@ -660,6 +660,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-c3", action="store_true", help="skip the stellar-EOS box (mixed + network vs FP64)")
     ap.add_argument("--c3-steps", type=int, default=4)
+    ap.add_argument("--c3-only", action="store_true",
+                    help="only the stellar-EOS box (its JSON object alone, for profiling)")
     ap.add_argument("--no-c4", action="store_true", help="skip the 24-box ensemble")
     ap.add_argument("--c4-steps", type=int, default=5)
     args = ap.parse_args()
@@ -682,6 +684,11 @@ def main():
     if args.poisson_only:
         if rank == 0:
             print(json.dumps(poisson_sphere(P, args.n, stream, hbm_peak, peak_kind)))
+        return 0
+    if args.c3_only:
+        c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws)
+        if rank == 0:
+            print(json.dumps(c3))
         return 0
     pr = make_problem(args.n)
     props = torch.cuda.get_device_properties(local)

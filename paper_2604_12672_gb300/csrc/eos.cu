@@ -186,6 +186,10 @@ phl_status phl_eos_table_create(double lrhoye_lo, double lrhoye_hi, int nrho, do
   t->t.y0 = lT_lo * log(10.0);
   t->t.dy = (lT_hi - lT_lo) * log(10.0) / (nT - 1);
   t->t.x0f = (float)t->t.x0; t->t.dxf = (float)t->t.dx; t->t.y0f = (float)t->t.y0; t->t.dyf = (float)t->t.dy;
+  t->t.idx = 1.0 / t->t.dx; t->t.idy = 1.0 / t->t.dy;
+  t->t.idxf = (float)t->t.idx; t->t.idyf = (float)t->t.idy;
+  t->t.Tlo = exp(t->t.y0); t->t.Thi = exp(t->t.y0 + (nT - 1) * t->t.dy);
+  t->t.Tlof = (float)t->t.Tlo; t->t.Thif = (float)t->t.Thi;
   const long nv = 4L * nrho * nT;
   int *fail = nullptr;
   e = cudaMalloc(&t->dv, nv * sizeof(double));

@@ -34,6 +34,10 @@ struct Table {
   const double *v;            // [ny][nx][4]: f, f_x, f_y, f_xy (device)
   const float *vf;            // FP32 copy
   float x0f, dxf, y0f, dyf;
+  double idx, idy;            // 1/dx, 1/dy: the evaluation multiplies (FP64 division
+  float idxf, idyf;           // is a dozen FP64-pipe instructions on this GPU)
+  double Tlo, Thi;            // the table's temperature range, exp(y0) and
+  float Tlof, Thif;           // exp(y0 + (ny - 1) dy), set with the table
 };
 
 struct Mix {                   // composition-derived constants of a cell
@@ -55,8 +59,8 @@ template <typename R> struct XB {
 template <typename R>
 __device__ __forceinline__ XB<R> xbasis(const Table &t, R x) {
   XB<R> X;
-  const R x0 = sizeof(R) == 8 ? (R)t.x0 : (R)t.x0f, dx = sizeof(R) == 8 ? (R)t.dx : (R)t.dxf;
-  const R gx = (x - x0) / dx;
+  const R x0 = sizeof(R) == 8 ? (R)t.x0 : (R)t.x0f, idx = sizeof(R) == 8 ? (R)t.idx : (R)t.idxf;
+  const R gx = (x - x0) * idx;
   X.ok = gx >= R(0) && gx <= R(t.nx - 1);
   int i = X.ok ? (int)gx : 0;
   if (i > t.nx - 2) i = t.nx - 2;
@@ -77,9 +81,10 @@ __device__ __forceinline__ XB<R> xbasis(const Table &t, R x) {
 // what e and c_v need).
 template <typename R, bool FULL = true>
 __device__ __forceinline__ bool table_eval_xb(const Table &t, const XB<R> &X, R y, TV<R> &o) {
-  const R dx = sizeof(R) == 8 ? (R)t.dx : (R)t.dxf;
+  const R dx = sizeof(R) == 8 ? (R)t.dx : (R)t.dxf, idx = sizeof(R) == 8 ? (R)t.idx : (R)t.idxf;
   const R y0 = sizeof(R) == 8 ? (R)t.y0 : (R)t.y0f, dy = sizeof(R) == 8 ? (R)t.dy : (R)t.dyf;
-  const R gy = (y - y0) / dy;
+  const R idy = sizeof(R) == 8 ? (R)t.idy : (R)t.idyf;
+  const R gy = (y - y0) * idy;
   if (!(X.ok && gy >= R(0) && gy <= R(t.ny - 1))) return false;
   const int i = X.i;
   int j = (int)gy;
@@ -111,11 +116,11 @@ __device__ __forceinline__ bool table_eval_xb(const Table &t, const XB<R> &X, R 
       }
     }
   o.f = a0;
-  o.fx = a1 / dx;
-  o.fy = a2 / dy;
-  o.fxx = a3 / (dx * dx);
-  o.fyy = a4 / (dy * dy);
-  o.fxy = a5 / (dx * dy);
+  o.fx = a1 * idx;
+  o.fy = a2 * idy;
+  o.fxx = a3 * (idx * idx);
+  o.fyy = a4 * (idy * idy);
+  o.fxy = a5 * (idx * idy);
   return true;
 }
 
@@ -126,18 +131,19 @@ __device__ __forceinline__ bool table_eval(const Table &t, R x, R y, TV<R> &o) {
 
 template <typename R> struct EosOut { R P, e, cv, Pr, PT, ge, gc; };
 
-// Full EOS at (rho, T) for a mixture with mean mass number abar and Y_e.
+// Full EOS at (rho, T) for a mixture with mean mass number abar and Y_e
+// (irho = 1/rho and iab = 1/abar: fixed during an inversion, formed once).
 template <typename R>
-__device__ __forceinline__ bool eos_rt_xb(const Table &t, const XB<R> &X, R rho, R T, R abar, EosOut<R> &o) {
+__device__ __forceinline__ bool eos_rt_xy(const Table &t, const XB<R> &X, R rho, R irho, R T, R lnT, R iab,
+                                          EosOut<R> &o) {
   TV<R> q;
-  if (!table_eval_xb<R>(t, X, log(T), q)) return false;
-  const R irho = R(1) / rho, iT = R(1) / T;
+  if (!table_eval_xb<R>(t, X, lnT, q)) return false;
+  const R iT = R(1) / T;
   const R Pe = q.fx - q.f;
   const R ee = (q.f - q.fy) * irho;
   const R cve = (q.fy - q.fyy) * irho * iT;
   const R PeT = (q.fxy - q.fy) * iT;
   const R Per = (q.fxx - q.fx) * irho;
-  const R iab = R(1) / abar;
   const R Rg = R(RGAS);
   R aT4, aT3;   // radiation a T^4 and a T^3
   if (sizeof(R) == 8) {
@@ -164,16 +170,15 @@ __device__ __forceinline__ bool eos_rt_xb(const Table &t, const XB<R> &X, R rho,
 
 template <typename R>
 __device__ __forceinline__ bool eos_rt(const Table &t, R rho, R T, R abar, R ye, EosOut<R> &o) {
-  return eos_rt_xb<R>(t, xbasis<R>(t, log(rho * ye * R(NAV))), rho, T, abar, o);
+  return eos_rt_xy<R>(t, xbasis<R>(t, log(rho * ye * R(NAV))), rho, R(1) / rho, T, log(T), R(1) / abar, o);
 }
 
 // Specific internal energy and c_v at (rho, T): what a Newton iteration needs.
 template <typename R>
-__device__ __forceinline__ bool eos_ecv_xb(const Table &t, const XB<R> &X, R rho, R T, R abar, R &e, R &cv) {
+__device__ __forceinline__ bool eos_ecv_xy(const Table &t, const XB<R> &X, R irho, R T, R lnT, R iab, R &e, R &cv) {
   TV<R> q;
-  if (!table_eval_xb<R, false>(t, X, log(T), q)) return false;
-  const R irho = R(1) / rho, iT = R(1) / T;
-  const R iab = R(1) / abar;
+  if (!table_eval_xb<R, false>(t, X, lnT, q)) return false;
+  const R iT = R(1) / T;
   const R Rg = R(RGAS);
   R aT4, aT3;
   if (sizeof(R) == 8) {
@@ -191,7 +196,18 @@ __device__ __forceinline__ bool eos_ecv_xb(const Table &t, const XB<R> &X, R rho
 
 template <typename R>
 __device__ __forceinline__ bool eos_ecv(const Table &t, R rho, R T, R abar, R ye, R &e, R &cv) {
-  return eos_ecv_xb<R>(t, xbasis<R>(t, log(rho * ye * R(NAV))), rho, T, abar, e, cv);
+  return eos_ecv_xy<R>(t, xbasis<R>(t, log(rho * ye * R(NAV))), R(1) / rho, T, log(T), R(1) / abar, e, cv);
+}
+
+// ln Tn from ln T for a Newton step T -> Tn: with d = (Tn - T) / T below
+// 2^-10, ln(1 + d) by its Taylor series to d^4 (truncation below d^5 / 5 <
+// 2e-16, under the rounding of ln T ~ 16..23); otherwise the logarithm.
+// Saves an FP64 logarithm per step once the iteration is close.
+template <typename R>
+__device__ __forceinline__ R next_lnT(R T, R lnT, R Tn) {
+  const R d = (Tn - T) / T;
+  if (!(fabs(d) < R(1.0 / 1024.0))) return log(Tn);
+  return lnT + d * (R(1) - d * (R(0.5) - d * (R(1.0 / 3.0) - d * R(0.25))));
 }
 
 // Newton inversion e_int -> T (Sect. 2.2): T <- T + (e - e_EoS)/c_v until
@@ -199,23 +215,27 @@ __device__ __forceinline__ bool eos_ecv(const Table &t, R rho, R T, R abar, R ye
 // The iterations evaluate only e and c_v; the full EOS (P, gamma_e, gamma_c)
 // is evaluated once, at the final T.  Returns the iteration count or -1.
 template <typename R>
-__device__ __forceinline__ int newton_loop(const Table &t, const XB<R> &X, R rho, R eint, R abar, R &T, R tol,
-                                           int maxit, EosOut<R> &o, bool have, R e0, R cv0) {
-  const R Tlo = exp(R(t.y0)), Thi = exp(R(t.y0 + (t.ny - 1) * t.dy));
+__device__ __forceinline__ int newton_loop(const Table &t, const XB<R> &X, R rho, R irho, R eint, R iab, R &T, R tol,
+                                           int maxit, EosOut<R> &o, bool have, R e0, R cv0, R lnT0) {
+  const R Tlo = sizeof(R) == 8 ? (R)t.Tlo : (R)t.Tlof, Thi = sizeof(R) == 8 ? (R)t.Thi : (R)t.Thif;
   R lo = Tlo, hi = Thi;
   if (!(T > Tlo && T < Thi)) { T = sqrt(Tlo * Thi); have = false; }
+  R lnT = have ? lnT0 : log(T);   // e0, cv0 were evaluated at (T, lnT0)
   for (int it = 1; it <= maxit; ++it) {
     R e = e0, cv = cv0;   // the first iteration may come evaluated
-    if (!(have && it == 1) && !eos_ecv_xb<R>(t, X, rho, T, abar, e, cv)) return -1;
+    if (!(have && it == 1) && !eos_ecv_xy<R>(t, X, irho, T, lnT, iab, e, cv)) return -1;
     const R de = eint - e;
     if (fabs(de) < tol * fabs(eint)) {
-      T = T + de / cv;
-      if (!eos_rt_xb<R>(t, X, rho, T, abar, o)) return -1;
+      const R Tn = T + de / cv;
+      lnT = next_lnT<R>(T, lnT, Tn);
+      T = Tn;
+      if (!eos_rt_xy<R>(t, X, rho, irho, T, lnT, iab, o)) return -1;
       return it;
     }
     if (de > R(0)) lo = T; else hi = T;
     R Tn = T + de / cv;
     if (!(Tn > lo && Tn < hi)) Tn = R(0.5) * (lo + hi);
+    lnT = next_lnT<R>(T, lnT, Tn);
     T = Tn;
   }
   return -1;
@@ -225,20 +245,21 @@ template <typename R>
 __device__ __forceinline__ int eos_invert(const Table &t, R rho, R eint, R abar, R ye, R &T, R tol, int maxit,
                                           EosOut<R> &o) {
   const XB<R> X = xbasis<R>(t, log(rho * ye * R(NAV)));   // rho and Y_e fixed
-  return newton_loop<R>(t, X, rho, eint, abar, T, tol, maxit, o, false, R(0), R(0));
+  return newton_loop<R>(t, X, rho, R(1) / rho, eint, R(1) / abar, T, tol, maxit, o, false, R(0), R(0), R(0));
 }
 
 // The FP32 phase of the mixed inversion: Newton on e and c_v only, until
 // |de|/e < tol or maxit; T keeps the last bracketed iterate.
 __device__ __forceinline__ int newton_fp32(const Table &t, float rho, float eint, float abar, float ye, float &T,
                                            float tol, int maxit) {
-  const float Tlo = expf((float)t.y0), Thi = expf((float)(t.y0 + (t.ny - 1) * t.dy));
+  const float Tlo = t.Tlof, Thi = t.Thif;
   float lo = Tlo, hi = Thi;
   if (!(T > Tlo && T < Thi)) T = sqrtf(Tlo * Thi);
   const XB<float> X = xbasis<float>(t, logf(rho * ye * float(NAV)));
+  const float irho = 1.0f / rho, iab = 1.0f / abar;
   for (int it = 1; it <= maxit; ++it) {
     float e, cv;
-    if (!eos_ecv_xb<float>(t, X, rho, T, abar, e, cv)) return -1;
+    if (!eos_ecv_xy<float>(t, X, irho, T, logf(T), iab, e, cv)) return -1;
     const float de = eint - e;
     if (de > 0.0f) lo = T; else hi = T;
     float Tn = T + de / cv;
@@ -262,16 +283,19 @@ __device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, doub
   // a time step) goes straight to the FP64 iteration: the FP32 phase could
   // only degrade it to FP32's ~1e-6
   const XB<double> X = xbasis<double>(t, log(rho * ye * NAV));
+  const double irho = 1.0 / rho, iab = 1.0 / abar;
   {
-    const double Tlo = exp(t.y0), Thi = exp(t.y0 + (t.ny - 1) * t.dy);
     double e, cv;
-    if (T > Tlo && T < Thi && eos_ecv_xb<double>(t, X, rho, T, abar, e, cv) && fabs(eint - e) < 1e-4 * fabs(eint))
-      return newton_loop<double>(t, X, rho, eint, abar, T, tol, maxit, o, true, e, cv);
+    if (T > t.Tlo && T < t.Thi) {
+      const double lnT = log(T);
+      if (eos_ecv_xy<double>(t, X, irho, T, lnT, iab, e, cv) && fabs(eint - e) < 1e-4 * fabs(eint))
+        return newton_loop<double>(t, X, rho, irho, eint, iab, T, tol, maxit, o, true, e, cv, lnT);
+    }
   }
   float Tf = (float)T;
   const int it32 = newton_fp32(t, (float)rho, (float)eint, (float)abar, (float)ye, Tf, 1e-5f, maxit < 12 ? maxit : 12);
   if (isfinite(Tf) && Tf > 0.0f) T = (double)Tf;
-  const int it64 = newton_loop<double>(t, X, rho, eint, abar, T, tol, maxit, o, false, 0.0, 0.0);
+  const int it64 = newton_loop<double>(t, X, rho, irho, eint, iab, T, tol, maxit, o, false, 0.0, 0.0, 0.0);
   return it64 < 0 ? -1 : it64 + (it32 > 0 ? it32 : 12);
 }
 
