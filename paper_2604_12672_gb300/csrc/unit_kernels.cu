@@ -80,9 +80,10 @@ __global__ void k_convert_batch(long n, const double *x, int k, float *f, double
 }  // namespace
 
 extern "C" phl_status phl_convert_batch(long n, const double *x, int k, float *f, double *back) {
-  if (n < 0 || k <= -800 || k >= 800) return PHL_EINVAL;
+  if (n < 0 || k <= -800 || k >= 800)
+    return (phl_status)set_error(PHL_EINVAL, "phl_convert_batch: n < 0 or scale exponent out of range");
   if (n == 0) return PHL_OK;
-  if (!x || !f || !back) return PHL_EINVAL;
+  if (!x || !f || !back) return (phl_status)set_error(PHL_EINVAL, "phl_convert_batch: null argument");
   char *d = nullptr;
   if (cudaMalloc(&d, n * (2 * sizeof(double) + sizeof(float))) != cudaSuccess) { cudaGetLastError(); return PHL_ENOMEM; }
   double *dx = (double *)d, *db = dx + n;
@@ -100,10 +101,12 @@ extern "C" phl_status phl_convert_batch(long n, const double *x, int k, float *f
 extern "C" phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const double *bn,
                                         const double *bg, int nspec, int solver, double mach_thr,
                                         int precision, double *f) {
-  if (n < 0 || nspec < 0 || nspec > PHL_MAXSPEC || solver < 0 || solver > 2) return PHL_EINVAL;
-  if ((precision == 2 || precision == 3) && nspec != 0) return PHL_EINVAL;
+  if (n < 0 || nspec < 0 || nspec > PHL_MAXSPEC || solver < 0 || solver > 2)
+    return (phl_status)set_error(PHL_EINVAL, "phl_riemann_batch: bad n, nspec or solver");
+  if ((precision == 2 || precision == 3) && nspec != 0)
+    return (phl_status)set_error(PHL_EINVAL, "phl_riemann_batch: the FP32 solvers take no species");
   if (n == 0) return PHL_OK;
-  if (!wl || !wr || !bn || !bg || !f) return PHL_EINVAL;
+  if (!wl || !wr || !bn || !bg || !f) return (phl_status)set_error(PHL_EINVAL, "phl_riemann_batch: null argument");
   const size_t nw = 9 + nspec, nf = 7 + nspec;
   double *d = nullptr;
   const size_t tot = n * (2 * nw + 1 + 4 + nf);

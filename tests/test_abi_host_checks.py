@@ -148,12 +148,18 @@ def test_unit_entry_points_reject_bad_options(P):
     L = P.lib()
     x = np.zeros(4)
     # the conversion's power-of-two scale must stay inside the double range
-    assert L.phl_convert_batch(4, x.ctypes.data, 900, x.ctypes.data, x.ctypes.data) == EINVAL
+    st = L.phl_convert_batch(4, x.ctypes.data, 900, x.ctypes.data, x.ctypes.data)
+    assert status_and_message(P, st) == (EINVAL, "phl_convert_batch: n < 0 or scale exponent out of range")
     assert L.phl_convert_batch(-1, None, 0, None, None) == EINVAL
+    assert status_and_message(P, L.phl_convert_batch(4, None, 0, None, None)) == \
+        (EINVAL, "phl_convert_batch: null argument")
     # unknown solver, species on the FP32 paths, too many species
-    for solver, nspec, prec in ((3, 0, 0), (0, 1, 2), (0, 99, 0)):
-        assert L.phl_riemann_batch(1, x.ctypes.data, x.ctypes.data, x.ctypes.data, x.ctypes.data,
-                                   nspec, solver, 0.6, prec, x.ctypes.data) == EINVAL
+    for solver, nspec, prec, words in ((3, 0, 0, "bad n, nspec or solver"), (0, 1, 2, "take no species"),
+                                       (0, 99, 0, "bad n, nspec or solver")):
+        st = L.phl_riemann_batch(1, x.ctypes.data, x.ctypes.data, x.ctypes.data, x.ctypes.data,
+                                 nspec, solver, 0.6, prec, x.ctypes.data)
+        st, msg = status_and_message(P, st)
+        assert st == EINVAL and words in msg, (solver, nspec, prec, msg)
     # empty batches succeed without touching the device
     assert L.phl_convert_batch(0, None, 0, None, None) == 0
     assert L.phl_riemann_batch(0, None, None, None, None, 0, 0, 0.6, 0, None) == 0
