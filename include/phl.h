@@ -492,7 +492,7 @@ const char *phl_last_error(void);
  * [2][ny][nx], the lower side first: 2 (ny nz + nx nz + nx ny) doubles. */
 enum { PHL_POISSON_RELATIVE = 0, PHL_POISSON_ABSOLUTE = 1 };
 typedef struct {
-  int n[3];                 /* cells per axis, >= 2 each; fewer than 2^32 cells  */
+  int n[3];                 /* cells per axis, >= 2 each; at most 2^32 - 2^24 cells */
   const double *xf[3];      /* host: n[d] + 1 increasing face coordinates (read */
                             /* at creation only)                               */
   double G;                 /* gravitational constant, > 0                      */
@@ -506,7 +506,7 @@ typedef struct phl_poisson phl_poisson;
 
 /* Allocates the solver (12 doubles per cell plus the ghost potentials).
  * PHL_EINVAL (dimensions, faces, lmax, criterion, tol, max_iter, G),
- * PHL_EUNSUPPORTED (2^32 cells or more), PHL_ENOMEM. */
+ * PHL_EUNSUPPORTED (more than 2^32 - 2^24 cells), PHL_ENOMEM. */
 phl_status phl_poisson_create(const phl_poisson_desc *d, phl_poisson **out);
 phl_status phl_poisson_destroy(phl_poisson *p);
 /* phi: in, the initial guess; out, the solution.  *iters (nullable): the

@@ -339,7 +339,7 @@ __device__ __forceinline__ int wrap_or_out(int x, int n, int per) {
 //   lambda = a sum_d w_d (G_upper - G_lower).
 // A face on a non-periodic side is zero.  The loads are software-pipelined:
 // the own slot two planes ahead, everything else one plane ahead, so the
-// two barriers of a plane do not wait on memory.  Indices are 32-bit (the
+// plane's barrier does not wait on memory.  Indices are 32-bit (the
 // caller checks the cell count).  FIRST: d^(m-1) = 0, lambda is the operator
 // at e_int^(0) (stored in l0) and d^(1) = mt lambda; else
 // d^(m) = mu d^(m-1) + nu d^(m-2) + mt lambda + gt l0.

@@ -559,7 +559,10 @@ phl_status phl_poisson_create(const phl_poisson_desc *d, phl_poisson **out) {
       if (!(d->xf[a][i + 1] > d->xf[a][i])) return pfail(PHL_EINVAL, "face coordinates must increase");
     cells *= d->n[a];
   }
-  if (cells >= 4294967295.0) return pfail(PHL_EUNSUPPORTED, "the Poisson solver indexes cells with 32 bits");
+  // 32-bit cell indices; the margin keeps q + (grid stride) of the grid-stride
+  // loops from wrapping past 2^32
+  if (cells > 4294967296.0 - 16777216.0)
+    return pfail(PHL_EUNSUPPORTED, "the Poisson solver indexes cells with 32 bits (at most 2^32 - 2^24 cells)");
   if (!(d->lmax == 0 || d->lmax == 2 || d->lmax == 3)) return pfail(PHL_EINVAL, "lmax must be 0, 2 or 3");
   if (d->criterion != PHL_POISSON_RELATIVE && d->criterion != PHL_POISSON_ABSOLUTE)
     return pfail(PHL_EINVAL, "bad convergence criterion");

@@ -144,6 +144,15 @@ def test_poisson_create_rejects_bad_descriptors(P, name, grid, fields, words):
     assert st == EINVAL and words in msg and not h.value, (name, st, msg)
 
 
+def test_poisson_rejects_grids_beyond_32_bit_indexing(P):
+    # 2^32 - 2^24 cells is the limit (checked before any allocation)
+    xf = [np.linspace(0.0, 1.0, 2049), np.linspace(0.0, 1.0, 2049), np.linspace(0.0, 1.0, 1025)]
+    d = poisson_desc(P, xf)
+    h = C.c_void_p()
+    st, msg = status_and_message(P, P.lib().phl_poisson_create(C.byref(d), C.byref(h)))
+    assert st == 8 and "32 bits" in msg and not h.value, (st, msg)      # PHL_EUNSUPPORTED
+
+
 def test_unit_entry_points_reject_bad_options(P):
     L = P.lib()
     x = np.zeros(4)
