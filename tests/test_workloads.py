@@ -107,3 +107,34 @@ def test_paper_poisson_inputs():
     inside = r2 < 0.25 ** 2
     assert np.allclose(rho[inside], (1 - r2[inside] / 0.0625) ** 2, rtol=1e-15, atol=0)
     assert np.array_equal(rho, rho[::-1]) and np.array_equal(rho, rho.transpose(2, 1, 0))
+
+
+def test_stellar_box_recipe():
+    n = 32
+    pr = W.stellar_box(n, n, n)
+    L = W.STELLAR_L
+    assert pr.hi == (L, L, L) and pr.eos == "stellar" and pr.nspec == 2
+    assert W.STELLAR_RHO_BASE == 1e7 and W.STELLAR_RHO_TOP == 1e5
+    assert list(W.STELLAR_X) == [0.5, 0.5] and list(W.STELLAR_A) == [16.0, 28.0]
+    bg = pr.bg
+    dz = L / n
+    # the polytrope starts at rho_base at z = 0 and reaches rho_top at L (1 + 4/n), so the
+    # three ghost layers above the box stay inside [rho_top, rho_base]
+    assert math.isclose(bg["rho_f"][3], 1e7, rel_tol=1e-14)
+    assert bg["rho_f"].min() > 1e5 and bg["rho_f"].max() < 1e8 and bg["rho_c"].min() > 1e5
+    K = bg["p_f"][3] / bg["rho_f"][3] ** (5.0 / 3.0)
+    assert np.allclose(bg["p_f"], K * bg["rho_f"] ** (5.0 / 3.0), rtol=1e-13, atol=0)
+    # hydrostatic under the stored g: d P / dz = -rho g on the faces' closed form
+    g0 = -pr.g[2]
+    rho_f13 = bg["rho_f"] ** (1.0 / 1.5)
+    assert np.allclose(np.diff(rho_f13), -g0 * dz / (K * 2.5), rtol=1e-9, atol=0)
+    z_top = L * (1 + 4.0 / n)
+    assert math.isclose((1e7 ** (1 / 1.5) - g0 * z_top / (K * 2.5)) ** 1.5, 1e5, rel_tol=1e-10)
+    # composition, rest, isobaric noise, uniform B_x with beta 1e6 at mid-height
+    prim = pr.meta["prim"]
+    assert np.all(prim["X"] == 0.5) and not prim["vel"].any()
+    rel = prim["rho"] / bg["rho_c"][3:3 + n][:, None, None] - 1.0
+    assert np.abs(rel).max() <= 1e-3 * (1 + 1e-12)
+    b0 = pr.bx[0, 0, 0]
+    p_mid = K * ((1e7 ** (1 / 1.5) - g0 * 0.5 * L / (K * 2.5)) ** 1.5) ** (5.0 / 3.0)
+    assert np.all(pr.bx == b0) and math.isclose(2 * p_mid / b0 ** 2, 1e6, rel_tol=1e-10)
