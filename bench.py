@@ -406,7 +406,7 @@ def stellar_c3(P, n, steps, warmup, stream, ws):
     seeded EOS samples by the project's own kernels."""
     import numpy as np
     import workloads as W
-    table = P.EosTable()
+    table = P.EosTable(nrho=321, nT=241)   # 80 nodes per decade: interpolation error ~1e-8 (P, e), ~4e-7 (c_v, gamma_c)
     net = P.Mlp(seed=7)
     train = net.train(table, nsamples=10_000_000, epochs=8, batch=4096, lr=1e-2, seed=2026)
     pr = W.stellar_box(n, n, n)

@@ -304,16 +304,28 @@ phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const d
  * device-wide synchronisation those calls may imply.
  *   desc     geometry and physics (n, lo, hi, gamma, cfl; ideal EOS only);
  *            no other field is read and no grid is needed;
- *   cons, bx, by, bz  device pointers, ABI layout above (read only);
+ *   cons, bx, by, bz  device pointers, ABI layout above (read only):
+ *            cons (5 + nspec) nx ny nz doubles, bx (nx+1) ny nz, by nx (ny+1) nz,
+ *            bz nx ny (nz+1); the caller keeps them alive until the kernels end;
  *   dt_out   device pointer to one double that receives cfl / max(...);
  *   stream   cudaStream_t the two kernels are queued on (asynchronous).
+ * Pointers that are not device (or managed) memory of the current device are
+ * rejected with PHL_EINVAL before anything is launched; sizes cannot be
+ * checked from a pointer and must match desc.
+ * Invalid states: unlike phl_compute_dt, which returns PHL_ENEGATIVE or
+ * PHL_ENAN, this call keeps no error word: a cell with rho <= 0, P <= 0 or any
+ * non-finite value makes dt_out exactly 0 (the call itself returns PHL_OK), so
+ * a caller checks dt_out > 0 before using it.
  * Scratch: a library-owned __device__ array of PHL_DT_NOALLOC_MAX_CELLS / 4096
  * doubles (128 KiB), present on every GPU that loads the library until the
  * process exits; grids above PHL_DT_NOALLOC_MAX_CELLS cells are rejected with
  * PHL_EINVAL ("too many cells").  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call shares the array and leaves its partial
- * results in it; calls whose kernels overlap on the GPU race on it.
+ * array's device address (cudaGetSymbolAddress) and keeps it for the current
+ * CUDA context; a call under another context (after cudaDeviceReset, or a
+ * non-primary context) looks it up again.  Make the first call in each
+ * context before any stream capture.  Every call shares the array and leaves
+ * its partial results in it; calls whose kernels overlap on the GPU race on
+ * it.
  * Errors: PHL_EINVAL, PHL_EUNSUPPORTED (stellar EOS), PHL_ECUDA. */
 #define PHL_DT_NOALLOC_MAX_CELLS 67108864L
 phl_status phl_cfl_dt_noalloc(const phl_grid_desc *desc, const double *cons, const double *bx,
@@ -322,11 +334,16 @@ phl_status phl_cfl_dt_noalloc(const phl_grid_desc *desc, const double *cons, con
 /* ---------------- stellar equation of state (Sect. 2.2, item ii) --------
  * Ions (ideal gas), radiation (Eqs. prad, erad) and an electron-positron gas
  * of arbitrary degeneracy and relativity in pair equilibrium.  The e-/e+ part
- * is a table of its Helmholtz free-energy density over (ln n_e, ln T),
- * n_e = rho Y_e N_A, with f_x, f_y, f_xy at each node, computed on the device
- * from generalised Fermi-Dirac integrals, and interpolated by bicubic
- * Hermite polynomials; P, e, c_v and the pressure derivatives all derive from
- * that one interpolant.  CGS units. */
+ * is a table of its Helmholtz free-energy density f over (x, y) =
+ * (ln n_e, ln T), n_e = rho Y_e N_A, holding f, f_x, f_y, f_xx, f_yy, f_xy,
+ * f_xxy, f_xyy and f_xxyy at each node, computed on the device from
+ * generalised Fermi-Dirac integrals, and interpolated biquintically (tensor
+ * product of quintic Hermite polynomials) as the paper does with its
+ * Helmholtz free-energy table; P, e, c_v and the pressure derivatives all
+ * derive from that one interpolant.  At 80 nodes per decade in both
+ * variables the interpolated P, e, gamma_e agree with direct quadrature to
+ * ~1e-8 and c_v, gamma_c to ~4e-7; at 40 per decade (the bindings' default)
+ * to ~1e-7 and ~7e-6.  CGS units. */
 typedef struct phl_eos_table phl_eos_table;
 
 /* Build the table on the current device: log10(rho Y_e) in [lrhoye_lo,
@@ -335,8 +352,9 @@ typedef struct phl_eos_table phl_eos_table;
 phl_status phl_eos_table_create(double lrhoye_lo, double lrhoye_hi, int nrho, double lT_lo,
                                 double lT_hi, int nT, phl_eos_table **out);
 void phl_eos_table_destroy(phl_eos_table *t);
-/* Copy the node data to host: [nx, ny, x0, dx, y0, dy, (f, f_x, f_y, f_xy)...]
- * (6 + 4 nx ny doubles); for tests. */
+/* Copy the node data to host: [nx, ny, x0, dx, y0, dy, then per node (x
+ * fastest) f, f_x, f_y, f_xx, f_yy, f_xy, f_xxy, f_xyy, f_xxyy] (6 + 9 nx ny
+ * doubles); for tests. */
 phl_status phl_eos_table_export(const phl_eos_table *t, double *out, long nout);
 
 /* Batch EOS: for each i, temperature from (rho, e_int) by Newton

@@ -48,12 +48,26 @@ _CRITERION = {"relative": 0, "absolute": 1}
 
 
 _lib = None
+_libs = {}
+_parallel = False
+
+
+def set_parallel(on: bool) -> None:
+    """Run the oracle's stage loops over all host cores (the -fopenmp build of
+    the same sources, bit-identical results) or single-threaded (default)."""
+    global _lib, _parallel
+    _parallel = bool(on)
+    _lib = None
 
 
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        _build.build()
+        path = _build.LIB_OMP if _parallel else _build.LIB
+        if path in _libs:
+            _lib = _libs[path]
+            return _lib
         L = C.CDLL(path)
         L.ora_run.restype = C.c_int
         L.ora_run.argtypes = [C.POINTER(OraCfg), _dp, _dp, _dp, _dp, _dp, C.c_int, C.c_double, _dp, _dp]
@@ -100,6 +114,12 @@ def lib():
         L.ora_eos_table_export.argtypes = [C.c_void_p, _dp, C.c_long]
         L.ora_ep_direct.restype = C.c_int
         L.ora_ep_direct.argtypes = [C.c_double, C.c_double, C.c_double] + [_dp] * 5
+        L.ora_ep_first.restype = C.c_int
+        L.ora_ep_first.argtypes = [C.c_double, C.c_double, _dp]
+        L.ora_ep_derivs.restype = C.c_int
+        L.ora_ep_derivs.argtypes = [C.c_double, C.c_double, _dp]
+        L.ora_ct_corner.restype = C.c_double
+        L.ora_ct_corner.argtypes = [_dp, _dp, _dp, C.c_double, C.c_double]
         L.ora_fd.restype = C.c_double
         L.ora_fd.argtypes = [C.c_double, C.c_double, C.c_double]
         L.ora_eos_rt.restype = C.c_int
@@ -111,6 +131,7 @@ def lib():
         L.ora_mlp_forward.argtypes = [_dp, C.c_int, C.c_int, _dp, C.c_long, _dp]
         L.ora_mlp_loss_grad.restype = C.c_double
         L.ora_mlp_loss_grad.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp, C.c_long, _dp]
+        _libs[path] = L
         _lib = L
     return _lib
 
@@ -359,6 +380,30 @@ def ep_direct(rho, ye, T):
 
 def fd(k, eta, beta):
     return lib().ora_fd(k, eta, beta)
+
+
+def ct_corner(Ef, Ec, F, rho, smax):
+    """Contact-CT corner EMF from four face EMFs, four cell EMFs and the four
+    faces' mass fluxes (see oracle.h)."""
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (Ef, Ec, F)]
+    return lib().ora_ct_corner(*[_ptr(v) for v in a], float(rho), float(smax))
+
+
+def ep_first(nnet, T):
+    """f, f_x, f_y, f_xy of the e-/e+ free-energy density from the integrals'
+    own combinations (x = ln n, y = ln T)."""
+    out = np.zeros(4)
+    if lib().ora_ep_first(nnet, T, _ptr(out)):
+        raise RuntimeError("oracle e-/e+ evaluation failed")
+    return out
+
+
+def ep_derivs(nnet, T):
+    """f, f_x, f_y, f_xx, f_yy, f_xy, f_xxy, f_xyy, f_xxyy (Taylor-mode)."""
+    out = np.zeros(9)
+    if lib().ora_ep_derivs(nnet, T, _ptr(out)):
+        raise RuntimeError("oracle e-/e+ evaluation failed")
+    return out
 
 
 def riemann(wl, wr, bn, solver="lhlld", mach_thr=0.6, nspec=0):

@@ -391,6 +391,34 @@ static int contact_dir(double frho, double rhol, double rhor, double SL, double 
   return frho > scale ? 1 : (frho < -scale ? -1 : 0);
 }
 
+/* Contact-CT corner EMF (Sect. 2.4; Gardiner & Stone 2005) of the edge at the
+ * corner (a-1/2, b-1/2): Ea1, Ea0 the face EMFs of the a-faces above and
+ * below the corner, Eb1, Eb0 those of the b-faces right and left of it, Eij
+ * the cell reference EMFs of cells (c_a - 1 + i, c_b - 1 + j), m* the contact
+ * directions of the four faces.  The corner averages the four face values
+ * and their extrapolations to the corner; each half-cell derivative is taken
+ * from the upwind cell of the face's mass flux, the mean of both with none. */
+static double ct_corner(double Ea1, double Ea0, double Eb1, double Eb0, double E00, double E10, double E01,
+                        double E11, int ma1, int ma0, int mb1, int mb0) {
+  /* derivatives along b on the a-faces, upwinded in a */
+  double lo_l = Eb0 - E00, lo_r = Eb1 - E10;    /* below the corner */
+  double up_l = E01 - Eb0, up_r = E11 - Eb1;    /* above the corner */
+  double dlo = ma0 > 0 ? lo_l : (ma0 < 0 ? lo_r : 0.5 * (lo_l + lo_r));
+  double dup = ma1 > 0 ? up_l : (ma1 < 0 ? up_r : 0.5 * (up_l + up_r));
+  /* derivatives along a on the b-faces, upwinded in b */
+  double le_d = Ea0 - E00, le_u = Ea1 - E01;    /* left of the corner  */
+  double ri_d = E10 - Ea0, ri_u = E11 - Ea1;    /* right of the corner */
+  double dle = mb0 > 0 ? le_d : (mb0 < 0 ? le_u : 0.5 * (le_d + le_u));
+  double dri = mb1 > 0 ? ri_d : (mb1 < 0 ? ri_u : 0.5 * (ri_d + ri_u));
+  return 0.25 * (Ea1 + Ea0 + Eb1 + Eb0) + 0.25 * (dlo - dup) + 0.25 * (dle - dri);
+}
+
+double ora_ct_corner(const double *Ef, const double *Ec, const double *F, double rho, double smax) {
+  int m[4];
+  for (int q = 0; q < 4; ++q) m[q] = contact_dir(F[q], rho, rho, -smax, smax);
+  return ct_corner(Ef[0], Ef[1], Ef[2], Ef[3], Ec[0], Ec[1], Ec[2], Ec[3], m[0], m[1], m[2], m[3]);
+}
+
 static void riemann_core(const double *wl, const double *wr, double bn, int nspec,
                          int solver, double mach_thr, double *f, int *up);
 
@@ -566,6 +594,7 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
   fill_face_ghosts(G, w->B);
 
   /* (2) primitives + EOS on interior cells, as deviations from the background */
+#pragma omp parallel for reduction(min : rc) schedule(static)
   for (int k = 0; k < G->n[2]; ++k)
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i) {
@@ -592,6 +621,7 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
   memset(w->raw, 0, G->ntot);
   memset(w->flag, 0, G->ntot);
   if (c->eps_sf > 0.0) {
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < G->n[2]; ++k)
       for (int j = 0; j < G->n[1]; ++j)
         for (int i = 0; i < G->n[0]; ++i) {
@@ -607,6 +637,7 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
           }
           w->raw[p] = (sum / (c->eps_sf * P0) > 1.0);
         }
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < G->n[2]; ++k)
       for (int j = 0; j < G->n[1]; ++j)
         for (int i = 0; i < G->n[0]; ++i) {
@@ -663,10 +694,11 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
       else if (G->act[e]) { lo[e] = -1; hi[e] = G->n[e] + 1; }
       else { lo[e] = 0; hi[e] = 1; }
     }
-    int c3[3];
-    for (c3[2] = lo[2]; c3[2] < hi[2]; ++c3[2])
-      for (c3[1] = lo[1]; c3[1] < hi[1]; ++c3[1])
-        for (c3[0] = lo[0]; c3[0] < hi[0]; ++c3[0]) {
+#pragma omp parallel for reduction(min : rc) schedule(static)
+    for (int kz = lo[2]; kz < hi[2]; ++kz)
+      for (int ky = lo[1]; ky < hi[1]; ++ky)
+        for (int kx = lo[0]; kx < hi[0]; ++kx) {
+          int c3[3] = {kx, ky, kz};
           long pR = IXv(G, c3), pL = pR - G->s[d];
           long sd = G->s[d];
           double wl[10 + ORA_MAXSPEC], wr[10 + ORA_MAXSPEC];
@@ -761,10 +793,11 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
     hi[d] = G->n[d];
     hi[a] = G->act[a] ? G->n[a] + 1 : 1;
     hi[b] = G->act[b] ? G->n[b] + 1 : 1;
-    int cc[3];
-    for (cc[2] = 0; cc[2] < hi[2]; ++cc[2])
-      for (cc[1] = 0; cc[1] < hi[1]; ++cc[1])
-        for (cc[0] = 0; cc[0] < hi[0]; ++cc[0]) {
+#pragma omp parallel for schedule(static)
+    for (int kz = 0; kz < hi[2]; ++kz)
+      for (int ky = 0; ky < hi[1]; ++ky)
+        for (int kx = 0; kx < hi[0]; ++kx) {
+          int cc[3] = {kx, ky, kz};
           long p = IXv(G, cc);
           double Ed = 0.0;
           if (G->act[a] && G->act[b]) {
@@ -782,17 +815,7 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
 #define ECELL(q) (-(w->W[W_VX + a][q] * w->W[W_BX + b][q] - w->W[W_VX + b][q] * w->W[W_BX + a][q]))
             double E00 = ECELL(q00), E10 = ECELL(q10), E01 = ECELL(q01), E11 = ECELL(q11);
 #undef ECELL
-            /* derivatives along b on the a-faces, upwinded in a */
-            double lo_l = Eb0 - E00, lo_r = Eb1 - E10;    /* below the corner */
-            double up_l = E01 - Eb0, up_r = E11 - Eb1;    /* above the corner */
-            double dlo = ma0 > 0 ? lo_l : (ma0 < 0 ? lo_r : 0.5 * (lo_l + lo_r));
-            double dup = ma1 > 0 ? up_l : (ma1 < 0 ? up_r : 0.5 * (up_l + up_r));
-            /* derivatives along a on the b-faces, upwinded in b */
-            double le_d = Ea0 - E00, le_u = Ea1 - E01;    /* left of the corner  */
-            double ri_d = E10 - Ea0, ri_u = E11 - Ea1;    /* right of the corner */
-            double dle = mb0 > 0 ? le_d : (mb0 < 0 ? le_u : 0.5 * (le_d + le_u));
-            double dri = mb1 > 0 ? ri_d : (mb1 < 0 ? ri_u : 0.5 * (ri_d + ri_u));
-            Ed = 0.25 * (Ea1 + Ea0 + Eb1 + Eb0) + 0.25 * (dlo - dup) + 0.25 * (dle - dri);
+            Ed = ct_corner(Ea1, Ea0, Eb1, Eb0, E00, E10, E01, E11, ma1, ma0, mb1, mb0);
           } else if (G->act[a]) {
             Ed = -w->F[a][F_BX + b][p];
           } else if (G->act[b]) {
@@ -811,6 +834,7 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
 
   /* (7) cell residual R = div F - (S - S_hat) (Eqs. fv, spatres, wb2) */
   long nc = abi_cells(G);
+#pragma omp parallel for schedule(static)
   for (int k = 0; k < G->n[2]; ++k)
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i) {
@@ -843,10 +867,11 @@ static int compute_rhs(work *w, const double *cons, const double *bx, const doub
   for (int d = 0; d < 3; ++d) {
     int a = (d + 1) % 3, b = (d + 2) % 3;
     int ext[3] = {G->n[0] + (d == 0), G->n[1] + (d == 1), G->n[2] + (d == 2)};
-    int cc[3];
-    for (cc[2] = 0; cc[2] < ext[2]; ++cc[2])
-      for (cc[1] = 0; cc[1] < ext[1]; ++cc[1])
-        for (cc[0] = 0; cc[0] < ext[0]; ++cc[0]) {
+#pragma omp parallel for schedule(static)
+    for (int kz = 0; kz < ext[2]; ++kz)
+      for (int ky = 0; ky < ext[1]; ++ky)
+        for (int kx = 0; kx < ext[0]; ++kx) {
+          int cc[3] = {kx, ky, kz};
           int e[3] = {cc[0], cc[1], cc[2]};
           if (!G->act[d]) e[d] = 0;
           long p = IXv(G, e);
@@ -894,6 +919,8 @@ double ora_dt(const ora_cfg *cfg, const double *cons, const double *bx,
   geo_init(&G, cfg);
   long nc = abi_cells(&G);
   double mx = 0.0;
+  int bad = 0;
+#pragma omp parallel for reduction(max : mx) reduction(max : bad) schedule(static)
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
       for (int i = 0; i < G.n[0]; ++i) {
@@ -904,7 +931,7 @@ double ora_dt(const ora_cfg *cfg, const double *cons, const double *bx,
         bc[1] = 0.5 * (by[AF(&G, 1, i, j, k)] + by[AF(&G, 1, i, j + 1, k)]);
         bc[2] = 0.5 * (bz[AF(&G, 2, i, j, k)] + bz[AF(&G, 2, i, j, k + 1)]);
         double Tl = T ? T[a] : 0.0;    /* the step's Newton guesses are left untouched */
-        if (cell_prims(&G, u, bc, k, T ? &Tl : NULL, w)) return -1.0;
+        if (cell_prims(&G, u, bc, k, T ? &Tl : NULL, w)) { bad = 1; continue; }
         bgstate b = bg_cell(&G, k);
         double rho = w[W_RHO] + b.rho, P = w[W_P] + b.p, gc = w[W_GC] + b.gc;
         double a2 = gc * P / rho;
@@ -920,6 +947,7 @@ double ora_dt(const ora_cfg *cfg, const double *cons, const double *bx,
         }
         if (s > mx) mx = s;
       }
+  if (bad) return -1.0;
   return cfg->cfl / mx;
 }
 

@@ -133,6 +133,12 @@ int ora_stage(const ora_cfg *cfg, const double *cons_in, const double *bx_in,
 void ora_riemann(const double *wl, const double *wr, double bn, int nspec,
                  int solver, double mach_thr, double *f);
 
+/* Contact-CT corner EMF (Sect. 2.4): Ef = face EMFs Ea1, Ea0, Eb1, Eb0; Ec =
+ * cell reference EMFs E00, E10, E01, E11; F = mass fluxes through the same
+ * four faces; rho, smax: the density and fastest signal speed of the faces
+ * (the contact direction's deadband is 1e-12 rho smax). */
+double ora_ct_corner(const double *Ef, const double *Ec, const double *F, double rho, double smax);
+
 /* Divergence max|div B| * min(dx) over interior cells (Eq. divb). */
 double ora_divb(const ora_cfg *cfg, const double *bx, const double *by, const double *bz);
 
@@ -148,6 +154,12 @@ long ora_eos_table_size(const ora_eos_table *t);
  * the mixture with Ye), free energy f = e - T s, s, eta.  Returns 0 or -1. */
 int ora_ep_direct(double rho, double ye, double T, double *P, double *e,
                   double *s, double *eta, double *npos);
+/* Free-energy density f(x, y) of the e-/e+ gas, x = ln nnet, y = ln T:
+ * ora_ep_first: f, f_x, f_y, f_xy from the integrals' own combinations;
+ * ora_ep_derivs: f, f_x, f_y, f_xx, f_yy, f_xy, f_xxy, f_xyy, f_xxyy by
+ * truncated Taylor arithmetic (the biquintic table's node values). */
+int ora_ep_first(double nnet, double T, double *fv);
+int ora_ep_derivs(double nnet, double T, double *out);
 /* Generalised Fermi-Dirac integral F_k(eta, beta). */
 double ora_fd(double k, double eta, double beta);
 

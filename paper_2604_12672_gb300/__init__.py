@@ -204,11 +204,24 @@ def cfl_dt_noalloc(grid_or_desc, cons, bx, by, bz, dt_out, stream=None):
     """CFL step without device allocation (phl_cfl_dt_noalloc in include/phl.h).
 
     For callers that cannot let the library allocate device memory.  All arrays
-    are CUDA tensors in the ABI layout; dt_out is a one-element float64 CUDA
-    tensor.  The call is asynchronous on `stream` (a cudaStream_t handle).
+    are contiguous float64 CUDA tensors in the ABI layout, checked against the
+    descriptor's sizes; dt_out is a one-element float64 CUDA tensor.  The call
+    is asynchronous on `stream` (a cudaStream_t handle).  dt_out = 0 marks a
+    state with rho <= 0, P <= 0 or a non-finite value.
     """
     d = grid_or_desc.desc if isinstance(grid_or_desc, Grid) else grid_or_desc
-    ptrs = [_ptr(a)[0] for a in (cons, bx, by, bz, dt_out)]
+    nx, ny, nz = d.n[0], d.n[1], d.n[2]
+    need = {"cons": (5 + d.nspec) * nx * ny * nz, "bx": (nx + 1) * ny * nz, "by": nx * (ny + 1) * nz,
+            "bz": nx * ny * (nz + 1), "dt_out": 1}
+    arrs = {"cons": cons, "bx": bx, "by": by, "bz": bz, "dt_out": dt_out}
+    for name, a in arrs.items():
+        import torch
+        ok = isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+        if not ok:
+            raise PhlError(1, f"phl_cfl_dt_noalloc: {name} must be a contiguous float64 CUDA tensor")
+        if a.numel() < need[name]:
+            raise PhlError(1, f"phl_cfl_dt_noalloc: {name} holds {a.numel()} values, the grid needs {need[name]}")
+    ptrs = [arrs[k].data_ptr() for k in ("cons", "bx", "by", "bz", "dt_out")]
     _check(lib().phl_cfl_dt_noalloc(C.byref(d), *ptrs, stream))
 
 
@@ -222,7 +235,7 @@ class EosTable:
         self.shape = (nrho, nT)
 
     def export(self):
-        n = 6 + 4 * self.shape[0] * self.shape[1]
+        n = 6 + 9 * self.shape[0] * self.shape[1]
         out = np.zeros(n)
         _check(lib().phl_eos_table_export(self.h, out.ctypes.data, n))
         return out

@@ -10,6 +10,10 @@
 // The array is shared by every call: a call overwrites exactly the slots it
 // later reads, so nothing has to start at zero, but two calls whose kernels
 // overlap on the GPU (e.g. on two streams) race on it.
+//
+// A cell whose state has no sound speed (rho <= 0, P <= 0, or anything
+// non-finite) contributes an infinite signal speed, so dt_out = 0 marks a bad
+// state; the kernels keep no error word of their own.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <mutex>
@@ -53,6 +57,10 @@ __global__ void k_dt_partial(NaGeo G, long ncells, const double *__restrict__ co
     const double bcz = 0.5 * (bz[c] + bz[c + (long)nx * ny]);
     const double b2 = bcx * bcx + bcy * bcy + bcz * bcz;
     const double P = (G.gamma - 1.0) * (cons[4 * ncells + c] - 0.5 * rho * (vx * vx + vy * vy + vz * vz) - 0.5 * b2);
+    if (!(rho > 0.0) || !(P > 0.0)) {   // no sound speed: the sentinel dt_out = 0
+      m = INFINITY;
+      continue;
+    }
     const double a2 = G.gamma * P / rho;
     const double bb = b2 / rho;
     const double v[3] = {vx, vy, vz}, bc[3] = {bcx, bcy, bcz};
@@ -91,10 +99,17 @@ __global__ void k_dt_final(const double *__restrict__ partial, int nblocks, doub
   }
 }
 
-// Device address of g_dt_partial, looked up once per device.
+// Device address of g_dt_partial, looked up once per device and context: the
+// module holding the array is loaded into each context, so after a device
+// reset, or under another (non-primary) context, the array lives at another
+// address and the lookup is redone.  The current context comes from the
+// driver's cuCtxGetCurrent, fetched through the runtime's entry-point query.
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mutex;
 double *g_na_ptr[NA_MAX_DEVICES] = {nullptr};
+void *g_na_ctx[NA_MAX_DEVICES] = {nullptr};
+typedef int (*ctx_get_fn)(void **);
+ctx_get_fn g_ctx_get = nullptr;
 
 cudaError_t partial_ptr(double **out) {
   int dev = 0;
@@ -102,14 +117,37 @@ cudaError_t partial_ptr(double **out) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_dt_partial);
+  if (!g_ctx_get) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_ctx_get = (ctx_get_fn)fn;
+  }
+  void *ctx = nullptr;
+  if (g_ctx_get(&ctx) != 0) return cudaErrorDeviceUninitialized;
+  if (!g_na_ptr[dev] || ctx != g_na_ctx[dev] || !ctx) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_dt_partial);   // also makes the primary context current if none was
+    if (e != cudaSuccess) return e;
+    if (!ctx && g_ctx_get(&ctx) != 0) return cudaErrorDeviceUninitialized;
     g_na_ptr[dev] = (double *)p;
+    g_na_ctx[dev] = ctx;
   }
   *out = g_na_ptr[dev];
   return cudaSuccess;
+}
+
+// True when p is memory the current device's kernels may read as device
+// memory (a device or managed allocation).
+bool device_accessible(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -131,11 +169,18 @@ extern "C" phl_status phl_cfl_dt_noalloc(const phl_grid_desc *desc, const double
     G.n[d] = desc->n[d];
     G.act[d] = desc->n[d] > 1;
     G.dx[d] = (desc->hi[d] - desc->lo[d]) / desc->n[d];
+    // checked after each factor: every factor and partial product stays at
+    // or below the maximum, so the product cannot overflow
+    if (desc->n[d] > PHL_DT_NOALLOC_MAX_CELLS || ncells * desc->n[d] > PHL_DT_NOALLOC_MAX_CELLS)
+      return (phl_status)set_error(PHL_EINVAL, "phl_cfl_dt_noalloc: too many cells (more than the maximum %ld)",
+                                   (long)PHL_DT_NOALLOC_MAX_CELLS);
     ncells *= desc->n[d];
   }
-  if (ncells > PHL_DT_NOALLOC_MAX_CELLS)   // the scratch array holds 16384 block partials
-    return (phl_status)set_error(PHL_EINVAL, "phl_cfl_dt_noalloc: too many cells (%ld > maximum %ld)", ncells,
-                                 (long)PHL_DT_NOALLOC_MAX_CELLS);
+  const void *ptrs[5] = {cons, bx, by, bz, dt_out};
+  static const char *names[5] = {"cons", "bx", "by", "bz", "dt_out"};
+  for (int q = 0; q < 5; ++q)
+    if (!device_accessible(ptrs[q]))
+      return (phl_status)set_error(PHL_EINVAL, "phl_cfl_dt_noalloc: %s is not device memory", names[q]);
   G.gamma = desc->gamma;
   G.cfl = desc->cfl;
   double *partial = nullptr;

@@ -7,6 +7,7 @@
 
 #include <vector>
 
+#include "eos_nodes.cuh"
 #include "eos_stellar.cuh"
 #include "phl.h"
 #include "phl_internal.cuh"
@@ -22,8 +23,7 @@ struct phl_eos_table {
 
 namespace {
 
-constexpr int GLN = 32;   // Gauss-Legendre order of the integral panels
-__constant__ double c_glx[GLN], c_glw[GLN];
+using eosn::GLN;
 
 // Gauss-Legendre nodes/weights on [-1, 1]: Newton on the Legendre recurrence.
 void gauss_legendre(int n, double *x, double *w) {
@@ -46,97 +46,15 @@ void gauss_legendre(int n, double *x, double *w) {
   }
 }
 
-// One species at (eta, b): F_1/2, F_3/2, F_5/2, dF_{1/2,3/2}/deta, dF_{1/2,3/2}/db.
-// Integration variable s with x = s^2.  Panel edges at fixed offsets (in kT)
-// from the Fermi edge x = max(eta, 0): the Fermi factor changes by at most
-// e^20 across a panel and is below e^-50 before the first edge, so the
-// exponential tails are resolved at every degeneracy.
-__device__ void fd_integrals(double eta, double b, double *F) {
-  for (int q = 0; q < 7; ++q) F[q] = 0.0;
-  constexpr int NOFF = 14;
-  const double off[NOFF] = {-50.0, -30.0, -16.0, -8.0, -4.0, -1.5, 0.0, 1.5, 4.0, 8.0, 16.0, 30.0, 50.0, 110.0};
-  const double base = fmax(eta, 0.0);
-  double a = 0.0;
-  for (int k = 0; k < NOFF; ++k) {
-    const double xe = base + off[k];
-    if (!(xe > 0.0)) continue;
-    const double c = sqrt(xe);
-    if (!(c > a)) continue;
-    const double hm = 0.5 * (c - a), cm = 0.5 * (c + a);
-    for (int g = 0; g < GLN; ++g) {
-      const double s = cm + hm * c_glx[g];
-      const double wgt = 2.0 * s * hm * c_glw[g];   // dx = 2 s ds
-      const double x = s * s, u = x - eta;
-      const double z = exp(-fabs(u));
-      const double fermi = u > 0.0 ? z / (1.0 + z) : 1.0 / (1.0 + z);
-      const double fder = z / ((1.0 + z) * (1.0 + z));   // f (1 - f)
-      const double S = sqrt(1.0 + 0.5 * b * x);
-      const double x12 = s, x32 = x * s, x52 = x * x * s;
-      F[0] += wgt * x12 * S * fermi;
-      F[1] += wgt * x32 * S * fermi;
-      F[2] += wgt * x52 * S * fermi;
-      F[3] += wgt * x12 * S * fder;
-      F[4] += wgt * x32 * S * fder;
-      F[5] += wgt * x32 * fermi / (4.0 * S);
-      F[6] += wgt * x52 * fermi / (4.0 * S);
-    }
-    a = c;
-  }
-}
-
-struct Species { double n, n_eta, n_b, P, Ek; };
-
-__device__ Species species(double eta, double b, double lam3) {
-  double F[7];
-  fd_integrals(eta, b, F);
-  const double Kn = 8.0 * PI_D * sqrt(2.0) * lam3;
-  const double rb = sqrt(b), b32 = b * rb, b52 = b * b * rb;
-  Species s;
-  s.n = Kn * b32 * (F[0] + b * F[1]);
-  s.n_eta = Kn * b32 * (F[3] + b * F[4]);
-  s.n_b = Kn * (1.5 * rb * (F[0] + b * F[1]) + b32 * (F[5] + F[1] + b * F[6]));
-  s.P = (2.0 / 3.0) * Kn * MEC2 * b52 * (F[1] + 0.5 * b * F[2]);
-  s.Ek = Kn * MEC2 * b52 * (F[1] + b * F[2]);
-  return s;
-}
-
-// Free-energy node of the e-/e+ gas at net density ne and temperature T.
+// One table node per thread: the free energy and its eight derivatives
+// (eos_nodes.cuh); gl holds the quadrature nodes then weights.
 __global__ void k_table_nodes(int nx, int ny, double x0, double dx, double y0, double dy, double lam3,
-                              double *v, int *fail) {
+                              const double *gl, double *v, int *fail) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nx * ny) return;
   const int i = idx % nx, j = idx / nx;
-  const double ne = exp(x0 + i * dx), T = exp(y0 + j * dy);
-  const double b = KB * T / MEC2, kT = KB * T;
-  // charge neutrality n-(eta) - n+(-eta - 2/b) = ne: bracketed Newton
-  const double Kn = 8.0 * PI_D * sqrt(2.0) * lam3;
-  const double xf = cbrt(3.0 * ne / (8.0 * PI_D * lam3));
-  double eta = fmax(log(ne / (Kn * b * sqrt(b) * 0.886226925452758)), (sqrt(1.0 + xf * xf) - 1.0) / b);
-  double lo = -700.0, hi = 1e7;
-  bool ok = false;
-  Species m, p;
-  for (int it = 0; it < 200; ++it) {
-    m = species(eta, b, lam3);
-    p = species(-eta - 2.0 / b, b, lam3);
-    const double r = m.n - p.n - ne;
-    if (r > 0.0) hi = eta; else lo = eta;
-    double en = eta - r / (m.n_eta + p.n_eta);
-    if (!(en > lo && en < hi)) en = 0.5 * (lo + hi);
-    const bool done = fabs(en - eta) <= 1e-15 * (fabs(eta) + 1.0) || hi - lo < 1e-14 * (fabs(eta) + 1.0);
-    eta = en;
-    if (done) { ok = true; break; }
-  }
-  if (!ok) { atomicOr(fail, 1); return; }
-  const double etap = -eta - 2.0 / b;
-  m = species(eta, b, lam3);
-  p = species(etap, b, lam3);
-  const double Ts = (m.Ek + m.P - eta * kT * m.n) + (p.Ek + p.P - etap * kT * p.n);
-  const double deta_db = -(m.n_b - (p.n_b + p.n_eta * 2.0 / (b * b))) / (m.n_eta + p.n_eta);
-  double *o = v + 4L * idx;
-  o[0] = ne * eta * kT - (m.P + p.P);     // f
-  o[1] = ne * eta * kT;                   // f_x
-  o[2] = -Ts;                             // f_y
-  o[3] = ne * kT * (eta + deta_db * b);   // f_xy
+  if (!eosn::node_values(exp(x0 + i * dx), exp(y0 + j * dy), lam3, gl, gl + GLN, v + (long)NQ * idx))
+    atomicOr(fail, 1);
 }
 
 template <typename R>
@@ -173,11 +91,9 @@ phl_status phl_eos_table_create(double lrhoye_lo, double lrhoye_hi, int nrho, do
   if (!out || nrho < 4 || nT < 4 || !(lrhoye_hi > lrhoye_lo) || !(lT_hi > lT_lo))
     return (phl_status)set_error(PHL_EINVAL, "phl_eos_table_create: bad arguments");
   *out = nullptr;
-  double gx[GLN], gw[GLN];
-  gauss_legendre(GLN, gx, gw);
-  cudaError_t e = cudaMemcpyToSymbol(c_glx, gx, sizeof(gx));
-  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_glw, gw, sizeof(gw));
-  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "eos table: %s", cudaGetErrorString(e));
+  double gxw[2 * GLN];
+  gauss_legendre(GLN, gxw, gxw + GLN);
+  cudaError_t e = cudaSuccess;
   phl_eos_table *t = new phl_eos_table();
   t->t.nx = nrho;
   t->t.ny = nT;
@@ -190,24 +106,28 @@ phl_status phl_eos_table_create(double lrhoye_lo, double lrhoye_hi, int nrho, do
   t->t.idxf = (float)t->t.idx; t->t.idyf = (float)t->t.idy;
   t->t.Tlo = exp(t->t.y0); t->t.Thi = exp(t->t.y0 + (nT - 1) * t->t.dy);
   t->t.Tlof = (float)t->t.Tlo; t->t.Thif = (float)t->t.Thi;
-  const long nv = 4L * nrho * nT;
+  const long nv = (long)NQ * nrho * nT;
   int *fail = nullptr;
+  double *dgl = nullptr;
   e = cudaMalloc(&t->dv, nv * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&t->dvf, nv * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&fail, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&dgl, sizeof(gxw));
   if (e == cudaSuccess) e = cudaMemset(fail, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(dgl, gxw, sizeof(gxw), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    cudaFree(t->dv); cudaFree(t->dvf); cudaFree(fail); delete t;
+    cudaFree(t->dv); cudaFree(t->dvf); cudaFree(fail); cudaFree(dgl); delete t;
     return (phl_status)set_error(PHL_ENOMEM, "eos table: %s", cudaGetErrorString(e));
   }
   const double me = MEC2 / (CL * CL), l = me * CL / HPL;
   const int nn = nrho * nT;
-  k_table_nodes<<<(nn + 63) / 64, 64>>>(nrho, nT, t->t.x0, t->t.dx, t->t.y0, t->t.dy, l * l * l, t->dv, fail);
+  k_table_nodes<<<(nn + 63) / 64, 64>>>(nrho, nT, t->t.x0, t->t.dx, t->t.y0, t->t.dy, l * l * l, dgl, t->dv, fail);
   std::vector<double> h(nv);
   int f = 0;
   e = cudaMemcpy(h.data(), t->dv, nv * sizeof(double), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(&f, fail, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(fail);
+  cudaFree(dgl);
   if (e != cudaSuccess || f) {
     cudaFree(t->dv); cudaFree(t->dvf); delete t;
     return (phl_status)set_error(e != cudaSuccess ? PHL_ECUDA : PHL_ENEWTON, "eos table: node solve failed");
@@ -230,7 +150,7 @@ void phl_eos_table_destroy(phl_eos_table *t) {
 
 phl_status phl_eos_table_export(const phl_eos_table *t, double *out, long nout) {
   if (!t || !out) return (phl_status)set_error(PHL_EINVAL, "null argument");
-  const long nv = 4L * t->t.nx * t->t.ny;
+  const long nv = (long)NQ * t->t.nx * t->t.ny;
   if (nout < 6 + nv) return (phl_status)set_error(PHL_EINVAL, "phl_eos_table_export: buffer too small");
   out[0] = t->t.nx; out[1] = t->t.ny; out[2] = t->t.x0; out[3] = t->t.dx; out[4] = t->t.y0; out[5] = t->t.dy;
   if (cudaMemcpy(out + 6, t->dv, nv * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -2,14 +2,24 @@
 //
 // Ions (ideal gas), radiation (Eqs. prad, erad) and an electron-positron gas
 // in pair equilibrium.  The e-/e+ part is a table of its Helmholtz
-// free-energy density f over (x, y) = (ln n_e, ln T), n_e = rho Y_e N_A, with
-// the derivatives f_x = n eta k T, f_y = -T s and f_xy at each node, built on
-// the device from the generalised Fermi-Dirac integrals
-//   F_k(eta, b) = int_0^inf x^k sqrt(1 + b x/2) / (exp(x - eta) + 1) dx,
-// b = kT / m_e c^2.  Bicubic Hermite interpolation of f gives P = f_x - f,
-// e = (f - f_y) / rho, c_v = (f_y - f_yy) / (rho T), dP/dT = (f_xy - f_y) / T,
-// dP/drho = (f_xx - f_x) / rho -- all from one interpolant, so the
-// thermodynamic identities hold for the interpolated EOS.
+// free-energy density f over (x, y) = (ln n_e, ln T), n_e = rho Y_e N_A,
+// holding at each node f and its derivatives f_x, f_y, f_xx, f_yy, f_xy,
+// f_xxy, f_xyy, f_xxyy (eos_nodes.cuh), interpolated biquintically as the
+// paper does with its Helmholtz table: the tensor product of quintic Hermite
+// polynomials, which takes f and its derivatives up to second order in each
+// variable from the nodes.  P = f_x - f, e = (f - f_y) / rho,
+// c_v = (f_y - f_yy) / (rho T), dP/dT = (f_xy - f_y) / T,
+// dP/drho = (f_xx - f_x) / rho all come from one interpolant, so the
+// thermodynamic identities hold for the interpolated EOS, and c_v, gamma_c
+// are continuous.
+//
+// Evaluation in two parts.  rho and the composition are fixed during an
+// inversion, so the x-direction is contracted once per table row pair: for
+// the two y-nodes j, j+1 of the current cell and each y-order r = 0, 1, 2,
+// g[m][b][r] = d^m/dx^m d^r/dy^r f at (x, y_(j+b)) by the quintic Hermite
+// polynomial in x.  A Newton iteration then needs only the one-dimensional
+// quintic in y on those six values (18 multiply-adds for f, f_y, f_yy), and
+// redoes the contraction only when T leaves the current table interval.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -27,11 +37,17 @@ constexpr double ARAD = 7.565733250e-15;
 constexpr double ARAD_QUARTER = 2.9492579329135276e-04;   // ARAD^(1/4)
 constexpr double RGAS = KB * NAV;
 constexpr double PI_D = 3.14159265358979323846;
+constexpr int NQ = 9;          // node values: f, f_x, f_y, f_xx, f_yy, f_xy, f_xxy, f_xyy, f_xxyy
+
+// node slot of d^(p + r) f / dx^p dy^r
+__host__ __device__ __forceinline__ int qslot(int p, int r) {
+  return p == 0 ? 2 * r : (p == 1 ? (r == 0 ? 1 : 3 + 2 * r) : (r == 0 ? 3 : 4 + 2 * r));
+}
 
 struct Table {
   int nx, ny;
   double x0, dx, y0, dy;      // x = ln n_e, y = ln T
-  const double *v;            // [ny][nx][4]: f, f_x, f_y, f_xy (device)
+  const double *v;            // [ny][nx][NQ] (device)
   const float *vf;            // FP32 copy
   float x0f, dxf, y0f, dyf;
   double idx, idy;            // 1/dx, 1/dy: the evaluation multiplies (FP64 division
@@ -46,87 +62,193 @@ struct Mix {                   // composition-derived constants of a cell
 
 template <typename R> struct TV { R f, fx, fy, fxx, fyy, fxy; };
 
-// x-part of the bicubic Hermite evaluation (x = ln n_e): cell, fraction and
-// the cubic Hermite basis (value at 0, slope at 0, value at 1, slope at 1)
-// with its first and second derivatives.  Constant during a Newton inversion
-// (rho and the composition are fixed), so it is computed once per cell.
+// Quintic Hermite basis on [0, 1]: h[a][q] has q-th derivative 1 at end a and
+// value, first and second derivative 0 otherwise at both ends; d, e are its
+// first and second derivatives.  At end 1 the functions are (-1)^q times those
+// of end 0 at 1 - u.  D selects what is formed: 0 values, 1 + first, 2 + second.
+template <typename R, int D>
+__device__ __forceinline__ void quintic(R u, R h[2][3], R d[2][3], R e[2][3]) {
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const R w = a == 0 ? u : R(1) - u;
+    const R w2 = w * w, w3 = w2 * w;
+    h[a][0] = R(1) + w3 * (R(-10) + w * (R(15) - R(6) * w));
+    h[a][1] = w + w3 * (R(-6) + w * (R(8) - R(3) * w));
+    h[a][2] = R(0.5) * w2 * (R(1) + w * (R(-3) + w * (R(3) - w)));
+    if (D >= 1) {
+      d[a][0] = w2 * (R(-30) + w * (R(60) - R(30) * w));
+      d[a][1] = R(1) + w2 * (R(-18) + w * (R(32) - R(15) * w));
+      d[a][2] = w * (R(1) + w * (R(-4.5) + w * (R(6) - R(2.5) * w)));
+    }
+    if (D >= 2) {
+      e[a][0] = w * (R(-60) + w * (R(180) - R(120) * w));
+      e[a][1] = w * (R(-36) + w * (R(96) - R(60) * w));
+      e[a][2] = R(1) + w * (R(-9) + w * (R(18) - R(10) * w));
+    }
+    if (a == 1) {   // (-1)^q, and d/du = -d/dw on the first derivative
+      h[1][1] = -h[1][1];
+      if (D >= 1) { d[1][0] = -d[1][0]; d[1][2] = -d[1][2]; }
+      if (D >= 2) e[1][1] = -e[1][1];
+    }
+  }
+}
+
+// Difference form of a tensor product.  The 2 x 2 corner values c[a][b] of
+// a quantity enter as sum c[a][b] X_a Y_b = sum D[a][b] X~_a Y~_b with
+// D00 = c00, D10 = c10 - c00, D01 = c01 - c00, D11 = (c11 - c10) - (c01 - c00),
+// X~_0 = X_0 + X_1, X~_1 = X_1 (the same in y): an identity, in which the
+// value functions' X~_0 is exactly 1 (value) or 0 (derivatives).  It keeps a
+// derivative from cancelling two large node values (f_y from f alone would
+// lose ~|f| / dy to rounding).
+template <typename R>
+__device__ __forceinline__ void diff_basis(R b[2][3], R first) {
+  b[0][0] = first;
+  b[0][1] += b[1][1];
+  b[0][2] += b[1][2];
+}
+
+// x-part (x = ln n_e), fixed during an inversion: cell and the quintic basis
+// in difference form, with dx^p folded into order p (value), dx^(p-1) (first
+// derivative) and dx^(p-2) (second), so contracted values are physical
+// derivatives.
 template <typename R> struct XB {
   int i;
   bool ok;
-  R hu[4], du[4], eu[4];
+  R h[2][3], d[2][3], e[2][3];
 };
 
 template <typename R>
 __device__ __forceinline__ XB<R> xbasis(const Table &t, R x) {
   XB<R> X;
   const R x0 = sizeof(R) == 8 ? (R)t.x0 : (R)t.x0f, idx = sizeof(R) == 8 ? (R)t.idx : (R)t.idxf;
+  const R dx = sizeof(R) == 8 ? (R)t.dx : (R)t.dxf;
   const R gx = (x - x0) * idx;
   X.ok = gx >= R(0) && gx <= R(t.nx - 1);
   int i = X.ok ? (int)gx : 0;
   if (i > t.nx - 2) i = t.nx - 2;
   X.i = i;
-  const R u = gx - (R)i;
-  const R u2 = u * u, u3 = u2 * u;
-  X.hu[0] = R(2) * u3 - R(3) * u2 + R(1); X.hu[1] = u3 - R(2) * u2 + u;
-  X.hu[2] = R(-2) * u3 + R(3) * u2;       X.hu[3] = u3 - u2;
-  X.du[0] = R(6) * u2 - R(6) * u;          X.du[1] = R(3) * u2 - R(4) * u + R(1);
-  X.du[2] = R(-6) * u2 + R(6) * u;         X.du[3] = R(3) * u2 - R(2) * u;
-  X.eu[0] = R(12) * u - R(6);              X.eu[1] = R(6) * u - R(4);
-  X.eu[2] = R(-12) * u + R(6);             X.eu[3] = R(6) * u - R(2);
+  quintic<R, 2>(gx - (R)i, X.h, X.d, X.e);
+  diff_basis<R>(X.h, R(1));
+  diff_basis<R>(X.d, R(0));
+  diff_basis<R>(X.e, R(0));
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    X.h[a][1] *= dx; X.h[a][2] *= dx * dx;
+    X.d[a][0] *= idx; X.d[a][2] *= dx;
+    X.e[a][0] *= idx * idx; X.e[a][1] *= idx;
+  }
   return X;
 }
 
-// Bicubic Hermite evaluation of the free energy and its derivatives at
-// (x, y = ln T) given the x-part (FULL = false: only f, f_y, f_yy, which is
-// what e and c_v need).
-template <typename R, bool FULL = true>
-__device__ __forceinline__ bool table_eval_xb(const Table &t, const XB<R> &X, R y, TV<R> &o) {
-  const R dx = sizeof(R) == 8 ? (R)t.dx : (R)t.dxf, idx = sizeof(R) == 8 ? (R)t.idx : (R)t.idxf;
-  const R y0 = sizeof(R) == 8 ? (R)t.y0 : (R)t.y0f, dy = sizeof(R) == 8 ? (R)t.dy : (R)t.dyf;
-  const R idy = sizeof(R) == 8 ? (R)t.idy : (R)t.idyf;
-  const R gy = (y - y0) * idy;
-  if (!(X.ok && gy >= R(0) && gy <= R(t.ny - 1))) return false;
-  const int i = X.i;
-  int j = (int)gy;
-  if (j > t.ny - 2) j = t.ny - 2;
-  const R v = gy - (R)j;
-  const R v2 = v * v, v3 = v2 * v;
-  const R hv[4] = {R(2) * v3 - R(3) * v2 + R(1), v3 - R(2) * v2 + v, R(-2) * v3 + R(3) * v2, v3 - v2};
-  const R dv[4] = {R(6) * v2 - R(6) * v, R(3) * v2 - R(4) * v + R(1), R(-6) * v2 + R(6) * v, R(3) * v2 - R(2) * v};
-  const R ev[4] = {R(12) * v - R(6), R(6) * v - R(4), R(-12) * v + R(6), R(6) * v - R(2)};
-  const R *hu = X.hu, *du = X.du, *eu = X.eu;
-  R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+// The x-contracted values of one y-interval, in difference form along y:
+// g[m][r] = d^m/dx^m d^r/dy^r f at (x, y_j) and dg[m][r] the same at y_(j+1)
+// minus that at y_j (contracted from node differences), m < M.
+template <typename R, int M> struct YC {
+  int j;
+  R g[M][3], dg[M][3];
+};
+
+template <typename R, int M>
+__device__ __forceinline__ void contract(const Table &t, const XB<R> &X, int j, YC<R, M> &c) {
+  c.j = j;
+  const long k0 = ((long)j * t.nx + X.i) * NQ, k1 = k0 + (long)t.nx * NQ;
+  R q[2][2][NQ];   // [b][a][slot]
 #pragma unroll
-  for (int cb = 0; cb < 2; ++cb)
+  for (int b = 0; b < 2; ++b)
 #pragma unroll
-    for (int ca = 0; ca < 2; ++ca) {
-      const long k = ((long)(j + cb) * t.nx + (i + ca)) * 4;
-      R q0, q1, q2, q3;
-      if (sizeof(R) == 8) { q0 = (R)t.v[k]; q1 = (R)t.v[k + 1]; q2 = (R)t.v[k + 2]; q3 = (R)t.v[k + 3]; }
-      else { q0 = (R)t.vf[k]; q1 = (R)t.vf[k + 1]; q2 = (R)t.vf[k + 2]; q3 = (R)t.vf[k + 3]; }
-      const R c0 = q0, c1 = q1 * dx, c2 = q2 * dy, c3 = q3 * dx * dy;
-      const int iv = 2 * ca, is = 2 * ca + 1, jv = 2 * cb, js = 2 * cb + 1;
-      a0 += c0 * hu[iv] * hv[jv] + c1 * hu[is] * hv[jv] + c2 * hu[iv] * hv[js] + c3 * hu[is] * hv[js];
-      a2 += c0 * hu[iv] * dv[jv] + c1 * hu[is] * dv[jv] + c2 * hu[iv] * dv[js] + c3 * hu[is] * dv[js];
-      a4 += c0 * hu[iv] * ev[jv] + c1 * hu[is] * ev[jv] + c2 * hu[iv] * ev[js] + c3 * hu[is] * ev[js];
-      if (FULL) {
-        a1 += c0 * du[iv] * hv[jv] + c1 * du[is] * hv[jv] + c2 * du[iv] * hv[js] + c3 * du[is] * hv[js];
-        a3 += c0 * eu[iv] * hv[jv] + c1 * eu[is] * hv[jv] + c2 * eu[iv] * hv[js] + c3 * eu[is] * hv[js];
-        a5 += c0 * du[iv] * dv[jv] + c1 * du[is] * dv[jv] + c2 * du[iv] * dv[js] + c3 * du[is] * dv[js];
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int s = 0; s < NQ; ++s) {
+        const long k = (b ? k1 : k0) + a * NQ + s;
+        q[b][a][s] = sizeof(R) == 8 ? (R)t.v[k] : (R)t.vf[k];
+      }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    R g0 = R(0), g1 = R(0), g2 = R(0), d0 = R(0), d1 = R(0), d2 = R(0);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int sl = qslot(p, r);
+      const R D00 = q[0][0][sl], D10 = q[0][1][sl] - q[0][0][sl], D01 = q[1][0][sl] - q[0][0][sl];
+      const R D11 = (q[1][1][sl] - q[0][1][sl]) - (q[1][0][sl] - q[0][0][sl]);
+      g0 += D00 * X.h[0][p] + D10 * X.h[1][p];
+      d0 += D01 * X.h[0][p] + D11 * X.h[1][p];
+      if (M > 1) {
+        g1 += D00 * X.d[0][p] + D10 * X.d[1][p];
+        d1 += D01 * X.d[0][p] + D11 * X.d[1][p];
+      }
+      if (M > 2) {
+        g2 += D00 * X.e[0][p] + D10 * X.e[1][p];
+        d2 += D01 * X.e[0][p] + D11 * X.e[1][p];
       }
     }
-  o.f = a0;
-  o.fx = a1 * idx;
-  o.fy = a2 * idy;
-  o.fxx = a3 * (idx * idx);
-  o.fyy = a4 * (idy * idy);
-  o.fxy = a5 * (idx * idy);
+    c.g[0][r] = g0; c.dg[0][r] = d0;
+    if (M > 1) { c.g[1][r] = g1; c.dg[1][r] = d1; }
+    if (M > 2) { c.g[2][r] = g2; c.dg[2][r] = d2; }
+  }
+}
+
+// Interval index of y and its fraction; false outside the table.
+template <typename R>
+__device__ __forceinline__ bool yloc(const Table &t, R y, int &j, R &v) {
+  const R y0 = sizeof(R) == 8 ? (R)t.y0 : (R)t.y0f, idy = sizeof(R) == 8 ? (R)t.idy : (R)t.idyf;
+  const R gy = (y - y0) * idy;
+  if (!(gy >= R(0) && gy <= R(t.ny - 1))) return false;
+  j = (int)gy;
+  if (j > t.ny - 2) j = t.ny - 2;
+  v = gy - (R)j;
   return true;
 }
 
-template <typename R, bool FULL = true>
+// f, f_y, f_yy (M = 1) and also f_x, f_xy (M >= 2), f_xx (M = 3) at fraction
+// v of the interval the contraction holds.
+template <typename R, int M>
+__device__ __forceinline__ void yeval(const Table &t, const YC<R, M> &c, R v, TV<R> &o) {
+  const R dy = sizeof(R) == 8 ? (R)t.dy : (R)t.dyf, idy = sizeof(R) == 8 ? (R)t.idy : (R)t.idyf;
+  R h[2][3], d[2][3], e[2][3];
+  quintic<R, 2>(v, h, d, e);
+  diff_basis<R>(h, R(1));
+  diff_basis<R>(d, R(0));
+  diff_basis<R>(e, R(0));
+  R a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, c0 = 0;
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const R sh[3] = {h[b][0], h[b][1] * dy, h[b][2] * dy * dy};
+    const R sd[3] = {d[b][0] * idy, d[b][1], d[b][2] * dy};
+    const R se[3] = {e[b][0] * idy * idy, e[b][1] * idy, e[b][2]};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const R g0 = b ? c.dg[0][r] : c.g[0][r];
+      a0 += g0 * sh[r];
+      a1 += g0 * sd[r];
+      a2 += g0 * se[r];
+      if (M > 1) {
+        const R g1 = b ? c.dg[1][r] : c.g[1][r];
+        b0 += g1 * sh[r];
+        b1 += g1 * sd[r];
+      }
+      if (M > 2) c0 += (b ? c.dg[2][r] : c.g[2][r]) * sh[r];
+    }
+  }
+  o.f = a0; o.fy = a1; o.fyy = a2;
+  o.fx = b0; o.fxy = b1; o.fxx = c0;
+}
+
+// Biquintic evaluation of f and its derivatives up to second order at
+// (x, y = ln T) given the x-part.
+template <typename R>
+__device__ __forceinline__ bool table_eval_xb(const Table &t, const XB<R> &X, R y, TV<R> &o) {
+  int j;
+  R v;
+  if (!(X.ok && yloc<R>(t, y, j, v))) return false;
+  YC<R, 3> c;
+  contract<R, 3>(t, X, j, c);
+  yeval<R, 3>(t, c, v, o);
+  return true;
+}
+
+template <typename R>
 __device__ __forceinline__ bool table_eval(const Table &t, R x, R y, TV<R> &o) {
-  return table_eval_xb<R, FULL>(t, xbasis<R>(t, x), y, o);
+  return table_eval_xb<R>(t, xbasis<R>(t, x), y, o);
 }
 
 template <typename R> struct EosOut { R P, e, cv, Pr, PT, ge, gc; };
@@ -174,10 +296,17 @@ __device__ __forceinline__ bool eos_rt(const Table &t, R rho, R T, R abar, R ye,
 }
 
 // Specific internal energy and c_v at (rho, T): what a Newton iteration needs.
+// c holds the x-contraction of the current table interval and is redone when
+// T has left it.
 template <typename R>
-__device__ __forceinline__ bool eos_ecv_xy(const Table &t, const XB<R> &X, R irho, R T, R lnT, R iab, R &e, R &cv) {
+__device__ __forceinline__ bool eos_ecv_xy(const Table &t, const XB<R> &X, YC<R, 1> &c, R irho, R T, R lnT, R iab,
+                                           R &e, R &cv) {
+  int j;
+  R v;
+  if (!(X.ok && yloc<R>(t, lnT, j, v))) return false;
+  if (j != c.j) contract<R, 1>(t, X, j, c);
   TV<R> q;
-  if (!table_eval_xb<R, false>(t, X, lnT, q)) return false;
+  yeval<R, 1>(t, c, v, q);
   const R iT = R(1) / T;
   const R Rg = R(RGAS);
   R aT4, aT3;
@@ -196,7 +325,9 @@ __device__ __forceinline__ bool eos_ecv_xy(const Table &t, const XB<R> &X, R irh
 
 template <typename R>
 __device__ __forceinline__ bool eos_ecv(const Table &t, R rho, R T, R abar, R ye, R &e, R &cv) {
-  return eos_ecv_xy<R>(t, xbasis<R>(t, log(rho * ye * R(NAV))), R(1) / rho, T, log(T), R(1) / abar, e, cv);
+  YC<R, 1> c;
+  c.j = -1;
+  return eos_ecv_xy<R>(t, xbasis<R>(t, log(rho * ye * R(NAV))), c, R(1) / rho, T, log(T), R(1) / abar, e, cv);
 }
 
 // ln Tn from ln T for a Newton step T -> Tn: with d = (Tn - T) / T below
@@ -221,9 +352,11 @@ __device__ __forceinline__ int newton_loop(const Table &t, const XB<R> &X, R rho
   R lo = Tlo, hi = Thi;
   if (!(T > Tlo && T < Thi)) { T = sqrt(Tlo * Thi); have = false; }
   R lnT = have ? lnT0 : log(T);   // e0, cv0 were evaluated at (T, lnT0)
+  YC<R, 1> c;
+  c.j = -1;
   for (int it = 1; it <= maxit; ++it) {
     R e = e0, cv = cv0;   // the first iteration may come evaluated
-    if (!(have && it == 1) && !eos_ecv_xy<R>(t, X, irho, T, lnT, iab, e, cv)) return -1;
+    if (!(have && it == 1) && !eos_ecv_xy<R>(t, X, c, irho, T, lnT, iab, e, cv)) return -1;
     const R de = eint - e;
     if (fabs(de) < tol * fabs(eint)) {
       const R Tn = T + de / cv;
@@ -257,9 +390,11 @@ __device__ __forceinline__ int newton_fp32(const Table &t, float rho, float eint
   if (!(T > Tlo && T < Thi)) T = sqrtf(Tlo * Thi);
   const XB<float> X = xbasis<float>(t, logf(rho * ye * float(NAV)));
   const float irho = 1.0f / rho, iab = 1.0f / abar;
+  YC<float, 1> c;
+  c.j = -1;
   for (int it = 1; it <= maxit; ++it) {
     float e, cv;
-    if (!eos_ecv_xy<float>(t, X, irho, T, logf(T), iab, e, cv)) return -1;
+    if (!eos_ecv_xy<float>(t, X, c, irho, T, logf(T), iab, e, cv)) return -1;
     const float de = eint - e;
     if (de > 0.0f) lo = T; else hi = T;
     float Tn = T + de / cv;
@@ -286,9 +421,11 @@ __device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, doub
   const double irho = 1.0 / rho, iab = 1.0 / abar;
   {
     double e, cv;
+    YC<double, 1> c;
+    c.j = -1;
     if (T > t.Tlo && T < t.Thi) {
       const double lnT = log(T);
-      if (eos_ecv_xy<double>(t, X, irho, T, lnT, iab, e, cv) && fabs(eint - e) < 1e-4 * fabs(eint))
+      if (eos_ecv_xy<double>(t, X, c, irho, T, lnT, iab, e, cv) && fabs(eint - e) < 1e-4 * fabs(eint))
         return newton_loop<double>(t, X, rho, irho, eint, iab, T, tol, maxit, o, true, e, cv, lnT);
     }
   }

@@ -44,24 +44,32 @@ def rel_linf(a, b):
 
 
 def test_table_nodes_match_oracle(tables):
-    """Both quadratures converge to rounding, so the nodes agree to 1e-12
-    where nothing cancels.  f = n mu - P (hot pairs), f_x = n eta k T (eta
-    crossing 0), f_y = -T s and f_xy = n k T (eta + b d eta/d b) (strongly
-    degenerate electrons, T s / (n mu) ~ (pi / eta)^2) are small differences of
-    terms of size |f| + |f_x| in parts of the table: there each side's
-    rounding of those terms bounds the agreement (2e-13 of |f| + |f_x|)."""
+    """The device and the oracle compute the nine node values of the
+    biquintic table (f and its derivatives up to f_xxyy) by different routes:
+    the device by implicit differentiation of charge neutrality with the
+    quadrature moments, the oracle by truncated Taylor arithmetic.  Where
+    something cancels -- f_x = n eta k T with eta crossing 0 for hot pairs,
+    and for strongly degenerate electrons the temperature derivatives, small
+    differences (relative size (pi / eta)^2) of terms of size |f| + |f_x| --
+    each side's rounding of those terms bounds the agreement.  Over the
+    stellar box's range (T >= 1e8 K, rho Y_e <= 1e7) that is 2e-13 of
+    |f| + |f_x|; at the cold, dense corner (eta ~ 2500), where the oracle's
+    Taylor coefficients in the Fermi-edge shift lose the most, 1e-10."""
     dt, ot = tables
     a, b = dt.export(), ot.export()
     assert a.shape == b.shape
     assert np.array_equal(a[:6], b[:6])
-    n = (a.size - 6) // 4
-    va, vb = a[6:].reshape(n, 4), b[6:].reshape(n, 4)
-    big = np.abs(vb[:, 0]) + np.abs(vb[:, 1])
-    for c in range(4):
-        err = np.abs(va[:, c] - vb[:, c])
-        bound = 1e-12 * np.abs(vb[:, c]) + 2e-13 * big
-        worst = int(np.argmax(err / bound))
-        assert (err <= bound).all(), (c, worst, va[worst, c], vb[worst, c])
+    nx, ny = int(b[0]), int(b[1])
+    va, vb = a[6:].reshape(ny, nx, 9), b[6:].reshape(ny, nx, 9)
+    lrye = (b[2] + b[3] * np.arange(nx)) / np.log(10.0) - np.log10(6.02214076e23)
+    lT = (b[4] + b[5] * np.arange(ny)) / np.log(10.0)
+    box = (lT[:, None] >= 8.0 - 1e-9) & (lrye[None, :] <= 7.0 + 1e-9)
+    big = np.abs(vb[..., 0]) + np.abs(vb[..., 1])
+    for c in range(9):
+        err = np.abs(va[..., c] - vb[..., c])
+        bound = 1e-12 * np.abs(vb[..., c]) + np.where(box, 2e-13, 1e-10) * big
+        worst = np.unravel_index(int(np.argmax(err / bound)), err.shape)
+        assert (err <= bound).all(), (c, worst, va[worst + (c,)], vb[worst + (c,)])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -89,8 +97,8 @@ def test_batch_inversion_vs_oracle(P, tables, precision):
     assert np.abs(Tref / T - 1).max() < 1e-9
     # T, P, gamma_e use first derivatives of f, which the two tables hold to
     # ~1e-13; gamma_c also uses f_xx, f_yy, f_xy, whose node values agree only
-    # to ~1e-13 of |f| + |f_x| (the cancellations of the strongly degenerate
-    # corner), so its bar is wider.
+    # to ~1e-13 of |f| + |f_x| where they are small differences, so its bar is
+    # wider.
     tol = 1e-11
     assert np.abs(out["T"] / Tref - 1).max() <= tol, np.abs(out["T"] / Tref - 1).max()
     for k, ref, t in (("P", Pref, tol), ("gamma_e", ge, tol), ("gamma_c", gc, 1e-9)):

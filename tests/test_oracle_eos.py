@@ -24,7 +24,7 @@ A, Z = [16.0, 28.0], [8.0, 14.0]
 
 @pytest.fixture(scope="module")
 def table():
-    return O.EosTable(nrho=321, nT=241)
+    return O.EosTable(nrho=321, nT=241)   # 80 nodes per decade in rho Y_e and T
 
 
 @pytest.mark.parametrize("k", [0.5, 1.5, 2.5])
@@ -90,19 +90,102 @@ def test_complete_degeneracy_chandrasekhar():
     assert abs(r["P"] / p_chandra - 1) < 1e-5, (r["P"], p_chandra)
 
 
+def _points():
+    """The stellar box's range on a grid, plus seeded points over the table."""
+    pts = [(rho, T) for rho in (1e5, 3e5, 1e6, 3e6, 1e7) for T in (1.1e8, 4e8, 1.3e9, 3e9)]
+    rng = np.random.default_rng(1)
+    pts += [(10 ** rng.uniform(4.3, 7.9), 10 ** rng.uniform(7.2, 9.95)) for _ in range(24)]
+    return pts
+
+
 def test_table_vs_direct_quadrature(table):
+    """Biquintic Hermite interpolation of the free energy (Sect. 2.2) at 80
+    nodes per decade against the exact derivatives of the integrals at the
+    same points: first-derivative quantities O(h^5), second-derivative ones
+    (c_v, gamma_c, dP/drho, dP/dT) O(h^4)."""
     cfg = O.stellar_cfg(A, Z, table)
     cfgd = O.stellar_cfg(A, Z, None)
     worst = {}
-    for rho in (1e5, 3e5, 1e6, 3e6, 1e7):
-        for T in (1.1e8, 4e8, 1.3e9, 3e9):
-            a, b = O.eos_rt(cfg, rho, T, X), O.eos_rt(cfgd, rho, T, X)
-            for k in ("P", "e", "gamma_e", "gamma_c", "cv"):
-                worst[k] = max(worst.get(k, 0), abs(a[k] - b[k]) / abs(b[k]))
-    # bicubic Hermite of the free energy, 80 nodes per decade: first-derivative
-    # quantities O(h^3), second-derivative quantities O(h^2)
-    assert worst["P"] < 5e-6 and worst["e"] < 5e-5 and worst["gamma_e"] < 1e-5, worst
-    assert worst["cv"] < 2e-3 and worst["gamma_c"] < 2e-3, worst
+    for rho, T in _points():
+        a, b = O.eos_rt(cfg, rho, T, X), O.eos_rt(cfgd, rho, T, X)
+        for k in ("P", "e", "gamma_e", "gamma_c", "cv", "dPdT", "dPdr"):
+            worst[k] = max(worst.get(k, 0), abs(a[k] - b[k]) / abs(b[k]))
+    assert worst["P"] < 1e-8 and worst["e"] < 1e-8 and worst["gamma_e"] < 1e-8, worst
+    for k in ("cv", "gamma_c", "dPdT", "dPdr"):
+        assert worst[k] < 1e-6, worst
+
+
+def test_interpolation_order():
+    """Halving the node spacing divides the interpolation error of first-
+    derivative quantities by ~2^5 and of second-derivative ones by ~2^4 (a
+    bicubic table would give 2^3 and 2^2)."""
+    cfgd = O.stellar_cfg(A, Z, None)
+    rng = np.random.default_rng(3)
+    pts = [(10 ** rng.uniform(5.2, 6.8) / 0.5, 10 ** rng.uniform(8.6, 9.4)) for _ in range(12)]
+    ref = [O.eos_rt(cfgd, r, T, X) for r, T in pts]
+    err = []
+    for per in (20, 40):
+        tb = O.EosTable(lrhoye=(5.0, 7.0), nrho=2 * per + 1, lT=(8.5, 9.5), nT=per + 1)
+        cfg = O.stellar_cfg(A, Z, tb)
+        w = {}
+        for (r, T), b in zip(pts, ref):
+            a = O.eos_rt(cfg, r, T, X)
+            for k in ("e", "gamma_e", "cv", "gamma_c"):
+                w[k] = max(w.get(k, 0), abs(a[k] - b[k]) / abs(b[k]))
+        err.append(w)
+    for k in ("e", "gamma_e"):
+        assert err[0][k] / err[1][k] > 16, (k, err)
+    for k in ("cv", "gamma_c"):
+        assert err[0][k] / err[1][k] > 11, (k, err)
+
+
+def test_table_reproduces_direct_values_at_nodes():
+    """At a node the interpolant takes the node's f and its derivatives, so
+    the EOS there equals the direct evaluation to rounding."""
+    tb = O.EosTable(lrhoye=(5.0, 7.0), nrho=21, lT=(8.5, 9.5), nT=11)
+    cfg, cfgd = O.stellar_cfg(A, Z, tb), O.stellar_cfg(A, Z, None)
+    ye = 0.5
+    for i, j in ((3, 2), (10, 5), (17, 9)):
+        rho = 10 ** (5.0 + 0.1 * i) / ye
+        T = 10 ** (8.5 + 0.1 * j)
+        a, b = O.eos_rt(cfg, rho, T, X), O.eos_rt(cfgd, rho, T, X)
+        for k in ("P", "e", "cv", "dPdT", "dPdr", "gamma_c"):
+            assert abs(a[k] - b[k]) <= 1e-11 * abs(b[k]), (k, a[k], b[k])
+
+
+@pytest.mark.parametrize("rho,T", [(1e5, 1e8), (3e6, 1.3e9), (1e7, 3e9), (2e4, 1e10), (2e8, 1e8)])
+def test_taylor_derivatives_match_direct_combinations(rho, T):
+    """The table's node values come from truncated Taylor arithmetic; f,
+    f_x = n eta k T, f_y = -T s and f_xy = n k T (eta + d eta/d ln T) also
+    follow from their own combinations of the integrals (P, E, s and
+    dn/db).  For degenerate electrons f_y and f_xy are small differences
+    (relative size (pi / eta)^2) of terms of size |f| + |f_x|: there the
+    rounding of those terms bounds the agreement."""
+    n = rho * 0.5 * N_A
+    d, f = O.ep_derivs(n, T), O.ep_first(n, T)
+    big = abs(f[0]) + abs(f[1])
+    for i, j in ((0, 0), (1, 1), (2, 2), (5, 3)):
+        assert abs(d[i] - f[j]) <= 1e-12 * abs(f[j]) + 1e-14 * big, (i, d[i], f[j])
+
+
+@pytest.mark.parametrize("rho,T", [(1e5, 1e8), (3e6, 1.3e9), (1e7, 3e9), (2e4, 1e10)])
+def test_taylor_higher_derivatives_vs_finite_differences(rho, T):
+    """f_xx, f_yy, f_xxy, f_xyy, f_xxyy against fourth-order central
+    differences (step 0.002 in ln n or ln T, truncation error ~1e-10) of the
+    lower derivatives."""
+    n = rho * 0.5 * N_A
+    h = 2e-3
+    d = O.ep_derivs(n, T)
+
+    def fd(fun):
+        return (-fun(2 * h) + 8 * fun(h) - 8 * fun(-h) + fun(-2 * h)) / (12 * h)
+
+    dx = lambda k: fd(lambda s: O.ep_derivs(n * math.exp(s), T)[k])
+    dy = lambda k: fd(lambda s: O.ep_derivs(n, T * math.exp(s))[k])
+    # (index, finite difference): f_xx = d_x f_x, f_yy = d_y f_y,
+    # f_xxy = d_x f_xy, f_xyy = d_y f_xy, f_xxyy = d_y f_xxy
+    for i, v in ((3, dx(1)), (4, dy(2)), (6, dx(5)), (7, dy(5)), (8, dy(6))):
+        assert abs(d[i] - v) <= 5e-9 * abs(d[i]), (i, d[i], v)
 
 
 def test_thermodynamic_consistency_of_the_table(table):

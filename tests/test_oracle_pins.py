@@ -592,3 +592,57 @@ def test_brio_wu_pqh_flattening_damps_oscillations():
     assert tv(raw) - tv(ref) > 1.5 * (tv(flat) - tv(ref)) > 0.0, (tv(raw), tv(flat), tv(ref))
     for r in (raw, flat):
         assert np.abs(r - ref).mean() < 3e-3
+
+
+# ---------------------------------------------------------------------------
+# Contact-CT upwinding of the corner EMF and its deadband (Sect. 2.4)
+# ---------------------------------------------------------------------------
+
+def _corner_weights(F, rho=1.0, smax=1.0, seed=0):
+    """d E_corner / d E_cell for the four cells (E00, E10, E01, E11), by
+    perturbing each cell's reference EMF (the corner EMF is linear in them)."""
+    rng = np.random.default_rng(seed)
+    Ef = rng.normal(size=4)
+    Ec = rng.normal(size=4)
+    e0 = O.ct_corner(Ef, Ec, F, rho, smax)
+    w = []
+    for q in range(4):
+        d = Ec.copy()
+        d[q] += 1.0
+        w.append(O.ct_corner(Ef, d, F, rho, smax) - e0)
+    return e0, np.array(w)
+
+
+def test_ct_corner_rounding_level_mass_flux_has_no_direction():
+    """A mass flux at the rounding level of the face's flux scale (here
+    |F_rho| = 1e-14 rho max|S|, either sign) carries no direction: the corner
+    EMF equals the one with exactly zero mass fluxes, and the four cells enter
+    it symmetrically (weight -1/4 each, Gardiner & Stone's zero-flux case)."""
+    e_zero, w_zero = _corner_weights(np.zeros(4))
+    np.testing.assert_allclose(w_zero, -0.25, rtol=0, atol=1e-15)
+    for signs in ((1, 1, 1, 1), (-1, 1, -1, 1), (1, -1, -1, 1), (-1, -1, -1, -1)):
+        F = 1e-14 * np.array(signs, dtype=float)
+        e, w = _corner_weights(F)
+        assert e == e_zero, (signs, e, e_zero)
+        np.testing.assert_array_equal(w, w_zero)
+
+
+@pytest.mark.parametrize("scale", [1e-10, 1e-6, 1.0])
+def test_ct_corner_takes_the_upwind_side(scale):
+    """Above the deadband each half-cell derivative comes from the upwind
+    cell of its face: with every mass flux positive (flow towards +a and +b)
+    the corner EMF does not depend on the downwind cell (c_a, c_b) and does
+    on the upwind one (c_a - 1, c_b - 1); negative fluxes swap them.  The
+    density and signal speed set the band (1e-12 rho max|S|): the same flux
+    below it has no direction."""
+    for rho, smax in ((1.0, 1.0), (3e7, 2e8)):
+        F = scale * rho * smax * np.ones(4)
+        _, wp = _corner_weights(F, rho, smax)
+        assert wp[3] == 0.0 and wp[0] != 0.0, wp
+        _, wm = _corner_weights(-F, rho, smax)
+        assert wm[0] == 0.0 and wm[3] != 0.0, wm
+        # the mixed cells are upwind of one face each
+        assert wp[1] != 0.0 and wp[2] != 0.0 and wm[1] != 0.0 and wm[2] != 0.0
+    # just below the band the same configuration is direction-free
+    _, w = _corner_weights(1e-13 * np.ones(4))
+    np.testing.assert_allclose(w, -0.25, rtol=0, atol=1e-15)
