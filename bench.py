@@ -210,11 +210,14 @@ def time_form(P, pr, form, steps, warmup, stream, ws, fused=-1):
     return g, ms, kt, st
 
 
-def roofline(kt, pr, form, hbm_peak, peak_kind):
-    """Dominant kernel (largest summed device time) against its bound."""
+def roofline(kt, pr, form, hbm_peak, peak_kind, alu):
+    """Dominant kernel (largest summed device time) against its bound.  alu:
+    the FMA throughputs measured on this GPU by the library's probe
+    (phl_probe_alu) in TFLOP/s, {"fp32": .., "fp64": ..}."""
     name, (launches, ms) = max(kt.items(), key=lambda kv: kv[1][1])
     avg_ms = ms / max(launches, 1)
     ncells = pr.ncells
+    fp32_peak, fp64_peak = alu["fp32"], alu["fp64"]
     if name == "stage_mixed":
         per_launch = ncells * sum(BYTES_PER_CELL_STAGE.values()) / 3.0
         achieved = per_launch / (avg_ms * 1e-3) / 1e9
@@ -227,23 +230,24 @@ def roofline(kt, pr, form, hbm_peak, peak_kind):
         flop = FUSED_FLOP_PER_CELL
         achieved = ncells * flop / (avg_ms * 1e-3) / 1e12
         traffic = ncells * FUSED_DRAM_BYTES_PER_CELL
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP32_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_NOMINAL_TFLOPS, "traffic": traffic,
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                 "traffic_note": "bytes per launch: ncu DRAM bytes per cell at 160^3 (RK3 mean) x cells",
-                "peak_kind": "nominal FP32 (152 SM x 128 lanes x 2 x 2.07 GHz)",
+                "peak_kind": "measured FP32 FFMA rate (phl_probe_alu, this run)",
+                "nominal_peak": FP32_NOMINAL_TFLOPS, "frac_of_nominal": achieved / FP32_NOMINAL_TFLOPS,
                 "flop_per_cell": flop, "avg_launch_ms": avg_ms, "launches": launches}
     if name.startswith("flux"):
         n = pr.n[0]
         faces = (n + 1) * (n + 2) * (n + 2)
         fp64 = form == "fp64"
         flop = FP64_FLOP_PER_FACE if fp64 else FP32_FLOP_PER_FACE[name]
-        peak = FP64_NOMINAL_TFLOPS if fp64 else FP32_NOMINAL_TFLOPS
+        peak = fp64_peak if fp64 else fp32_peak
         achieved = faces * flop / (avg_ms * 1e-3) / 1e12
         traffic = None if fp64 else faces * FP32_DRAM_BYTES_PER_FACE[name]
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_note": None if fp64 else "bytes per launch: ncu DRAM bytes per face at 160^3 x faces",
-                "peak_kind": "nominal FP64 (recipe)" if fp64 else "nominal FP32 (152 SM x 128 lanes x 2.07 GHz)",
+                "peak_kind": "measured FP64 DFMA rate (phl_probe_alu)" if fp64 else "measured FP32 FFMA rate (phl_probe_alu)",
                 "flop_per_face": flop, "avg_launch_ms": avg_ms, "launches": launches}
     # HBM view of the whole stage for any other dominant kernel
     stage_ms = sum(v[1] for v in kt.values()) / max(kt.get("update_cells", (1, 0))[0], 1)
@@ -254,14 +258,33 @@ def roofline(kt, pr, form, hbm_peak, peak_kind):
             "avg_launch_ms": avg_ms, "launches": launches, "note": "whole-stage algorithmic bytes / stage time"}
 
 
+def kernel_hbm(kt, pr, hbm_peak, peak_kind):
+    """The dominant kernel against HBM: the stage's algorithmic bytes (170.7 B
+    per cell-stage: read the FP64 stage input and U^n, write the output) for
+    the cells one launch updates, over its average launch time."""
+    name, (launches, ms) = max(kt.items(), key=lambda kv: kv[1][1])
+    avg_ms = ms / max(launches, 1)
+    b = sum(BYTES_PER_CELL_STAGE.values()) / 3.0
+    gbs = pr.ncells * b / (avg_ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "bytes_per_cell_stage": b, "achieved": gbs, "peak": hbm_peak,
+            "unit": "GB/s", "frac": gbs / hbm_peak, "peak_kind": f"{peak_kind} HBM copy",
+            "avg_launch_ms": avg_ms}
+
+
 def stage_hbm(rate, form, hbm_peak, peak_kind):
-    """Whole stage against HBM: algorithmic bytes per cell-stage x rate.
-    FP64 form: read stage input + U^n, write output, FP64 (170.7 B average);
-    mixed form: FP64 U^n + FP32 increments (128 B average)."""
-    b = sum(BYTES_PER_CELL_STAGE.values()) / 3.0 if form == "fp64" else 128.0
+    """Whole stage against HBM: algorithmic bytes per cell-stage x rate, 170.7 B
+    (read the stage input, 5 cell + 3 face doubles, read U^n in stages 2-3,
+    write the output; the state is FP64 in both forms).  The mixed form keeps
+    its stage increments in FP32, so its own layout moves 128 B (U^n read,
+    increment read and written): reported beside it."""
+    b = sum(BYTES_PER_CELL_STAGE.values()) / 3.0
     gbs = rate * b / 1e9
-    return {"bytes_per_cell_stage": b, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-            "peak_kind": f"{peak_kind} HBM copy", "frac_of_8tbs": gbs / 8000.0}
+    out = {"bytes_per_cell_stage": b, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+           "peak_kind": f"{peak_kind} HBM copy", "frac_of_8tbs": gbs / 8000.0}
+    if form == "mixed":
+        out["mixed_layout_bytes_per_cell_stage"] = 128.0
+        out["mixed_layout_frac"] = rate * 128.0 / 1e9 / hbm_peak
+    return out
 
 
 def e2e_measure(P, g, pr, steps, form="mixed", fused=-1, inflight=3):
@@ -324,29 +347,65 @@ def e2e_measure(P, g, pr, steps, form="mixed", fused=-1, inflight=3):
             "steps": inflight * steps, "pipeline": f"{inflight} grids in flight (own stream and host thread each)"}
 
 
+def host_info():
+    """Core count and CPU model of the host the oracle runs on."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Architecture", "CPU(s)", "Thread(s) per core", "Socket(s)"):
+                info[k.strip()] = v.strip()
+    except Exception:
+        pass
+    return info
+
+
+# The paper's own CPU figure (context only, other hardware): 1.03 us per cell
+# per time step for the Godunov MHD update on one AMD EPYC 9554 core at 3.8 GHz
+# (32^3, PPH + LHLLD + SSP-RK3, EOS excluded): 3 stages per step.
+PAPER_CPU = {"value": 3.0 / 1.03e-6, "unit": UNIT, "cores": 1,
+             "hardware": "AMD EPYC 9554 @3.8 GHz, one core (the paper's figure: 1.03 us per cell per step)",
+             "note": "context only: another machine, PPH reconstruction, EOS excluded"}
+
+
 def oracle_sample(steps=2, nxy=64, nz=256):
-    """The CPU oracle as it stands, single thread, on a sample of the workload:
-    the same box physics on nxy x nxy x nz cells."""
+    """The CPU oracle as it stands, on a sample of the workload (the same box
+    physics on nxy x nxy x nz cells): single-threaded, and the same sources
+    built with OpenMP over all host cores (bit-identical results)."""
     import workloads as W
     import oracle as O
     pr = W.stratified_box(nxy, nxy, nz)
-    o = O.Oracle(pr)
-    t0 = time.perf_counter()
-    o.run(steps)
-    dt = time.perf_counter() - t0
-    return {"value": pr.ncells * STAGES * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nxy}x{nxy}x{nz} cells of the same box physics, {steps} SSP-RK3 steps, "
-                      f"{dt:.1f} s single-threaded FP64 C"}
+    legs = {}
+    for par in (False, True):
+        O.set_parallel(par)
+        o = O.Oracle(pr)
+        t0 = time.perf_counter()
+        o.run(steps)
+        legs[par] = time.perf_counter() - t0
+    O.set_parallel(False)
+    ncores = os.cpu_count()
+    one, allc = legs[False], legs[True]
+    return {"value": pr.ncells * STAGES * steps / allc, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": f"{nxy}x{nxy}x{nz} cells of the same box physics, {steps} SSP-RK3 steps: "
+                      f"{allc:.1f} s on all {ncores} host cores (OpenMP build of the same C), "
+                      f"{one:.1f} s single-threaded",
+            "single_thread": {"value": pr.ncells * STAGES * steps / one, "unit": UNIT, "cores": 1},
+            "host": host_info(), "paper_cpu_context": PAPER_CPU}
 
 
 def run_reference(args):
+    """The reference arm of this workload: the CPU oracle as it stands (the
+    OpenMP build of its C over all host cores), on a sample of the box (64 x 64
+    columns of the full height) per step."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import workloads as W
     import oracle as O
-    nxy = 32
+    O.set_parallel(True)
+    nxy = 64
     pr = W.stratified_box(nxy, nxy, args.n)
     o = O.Oracle(pr)
     st = None
@@ -357,14 +416,16 @@ def run_reference(args):
         st, _, _ = o.run(1, st)
     dt = time.perf_counter() - t0
     val = pr.ncells * STAGES * args.steps / dt
+    ncores = os.cpu_count()
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_cells": [nxy, nxy, args.n], "form": "oracle"},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{nxy}x{nxy}x{args.n} cells per step of the same box physics"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": f"{nxy}x{nxy}x{args.n} cells per step of the same box physics, "
+                                   f"OpenMP over {ncores} host cores", "host": host_info()},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -677,6 +738,7 @@ def main():
 
     hbm_peak, peak_kind = read_peaks()
     stream = torch.cuda.Stream()
+    alu = {k: P.probe_alu(k) for k in ("fp32", "fp64")}
     if args.sts_only:
         if rank == 0:
             print(json.dumps(diffusion_sts(P, args.n, stream, hbm_peak, peak_kind)))
@@ -709,7 +771,8 @@ def main():
             g.close()
     h = res[head]
     g = h["g"]
-    roof = roofline(h["kt"], pr, head, hbm_peak, peak_kind)
+    roof = roofline(h["kt"], pr, head, hbm_peak, peak_kind, alu)
+    roof_hbm = kernel_hbm(h["kt"], pr, hbm_peak, peak_kind)
     e2e = e2e_measure(P, g, pr, args.e2e_steps, head, args.fused)
     g.close()
     cpu = None
@@ -764,6 +827,8 @@ def main():
                    "forms_timed": forms, "stages_per_step": STAGES, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (state 1.07 GB per copy, no flush)"},
         "roofline": roof,
+        "roofline_hbm": roof_hbm,
+        "alu_peaks_measured": alu,
         "forms": forms_out,
         "l1_mixed_vs_fp64": l1,
         "stellar_eos_box": c3,

@@ -297,6 +297,14 @@ phl_status phl_riemann_batch(long n, const double *wl, const double *wr, const d
                              const double *bg, int nspec, int solver, double mach_thr,
                              int precision, double *f);
 
+/* Arithmetic-throughput probe: the current GPU's fused multiply-add rate in
+ * TFLOP/s (2 flop per FMA), kind 0 = FP32, 1 = FP64, from register-only
+ * kernels of independent FMA chains over all SMs (best of three timed runs
+ * after a warm-up, CUDA events on `stream`; synchronous).  It gives the
+ * measured denominators of the ALU rooflines (no counterpart in the paper).
+ * Errors: PHL_EINVAL, PHL_ECUDA. */
+phl_status phl_probe_alu(int kind, double *tflops, void *stream);
+
 /* CFL step (same definition as phl_compute_dt) computed without allocating
  * any device memory.  No counterpart in the paper: it exists for callers that
  * cannot let a library call cudaMalloc/cudaFree -- a host program whose own

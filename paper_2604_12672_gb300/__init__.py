@@ -106,6 +106,7 @@ _SIGS = {
     "phl_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "phl_destroy": (None, [C.c_void_p]),
     "phl_last_error": (C.c_char_p, []),
+    "phl_probe_alu": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "phl_cfl_dt_noalloc": (C.c_int, [C.POINTER(GridDesc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p]),
     "phl_eos_table_create": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
@@ -198,6 +199,14 @@ def riemann_batch(wl, wr, bn, bg=None, nspec=0, solver="lhlld", mach_thr=0.6, pr
     _check(lib().phl_riemann_batch(n, wl.ctypes.data, wr.ctypes.data, bn.ctypes.data, bg.ctypes.data, nspec,
                                    RIEMANN[solver], float(mach_thr), PRECISION[precision], f.ctypes.data))
     return f
+
+
+def probe_alu(kind, stream=None):
+    """Measured FMA throughput of the current GPU in TFLOP/s: kind "fp32" or
+    "fp64" (phl_probe_alu)."""
+    v = C.c_double()
+    _check(lib().phl_probe_alu({"fp32": 0, "fp64": 1}[kind], C.byref(v), stream))
+    return v.value
 
 
 def cfl_dt_noalloc(grid_or_desc, cons, bx, by, bz, dt_out, stream=None):

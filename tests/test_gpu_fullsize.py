@@ -100,9 +100,7 @@ def test_full_size_mixed_step_on_sampled_subvolumes(full_step_mixed, c):
     """The mixed form against the oracle on the compared cells: relative L1 of
     the deviation from the background <= 1e-5 (the mixed form's bar) for rho,
     E and B_x; the momentum, born from the buoyancy of the density noise in
-    this first step (vertical; the horizontal components are rounding residue
-    of the pressure balance on both sides), as one vector field against its
-    own L1 <= 1e-4."""
+    this first step, as one vector field (zero background) at the same bar."""
     pr, dt, st = full_step_mixed
     q, (ix, iy, iz) = sub_problem(pr, c, H)
     out, _, _ = O.Oracle(q).run(1, dt_fixed=dt)
@@ -121,7 +119,8 @@ def test_full_size_mixed_step_on_sampled_subvolumes(full_step_mixed, c):
     a = np.stack([st["cons"][v][np.ix_(gz, gy, gx)] for v in (1, 2, 3)])
     b = np.stack([out["cons"][v][sz, sy, sx] for v in (1, 2, 3)])
     rel = np.abs(a - b).sum() / np.abs(b).sum()
-    assert rel <= 1e-4, ("momentum", rel)
+    print("full-size mixed step, momentum L1:", f"{rel:.2e}")
+    assert rel <= 1e-5, ("momentum", rel)
     a = st["bx"][np.ix_(gz, gy, gx)]
     b = out["bx"][sz, sy, sx]
     assert np.abs(a - b).sum() / np.abs(b).sum() <= 1e-5

@@ -113,7 +113,16 @@ def test_fused_blast_with_flags(P):
         a, b, c = fu[key], pd[key], ref[key]
         scale = np.abs(c).max()
         assert np.abs(a - b).max() <= 1e-5 * scale, key
-        assert np.abs(a - c).max() <= 1e-4 * scale, key
+    # against the oracle: the mixed form's measure, relative L1 per field (no
+    # background here, so the deviation is the field; m and B as vectors)
+    rel = lambda x, y: np.abs(x - y).sum() / np.abs(y).sum()
+    l1 = {"rho": rel(fu["cons"][0], ref["cons"][0]), "m": rel(fu["cons"][1:4], ref["cons"][1:4]),
+          "E": rel(fu["cons"][4], ref["cons"][4]),
+          "B": (sum(np.abs(fu[k] - ref[k]).sum() for k in ("bx", "by", "bz")) /
+                sum(np.abs(ref[k]).sum() for k in ("bx", "by", "bz")))}
+    print("blast, fused vs oracle:", {k: f"{v:.2e}" for k, v in l1.items()})
+    for k, v in l1.items():
+        assert v <= 1e-5, (k, v)
     # total mass and energy: exactly conserved up to FP64 accumulation of FP32 increments
     for v_ in (0, 4):
         t0 = pr.cons[v_].sum()
