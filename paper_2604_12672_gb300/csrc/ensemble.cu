@@ -293,6 +293,10 @@ cudaError_t launch_step_chains(phl_ensemble *E) {
     for (int k = 0; k < 3; ++k) M.F[k] = v.F[k];
     M.E = v.E; M.raw = v.raw; M.flag = v.flag; M.dt = v.dt; M.dflag = v.dflag; M.Tin = nullptr; M.Tout = nullptr;
     M.tmapW = v.tmapW; M.fused_variant = v.fused;   // the box's own stage decomposition
+    M.pipeline3 = v.pipeline3;
+    M.primed = false;   // each replay forms W from the state it finds
+    M.fmax = nullptr;   // the step's own CFL launch comes first: no maximum to carry
+    *v.w_valid = false;
     int nl = 0;
     launch_dt_mixed(*v.G, v.U, v.B, v.fmax, v.dt, v.dflag, st, &nl, nullptr);
     for (int stg = 0; stg < 3; ++stg) launch_stage_mixed(*v.G, M, stg, 3, b3[stg], st, &nl, nullptr);
@@ -487,7 +491,11 @@ phl_status phl_ensemble_step(phl_ensemble *E, int nsteps) {
     cudaError_t e = E->exec ? cudaGraphLaunch(E->exec, E->stream) : launch_step(E);
     if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_ensemble_step: %s", cudaGetErrorString(e));
   }
-  for (phl_grid *g : E->grids) *grid_view(g).steps += nsteps;
+  for (phl_grid *g : E->grids) {
+    const GridView v = grid_view(g);
+    *v.steps += nsteps;
+    *v.w_valid = false;   // the ensemble moved the state: a later phl_step forms W again
+  }
   return PHL_OK;
 }
 

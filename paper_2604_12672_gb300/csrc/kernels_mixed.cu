@@ -49,6 +49,13 @@ __global__ void k_dt_mx_finalize(double cfl, double t_s, unsigned int *fmax_bits
   *fmax_bits = 0u;
 }
 
+// A step of given length: sets dt and clears the CFL maximum the step's last
+// stage folds into.
+__global__ void k_dt_fixed(double v, unsigned int *fmax_bits, double *dt) {
+  *dt = v;
+  *fmax_bits = 0u;
+}
+
 }  // namespace
 
 void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigned int *fmax_bits, double *dt,
@@ -57,6 +64,13 @@ void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigne
   PHL_LAUNCH(KC_DT, prof, s, k_dt_mx<<<nblocks(b.n), TPB, 0, s>>>(G, b, U, Bf, fmax_bits, dflag));
   PHL_LAUNCH(KC_DT, prof, s, k_dt_mx_finalize<<<1, 1, 0, s>>>(G.cfl, G.sc_t, fmax_bits, dt));
   if (nlaunch) *nlaunch += 2;
+}
+
+void launch_dt_mixed_from_max(const DevGeo &G, double fixed_dt, unsigned int *fmax_bits, double *dt, cudaStream_t s,
+                              int *nlaunch, Prof *prof) {
+  if (fixed_dt > 0.0) PHL_LAUNCH(KC_DT, prof, s, k_dt_fixed<<<1, 1, 0, s>>>(fixed_dt, fmax_bits, dt));
+  else PHL_LAUNCH(KC_DT, prof, s, k_dt_mx_finalize<<<1, 1, 0, s>>>(G.cfl, G.sc_t, fmax_bits, dt));
+  if (nlaunch) *nlaunch += 1;
 }
 
 void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
@@ -69,7 +83,11 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
     if (G.act[d]) { lo = -lo_g; hi = G.n[d] + hi_extra; }
     else { lo = 0; hi = 1; }
   };
-  {
+  const bool fused = M.tmapW && fused_stage_ok(G);
+  const bool three = fused && M.pipeline3;
+  // on the three-launch path the previous stage formed this stage's W and raw
+  // flags; only a stage whose input was set from outside starts with them
+  if (!three || (first && !M.primed)) {
     int l[3], h[3];
     for (int d = 0; d < 3; ++d) rng(d, G.ge[d], G.ge[d], l[d], h[d]);
     Box bx = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
@@ -79,8 +97,12 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
       PHL_LAUNCH(KC_PRIM, prof, s, k_prim_mx<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, dU, dB, M.W, M.dflag));
       ++nl;
     }
+    if (three && G.eps_sf > 0.0) {
+      Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
+      PHL_LAUNCH(KC_FLAG_RAW, prof, s, k_flag_raw<float><<<grid3(bi), block3(bi), 0, s>>>(G, bi, M.W, M.raw));
+      ++nl;
+    }
   }
-  const bool fused = M.tmapW && fused_stage_ok(G);
   if (G.eps_sf > 0.0 && !fused) {
     Box bx = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
     PHL_LAUNCH(KC_FLAG_RAW, prof, s, k_flag_raw<float><<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.W, M.raw));

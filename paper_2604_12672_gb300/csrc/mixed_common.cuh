@@ -175,12 +175,10 @@ __device__ __forceinline__ void k_update_faces_mx_at(long tl, const DevGeo &G, c
 }
 
 
-// CFL rate sum_d (|u_d| + c_f,d) / dx_d of one interior cell, in scaled units.
-__device__ __forceinline__ float dt_rate_mx(const DevGeo &G, const double *__restrict__ U,
-                                            const double *__restrict__ Bf, const int *c, int *dflag) {
-  float w[NW_MAX];
-  cell_prims_mx(G, U, Bf, nullptr, nullptr, c[0], c[1], c[2], w, dflag);
-  const BgT<float> b = bg_cell_t<float>(G, c[2]);
+// CFL rate sum_d (|u_d| + c_f,d) / dx_d of a cell from its deviations w at
+// height k, in scaled units.
+__device__ __forceinline__ float dt_rate_w(const DevGeo &G, const float *w, int k) {
+  const BgT<float> b = bg_cell_t<float>(G, k);
   const float rho = b.rho + w[W_RHO], P = b.p + w[W_P], gc = b.gc + w[W_GC];
   const float ir = 1.0f / rho;
   const float a2 = gc * P * ir;
@@ -195,6 +193,14 @@ __device__ __forceinline__ float dt_rate_mx(const DevGeo &G, const double *__res
     s += (fabsf(w[W_VX + d]) + cf) * G.idxf[d];
   }
   return (s == s) ? s : INFINITY;
+}
+
+// CFL rate of one interior cell of U^n, in scaled units.
+__device__ __forceinline__ float dt_rate_mx(const DevGeo &G, const double *__restrict__ U,
+                                            const double *__restrict__ Bf, const int *c, int *dflag) {
+  float w[NW_MAX];
+  cell_prims_mx(G, U, Bf, nullptr, nullptr, c[0], c[1], c[2], w, dflag);
+  return dt_rate_w(G, w, c[2]);
 }
 
 }  // namespace

@@ -72,8 +72,10 @@ struct phl_grid {
   uint8_t *raw = nullptr, *flag = nullptr;
   // mixed precision: FP32 increments and work arrays
   float *dUf = nullptr, *dBf = nullptr, *Wf = nullptr, *Ff[3] = {nullptr, nullptr, nullptr}, *Ef = nullptr;
-  unsigned int *fmax = nullptr;
+  unsigned int *fmax = nullptr;         // [0]: the step's CFL maximum (three-launch path), [1]: phl_compute_dt
   bool mixed = false;
+  bool pipeline3 = true;                // fused mixed stage in three launches (phl_set_fused)
+  bool w_valid = false;                 // W, raw flags and fmax[0] hold the current state's (three-launch path)
   // scalars
   double *dt = nullptr;
   unsigned long long *dmax = nullptr;
@@ -171,6 +173,9 @@ phl_status state_io(phl_grid *g, double *cons, double *bx, double *by, double *b
         return st;
     return PHL_OK;
   }
+  // the staging work arrays hold the next stage's primitives on the
+  // three-launch path: reading the state through them retires those
+  if (staged) g->w_valid = false;
   double *ca = staged ? g->stage_a : cons;
   double *fa[3];
   fa[0] = staged ? g->stage_b : bx;
@@ -218,7 +223,7 @@ void launch_dt(phl_grid *g, int *nl) {
   if (g->G.eos == PHL_EOS_STELLAR)
     launch_dt_stellar(g->G, g->mixed, g->U, g->B, g->T, g->dmax, g->dt, g->dflag, g->stream, nl, pf);
   else if (g->mixed)
-    launch_dt_mixed(g->G, g->U, g->B, g->fmax, g->dt, g->dflag, g->stream, nl, pf);
+    launch_dt_mixed(g->G, g->U, g->B, g->fmax + 1, g->dt, g->dflag, g->stream, nl, pf);
   else
     launch_dt_fp64(g->G, g->U, g->B, g->T, g->dmax, g->dt, g->dflag, g->stream, nl, pf);
 }
@@ -245,7 +250,9 @@ GridView grid_view(phl_grid *g) {
   for (int k = 0; k < 3; ++k) v.F[k] = g->Ff[k];
   v.E = g->Ef;
   v.raw = g->raw; v.flag = g->flag;
-  v.dt = g->dt; v.fmax = g->fmax; v.dflag = g->dflag;
+  v.dt = g->dt; v.fmax = g->fmax + 1; v.dflag = g->dflag;
+  v.w_valid = &g->w_valid;
+  v.pipeline3 = g->pipeline3;
   v.stream = g->stream;
   v.steps = &g->steps;
   v.mixed = g->mixed;
@@ -400,7 +407,7 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     for (int k = 0; k < 3; ++k)
       if (G.act[k]) AL(&g->Ff[k], (long)(G.nf + 1) * G.wtot);
     AL(&g->Ef, 3 * G.wtot);
-    AL(&g->fmax, 1);
+    AL(&g->fmax, 2);
     g->stage_a = (double *)g->Wf;
     g->stage_a_bytes = (size_t)(G.wstr + NAUX) * G.wtot * sizeof(float);
     g->stage_b = (double *)g->Ff[0];
@@ -500,6 +507,7 @@ phl_status phl_set_stream(phl_grid *g, void *stream) {
 
 phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx, const double *by,
                          const double *bz, const double *T, int where) {
+  if (g) g->w_valid = false;   // the state changes from outside: the next step forms W again
   if (!g || !cons || !bx || !by || !bz) return fail(PHL_EINVAL, "null argument");
   if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
   const DevGeo &G = g->G;
@@ -538,6 +546,7 @@ phl_status phl_get_state(phl_grid *g, double *cons, double *bx, double *by, doub
 
 phl_status phl_set_state_prim(phl_grid *g, const double *prim, const double *bx, const double *by,
                               const double *bz, int where) {
+  if (g) g->w_valid = false;   // the state changes from outside: the next step forms W again
   if (!g || !prim || !bx || !by || !bz) return fail(PHL_EINVAL, "null argument");
   if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
   const DevGeo &G = g->G;
@@ -584,11 +593,19 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
   if (nsteps < 0) return fail(PHL_EINVAL, "nsteps < 0");
   for (int s = 0; s < nsteps; ++s) {
     int nl = 0;
-    if (dt > 0.0) {
-      launch_set_scalar(g->dt, dt, g->stream, g->prof.on ? &g->prof : nullptr);
-      ++nl;
+    const bool three = g->mixed && g->fused && g->pipeline3;
+    const bool primed = three && g->w_valid;
+    if (primed) {   // the previous step's last stage left the CFL maximum of this state
+      launch_dt_mixed_from_max(g->G, dt, g->fmax, g->dt, g->stream, &nl, g->prof.on ? &g->prof : nullptr);
+    } else if (dt > 0.0) {
+      if (three) launch_dt_mixed_from_max(g->G, dt, g->fmax, g->dt, g->stream, &nl, g->prof.on ? &g->prof : nullptr);
+      else {
+        launch_set_scalar(g->dt, dt, g->stream, g->prof.on ? &g->prof : nullptr);
+        ++nl;
+      }
     } else {
       launch_dt(g, &nl);
+      if (three) CK(cudaMemsetAsync(g->fmax, 0, sizeof(unsigned int), g->stream), "clear CFL maximum");
     }
     if (g->mixed) {
       const double bs3[3] = {1.0, 0.25, 2.0 / 3.0}, bs2[2] = {1.0, 0.5};
@@ -600,6 +617,9 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
       M.tmapW = g->fused ? g->tmapW : nullptr;
       M.fused_variant = g->fused;
       M.test_extra_tx = g->test_extra_tx;
+      M.pipeline3 = three;
+      M.primed = primed;
+      M.fmax = g->fmax;
       for (int st = 0; st < ns; ++st) {
         M.Tin = g->T;
         M.Tout = g->T2;
@@ -618,6 +638,7 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
     CK(cudaGetLastError(), "launch stage");
     g->launches_per_step = nl;
     ++g->steps;
+    if (three) g->w_valid = true;
   }
   return PHL_OK;
 }
@@ -675,16 +696,23 @@ phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, 
 
 phl_status phl_set_fused(phl_grid *g, int on) {
   if (!g) return fail(PHL_EINVAL, "null grid");
-  if (on < 0 || on > PHL_FUSED_SHAPES) return fail(PHL_EINVAL, "fused launch shape must be 0..%d", PHL_FUSED_SHAPES);
+  g->w_valid = false;
+  // 101..109: the same launch shapes with the six-launch stage decomposition
+  const bool six = on > 100;
+  if (six) on -= 100;
+  if (on < 0 || on > PHL_FUSED_SHAPES) return fail(PHL_EINVAL, "fused launch shape must be 0..%d (or 101..%d)",
+                                                   PHL_FUSED_SHAPES, 100 + PHL_FUSED_SHAPES);
   if (!on) { g->fused = 0; return PHL_OK; }
   if (!g->mixed || !fused_stage_ok(g->G))
     return fail(PHL_EUNSUPPORTED, "the fused stage needs the mixed form, an ideal gas without species and 3 active dimensions");
   if (make_fused_tmap(g->G, g->Wf, g->tmapW) != PHL_OK) return PHL_ECUDA;
   g->fused = on == 1 ? PHL_FUSED_DEFAULT : on;
+  g->pipeline3 = !six;
   return PHL_OK;
 }
 
 phl_status phl_diffuse(phl_grid *g, const phl_diffusion *p, double dt, int max_stages, int *nsts_out) {
+  if (g) g->w_valid = false;   // the state changes from outside: the next step forms W again
   if (!g || !p) return fail(PHL_EINVAL, "null argument");
   if (g->G.eos != PHL_EOS_IDEAL) return fail(PHL_EUNSUPPORTED, "thermal diffusion is built for the ideal gas");
   if (!(p->k0 >= 0.0) || !(p->cv > 0.0) || p->nT < 0 || p->nT > 4 || p->nR < 0 || p->nR > 2 || !(dt > 0.0) ||
@@ -715,6 +743,7 @@ phl_status phl_diffuse(phl_grid *g, const phl_diffusion *p, double dt, int max_s
 
 phl_status phl_test_tile_wait_timeout(phl_grid *g, int on) {
   if (!g) return fail(PHL_EINVAL, "null grid");
+  g->w_valid = false;
   if (on && !g->fused) return fail(PHL_EUNSUPPORTED, "the grid does not run the fused tile kernel");
   g->test_extra_tx = on ? 16u : 0u;
   return PHL_OK;

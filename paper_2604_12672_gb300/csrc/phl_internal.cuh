@@ -280,11 +280,24 @@ struct MixedBufs {
   const void *tmapW = nullptr; // TMA descriptor of W (fused path), or null
   int fused_variant = 1;       // launch shape of the fused tile kernel (phl_set_fused)
   unsigned test_extra_tx = 0;  // timeout test: bytes announced to the tile barrier that never arrive
+  // Fused path in three launches per stage (tile kernel, Contact-CT + face
+  // update, next primitives + raw flags); otherwise six (primitives, raw
+  // flags, dilation, tile kernel, EMFs, face update).
+  bool pipeline3 = false;
+  // pipeline3: W, the auxiliaries and the raw flags already hold the stage
+  // input (the previous stage's last kernel formed them); false at the first
+  // stage after the state was set from outside
+  bool primed = false;
+  unsigned int *fmax = nullptr; // CFL rate maximum the last stage folds into (pipeline3)
 };
 void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
                         int *nlaunch, Prof *prof);
 void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigned int *fmax_bits, double *dt,
                      int *dflag, cudaStream_t s, int *nlaunch, Prof *prof);
+// The step length from the CFL maximum the previous step's last stage folded
+// into fmax_bits (three-launch path), or fixed_dt > 0; clears fmax_bits.
+void launch_dt_mixed_from_max(const DevGeo &G, double fixed_dt, unsigned int *fmax_bits, double *dt, cudaStream_t s,
+                              int *nlaunch, Prof *prof);
 
 // Thermal diffusion by RKL2 super-time-stepping (diffusion.cu).
 cudaError_t launch_diffuse(const DevGeo &G, double *U, const double *Bf, const phl_diffusion &p, double dt,
@@ -300,6 +313,10 @@ int make_fused_tmap(const DevGeo &G, const float *W, void *tmap128);
 cudaError_t fused_init();   // shared-memory limits of the tile kernels (once per process)
 void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool last, double b, cudaStream_t s,
                        int *nl, Prof *prof);
+// Contact-CT + face update and next primitives + raw flags (stage_ct.cu).
+cudaError_t ct_init();
+void launch_ct_prim(const DevGeo &G, const MixedBufs &M, bool first, bool last, double b, unsigned int *fmax,
+                    cudaStream_t s, int *nl, Prof *prof);
 
 // Buffers of a grid for the ensemble path (ensemble.cu); mixed grids only.
 struct GridView {
@@ -315,6 +332,8 @@ struct GridView {
   bool mixed;
   const void *tmapW;           // TMA descriptor of W when the grid runs the fused stage
   int fused;                   // its launch shape (0: per-direction kernels)
+  bool *w_valid;               // the grid's record that W holds its state (cleared by ensemble steps)
+  bool pipeline3;              // its fused stage runs in three launches
 };
 GridView grid_view(::phl_grid *g);
 

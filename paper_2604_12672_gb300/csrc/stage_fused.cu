@@ -396,7 +396,7 @@ template <int NT, int MINB, bool PHASED, bool PAIRED = false, bool LR = false, b
 __global__ void __launch_bounds__(NT, MINB)
     k_flux_update_mx(const __grid_constant__ CUtensorMap tmW, DevGeo G, StageMx S, const uint8_t *__restrict__ flag,
                      float *__restrict__ F0, float *__restrict__ F1, float *__restrict__ F2, int ntx, int nty,
-                     int *dflag, unsigned extra_tx) {
+                     int *dflag, unsigned extra_tx, int raw_flags) {
   extern __shared__ unsigned char smraw[];
   FusedSmem &sm = *reinterpret_cast<FusedSmem *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
   const int tid = threadIdx.x;
@@ -437,26 +437,88 @@ __global__ void __launch_bounds__(NT, MINB)
       sm.bgc[1][tid] = inc ? G.bgf_p_c[z + BG_NG] : 0.0f;
     }
   }
-  for (int q = tid; q < (FX + 2) * (FY + 2) * (FZ + 2); q += NT) {
-    const int l[3] = {q % (FX + 2), (q / (FX + 2)) % (FY + 2), q / ((FX + 2) * (FY + 2))};
+  if (raw_flags) {
+    // flag holds the raw flags (interior layout): the 5^3 dilation of the
+    // tile's cells -1 .. F is done here from the raw flags of cells -3 .. F+2,
+    // wrapped on periodic axes and unflagged beyond any other boundary, the
+    // ORs nested axis by axis (x, y, z) in the face buffer (unused until the
+    // faces).  A ghost cell then carries the dilated flag of the interior cell
+    // its data comes from, cells further out none -- as the dilation kernel
+    // and the staging below give on the other path.
+    constexpr int RB = FX + 6, RY = FY + 6, RZ = FZ + 6;   // raw box: cells -3 .. F+2
+    uint8_t *rb = reinterpret_cast<uint8_t *>(&sm.f[0][0]);
+    uint8_t *r1 = rb + RB * RY * RZ;             // x-ORed: cells -1 .. F along x
+    uint8_t *r2 = r1 + (FX + 2) * RY * RZ;       // then y
+    uint8_t *r3 = r2 + (FX + 2) * (FY + 2) * RZ; // then z
     const int o[3] = {x0, y0, z0};
-    uint8_t v = 0;
-    if (flag) {
+    for (int q = tid; q < RB * RY * RZ; q += NT) {
+      const int l[3] = {q % RB, (q / RB) % RY, q / (RB * RY)};
       int g[3];
       bool in = true;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        int x = o[d] - 1 + l[d];
-        if (x < -1 || x > G.n[d]) in = false;
-        else if (x == -1 || x == G.n[d]) {
-          bool fl;
-          x = cell_src(x, G.n[d], G.bc[d][0], G.bc[d][1], fl);
+        int x = o[d] - 3 + l[d];
+        if (x < 0 || x >= G.n[d]) {
+          if (G.bc[d][0] == 0) x = (x % G.n[d] + G.n[d]) % G.n[d];
+          else in = false;
         }
         g[d] = x;
       }
-      if (in) v = flag[g[0] + (long)G.n[0] * (g[1] + (long)G.n[1] * g[2])];
+      rb[q] = in ? flag[g[0] + (long)G.n[0] * (g[1] + (long)G.n[1] * g[2])] : (uint8_t)0;
     }
-    (&sm.flg[0][0][0])[q] = v;
+    __syncthreads();
+    for (int q = tid; q < (FX + 2) * RY * RZ; q += NT) {
+      const int i = q % (FX + 2), r = q / (FX + 2);
+      const uint8_t *a = rb + r * RB + i;
+      r1[q] = a[0] | a[1] | a[2] | a[3] | a[4];
+    }
+    __syncthreads();
+    for (int q = tid; q < (FX + 2) * (FY + 2) * RZ; q += NT) {
+      const int i = q % (FX + 2), j = (q / (FX + 2)) % (FY + 2), k = q / ((FX + 2) * (FY + 2));
+      const uint8_t *a = r1 + (k * RY + j) * (FX + 2) + i;
+      r2[q] = a[0] | a[FX + 2] | a[2 * (FX + 2)] | a[3 * (FX + 2)] | a[4 * (FX + 2)];
+    }
+    __syncthreads();
+    for (int q = tid; q < (FX + 2) * (FY + 2) * (FZ + 2); q += NT) {
+      constexpr int P2 = (FX + 2) * (FY + 2);
+      const uint8_t *a = r2 + q;
+      r3[q] = a[0] | a[P2] | a[2 * P2] | a[3 * P2] | a[4 * P2];
+    }
+    __syncthreads();
+    for (int q = tid; q < (FX + 2) * (FY + 2) * (FZ + 2); q += NT) {
+      int l[3] = {q % (FX + 2), (q / (FX + 2)) % (FY + 2), q / ((FX + 2) * (FY + 2))};
+      bool in = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int x = o[d] - 1 + l[d];
+        if (x < -1 || x > G.n[d]) in = false;
+        else if (G.bc[d][0] != 0 && x == -1) l[d] += 1;        // the source cell 0
+        else if (G.bc[d][1] != 0 && x == G.n[d]) l[d] -= 1;    // the source cell n - 1
+      }
+      (&sm.flg[0][0][0])[q] = in ? r3[(l[2] * (FY + 2) + l[1]) * (FX + 2) + l[0]] : (uint8_t)0;
+    }
+  } else {
+    for (int q = tid; q < (FX + 2) * (FY + 2) * (FZ + 2); q += NT) {
+      const int l[3] = {q % (FX + 2), (q / (FX + 2)) % (FY + 2), q / ((FX + 2) * (FY + 2))};
+      const int o[3] = {x0, y0, z0};
+      uint8_t v = 0;
+      if (flag) {
+        int g[3];
+        bool in = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          int x = o[d] - 1 + l[d];
+          if (x < -1 || x > G.n[d]) in = false;
+          else if (x == -1 || x == G.n[d]) {
+            bool fl;
+            x = cell_src(x, G.n[d], G.bc[d][0], G.bc[d][1], fl);
+          }
+          g[d] = x;
+        }
+        if (in) v = flag[g[0] + (long)G.n[0] * (g[1] + (long)G.n[1] * g[2])];
+      }
+      (&sm.flg[0][0][0])[q] = v;
+    }
   }
   const bool ok = mbar_wait_bounded(bar, 0u, 1000000000ull);
   if (__syncthreads_or(!ok)) {   // the copy did not land in 1 s: report, let it finish, leave
@@ -749,7 +811,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 cudaError_t fused_init() {
   static cudaError_t done = cudaErrorNotReady;
   if (done == cudaSuccess) return done;
-  cudaError_t e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = ct_init();
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes(false));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_flux_update_mx<288, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -842,7 +905,11 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   const int nb = ntx * nty * ntz;
   const long ncell = (long)G.n[0] * G.n[1] * G.n[2];
   const uint8_t *dil = nullptr;
-  if (G.eps_sf > 0.0) {   // raw flags, then their 5^3 dilation, both on the interior layout
+  int raw_mode = 0;
+  if (G.eps_sf > 0.0 && M.pipeline3) {   // the tile kernel dilates the raw flags itself
+    dil = M.raw;
+    raw_mode = 1;
+  } else if (G.eps_sf > 0.0) {   // raw flags, then their 5^3 dilation, both on the interior layout
     Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
     PHL_LAUNCH(KC_FLAG_RAW, prof, s, k_flag_raw<float><<<grid3(bi), block3(bi), 0, s>>>(G, bi, M.W, M.raw));
     PHL_LAUNCH(KC_FLAG_DILATE, prof, s, k_flag_dilate3<<<nb, 256, 0, s>>>(G, M.raw, M.raw + ncell, ntx, nty));
@@ -855,7 +922,7 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   PHL_LAUNCH(KC_FLUX_UPDATE, prof, s,                                                                          \
              (k_flux_update_mx<NT, MB, PH, PA, LRS, PP><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0],   \
                                                                                    M.F[1], M.F[2], ntx, nty,     \
-                                                                                   M.dflag, M.test_extra_tx)))
+                                                                                   M.dflag, M.test_extra_tx, raw_mode)))
   // the reconstruction is a template parameter: the van Leer kernels carry no PPH code
 #define PHL_FUSED(NT, MB, PH, PA, LRS)                      \
   do {                                                     \
@@ -876,6 +943,10 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
 #undef PHL_FUSED
 #undef PHL_FUSED1
   ++*nl;
+  if (M.pipeline3) {   // Contact-CT with the face update, then the next stage's primitives and raw flags
+    launch_ct_prim(G, M, first, last, b, M.fmax, s, nl, prof);
+    return;
+  }
   Box bs = make_box(0, G.n[0] + 1, 0, G.n[1] + 1, 0, G.n[2] + 1);
   const dim3 sg = site_grid(G), sb(EB_X, EB_Y, EB_Z);
   PHL_LAUNCH(KC_EMF, prof, s, k_emf3<<<sg, sb, 0, s>>>(G, bs, M.W, M.F[0], M.F[1], M.F[2], M.E));

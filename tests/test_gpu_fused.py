@@ -156,3 +156,58 @@ def test_fused_only_where_eligible(P):
         g.set_fused(True)
     g.set_fused(False)
     g.close()
+
+
+def _box_bc(bc, n=(21, 18, 27)):
+    pr = W.stratified_box(*n, amp=3e-2, beta=1e3, mach_heat=3e-2)
+    pr.bc = BCS[bc]
+    return pr
+
+
+@pytest.mark.parametrize("bc", list(BCS))
+@pytest.mark.parametrize("shape", [1, 2])
+def test_three_launch_stage_matches_six_launch_stage(P, bc, shape):
+    """The stage in three launches (tile kernel with the flag dilation inside;
+    Contact-CT with the face update; next primitives with their ghost images
+    and the raw flags) against the same tile kernel in six launches, with the
+    device CFL step (folded into the last stage on the three-launch path) and
+    shock flags active, on ragged boxes with every boundary kind: the same
+    arithmetic in other kernels, equal to FP32 rounding of the deviations."""
+    pr = _box_bc(bc)
+    pr.eps_sf = 0.02   # a low threshold: many flagged cells and HLL faces
+    outs = []
+    for on in (shape, 100 + shape):
+        g = P.Grid(pr, precision="mixed")
+        g.set_fused(on)
+        g.load()
+        g.step(6)   # device CFL step each step
+        outs.append(g.get_state())
+        g.close()
+    same = all(np.array_equal(outs[0][k], outs[1][k]) for k in ("cons", "bx", "by", "bz"))
+    l1 = deviation_l1(pr, outs[0], outs[1])
+    print(bc, shape, "bit-identical" if same else {k: f"{v:.1e}" for k, v in l1.items()})
+    for k, v in l1.items():
+        assert v <= 1e-6, (k, v)
+
+
+def test_three_launch_stage_resumes_after_set_state(P):
+    """The state set from outside between steps (as a restart does) is picked
+    up: the next step forms the primitives, flags and CFL step again, and the
+    run equals one that never stopped."""
+    pr = _box_bc("periodic_xy", (16, 24, 20))
+    g = P.Grid(pr, precision="mixed")
+    g.load()
+    g.step(3)
+    mid = g.get_state()
+    g.step(3)
+    ref = g.get_state()
+    g.close()
+    h = P.Grid(pr, precision="mixed")
+    h.load()
+    h.step(1)                      # leaves W of a state about to be replaced
+    h.set_state(mid["cons"], mid["bx"], mid["by"], mid["bz"])
+    h.step(3)
+    got = h.get_state()
+    h.close()
+    for k in ("cons", "bx", "by", "bz"):
+        assert np.array_equal(got[k], ref[k]), k
