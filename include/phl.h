@@ -231,37 +231,41 @@ phl_status phl_diffuse(phl_grid *g, const phl_diffusion *p, double dt, int max_s
 
 /* Selects how a mixed-precision grid evaluates a stage (Sects. 2.4-2.9; the
  * arithmetic is the same, only the kernel decomposition differs).
- *   on = 1: the fused path in three launches per stage (default where
- *           eligible).  (i) The tile kernel: each CTA stages an 8x8x8 tile of
- *           the primitive deviations with two ghost layers by TMA, dilates
- *           the raw shock flags of the tile in shared memory, computes the
- *           faces of all three directions and applies the cell update.
- *           (ii) Contact-CT: the edge EMFs of an 8^3 tile of sites from the
- *           tangential-B fluxes the faces left, in shared memory, and the
- *           update of the tile's own faces.  (iii) The primitive deviations
- *           of the next stage for an 8^3 tile of cells, written with their
- *           ghost images, the raw shock flags of the tile from the pressures
- *           of a one-cell halo, and in the last stage the CFL rate of the new
- *           state folded into the next step's maximum (so a step with the
- *           device CFL step adds one one-thread launch).  The first step
- *           after the state was set from outside (phl_set_state,
- *           phl_set_state_prim, phl_diffuse, an ensemble step, this call)
- *           first forms the primitives, raw flags and CFL step in their own
- *           kernels.  Needs precision = PHL_MIXED, an ideal gas, nspec = 0
- *           and three active dimensions (PHL_EUNSUPPORTED otherwise).
- *   on = 2..9: the same tile kernel in other launch shapes (threads per CTA,
+ *   on = 1: the fused tile kernel -- each CTA stages an 8x8x8 tile of the
+ *           primitive deviations with two ghost layers by TMA, computes the
+ *           faces of all three directions in shared memory and applies the
+ *           cell update; the primitives, raw shock flags and their dilation
+ *           before it and the Contact-CT EMFs and face updates after it run as
+ *           one kernel each (six launches per stage).  Needs
+ *           precision = PHL_MIXED, an ideal gas, nspec = 0 and at least four
+ *           cells along each of three active dimensions (PHL_EUNSUPPORTED
+ *           otherwise).  Default where eligible.
+ *   on = 2..9: the same kernel in other launch shapes (threads per CTA,
  *           CTAs per SM, faces of one direction at a time through a smaller
  *           shared buffer; 5 to 7 evaluate two faces per thread on packed
  *           FP32x2 arithmetic; 8 and 9 pair the left and right states of
  *           each face on FP32x2 arithmetic), for tuning; 1 selects the
  *           default shape.
- *   on = 101..109: shapes 1..9 with the stage in six launches (primitives,
- *           raw flags, dilation, tile kernel, EMFs, face update), for
- *           comparison.
+ *   on = 201..209: shapes 1..9 with the stage in three launches: (i) the
+ *           tile kernel, which dilates the raw shock flags of its tile in
+ *           shared memory; (ii) Contact-CT: the edge EMFs an 8^3 tile of
+ *           sites needs, in shared memory, and the update of the tile's own
+ *           faces; (iii) the next stage's primitive deviations for a 16x16x8
+ *           tile of cells with their ghost images, the raw flags from the
+ *           pressures of a one-cell halo, and in the last stage the CFL rate
+ *           of the new state folded into the next step's maximum (a step
+ *           with the device CFL step adds one one-thread launch).  The first
+ *           step after the state was set from outside (phl_set_state,
+ *           phl_set_state_prim, phl_diffuse, a host phl_get_state, an
+ *           ensemble step, this call) forms the primitives, raw flags and
+ *           CFL step in their own kernels first.  Ten launches per step
+ *           instead of twenty, but slower per cell on this GPU (the flag
+ *           dilation no longer overlaps the tile's copy; the halo primitives
+ *           and the small CT tiles cost more than they save).
  *   on = 0: one kernel per direction for the faces, then EMFs and updates.
  * Results of all of these agree to FP32 rounding of the deviations.  Call
  * between steps only (no stage of the grid in flight on its stream).
- * PHL_EINVAL for on outside 0..9 and 101..109. */
+ * PHL_EINVAL for on outside 0..9 and 201..209. */
 phl_status phl_set_fused(phl_grid *g, int on);
 
 /* Test of the failure path of the fused tile kernel's bounded wait.  With

@@ -579,9 +579,9 @@ class Grid:
 
     def set_fused(self, on=1):
         """Mixed-precision stage decomposition (phl_set_fused): 0/False = one
-        face kernel per direction, 1/True = the fused path (three launches per
-        stage) in the tile kernel's default launch shape, 2..9 = other launch
-        shapes of it, 101..109 = shapes 1..9 with the stage in six launches."""
+        face kernel per direction, 1/True = the fused tile kernel in its
+        default launch shape (six launches per stage), 2..9 = other launch
+        shapes of it, 201..209 = shapes 1..9 with the stage in three launches."""
         _check(lib().phl_set_fused(self.h, int(on)))
 
     def kernel_times(self, reset=True):

@@ -25,7 +25,7 @@ PER_FILE_FLAGS = {
     "kernels_mixed.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "unit_kernels.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "stage_fused.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
-    "stage_ct.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "stage_prim.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
 }
 
 

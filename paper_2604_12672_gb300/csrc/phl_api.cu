@@ -74,7 +74,7 @@ struct phl_grid {
   float *dUf = nullptr, *dBf = nullptr, *Wf = nullptr, *Ff[3] = {nullptr, nullptr, nullptr}, *Ef = nullptr;
   unsigned int *fmax = nullptr;         // [0]: the step's CFL maximum (three-launch path), [1]: phl_compute_dt
   bool mixed = false;
-  bool pipeline3 = true;                // fused mixed stage in three launches (phl_set_fused)
+  bool pipeline3 = false;               // fused mixed stage in three launches (phl_set_fused 201..209)
   bool w_valid = false;                 // W, raw flags and fmax[0] hold the current state's (three-launch path)
   // scalars
   double *dt = nullptr;
@@ -697,17 +697,17 @@ phl_status phl_kernel_times(phl_grid *g, phl_kernel_time *out, int max, int *n, 
 phl_status phl_set_fused(phl_grid *g, int on) {
   if (!g) return fail(PHL_EINVAL, "null grid");
   g->w_valid = false;
-  // 101..109: the same launch shapes with the six-launch stage decomposition
-  const bool six = on > 100;
-  if (six) on -= 100;
-  if (on < 0 || on > PHL_FUSED_SHAPES) return fail(PHL_EINVAL, "fused launch shape must be 0..%d (or 101..%d)",
-                                                   PHL_FUSED_SHAPES, 100 + PHL_FUSED_SHAPES);
+  // 201..209: the same launch shapes with the stage in three launches
+  const bool three = on > 200;
+  if (three) on -= 200;
+  if (on < 0 || on > PHL_FUSED_SHAPES) return fail(PHL_EINVAL, "fused launch shape must be 0..%d (or 201..%d)",
+                                                   PHL_FUSED_SHAPES, 200 + PHL_FUSED_SHAPES);
   if (!on) { g->fused = 0; return PHL_OK; }
   if (!g->mixed || !fused_stage_ok(g->G))
     return fail(PHL_EUNSUPPORTED, "the fused stage needs the mixed form, an ideal gas without species and 3 active dimensions");
   if (make_fused_tmap(g->G, g->Wf, g->tmapW) != PHL_OK) return PHL_ECUDA;
   g->fused = on == 1 ? PHL_FUSED_DEFAULT : on;
-  g->pipeline3 = !six;
+  g->pipeline3 = three;
   return PHL_OK;
 }
 

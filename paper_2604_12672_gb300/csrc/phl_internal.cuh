@@ -313,10 +313,10 @@ int make_fused_tmap(const DevGeo &G, const float *W, void *tmap128);
 cudaError_t fused_init();   // shared-memory limits of the tile kernels (once per process)
 void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool last, double b, cudaStream_t s,
                        int *nl, Prof *prof);
-// Contact-CT + face update and next primitives + raw flags (stage_ct.cu).
-cudaError_t ct_init();
-void launch_ct_prim(const DevGeo &G, const MixedBufs &M, bool first, bool last, double b, unsigned int *fmax,
-                    cudaStream_t s, int *nl, Prof *prof);
+// The next stage's primitives with their ghost images, the raw flags and,
+// in the last stage, the CFL maximum (stage_prim.cu).
+void launch_prim_flags(const DevGeo &G, const MixedBufs &M, bool last, unsigned int *fmax, cudaStream_t s, int *nl,
+                       Prof *prof);
 
 // Buffers of a grid for the ensemble path (ensemble.cu); mixed grids only.
 struct GridView {

@@ -451,20 +451,23 @@ __global__ void __launch_bounds__(NT, MINB)
     uint8_t *r2 = r1 + (FX + 2) * RY * RZ;       // then y
     uint8_t *r3 = r2 + (FX + 2) * (FY + 2) * RZ; // then z
     const int o[3] = {x0, y0, z0};
-    for (int q = tid; q < RB * RY * RZ; q += NT) {
-      const int l[3] = {q % RB, (q / RB) % RY, q / (RB * RY)};
-      int g[3];
+    // one thread per raw-box row of RB bytes: the row's y, z wrap once; along
+    // x a step of at most 3 cells past a boundary wraps by one period (the
+    // fused path needs n >= 4 along every axis -- fused_stage_ok)
+    for (int row = tid; row < RY * RZ; row += NT) {
+      int y = o[1] - 3 + row % RY, z = o[2] - 3 + row / RY;
       bool in = true;
+      if (y < 0 || y >= G.n[1]) { if (G.bc[1][0] == 0) y += y < 0 ? G.n[1] : -G.n[1]; else in = false; }
+      if (z < 0 || z >= G.n[2]) { if (G.bc[2][0] == 0) z += z < 0 ? G.n[2] : -G.n[2]; else in = false; }
+      const uint8_t *fr = flag + (long)G.n[0] * (y + (long)G.n[1] * z);
+      uint8_t *dst = rb + row * RB;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        int x = o[d] - 3 + l[d];
-        if (x < 0 || x >= G.n[d]) {
-          if (G.bc[d][0] == 0) x = (x % G.n[d] + G.n[d]) % G.n[d];
-          else in = false;
-        }
-        g[d] = x;
+      for (int i = 0; i < RB; ++i) {
+        int x = o[0] - 3 + i;
+        bool ok = in;
+        if (x < 0 || x >= G.n[0]) { if (G.bc[0][0] == 0) x += x < 0 ? G.n[0] : -G.n[0]; else ok = false; }
+        dst[i] = ok ? fr[x] : (uint8_t)0;
       }
-      rb[q] = in ? flag[g[0] + (long)G.n[0] * (g[1] + (long)G.n[1] * g[2])] : (uint8_t)0;
     }
     __syncthreads();
     for (int q = tid; q < (FX + 2) * RY * RZ; q += NT) {
@@ -765,6 +768,84 @@ __global__ void k_emf3(DevGeo G, Box box, const float *__restrict__ W, const flo
   if (c[2] < G.n[2]) E[2 * wt + p] = emf_edge<2>(G, c, interior, p, W, F0, F1);
 }
 
+// Contact-CT and the face update in one kernel (the three-launch stage): an
+// 8^3 tile of sites computes, with emf_edge, the edge EMFs its faces need --
+// E_D at sites s_D in [o_D, hi_D] (s_D < n_D), s_A in [o_A, hi_A + 1] (<= n_A),
+// the same for B, hi the tile's last site (n for the tile at the upper
+// boundary, which also owns the boundary faces) -- into shared memory, then
+// updates its own faces from the curl of those EMFs.  The EMF inputs come
+// straight from the tile kernel's output (L1/L2), as in k_emf3; only the
+// tile's ~1.27 edges per site are kept.
+constexpr int CTT = 8, CTE = CTT + 2, CTE3 = CTE * CTE * CTE;
+__device__ __forceinline__ int ct_hi(int o, int n) { return o + CTT >= n ? n : o + CTT - 1; }
+
+// The edges along D a tile needs, into ed (box of CTE^3 sites from o).
+template <int D>
+__device__ __forceinline__ void ct_edges(const DevGeo &G, const StageMx &S, const int *o, const int *hi, float *ed,
+                                         int tid) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  const float *FA = S.F[A], *FB = S.F[B];
+  for (int r = tid; r < CTE3; r += 256) {
+    const int ex = r % CTE, ey = (r / CTE) % CTE, ez = r / (CTE * CTE);
+    const int c[3] = {o[0] + ex, o[1] + ey, o[2] + ez};
+    const bool need = c[D] <= hi[D] && c[D] < G.n[D] && c[A] <= hi[A] + 1 && c[A] <= G.n[A] &&
+                      c[B] <= hi[B] + 1 && c[B] <= G.n[B];
+    float v = 0.0f;
+    if (need) {
+      const long p = widx(G, c[0], c[1], c[2]);
+      const bool interior =
+          c[0] >= 1 && c[0] < G.n[0] && c[1] >= 1 && c[1] < G.n[1] && c[2] >= 1 && c[2] < G.n[2];
+      v = emf_edge<D>(G, c, interior, p, S.W, FA, FB);
+    }
+    ed[r] = v;
+  }
+}
+
+// The tile's own D-faces from the curl of the edge EMFs in shared memory.
+template <int D>
+__device__ __forceinline__ void ct_faces(const DevGeo &G, const StageMx &S, const int *o, const int *hi,
+                                         float (*ed)[CTE3], float dt, int tid) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  constexpr int NFT = (CTT + 1) * CTT * CTT;
+  constexpr int eA = A == 0 ? 1 : (A == 1 ? CTE : CTE * CTE), eB = B == 0 ? 1 : (B == 1 ? CTE : CTE * CTE);
+  for (int r = tid; r < NFT; r += 256) {
+    int e[3];
+    e[D] = r % (CTT + 1);
+    e[A] = (r / (CTT + 1)) % CTT;
+    e[B] = r / ((CTT + 1) * CTT);
+    const int c[3] = {o[0] + e[0], o[1] + e[1], o[2] + e[2]};
+    if (c[D] > hi[D] || c[A] > hi[A] || c[A] >= G.n[A] || c[B] > hi[B] || c[B] >= G.n[B]) continue;
+    const int k0 = (e[2] * CTE + e[1]) * CTE + e[0];
+    float rr = 0.0f;
+    rr += (ed[B][k0 + eA] - ed[B][k0]) * G.idxf[A];
+    rr -= (ed[A][k0 + eB] - ed[A][k0]) * G.idxf[B];
+    const long qg = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
+    const float din = S.first ? 0.0f : S.dB[qg];
+    const float dout = S.b * (din - dt * rr);
+    if (S.last) S.B[qg] += f2d_scaled(dout, G.e_b);
+    else S.dB[qg] = dout;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ct_faces(DevGeo G, StageMx S, int ntx, int nty) {
+  __shared__ float ed[3][CTE3];
+  const int tid = threadIdx.x;
+  int t = blockIdx.x;
+  const int tx = t % ntx;
+  t /= ntx;
+  const int ty = t % nty, tz = t / nty;
+  const int o[3] = {tx * CTT, ty * CTT, tz * CTT};
+  const int hi[3] = {ct_hi(o[0], G.n[0]), ct_hi(o[1], G.n[1]), ct_hi(o[2], G.n[2])};
+  ct_edges<0>(G, S, o, hi, ed[0], tid);
+  ct_edges<1>(G, S, o, hi, ed[1], tid);
+  ct_edges<2>(G, S, o, hi, ed[2], tid);
+  __syncthreads();
+  const float dt = d2f_scaled(*S.dt, -G.e_t);
+  ct_faces<0>(G, S, o, hi, ed, dt, tid);
+  ct_faces<1>(G, S, o, hi, ed, dt, tid);
+  ct_faces<2>(G, S, o, hi, ed, dt, tid);
+}
+
 // Face update of the normal field on the D-face at site c from the curl of
 // the edge EMFs (Eq. induction in discrete form), as k_update_faces_mx.
 template <int D>
@@ -811,8 +892,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 cudaError_t fused_init() {
   static cudaError_t done = cudaErrorNotReady;
   if (done == cudaSuccess) return done;
-  cudaError_t e = ct_init();
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_flux_update_mx<256, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_bytes(false));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_flux_update_mx<288, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -872,6 +952,7 @@ cudaError_t fused_init() {
 
 bool fused_stage_ok(const DevGeo &G) {
   return G.eos == PHL_EOS_IDEAL && G.nspec == 0 && G.wstr == 8 && G.act[0] && G.act[1] && G.act[2] &&
+         G.n[0] >= 4 && G.n[1] >= 4 && G.n[2] >= 4 &&
          G.recon != PHL_RECON_PQH;   // the tile stages two ghost layers; PQH needs three
 }
 
@@ -944,7 +1025,10 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
 #undef PHL_FUSED1
   ++*nl;
   if (M.pipeline3) {   // Contact-CT with the face update, then the next stage's primitives and raw flags
-    launch_ct_prim(G, M, first, last, b, M.fmax, s, nl, prof);
+    const int ctx = (G.n[0] + CTT - 1) / CTT, cty = (G.n[1] + CTT - 1) / CTT, ctz = (G.n[2] + CTT - 1) / CTT;
+    PHL_LAUNCH(KC_EMF, prof, s, k_ct_faces<<<ctx * cty * ctz, 256, 0, s>>>(G, S, ctx, cty));
+    ++*nl;
+    launch_prim_flags(G, M, last, M.fmax, s, nl, prof);
     return;
   }
   Box bs = make_box(0, G.n[0] + 1, 0, G.n[1] + 1, 0, G.n[2] + 1);

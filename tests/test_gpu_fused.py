@@ -176,7 +176,7 @@ def test_three_launch_stage_matches_six_launch_stage(P, bc, shape):
     pr = _box_bc(bc)
     pr.eps_sf = 0.02   # a low threshold: many flagged cells and HLL faces
     outs = []
-    for on in (shape, 100 + shape):
+    for on in (200 + shape, shape):
         g = P.Grid(pr, precision="mixed")
         g.set_fused(on)
         g.load()
@@ -196,6 +196,7 @@ def test_three_launch_stage_resumes_after_set_state(P):
     run equals one that never stopped."""
     pr = _box_bc("periodic_xy", (16, 24, 20))
     g = P.Grid(pr, precision="mixed")
+    g.set_fused(201)
     g.load()
     g.step(3)
     mid = g.get_state()
@@ -203,6 +204,7 @@ def test_three_launch_stage_resumes_after_set_state(P):
     ref = g.get_state()
     g.close()
     h = P.Grid(pr, precision="mixed")
+    h.set_fused(201)
     h.load()
     h.step(1)                      # leaves W of a state about to be replaced
     h.set_state(mid["cons"], mid["bx"], mid["by"], mid["bz"])
