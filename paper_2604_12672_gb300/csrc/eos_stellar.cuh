@@ -148,7 +148,7 @@ template <typename R, int M> struct YC {
   R g[M][3], dg[M][3];
 };
 
-template <typename R, int M>
+template <typename R, int M, int M0 = 0>
 __device__ __forceinline__ void contract(const Table &t, const XB<R> &X, int j, YC<R, M> &c) {
   c.j = j;
   const long k0 = ((long)j * t.nx + X.i) * NQ, k1 = k0 + (long)t.nx * NQ;
@@ -170,8 +170,10 @@ __device__ __forceinline__ void contract(const Table &t, const XB<R> &X, int j, 
       const int sl = qslot(p, r);
       const R D00 = q[0][0][sl], D10 = q[0][1][sl] - q[0][0][sl], D01 = q[1][0][sl] - q[0][0][sl];
       const R D11 = (q[1][1][sl] - q[0][1][sl]) - (q[1][0][sl] - q[0][0][sl]);
-      g0 += D00 * X.h[0][p] + D10 * X.h[1][p];
-      d0 += D01 * X.h[0][p] + D11 * X.h[1][p];
+      if (M0 == 0) {
+        g0 += D00 * X.h[0][p] + D10 * X.h[1][p];
+        d0 += D01 * X.h[0][p] + D11 * X.h[1][p];
+      }
       if (M > 1) {
         g1 += D00 * X.d[0][p] + D10 * X.d[1][p];
         d1 += D01 * X.d[0][p] + D11 * X.d[1][p];
@@ -181,9 +183,22 @@ __device__ __forceinline__ void contract(const Table &t, const XB<R> &X, int j, 
         d2 += D01 * X.e[0][p] + D11 * X.e[1][p];
       }
     }
-    c.g[0][r] = g0; c.dg[0][r] = d0;
+    if (M0 == 0) { c.g[0][r] = g0; c.dg[0][r] = d0; }
     if (M > 1) { c.g[1][r] = g1; c.dg[1][r] = d1; }
     if (M > 2) { c.g[2][r] = g2; c.dg[2][r] = d2; }
+  }
+}
+
+// The full contraction of interval j, reusing the values of a Newton
+// iteration's contraction c1 when it holds the same interval.
+template <typename R>
+__device__ __forceinline__ void contract_full(const Table &t, const XB<R> &X, int j, const YC<R, 1> *c1, YC<R, 3> &c) {
+  if (c1 && c1->j == j) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) { c.g[0][r] = c1->g[0][r]; c.dg[0][r] = c1->dg[0][r]; }
+    contract<R, 3, 1>(t, X, j, c);
+  } else {
+    contract<R, 3>(t, X, j, c);
   }
 }
 
@@ -236,12 +251,13 @@ __device__ __forceinline__ void yeval(const Table &t, const YC<R, M> &c, R v, TV
 // Biquintic evaluation of f and its derivatives up to second order at
 // (x, y = ln T) given the x-part.
 template <typename R>
-__device__ __forceinline__ bool table_eval_xb(const Table &t, const XB<R> &X, R y, TV<R> &o) {
+__device__ __forceinline__ bool table_eval_xb(const Table &t, const XB<R> &X, R y, TV<R> &o,
+                                              const YC<R, 1> *c1 = nullptr) {
   int j;
   R v;
   if (!(X.ok && yloc<R>(t, y, j, v))) return false;
   YC<R, 3> c;
-  contract<R, 3>(t, X, j, c);
+  contract_full<R>(t, X, j, c1, c);
   yeval<R, 3>(t, c, v, o);
   return true;
 }
@@ -257,9 +273,9 @@ template <typename R> struct EosOut { R P, e, cv, Pr, PT, ge, gc; };
 // (irho = 1/rho and iab = 1/abar: fixed during an inversion, formed once).
 template <typename R>
 __device__ __forceinline__ bool eos_rt_xy(const Table &t, const XB<R> &X, R rho, R irho, R T, R lnT, R iab,
-                                          EosOut<R> &o) {
+                                          EosOut<R> &o, const YC<R, 1> *c1 = nullptr) {
   TV<R> q;
-  if (!table_eval_xb<R>(t, X, lnT, q)) return false;
+  if (!table_eval_xb<R>(t, X, lnT, q, c1)) return false;
   const R iT = R(1) / T;
   const R Pe = q.fx - q.f;
   const R ee = (q.f - q.fy) * irho;
@@ -346,14 +362,12 @@ __device__ __forceinline__ R next_lnT(R T, R lnT, R Tn) {
 // The iterations evaluate only e and c_v; the full EOS (P, gamma_e, gamma_c)
 // is evaluated once, at the final T.  Returns the iteration count or -1.
 template <typename R>
-__device__ __forceinline__ int newton_loop(const Table &t, const XB<R> &X, R rho, R irho, R eint, R iab, R &T, R tol,
-                                           int maxit, EosOut<R> &o, bool have, R e0, R cv0, R lnT0) {
+__device__ __forceinline__ int newton_loop(const Table &t, const XB<R> &X, YC<R, 1> &c, R rho, R irho, R eint, R iab,
+                                           R &T, R tol, int maxit, EosOut<R> &o, bool have, R e0, R cv0, R lnT0) {
   const R Tlo = sizeof(R) == 8 ? (R)t.Tlo : (R)t.Tlof, Thi = sizeof(R) == 8 ? (R)t.Thi : (R)t.Thif;
   R lo = Tlo, hi = Thi;
   if (!(T > Tlo && T < Thi)) { T = sqrt(Tlo * Thi); have = false; }
-  R lnT = have ? lnT0 : log(T);   // e0, cv0 were evaluated at (T, lnT0)
-  YC<R, 1> c;
-  c.j = -1;
+  R lnT = have ? lnT0 : log(T);   // e0, cv0 were evaluated at (T, lnT0), c may hold its interval
   for (int it = 1; it <= maxit; ++it) {
     R e = e0, cv = cv0;   // the first iteration may come evaluated
     if (!(have && it == 1) && !eos_ecv_xy<R>(t, X, c, irho, T, lnT, iab, e, cv)) return -1;
@@ -362,7 +376,7 @@ __device__ __forceinline__ int newton_loop(const Table &t, const XB<R> &X, R rho
       const R Tn = T + de / cv;
       lnT = next_lnT<R>(T, lnT, Tn);
       T = Tn;
-      if (!eos_rt_xy<R>(t, X, rho, irho, T, lnT, iab, o)) return -1;
+      if (!eos_rt_xy<R>(t, X, rho, irho, T, lnT, iab, o, &c)) return -1;
       return it;
     }
     if (de > R(0)) lo = T; else hi = T;
@@ -378,7 +392,9 @@ template <typename R>
 __device__ __forceinline__ int eos_invert(const Table &t, R rho, R eint, R abar, R ye, R &T, R tol, int maxit,
                                           EosOut<R> &o) {
   const XB<R> X = xbasis<R>(t, log(rho * ye * R(NAV)));   // rho and Y_e fixed
-  return newton_loop<R>(t, X, rho, R(1) / rho, eint, R(1) / abar, T, tol, maxit, o, false, R(0), R(0), R(0));
+  YC<R, 1> c;
+  c.j = -1;
+  return newton_loop<R>(t, X, c, rho, R(1) / rho, eint, R(1) / abar, T, tol, maxit, o, false, R(0), R(0), R(0));
 }
 
 // The FP32 phase of the mixed inversion: Newton on e and c_v only, until
@@ -419,20 +435,20 @@ __device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, doub
   // only degrade it to FP32's ~1e-6
   const XB<double> X = xbasis<double>(t, log(rho * ye * NAV));
   const double irho = 1.0 / rho, iab = 1.0 / abar;
+  YC<double, 1> c;
+  c.j = -1;
   {
     double e, cv;
-    YC<double, 1> c;
-    c.j = -1;
     if (T > t.Tlo && T < t.Thi) {
       const double lnT = log(T);
       if (eos_ecv_xy<double>(t, X, c, irho, T, lnT, iab, e, cv) && fabs(eint - e) < 1e-4 * fabs(eint))
-        return newton_loop<double>(t, X, rho, irho, eint, iab, T, tol, maxit, o, true, e, cv, lnT);
+        return newton_loop<double>(t, X, c, rho, irho, eint, iab, T, tol, maxit, o, true, e, cv, lnT);
     }
   }
   float Tf = (float)T;
   const int it32 = newton_fp32(t, (float)rho, (float)eint, (float)abar, (float)ye, Tf, 1e-5f, maxit < 12 ? maxit : 12);
   if (isfinite(Tf) && Tf > 0.0f) T = (double)Tf;
-  const int it64 = newton_loop<double>(t, X, rho, irho, eint, iab, T, tol, maxit, o, false, 0.0, 0.0, 0.0);
+  const int it64 = newton_loop<double>(t, X, c, rho, irho, eint, iab, T, tol, maxit, o, false, 0.0, 0.0, 0.0);
   return it64 < 0 ? -1 : it64 + (it32 > 0 ? it32 : 12);
 }
 

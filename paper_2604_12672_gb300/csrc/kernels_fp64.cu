@@ -206,7 +206,8 @@ void launch_stage_fp64(const DevGeo &G, const StageBufs &S, cudaStream_t s, int 
     for (int d = 0; d < 3; ++d) rng(d, G.ge[d], G.ge[d], l[d], h[d]);
     Box b = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
     if (G.eos == 1) {
-      launch_eos_cells<double>(G, S.Uin, S.Bin, nullptr, nullptr, S.Tin, S.Tout, S.W, S.dflag, s, &nl, prof);
+      launch_eos_cells<double>(G, S.Uin, S.Bin, nullptr, nullptr, S.Tin, S.Tout, S.W, S.dflag, s, &nl, prof,
+                               S.cfl_dmax, const_cast<double *>(S.dt));
     } else {
       PHL_LAUNCH(KC_PRIM, prof, s, k_prim<<<grid3(b), block3(b), 0, s>>>(G, b, S.Uin, S.Bin, S.W, S.dflag));
       ++nl;

@@ -96,13 +96,14 @@ __global__ void k_mlp_guess(DevGeo G, Box box, const double *__restrict__ U, con
 // else FP32 Newton iterations to about 1e-5 finished in FP64 to the same
 // tolerance.  First guess: Tg (the network's, with use_mlp) or Tin; with the
 // network the previous temperature is the fallback.  Writes W and T_out.
+// One interior cell of k_eos_cells: inversion, deviations, and (rate) the
+// CFL sum of the cell, returned (0 otherwise).
 template <typename R>
-__global__ void __launch_bounds__(256, 2) k_eos_cells(DevGeo G, Box box, const double *__restrict__ U,
-                                                       const double *__restrict__ Bf, const float *__restrict__ dU,
-                                                       const float *__restrict__ dB, const double *__restrict__ Tin,
-                                                       double *__restrict__ Tout, R *__restrict__ W, int *dflag) {
-  int c[3];
-  if (!cell3(box, c)) return;
+__device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, const double *__restrict__ U,
+                                                const double *__restrict__ Bf, const float *__restrict__ dU,
+                                                const float *__restrict__ dB, const double *__restrict__ Tin,
+                                                double *__restrict__ Tout, R *__restrict__ W, int *dflag,
+                                                bool rate) {
   const long p = sidx(G, c[0], c[1], c[2]);
   const CellState cs = cell_state(G, p, U, Bf, dU, dB);
   const double rho = cs.rho, eint = cs.eint;
@@ -150,6 +151,44 @@ __global__ void __launch_bounds__(256, 2) k_eos_cells(DevGeo G, Box box, const d
     for (int v = 0; v <= W_P; ++v) w[v] = W[wix<float>(G, v, q)];
     write_aux(G, W, q, w);
   }
+  if (!rate) return 0.0;
+  // CFL sum of the cell (as k_dt_stellar, from this stage's inversion)
+  const double a2 = o.gc * o.P / rho, b2 = (bx * bx + by * by + bz * bz) / rho;
+  const double vv[3] = {vx, vy, vz}, bb[3] = {bx, by, bz};
+  double sum = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    if (!G.act[d]) continue;
+    const double bd2 = bb[d] * bb[d] / rho;
+    const double disc = fmax((a2 + b2) * (a2 + b2) - 4.0 * a2 * bd2, 0.0);
+    sum += (fabs(vv[d]) + sqrt(0.5 * (a2 + b2 + sqrt(disc)))) / G.dx[d];
+  }
+  return (sum == sum) ? sum : INFINITY;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, 2) k_eos_cells(DevGeo G, Box box, const double *__restrict__ U,
+                                                       const double *__restrict__ Bf, const float *__restrict__ dU,
+                                                       const float *__restrict__ dB, const double *__restrict__ Tin,
+                                                       double *__restrict__ Tout, R *__restrict__ W, int *dflag,
+                                                       unsigned long long *cfl_dmax) {
+  int c[3];
+  const bool in = cell3(box, c);
+  if (cfl_dmax) {   // the CFL rate of the step's own state (Eq. cfl), from this inversion
+    double m = 0.0;
+    if (in) m = eos_cell_step<R>(G, c, U, Bf, dU, dB, Tin, Tout, W, dflag, true);
+    for (int o2 = 16; o2 > 0; o2 >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o2));
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+      atomicMax(cfl_dmax, (unsigned long long)__double_as_longlong(v));
+    }
+    return;
+  }
+  if (!in) return;
+  eos_cell_step<R>(G, c, U, Bf, dU, dB, Tin, Tout, W, dflag, false);
 }
 
 // Cells of the work layout outside the interior take the deviations of the
@@ -322,13 +361,19 @@ __global__ void k_prim_to_cons(DevGeo G, Box box, const double *__restrict__ pri
 
 template <typename R>
 void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
-                      const double *Tin, double *Tout, R *W, int *dflag, cudaStream_t s, int *nl, Prof *prof) {
+                      const double *Tin, double *Tout, R *W, int *dflag, cudaStream_t s, int *nl, Prof *prof,
+                      unsigned long long *cfl_dmax, double *dt) {
   Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
   if (G.use_mlp) {
     PHL_LAUNCH(KC_PRIM, prof, s, k_mlp_guess<<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout));
     if (nl) *nl += 1;
   }
-  PHL_LAUNCH(KC_PRIM, prof, s, k_eos_cells<R><<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout, W, dflag));
+  PHL_LAUNCH(KC_PRIM, prof, s,
+             k_eos_cells<R><<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout, W, dflag, cfl_dmax));
+  if (cfl_dmax) {   // the step's CFL step from the rates this inversion folded in
+    PHL_LAUNCH(KC_DT, prof, s, k_dt_finalize_st<<<1, 1, 0, s>>>(G.cfl, cfl_dmax, dt));
+    if (nl) *nl += 1;
+  }
   int l[3], h[3];
   for (int d = 0; d < 3; ++d) {
     if (G.act[d]) { l[d] = -G.ge[d]; h[d] = G.n[d] + G.ge[d]; } else { l[d] = 0; h[d] = 1; }
@@ -338,9 +383,11 @@ void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const 
   if (nl) *nl += 2;
 }
 template void launch_eos_cells<double>(const DevGeo &, const double *, const double *, const float *, const float *,
-                                       const double *, double *, double *, int *, cudaStream_t, int *, Prof *);
+                                       const double *, double *, double *, int *, cudaStream_t, int *, Prof *,
+                                       unsigned long long *, double *);
 template void launch_eos_cells<float>(const DevGeo &, const double *, const double *, const float *, const float *,
-                                      const double *, double *, float *, int *, cudaStream_t, int *, Prof *);
+                                      const double *, double *, float *, int *, cudaStream_t, int *, Prof *,
+                                      unsigned long long *, double *);
 
 void launch_dt_stellar(const DevGeo &G, bool fp32, const double *U, const double *Bf, const double *T,
                        unsigned long long *dmax, double *dt, int *dflag, cudaStream_t s, int *nl, Prof *prof) {

@@ -229,8 +229,9 @@ void launch_dt(phl_grid *g, int *nl) {
 }
 
 void do_stage(phl_grid *g, const double *Uin, const double *Bin, double *Uout, double *Bout, double a,
-              double b, int *nl) {
+              double b, int *nl, unsigned long long *cfl_dmax = nullptr) {
   StageBufs S;
+  S.cfl_dmax = cfl_dmax;
   S.Uin = Uin; S.Bin = Bin; S.Ubase = g->U; S.Bbase = g->B;
   S.Uout = Uout; S.Bout = Bout; S.a = a; S.b = b; S.dt = g->dt;
   S.W = g->W; S.F[0] = g->F[0]; S.F[1] = g->F[1]; S.F[2] = g->F[2]; S.E = g->E;
@@ -603,10 +604,12 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
         launch_set_scalar(g->dt, dt, g->stream, g->prof.on ? &g->prof : nullptr);
         ++nl;
       }
-    } else {
+    } else if (g->G.eos != PHL_EOS_STELLAR) {
       launch_dt(g, &nl);
       if (three) CK(cudaMemsetAsync(g->fmax, 0, sizeof(unsigned int), g->stream), "clear CFL maximum");
     }
+    // stellar EOS with the device CFL step: the first stage's inversion gives it
+    unsigned long long *cfl_dmax = (g->G.eos == PHL_EOS_STELLAR && !(dt > 0.0)) ? g->dmax : nullptr;
     if (g->mixed) {
       const double bs3[3] = {1.0, 0.25, 2.0 / 3.0}, bs2[2] = {1.0, 0.5};
       const int ns = g->desc.rk == 2 ? 2 : 3;
@@ -620,6 +623,7 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
       M.pipeline3 = three;
       M.primed = primed;
       M.fmax = g->fmax;
+      M.cfl_dmax = cfl_dmax;
       for (int st = 0; st < ns; ++st) {
         M.Tin = g->T;
         M.Tout = g->T2;
@@ -628,10 +632,10 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
         if (g->T) std::swap(g->T, g->T2);
       }
     } else if (g->desc.rk == 2) {
-      do_stage(g, g->U, g->B, g->U1, g->B1, 0.0, 1.0, &nl);
+      do_stage(g, g->U, g->B, g->U1, g->B1, 0.0, 1.0, &nl, cfl_dmax);
       do_stage(g, g->U1, g->B1, g->U, g->B, 0.5, 0.5, &nl);
     } else {
-      do_stage(g, g->U, g->B, g->U1, g->B1, 0.0, 1.0, &nl);
+      do_stage(g, g->U, g->B, g->U1, g->B1, 0.0, 1.0, &nl, cfl_dmax);
       do_stage(g, g->U1, g->B1, g->U1, g->B1, 0.75, 0.25, &nl);
       do_stage(g, g->U1, g->B1, g->U, g->B, 1.0 / 3.0, 2.0 / 3.0, &nl);
     }

@@ -264,6 +264,7 @@ struct StageBufs {
   const double *Tin;           // temperature guesses (stellar), state layout
   double *Tout;                // temperatures found by this stage
   int *dflag;                  // device error word
+  unsigned long long *cfl_dmax = nullptr;   // stellar: the CFL step from this stage's inversion into dt
 };
 
 // Buffers of the mixed-precision stage (kernels_mixed.cu): FP64 U^n, FP32
@@ -277,6 +278,7 @@ struct MixedBufs {
   int *dflag;
   const double *Tin;           // stellar EOS: guesses in, temperatures out
   double *Tout;
+  unsigned long long *cfl_dmax = nullptr;   // stellar: the CFL step from this stage's inversion into dt
   const void *tmapW = nullptr; // TMA descriptor of W (fused path), or null
   int fused_variant = 1;       // launch shape of the fused tile kernel (phl_set_fused)
   unsigned test_extra_tx = 0;  // timeout test: bytes announced to the tile barrier that never arrive
@@ -338,9 +340,12 @@ struct GridView {
 GridView grid_view(::phl_grid *g);
 
 // Stellar EOS path (kernels_stellar.cu)
+// cfl_dmax non-null: also the CFL step of this state into *dt (the step's
+// first stage; cfl_dmax is the grid's double-bits maximum, left at zero).
 template <typename R>
 void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
-                      const double *Tin, double *Tout, R *W, int *dflag, cudaStream_t s, int *nl, Prof *prof);
+                      const double *Tin, double *Tout, R *W, int *dflag, cudaStream_t s, int *nl, Prof *prof,
+                      unsigned long long *cfl_dmax = nullptr, double *dt = nullptr);
 void launch_dt_stellar(const DevGeo &G, bool fp32, const double *U, const double *Bf, const double *T,
                        unsigned long long *dmax, double *dt, int *dflag, cudaStream_t s, int *nl, Prof *prof);
 cudaError_t stellar_background(const DevGeo &G, int L, double *bg, const double *bgX_host);
