@@ -118,6 +118,22 @@ def lib():
         L.ora_ep_first.argtypes = [C.c_double, C.c_double, _dp]
         L.ora_ep_derivs.restype = C.c_int
         L.ora_ep_derivs.argtypes = [C.c_double, C.c_double, _dp]
+        L.ora_sphere_create.restype = C.c_void_p
+        L.ora_sphere_create.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double] + [_dp] * 6 + \
+            [C.c_double, C.c_int, C.c_double]
+        L.ora_sphere_free.restype = None
+        L.ora_sphere_free.argtypes = [C.c_void_p]
+        for nm in ("ncells", "nfaces", "nedges", "nabi_faces"):
+            getattr(L, "ora_sphere_" + nm).restype = C.c_long
+            getattr(L, "ora_sphere_" + nm).argtypes = [C.c_void_p]
+        L.ora_sphere_geometry.restype = C.c_int
+        L.ora_sphere_geometry.argtypes = [C.c_void_p] + [_dp] * 5
+        L.ora_sphere_dt.restype = C.c_double
+        L.ora_sphere_dt.argtypes = [C.c_void_p] + [_dp] * 4
+        L.ora_sphere_run.restype = C.c_int
+        L.ora_sphere_run.argtypes = [C.c_void_p] + [_dp] * 4 + [C.c_int, C.c_double, _dp]
+        L.ora_sphere_divb.restype = C.c_int
+        L.ora_sphere_divb.argtypes = [C.c_void_p] + [_dp] * 4
         L.ora_ct_corner.restype = C.c_double
         L.ora_ct_corner.argtypes = [_dp, _dp, _dp, C.c_double, C.c_double]
         L.ora_fd.restype = C.c_double
@@ -387,6 +403,71 @@ def ct_corner(Ef, Ec, F, rho, smax):
     faces' mass fluxes (see oracle.h)."""
     a = [np.ascontiguousarray(v, dtype=np.float64) for v in (Ef, Ec, F)]
     return lib().ora_ct_corner(*[_ptr(v) for v in a], float(rho), float(smax))
+
+
+class Sphere:
+    """The oracle's cubed-sphere shell (sphere.c) for a problem from
+    workloads.shell_problem: state arrays in the ABI layout."""
+
+    def __init__(self, pr, riemann="lhlld", cfl=0.4, mach_thr=0.6, wb=True):
+        self.pr = pr
+        bg = pr.bg if wb and pr.bg is not None else None
+        keep = []
+
+        def arr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return _ptr(a)
+        self._keep = keep
+        self.h = lib().ora_sphere_create(pr.N, pr.Nr, pr.r_in, pr.r_out, pr.gamma,
+                                         arr(bg["rho_c"]) if bg else None, arr(bg["p_c"]) if bg else None,
+                                         arr(bg["rho_f"]) if bg else None, arr(bg["p_f"]) if bg else None,
+                                         arr(pr.g_c), arr(pr.heat), cfl, _RIEMANN[riemann], mach_thr)
+        if not self.h:
+            raise RuntimeError("oracle sphere creation failed")
+
+    def __del__(self):
+        try:
+            lib().ora_sphere_free(self.h)
+        except Exception:
+            pass
+
+    def counts(self):
+        L = lib()
+        return dict(cells=L.ora_sphere_ncells(self.h), faces=L.ora_sphere_nfaces(self.h),
+                    edges=L.ora_sphere_nedges(self.h), abi_faces=L.ora_sphere_nabi_faces(self.h))
+
+    def geometry(self):
+        n = self.counts()
+        vol, xc, csum = np.zeros(n["cells"]), np.zeros((n["cells"], 3)), np.zeros((n["cells"], 3))
+        S, xf = np.zeros((n["faces"], 3)), np.zeros((n["faces"], 3))
+        lib().ora_sphere_geometry(self.h, _ptr(vol), _ptr(xc), _ptr(S), _ptr(xf), _ptr(csum))
+        return dict(vol=vol, xc=xc, S=S, xf=xf, csum=csum)
+
+    def _state(self, st):
+        st = st or dict(cons=self.pr.cons, pa=self.pr.pa, pb=self.pr.pb, pr=self.pr.pr)
+        return {k: np.ascontiguousarray(st[k], dtype=np.float64).copy() for k in ("cons", "pa", "pb", "pr")}
+
+    def dt(self, state=None):
+        st = self._state(state)
+        return lib().ora_sphere_dt(self.h, *[_ptr(st[k]) for k in ("cons", "pa", "pb", "pr")])
+
+    def run(self, nsteps, state=None, dt_fixed=0.0):
+        st = self._state(state)
+        last = C.c_double()
+        rc = lib().ora_sphere_run(self.h, *[_ptr(st[k]) for k in ("cons", "pa", "pb", "pr")], int(nsteps),
+                                  float(dt_fixed), C.byref(last))
+        if rc:
+            raise RuntimeError(f"oracle sphere run failed ({rc})")
+        return st, last.value
+
+    def divb(self, state=None):
+        st = self._state(state)
+        out = np.zeros(self.counts()["cells"])
+        lib().ora_sphere_divb(self.h, *[_ptr(st[k]) for k in ("pa", "pb", "pr")], _ptr(out))
+        return out
 
 
 def ep_first(nnet, T):

@@ -12,7 +12,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["mhd.c", "eos.c", "mlp.c", "diffusion.c", "poisson.c"]
+SOURCES = ["mhd.c", "eos.c", "mlp.c", "diffusion.c", "poisson.c", "sphere.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 

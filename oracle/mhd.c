@@ -428,6 +428,11 @@ void ora_riemann(const double *wl, const double *wr, double bn, int nspec,
   riemann_core(wl, wr, bn, nspec, solver, mach_thr, f, &up);
 }
 
+void ora_riemann_up(const double *wl, const double *wr, double bn, int nspec,
+                    int solver, double mach_thr, double *f, int *up) {
+  riemann_core(wl, wr, bn, nspec, solver, mach_thr, f, up);
+}
+
 static void riemann_core(const double *wl, const double *wr, double bn, int nspec,
                          int solver, double mach_thr, double *f, int *up) {
   rstate L, R;

@@ -172,6 +172,31 @@ int ora_eos_rt(const ora_cfg *cfg, double rho, double T, const double *X,
 int ora_eos_invert(const ora_cfg *cfg, double rho, double eint, const double *X,
                    double *T_inout, double *P, double *ge, double *gc, int *iters);
 
+/* ---------------- cubed-sphere shell (sphere.c) ----------------
+ * Six equiangular patches of N x N angular cells times Nr radial cells, r in
+ * [r_in, r_out] uniform; ideal gas; per-shell background rho_c, p_c (Nr, at
+ * the shell's middle radius) and rho_f, p_f (Nr + 1, at the shell radii), or
+ * NULL (no well-balancing); inward gravity g_c (Nr) and heating (Nr) or NULL.
+ * Layouts: see sphere.c. */
+typedef struct ora_sphere ora_sphere;
+ora_sphere *ora_sphere_create(int N, int Nr, double r_in, double r_out, double gamma, const double *rho_c,
+                              const double *p_c, const double *rho_f, const double *p_f, const double *g_c,
+                              const double *heat, double cfl, int riemann, double mach_thr);
+void ora_sphere_free(ora_sphere *s);
+long ora_sphere_ncells(const ora_sphere *s);
+long ora_sphere_nfaces(const ora_sphere *s);
+long ora_sphere_nedges(const ora_sphere *s);
+long ora_sphere_nabi_faces(const ora_sphere *s);
+/* vol[nc], xc[nc][3], S[nf][3] (unique faces), xf[nf][3], csum[nc][3] (sum of a
+ * cell's outward area vectors); any may be NULL */
+int ora_sphere_geometry(const ora_sphere *s, double *vol, double *xc, double *S, double *xf, double *csum);
+double ora_sphere_dt(const ora_sphere *s, const double *cons, const double *pa, const double *pb, const double *pr);
+int ora_sphere_run(const ora_sphere *s, double *cons, double *pa, double *pb, double *pr, int nsteps,
+                   double dt_fixed, double *dt_last);
+int ora_sphere_divb(const ora_sphere *s, const double *pa, const double *pb, const double *pr, double *div);
+void ora_riemann_up(const double *wl, const double *wr, double bn, int nspec, int solver, double mach_thr,
+                    double *f, int *up);
+
 /* ---------------- MLP (mlp.c) ---------------- */
 void ora_mlp_forward(const double *w, int nin, int nh, const double *x, long n,
                      double *y);

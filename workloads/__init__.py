@@ -523,3 +523,278 @@ def lumpy_density(xf, seed, nblob=5, floor=1e-3):
         w = rng.uniform(0.04, 0.12)
         rho += rng.uniform(0.2, 1.0) * np.exp(-((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) / w ** 2)
     return rho
+
+
+# ---------------------------------------------------------------------------
+# cubed-sphere shell: six equiangular patches of N x N angular cells times Nr
+# radial cells between r_in and r_out (the layout of the library's phl_sphere
+# calls and of the oracle's sphere.c):
+#   cons[v, p, k, j, i]   (5, 6, Nr, N, N), v = rho, m_x, m_y, m_z, E
+#   pa[p, k, j, i]        magnetic flux through alpha faces i = 0..N  (6, Nr, N, N+1)
+#   pb[p, k, j, i]        ... beta faces j = 0..N                      (6, Nr, N+1, N)
+#   pr[p, k, j, i]        ... radial faces k = 0..Nr                   (6, Nr+1, N, N)
+# each flux in its patch's orientation (+alpha, +beta, +r).  Patch p has
+# centre direction c_p and axes a_p (alpha), b_p (beta), a_p x b_p = c_p;
+# the direction of (alpha, beta) is c_p + tan(alpha) a_p + tan(beta) b_p.
+# ---------------------------------------------------------------------------
+
+PATCH_C = np.array([[1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], dtype=float)
+PATCH_A = np.array([[0, 1, 0], [-1, 0, 0], [0, -1, 0], [1, 0, 0], [0, 1, 0], [0, 1, 0]], dtype=float)
+PATCH_B = np.array([[0, 0, 1], [0, 0, 1], [0, 0, 1], [0, 0, 1], [-1, 0, 0], [1, 0, 0]], dtype=float)
+
+
+@dataclasses.dataclass
+class ShellProblem:
+    name: str
+    N: int
+    Nr: int
+    r_in: float
+    r_out: float
+    gamma: float
+    cons: np.ndarray
+    pa: np.ndarray
+    pb: np.ndarray
+    pr: np.ndarray
+    bg: Optional[dict] = None      # rho_c, p_c (Nr, shell middles), rho_f, p_f (Nr + 1, shell radii)
+    g_c: Optional[np.ndarray] = None   # inward gravity at the shell middles (Nr,)
+    heat: Optional[np.ndarray] = None  # volumetric heating per shell (Nr,)
+    cfl: float = 0.4
+    riemann: str = "lhlld"
+    mach_thr: float = 0.6
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def ncells(self):
+        return 6 * self.N * self.N * self.Nr
+
+    def copy(self):
+        return dataclasses.replace(self, cons=self.cons.copy(), pa=self.pa.copy(), pb=self.pb.copy(),
+                                   pr=self.pr.copy())
+
+
+def _tline(m, N):
+    q = 2 * m - N
+    if q == N:
+        return 1.0
+    if q == -N:
+        return -1.0
+    t = math.tan(abs(q) * (math.pi / (4.0 * N)))
+    return -t if q < 0 else t
+
+
+def shell_dirs(N):
+    """Unit directions of the angular vertices, shape (6, N+1, N+1, 3) [p, j, i]."""
+    t = np.array([_tline(m, N) for m in range(N + 1)])
+    d = (PATCH_C[:, None, None, :] + t[None, None, :, None] * PATCH_A[:, None, None, :]
+         + t[None, :, None, None] * PATCH_B[:, None, None, :])
+    return d / np.linalg.norm(d, axis=-1, keepdims=True)
+
+
+def lane_emden(n_poly=1.5, nodes=100000):
+    """Lane-Emden theta(xi), theta'(xi) of index n by RK4 on `nodes` steps up to
+    the first zero (series start at xi = 1e-6)."""
+    def f(x, y):
+        th = max(y[0], 0.0)
+        return np.array([y[1], -th ** n_poly - 2.0 * y[1] / x])
+    xi1_guess = {1.0: math.pi, 1.5: 3.65375, 2.0: 4.35287, 3.0: 6.89685}.get(n_poly, 3.65375)
+    x0 = 1e-6
+    h = (xi1_guess - x0) / nodes
+    xs = np.empty(nodes + 1)
+    ys = np.empty((nodes + 1, 2))
+    y = np.array([1.0 - x0 * x0 / 6.0, -x0 / 3.0])
+    x = x0
+    xs[0], ys[0] = x, y
+    for q in range(nodes):
+        k1 = f(x, y)
+        k2 = f(x + 0.5 * h, y + 0.5 * h * k1)
+        k3 = f(x + 0.5 * h, y + 0.5 * h * k2)
+        k4 = f(x + h, y + h * k3)
+        y = y + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+        x += h
+        xs[q + 1], ys[q + 1] = x, y
+    return xs, ys
+
+
+def shell_background(r_mid, r_faces, r_star=1.2, n_poly=1.5, rho_c=1.0, G=1.0):
+    """A Lane-Emden polytrope of index n whose surface sits at r_star (beyond
+    the shell): rho = rho_c theta^n, P = K rho_c^(1+1/n) theta^(n+1),
+    g = 4 pi G rho_c alpha (-theta'), r = alpha xi (hydrostatic by
+    construction), at the shell middles and the shell radii."""
+    xs, ys = lane_emden(n_poly)
+    xi1 = xs[np.argmax(ys[:, 0] <= 0.0)] if (ys[:, 0] <= 0.0).any() else xs[-1]
+    alpha = r_star / xi1
+    K = 4.0 * math.pi * G * alpha * alpha * rho_c ** (1.0 - 1.0 / n_poly) / (n_poly + 1.0)
+
+    def at(r):
+        xi = np.asarray(r) / alpha
+        th = np.interp(xi, xs, ys[:, 0])
+        dth = np.interp(xi, xs, ys[:, 1])
+        rho = rho_c * th ** n_poly
+        p = K * rho_c ** (1.0 + 1.0 / n_poly) * th ** (n_poly + 1.0)
+        g = 4.0 * math.pi * G * rho_c * alpha * (-dth)
+        return rho, p, g
+
+    rc, pc, gc = at(r_mid)
+    rf, pf, _ = at(r_faces)
+    return dict(rho_c=rc, p_c=pc, rho_f=rf, p_f=pf), gc
+
+
+def _edge_integral(A, x0, x1, radial, r, ng=8):
+    """Line integral of the vector potential A(x) from x0 to x1 along a radial
+    segment or a great-circle arc of radius r (Gauss-Legendre, ng points)."""
+    gx, gw = np.polynomial.legendre.leggauss(ng)
+    if radial:
+        t = 0.5 * (gx + 1.0)
+        pts = x0[None, :] + t[:, None] * (x1 - x0)[None, :]
+        dx = (x1 - x0)
+        return 0.5 * float(np.sum(gw * np.einsum("ij,j->i", A(pts), dx)))
+    u, w = x0 / r, x1 / r
+    th = math.atan2(np.linalg.norm(np.cross(u, w)), float(np.dot(u, w)))
+    wp = w - np.dot(w, u) * u
+    wp /= np.linalg.norm(wp)
+    s = 0.5 * th * (gx + 1.0)
+    pts = r * (np.cos(s)[:, None] * u[None, :] + np.sin(s)[:, None] * wp[None, :])
+    tang = r * (-np.sin(s)[:, None] * u[None, :] + np.cos(s)[:, None] * wp[None, :])
+    return 0.5 * th * float(np.sum(gw * np.einsum("ij,ij->i", A(pts), tang)))
+
+
+def shell_fluxes_from_potential(N, Nr, r, A):
+    """Magnetic fluxes (pa, pb, pr) of B = curl A through every face, each the
+    circulation of A around the face (counter-clockwise about the patch's
+    +alpha, +beta or +r normal).  Each edge's line integral is computed once,
+    from the lexicographically smaller end, and reused with its sign, so the
+    discrete divergence of every cell vanishes up to rounding."""
+    d = shell_dirs(N)
+    cache = {}
+
+    def edge(v0, v1, radial, rr):
+        k0, k1 = tuple(v0), tuple(v1)
+        if k0 <= k1:
+            key, sgn, a, b = (k0, k1), 1.0, v0, v1
+        else:
+            key, sgn, a, b = (k1, k0), -1.0, v1, v0
+        if key not in cache:
+            cache[key] = _edge_integral(A, np.array(a), np.array(b), radial, rr)
+        return sgn * cache[key]
+
+    def P(p, j, i, k):   # vertex position (rounded to stabilise the cache key: exact shared values)
+        return tuple(float(x) for x in r[k] * d[p, j, i])
+
+    def loop(vs, radials, radii):
+        t = 0.0
+        for q in range(4):
+            t += edge(np.array(vs[q]), np.array(vs[(q + 1) % 4]), radials[q], radii[q])
+        return t
+
+    pa = np.zeros((6, Nr, N, N + 1))
+    pb = np.zeros((6, Nr, N + 1, N))
+    prr = np.zeros((6, Nr + 1, N, N))
+    for p in range(6):
+        for k in range(Nr):
+            for j in range(N):
+                for i in range(N + 1):   # alpha face: corners (i,j,k) (i,j+1,k) (i,j+1,k+1) (i,j,k+1), CCW about +alpha
+                    vs = [P(p, j, i, k), P(p, j + 1, i, k), P(p, j + 1, i, k + 1), P(p, j, i, k + 1)]
+                    pa[p, k, j, i] = loop(vs, [False, True, False, True], [r[k], 0, r[k + 1], 0])
+            for j in range(N + 1):
+                for i in range(N):       # beta face: corners (i,j,k) (i,j,k+1) (i+1,j,k+1) (i+1,j,k), CCW about +beta
+                    vs = [P(p, j, i, k), P(p, j, i, k + 1), P(p, j, i + 1, k + 1), P(p, j, i + 1, k)]
+                    pb[p, k, j, i] = loop(vs, [True, False, True, False], [0, r[k + 1], 0, r[k]])
+        for k in range(Nr + 1):
+            for j in range(N):
+                for i in range(N):       # radial face: corners (i,j) (i+1,j) (i+1,j+1) (i,j+1), CCW about +r
+                    vs = [P(p, j, i, k), P(p, j, i + 1, k), P(p, j + 1, i + 1, k), P(p, j + 1, i, k)]
+                    prr[p, k, j, i] = loop(vs, [False] * 4, [r[k]] * 4)
+    return pa, pb, prr
+
+
+def shell_problem(N, Nr, r_in=0.2, r_out=1.0, seed=1234, amp=1e-3, beta=1e5, heat_frac=0.3, mach_heat=1e-3,
+                  gamma=5.0 / 3.0, vel_amp=0.0, background=True, gravity=True, cfl=0.4, name=None,
+                  uniform=False):
+    """The cubed-sphere shell of the spherical configuration: a Lane-Emden
+    n = 1.5 polytrope (surface at 1.2, so the whole shell r in [0.2, 1] is
+    inside the star) in hydrostatic balance under its own radial gravity,
+    isobaric density noise amp U(-1, 1) (seeded), a seed field from the
+    toroidal vector potential A = f(r) (z x r) / r with f vanishing at both
+    walls (poloidal, dipole-like, no flux through the walls), plasma beta
+    2 P_hat(r_mid) / B^2 at the shell's middle radius, heating in the inner
+    heat_frac of the radial span sized so (q dr / rho)^(1/3) ~ mach_heat c_s.
+    vel_amp > 0 adds a swirl u = vel_amp c_s (z x r) / r.  uniform: density and
+    pressure of the shell's middle everywhere, no gravity and no background
+    (a medium in which the total energy is conserved)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = r_in + (r_out - r_in) * np.arange(Nr + 1) / Nr
+    rm = 0.5 * (r[:-1] + r[1:])
+    bg, g_c = shell_background(rm, r)
+    if uniform:
+        rmid = 0.5 * (r_in + r_out)
+        rho0, p0 = float(np.interp(rmid, rm, bg["rho_c"])), float(np.interp(rmid, rm, bg["p_c"]))
+        bg = dict(rho_c=np.full(Nr, rho0), p_c=np.full(Nr, p0), rho_f=np.full(Nr + 1, rho0), p_f=np.full(Nr + 1, p0))
+        gravity, background = False, False
+    if not gravity:
+        g_c = np.zeros(Nr)
+    d = shell_dirs(N)
+    # cell centre directions [p, j, i]
+    dc = d[:, :-1, :-1] + d[:, 1:, :-1] + d[:, :-1, 1:] + d[:, 1:, 1:]
+    dc /= np.linalg.norm(dc, axis=-1, keepdims=True)
+    xc = rm[None, :, None, None, None] * dc[:, None, :, :, :]          # (6, Nr, N, N, 3)
+    rho_hat = bg["rho_c"][None, :, None, None] * np.ones((6, Nr, N, N))
+    p_hat = bg["p_c"][None, :, None, None] * np.ones((6, Nr, N, N))
+    rho = rho_hat * (1.0 + amp * rng.uniform(-1.0, 1.0, rho_hat.shape))
+    p = p_hat.copy()
+    cs_mid = math.sqrt(gamma * float(np.interp(0.5 * (r_in + r_out), rm, bg["p_c"]))
+                       / float(np.interp(0.5 * (r_in + r_out), rm, bg["rho_c"])))
+    vel = np.zeros(xc.shape)
+    if vel_amp > 0.0:
+        zr = np.stack([-xc[..., 1], xc[..., 0], np.zeros(xc.shape[:-1])], axis=-1)
+        vel = vel_amp * cs_mid * zr / np.linalg.norm(xc, axis=-1, keepdims=True)
+    p_mid = float(np.interp(0.5 * (r_in + r_out), rm, bg["p_c"]))
+    span = r_out - r_in
+    if beta and beta > 0:
+        b0 = math.sqrt(2.0 * p_mid / beta)
+
+        def fr(rr):
+            return (rr - r_in) ** 2 * (r_out - rr) ** 2 / (0.25 * span) ** 4
+
+        def A(x):
+            rr = np.linalg.norm(x, axis=-1)
+            zx = np.stack([-x[..., 1], x[..., 0], np.zeros(x.shape[:-1])], axis=-1)
+            return (b0 * 0.25 * span * fr(rr) / rr)[..., None] * zx
+        pa, pb, prr = shell_fluxes_from_potential(N, Nr, r, A)
+    else:
+        pa, pb, prr = np.zeros((6, Nr, N, N + 1)), np.zeros((6, Nr, N + 1, N)), np.zeros((6, Nr + 1, N, N))
+    heat = None
+    if heat_frac and heat_frac > 0:
+        rho_b = float(bg["rho_c"][0])
+        q = rho_b * (mach_heat * cs_mid) ** 3 / (heat_frac * span)
+        heat = np.where(rm < r_in + heat_frac * span, q, 0.0)
+    # cell-centred field for the energy: the average of the two face fields of
+    # each direction would be the Cartesian definition; here the energy is
+    # assembled with the field the method forms from the face fluxes, so it is
+    # left to the caller (E_mag is tiny at beta 1e5); the initial magnetic
+    # energy is taken from the potential field at the cell centres.
+    if beta and beta > 0:
+        eps = 1e-6 * span
+        def curlA(x):
+            out = np.zeros(x.shape)
+            for a_ in range(3):
+                e = np.zeros(3)
+                e[a_] = eps
+                dA = (A(x + e) - A(x - e)) / (2 * eps)   # dA / dx_a
+                # (curl A)_i = eps_ijk d_j A_k
+                if a_ == 0:
+                    out[..., 1] -= dA[..., 2]; out[..., 2] += dA[..., 1]
+                elif a_ == 1:
+                    out[..., 2] -= dA[..., 0]; out[..., 0] += dA[..., 2]
+                else:
+                    out[..., 0] -= dA[..., 1]; out[..., 1] += dA[..., 0]
+            return out
+        bc = curlA(xc)
+    else:
+        bc = np.zeros(xc.shape)
+    cons = np.zeros((5, 6, Nr, N, N))
+    cons[0] = rho
+    cons[1:4] = np.moveaxis(rho[..., None] * vel, -1, 0)
+    cons[4] = p / (gamma - 1.0) + 0.5 * rho * (vel ** 2).sum(-1) + 0.5 * (bc ** 2).sum(-1)
+    return ShellProblem(name=name or f"shell_{N}x{N}x{Nr}", N=N, Nr=Nr, r_in=r_in, r_out=r_out, gamma=gamma,
+                        cons=cons, pa=pa, pb=pb, pr=prr, bg=bg if background else None, g_c=g_c, heat=heat,
+                        cfl=cfl, meta=dict(seed=seed, amp=amp, beta=beta, r=r, r_mid=rm))
