@@ -567,6 +567,79 @@ phl_status phl_poisson_ghost(phl_poisson *p, double *ghost, int where);
  * sides.  Synchronous. */
 phl_status phl_poisson_gravity(phl_poisson *p, const double *phi, double *gx, double *gy, double *gz, int where);
 
+/* ---------------------------------------------------------------------
+ * MHD on a cubed-sphere shell (the stage of Sects. 2.4-2.9 on the grid of
+ * Sect. 2.3, in FP64).
+ *
+ * The shell r_in < r < r_out is covered by six equiangular patches of N x N
+ * angular cells (Sect. 2.3) times Nr uniform radial cells.  Patch p has the
+ * centre direction c_p, the alpha axis a_p and the beta axis b_p (a x b = c):
+ *   p:   0     1     2     3     4     5
+ *   c:  +x    +y    -x    -y    +z    -z
+ *   a:  +y    -x    -y    +x    +y    +y
+ *   b:  +z    +z    +z    +z    -x    +x
+ * and the cube-surface point of the angles (alpha, beta) in [-pi/4, pi/4]^2
+ * is c + tan(alpha) a + tan(beta) b; grid line m of N sits at the angle
+ * (2m - N) pi / (4N).  The paper runs hydrodynamics on this grid; the field
+ * here is its extension: magnetic fluxes through the faces advanced by the
+ * circulation of Contact-CT edge EMFs (Sect. 2.4, Eq. induction), momentum
+ * and field as Cartesian vectors, van Leer PLM along the mesh lines (Sect.
+ * 2.5), LHLLD / HLLD / HLL (Sect. 2.6) in each face's normal frame, the
+ * deviation form with a radial background (Sect. 2.8), radial gravity and
+ * heating, SSP-RK3 (Sect. 2.9), reflecting radial walls.  Ideal gas.
+ *
+ * State layout (doubles, host or device as `where` says):
+ *   cons  [5][6][Nr][N][N]: rho, m_x, m_y, m_z, E (Cartesian components);
+ *   pa    [6][Nr][N][N+1]: flux through the alpha faces (i = 0..N), along +a_p;
+ *   pb    [6][Nr][N+1][N]: flux through the beta faces (j = 0..N), along +b_p;
+ *   pr    [6][Nr+1][N][N]: flux through the radial faces (k = 0..Nr), outwards.
+ * A face on a seam between two patches has a copy in each; set_state reads
+ * the copy of the lower-numbered array position (alpha before beta, then
+ * patch, shell, j, i), get_state writes both, each in its patch's direction.
+ * The library copies the arrays; it keeps no caller pointer. */
+typedef struct {
+  int N, Nr;                /* angular cells per patch side, radial cells; >= 2 */
+  double r_in, r_out;       /* 0 < r_in < r_out                                 */
+  double gamma;             /* > 1                                              */
+  double cfl;               /* Courant number (Eq. cfl), > 0                    */
+  int riemann;              /* PHL_LHLLD / PHL_HLLD / PHL_HLL                   */
+  double mach_thr;          /* LHLLD Mach threshold, > 0                        */
+  const double *rho_c, *p_c;  /* host: hydrostatic background at the shell    */
+                              /* middles (Nr each), or both null with rho_f,  */
+                              /* p_f: no background (full-state fluxes)       */
+  const double *rho_f, *p_f;  /* host: the background at the Nr + 1 radii     */
+  const double *g_c;        /* host, nullable: inward gravity per shell (Nr)    */
+  const double *heat;       /* host, nullable: heating per unit volume (Nr)     */
+  void *stream;             /* cudaStream_t (null: the legacy default stream)   */
+} phl_sphere_desc;
+typedef struct phl_sphere phl_sphere;
+
+/* Builds the mesh on the host and uploads it (profiles are read here only).
+ * PHL_EINVAL (sizes, radii, gamma, cfl, solver, a partial background, more
+ * than 2^31 faces or edges), PHL_ENOMEM. */
+phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out);
+void phl_sphere_destroy(phl_sphere *s);
+/* Unique cells, faces (seam faces once) and edges of the mesh. */
+phl_status phl_sphere_counts(const phl_sphere *s, long *cells, long *faces, long *edges);
+/* Loads a state (layout above).  Host sources: synchronous; device sources:
+ * stream-ordered.  Clears the error flags. */
+phl_status phl_sphere_set_state(phl_sphere *s, const double *cons, const double *pa, const double *pb,
+                                const double *pr, int where);
+/* Writes the state back and synchronises the stream; returns PHL_ENEGATIVE or
+ * PHL_ENAN when a kernel since set_state met rho <= 0, P <= 0 or a
+ * non-finite value. */
+phl_status phl_sphere_get_state(phl_sphere *s, double *cons, double *pa, double *pb, double *pr, int where);
+/* The CFL step of the current state (Eq. cfl with the fast speed along each
+ * cell's three mesh directions over the distance between its opposite face
+ * centres), to host memory; synchronous. */
+phl_status phl_sphere_compute_dt(phl_sphere *s, double *dt_out);
+/* nsteps SSP-RK3 steps of size dt (dt <= 0: each step takes its CFL step
+ * on the device); asynchronous on the stream.  Errors show in
+ * phl_sphere_check / get_state. */
+phl_status phl_sphere_step(phl_sphere *s, double dt, int nsteps);
+/* Synchronises the stream; PHL_ENEGATIVE / PHL_ENAN as in get_state. */
+phl_status phl_sphere_check(phl_sphere *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -143,6 +143,14 @@ _SIGS = {
                                     C.POINTER(C.c_double)]),
     "phl_poisson_ghost": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "phl_poisson_gravity": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_sphere_create": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    "phl_sphere_destroy": (None, [C.c_void_p]),
+    "phl_sphere_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_long), C.POINTER(C.c_long), C.POINTER(C.c_long)]),
+    "phl_sphere_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_sphere_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_sphere_compute_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "phl_sphere_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "phl_sphere_check": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -654,6 +662,97 @@ class Poisson:
     def close(self):
         if self.h:
             lib().phl_poisson_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SphereDesc(C.Structure):
+    _fields_ = [("N", C.c_int), ("Nr", C.c_int), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("gamma", C.c_double), ("cfl", C.c_double), ("riemann", C.c_int), ("mach_thr", C.c_double),
+                ("rho_c", C.c_void_p), ("p_c", C.c_void_p), ("rho_f", C.c_void_p), ("p_f", C.c_void_p),
+                ("g_c", C.c_void_p), ("heat", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class Sphere:
+    """MHD on a cubed-sphere shell (phl_sphere_*): six equiangular patches of
+    N x N angular cells times Nr radial cells, FP64 on the device.  The state
+    is cons [5][6][Nr][N][N] and the face fluxes pa [6][Nr][N][N+1],
+    pb [6][Nr][N+1][N], pr [6][Nr+1][N][N], as numpy float64 arrays (host)
+    or CUDA tensors (device).  `bg` holds rho_c, p_c (Nr) and rho_f, p_f
+    (Nr + 1), or is None for full-state fluxes."""
+
+    def __init__(self, N, Nr, r_in, r_out, gamma=5.0 / 3.0, cfl=0.4, riemann="lhlld", mach_thr=0.6, bg=None,
+                 g_c=None, heat=None, stream=None):
+        self.N, self.Nr = int(N), int(Nr)
+        keep = []
+
+        def arr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data
+        d = SphereDesc()
+        d.N, d.Nr, d.r_in, d.r_out = self.N, self.Nr, float(r_in), float(r_out)
+        d.gamma, d.cfl, d.riemann, d.mach_thr = float(gamma), float(cfl), RIEMANN[riemann], float(mach_thr)
+        if bg is not None:
+            d.rho_c, d.p_c, d.rho_f, d.p_f = (arr(bg[k]) for k in ("rho_c", "p_c", "rho_f", "p_f"))
+        d.g_c, d.heat, d.stream = arr(g_c), arr(heat), stream
+        h = C.c_void_p()
+        _check(lib().phl_sphere_create(C.byref(d), C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_problem(cls, pr, wb=True, stream=None):
+        """From a workloads.ShellProblem (its solver, CFL, background, gravity
+        and heating); wb=False drops the background."""
+        return cls(pr.N, pr.Nr, pr.r_in, pr.r_out, gamma=pr.gamma, cfl=pr.cfl, riemann=pr.riemann,
+                   mach_thr=pr.mach_thr, bg=pr.bg if wb else None, g_c=pr.g_c, heat=pr.heat, stream=stream)
+
+    def shapes(self):
+        N, Nr = self.N, self.Nr
+        return dict(cons=(5, 6, Nr, N, N), pa=(6, Nr, N, N + 1), pb=(6, Nr, N + 1, N), pr=(6, Nr + 1, N, N))
+
+    def counts(self):
+        c, f, e = C.c_long(), C.c_long(), C.c_long()
+        _check(lib().phl_sphere_counts(self.h, C.byref(c), C.byref(f), C.byref(e)))
+        return dict(cells=c.value, faces=f.value, edges=e.value)
+
+    def set_state(self, cons, pa, pb, pr):
+        ptrs = [_ptr(a) for a in (cons, pa, pb, pr)]
+        for (a, (p, w)), (k, shp) in zip(zip((cons, pa, pb, pr), ptrs), self.shapes().items()):
+            assert tuple(a.shape) == shp, (k, tuple(a.shape), shp)
+        assert len({w for _, w in ptrs}) == 1, "all state arrays must live in the same memory"
+        _check(lib().phl_sphere_set_state(self.h, *[p for p, _ in ptrs], ptrs[0][1]))
+
+    def get_state(self, out=None):
+        """Returns dict(cons, pa, pb, pr); `out` (a dict of arrays or tensors of
+        the right shapes) receives them instead of new numpy arrays."""
+        if out is None:
+            out = {k: np.zeros(s) for k, s in self.shapes().items()}
+        ptrs = [_ptr(out[k]) for k in ("cons", "pa", "pb", "pr")]
+        _check(lib().phl_sphere_get_state(self.h, *[p for p, _ in ptrs], ptrs[0][1]))
+        return out
+
+    def step(self, nsteps=1, dt=0.0):
+        _check(lib().phl_sphere_step(self.h, float(dt), int(nsteps)))
+
+    def compute_dt(self):
+        v = C.c_double()
+        _check(lib().phl_sphere_compute_dt(self.h, C.byref(v)))
+        return v.value
+
+    def check(self):
+        _check(lib().phl_sphere_check(self.h))
+
+    def close(self):
+        if self.h:
+            lib().phl_sphere_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,1006 @@
+// sphere.cu -- the explicit MHD stage on a cubed-sphere shell (FP64): six
+// equiangular patches of N x N angular cells times Nr radial cells between
+// r_in and r_out, reflecting radial walls, the well-balanced deviation form
+// under radial gravity, Contact-CT on the magnetic fluxes of the faces.
+//
+// The paper runs hydrodynamics on its cubed-sphere grid (Sect. 2.3) and MHD
+// on its other grids; MHD here is the same scheme carried to this grid:
+//   - The shell is a hexahedral mesh whose every cell, face and edge is an
+//     angular entity (a cell, a side or a vertex of the spherical quad mesh
+//     of the six patches, built once on the host) times a radial index.  A
+//     side or vertex on a patch seam is one entity, shared by the patches
+//     that meet there, so a seam face's flux and a seam edge's EMF are
+//     computed once and enter every cell and face that touches them.
+//   - Momentum and B are Cartesian vectors: dU/dt = -(1/V) sum_f s_f F_f |S_f|
+//     + S with the faces' area vectors S_f, no geometric source terms.
+//   - van Leer PLM (Sect. 2.5) along mesh lines: a face's stencil is its two
+//     cells and the cells across their opposite faces, mirrored at a wall;
+//     LHLLD / HLLD / HLL (Sect. 2.6) in the face's normal frame, deviation
+//     form (Sect. 2.8).
+//   - The field lives as face fluxes Phi_f; dPhi_f/dt is minus the
+//     circulation of the edge EMFs about the face (Eq. induction).  Edge EMFs
+//     are Contact-CT (Sect. 2.4) on E . l over the edge's four faces and
+//     cells, upwinded by the faces' mass fluxes; a radial edge at a cube
+//     corner (three faces) takes their mean; an edge on a wall has none.
+//   - Cell-centred B = (1/V) sum_f s_f Phi_f x_f (divergence theorem on B x).
+// Geometry from the factorisation: an angular face of side s between radii
+// r0 < r1 has the normal n_s (of the side's great-circle plane) and the area
+// (r1^2 - r0^2) theta_s / 2; a radial face of angular cell a at radius r has
+// the area r^2 |A_a| along A_a, the vector area of the unit spherical quad;
+// cell volumes are (r1^3 - r0^3) Omega_a / 3.
+//
+// Internal layout: cells c = k NC + a (NC = 6 N^2 angular cells, a = (p N + j)
+// N + i); angular faces f = k NS + s (NS = 12 N^2 sides), then radial faces
+// FA + k NC + a; radial edges e = k NV + v (NV = 6 N^2 + 2 vertices), then
+// angular edges ER + k NS + s.  One thread per cell, face or edge.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <map>
+#include <stdexcept>
+#include <utility>
+#include <vector>
+
+#include "phl.h"
+#include "phl_internal.cuh"
+#include "riemann.cuh"
+
+using namespace phl;
+
+namespace {
+
+constexpr double PI_S = 3.14159265358979323846;
+constexpr int SPT = 256;
+
+// patch frames: centre c, alpha axis a, beta axis b, a x b = c
+const int PCI[6][3] = {{1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+const int PAI[6][3] = {{0, 1, 0}, {-1, 0, 0}, {0, -1, 0}, {1, 0, 0}, {0, 1, 0}, {0, 1, 0}};
+const int PBI[6][3] = {{0, 0, 1}, {0, 0, 1}, {0, 0, 1}, {0, 0, 1}, {-1, 0, 0}, {1, 0, 0}};
+
+struct V3 {
+  double x, y, z;
+};
+__host__ __device__ inline V3 v3(double x, double y, double z) { return V3{x, y, z}; }
+__host__ __device__ inline V3 operator+(V3 a, V3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__host__ __device__ inline V3 operator-(V3 a, V3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__host__ __device__ inline V3 operator*(V3 a, double s) { return v3(a.x * s, a.y * s, a.z * s); }
+__host__ __device__ inline double dot3(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ inline V3 cross3(V3 a, V3 b) {
+  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline double len3(V3 a) { return sqrt(dot3(a, a)); }
+__host__ __device__ inline V3 unit3(V3 a) { return a * (1.0 / len3(a)); }
+__host__ __device__ inline V3 ld3(const double *p, long i) { return v3(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
+
+// ---------------------------------------------------------------------------
+// host: the angular mesh
+
+struct Ang {
+  int N = 0;
+  long NC = 0, NS = 0, NV = 0;
+  std::vector<double> vd;              // 3 per vertex: unit direction
+  // sides
+  std::vector<int> sv0, sv1;           // vertices (sv0 < sv1)
+  std::vector<int> sL, sR, sLL, sRR;   // cells on the -n / +n side, and across their opposite sides
+  std::vector<double> sn, sl, smid, sth;   // unit normal, chord direction (v0 -> v1), midpoint direction, angle
+  std::vector<signed char> s_in, s_v0, s_v1, s_swap;   // boundary orientations; Contact-CT ordering
+  // cells
+  std::vector<int> cs;                 // 4 per cell: sides -a, +a, -b, +b
+  std::vector<signed char> csg, crs;   // 4 per cell: +1 when n_s leaves the cell; orientation in the radial face
+  std::vector<double> com, cdc, cna, cva;   // solid angle, centre direction, unit vector area, |vector area|
+  // vertices: Contact-CT of the radial edges
+  std::vector<unsigned char> vcnt;     // 3 (cube corner) or 4
+  std::vector<int> vcell, vside;       // 4 per vertex, cyclic for 4
+  std::vector<signed char> vsgn;       // 4 per vertex: +1 when the side's -n cell is the from-cell
+  // ABI copies of the angular faces: alpha [p][j][i] (i = 0..N), then beta [p][j][i] (j = 0..N)
+  std::vector<int> abi_s;
+  std::vector<signed char> abi_sg, abi_own;
+};
+
+std::array<int, 3> vcode(int p, int i, int j, int N) {   // grid-line codes in [-N, N] per axis
+  std::array<int, 3> c;
+  for (int d = 0; d < 3; ++d) c[d] = PCI[p][d] * N + PAI[p][d] * (2 * i - N) + PBI[p][d] * (2 * j - N);
+  return c;
+}
+
+// the cube-surface point of the codes (tan of q pi / 4N per axis, exactly
+// +-1 on the centre axis), normalised
+V3 vdir(const std::array<int, 3> &c, int N) {
+  double x[3];
+  for (int d = 0; d < 3; ++d) {
+    const int q = c[d], a = std::abs(q);
+    const double t = a == N ? 1.0 : (a == 0 ? 0.0 : tan(a * (PI_S / (4.0 * N))));
+    x[d] = q < 0 ? -t : t;
+  }
+  return unit3(v3(x[0], x[1], x[2]));
+}
+
+double tri_solid_angle(V3 a, V3 b, V3 c) {   // Van Oosterom & Strackee (1983)
+  return 2.0 * atan2(fabs(dot3(a, cross3(b, c))), 1.0 + dot3(a, b) + dot3(b, c) + dot3(c, a));
+}
+
+// vector area of a unit spherical quadrilateral with great-circle sides,
+// corners counter-clockwise: half the sum of each side's angle times the unit
+// normal of its plane
+V3 quad_vector_area(const V3 *d) {
+  V3 s = v3(0, 0, 0);
+  for (int q = 0; q < 4; ++q) {
+    const V3 u = d[q], w = d[(q + 1) % 4], c = cross3(u, w);
+    s = s + unit3(c) * (0.5 * atan2(len3(c), dot3(u, w)));
+  }
+  return s;
+}
+
+void build_ang(int N, Ang &M) {
+  M.N = N;
+  const int N1 = N + 1;
+  // vertices (only patch-boundary vertices can be shared)
+  std::map<std::array<int, 3>, int> vid;
+  std::vector<V3> vd;
+  std::vector<int> av(6 * N1 * N1);
+  for (int p = 0; p < 6; ++p)
+    for (int j = 0; j <= N; ++j)
+      for (int i = 0; i <= N; ++i) {
+        const bool bnd = i == 0 || i == N || j == 0 || j == N;
+        const auto c = vcode(p, i, j, N);
+        auto it = bnd ? vid.find(c) : vid.end();
+        int id;
+        if (it == vid.end()) {
+          id = (int)vd.size();
+          if (bnd) vid[c] = id;
+          vd.push_back(vdir(c, N));
+        } else {
+          id = it->second;
+        }
+        av[(p * N1 + j) * N1 + i] = id;
+      }
+  M.NV = (long)vd.size();
+  if (M.NV != 6L * N * N + 2) throw std::runtime_error("cubed-sphere vertex count");
+  auto AV = [&](int p, int i, int j) { return av[(p * N1 + j) * N1 + i]; };
+  auto CELL = [&](int p, int i, int j) { return (p * N + j) * N + i; };
+  M.NC = 6L * N * N;
+  // sides in ABI order: alpha sides (from (i, j) to (i, j+1)), then beta
+  // sides (from (i, j) to (i+1, j)); the first copy fixes the orientation
+  M.abi_s.assign(2 * 6 * N * N1, -1);
+  M.abi_sg.assign(2 * 6 * N * N1, 1);
+  M.abi_own.assign(2 * 6 * N * N1, 0);
+  std::map<std::pair<int, int>, int> sid;
+  std::vector<V3> nrm;
+  long t = 0;
+  for (int kind = 0; kind < 2; ++kind)
+    for (int p = 0; p < 6; ++p) {
+      const int JJ = kind == 1 ? N1 : N, II = kind == 0 ? N1 : N;
+      for (int j = 0; j < JJ; ++j)
+        for (int i = 0; i < II; ++i, ++t) {
+          const int v0 = AV(p, i, j), v1 = kind == 0 ? AV(p, i, j + 1) : AV(p, i + 1, j);
+          const int lo = kind == 0 ? (i > 0 ? CELL(p, i - 1, j) : -1) : (j > 0 ? CELL(p, i, j - 1) : -1);
+          const int hi = kind == 0 ? (i < N ? CELL(p, i, j) : -1) : (j < N ? CELL(p, i, j) : -1);
+          const bool bnd = kind == 0 ? (i == 0 || i == N) : (j == 0 || j == N);
+          const int *ax = kind == 0 ? PAI[p] : PBI[p];
+          const V3 axv = v3(ax[0], ax[1], ax[2]);
+          const std::pair<int, int> key(std::min(v0, v1), std::max(v0, v1));
+          auto it = bnd ? sid.find(key) : sid.end();
+          if (it != sid.end()) {   // the second copy of a seam side
+            const int s = it->second;
+            const bool same = dot3(nrm[s], axv) > 0.0;
+            M.abi_s[t] = s;
+            M.abi_sg[t] = same ? 1 : -1;
+            if (lo >= 0) { if (same) M.sL[s] = lo; else M.sR[s] = lo; }
+            if (hi >= 0) { if (same) M.sR[s] = hi; else M.sL[s] = hi; }
+            continue;
+          }
+          const int s = (int)M.sv0.size();
+          if (bnd) sid[key] = s;
+          M.abi_s[t] = s;
+          M.abi_own[t] = 1;
+          M.sv0.push_back(key.first);
+          M.sv1.push_back(key.second);
+          V3 n = unit3(cross3(vd[v0], vd[v1]));
+          if (dot3(n, axv) < 0.0) n = n * -1.0;
+          nrm.push_back(n);
+          M.sL.push_back(lo);
+          M.sR.push_back(hi);
+        }
+    }
+  M.NS = (long)M.sv0.size();
+  if (M.NS != 12L * N * N) throw std::runtime_error("cubed-sphere side count");
+  // cells
+  M.cs.resize(4 * M.NC);
+  M.csg.resize(4 * M.NC);
+  M.crs.resize(4 * M.NC);
+  M.com.resize(M.NC);
+  M.cdc.resize(3 * M.NC);
+  M.cna.resize(3 * M.NC);
+  M.cva.resize(M.NC);
+  const long na = 6L * N * N1;
+  for (int p = 0; p < 6; ++p)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        const int a = CELL(p, i, j);
+        const long u4[4] = {(long)(p * N + j) * N1 + i, (long)(p * N + j) * N1 + i + 1, na + (long)(p * N1 + j) * N + i,
+                            na + (long)(p * N1 + j + 1) * N + i};
+        for (int m = 0; m < 4; ++m) {
+          const int s = M.abi_s[u4[m]];
+          M.cs[4 * a + m] = s;
+          M.csg[4 * a + m] = M.sL[s] == a ? 1 : -1;
+        }
+        const V3 d[4] = {vd[AV(p, i, j)], vd[AV(p, i + 1, j)], vd[AV(p, i + 1, j + 1)], vd[AV(p, i, j + 1)]};
+        M.com[a] = tri_solid_angle(d[0], d[1], d[2]) + tri_solid_angle(d[0], d[2], d[3]);
+        const V3 dc = unit3(d[0] + d[1] + d[2] + d[3]), A = quad_vector_area(d);
+        const double Al = len3(A);
+        M.cdc[3 * a] = dc.x; M.cdc[3 * a + 1] = dc.y; M.cdc[3 * a + 2] = dc.z;
+        M.cna[3 * a] = A.x / Al; M.cna[3 * a + 1] = A.y / Al; M.cna[3 * a + 2] = A.z / Al;
+        M.cva[a] = Al;
+      }
+  // side geometry and stencils
+  M.sn.resize(3 * M.NS); M.sl.resize(3 * M.NS); M.smid.resize(3 * M.NS); M.sth.resize(M.NS);
+  M.sLL.resize(M.NS); M.sRR.resize(M.NS);
+  M.s_in.resize(M.NS); M.s_v0.resize(M.NS); M.s_v1.resize(M.NS); M.s_swap.resize(M.NS);
+  auto across_opposite = [&](int a, int s) {   // the cell across a's side opposite to s
+    int m = 0;
+    for (int q = 0; q < 4; ++q)
+      if (M.cs[4 * a + q] == s) m = q;
+    const int g = M.cs[4 * a + (m ^ 1)];
+    return M.sL[g] == a ? M.sR[g] : M.sL[g];
+  };
+  for (long s = 0; s < M.NS; ++s) {
+    if (M.sL[s] < 0 || M.sR[s] < 0) throw std::runtime_error("cubed-sphere side without two cells");
+    const V3 d0 = vd[M.sv0[s]], d1 = vd[M.sv1[s]], n = nrm[s];
+    const V3 l = unit3(d1 - d0), mid = unit3(d0 + d1);
+    M.sn[3 * s] = n.x; M.sn[3 * s + 1] = n.y; M.sn[3 * s + 2] = n.z;
+    M.sl[3 * s] = l.x; M.sl[3 * s + 1] = l.y; M.sl[3 * s + 2] = l.z;
+    M.smid[3 * s] = mid.x; M.smid[3 * s + 1] = mid.y; M.smid[3 * s + 2] = mid.z;
+    M.sth[s] = atan2(len3(cross3(d0, d1)), dot3(d0, d1));
+    M.sLL[s] = across_opposite(M.sL[s], (int)s);
+    M.sRR[s] = across_opposite(M.sR[s], (int)s);
+    if (M.sLL[s] < 0 || M.sRR[s] < 0) throw std::runtime_error("cubed-sphere stencil");
+    // counter-clockwise about n: the edge at the face's inner radius (x_e -
+    // x_f along -mid), and the radial edges at v0 and v1 (along d_v - mid)
+    M.s_in[s] = dot3(l, cross3(n, mid * -1.0)) > 0.0 ? 1 : -1;
+    M.s_v0[s] = dot3(d0, cross3(n, d0 - mid)) > 0.0 ? 1 : -1;
+    M.s_v1[s] = dot3(d1, cross3(n, d1 - mid)) > 0.0 ? 1 : -1;
+    // Contact-CT about the angular edge (s, k): from c00 = (L, k-1) the
+    // a-neighbour is (R, k-1) and the b-neighbour (L, k), unless l . (da x db) < 0
+    const V3 dL = ld3(M.cdc.data(), M.sL[s]), dR = ld3(M.cdc.data(), M.sR[s]);
+    M.s_swap[s] = dot3(l, cross3(dR - dL, dL)) < 0.0 ? 1 : 0;
+  }
+  // radial faces: orientation of each side's angular edge about A_a
+  for (long a = 0; a < M.NC; ++a) {
+    const V3 na_ = ld3(M.cna.data(), a), dc = ld3(M.cdc.data(), a);
+    for (int m = 0; m < 4; ++m) {
+      const int s = M.cs[4 * a + m];
+      M.crs[4 * a + m] = dot3(ld3(M.sl.data(), s), cross3(na_, ld3(M.smid.data(), s) - dc)) > 0.0 ? 1 : -1;
+    }
+  }
+  // vertices: the sides and cells about each radial edge, cyclic
+  M.vcnt.assign(M.NV, 0);
+  M.vcell.assign(4 * M.NV, -1);
+  M.vside.assign(4 * M.NV, -1);
+  M.vsgn.assign(4 * M.NV, 0);
+  std::vector<int> vs(4 * M.NV, -1);
+  for (long s = 0; s < M.NS; ++s)
+    for (int v : {M.sv0[s], M.sv1[s]}) {
+      if (M.vcnt[v] >= 4) throw std::runtime_error("cubed-sphere vertex with more than four sides");
+      vs[4 * v + M.vcnt[v]++] = (int)s;
+    }
+  for (long v = 0; v < M.NV; ++v) {
+    const int n = M.vcnt[v], *S = &vs[4 * v];
+    if (n == 3) {
+      for (int m = 0; m < 3; ++m) M.vside[4 * v + m] = S[m];
+      continue;
+    }
+    if (n != 4) throw std::runtime_error("cubed-sphere vertex without four sides");
+    int cells[8], nc4 = 0;
+    for (int m = 0; m < 4; ++m)
+      for (int c : {M.sL[S[m]], M.sR[S[m]]}) {
+        bool seen = false;
+        for (int q = 0; q < nc4; ++q) seen |= cells[q] == c;
+        if (!seen) cells[nc4++] = c;
+      }
+    if (nc4 != 4) throw std::runtime_error("cubed-sphere vertex without four cells");
+    auto between = [&](int a, int b) {
+      for (int m = 0; m < 4; ++m)
+        if ((M.sL[S[m]] == a && M.sR[S[m]] == b) || (M.sL[S[m]] == b && M.sR[S[m]] == a)) return S[m];
+      return -1;
+    };
+    const int c00 = cells[0];
+    int X = -1, Y = -1, c11 = -1;
+    for (int q = 1; q < 4; ++q)
+      if (between(c00, cells[q]) >= 0) { if (X < 0) X = cells[q]; else Y = cells[q]; }
+    for (int q = 1; q < 4; ++q)
+      if (cells[q] != X && cells[q] != Y) c11 = cells[q];
+    if (X < 0 || Y < 0 || c11 < 0) throw std::runtime_error("cubed-sphere vertex cells not cyclic");
+    const V3 x00 = ld3(M.cdc.data(), c00);
+    const V3 da = ld3(M.cdc.data(), X) - x00, db = ld3(M.cdc.data(), Y) - x00;
+    int c10 = X, c01 = Y;
+    if (dot3(vd[v], cross3(da, db)) < 0.0) std::swap(c10, c01);
+    const int cc[4] = {c00, c10, c11, c01};
+    const int ff[4] = {between(c00, c10), between(c10, c11), between(c01, c11), between(c00, c01)};
+    const int from[4] = {c00, c10, c01, c00};   // the mass flux counts positive leaving this cell
+    for (int m = 0; m < 4; ++m) {
+      if (ff[m] < 0) throw std::runtime_error("cubed-sphere vertex faces not cyclic");
+      M.vcell[4 * v + m] = cc[m];
+      M.vside[4 * v + m] = ff[m];
+      M.vsgn[4 * v + m] = M.sL[ff[m]] == from[m] ? 1 : -1;
+    }
+  }
+  M.vd.resize(3 * M.NV);
+  for (long v = 0; v < M.NV; ++v) { M.vd[3 * v] = vd[v].x; M.vd[3 * v + 1] = vd[v].y; M.vd[3 * v + 2] = vd[v].z; }
+}
+
+// ---------------------------------------------------------------------------
+// device
+
+enum { SW_RHO = 0, SW_U = 1, SW_B = 4, SW_P = 7, SW_N = 8 };
+
+struct SphDev {
+  int N, Nr;
+  long NC, NS, NV, FA, NF, ER, NE, ncell;
+  double gamma, cfl, mach;
+  int riemann;
+  const double *r;   // Nr + 1 radii
+  const double *vd, *sn, *sl, *smid, *sth, *cdc, *cna, *cva, *com;
+  const int *sL, *sR, *sLL, *sRR, *sv0, *sv1, *cs, *vcell, *vside;
+  const signed char *s_in, *s_v0, *s_v1, *s_swap, *csg, *crs, *vsgn;
+  const unsigned char *vcnt;
+  const double *rho_c, *p_c, *rho_f, *p_f, *g_c, *heat;   // null when absent
+  double *W;              // 8 deviations per cell, SoA
+  double *FC, *EF;        // 5 integrated fluxes, 3 face-EMF components per face, SoA
+  signed char *UP;        // contact direction per face
+  double *EE;             // edge EMFs
+  int *dflag;
+};
+
+__device__ __forceinline__ double bg_rho(const SphDev &D, int k) { return D.rho_c ? D.rho_c[k] : 0.0; }
+__device__ __forceinline__ double bg_p(const SphDev &D, int k) { return D.p_c ? D.p_c[k] : 0.0; }
+
+// The six faces of cell (a, k) in the order -a, +a, -b, +b, -r, +r: index,
+// outward sign, centre.
+struct CellFaces {
+  long f[6];
+  double s[6];
+  V3 x[6];
+};
+__device__ __forceinline__ void cell_faces(const SphDev &D, long a, int k, CellFaces &F) {
+  const double rm = 0.5 * (D.r[k] + D.r[k + 1]);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int s = D.cs[4 * a + m];
+    F.f[m] = (long)k * D.NS + s;
+    F.s[m] = D.csg[4 * a + m];
+    F.x[m] = ld3(D.smid, s) * rm;
+  }
+  const V3 dc = ld3(D.cdc, a);
+  F.f[4] = D.FA + (long)k * D.NC + a;
+  F.s[4] = -1.0;
+  F.x[4] = dc * D.r[k];
+  F.f[5] = D.FA + (long)(k + 1) * D.NC + a;
+  F.s[5] = 1.0;
+  F.x[5] = dc * D.r[k + 1];
+}
+
+__device__ __forceinline__ double cell_vol(const SphDev &D, long a, int k) {
+  const double r0 = D.r[k], r1 = D.r[k + 1];
+  return (r1 * r1 * r1 - r0 * r0 * r0) / 3.0 * D.com[a];
+}
+
+__global__ void k_sph_prims(SphDev D, const double *__restrict__ U, const double *__restrict__ phi) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (c >= D.ncell) return;
+  const int k = (int)(c / D.NC);
+  const long a = c - (long)k * D.NC;
+  CellFaces F;
+  cell_faces(D, a, k, F);
+  V3 B = v3(0, 0, 0);
+#pragma unroll
+  for (int m = 0; m < 6; ++m) B = B + F.x[m] * (F.s[m] * phi[F.f[m]]);
+  B = B * (1.0 / cell_vol(D, a, k));
+  const long n = D.ncell;
+  const double rho = U[c];
+  const V3 u = v3(U[n + c] / rho, U[2 * n + c] / rho, U[3 * n + c] / rho);
+  const double P = (D.gamma - 1.0) * (U[4 * n + c] - 0.5 * rho * dot3(u, u) - 0.5 * dot3(B, B));
+  if (!(rho > 0.0) || !(P > 0.0)) atomicOr(D.dflag, FLAG_NEG);
+  if (!isfinite(rho) || !isfinite(P)) atomicOr(D.dflag, FLAG_NAN);
+  D.W[SW_RHO * n + c] = rho - bg_rho(D, k);
+  D.W[(SW_U + 0) * n + c] = u.x; D.W[(SW_U + 1) * n + c] = u.y; D.W[(SW_U + 2) * n + c] = u.z;
+  D.W[(SW_B + 0) * n + c] = B.x; D.W[(SW_B + 1) * n + c] = B.y; D.W[(SW_B + 2) * n + c] = B.z;
+  D.W[SW_P * n + c] = P - bg_p(D, k);
+}
+
+// deviations of cell c, mirrored across a wall of unit normal nw when mir
+__device__ __forceinline__ void load_w(const SphDev &D, long c, bool mir, V3 nw, double *w) {
+#pragma unroll
+  for (int v = 0; v < SW_N; ++v) w[v] = D.W[v * D.ncell + c];
+  if (mir) {
+    V3 u = v3(w[SW_U], w[SW_U + 1], w[SW_U + 2]), b = v3(w[SW_B], w[SW_B + 1], w[SW_B + 2]);
+    u = u - nw * (2.0 * dot3(u, nw));
+    b = b - nw * (2.0 * dot3(b, nw));
+    w[SW_U] = u.x; w[SW_U + 1] = u.y; w[SW_U + 2] = u.z;
+    w[SW_B] = b.x; w[SW_B + 1] = b.y; w[SW_B + 2] = b.z;
+  }
+}
+
+__device__ __forceinline__ double vl_d(double a, double b, double c) {
+  const double dm = b - a, dp = c - b;
+  return dm * dp > 0.0 ? 2.0 * dm * dp / (dm + dp) : 0.0;
+}
+
+__global__ void k_sph_flux(SphDev D, const double *__restrict__ phi) {
+  const long f = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (f >= D.NF) return;
+  double wL[SW_N], wR[SW_N], wLL[SW_N], wRR[SW_N];
+  V3 n;
+  double A, brho = 0.0, bp = 0.0;
+  bool wall = false;
+  if (f < D.FA) {   // angular face (s, k)
+    const int k = (int)(f / D.NS);
+    const long s = f - (long)k * D.NS, base = (long)k * D.NC;
+    const V3 z = v3(0, 0, 0);
+    load_w(D, base + D.sL[s], false, z, wL);
+    load_w(D, base + D.sR[s], false, z, wR);
+    load_w(D, base + D.sLL[s], false, z, wLL);
+    load_w(D, base + D.sRR[s], false, z, wRR);
+    n = ld3(D.sn, s);
+    const double r0 = D.r[k], r1 = D.r[k + 1];
+    A = 0.5 * (r1 * r1 - r0 * r0) * D.sth[s];
+    if (D.rho_c) { brho = D.rho_c[k]; bp = D.p_c[k]; }
+  } else {          // radial face (a, k)
+    const long q = f - D.FA;
+    const int k = (int)(q / D.NC), Nr = D.Nr;
+    const long a = q - (long)k * D.NC;
+    n = ld3(D.cna, a);
+    A = D.r[k] * D.r[k] * D.cva[a];
+    if (D.rho_c) { brho = D.rho_f[k]; bp = D.p_f[k]; }
+    const long c0 = a, cst = D.NC;   // cell (a, kk) = c0 + kk cst
+    if (k == 0) {            // inner wall: the ghost side mirrors cells 0 and 1
+      wall = true;
+      load_w(D, c0, false, n, wR);
+      load_w(D, c0 + cst, false, n, wRR);
+      load_w(D, c0, true, n, wL);
+      load_w(D, c0 + cst, true, n, wLL);
+    } else if (k == Nr) {    // outer wall
+      wall = true;
+      load_w(D, c0 + (Nr - 1) * cst, false, n, wL);
+      load_w(D, c0 + (Nr - 2) * cst, false, n, wLL);
+      load_w(D, c0 + (Nr - 1) * cst, true, n, wR);
+      load_w(D, c0 + (Nr - 2) * cst, true, n, wRR);
+    } else {                 // beside a wall the far cell is the near one's mirror
+      load_w(D, c0 + (k - 1) * cst, false, n, wL);
+      load_w(D, c0 + k * cst, false, n, wR);
+      if (k >= 2) load_w(D, c0 + (k - 2) * cst, false, n, wLL);
+      else load_w(D, c0, true, n, wLL);
+      if (k + 1 <= Nr - 1) load_w(D, c0 + (k + 1) * cst, false, n, wRR);
+      else load_w(D, c0 + (Nr - 1) * cst, true, n, wRR);
+    }
+  }
+  double ql[SW_N], qr[SW_N];
+#pragma unroll
+  for (int v = 0; v < SW_N; ++v) {
+    ql[v] = wL[v] + 0.5 * vl_d(wLL[v], wL[v], wR[v]);
+    qr[v] = wR[v] - 0.5 * vl_d(wL[v], wR[v], wRR[v]);
+  }
+  // tangents from the Cartesian axis least aligned with n
+  const double an0 = fabs(n.x), an1 = fabs(n.y), an2 = fabs(n.z);
+  const int ax = an1 < an0 ? (an2 < an1 ? 2 : 1) : (an2 < an0 ? 2 : 0);
+  const V3 t1 = unit3(cross3(v3(ax == 0, ax == 1, ax == 2), n)), t2 = cross3(n, t1);
+  const V3 ul = v3(ql[SW_U], ql[SW_U + 1], ql[SW_U + 2]), ur = v3(qr[SW_U], qr[SW_U + 1], qr[SW_U + 2]);
+  const V3 bl = v3(ql[SW_B], ql[SW_B + 1], ql[SW_B + 2]), br = v3(qr[SW_B], qr[SW_B + 1], qr[SW_B + 2]);
+  double wl[RD_X0], wr[RD_X0];
+  wl[RD_RHO] = ql[SW_RHO]; wr[RD_RHO] = qr[SW_RHO];
+  wl[RD_UN] = dot3(ul, n); wl[RD_UT1] = dot3(ul, t1); wl[RD_UT2] = dot3(ul, t2);
+  wr[RD_UN] = dot3(ur, n); wr[RD_UT1] = dot3(ur, t1); wr[RD_UT2] = dot3(ur, t2);
+  wl[RD_BT1] = dot3(bl, t1); wl[RD_BT2] = dot3(bl, t2);
+  wr[RD_BT1] = dot3(br, t1); wr[RD_BT2] = dot3(br, t2);
+  wl[RD_P] = ql[SW_P]; wr[RD_P] = qr[SW_P];
+  wl[RD_GE] = wl[RD_GC] = wr[RD_GE] = wr[RD_GC] = 0.0;
+  if (!(brho + wl[RD_RHO] > 0.0 && brho + wr[RD_RHO] > 0.0 && bp + wl[RD_P] > 0.0 && bp + wr[RD_P] > 0.0))
+    atomicOr(D.dflag, FLAG_NEG);
+  GasK<double> K;
+  K.g = D.gamma;
+  K.igm1 = 1.0 / (D.gamma - 1.0);
+  K.ggm1 = D.gamma * K.igm1;
+  double fl[7];
+  int up;
+  riemann_dev<double, 0, true>(wl, wr, phi[f] / A, brho, bp, D.gamma, D.gamma, 0, D.riemann, D.mach, fl, up, K);
+  if (wall) {   // a symmetry plane: only the normal-momentum flux survives
+#pragma unroll
+    for (int q = 0; q < 7; ++q)
+      if (q != RF_MN) fl[q] = 0.0;
+    up = 0;
+  }
+  const V3 fm = n * fl[RF_MN] + t1 * fl[RF_MT1] + t2 * fl[RF_MT2];
+  const V3 fb = t1 * fl[RF_BT1] + t2 * fl[RF_BT2];
+  const long nf = D.NF;
+  D.FC[f] = A * fl[RF_RHO];
+  D.FC[nf + f] = A * fm.x; D.FC[2 * nf + f] = A * fm.y; D.FC[3 * nf + f] = A * fm.z;
+  D.FC[4 * nf + f] = A * fl[RF_E];
+  const V3 ef = cross3(n, fb) * -1.0;   // E_f = -n x F_B
+  D.EF[f] = ef.x; D.EF[nf + f] = ef.y; D.EF[2 * nf + f] = ef.z;
+  D.UP[f] = (signed char)up;
+}
+
+__device__ __forceinline__ double efl(const SphDev &D, long f, V3 l) {
+  return D.EF[f] * l.x + D.EF[D.NF + f] * l.y + D.EF[2 * D.NF + f] * l.z;
+}
+__device__ __forceinline__ double ecl(const SphDev &D, long c, V3 l) {   // (-u x B) . l of a cell
+  const long n = D.ncell;
+  const V3 u = v3(D.W[SW_U * n + c], D.W[(SW_U + 1) * n + c], D.W[(SW_U + 2) * n + c]);
+  const V3 b = v3(D.W[SW_B * n + c], D.W[(SW_B + 1) * n + c], D.W[(SW_B + 2) * n + c]);
+  return -dot3(cross3(u, b), l);
+}
+
+// Contact-CT (Sect. 2.4) on E . l: cells c00, c10, c11, c01 and faces a0
+// (c00|c10), b1 (c10|c11), a1 (c01|c11), b0 (c00|c01); ms: mass-flux signs
+__device__ __forceinline__ double contact_ct(const double *Ec, const double *Ef, const int *ms) {
+  const double E00 = Ec[0], E10 = Ec[1], E11 = Ec[2], E01 = Ec[3];
+  const double Ea0 = Ef[0], Eb1 = Ef[1], Ea1 = Ef[2], Eb0 = Ef[3];
+  const int ma0 = ms[0], mb1 = ms[1], ma1 = ms[2], mb0 = ms[3];
+  const double lo_l = Eb0 - E00, lo_r = Eb1 - E10, up_l = E01 - Eb0, up_r = E11 - Eb1;
+  const double dlo = ma0 > 0 ? lo_l : (ma0 < 0 ? lo_r : 0.5 * (lo_l + lo_r));
+  const double dup = ma1 > 0 ? up_l : (ma1 < 0 ? up_r : 0.5 * (up_l + up_r));
+  const double le_d = Ea0 - E00, le_u = Ea1 - E01, ri_d = E10 - Ea0, ri_u = E11 - Ea1;
+  const double dle = mb0 > 0 ? le_d : (mb0 < 0 ? le_u : 0.5 * (le_d + le_u));
+  const double dri = mb1 > 0 ? ri_d : (mb1 < 0 ? ri_u : 0.5 * (ri_d + ri_u));
+  return 0.25 * (Ea1 + Ea0 + Eb1 + Eb0) + 0.25 * (dlo - dup) + 0.25 * (dle - dri);
+}
+
+__global__ void k_sph_emf(SphDev D) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= D.NE) return;
+  double Ec[4], Ef[4];
+  int ms[4];
+  if (e < D.ER) {   // radial edge (v, k)
+    const int k = (int)(e / D.NV);
+    const long v = e - (long)k * D.NV, fb = (long)k * D.NS, cb = (long)k * D.NC;
+    const V3 l = ld3(D.vd, v);
+    if (D.vcnt[v] == 3) {   // a cube corner: the mean of the three face EMFs
+      double t = 0.0;
+      for (int m = 0; m < 3; ++m) t += efl(D, fb + D.vside[4 * v + m], l);
+      D.EE[e] = t / 3.0;
+      return;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const long f = fb + D.vside[4 * v + m];
+      Ec[m] = ecl(D, cb + D.vcell[4 * v + m], l);
+      Ef[m] = efl(D, f, l);
+      ms[m] = D.vsgn[4 * v + m] * D.UP[f];
+    }
+  } else {          // angular edge (s, k); none on a wall
+    const long q = e - D.ER;
+    const int k = (int)(q / D.NS);
+    const long s = q - (long)k * D.NS;
+    if (k == 0 || k == D.Nr) { D.EE[e] = 0.0; return; }
+    const V3 l = ld3(D.sl, s);
+    const long cL0 = (long)(k - 1) * D.NC + D.sL[s], cR0 = (long)(k - 1) * D.NC + D.sR[s];
+    const long cL1 = (long)k * D.NC + D.sL[s], cR1 = (long)k * D.NC + D.sR[s];
+    const long A0 = (long)(k - 1) * D.NS + s, A1 = (long)k * D.NS + s;
+    const long RL = D.FA + (long)k * D.NC + D.sL[s], RR = D.FA + (long)k * D.NC + D.sR[s];
+    long cc[4], ff[4];
+    if (!D.s_swap[s]) {
+      cc[0] = cL0; cc[1] = cR0; cc[2] = cR1; cc[3] = cL1;
+      ff[0] = A0; ff[1] = RR; ff[2] = A1; ff[3] = RL;
+    } else {
+      cc[0] = cL0; cc[1] = cL1; cc[2] = cR1; cc[3] = cR0;
+      ff[0] = RL; ff[1] = A1; ff[2] = RR; ff[3] = A0;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {   // every face's -n cell is its from-cell here
+      Ec[m] = ecl(D, cc[m], l);
+      Ef[m] = efl(D, ff[m], l);
+      ms[m] = D.UP[ff[m]];
+    }
+  }
+  D.EE[e] = contact_ct(Ec, Ef, ms);
+}
+
+// out = a base + b (in - dt R) on the cells, R = (1/V) sum_f s_f F_f - S
+__global__ void k_sph_update_cells(SphDev D, const double *Uin, const double *Ubase, double *Uout, double a,
+                                   double b, const double *__restrict__ dtp) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (c >= D.ncell) return;
+  const int k = (int)(c / D.NC);
+  const long an = c - (long)k * D.NC, nf = D.NF, nc = D.ncell;
+  CellFaces F;
+  cell_faces(D, an, k, F);
+  double r[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+  for (int m = 0; m < 6; ++m)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) r[v] += F.s[m] * D.FC[v * nf + F.f[m]];
+  const double iv = 1.0 / cell_vol(D, an, k);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) r[v] *= iv;
+  const double g = D.g_c ? D.g_c[k] : 0.0;
+  const V3 gv = ld3(D.cdc, an) * -g;   // radial, inward
+  const double rho = Uin[c], drho = rho - bg_rho(D, k);
+  r[1] -= drho * gv.x; r[2] -= drho * gv.y; r[3] -= drho * gv.z;
+  double se = Uin[nc + c] * gv.x + Uin[2 * nc + c] * gv.y + Uin[3 * nc + c] * gv.z;
+  if (D.heat) se += D.heat[k];
+  r[4] -= se;
+  const double dt = *dtp;
+  double o[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) o[v] = a * Ubase[v * nc + c] + b * (Uin[v * nc + c] - dt * r[v]);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Uout[v * nc + c] = o[v];
+}
+
+// out = a base + b (in - dt sum_e sigma l E) on the faces (Eq. induction)
+__global__ void k_sph_update_faces(SphDev D, const double *pin, const double *pbase, double *pout, double a,
+                                   double b, const double *__restrict__ dtp) {
+  const long f = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (f >= D.NF) return;
+  double t;
+  if (f < D.FA) {   // angular face (s, k): edges (s, k), (v1, k), (s, k+1), (v0, k)
+    const int k = (int)(f / D.NS);
+    const long s = f - (long)k * D.NS;
+    const double dr = D.r[k + 1] - D.r[k], th = D.sth[s];
+    const double si = D.s_in[s];
+    t = si * D.r[k] * th * D.EE[D.ER + (long)k * D.NS + s];
+    t += D.s_v1[s] * dr * D.EE[(long)k * D.NV + D.sv1[s]];
+    t += -si * D.r[k + 1] * th * D.EE[D.ER + (long)(k + 1) * D.NS + s];
+    t += D.s_v0[s] * dr * D.EE[(long)k * D.NV + D.sv0[s]];
+  } else {          // radial face (a, k): the angular edges (s_m, k)
+    const long q = f - D.FA;
+    const int k = (int)(q / D.NC);
+    const long an = q - (long)k * D.NC;
+    t = 0.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int s = D.cs[4 * an + m];
+      t += D.crs[4 * an + m] * D.r[k] * D.sth[s] * D.EE[D.ER + (long)k * D.NS + s];
+    }
+  }
+  const double o = a * pbase[f] + b * (pin[f] - *dtp * t);
+  pout[f] = o;
+}
+
+__global__ void k_sph_dt(SphDev D, unsigned long long *dmax) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (c < D.ncell) {
+    const long n = D.ncell;
+    const int k = (int)(c / D.NC);
+    const long a = c - (long)k * D.NC;
+    const double rho = D.W[SW_RHO * n + c] + bg_rho(D, k);
+    const double P = D.W[SW_P * n + c] + bg_p(D, k);
+    const V3 u = v3(D.W[SW_U * n + c], D.W[(SW_U + 1) * n + c], D.W[(SW_U + 2) * n + c]);
+    const V3 b = v3(D.W[SW_B * n + c], D.W[(SW_B + 1) * n + c], D.W[(SW_B + 2) * n + c]);
+    const double a2 = D.gamma * P / rho, b2 = dot3(b, b) / rho;
+    CellFaces F;
+    cell_faces(D, a, k, F);
+    double sum = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {   // the cell's three mesh directions
+      const V3 span = F.x[2 * d + 1] - F.x[2 * d];
+      const double width = len3(span);
+      const V3 ed = span * (1.0 / width);
+      const double bd = dot3(b, ed);
+      double disc = (a2 + b2) * (a2 + b2) - 4.0 * a2 * bd * bd / rho;
+      if (disc < 0.0) disc = 0.0;
+      sum += (fabs(dot3(u, ed)) + sqrt(0.5 * (a2 + b2 + sqrt(disc)))) / width;
+    }
+    m = (sum == sum) ? sum : INFINITY;
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double red[SPT / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < SPT / 32; ++w) v = fmax(v, red[w]);
+    atomicMax(dmax, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+__global__ void k_sph_dt_fin(double cfl, unsigned long long *dmax, double *dt) {
+  const double m = __longlong_as_double((long long)*dmax);
+  *dt = m > 0.0 ? cfl / m : 0.0;
+  *dmax = 0ull;
+}
+
+__global__ void k_sph_set(double v, double *p) { *p = v; }
+
+// ABI <-> internal.  Cells: [v][p][k][j][i] <-> [v][k][a].  Faces: alpha
+// [p][k][j][i] (N + 1 per row), beta [p][k][j][i] (N + 1 rows), radial
+// [p][k][j][i] (Nr + 1 radii).
+struct AbiMap {
+  const int *s;
+  const signed char *sg, *own;
+};
+
+__device__ __forceinline__ long abi_face(const SphDev &D, const AbiMap &M, long t, int &sign, bool &own) {
+  const long N = D.N, N1 = N + 1, Nr = D.Nr;
+  const long na = 6 * Nr * N * N1;
+  if (t < 2 * na) {   // alpha or beta copy: (p, k, rest) -> side entry (kind, p, rest)
+    const long kind = t >= na ? 1 : 0;
+    const long u = t - kind * na;
+    const long per = N * N1;
+    const long pk = u / per, rem = u - pk * per;
+    const long p = pk / Nr, k = pk - p * Nr;
+    const long q = kind * 6 * per + p * per + rem;
+    sign = M.sg[q];
+    own = M.own[q] != 0;
+    return k * D.NS + M.s[q];
+  }
+  const long u = t - 2 * na, per = N * N;
+  const long pk = u / per, rem = u - pk * per;
+  const long p = pk / (Nr + 1), k = pk - p * (Nr + 1);
+  sign = 1;
+  own = true;
+  return D.FA + k * D.NC + p * per + rem;
+}
+
+__global__ void k_sph_gather_faces(SphDev D, AbiMap M, long n, const double *__restrict__ abi,
+                                   double *__restrict__ phi) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int sg;
+  bool own;
+  const long f = abi_face(D, M, t, sg, own);
+  if (own) phi[f] = abi[t];
+}
+__global__ void k_sph_scatter_faces(SphDev D, AbiMap M, long n, const double *__restrict__ phi,
+                                    double *__restrict__ abi) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int sg;
+  bool own;
+  const long f = abi_face(D, M, t, sg, own);
+  abi[t] = sg * phi[f];
+}
+// to_int: ABI [5][p][k][j][i] -> internal [5][k][a]; else the reverse
+__global__ void k_sph_cells(SphDev D, const double *__restrict__ in, double *__restrict__ out, int to_int) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= 5 * D.ncell) return;
+  const long v = t / D.ncell, u = t - v * D.ncell;   // u: ABI cell index
+  const long per = (long)D.N * D.N;
+  const long pk = u / per, rem = u - pk * per;
+  const long p = pk / D.Nr, k = pk - p * D.Nr;
+  const long c = k * D.NC + p * per + rem;
+  if (to_int) out[v * D.ncell + c] = in[t];
+  else out[t] = in[v * D.ncell + c];
+}
+
+inline unsigned nblk(long n) { return (unsigned)((n + SPT - 1) / SPT); }
+
+}  // namespace
+
+struct phl_sphere {
+  phl_sphere_desc desc;
+  SphDev D;
+  AbiMap AM;
+  cudaStream_t s = nullptr;
+  std::vector<void *> allocs;
+  double *U = nullptr, *U1 = nullptr, *phi = nullptr, *phi1 = nullptr, *dt = nullptr, *abi_buf = nullptr;
+  unsigned long long *dmax = nullptr;
+  long nabi = 0;
+  long steps = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t up_vec(phl_sphere *S, const T **dst, const std::vector<T> &v) {
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(1, v.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  S->allocs.push_back(p);
+  if (!v.empty()) e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  *dst = (const T *)p;
+  return e;
+}
+template <typename T>
+cudaError_t alloc_n(phl_sphere *S, T **dst, long n) {
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<long>(1, n) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  S->allocs.push_back(p);
+  e = cudaMemset(p, 0, std::max<long>(1, n) * sizeof(T));
+  *dst = (T *)p;
+  return e;
+}
+cudaError_t up_arr(phl_sphere *S, const double **dst, const double *src, long n) {
+  if (!src) { *dst = nullptr; return cudaSuccess; }
+  return up_vec(S, dst, std::vector<double>(src, src + n));
+}
+
+phl_status sph_flags(phl_sphere *S) {
+  int f = 0;
+  cudaError_t e = cudaMemcpyAsync(&f, S->D.dflag, sizeof(int), cudaMemcpyDeviceToHost, S->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S->s);
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "sphere: %s", cudaGetErrorString(e));
+  if (f & FLAG_NAN) return (phl_status)set_error(PHL_ENAN, "sphere: non-finite value in the state");
+  if (f & FLAG_NEG) return (phl_status)set_error(PHL_ENEGATIVE, "sphere: non-positive density or pressure");
+  return PHL_OK;
+}
+
+void sph_dt(phl_sphere *S, const double *U, const double *phi) {
+  k_sph_prims<<<nblk(S->D.ncell), SPT, 0, S->s>>>(S->D, U, phi);
+  k_sph_dt<<<nblk(S->D.ncell), SPT, 0, S->s>>>(S->D, S->dmax);
+  k_sph_dt_fin<<<1, 1, 0, S->s>>>(S->D.cfl, S->dmax, S->dt);
+}
+
+}  // namespace
+
+extern "C" {
+
+phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
+  if (!d || !out) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: null argument");
+  *out = nullptr;
+  if (d->N < 2 || d->Nr < 2 || !(d->r_in > 0.0) || !(d->r_out > d->r_in) || !(d->gamma > 1.0) || !(d->cfl > 0.0) ||
+      !(d->mach_thr > 0.0))
+    return (phl_status)set_error(PHL_EINVAL,
+                                 "phl_sphere_create: need N, Nr >= 2, 0 < r_in < r_out, gamma > 1, cfl > 0, mach_thr > 0");
+  if (d->riemann < PHL_LHLLD || d->riemann > PHL_HLL)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: bad solver");
+  const bool any = d->rho_c || d->p_c || d->rho_f || d->p_f, all = d->rho_c && d->p_c && d->rho_f && d->p_f;
+  if (any && !all) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: the background needs all four profiles");
+  // face and edge indices must fit int32 per shell and long overall
+  const double nf = 12.0 * d->N * d->N * d->Nr + 6.0 * d->N * d->N * (d->Nr + 1.0);
+  const double ne = (6.0 * d->N * d->N + 2.0) * d->Nr + 12.0 * d->N * d->N * (d->Nr + 1.0);
+  if (nf > 2147483647.0 || ne > 2147483647.0 || d->N > 8192)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: more than 2^31 faces or edges");
+  phl_sphere *S = new phl_sphere();
+  S->desc = *d;
+  S->s = (cudaStream_t)d->stream;
+  Ang M;
+  try {
+    build_ang(d->N, M);
+  } catch (const std::exception &ex) {
+    delete S;
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: %s", ex.what());
+  }
+  SphDev &D = S->D;
+  D.N = d->N; D.Nr = d->Nr;
+  D.NC = M.NC; D.NS = M.NS; D.NV = M.NV;
+  D.ncell = M.NC * d->Nr;
+  D.FA = M.NS * d->Nr;
+  D.NF = D.FA + M.NC * (d->Nr + 1);
+  D.ER = M.NV * d->Nr;
+  D.NE = D.ER + M.NS * (d->Nr + 1);
+  D.gamma = d->gamma; D.cfl = d->cfl; D.mach = d->mach_thr; D.riemann = d->riemann;
+  std::vector<double> r(d->Nr + 1);
+  for (int k = 0; k <= d->Nr; ++k) r[k] = d->r_in + (d->r_out - d->r_in) * k / d->Nr;
+  cudaError_t e = up_vec(S, &D.r, r);
+  auto U = [&](auto **dst, const auto &v) { if (e == cudaSuccess) e = up_vec(S, dst, v); };
+  U(&D.vd, M.vd); U(&D.sn, M.sn); U(&D.sl, M.sl); U(&D.smid, M.smid); U(&D.sth, M.sth);
+  U(&D.cdc, M.cdc); U(&D.cna, M.cna); U(&D.cva, M.cva); U(&D.com, M.com);
+  U(&D.sL, M.sL); U(&D.sR, M.sR); U(&D.sLL, M.sLL); U(&D.sRR, M.sRR); U(&D.sv0, M.sv0); U(&D.sv1, M.sv1);
+  U(&D.cs, M.cs); U(&D.vcell, M.vcell); U(&D.vside, M.vside);
+  U(&D.s_in, M.s_in); U(&D.s_v0, M.s_v0); U(&D.s_v1, M.s_v1); U(&D.s_swap, M.s_swap);
+  U(&D.csg, M.csg); U(&D.crs, M.crs); U(&D.vsgn, M.vsgn); U(&D.vcnt, M.vcnt);
+  U(&S->AM.s, M.abi_s); U(&S->AM.sg, M.abi_sg); U(&S->AM.own, M.abi_own);
+  if (e == cudaSuccess) e = up_arr(S, &D.rho_c, d->rho_c, d->Nr);
+  if (e == cudaSuccess) e = up_arr(S, &D.p_c, d->p_c, d->Nr);
+  if (e == cudaSuccess) e = up_arr(S, &D.rho_f, d->rho_f, d->Nr + 1);
+  if (e == cudaSuccess) e = up_arr(S, &D.p_f, d->p_f, d->Nr + 1);
+  if (e == cudaSuccess) e = up_arr(S, &D.g_c, d->g_c, d->Nr);
+  if (e == cudaSuccess) e = up_arr(S, &D.heat, d->heat, d->Nr);
+  if (e == cudaSuccess) e = alloc_n(S, &D.W, SW_N * D.ncell);
+  if (e == cudaSuccess) e = alloc_n(S, &D.FC, 5 * D.NF);
+  if (e == cudaSuccess) e = alloc_n(S, &D.EF, 3 * D.NF);
+  if (e == cudaSuccess) e = alloc_n(S, &D.UP, D.NF);
+  if (e == cudaSuccess) e = alloc_n(S, &D.EE, D.NE);
+  if (e == cudaSuccess) e = alloc_n(S, &D.dflag, 1);
+  if (e == cudaSuccess) e = alloc_n(S, &S->U, 5 * D.ncell);
+  if (e == cudaSuccess) e = alloc_n(S, &S->U1, 5 * D.ncell);
+  if (e == cudaSuccess) e = alloc_n(S, &S->phi, D.NF);
+  if (e == cudaSuccess) e = alloc_n(S, &S->phi1, D.NF);
+  if (e == cudaSuccess) e = alloc_n(S, &S->dt, 1);
+  if (e == cudaSuccess) e = alloc_n(S, &S->dmax, 1);
+  S->nabi = 2L * 6 * d->Nr * d->N * (d->N + 1) + 6L * (d->Nr + 1) * d->N * d->N;
+  if (e == cudaSuccess) e = alloc_n(S, &S->abi_buf, std::max<long>(S->nabi, 5 * D.ncell));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    phl_sphere_destroy(S);
+    return (phl_status)set_error(PHL_ENOMEM, "phl_sphere_create: %s", cudaGetErrorString(e));
+  }
+  *out = S;
+  return PHL_OK;
+}
+
+void phl_sphere_destroy(phl_sphere *S) {
+  if (!S) return;
+  for (void *p : S->allocs) cudaFree(p);
+  delete S;
+}
+
+phl_status phl_sphere_counts(const phl_sphere *S, long *cells, long *faces, long *edges) {
+  if (!S) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_counts: null sphere");
+  if (cells) *cells = S->D.ncell;
+  if (faces) *faces = S->D.NF;
+  if (edges) *edges = S->D.NE;
+  return PHL_OK;
+}
+
+phl_status phl_sphere_set_state(phl_sphere *S, const double *cons, const double *pa, const double *pb,
+                                const double *pr, int where) {
+  if (!S || !cons || !pa || !pb || !pr) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_state: null argument");
+  if (where != PHL_HOST && where != PHL_DEVICE)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_state: bad where");
+  const cudaMemcpyKind kd = where == PHL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const long N = S->D.N, Nr = S->D.Nr, na = 6 * Nr * N * (N + 1), nr = 6 * (Nr + 1) * N * N;
+  const long nc5 = 5 * S->D.ncell;
+  cudaError_t e = cudaMemcpyAsync(S->abi_buf, cons, nc5 * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) {
+    k_sph_cells<<<nblk(nc5), SPT, 0, S->s>>>(S->D, S->abi_buf, S->U, 1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->abi_buf, pa, na * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->abi_buf + na, pb, na * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->abi_buf + 2 * na, pr, nr * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) {
+    k_sph_gather_faces<<<nblk(S->nabi), SPT, 0, S->s>>>(S->D, S->AM, S->nabi, S->abi_buf, S->phi);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(S->D.dflag, 0, sizeof(int), S->s);
+  if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_set_state: %s", cudaGetErrorString(e));
+  return PHL_OK;
+}
+
+phl_status phl_sphere_get_state(phl_sphere *S, double *cons, double *pa, double *pb, double *pr, int where) {
+  if (!S || !cons || !pa || !pb || !pr) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_get_state: null argument");
+  if (where != PHL_HOST && where != PHL_DEVICE)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_get_state: bad where");
+  const cudaMemcpyKind kd = where == PHL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const long N = S->D.N, Nr = S->D.Nr, na = 6 * Nr * N * (N + 1), nr = 6 * (Nr + 1) * N * N;
+  const long nc5 = 5 * S->D.ncell;
+  k_sph_cells<<<nblk(nc5), SPT, 0, S->s>>>(S->D, S->U, S->abi_buf, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cons, S->abi_buf, nc5 * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) {
+    k_sph_scatter_faces<<<nblk(S->nabi), SPT, 0, S->s>>>(S->D, S->AM, S->nabi, S->phi, S->abi_buf);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pa, S->abi_buf, na * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pb, S->abi_buf + na, na * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pr, S->abi_buf + 2 * na, nr * sizeof(double), kd, S->s);
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_get_state: %s", cudaGetErrorString(e));
+  return sph_flags(S);
+}
+
+phl_status phl_sphere_compute_dt(phl_sphere *S, double *dt_out) {
+  if (!S || !dt_out) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_compute_dt: null argument");
+  sph_dt(S, S->U, S->phi);
+  cudaError_t e = cudaMemcpyAsync(dt_out, S->dt, sizeof(double), cudaMemcpyDeviceToHost, S->s);
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_compute_dt: %s", cudaGetErrorString(e));
+  return sph_flags(S);
+}
+
+phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
+  if (!S || nsteps < 0 || !(dt == dt)) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_step: bad arguments");
+  static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
+  const SphDev &D = S->D;
+  for (int n = 0; n < nsteps; ++n) {
+    if (dt > 0.0) k_sph_set<<<1, 1, 0, S->s>>>(dt, S->dt);
+    else sph_dt(S, S->U, S->phi);   // the CFL step of U^n (Eq. cfl); leaves W of U^n
+    // Shu-Osher SSP-RK3 (Sect. 2.9); stage input U1 (U^n at the first stage)
+    for (int st = 0; st < 3; ++st) {
+      const double *Uin = st == 0 ? S->U : S->U1, *pin = st == 0 ? S->phi : S->phi1;
+      double *Uout = st == 2 ? S->U : S->U1, *pout = st == 2 ? S->phi : S->phi1;
+      if (st > 0 || dt > 0.0) k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, Uin, pin);
+      k_sph_flux<<<nblk(D.NF), SPT, 0, S->s>>>(D, pin);
+      k_sph_emf<<<nblk(D.NE), SPT, 0, S->s>>>(D);
+      // each thread reads its own element of in and base before writing out
+      k_sph_update_faces<<<nblk(D.NF), SPT, 0, S->s>>>(D, pin, S->phi, pout, A3[st], B3[st], S->dt);
+      k_sph_update_cells<<<nblk(D.ncell), SPT, 0, S->s>>>(D, Uin, S->U, Uout, A3[st], B3[st], S->dt);
+    }
+    ++S->steps;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_step: %s", cudaGetErrorString(e));
+  return PHL_OK;
+}
+
+phl_status phl_sphere_check(phl_sphere *S) {
+  if (!S) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_check: null sphere");
+  return sph_flags(S);
+}
+
+}  // extern "C"

@@ -180,3 +180,48 @@ def test_status_names_cover_the_header(P):
     hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "phl.h")).read()
     codes = {int(v): k for k, v in re.findall(r"\b(PHL_E[A-Z]+|PHL_OK)\s*=\s*(\d+)", hdr)}
     assert codes == P.STATUS
+
+
+def _sphere_desc(P, bg):
+    d = P.SphereDesc()
+    d.N, d.Nr, d.r_in, d.r_out, d.gamma, d.cfl, d.riemann, d.mach_thr = 4, 3, 0.2, 1.0, 5.0 / 3.0, 0.4, 0, 0.6
+    for k in ("rho_c", "p_c", "rho_f", "p_f"):
+        setattr(d, k, bg[k].ctypes.data)
+    return d
+
+
+SPHERE_CASES = [
+    ("one angular cell", set_field("N", 1), "N, Nr >= 2"),
+    ("one shell", set_field("Nr", 1), "N, Nr >= 2"),
+    ("inner radius zero", set_field("r_in", 0.0), "0 < r_in < r_out"),
+    ("inverted radii", set_field("r_out", 0.1), "0 < r_in < r_out"),
+    ("gamma = 1", set_field("gamma", 1.0), "gamma > 1"),
+    ("zero cfl", set_field("cfl", 0.0), "cfl > 0"),
+    ("zero Mach threshold", set_field("mach_thr", 0.0), "mach_thr > 0"),
+    ("unknown solver", set_field("riemann", 5), "bad solver"),
+    ("partial background", set_field("p_f", None), "all four profiles"),
+    ("too many faces", lambda d: (setattr(d, "N", 8000), setattr(d, "Nr", 8000)), "2^31"),
+]
+
+
+@pytest.mark.parametrize("name,breaker,needle", SPHERE_CASES, ids=[c[0] for c in SPHERE_CASES])
+def test_sphere_create_rejects(P, name, breaker, needle):
+    bg = {k: np.ones(3 if k.endswith("_c") else 4) for k in ("rho_c", "p_c", "rho_f", "p_f")}
+    d = _sphere_desc(P, bg)
+    breaker(d)
+    h = C.c_void_p()
+    st, msg = status_and_message(P, P.lib().phl_sphere_create(C.byref(d), C.byref(h)))
+    assert not h.value
+    assert st == EINVAL and needle in msg, (st, msg)
+
+
+def test_sphere_null_handles(P):
+    L = P.lib()
+    assert L.phl_sphere_create(None, None) == EINVAL
+    assert L.phl_sphere_step(None, 0.0, 1) == EINVAL
+    assert L.phl_sphere_check(None) == EINVAL
+    assert L.phl_sphere_counts(None, None, None, None) == EINVAL
+    assert L.phl_sphere_set_state(None, None, None, None, None, 0) == EINVAL
+    assert L.phl_sphere_get_state(None, None, None, None, None, 0) == EINVAL
+    assert L.phl_sphere_compute_dt(None, None) == EINVAL
+    L.phl_sphere_destroy(None)

@@ -1,0 +1,213 @@
+"""The cubed-sphere shell on the GPU (phl_sphere_*, FP64) against the CPU
+oracle (oracle/sphere.c), element by element, and at the full
+6 x 256 x 256 x 384 shell through properties that hold at any size.
+
+Bar: relative L-infinity error per field <= 1e-11,
+    max |gpu - oracle| / max |oracle|
+for rho, momentum (as one vector field), E and each face-flux array, after
+the stated number of steps; both sides take their own CFL steps from their
+own state unless a fixed dt is given.  Inputs come from workloads/ only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2604_12672_gb300 as P
+    return P
+
+
+def rel_linf(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def errors(st, ref):
+    e = dict(rho=rel_linf(st["cons"][0], ref["cons"][0]), m=rel_linf(st["cons"][1:4], ref["cons"][1:4]),
+             E=rel_linf(st["cons"][4], ref["cons"][4]))
+    for k in ("pa", "pb", "pr"):
+        e[k] = rel_linf(st[k], ref[k])
+    return e
+
+
+def state0(pr):
+    return dict(cons=pr.cons, pa=pr.pa, pb=pr.pb, pr=pr.pr)
+
+
+def gpu_run(P, pr, nsteps, dt=0.0, wb=True, state=None):
+    s = P.Sphere.from_problem(pr, wb=wb)
+    st = state or state0(pr)
+    s.set_state(*(np.ascontiguousarray(st[k]) for k in ("cons", "pa", "pb", "pr")))
+    s.step(nsteps, dt=dt)
+    out = s.get_state()
+    s.close()
+    return out
+
+
+def oracle_run(pr, nsteps, dt=0.0, wb=True):
+    o = O.Sphere(pr, riemann=pr.riemann, cfl=pr.cfl, mach_thr=pr.mach_thr, wb=wb)
+    st, _ = o.run(nsteps, dt_fixed=dt)
+    return st, o
+
+
+CASES = [
+    # name, shell_problem kwargs, steps, solver, wb
+    ("polytrope_field_heat", dict(N=6, Nr=5, amp=2e-2, beta=1e2, vel_amp=0.05, heat_frac=0.3, mach_heat=0.05), 8,
+     "lhlld", True),
+    ("no_background", dict(N=6, Nr=5, amp=2e-2, beta=1e2, vel_amp=0.05, heat_frac=0.3, mach_heat=0.05), 8,
+     "lhlld", False),
+    ("hlld", dict(N=5, Nr=4, amp=2e-2, beta=30.0, vel_amp=0.1, heat_frac=0.0), 6, "hlld", True),
+    ("hll", dict(N=5, Nr=4, amp=2e-2, beta=30.0, vel_amp=0.1, heat_frac=0.0), 6, "hll", True),
+    ("smallest_shell", dict(N=2, Nr=2, amp=5e-2, beta=1e2, vel_amp=0.05, heat_frac=0.5), 6, "lhlld", True),
+    ("odd_ragged", dict(N=7, Nr=3, amp=1e-2, beta=1e3, vel_amp=0.02, heat_frac=0.3), 5, "lhlld", True),
+    ("uniform_medium", dict(N=6, Nr=4, uniform=True, amp=5e-2, beta=1e3, vel_amp=0.05, heat_frac=0.0), 8,
+     "lhlld", True),
+]
+
+
+@pytest.mark.parametrize("name,kw,nsteps,solver,wb", CASES, ids=[c[0] for c in CASES])
+def test_sphere_matches_oracle(P, name, kw, nsteps, solver, wb):
+    kw = dict(kw)
+    N, Nr = kw.pop("N"), kw.pop("Nr")
+    pr = W.shell_problem(N, Nr, **kw)
+    pr.riemann = solver
+    ref, o = oracle_run(pr, nsteps, wb=wb)
+    st = gpu_run(P, pr, nsteps, wb=wb)
+    err = errors(st, ref)
+    print(name, {k: f"{v:.2e}" for k, v in err.items()})
+    assert all(v <= TOL for v in err.values()), err
+    # the state moved: the comparison is not of two copies of the input
+    assert np.abs(ref["cons"][1:4] - pr.cons[1:4]).max() > 0
+    # every copy of a seam face carries the face's flux in its own orientation
+    assert np.abs(o.divb(st)).max() <= 1e-13 * max(np.abs(st["pa"]).max(), np.abs(st["pr"]).max(), 1e-300)
+
+
+def test_sphere_fixed_dt_and_counts(P):
+    pr = W.shell_problem(5, 3, amp=1e-2, beta=1e2, vel_amp=0.05, heat_frac=0.3)
+    ref, o = oracle_run(pr, 4, dt=2e-3)
+    s = P.Sphere.from_problem(pr)
+    c, oc = s.counts(), o.counts()
+    assert (c["cells"], c["faces"], c["edges"]) == (oc["cells"], oc["faces"], oc["edges"])
+    s.set_state(pr.cons, pr.pa, pr.pb, pr.pr)
+    dt_gpu = s.compute_dt()
+    dt_ora = o.dt()
+    assert abs(dt_gpu - dt_ora) <= 1e-13 * dt_ora
+    s.step(4, dt=2e-3)
+    st = s.get_state()
+    err = errors(st, ref)
+    assert all(v <= TOL for v in err.values()), err
+
+
+def test_sphere_device_state_roundtrip(P):
+    import torch
+    pr = W.shell_problem(4, 3, amp=1e-2, beta=1e2, vel_amp=0.05)
+    host = gpu_run(P, pr, 3)
+    s = P.Sphere.from_problem(pr)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in state0(pr).items()}
+    s.set_state(dev["cons"], dev["pa"], dev["pb"], dev["pr"])
+    s.step(3)
+    out = {k: torch.empty_like(v) for k, v in dev.items()}
+    s.get_state(out)
+    torch.cuda.synchronize()
+    for k in out:
+        assert np.array_equal(out[k].cpu().numpy(), host[k]), k
+
+
+def test_sphere_flags_negative_density(P):
+    pr = W.shell_problem(3, 2, amp=0.0, beta=0.0)
+    cons = pr.cons.copy()
+    cons[0, 2, 1, 1, 1] = -1.0
+    s = P.Sphere.from_problem(pr)
+    s.set_state(cons, pr.pa, pr.pb, pr.pr)
+    with pytest.raises(P.PhlError) as ei:
+        s.compute_dt()
+    assert ei.value.status == 4   # PHL_ENEGATIVE
+    s.set_state(cons, pr.pa, pr.pb, pr.pr)
+    s.step(1, dt=1e-6)
+    with pytest.raises(P.PhlError) as ei:
+        s.check()
+    assert ei.value.status in (4, 5)   # the bad cell also poisons its faces' fluxes
+    # set_state clears the flags
+    s.set_state(pr.cons, pr.pa, pr.pb, pr.pr)
+    s.step(1, dt=1e-6)
+    s.check()
+
+
+# ---------------------------------------------------------------------------
+# the full 6 x 256 x 256 x 384 shell
+
+FULL = dict(N=256, Nr=384)
+
+
+def torch_divb(st):
+    """Discrete divergence of every cell from the ABI face fluxes (sum of the
+    outward fluxes: + on the upper face of each direction, - on the lower)."""
+    pa, pb, prr = st["pa"], st["pb"], st["pr"]
+    return (pa[..., 1:] - pa[..., :-1]) + (pb[..., 1:, :] - pb[..., :-1, :]) + (prr[:, 1:] - prr[:, :-1])
+
+
+def shell_volumes(N, Nr, r):
+    """Cell volumes (6, Nr, N, N): (r1^3 - r0^3) / 3 times the solid angle of
+    the spherical quad (two triangles, Van Oosterom & Strackee)."""
+    d = W.shell_dirs(N)
+    a, b, c, e = d[:, :-1, :-1], d[:, :-1, 1:], d[:, 1:, 1:], d[:, 1:, :-1]
+
+    def tri(x, y, z):
+        num = np.abs(np.einsum("...i,...i->...", x, np.cross(y, z)))
+        den = 1.0 + np.einsum("...i,...i->...", x, y) + np.einsum("...i,...i->...", y, z) + \
+            np.einsum("...i,...i->...", z, x)
+        return 2.0 * np.arctan2(num, den)
+    om = tri(a, b, c) + tri(a, c, e)
+    shell = (r[1:] ** 3 - r[:-1] ** 3) / 3.0
+    return shell[None, :, None, None] * om[:, None]
+
+
+def _full_run(P, nsteps, **kw):
+    import torch
+    pr = W.shell_problem(FULL["N"], FULL["Nr"], device="cuda", **kw)
+    s = P.Sphere.from_problem(pr)
+    s.set_state(pr.cons, pr.pa, pr.pb, pr.pr)
+    s.step(nsteps)
+    out = {k: torch.empty_like(getattr(pr, k)) for k in ("cons", "pa", "pb", "pr")}
+    s.get_state(out)
+    torch.cuda.synchronize()
+    s.close()
+    return pr, out
+
+
+def test_full_shell_well_balanced_rest(P):
+    import torch
+    pr, st = _full_run(P, 3, amp=0.0, beta=0.0, heat_frac=0.0)
+    cs = math.sqrt(pr.gamma * pr.bg["p_c"].max() / pr.bg["rho_c"].min())
+    u = st["cons"][1:4] / st["cons"][0]
+    assert float(u.abs().max()) <= 1e-12 * cs
+    assert float((st["cons"] - pr.cons).abs().max()) <= 1e-12 * float(pr.cons.abs().max())
+    del st, pr
+    torch.cuda.empty_cache()
+
+
+def test_full_shell_divb_and_conservation(P):
+    import torch
+    pr, st = _full_run(P, 3, uniform=True, amp=2e-2, beta=1e3, vel_amp=0.05, heat_frac=0.0)
+    scale = max(float(pr.pa.abs().max()), float(pr.pr.abs().max()))
+    assert float(torch_divb(st).abs().max()) <= 1e-13 * scale
+    assert float(torch_divb(dict(pa=pr.pa, pb=pr.pb, pr=pr.pr)).abs().max()) <= 1e-13 * scale
+    vol = torch.from_numpy(shell_volumes(pr.N, pr.Nr, pr.meta["r"])).cuda()
+    for v in (0, 4):   # mass and total energy between reflecting walls
+        q0, q1 = float((vol * pr.cons[v]).sum()), float((vol * st["cons"][v]).sum())
+        assert abs(q1 - q0) <= 1e-13 * abs(q0), (v, q0, q1)
+    assert float((st["cons"][1:4] - pr.cons[1:4]).abs().max()) > 0
+    del st, pr
+    torch.cuda.empty_cache()

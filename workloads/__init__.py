@@ -639,89 +639,81 @@ def shell_background(r_mid, r_faces, r_star=1.2, n_poly=1.5, rho_c=1.0, G=1.0):
     return dict(rho_c=rc, p_c=pc, rho_f=rf, p_f=pf), gc
 
 
-def _edge_integral(A, x0, x1, radial, r, ng=8):
-    """Line integral of the vector potential A(x) from x0 to x1 along a radial
-    segment or a great-circle arc of radius r (Gauss-Legendre, ng points)."""
+def _gl(ng, dev):
+    import torch
     gx, gw = np.polynomial.legendre.leggauss(ng)
-    if radial:
-        t = 0.5 * (gx + 1.0)
-        pts = x0[None, :] + t[:, None] * (x1 - x0)[None, :]
-        dx = (x1 - x0)
-        return 0.5 * float(np.sum(gw * np.einsum("ij,j->i", A(pts), dx)))
-    u, w = x0 / r, x1 / r
-    th = math.atan2(np.linalg.norm(np.cross(u, w)), float(np.dot(u, w)))
-    wp = w - np.dot(w, u) * u
-    wp /= np.linalg.norm(wp)
-    s = 0.5 * th * (gx + 1.0)
-    pts = r * (np.cos(s)[:, None] * u[None, :] + np.sin(s)[:, None] * wp[None, :])
-    tang = r * (-np.sin(s)[:, None] * u[None, :] + np.cos(s)[:, None] * wp[None, :])
-    return 0.5 * th * float(np.sum(gw * np.einsum("ij,ij->i", A(pts), tang)))
+    return torch.tensor(gx, dtype=torch.float64, device=dev), torch.tensor(gw, dtype=torch.float64, device=dev)
 
 
-def shell_fluxes_from_potential(N, Nr, r, A):
+def _arc_integrals(A, u, w, r, gx, gw):
+    """Line integrals of A along the great-circle arcs of radius r from the
+    unit directions u to w (..., 3), Gauss-Legendre on the angle."""
+    import torch
+    c = torch.linalg.cross(u, w, dim=-1)
+    th = torch.atan2(torch.linalg.norm(c, dim=-1), (u * w).sum(-1))
+    wp = w - (w * u).sum(-1, keepdim=True) * u
+    wp = wp / torch.linalg.norm(wp, dim=-1, keepdim=True)
+    s = 0.5 * th[..., None] * (gx + 1.0)                                  # (..., ng)
+    cs, sn = torch.cos(s)[..., None], torch.sin(s)[..., None]
+    pts = r * (cs * u[..., None, :] + sn * wp[..., None, :])
+    tang = r * (-sn * u[..., None, :] + cs * wp[..., None, :])
+    return 0.5 * th * ((A(pts) * tang).sum(-1) * gw).sum(-1)
+
+
+def _radial_integrals(A, d, r0, r1, gx, gw):
+    """Line integrals of A along the radial segments r0 d -> r1 d."""
+    t = 0.5 * (gx + 1.0)
+    x0, dx = r0 * d, (r1 - r0) * d
+    pts = x0[..., None, :] + t[:, None] * dx[..., None, :]
+    return 0.5 * ((A(pts) * dx[..., None, :]).sum(-1) * gw).sum(-1)
+
+
+def shell_fluxes_from_potential(N, Nr, r, A, device="cpu", ng=8):
     """Magnetic fluxes (pa, pb, pr) of B = curl A through every face, each the
-    circulation of A around the face (counter-clockwise about the patch's
-    +alpha, +beta or +r normal).  Each edge's line integral is computed once,
-    from the lexicographically smaller end, and reused with its sign, so the
-    discrete divergence of every cell vanishes up to rounding."""
-    d = shell_dirs(N)
-    cache = {}
-
-    def edge(v0, v1, radial, rr):
-        k0, k1 = tuple(v0), tuple(v1)
-        if k0 <= k1:
-            key, sgn, a, b = (k0, k1), 1.0, v0, v1
-        else:
-            key, sgn, a, b = (k1, k0), -1.0, v1, v0
-        if key not in cache:
-            cache[key] = _edge_integral(A, np.array(a), np.array(b), radial, rr)
-        return sgn * cache[key]
-
-    def P(p, j, i, k):   # vertex position (rounded to stabilise the cache key: exact shared values)
-        return tuple(float(x) for x in r[k] * d[p, j, i])
-
-    def loop(vs, radials, radii):
-        t = 0.0
-        for q in range(4):
-            t += edge(np.array(vs[q]), np.array(vs[(q + 1) % 4]), radials[q], radii[q])
-        return t
-
-    pa = np.zeros((6, Nr, N, N + 1))
-    pb = np.zeros((6, Nr, N + 1, N))
-    prr = np.zeros((6, Nr + 1, N, N))
-    for p in range(6):
-        for k in range(Nr):
-            for j in range(N):
-                for i in range(N + 1):   # alpha face: corners (i,j,k) (i,j+1,k) (i,j+1,k+1) (i,j,k+1), CCW about +alpha
-                    vs = [P(p, j, i, k), P(p, j + 1, i, k), P(p, j + 1, i, k + 1), P(p, j, i, k + 1)]
-                    pa[p, k, j, i] = loop(vs, [False, True, False, True], [r[k], 0, r[k + 1], 0])
-            for j in range(N + 1):
-                for i in range(N):       # beta face: corners (i,j,k) (i,j,k+1) (i+1,j,k+1) (i+1,j,k), CCW about +beta
-                    vs = [P(p, j, i, k), P(p, j, i, k + 1), P(p, j, i + 1, k + 1), P(p, j, i + 1, k)]
-                    pb[p, k, j, i] = loop(vs, [True, False, True, False], [0, r[k + 1], 0, r[k]])
-        for k in range(Nr + 1):
-            for j in range(N):
-                for i in range(N):       # radial face: corners (i,j) (i+1,j) (i+1,j+1) (i,j+1), CCW about +r
-                    vs = [P(p, j, i, k), P(p, j, i + 1, k), P(p, j + 1, i + 1, k), P(p, j + 1, i, k)]
-                    prr[p, k, j, i] = loop(vs, [False] * 4, [r[k]] * 4)
-    return pa, pb, prr
+    circulation of A around the face counter-clockwise about the patch's
+    +alpha, +beta or +r direction, from the line integrals of A along the
+    mesh's edges (Gauss-Legendre, ng points per edge; torch float64 on
+    `device`, one shell at a time).  Each patch integrates its own edges; the
+    two patches of a seam integrate a shared edge from the same end points,
+    so the discrete divergence of every cell vanishes to rounding."""
+    import torch
+    dev = torch.device(device)
+    d = torch.tensor(shell_dirs(N), dtype=torch.float64, device=dev)     # (6, N+1, N+1, 3) [p, j, i]
+    gx, gw = _gl(ng, dev)
+    rr = [float(x) for x in r]
+    # arcs: Ea from (i, j) to (i+1, j), Eb from (i, j) to (i, j+1), per radius
+    Ea = torch.stack([_arc_integrals(A, d[:, :, :-1], d[:, :, 1:], rr[k], gx, gw) for k in range(Nr + 1)], 1)
+    Eb = torch.stack([_arc_integrals(A, d[:, :-1, :], d[:, 1:, :], rr[k], gx, gw) for k in range(Nr + 1)], 1)
+    # radial segments at every vertex, per shell
+    R = torch.stack([_radial_integrals(A, d, rr[k], rr[k + 1], gx, gw) for k in range(Nr)], 1)
+    # Ea (6, Nr+1, N+1, N) [p, k, j, i]; Eb (6, Nr+1, N, N+1); R (6, Nr, N+1, N+1)
+    pa = Eb[:, :-1] + R[:, :, 1:, :] - Eb[:, 1:] - R[:, :, :-1, :]
+    pb = R[:, :, :, :-1] + Ea[:, 1:] - R[:, :, :, 1:] - Ea[:, :-1]
+    prr = Ea[:, :, :-1, :] + Eb[:, :, :, 1:] - Ea[:, :, 1:, :] - Eb[:, :, :, :-1]
+    return pa.contiguous(), pb.contiguous(), prr.contiguous()
 
 
 def shell_problem(N, Nr, r_in=0.2, r_out=1.0, seed=1234, amp=1e-3, beta=1e5, heat_frac=0.3, mach_heat=1e-3,
                   gamma=5.0 / 3.0, vel_amp=0.0, background=True, gravity=True, cfl=0.4, name=None,
-                  uniform=False):
+                  uniform=False, device="cpu"):
     """The cubed-sphere shell of the spherical configuration: a Lane-Emden
     n = 1.5 polytrope (surface at 1.2, so the whole shell r in [0.2, 1] is
     inside the star) in hydrostatic balance under its own radial gravity,
-    isobaric density noise amp U(-1, 1) (seeded), a seed field from the
-    toroidal vector potential A = f(r) (z x r) / r with f vanishing at both
-    walls (poloidal, dipole-like, no flux through the walls), plasma beta
-    2 P_hat(r_mid) / B^2 at the shell's middle radius, heating in the inner
-    heat_frac of the radial span sized so (q dr / rho)^(1/3) ~ mach_heat c_s.
-    vel_amp > 0 adds a swirl u = vel_amp c_s (z x r) / r.  uniform: density and
-    pressure of the shell's middle everywhere, no gravity and no background
-    (a medium in which the total energy is conserved)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
+    isobaric density noise amp U(-1, 1) (seeded torch generator on `device`),
+    a seed field from the toroidal vector potential A = f(r) (z x r) / r with
+    f vanishing at both walls (poloidal, dipole-like, no flux through the
+    walls), plasma beta 2 P_hat(r_mid) / B^2 at the shell's middle radius,
+    heating in the inner heat_frac of the radial span sized so
+    (q dr / rho)^(1/3) ~ mach_heat c_s.  vel_amp > 0 adds a swirl
+    u = vel_amp c_s (z x r) / r.  uniform: density and pressure of the shell's
+    middle everywhere, no gravity and no background (a medium in which the
+    total energy is conserved).  device "cpu": numpy arrays; otherwise the
+    state arrays are torch tensors on that device (profiles stay numpy)."""
+    import torch
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed))
+    f64 = dict(dtype=torch.float64, device=dev)
     r = r_in + (r_out - r_in) * np.arange(Nr + 1) / Nr
     rm = 0.5 * (r[:-1] + r[1:])
     bg, g_c = shell_background(rm, r)
@@ -732,69 +724,61 @@ def shell_problem(N, Nr, r_in=0.2, r_out=1.0, seed=1234, amp=1e-3, beta=1e5, hea
         gravity, background = False, False
     if not gravity:
         g_c = np.zeros(Nr)
-    d = shell_dirs(N)
-    # cell centre directions [p, j, i]
-    dc = d[:, :-1, :-1] + d[:, 1:, :-1] + d[:, :-1, 1:] + d[:, 1:, 1:]
-    dc /= np.linalg.norm(dc, axis=-1, keepdims=True)
-    xc = rm[None, :, None, None, None] * dc[:, None, :, :, :]          # (6, Nr, N, N, 3)
-    rho_hat = bg["rho_c"][None, :, None, None] * np.ones((6, Nr, N, N))
-    p_hat = bg["p_c"][None, :, None, None] * np.ones((6, Nr, N, N))
-    rho = rho_hat * (1.0 + amp * rng.uniform(-1.0, 1.0, rho_hat.shape))
-    p = p_hat.copy()
-    cs_mid = math.sqrt(gamma * float(np.interp(0.5 * (r_in + r_out), rm, bg["p_c"]))
-                       / float(np.interp(0.5 * (r_in + r_out), rm, bg["rho_c"])))
-    vel = np.zeros(xc.shape)
+    d = torch.tensor(shell_dirs(N), **f64)
+    dc = d[:, :-1, :-1] + d[:, 1:, :-1] + d[:, :-1, 1:] + d[:, 1:, 1:]    # cell centre directions [p, j, i]
+    dc = dc / torch.linalg.norm(dc, dim=-1, keepdim=True)
+    xc = torch.tensor(rm, **f64)[None, :, None, None, None] * dc[:, None]  # (6, Nr, N, N, 3)
+    rho_hat = torch.tensor(bg["rho_c"], **f64)[None, :, None, None].expand(6, Nr, N, N)
+    p = torch.tensor(bg["p_c"], **f64)[None, :, None, None].expand(6, Nr, N, N).contiguous()
+    rho = rho_hat * (1.0 + amp * (2.0 * torch.rand((6, Nr, N, N), generator=gen, **f64) - 1.0))
+    rmid = 0.5 * (r_in + r_out)
+    p_mid = float(np.interp(rmid, rm, bg["p_c"]))
+    cs_mid = math.sqrt(gamma * p_mid / float(np.interp(rmid, rm, bg["rho_c"])))
+    vel = torch.zeros(xc.shape, **f64)
     if vel_amp > 0.0:
-        zr = np.stack([-xc[..., 1], xc[..., 0], np.zeros(xc.shape[:-1])], axis=-1)
-        vel = vel_amp * cs_mid * zr / np.linalg.norm(xc, axis=-1, keepdims=True)
-    p_mid = float(np.interp(0.5 * (r_in + r_out), rm, bg["p_c"]))
+        zr = torch.stack([-xc[..., 1], xc[..., 0], torch.zeros(xc.shape[:-1], **f64)], -1)
+        vel = vel_amp * cs_mid * zr / torch.linalg.norm(xc, dim=-1, keepdim=True)
     span = r_out - r_in
+    bc = torch.zeros(xc.shape, **f64)
     if beta and beta > 0:
         b0 = math.sqrt(2.0 * p_mid / beta)
 
-        def fr(rr):
-            return (rr - r_in) ** 2 * (r_out - rr) ** 2 / (0.25 * span) ** 4
-
         def A(x):
-            rr = np.linalg.norm(x, axis=-1)
-            zx = np.stack([-x[..., 1], x[..., 0], np.zeros(x.shape[:-1])], axis=-1)
-            return (b0 * 0.25 * span * fr(rr) / rr)[..., None] * zx
-        pa, pb, prr = shell_fluxes_from_potential(N, Nr, r, A)
+            rr = torch.linalg.norm(x, dim=-1)
+            fr = (rr - r_in) ** 2 * (r_out - rr) ** 2 / (0.25 * span) ** 4
+            zx = torch.stack([-x[..., 1], x[..., 0], torch.zeros(x.shape[:-1], dtype=x.dtype, device=x.device)], -1)
+            return (b0 * 0.25 * span * fr / rr)[..., None] * zx
+        pa, pb, prr = shell_fluxes_from_potential(N, Nr, r, A, device=dev)
+        # the energy takes the potential field's curl at the cell centres
+        # (central differences); the method's own cell field differs at the
+        # truncation level, a negligible share of E at beta >> 1
+        eps = 1e-6 * span
+        for a_ in range(3):
+            e = torch.zeros(3, **f64)
+            e[a_] = eps
+            dA = (A(xc + e) - A(xc - e)) / (2 * eps)       # dA / dx_a
+            if a_ == 0:
+                bc[..., 1] -= dA[..., 2]; bc[..., 2] += dA[..., 1]
+            elif a_ == 1:
+                bc[..., 2] -= dA[..., 0]; bc[..., 0] += dA[..., 2]
+            else:
+                bc[..., 0] -= dA[..., 1]; bc[..., 1] += dA[..., 0]
     else:
-        pa, pb, prr = np.zeros((6, Nr, N, N + 1)), np.zeros((6, Nr, N + 1, N)), np.zeros((6, Nr + 1, N, N))
+        pa = torch.zeros((6, Nr, N, N + 1), **f64)
+        pb = torch.zeros((6, Nr, N + 1, N), **f64)
+        prr = torch.zeros((6, Nr + 1, N, N), **f64)
     heat = None
     if heat_frac and heat_frac > 0:
         rho_b = float(bg["rho_c"][0])
         q = rho_b * (mach_heat * cs_mid) ** 3 / (heat_frac * span)
         heat = np.where(rm < r_in + heat_frac * span, q, 0.0)
-    # cell-centred field for the energy: the average of the two face fields of
-    # each direction would be the Cartesian definition; here the energy is
-    # assembled with the field the method forms from the face fluxes, so it is
-    # left to the caller (E_mag is tiny at beta 1e5); the initial magnetic
-    # energy is taken from the potential field at the cell centres.
-    if beta and beta > 0:
-        eps = 1e-6 * span
-        def curlA(x):
-            out = np.zeros(x.shape)
-            for a_ in range(3):
-                e = np.zeros(3)
-                e[a_] = eps
-                dA = (A(x + e) - A(x - e)) / (2 * eps)   # dA / dx_a
-                # (curl A)_i = eps_ijk d_j A_k
-                if a_ == 0:
-                    out[..., 1] -= dA[..., 2]; out[..., 2] += dA[..., 1]
-                elif a_ == 1:
-                    out[..., 2] -= dA[..., 0]; out[..., 0] += dA[..., 2]
-                else:
-                    out[..., 0] -= dA[..., 1]; out[..., 1] += dA[..., 0]
-            return out
-        bc = curlA(xc)
-    else:
-        bc = np.zeros(xc.shape)
-    cons = np.zeros((5, 6, Nr, N, N))
+    cons = torch.empty((5, 6, Nr, N, N), **f64)
     cons[0] = rho
-    cons[1:4] = np.moveaxis(rho[..., None] * vel, -1, 0)
+    cons[1:4] = torch.movedim(rho[..., None] * vel, -1, 0)
     cons[4] = p / (gamma - 1.0) + 0.5 * rho * (vel ** 2).sum(-1) + 0.5 * (bc ** 2).sum(-1)
+    out = [cons, pa, pb, prr]
+    if dev.type == "cpu":
+        out = [t.numpy() for t in out]
     return ShellProblem(name=name or f"shell_{N}x{N}x{Nr}", N=N, Nr=Nr, r_in=r_in, r_out=r_out, gamma=gamma,
-                        cons=cons, pa=pa, pb=pb, pr=prr, bg=bg if background else None, g_c=g_c, heat=heat,
-                        cfl=cfl, meta=dict(seed=seed, amp=amp, beta=beta, r=r, r_mid=rm))
+                        cons=out[0], pa=out[1], pb=out[2], pr=out[3], bg=bg if background else None, g_c=g_c,
+                        heat=heat, cfl=cfl, meta=dict(seed=seed, amp=amp, beta=beta, r=r, r_mid=rm))
