@@ -697,6 +697,77 @@ def ensemble_c4(P, steps, warmup, stream, ws):
                                  "launches_per_step": launches_seq}}
 
 
+# Cubed-sphere shell (FP64): the flux kernel's FP64 operations per face
+# (DADD + DMUL + 2 DFMA from the ncu SASS counters of k_sph_flux on the
+# 6 x 64 x 64 x 64 shell: 4690.3 M over 4.743 M faces) and its DRAM bytes
+# per face in the same capture (517.4 MB; the work arrays exceed L2 there).
+SPH_FP64_FLOP_PER_FACE = 988.9
+SPH_FLUX_DRAM_BYTES_PER_FACE = 109.1
+
+
+def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, Nr=384):
+    """The cubed-sphere shell 6 x N x N x Nr (phl_sphere_*, FP64): the
+    n = 1.5 polytrope between r = 0.2 and 1 under its own radial gravity,
+    density noise 1e-3, a poloidal seed field at beta 1e5, heating in the
+    inner 30%, LHLLD, CFL 0.4, reflecting radial walls, well-balanced.  State
+    resident on the device; CUDA events on the sphere's stream around K
+    steps after W warm-up steps; then one more step with per-kernel timing
+    for the dominant kernel's roofline."""
+    import torch
+    import workloads as W
+    torch.cuda.empty_cache()
+    pr = W.shell_problem(N, Nr, device="cuda")
+    S = P.Sphere.from_problem(pr, stream=stream.cuda_stream)
+    torch.cuda.synchronize()          # the inputs were written on torch's stream
+    S.set_state(pr.cons, pr.pa, pr.pb, pr.pr)
+    counts = S.counts()
+    S.check()                         # synchronises the sphere's stream before the inputs go
+    del pr
+    torch.cuda.empty_cache()
+    S.step(warmup)
+    S.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    S.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    S.check()
+    S.set_timing(True)
+    S.step(1)
+    kt = S.kernel_times(reset=True)
+    S.set_timing(False)
+    S.check()
+    S.close()
+    cells, faces = counts["cells"], counts["faces"]
+    name, (launches, kms) = max(kt.items(), key=lambda kv: kv[1][1])
+    avg = kms / max(launches, 1)
+    out = {"workload": f"cubed-sphere shell 6 x {N} x {N} x {Nr} (r 0.2..1), n=1.5 polytrope, radial g, "
+                       "density noise 1e-3 seed 1234, poloidal field beta 1e5, heating inner 30%, LHLLD, "
+                       "CFL 0.4, reflecting walls, well-balanced, FP64",
+           "cells": cells, "faces": faces, "edges": counts["edges"],
+           "value": cells * STAGES * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+           "steps": steps, "warmup": warmup, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
+           "launches_per_step": sum(v[0] for v in kt.values())}
+    roof = {"kernel": name, "avg_launch_ms": avg, "launches": launches}
+    if name == "sph_flux":
+        # HBM view: W read once per cell, phi read and F, E, contact sign
+        # written once per face
+        b = cells * 64.0 + faces * (8.0 + 40.0 + 24.0 + 1.0)
+        gbs = b / (avg * 1e-3) / 1e9
+        roof["hbm"] = {"bytes_per_launch": b, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": gbs / hbm_peak, "peak_kind": f"{peak_kind} HBM copy"}
+        tf = faces * SPH_FP64_FLOP_PER_FACE / (avg * 1e-3) / 1e12
+        roof.update({"bound": "alu", "achieved": tf, "peak": alu["fp64"], "unit": "TFLOP/s",
+                     "frac": tf / alu["fp64"], "flop_per_face": SPH_FP64_FLOP_PER_FACE,
+                     "traffic": faces * SPH_FLUX_DRAM_BYTES_PER_FACE,
+                     "traffic_note": "ncu DRAM bytes per face on the 6 x 64^3 shell x faces",
+                     "peak_kind": "measured FP64 DFMA rate (phl_probe_alu)"})
+    out["roofline"] = roof
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -725,6 +796,11 @@ def main():
                     help="only the stellar-EOS box (its JSON object alone, for profiling)")
     ap.add_argument("--no-c4", action="store_true", help="skip the 24-box ensemble")
     ap.add_argument("--c4-steps", type=int, default=5)
+    ap.add_argument("--no-c5", action="store_true", help="skip the cubed-sphere shell")
+    ap.add_argument("--c5-steps", type=int, default=2)
+    ap.add_argument("--c5-only", action="store_true", help="only the cubed-sphere shell (its JSON object alone)")
+    ap.add_argument("--c5-n", type=int, default=256, help="cubed sphere: angular cells per patch side")
+    ap.add_argument("--c5-nr", type=int, default=384, help="cubed sphere: radial cells")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -746,6 +822,11 @@ def main():
     if args.poisson_only:
         if rank == 0:
             print(json.dumps(poisson_sphere(P, args.n, stream, hbm_peak, peak_kind)))
+        return 0
+    if args.c5_only:
+        if rank == 0:
+            print(json.dumps(cubed_sphere_c5(P, args.c5_steps, 1, stream, alu, hbm_peak, peak_kind, args.c5_n,
+                                             args.c5_nr)))
         return 0
     if args.c3_only:
         c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws)
@@ -793,6 +874,9 @@ def main():
     poisson = None
     if not args.no_poisson and len(forms) == 2:
         poisson = poisson_sphere(P, args.n, stream, hbm_peak, peak_kind)
+    c5 = None
+    if not args.no_c5 and len(forms) == 2:
+        c5 = cubed_sphere_c5(P, args.c5_steps, 1, stream, alu, hbm_peak, peak_kind, args.c5_n, args.c5_nr)
     launches = sum(v[0] for v in h["kt"].values())
     forms_out = {f: {"value": r["value"], "ms_per_step": r["ms"] / args.steps,
                      "stage_hbm": stage_hbm(r["value"] / max(ws, 1), f, hbm_peak, peak_kind),
@@ -835,6 +919,7 @@ def main():
         "ensemble_24_boxes": c4,
         "thermal_diffusion_sts": sts,
         "poisson_sphere": poisson,
+        "cubed_sphere_shell": c5,
         "gpu_launches": launches,
         "e2e": e2e,
         "clocks": clk,

@@ -639,6 +639,11 @@ phl_status phl_sphere_compute_dt(phl_sphere *s, double *dt_out);
 phl_status phl_sphere_step(phl_sphere *s, double dt, int nsteps);
 /* Synchronises the stream; PHL_ENEGATIVE / PHL_ENAN as in get_state. */
 phl_status phl_sphere_check(phl_sphere *s);
+/* Per-kernel CUDA-event timing of the sphere's launches, as phl_set_timing /
+ * phl_kernel_times for a grid (classes "sph_prim", "sph_flux", "sph_emf",
+ * "sph_update_faces", "sph_update_cells", "sph_dt", "set_scalar"). */
+phl_status phl_sphere_set_timing(phl_sphere *s, int on);
+phl_status phl_sphere_kernel_times(phl_sphere *s, phl_kernel_time *out, int max, int *n, int reset);
 
 #ifdef __cplusplus
 }

@@ -151,6 +151,8 @@ _SIGS = {
     "phl_sphere_compute_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "phl_sphere_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "phl_sphere_check": (C.c_int, [C.c_void_p]),
+    "phl_sphere_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "phl_sphere_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
 }
 
 
@@ -749,6 +751,16 @@ class Sphere:
 
     def check(self):
         _check(lib().phl_sphere_check(self.h))
+
+    def set_timing(self, on=True):
+        _check(lib().phl_sphere_set_timing(self.h, int(bool(on))))
+
+    def kernel_times(self, reset=True):
+        """{kernel class: (launches, summed ms)} since the last reset."""
+        arr = (KernelTime * 32)()
+        n = C.c_int()
+        _check(lib().phl_sphere_kernel_times(self.h, arr, 32, C.byref(n), int(bool(reset))))
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].ms) for i in range(min(n.value, 32))}
 
     def close(self):
         if self.h:

@@ -231,7 +231,8 @@ __device__ __forceinline__ double f2d_scaled(float f, int k) {
 // Kernel classes for the optional per-kernel event timing.
 enum KClass {
   KC_PRIM = 0, KC_FLAG_RAW, KC_FLAG_DILATE, KC_FLUX_X, KC_FLUX_Y, KC_FLUX_Z, KC_EMF, KC_UPDATE_CELLS,
-  KC_UPDATE_FACES, KC_DT, KC_SCALAR, KC_STAGE_MIXED, KC_FLUX_UPDATE, KC_COUNT
+  KC_UPDATE_FACES, KC_DT, KC_SCALAR, KC_STAGE_MIXED, KC_FLUX_UPDATE,
+  KC_SPH_PRIM, KC_SPH_FLUX, KC_SPH_EMF, KC_SPH_UPDATE_FACES, KC_SPH_UPDATE_CELLS, KC_SPH_DT, KC_COUNT
 };
 const char *kclass_name(int c);
 

@@ -9,7 +9,8 @@ const char *kclass_name(int c) {
   static const char *names[KC_COUNT] = {"prim",         "flag_raw",     "flag_dilate", "flux_x",
                                         "flux_y",       "flux_z",       "emf",         "update_cells",
                                         "update_faces", "dt",           "set_scalar",  "stage_mixed",
-                                        "flux_update"};
+                                        "flux_update",  "sph_prim",     "sph_flux",    "sph_emf",
+                                        "sph_update_faces", "sph_update_cells", "sph_dt"};
   return (c >= 0 && c < KC_COUNT) ? names[c] : "?";
 }
 

@@ -774,6 +774,7 @@ struct phl_sphere {
   phl_sphere_desc desc;
   SphDev D;
   AbiMap AM;
+  Prof prof;
   cudaStream_t s = nullptr;
   std::vector<void *> allocs;
   double *U = nullptr, *U1 = nullptr, *phi = nullptr, *phi1 = nullptr, *dt = nullptr, *abi_buf = nullptr;
@@ -819,10 +820,21 @@ phl_status sph_flags(phl_sphere *S) {
   return PHL_OK;
 }
 
+// a launch between the timing events of its kernel class (when timing is on)
+template <typename F>
+void timed(phl_sphere *S, int cls, F &&launch) {
+  S->prof.begin(cls, S->s);
+  launch();
+  S->prof.end(S->s);
+}
+
 void sph_dt(phl_sphere *S, const double *U, const double *phi) {
-  k_sph_prims<<<nblk(S->D.ncell), SPT, 0, S->s>>>(S->D, U, phi);
-  k_sph_dt<<<nblk(S->D.ncell), SPT, 0, S->s>>>(S->D, S->dmax);
-  k_sph_dt_fin<<<1, 1, 0, S->s>>>(S->D.cfl, S->dmax, S->dt);
+  const SphDev &D = S->D;
+  timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, U, phi); });
+  timed(S, KC_SPH_DT, [&] {
+    k_sph_dt<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->dmax);
+    k_sph_dt_fin<<<1, 1, 0, S->s>>>(D.cfl, S->dmax, S->dt);
+  });
 }
 
 }  // namespace
@@ -906,8 +918,36 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
 
 void phl_sphere_destroy(phl_sphere *S) {
   if (!S) return;
+  S->prof.release();
   for (void *p : S->allocs) cudaFree(p);
   delete S;
+}
+
+phl_status phl_sphere_set_timing(phl_sphere *S, int on) {
+  if (!S) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_timing: null sphere");
+  S->prof.on = on != 0;
+  return PHL_OK;
+}
+
+phl_status phl_sphere_kernel_times(phl_sphere *S, phl_kernel_time *out, int max, int *n, int reset) {
+  if (!S || !n || (max > 0 && !out)) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_kernel_times: null argument");
+  cudaError_t e = S->prof.fold();
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_kernel_times: %s", cudaGetErrorString(e));
+  int k = 0;
+  for (int c = 0; c < KC_COUNT; ++c) {
+    if (S->prof.cnt[c] == 0) continue;
+    if (k < max) {
+      memset(&out[k], 0, sizeof(out[k]));
+      strncpy(out[k].name, kclass_name(c), sizeof(out[k].name) - 1);
+      out[k].launches = S->prof.cnt[c];
+      out[k].ms = S->prof.ms[c];
+    }
+    ++k;
+  }
+  *n = k;
+  if (reset)
+    for (int c = 0; c < KC_COUNT; ++c) { S->prof.cnt[c] = 0; S->prof.ms[c] = 0.0; }
+  return PHL_OK;
 }
 
 phl_status phl_sphere_counts(const phl_sphere *S, long *cells, long *faces, long *edges) {
@@ -978,18 +1018,22 @@ phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
   static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
   const SphDev &D = S->D;
   for (int n = 0; n < nsteps; ++n) {
-    if (dt > 0.0) k_sph_set<<<1, 1, 0, S->s>>>(dt, S->dt);
+    if (dt > 0.0) timed(S, KC_SCALAR, [&] { k_sph_set<<<1, 1, 0, S->s>>>(dt, S->dt); });
     else sph_dt(S, S->U, S->phi);   // the CFL step of U^n (Eq. cfl); leaves W of U^n
     // Shu-Osher SSP-RK3 (Sect. 2.9); stage input U1 (U^n at the first stage)
     for (int st = 0; st < 3; ++st) {
       const double *Uin = st == 0 ? S->U : S->U1, *pin = st == 0 ? S->phi : S->phi1;
       double *Uout = st == 2 ? S->U : S->U1, *pout = st == 2 ? S->phi : S->phi1;
-      if (st > 0 || dt > 0.0) k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, Uin, pin);
-      k_sph_flux<<<nblk(D.NF), SPT, 0, S->s>>>(D, pin);
-      k_sph_emf<<<nblk(D.NE), SPT, 0, S->s>>>(D);
+      const double a = A3[st], b = B3[st];
+      if (st > 0 || dt > 0.0)
+        timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, Uin, pin); });
+      timed(S, KC_SPH_FLUX, [&] { k_sph_flux<<<nblk(D.NF), SPT, 0, S->s>>>(D, pin); });
+      timed(S, KC_SPH_EMF, [&] { k_sph_emf<<<nblk(D.NE), SPT, 0, S->s>>>(D); });
       // each thread reads its own element of in and base before writing out
-      k_sph_update_faces<<<nblk(D.NF), SPT, 0, S->s>>>(D, pin, S->phi, pout, A3[st], B3[st], S->dt);
-      k_sph_update_cells<<<nblk(D.ncell), SPT, 0, S->s>>>(D, Uin, S->U, Uout, A3[st], B3[st], S->dt);
+      timed(S, KC_SPH_UPDATE_FACES,
+            [&] { k_sph_update_faces<<<nblk(D.NF), SPT, 0, S->s>>>(D, pin, S->phi, pout, a, b, S->dt); });
+      timed(S, KC_SPH_UPDATE_CELLS,
+            [&] { k_sph_update_cells<<<nblk(D.ncell), SPT, 0, S->s>>>(D, Uin, S->U, Uout, a, b, S->dt); });
     }
     ++S->steps;
   }
