@@ -703,21 +703,24 @@ def ensemble_c4(P, steps, warmup, stream, ws):
 # per face in the same capture (517.4 MB; the work arrays exceed L2 there).
 SPH_FP64_FLOP_PER_FACE = 988.9
 SPH_FLUX_DRAM_BYTES_PER_FACE = 109.1
+# the mixed form's flux kernel: FP32 operations per face (FADD + FMUL + 2 FFMA,
+# same capture recipe); None until measured
+SPH_FP32_FLOP_PER_FACE = None
 
 
-def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, Nr=384):
+def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, Nr=384, precision="fp64"):
     """The cubed-sphere shell 6 x N x N x Nr (phl_sphere_*, FP64): the
     n = 1.5 polytrope between r = 0.2 and 1 under its own radial gravity,
     density noise 1e-3, a poloidal seed field at beta 1e5, heating in the
-    inner 30%, LHLLD, CFL 0.4, reflecting radial walls, well-balanced.  State
-    resident on the device; CUDA events on the sphere's stream around K
-    steps after W warm-up steps; then one more step with per-kernel timing
-    for the dominant kernel's roofline."""
+    inner 30%, LHLLD, CFL 0.4, reflecting radial walls, well-balanced, in
+    the FP64 or the mixed form.  State resident on the device; CUDA events on
+    the sphere's stream around K steps after W warm-up steps; then one more
+    step with per-kernel timing for the dominant kernel's roofline."""
     import torch
     import workloads as W
     torch.cuda.empty_cache()
     pr = W.shell_problem(N, Nr, device="cuda")
-    S = P.Sphere.from_problem(pr, stream=stream.cuda_stream)
+    S = P.Sphere.from_problem(pr, stream=stream.cuda_stream, precision=precision)
     torch.cuda.synchronize()          # the inputs were written on torch's stream
     S.set_state(pr.cons, pr.pa, pr.pb, pr.pr)
     counts = S.counts()
@@ -745,13 +748,13 @@ def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, N
     avg = kms / max(launches, 1)
     out = {"workload": f"cubed-sphere shell 6 x {N} x {N} x {Nr} (r 0.2..1), n=1.5 polytrope, radial g, "
                        "density noise 1e-3 seed 1234, poloidal field beta 1e5, heating inner 30%, LHLLD, "
-                       "CFL 0.4, reflecting walls, well-balanced, FP64",
+                       f"CFL 0.4, reflecting walls, well-balanced, {precision}",
            "cells": cells, "faces": faces, "edges": counts["edges"],
            "value": cells * STAGES * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
            "steps": steps, "warmup": warmup, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
            "launches_per_step": sum(v[0] for v in kt.values())}
     roof = {"kernel": name, "avg_launch_ms": avg, "launches": launches}
-    if name == "sph_flux":
+    if name == "sph_flux" and precision == "fp64":
         # HBM view: W read once per cell, phi read and F, E, contact sign
         # written once per face
         b = cells * 64.0 + faces * (8.0 + 40.0 + 24.0 + 1.0)
@@ -764,8 +767,30 @@ def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, N
                      "traffic": faces * SPH_FLUX_DRAM_BYTES_PER_FACE,
                      "traffic_note": "ncu DRAM bytes per face on the 6 x 64^3 shell x faces",
                      "peak_kind": "measured FP64 DFMA rate (phl_probe_alu)"})
+    elif name == "sph_flux":
+        # mixed: FP32 work arrays; W read once per cell, phi (FP64) and dPhi
+        # (FP32) read, F, E (FP32) and the contact sign written once per face
+        b = cells * 32.0 + faces * (8.0 + 4.0 + 20.0 + 12.0 + 1.0)
+        gbs = b / (avg * 1e-3) / 1e9
+        roof["hbm"] = {"bytes_per_launch": b, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": gbs / hbm_peak, "peak_kind": f"{peak_kind} HBM copy"}
+        if SPH_FP32_FLOP_PER_FACE:
+            tf = faces * SPH_FP32_FLOP_PER_FACE / (avg * 1e-3) / 1e12
+            roof.update({"bound": "alu", "achieved": tf, "peak": alu["fp32"], "unit": "TFLOP/s",
+                         "frac": tf / alu["fp32"], "flop_per_face": SPH_FP32_FLOP_PER_FACE,
+                         "peak_kind": "measured FP32 FFMA rate (phl_probe_alu)"})
     out["roofline"] = roof
     return out
+
+
+def cubed_sphere_forms(P, args, stream, alu, hbm_peak, peak_kind):
+    """The shell in the mixed form (the value) and in the FP64 form beside it."""
+    mx = cubed_sphere_c5(P, args.c5_steps_mixed, 2, stream, alu, hbm_peak, peak_kind, args.c5_n, args.c5_nr,
+                         "mixed")
+    f64 = cubed_sphere_c5(P, args.c5_steps, 1, stream, alu, hbm_peak, peak_kind, args.c5_n, args.c5_nr, "fp64")
+    mx["fp64"] = f64
+    mx["mixed_over_fp64"] = mx["value"] / f64["value"]
+    return mx
 
 
 def main():
@@ -797,7 +822,9 @@ def main():
     ap.add_argument("--no-c4", action="store_true", help="skip the 24-box ensemble")
     ap.add_argument("--c4-steps", type=int, default=5)
     ap.add_argument("--no-c5", action="store_true", help="skip the cubed-sphere shell")
-    ap.add_argument("--c5-steps", type=int, default=2)
+    ap.add_argument("--c5-steps", type=int, default=2, help="cubed sphere: timed FP64 steps")
+    ap.add_argument("--c5-steps-mixed", type=int, default=5, help="cubed sphere: timed mixed steps")
+    ap.add_argument("--c5-precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--c5-only", action="store_true", help="only the cubed-sphere shell (its JSON object alone)")
     ap.add_argument("--c5-n", type=int, default=256, help="cubed sphere: angular cells per patch side")
     ap.add_argument("--c5-nr", type=int, default=384, help="cubed sphere: radial cells")
@@ -825,8 +852,12 @@ def main():
         return 0
     if args.c5_only:
         if rank == 0:
-            print(json.dumps(cubed_sphere_c5(P, args.c5_steps, 1, stream, alu, hbm_peak, peak_kind, args.c5_n,
-                                             args.c5_nr)))
+            if args.c5_precision == "both":
+                print(json.dumps(cubed_sphere_forms(P, args, stream, alu, hbm_peak, peak_kind)))
+            else:
+                steps = args.c5_steps if args.c5_precision == "fp64" else args.c5_steps_mixed
+                print(json.dumps(cubed_sphere_c5(P, steps, 1, stream, alu, hbm_peak, peak_kind, args.c5_n,
+                                                 args.c5_nr, args.c5_precision)))
         return 0
     if args.c3_only:
         c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws)
@@ -876,7 +907,7 @@ def main():
         poisson = poisson_sphere(P, args.n, stream, hbm_peak, peak_kind)
     c5 = None
     if not args.no_c5 and len(forms) == 2:
-        c5 = cubed_sphere_c5(P, args.c5_steps, 1, stream, alu, hbm_peak, peak_kind, args.c5_n, args.c5_nr)
+        c5 = cubed_sphere_forms(P, args, stream, alu, hbm_peak, peak_kind)
     launches = sum(v[0] for v in h["kt"].values())
     forms_out = {f: {"value": r["value"], "ms_per_step": r["ms"] / args.steps,
                      "stage_hbm": stage_hbm(r["value"] / max(ws, 1), f, hbm_peak, peak_kind),

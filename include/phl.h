@@ -604,6 +604,9 @@ typedef struct {
   double cfl;               /* Courant number (Eq. cfl), > 0                    */
   int riemann;              /* PHL_LHLLD / PHL_HLLD / PHL_HLL                   */
   double mach_thr;          /* LHLLD Mach threshold, > 0                        */
+  int precision;            /* PHL_FP64, or PHL_MIXED: FP64 U^n and face fluxes */
+                            /* (FP64 face stages, circulations summed in FP64),*/
+                            /* FP32 cell increments, deviations, fluxes, EMFs  */
   const double *rho_c, *p_c;  /* host: hydrostatic background at the shell    */
                               /* middles (Nr each), or both null with rho_f,  */
                               /* p_f: no background (full-state fluxes)       */
@@ -615,8 +618,9 @@ typedef struct {
 typedef struct phl_sphere phl_sphere;
 
 /* Builds the mesh on the host and uploads it (profiles are read here only).
- * PHL_EINVAL (sizes, radii, gamma, cfl, solver, a partial background, more
- * than 2^31 faces or edges), PHL_ENOMEM. */
+ * PHL_EINVAL (sizes, radii, gamma, cfl, solver, precision, a partial
+ * background, more than 2^31 faces or edges), PHL_ENOMEM.  Device memory:
+ * FP64 about 450 bytes per cell, mixed about 270. */
 phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out);
 void phl_sphere_destroy(phl_sphere *s);
 /* Unique cells, faces (seam faces once) and edges of the mesh. */

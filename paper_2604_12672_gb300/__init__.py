@@ -676,7 +676,7 @@ class Poisson:
 class SphereDesc(C.Structure):
     _fields_ = [("N", C.c_int), ("Nr", C.c_int), ("r_in", C.c_double), ("r_out", C.c_double),
                 ("gamma", C.c_double), ("cfl", C.c_double), ("riemann", C.c_int), ("mach_thr", C.c_double),
-                ("rho_c", C.c_void_p), ("p_c", C.c_void_p), ("rho_f", C.c_void_p), ("p_f", C.c_void_p),
+                ("precision", C.c_int), ("rho_c", C.c_void_p), ("p_c", C.c_void_p), ("rho_f", C.c_void_p), ("p_f", C.c_void_p),
                 ("g_c", C.c_void_p), ("heat", C.c_void_p), ("stream", C.c_void_p)]
 
 
@@ -689,7 +689,7 @@ class Sphere:
     (Nr + 1), or is None for full-state fluxes."""
 
     def __init__(self, N, Nr, r_in, r_out, gamma=5.0 / 3.0, cfl=0.4, riemann="lhlld", mach_thr=0.6, bg=None,
-                 g_c=None, heat=None, stream=None):
+                 g_c=None, heat=None, stream=None, precision="fp64"):
         self.N, self.Nr = int(N), int(Nr)
         keep = []
 
@@ -702,6 +702,7 @@ class Sphere:
         d = SphereDesc()
         d.N, d.Nr, d.r_in, d.r_out = self.N, self.Nr, float(r_in), float(r_out)
         d.gamma, d.cfl, d.riemann, d.mach_thr = float(gamma), float(cfl), RIEMANN[riemann], float(mach_thr)
+        d.precision = PRECISION[precision]
         if bg is not None:
             d.rho_c, d.p_c, d.rho_f, d.p_f = (arr(bg[k]) for k in ("rho_c", "p_c", "rho_f", "p_f"))
         d.g_c, d.heat, d.stream = arr(g_c), arr(heat), stream
@@ -710,11 +711,12 @@ class Sphere:
         self.h = h
 
     @classmethod
-    def from_problem(cls, pr, wb=True, stream=None):
+    def from_problem(cls, pr, wb=True, stream=None, precision="fp64"):
         """From a workloads.ShellProblem (its solver, CFL, background, gravity
         and heating); wb=False drops the background."""
         return cls(pr.N, pr.Nr, pr.r_in, pr.r_out, gamma=pr.gamma, cfl=pr.cfl, riemann=pr.riemann,
-                   mach_thr=pr.mach_thr, bg=pr.bg if wb else None, g_c=pr.g_c, heat=pr.heat, stream=stream)
+                   mach_thr=pr.mach_thr, bg=pr.bg if wb else None, g_c=pr.g_c, heat=pr.heat, stream=stream,
+                   precision=precision)
 
     def shapes(self):
         N, Nr = self.N, self.Nr

@@ -26,6 +26,7 @@ PER_FILE_FLAGS = {
     "unit_kernels.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "stage_fused.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "stage_prim.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "sphere.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
 }
 
 

@@ -333,6 +333,18 @@ void build_ang(int N, Ang &M) {
 
 // ---------------------------------------------------------------------------
 // device
+//
+// Two forms of the stage.  FP64: every work array in double.  Mixed (the
+// paper's mixed-precision form, Sect. 2.8): U^n stays FP64 and a stage
+// carries the cells' increments dU = U^(s) - U^n in FP32 (SSP-RK3 has
+// a + b = 1 in every stage, so dU^(s) = b (dU^(s-1) - dt R)); primitives are
+// formed as FP32 deviations from the background out of an FP64 difference
+// U^n - U_hat plus the FP32 increment; fluxes, EMFs and residuals are FP32;
+// the last stage adds the increment to U^n in FP64.  The face fluxes keep
+// FP64 stage values, advanced by circulations summed in FP64 from the FP32
+// edge EMFs: every edge's term enters its faces as the same FP64 product, so
+// the divergence of each cell stays at FP64 rounding (Eq. divb), as in the
+// FP64 form.
 
 enum { SW_RHO = 0, SW_U = 1, SW_B = 4, SW_P = 7, SW_N = 8 };
 
@@ -347,15 +359,22 @@ struct SphDev {
   const signed char *s_in, *s_v0, *s_v1, *s_swap, *csg, *crs, *vsgn;
   const unsigned char *vcnt;
   const double *rho_c, *p_c, *rho_f, *p_f, *g_c, *heat;   // null when absent
-  double *W;              // 8 deviations per cell, SoA
-  double *FC, *EF;        // 5 integrated fluxes, 3 face-EMF components per face, SoA
-  signed char *UP;        // contact direction per face
-  double *EE;             // edge EMFs
   int *dflag;
 };
 
-__device__ __forceinline__ double bg_rho(const SphDev &D, int k) { return D.rho_c ? D.rho_c[k] : 0.0; }
-__device__ __forceinline__ double bg_p(const SphDev &D, int k) { return D.p_c ? D.p_c[k] : 0.0; }
+// work arrays of one form (R = double: FP64, float: mixed)
+template <typename R>
+struct SphWork {
+  R *W;             // 8 deviations per cell, SoA
+  R *FC, *EF;       // 5 integrated fluxes, 3 face-EMF components per face, SoA
+  R *EE;            // edge EMFs (E . l)
+  signed char *UP;  // contact direction per face
+};
+
+template <typename R>
+__device__ __forceinline__ R bg_rho(const SphDev &D, int k) { return D.rho_c ? (R)D.rho_c[k] : R(0); }
+template <typename R>
+__device__ __forceinline__ R bg_p(const SphDev &D, int k) { return D.p_c ? (R)D.p_c[k] : R(0); }
 
 // The six faces of cell (a, k) in the order -a, +a, -b, +b, -r, +r: index,
 // outward sign, centre.
@@ -387,7 +406,16 @@ __device__ __forceinline__ double cell_vol(const SphDev &D, long a, int k) {
   return (r1 * r1 * r1 - r0 * r0 * r0) / 3.0 * D.com[a];
 }
 
-__global__ void k_sph_prims(SphDev D, const double *__restrict__ U, const double *__restrict__ phi) {
+template <typename R>
+__device__ __forceinline__ void store_w(const SphDev &D, const SphWork<R> &Wk, long c, R drho, V3 u, V3 B, R dP) {
+  const long n = D.ncell;
+  Wk.W[SW_RHO * n + c] = drho;
+  Wk.W[(SW_U + 0) * n + c] = (R)u.x; Wk.W[(SW_U + 1) * n + c] = (R)u.y; Wk.W[(SW_U + 2) * n + c] = (R)u.z;
+  Wk.W[(SW_B + 0) * n + c] = (R)B.x; Wk.W[(SW_B + 1) * n + c] = (R)B.y; Wk.W[(SW_B + 2) * n + c] = (R)B.z;
+  Wk.W[SW_P * n + c] = dP;
+}
+
+__global__ void k_sph_prims(SphDev D, SphWork<double> Wk, const double *__restrict__ U, const double *__restrict__ phi) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= D.ncell) return;
   const int k = (int)(c / D.NC);
@@ -404,177 +432,237 @@ __global__ void k_sph_prims(SphDev D, const double *__restrict__ U, const double
   const double P = (D.gamma - 1.0) * (U[4 * n + c] - 0.5 * rho * dot3(u, u) - 0.5 * dot3(B, B));
   if (!(rho > 0.0) || !(P > 0.0)) atomicOr(D.dflag, FLAG_NEG);
   if (!isfinite(rho) || !isfinite(P)) atomicOr(D.dflag, FLAG_NAN);
-  D.W[SW_RHO * n + c] = rho - bg_rho(D, k);
-  D.W[(SW_U + 0) * n + c] = u.x; D.W[(SW_U + 1) * n + c] = u.y; D.W[(SW_U + 2) * n + c] = u.z;
-  D.W[(SW_B + 0) * n + c] = B.x; D.W[(SW_B + 1) * n + c] = B.y; D.W[(SW_B + 2) * n + c] = B.z;
-  D.W[SW_P * n + c] = P - bg_p(D, k);
+  store_w<double>(D, Wk, c, rho - bg_rho<double>(D, k), u, B, P - bg_p<double>(D, k));
 }
 
-// deviations of cell c, mirrored across a wall of unit normal nw when mir
-__device__ __forceinline__ void load_w(const SphDev &D, long c, bool mir, V3 nw, double *w) {
+// Mixed form: the stage input is U^n + dU (dU null at the first stage) and
+// the stage's face fluxes.  The density and energy deviations start from the
+// FP64 differences rho^n - rho_hat and E^n - P_hat / (gamma - 1); the rest is
+// FP32.
+__global__ void k_sph_prims_mx(SphDev D, SphWork<float> Wk, const double *__restrict__ U, const float *__restrict__ dU,
+                               const double *__restrict__ phi) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (c >= D.ncell) return;
+  const int k = (int)(c / D.NC);
+  const long a = c - (long)k * D.NC, n = D.ncell;
+  CellFaces F;
+  cell_faces(D, a, k, F);
+  float bx = 0.f, by = 0.f, bz = 0.f;
 #pragma unroll
-  for (int v = 0; v < SW_N; ++v) w[v] = D.W[v * D.ncell + c];
+  for (int m = 0; m < 6; ++m) {
+    const float w = (float)(F.s[m] * phi[F.f[m]]);
+    bx += (float)F.x[m].x * w; by += (float)F.x[m].y * w; bz += (float)F.x[m].z * w;
+  }
+  const float iv = (float)(1.0 / cell_vol(D, a, k));
+  bx *= iv; by *= iv; bz *= iv;
+  const double rh = D.rho_c ? D.rho_c[k] : 0.0, eh = D.p_c ? D.p_c[k] / (D.gamma - 1.0) : 0.0;
+  float drho = (float)(U[c] - rh), dE = (float)(U[4 * n + c] - eh);
+  float mx = (float)U[n + c], my = (float)U[2 * n + c], mz = (float)U[3 * n + c];
+  if (dU) {
+    drho += dU[c]; dE += dU[4 * n + c];
+    mx += dU[n + c]; my += dU[2 * n + c]; mz += dU[3 * n + c];
+  }
+  const float rho = (float)rh + drho, ir = 1.0f / rho;
+  const float ux = mx * ir, uy = my * ir, uz = mz * ir;
+  const float gm1 = (float)(D.gamma - 1.0);
+  // P - P_hat = (gamma - 1) (E - E_hat - rho u^2 / 2 - B^2 / 2)
+  const float dP = gm1 * (dE - 0.5f * (mx * ux + my * uy + mz * uz) - 0.5f * (bx * bx + by * by + bz * bz));
+  const float P = (float)(D.p_c ? D.p_c[k] : 0.0) + dP;
+  if (!(rho > 0.f) || !(P > 0.f)) atomicOr(D.dflag, FLAG_NEG);
+  if (!isfinite(rho) || !isfinite(P)) atomicOr(D.dflag, FLAG_NAN);
+  Wk.W[SW_RHO * n + c] = drho;
+  Wk.W[(SW_U + 0) * n + c] = ux; Wk.W[(SW_U + 1) * n + c] = uy; Wk.W[(SW_U + 2) * n + c] = uz;
+  Wk.W[(SW_B + 0) * n + c] = bx; Wk.W[(SW_B + 1) * n + c] = by; Wk.W[(SW_B + 2) * n + c] = bz;
+  Wk.W[SW_P * n + c] = dP;
+}
+
+// deviations of cell c, mirrored across a wall of unit normal (nx, ny, nz) when mir
+template <typename R>
+__device__ __forceinline__ void load_w(const SphDev &D, const SphWork<R> &Wk, long c, bool mir, R nx, R ny, R nz,
+                                       R *w) {
+#pragma unroll
+  for (int v = 0; v < SW_N; ++v) w[v] = Wk.W[v * D.ncell + c];
   if (mir) {
-    V3 u = v3(w[SW_U], w[SW_U + 1], w[SW_U + 2]), b = v3(w[SW_B], w[SW_B + 1], w[SW_B + 2]);
-    u = u - nw * (2.0 * dot3(u, nw));
-    b = b - nw * (2.0 * dot3(b, nw));
-    w[SW_U] = u.x; w[SW_U + 1] = u.y; w[SW_U + 2] = u.z;
-    w[SW_B] = b.x; w[SW_B + 1] = b.y; w[SW_B + 2] = b.z;
+    const R un = R(2) * (w[SW_U] * nx + w[SW_U + 1] * ny + w[SW_U + 2] * nz);
+    const R bn = R(2) * (w[SW_B] * nx + w[SW_B + 1] * ny + w[SW_B + 2] * nz);
+    w[SW_U] -= un * nx; w[SW_U + 1] -= un * ny; w[SW_U + 2] -= un * nz;
+    w[SW_B] -= bn * nx; w[SW_B + 1] -= bn * ny; w[SW_B + 2] -= bn * nz;
   }
 }
 
-__device__ __forceinline__ double vl_d(double a, double b, double c) {
-  const double dm = b - a, dp = c - b;
-  return dm * dp > 0.0 ? 2.0 * dm * dp / (dm + dp) : 0.0;
+template <typename R>
+__device__ __forceinline__ R vl_t(R a, R b, R c) {
+  const R dm = b - a, dp = c - b;
+  return dm * dp > R(0) ? R(2) * dm * dp / (dm + dp) : R(0);
 }
 
-__global__ void k_sph_flux(SphDev D, const double *__restrict__ phi) {
+template <typename R>
+__global__ void k_sph_flux(SphDev D, SphWork<R> Wk, const double *__restrict__ phi) {
   const long f = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (f >= D.NF) return;
-  double wL[SW_N], wR[SW_N], wLL[SW_N], wRR[SW_N];
-  V3 n;
-  double A, brho = 0.0, bp = 0.0;
+  R wL[SW_N], wR[SW_N], wLL[SW_N], wRR[SW_N];
+  double nd[3], Ad;
+  R brho = R(0), bp = R(0);
   bool wall = false;
   if (f < D.FA) {   // angular face (s, k)
     const int k = (int)(f / D.NS);
     const long s = f - (long)k * D.NS, base = (long)k * D.NC;
-    const V3 z = v3(0, 0, 0);
-    load_w(D, base + D.sL[s], false, z, wL);
-    load_w(D, base + D.sR[s], false, z, wR);
-    load_w(D, base + D.sLL[s], false, z, wLL);
-    load_w(D, base + D.sRR[s], false, z, wRR);
-    n = ld3(D.sn, s);
+    load_w<R>(D, Wk, base + D.sL[s], false, R(0), R(0), R(0), wL);
+    load_w<R>(D, Wk, base + D.sR[s], false, R(0), R(0), R(0), wR);
+    load_w<R>(D, Wk, base + D.sLL[s], false, R(0), R(0), R(0), wLL);
+    load_w<R>(D, Wk, base + D.sRR[s], false, R(0), R(0), R(0), wRR);
+    nd[0] = D.sn[3 * s]; nd[1] = D.sn[3 * s + 1]; nd[2] = D.sn[3 * s + 2];
     const double r0 = D.r[k], r1 = D.r[k + 1];
-    A = 0.5 * (r1 * r1 - r0 * r0) * D.sth[s];
-    if (D.rho_c) { brho = D.rho_c[k]; bp = D.p_c[k]; }
+    Ad = 0.5 * (r1 * r1 - r0 * r0) * D.sth[s];
+    if (D.rho_c) { brho = (R)D.rho_c[k]; bp = (R)D.p_c[k]; }
   } else {          // radial face (a, k)
     const long q = f - D.FA;
     const int k = (int)(q / D.NC), Nr = D.Nr;
     const long a = q - (long)k * D.NC;
-    n = ld3(D.cna, a);
-    A = D.r[k] * D.r[k] * D.cva[a];
-    if (D.rho_c) { brho = D.rho_f[k]; bp = D.p_f[k]; }
+    nd[0] = D.cna[3 * a]; nd[1] = D.cna[3 * a + 1]; nd[2] = D.cna[3 * a + 2];
+    Ad = D.r[k] * D.r[k] * D.cva[a];
+    if (D.rho_c) { brho = (R)D.rho_f[k]; bp = (R)D.p_f[k]; }
+    const R nx = (R)nd[0], ny = (R)nd[1], nz = (R)nd[2];
     const long c0 = a, cst = D.NC;   // cell (a, kk) = c0 + kk cst
     if (k == 0) {            // inner wall: the ghost side mirrors cells 0 and 1
       wall = true;
-      load_w(D, c0, false, n, wR);
-      load_w(D, c0 + cst, false, n, wRR);
-      load_w(D, c0, true, n, wL);
-      load_w(D, c0 + cst, true, n, wLL);
+      load_w<R>(D, Wk, c0, false, nx, ny, nz, wR);
+      load_w<R>(D, Wk, c0 + cst, false, nx, ny, nz, wRR);
+      load_w<R>(D, Wk, c0, true, nx, ny, nz, wL);
+      load_w<R>(D, Wk, c0 + cst, true, nx, ny, nz, wLL);
     } else if (k == Nr) {    // outer wall
       wall = true;
-      load_w(D, c0 + (Nr - 1) * cst, false, n, wL);
-      load_w(D, c0 + (Nr - 2) * cst, false, n, wLL);
-      load_w(D, c0 + (Nr - 1) * cst, true, n, wR);
-      load_w(D, c0 + (Nr - 2) * cst, true, n, wRR);
+      load_w<R>(D, Wk, c0 + (Nr - 1) * cst, false, nx, ny, nz, wL);
+      load_w<R>(D, Wk, c0 + (Nr - 2) * cst, false, nx, ny, nz, wLL);
+      load_w<R>(D, Wk, c0 + (Nr - 1) * cst, true, nx, ny, nz, wR);
+      load_w<R>(D, Wk, c0 + (Nr - 2) * cst, true, nx, ny, nz, wRR);
     } else {                 // beside a wall the far cell is the near one's mirror
-      load_w(D, c0 + (k - 1) * cst, false, n, wL);
-      load_w(D, c0 + k * cst, false, n, wR);
-      if (k >= 2) load_w(D, c0 + (k - 2) * cst, false, n, wLL);
-      else load_w(D, c0, true, n, wLL);
-      if (k + 1 <= Nr - 1) load_w(D, c0 + (k + 1) * cst, false, n, wRR);
-      else load_w(D, c0 + (Nr - 1) * cst, true, n, wRR);
+      load_w<R>(D, Wk, c0 + (k - 1) * cst, false, nx, ny, nz, wL);
+      load_w<R>(D, Wk, c0 + k * cst, false, nx, ny, nz, wR);
+      if (k >= 2) load_w<R>(D, Wk, c0 + (k - 2) * cst, false, nx, ny, nz, wLL);
+      else load_w<R>(D, Wk, c0, true, nx, ny, nz, wLL);
+      if (k + 1 <= Nr - 1) load_w<R>(D, Wk, c0 + (k + 1) * cst, false, nx, ny, nz, wRR);
+      else load_w<R>(D, Wk, c0 + (Nr - 1) * cst, true, nx, ny, nz, wRR);
     }
   }
-  double ql[SW_N], qr[SW_N];
+  R ql[SW_N], qr[SW_N];
 #pragma unroll
   for (int v = 0; v < SW_N; ++v) {
-    ql[v] = wL[v] + 0.5 * vl_d(wLL[v], wL[v], wR[v]);
-    qr[v] = wR[v] - 0.5 * vl_d(wL[v], wR[v], wRR[v]);
+    ql[v] = wL[v] + R(0.5) * vl_t<R>(wLL[v], wL[v], wR[v]);
+    qr[v] = wR[v] - R(0.5) * vl_t<R>(wL[v], wR[v], wRR[v]);
   }
-  // tangents from the Cartesian axis least aligned with n
-  const double an0 = fabs(n.x), an1 = fabs(n.y), an2 = fabs(n.z);
+  // normal frame: tangents from the Cartesian axis least aligned with n
+  const R n0 = (R)nd[0], n1 = (R)nd[1], n2 = (R)nd[2];
+  const R an0 = fabs(n0), an1 = fabs(n1), an2 = fabs(n2);
   const int ax = an1 < an0 ? (an2 < an1 ? 2 : 1) : (an2 < an0 ? 2 : 0);
-  const V3 t1 = unit3(cross3(v3(ax == 0, ax == 1, ax == 2), n)), t2 = cross3(n, t1);
-  const V3 ul = v3(ql[SW_U], ql[SW_U + 1], ql[SW_U + 2]), ur = v3(qr[SW_U], qr[SW_U + 1], qr[SW_U + 2]);
-  const V3 bl = v3(ql[SW_B], ql[SW_B + 1], ql[SW_B + 2]), br = v3(qr[SW_B], qr[SW_B + 1], qr[SW_B + 2]);
-  double wl[RD_X0], wr[RD_X0];
+  // t1 = unit(e_ax x n), t2 = n x t1
+  R t1x = ax == 0 ? R(0) : (ax == 1 ? n2 : -n1);
+  R t1y = ax == 0 ? -n2 : (ax == 1 ? R(0) : n0);
+  R t1z = ax == 0 ? n1 : (ax == 1 ? -n0 : R(0));
+  const R it = R(1) / sqrt(t1x * t1x + t1y * t1y + t1z * t1z);
+  t1x *= it; t1y *= it; t1z *= it;
+  const R t2x = n1 * t1z - n2 * t1y, t2y = n2 * t1x - n0 * t1z, t2z = n0 * t1y - n1 * t1x;
+  auto dn = [&](const R *q, int o) { return q[o] * n0 + q[o + 1] * n1 + q[o + 2] * n2; };
+  auto d1 = [&](const R *q, int o) { return q[o] * t1x + q[o + 1] * t1y + q[o + 2] * t1z; };
+  auto d2 = [&](const R *q, int o) { return q[o] * t2x + q[o + 1] * t2y + q[o + 2] * t2z; };
+  R wl[RD_X0], wr[RD_X0];
   wl[RD_RHO] = ql[SW_RHO]; wr[RD_RHO] = qr[SW_RHO];
-  wl[RD_UN] = dot3(ul, n); wl[RD_UT1] = dot3(ul, t1); wl[RD_UT2] = dot3(ul, t2);
-  wr[RD_UN] = dot3(ur, n); wr[RD_UT1] = dot3(ur, t1); wr[RD_UT2] = dot3(ur, t2);
-  wl[RD_BT1] = dot3(bl, t1); wl[RD_BT2] = dot3(bl, t2);
-  wr[RD_BT1] = dot3(br, t1); wr[RD_BT2] = dot3(br, t2);
+  wl[RD_UN] = dn(ql, SW_U); wl[RD_UT1] = d1(ql, SW_U); wl[RD_UT2] = d2(ql, SW_U);
+  wr[RD_UN] = dn(qr, SW_U); wr[RD_UT1] = d1(qr, SW_U); wr[RD_UT2] = d2(qr, SW_U);
+  wl[RD_BT1] = d1(ql, SW_B); wl[RD_BT2] = d2(ql, SW_B);
+  wr[RD_BT1] = d1(qr, SW_B); wr[RD_BT2] = d2(qr, SW_B);
   wl[RD_P] = ql[SW_P]; wr[RD_P] = qr[SW_P];
-  wl[RD_GE] = wl[RD_GC] = wr[RD_GE] = wr[RD_GC] = 0.0;
-  if (!(brho + wl[RD_RHO] > 0.0 && brho + wr[RD_RHO] > 0.0 && bp + wl[RD_P] > 0.0 && bp + wr[RD_P] > 0.0))
+  wl[RD_GE] = wl[RD_GC] = wr[RD_GE] = wr[RD_GC] = R(0);
+  if (!(brho + wl[RD_RHO] > R(0) && brho + wr[RD_RHO] > R(0) && bp + wl[RD_P] > R(0) && bp + wr[RD_P] > R(0)))
     atomicOr(D.dflag, FLAG_NEG);
-  GasK<double> K;
-  K.g = D.gamma;
-  K.igm1 = 1.0 / (D.gamma - 1.0);
-  K.ggm1 = D.gamma * K.igm1;
-  double fl[7];
+  GasK<R> K;
+  K.g = (R)D.gamma;
+  K.igm1 = (R)(1.0 / (D.gamma - 1.0));
+  K.ggm1 = (R)(D.gamma / (D.gamma - 1.0));
+  const R A = (R)Ad;
+  const R ph = (R)phi[f];
+  R fl[7];
   int up;
-  riemann_dev<double, 0, true>(wl, wr, phi[f] / A, brho, bp, D.gamma, D.gamma, 0, D.riemann, D.mach, fl, up, K);
+  riemann_dev<R, 0, true>(wl, wr, ph / A, brho, bp, K.g, K.g, 0, D.riemann, (R)D.mach, fl, up, K);
   if (wall) {   // a symmetry plane: only the normal-momentum flux survives
 #pragma unroll
     for (int q = 0; q < 7; ++q)
-      if (q != RF_MN) fl[q] = 0.0;
+      if (q != RF_MN) fl[q] = R(0);
     up = 0;
   }
-  const V3 fm = n * fl[RF_MN] + t1 * fl[RF_MT1] + t2 * fl[RF_MT2];
-  const V3 fb = t1 * fl[RF_BT1] + t2 * fl[RF_BT2];
   const long nf = D.NF;
-  D.FC[f] = A * fl[RF_RHO];
-  D.FC[nf + f] = A * fm.x; D.FC[2 * nf + f] = A * fm.y; D.FC[3 * nf + f] = A * fm.z;
-  D.FC[4 * nf + f] = A * fl[RF_E];
-  const V3 ef = cross3(n, fb) * -1.0;   // E_f = -n x F_B
-  D.EF[f] = ef.x; D.EF[nf + f] = ef.y; D.EF[2 * nf + f] = ef.z;
-  D.UP[f] = (signed char)up;
+  Wk.FC[f] = A * fl[RF_RHO];
+  Wk.FC[nf + f] = A * (n0 * fl[RF_MN] + t1x * fl[RF_MT1] + t2x * fl[RF_MT2]);
+  Wk.FC[2 * nf + f] = A * (n1 * fl[RF_MN] + t1y * fl[RF_MT1] + t2y * fl[RF_MT2]);
+  Wk.FC[3 * nf + f] = A * (n2 * fl[RF_MN] + t1z * fl[RF_MT1] + t2z * fl[RF_MT2]);
+  Wk.FC[4 * nf + f] = A * fl[RF_E];
+  // E_f = -n x F_B with F_B = t1 F_bt1 + t2 F_bt2
+  const R fbx = t1x * fl[RF_BT1] + t2x * fl[RF_BT2], fby = t1y * fl[RF_BT1] + t2y * fl[RF_BT2],
+          fbz = t1z * fl[RF_BT1] + t2z * fl[RF_BT2];
+  Wk.EF[f] = -(n1 * fbz - n2 * fby);
+  Wk.EF[nf + f] = -(n2 * fbx - n0 * fbz);
+  Wk.EF[2 * nf + f] = -(n0 * fby - n1 * fbx);
+  Wk.UP[f] = (signed char)up;
 }
 
-__device__ __forceinline__ double efl(const SphDev &D, long f, V3 l) {
-  return D.EF[f] * l.x + D.EF[D.NF + f] * l.y + D.EF[2 * D.NF + f] * l.z;
+template <typename R>
+__device__ __forceinline__ R efl(const SphDev &D, const SphWork<R> &Wk, long f, R lx, R ly, R lz) {
+  return Wk.EF[f] * lx + Wk.EF[D.NF + f] * ly + Wk.EF[2 * D.NF + f] * lz;
 }
-__device__ __forceinline__ double ecl(const SphDev &D, long c, V3 l) {   // (-u x B) . l of a cell
+template <typename R>
+__device__ __forceinline__ R ecl(const SphDev &D, const SphWork<R> &Wk, long c, R lx, R ly, R lz) {   // (-u x B) . l
   const long n = D.ncell;
-  const V3 u = v3(D.W[SW_U * n + c], D.W[(SW_U + 1) * n + c], D.W[(SW_U + 2) * n + c]);
-  const V3 b = v3(D.W[SW_B * n + c], D.W[(SW_B + 1) * n + c], D.W[(SW_B + 2) * n + c]);
-  return -dot3(cross3(u, b), l);
+  const R ux = Wk.W[SW_U * n + c], uy = Wk.W[(SW_U + 1) * n + c], uz = Wk.W[(SW_U + 2) * n + c];
+  const R bx = Wk.W[SW_B * n + c], by = Wk.W[(SW_B + 1) * n + c], bz = Wk.W[(SW_B + 2) * n + c];
+  return -((uy * bz - uz * by) * lx + (uz * bx - ux * bz) * ly + (ux * by - uy * bx) * lz);
 }
 
 // Contact-CT (Sect. 2.4) on E . l: cells c00, c10, c11, c01 and faces a0
 // (c00|c10), b1 (c10|c11), a1 (c01|c11), b0 (c00|c01); ms: mass-flux signs
-__device__ __forceinline__ double contact_ct(const double *Ec, const double *Ef, const int *ms) {
-  const double E00 = Ec[0], E10 = Ec[1], E11 = Ec[2], E01 = Ec[3];
-  const double Ea0 = Ef[0], Eb1 = Ef[1], Ea1 = Ef[2], Eb0 = Ef[3];
+template <typename R>
+__device__ __forceinline__ R contact_ct(const R *Ec, const R *Ef, const int *ms) {
+  const R E00 = Ec[0], E10 = Ec[1], E11 = Ec[2], E01 = Ec[3];
+  const R Ea0 = Ef[0], Eb1 = Ef[1], Ea1 = Ef[2], Eb0 = Ef[3];
   const int ma0 = ms[0], mb1 = ms[1], ma1 = ms[2], mb0 = ms[3];
-  const double lo_l = Eb0 - E00, lo_r = Eb1 - E10, up_l = E01 - Eb0, up_r = E11 - Eb1;
-  const double dlo = ma0 > 0 ? lo_l : (ma0 < 0 ? lo_r : 0.5 * (lo_l + lo_r));
-  const double dup = ma1 > 0 ? up_l : (ma1 < 0 ? up_r : 0.5 * (up_l + up_r));
-  const double le_d = Ea0 - E00, le_u = Ea1 - E01, ri_d = E10 - Ea0, ri_u = E11 - Ea1;
-  const double dle = mb0 > 0 ? le_d : (mb0 < 0 ? le_u : 0.5 * (le_d + le_u));
-  const double dri = mb1 > 0 ? ri_d : (mb1 < 0 ? ri_u : 0.5 * (ri_d + ri_u));
-  return 0.25 * (Ea1 + Ea0 + Eb1 + Eb0) + 0.25 * (dlo - dup) + 0.25 * (dle - dri);
+  const R h = R(0.5), q = R(0.25);
+  const R lo_l = Eb0 - E00, lo_r = Eb1 - E10, up_l = E01 - Eb0, up_r = E11 - Eb1;
+  const R dlo = ma0 > 0 ? lo_l : (ma0 < 0 ? lo_r : h * (lo_l + lo_r));
+  const R dup = ma1 > 0 ? up_l : (ma1 < 0 ? up_r : h * (up_l + up_r));
+  const R le_d = Ea0 - E00, le_u = Ea1 - E01, ri_d = E10 - Ea0, ri_u = E11 - Ea1;
+  const R dle = mb0 > 0 ? le_d : (mb0 < 0 ? le_u : h * (le_d + le_u));
+  const R dri = mb1 > 0 ? ri_d : (mb1 < 0 ? ri_u : h * (ri_d + ri_u));
+  return q * (Ea1 + Ea0 + Eb1 + Eb0) + q * (dlo - dup) + q * (dle - dri);
 }
 
-__global__ void k_sph_emf(SphDev D) {
+template <typename R>
+__global__ void k_sph_emf(SphDev D, SphWork<R> Wk) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= D.NE) return;
-  double Ec[4], Ef[4];
+  R Ec[4], Ef[4];
   int ms[4];
   if (e < D.ER) {   // radial edge (v, k)
     const int k = (int)(e / D.NV);
     const long v = e - (long)k * D.NV, fb = (long)k * D.NS, cb = (long)k * D.NC;
-    const V3 l = ld3(D.vd, v);
+    const R lx = (R)D.vd[3 * v], ly = (R)D.vd[3 * v + 1], lz = (R)D.vd[3 * v + 2];
     if (D.vcnt[v] == 3) {   // a cube corner: the mean of the three face EMFs
-      double t = 0.0;
-      for (int m = 0; m < 3; ++m) t += efl(D, fb + D.vside[4 * v + m], l);
-      D.EE[e] = t / 3.0;
+      R t = R(0);
+      for (int m = 0; m < 3; ++m) t += efl<R>(D, Wk, fb + D.vside[4 * v + m], lx, ly, lz);
+      Wk.EE[e] = t / R(3);
       return;
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const long f = fb + D.vside[4 * v + m];
-      Ec[m] = ecl(D, cb + D.vcell[4 * v + m], l);
-      Ef[m] = efl(D, f, l);
-      ms[m] = D.vsgn[4 * v + m] * D.UP[f];
+      Ec[m] = ecl<R>(D, Wk, cb + D.vcell[4 * v + m], lx, ly, lz);
+      Ef[m] = efl<R>(D, Wk, f, lx, ly, lz);
+      ms[m] = D.vsgn[4 * v + m] * Wk.UP[f];
     }
   } else {          // angular edge (s, k); none on a wall
     const long q = e - D.ER;
     const int k = (int)(q / D.NS);
     const long s = q - (long)k * D.NS;
-    if (k == 0 || k == D.Nr) { D.EE[e] = 0.0; return; }
-    const V3 l = ld3(D.sl, s);
+    if (k == 0 || k == D.Nr) { Wk.EE[e] = R(0); return; }
+    const R lx = (R)D.sl[3 * s], ly = (R)D.sl[3 * s + 1], lz = (R)D.sl[3 * s + 2];
     const long cL0 = (long)(k - 1) * D.NC + D.sL[s], cR0 = (long)(k - 1) * D.NC + D.sR[s];
     const long cL1 = (long)k * D.NC + D.sL[s], cR1 = (long)k * D.NC + D.sR[s];
     const long A0 = (long)(k - 1) * D.NS + s, A1 = (long)k * D.NS + s;
@@ -589,38 +677,50 @@ __global__ void k_sph_emf(SphDev D) {
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {   // every face's -n cell is its from-cell here
-      Ec[m] = ecl(D, cc[m], l);
-      Ef[m] = efl(D, ff[m], l);
-      ms[m] = D.UP[ff[m]];
+      Ec[m] = ecl<R>(D, Wk, cc[m], lx, ly, lz);
+      Ef[m] = efl<R>(D, Wk, ff[m], lx, ly, lz);
+      ms[m] = Wk.UP[ff[m]];
     }
   }
-  D.EE[e] = contact_ct(Ec, Ef, ms);
+  Wk.EE[e] = contact_ct<R>(Ec, Ef, ms);
 }
 
-// out = a base + b (in - dt R) on the cells, R = (1/V) sum_f s_f F_f - S
-__global__ void k_sph_update_cells(SphDev D, const double *Uin, const double *Ubase, double *Uout, double a,
-                                   double b, const double *__restrict__ dtp) {
+// R = (1/V) sum_f s_f F_f - S of cell (a, k) given its stage-input density
+// deviation and momentum
+template <typename R>
+__device__ __forceinline__ void residual(const SphDev &D, const SphWork<R> &Wk, long an, int k, R drho, R mx, R my,
+                                         R mz, R *r) {
+  CellFaces F;
+  cell_faces(D, an, k, F);
+  const long nf = D.NF;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) r[v] = R(0);
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const R s = (R)F.s[m];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) r[v] += s * Wk.FC[v * nf + F.f[m]];
+  }
+  const R iv = (R)(1.0 / cell_vol(D, an, k));
+#pragma unroll
+  for (int v = 0; v < 5; ++v) r[v] *= iv;
+  const R g = D.g_c ? (R)D.g_c[k] : R(0);
+  const R gx = -g * (R)D.cdc[3 * an], gy = -g * (R)D.cdc[3 * an + 1], gz = -g * (R)D.cdc[3 * an + 2];   // inward
+  r[1] -= drho * gx; r[2] -= drho * gy; r[3] -= drho * gz;
+  R se = mx * gx + my * gy + mz * gz;
+  if (D.heat) se += (R)D.heat[k];
+  r[4] -= se;
+}
+
+// FP64: out = a base + b (in - dt R)
+__global__ void k_sph_update_cells(SphDev D, SphWork<double> Wk, const double *Uin, const double *Ubase, double *Uout,
+                                   double a, double b, const double *__restrict__ dtp) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= D.ncell) return;
   const int k = (int)(c / D.NC);
-  const long an = c - (long)k * D.NC, nf = D.NF, nc = D.ncell;
-  CellFaces F;
-  cell_faces(D, an, k, F);
-  double r[5] = {0, 0, 0, 0, 0};
-#pragma unroll
-  for (int m = 0; m < 6; ++m)
-#pragma unroll
-    for (int v = 0; v < 5; ++v) r[v] += F.s[m] * D.FC[v * nf + F.f[m]];
-  const double iv = 1.0 / cell_vol(D, an, k);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) r[v] *= iv;
-  const double g = D.g_c ? D.g_c[k] : 0.0;
-  const V3 gv = ld3(D.cdc, an) * -g;   // radial, inward
-  const double rho = Uin[c], drho = rho - bg_rho(D, k);
-  r[1] -= drho * gv.x; r[2] -= drho * gv.y; r[3] -= drho * gv.z;
-  double se = Uin[nc + c] * gv.x + Uin[2 * nc + c] * gv.y + Uin[3 * nc + c] * gv.z;
-  if (D.heat) se += D.heat[k];
-  r[4] -= se;
+  const long an = c - (long)k * D.NC, nc = D.ncell;
+  double r[5];
+  residual<double>(D, Wk, an, k, Uin[c] - bg_rho<double>(D, k), Uin[nc + c], Uin[2 * nc + c], Uin[3 * nc + c], r);
   const double dt = *dtp;
   double o[5];
 #pragma unroll
@@ -629,62 +729,100 @@ __global__ void k_sph_update_cells(SphDev D, const double *Uin, const double *Ub
   for (int v = 0; v < 5; ++v) Uout[v * nc + c] = o[v];
 }
 
-// out = a base + b (in - dt sum_e sigma l E) on the faces (Eq. induction)
-__global__ void k_sph_update_faces(SphDev D, const double *pin, const double *pbase, double *pout, double a,
-                                   double b, const double *__restrict__ dtp) {
-  const long f = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (f >= D.NF) return;
-  double t;
+// Mixed: dU_out = b (dU_in - dt R) (dU_in null at the first stage); the last
+// stage writes U^n + dU_out into U in FP64
+__global__ void k_sph_update_cells_mx(SphDev D, SphWork<float> Wk, double *U, const float *dUin, float *dUout, float b,
+                                      const double *__restrict__ dtp, int last) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (c >= D.ncell) return;
+  const int k = (int)(c / D.NC);
+  const long an = c - (long)k * D.NC, nc = D.ncell;
+  float du[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) du[v] = dUin ? dUin[v * nc + c] : 0.f;
+  const double rh = D.rho_c ? D.rho_c[k] : 0.0;
+  const float drho = (float)(U[c] - rh) + du[0];
+  const float mx = (float)U[nc + c] + du[1], my = (float)U[2 * nc + c] + du[2], mz = (float)U[3 * nc + c] + du[3];
+  float r[5];
+  residual<float>(D, Wk, an, k, drho, mx, my, mz, r);
+  const float dt = (float)*dtp;
+  float o[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) o[v] = b * (du[v] - dt * r[v]);
+  if (last) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v * nc + c] += (double)o[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dUout[v * nc + c] = o[v];
+  }
+}
+
+// the circulation sum_e sigma l (E . l) about face f (Eq. induction), in
+// FP64 from the edge EMFs of either form: each edge's term is the same FP64
+// product (sign) r theta E or (sign) dr E in every face that has the edge
+template <typename R>
+__device__ __forceinline__ double circulation(const SphDev &D, const R *__restrict__ EE, long f) {
   if (f < D.FA) {   // angular face (s, k): edges (s, k), (v1, k), (s, k+1), (v0, k)
     const int k = (int)(f / D.NS);
     const long s = f - (long)k * D.NS;
-    const double dr = D.r[k + 1] - D.r[k], th = D.sth[s];
-    const double si = D.s_in[s];
-    t = si * D.r[k] * th * D.EE[D.ER + (long)k * D.NS + s];
-    t += D.s_v1[s] * dr * D.EE[(long)k * D.NV + D.sv1[s]];
-    t += -si * D.r[k + 1] * th * D.EE[D.ER + (long)(k + 1) * D.NS + s];
-    t += D.s_v0[s] * dr * D.EE[(long)k * D.NV + D.sv0[s]];
-  } else {          // radial face (a, k): the angular edges (s_m, k)
-    const long q = f - D.FA;
-    const int k = (int)(q / D.NC);
-    const long an = q - (long)k * D.NC;
-    t = 0.0;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int s = D.cs[4 * an + m];
-      t += D.crs[4 * an + m] * D.r[k] * D.sth[s] * D.EE[D.ER + (long)k * D.NS + s];
-    }
+    const double dr = D.r[k + 1] - D.r[k], th = D.sth[s], si = D.s_in[s];
+    double t = si * D.r[k] * th * (double)EE[D.ER + (long)k * D.NS + s];
+    t += D.s_v1[s] * dr * (double)EE[(long)k * D.NV + D.sv1[s]];
+    t += -si * D.r[k + 1] * th * (double)EE[D.ER + (long)(k + 1) * D.NS + s];
+    t += D.s_v0[s] * dr * (double)EE[(long)k * D.NV + D.sv0[s]];
+    return t;
   }
+  const long q = f - D.FA;   // radial face (a, k): the angular edges (s_m, k)
+  const int k = (int)(q / D.NC);
+  const long an = q - (long)k * D.NC;
+  double t = 0.0;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int s = D.cs[4 * an + m];
+    t += D.crs[4 * an + m] * D.r[k] * D.sth[s] * (double)EE[D.ER + (long)k * D.NS + s];
+  }
+  return t;
+}
+
+// out = a base + b (in - dt circulation), FP64 in both forms
+template <typename R>
+__global__ void k_sph_update_faces(SphDev D, const R *__restrict__ EE, const double *pin, const double *pbase,
+                                   double *pout, double a, double b, const double *__restrict__ dtp) {
+  const long f = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (f >= D.NF) return;
+  const double t = circulation<R>(D, EE, f);
   const double o = a * pbase[f] + b * (pin[f] - *dtp * t);
   pout[f] = o;
 }
 
-__global__ void k_sph_dt(SphDev D, unsigned long long *dmax) {
+template <typename R>
+__global__ void k_sph_dt(SphDev D, SphWork<R> Wk, unsigned long long *dmax) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   double m = 0.0;
   if (c < D.ncell) {
     const long n = D.ncell;
     const int k = (int)(c / D.NC);
     const long a = c - (long)k * D.NC;
-    const double rho = D.W[SW_RHO * n + c] + bg_rho(D, k);
-    const double P = D.W[SW_P * n + c] + bg_p(D, k);
-    const V3 u = v3(D.W[SW_U * n + c], D.W[(SW_U + 1) * n + c], D.W[(SW_U + 2) * n + c]);
-    const V3 b = v3(D.W[SW_B * n + c], D.W[(SW_B + 1) * n + c], D.W[(SW_B + 2) * n + c]);
-    const double a2 = D.gamma * P / rho, b2 = dot3(b, b) / rho;
+    const R rho = Wk.W[SW_RHO * n + c] + bg_rho<R>(D, k);
+    const R P = Wk.W[SW_P * n + c] + bg_p<R>(D, k);
+    const R ux = Wk.W[SW_U * n + c], uy = Wk.W[(SW_U + 1) * n + c], uz = Wk.W[(SW_U + 2) * n + c];
+    const R bx = Wk.W[SW_B * n + c], by = Wk.W[(SW_B + 1) * n + c], bz = Wk.W[(SW_B + 2) * n + c];
+    const R a2 = (R)D.gamma * P / rho, b2 = (bx * bx + by * by + bz * bz) / rho;
     CellFaces F;
     cell_faces(D, a, k, F);
-    double sum = 0.0;
+    R sum = R(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {   // the cell's three mesh directions
       const V3 span = F.x[2 * d + 1] - F.x[2 * d];
-      const double width = len3(span);
-      const V3 ed = span * (1.0 / width);
-      const double bd = dot3(b, ed);
-      double disc = (a2 + b2) * (a2 + b2) - 4.0 * a2 * bd * bd / rho;
-      if (disc < 0.0) disc = 0.0;
-      sum += (fabs(dot3(u, ed)) + sqrt(0.5 * (a2 + b2 + sqrt(disc)))) / width;
+      const double wd = len3(span);
+      const R ex = (R)(span.x / wd), ey = (R)(span.y / wd), ez = (R)(span.z / wd);
+      const R bd = bx * ex + by * ey + bz * ez;
+      R disc = (a2 + b2) * (a2 + b2) - R(4) * a2 * bd * bd / rho;
+      if (disc < R(0)) disc = R(0);
+      sum += (fabs(ux * ex + uy * ey + uz * ez) + sqrt(R(0.5) * (a2 + b2 + sqrt(disc)))) / (R)wd;
     }
-    m = (sum == sum) ? sum : INFINITY;
+    m = (sum == sum) ? (double)sum : INFINITY;
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   __shared__ double red[SPT / 32];
@@ -773,11 +911,15 @@ inline unsigned nblk(long n) { return (unsigned)((n + SPT - 1) / SPT); }
 struct phl_sphere {
   phl_sphere_desc desc;
   SphDev D;
+  SphWork<double> W64{};
+  SphWork<float> W32{};
+  bool mixed = false;
   AbiMap AM;
   Prof prof;
   cudaStream_t s = nullptr;
   std::vector<void *> allocs;
   double *U = nullptr, *U1 = nullptr, *phi = nullptr, *phi1 = nullptr, *dt = nullptr, *abi_buf = nullptr;
+  float *dU = nullptr;   // mixed: the cells' stage increments
   unsigned long long *dmax = nullptr;
   long nabi = 0;
   long steps = 0;
@@ -809,6 +951,16 @@ cudaError_t up_arr(phl_sphere *S, const double **dst, const double *src, long n)
   if (!src) { *dst = nullptr; return cudaSuccess; }
   return up_vec(S, dst, std::vector<double>(src, src + n));
 }
+template <typename R>
+cudaError_t alloc_work(phl_sphere *S, SphWork<R> &Wk) {
+  const SphDev &D = S->D;
+  cudaError_t e = alloc_n(S, &Wk.W, SW_N * D.ncell);
+  if (e == cudaSuccess) e = alloc_n(S, &Wk.FC, 5 * D.NF);
+  if (e == cudaSuccess) e = alloc_n(S, &Wk.EF, 3 * D.NF);
+  if (e == cudaSuccess) e = alloc_n(S, &Wk.EE, D.NE);
+  if (e == cudaSuccess) e = alloc_n(S, &Wk.UP, D.NF);
+  return e;
+}
 
 phl_status sph_flags(phl_sphere *S) {
   int f = 0;
@@ -828,11 +980,24 @@ void timed(phl_sphere *S, int cls, F &&launch) {
   S->prof.end(S->s);
 }
 
-void sph_dt(phl_sphere *S, const double *U, const double *phi) {
+// primitives of the stage input (mixed: U^n + dU when inc)
+void sph_prims(phl_sphere *S, const double *U, const double *phi, bool inc) {
   const SphDev &D = S->D;
-  timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, U, phi); });
+  if (S->mixed)
+    timed(S, KC_SPH_PRIM, [&] {
+      k_sph_prims_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->U, inc ? S->dU : nullptr, phi);
+    });
+  else
+    timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, U, phi); });
+}
+
+// the CFL step of U^n (Eq. cfl) into S->dt; leaves the primitives of U^n in W
+void sph_dt(phl_sphere *S) {
+  const SphDev &D = S->D;
+  sph_prims(S, S->U, S->phi, false);
   timed(S, KC_SPH_DT, [&] {
-    k_sph_dt<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->dmax);
+    if (S->mixed) k_sph_dt<float><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->dmax);
+    else k_sph_dt<double><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, S->dmax);
     k_sph_dt_fin<<<1, 1, 0, S->s>>>(D.cfl, S->dmax, S->dt);
   });
 }
@@ -850,6 +1015,8 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
                                  "phl_sphere_create: need N, Nr >= 2, 0 < r_in < r_out, gamma > 1, cfl > 0, mach_thr > 0");
   if (d->riemann < PHL_LHLLD || d->riemann > PHL_HLL)
     return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: bad solver");
+  if (d->precision != PHL_FP64 && d->precision != PHL_MIXED)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: bad precision");
   const bool any = d->rho_c || d->p_c || d->rho_f || d->p_f, all = d->rho_c && d->p_c && d->rho_f && d->p_f;
   if (any && !all) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: the background needs all four profiles");
   // face and edge indices must fit int32 per shell and long overall
@@ -860,6 +1027,7 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
   phl_sphere *S = new phl_sphere();
   S->desc = *d;
   S->s = (cudaStream_t)d->stream;
+  S->mixed = d->precision == PHL_MIXED;
   Ang M;
   try {
     build_ang(d->N, M);
@@ -893,16 +1061,15 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
   if (e == cudaSuccess) e = up_arr(S, &D.p_f, d->p_f, d->Nr + 1);
   if (e == cudaSuccess) e = up_arr(S, &D.g_c, d->g_c, d->Nr);
   if (e == cudaSuccess) e = up_arr(S, &D.heat, d->heat, d->Nr);
-  if (e == cudaSuccess) e = alloc_n(S, &D.W, SW_N * D.ncell);
-  if (e == cudaSuccess) e = alloc_n(S, &D.FC, 5 * D.NF);
-  if (e == cudaSuccess) e = alloc_n(S, &D.EF, 3 * D.NF);
-  if (e == cudaSuccess) e = alloc_n(S, &D.UP, D.NF);
-  if (e == cudaSuccess) e = alloc_n(S, &D.EE, D.NE);
   if (e == cudaSuccess) e = alloc_n(S, &D.dflag, 1);
+  if (e == cudaSuccess) e = S->mixed ? alloc_work(S, S->W32) : alloc_work(S, S->W64);
   if (e == cudaSuccess) e = alloc_n(S, &S->U, 5 * D.ncell);
-  if (e == cudaSuccess) e = alloc_n(S, &S->U1, 5 * D.ncell);
   if (e == cudaSuccess) e = alloc_n(S, &S->phi, D.NF);
   if (e == cudaSuccess) e = alloc_n(S, &S->phi1, D.NF);
+  if (e == cudaSuccess) {
+    if (S->mixed) e = alloc_n(S, &S->dU, 5 * D.ncell);
+    else e = alloc_n(S, &S->U1, 5 * D.ncell);
+  }
   if (e == cudaSuccess) e = alloc_n(S, &S->dt, 1);
   if (e == cudaSuccess) e = alloc_n(S, &S->dmax, 1);
   S->nabi = 2L * 6 * d->Nr * d->N * (d->N + 1) + 6L * (d->Nr + 1) * d->N * d->N;
@@ -1007,7 +1174,7 @@ phl_status phl_sphere_get_state(phl_sphere *S, double *cons, double *pa, double 
 
 phl_status phl_sphere_compute_dt(phl_sphere *S, double *dt_out) {
   if (!S || !dt_out) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_compute_dt: null argument");
-  sph_dt(S, S->U, S->phi);
+  sph_dt(S);
   cudaError_t e = cudaMemcpyAsync(dt_out, S->dt, sizeof(double), cudaMemcpyDeviceToHost, S->s);
   if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_compute_dt: %s", cudaGetErrorString(e));
   return sph_flags(S);
@@ -1019,21 +1186,43 @@ phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
   const SphDev &D = S->D;
   for (int n = 0; n < nsteps; ++n) {
     if (dt > 0.0) timed(S, KC_SCALAR, [&] { k_sph_set<<<1, 1, 0, S->s>>>(dt, S->dt); });
-    else sph_dt(S, S->U, S->phi);   // the CFL step of U^n (Eq. cfl); leaves W of U^n
-    // Shu-Osher SSP-RK3 (Sect. 2.9); stage input U1 (U^n at the first stage)
+    else sph_dt(S);   // leaves the primitives of U^n for the first stage
+    // Shu-Osher SSP-RK3 (Sect. 2.9)
     for (int st = 0; st < 3; ++st) {
-      const double *Uin = st == 0 ? S->U : S->U1, *pin = st == 0 ? S->phi : S->phi1;
-      double *Uout = st == 2 ? S->U : S->U1, *pout = st == 2 ? S->phi : S->phi1;
+      const bool last = st == 2;
+      // faces (both forms): stage input phi1 (Phi^n at the first stage),
+      // out = a Phi^n + b (in - dt circulation); each thread reads its own
+      // element of in and base before writing out
+      const double *pin = st == 0 ? S->phi : S->phi1;
+      double *pout = last ? S->phi : S->phi1;
       const double a = A3[st], b = B3[st];
-      if (st > 0 || dt > 0.0)
-        timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, Uin, pin); });
-      timed(S, KC_SPH_FLUX, [&] { k_sph_flux<<<nblk(D.NF), SPT, 0, S->s>>>(D, pin); });
-      timed(S, KC_SPH_EMF, [&] { k_sph_emf<<<nblk(D.NE), SPT, 0, S->s>>>(D); });
-      // each thread reads its own element of in and base before writing out
-      timed(S, KC_SPH_UPDATE_FACES,
-            [&] { k_sph_update_faces<<<nblk(D.NF), SPT, 0, S->s>>>(D, pin, S->phi, pout, a, b, S->dt); });
-      timed(S, KC_SPH_UPDATE_CELLS,
-            [&] { k_sph_update_cells<<<nblk(D.ncell), SPT, 0, S->s>>>(D, Uin, S->U, Uout, a, b, S->dt); });
+      if (S->mixed) {
+        // cells: stage input U^n + dU; increments out dU = b (dU - dt R)
+        const float *dUin = st == 0 ? nullptr : S->dU;
+        if (st > 0 || dt > 0.0) sph_prims(S, S->U, pin, st > 0);
+        timed(S, KC_SPH_FLUX, [&] { k_sph_flux<float><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin); });
+        timed(S, KC_SPH_EMF, [&] { k_sph_emf<float><<<nblk(D.NE), SPT, 0, S->s>>>(D, S->W32); });
+        timed(S, KC_SPH_UPDATE_FACES, [&] {
+          k_sph_update_faces<float><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32.EE, pin, S->phi, pout, a, b, S->dt);
+        });
+        timed(S, KC_SPH_UPDATE_CELLS, [&] {
+          k_sph_update_cells_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->U, dUin, S->dU, (float)b, S->dt,
+                                                                 last);
+        });
+      } else {
+        // cells: stage input U1 (U^n at the first stage): out = a U^n + b (in - dt R)
+        const double *Uin = st == 0 ? S->U : S->U1;
+        double *Uout = last ? S->U : S->U1;
+        if (st > 0 || dt > 0.0) sph_prims(S, Uin, pin, false);
+        timed(S, KC_SPH_FLUX, [&] { k_sph_flux<double><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64, pin); });
+        timed(S, KC_SPH_EMF, [&] { k_sph_emf<double><<<nblk(D.NE), SPT, 0, S->s>>>(D, S->W64); });
+        timed(S, KC_SPH_UPDATE_FACES, [&] {
+          k_sph_update_faces<double><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64.EE, pin, S->phi, pout, a, b, S->dt);
+        });
+        timed(S, KC_SPH_UPDATE_CELLS, [&] {
+          k_sph_update_cells<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, Uin, S->U, Uout, a, b, S->dt);
+        });
+      }
     }
     ++S->steps;
   }

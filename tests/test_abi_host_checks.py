@@ -199,6 +199,7 @@ SPHERE_CASES = [
     ("zero cfl", set_field("cfl", 0.0), "cfl > 0"),
     ("zero Mach threshold", set_field("mach_thr", 0.0), "mach_thr > 0"),
     ("unknown solver", set_field("riemann", 5), "bad solver"),
+    ("unknown precision", set_field("precision", 7), "bad precision"),
     ("partial background", set_field("p_f", None), "all four profiles"),
     ("too many faces", lambda d: (setattr(d, "N", 8000), setattr(d, "Nr", 8000)), "2^31"),
 ]
