@@ -703,9 +703,13 @@ def ensemble_c4(P, steps, warmup, stream, ws):
 # per face in the same capture (517.4 MB; the work arrays exceed L2 there).
 SPH_FP64_FLOP_PER_FACE = 988.9
 SPH_FLUX_DRAM_BYTES_PER_FACE = 109.1
-# the mixed form's flux kernel: FP32 operations per face (FADD + FMUL + 2 FFMA,
-# same capture recipe); None until measured
-SPH_FP32_FLOP_PER_FACE = None
+# the mixed form's flux kernel: FP32 operations per face, FADD + FMUL + 2 FFMA
+# of the scalar solver on the same shell (2533.6 M over 4.743 M faces; the
+# packed-lane solver the kernel runs does the same arithmetic, partly as
+# f32x2 instructions those counters leave out), and its DRAM bytes per face
+# (241.0 MB in the capture of the packed-lane kernel)
+SPH_FP32_FLOP_PER_FACE = 534.2
+SPH_MX_FLUX_DRAM_BYTES_PER_FACE = 50.8
 
 
 def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, Nr=384, precision="fp64"):
@@ -774,11 +778,12 @@ def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, N
         gbs = b / (avg * 1e-3) / 1e9
         roof["hbm"] = {"bytes_per_launch": b, "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                        "frac": gbs / hbm_peak, "peak_kind": f"{peak_kind} HBM copy"}
-        if SPH_FP32_FLOP_PER_FACE:
-            tf = faces * SPH_FP32_FLOP_PER_FACE / (avg * 1e-3) / 1e12
-            roof.update({"bound": "alu", "achieved": tf, "peak": alu["fp32"], "unit": "TFLOP/s",
-                         "frac": tf / alu["fp32"], "flop_per_face": SPH_FP32_FLOP_PER_FACE,
-                         "peak_kind": "measured FP32 FFMA rate (phl_probe_alu)"})
+        tf = faces * SPH_FP32_FLOP_PER_FACE / (avg * 1e-3) / 1e12
+        roof.update({"bound": "alu", "achieved": tf, "peak": alu["fp32"], "unit": "TFLOP/s",
+                     "frac": tf / alu["fp32"], "flop_per_face": SPH_FP32_FLOP_PER_FACE,
+                     "traffic": faces * SPH_MX_FLUX_DRAM_BYTES_PER_FACE,
+                     "traffic_note": "ncu DRAM bytes per face on the 6 x 64^3 shell x faces",
+                     "peak_kind": "measured FP32 FFMA rate (phl_probe_alu)"})
     out["roofline"] = roof
     return out
 

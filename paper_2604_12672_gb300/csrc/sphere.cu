@@ -47,6 +47,7 @@
 #include "phl.h"
 #include "phl_internal.cuh"
 #include "riemann.cuh"
+#include "riemann_x2.cuh"
 
 using namespace phl;
 
@@ -339,12 +340,14 @@ void build_ang(int N, Ang &M) {
 // carries the cells' increments dU = U^(s) - U^n in FP32 (SSP-RK3 has
 // a + b = 1 in every stage, so dU^(s) = b (dU^(s-1) - dt R)); primitives are
 // formed as FP32 deviations from the background out of an FP64 difference
-// U^n - U_hat plus the FP32 increment; fluxes, EMFs and residuals are FP32;
-// the last stage adds the increment to U^n in FP64.  The face fluxes keep
-// FP64 stage values, advanced by circulations summed in FP64 from the FP32
-// edge EMFs: every edge's term enters its faces as the same FP64 product, so
-// the divergence of each cell stays at FP64 rounding (Eq. divb), as in the
-// FP64 form.
+// U^n - U_hat plus the FP32 increment; fluxes, EMFs and residuals are FP32 on
+// FP32 copies of the geometry; the last stage adds the increment to U^n in
+// FP64.  The face fluxes keep FP64 stage values, advanced by circulations
+// summed in FP64 from the edge EMFs: every edge's term enters its faces as
+// the same FP64 product, so the divergence of each cell stays at FP64
+// rounding (Eq. divb), as in the FP64 form; an FP32 copy of the stage's face
+// fluxes feeds the FP32 kernels.  GB300 runs FP64 at 1/64 of its FP32 rate,
+// so the mixed kernels keep FP64 instructions to the few that the form needs.
 
 enum { SW_RHO = 0, SW_U = 1, SW_B = 4, SW_P = 7, SW_N = 8 };
 
@@ -359,6 +362,14 @@ struct SphDev {
   const signed char *s_in, *s_v0, *s_v1, *s_swap, *csg, *crs, *vsgn;
   const unsigned char *vcnt;
   const double *rho_c, *p_c, *rho_f, *p_f, *g_c, *heat;   // null when absent
+  const double *eh_c;          // P_hat / (gamma - 1) per shell (null without a background)
+  // FP32 copies for the mixed form: geometry, per-radius factors, background
+  const float *vd_f, *sn_f, *sl_f, *smid_f, *sth_f, *cdc_f, *cna_f, *cva_f;
+  const float *iom_f;          // 1 / Omega per angular cell
+  const float *cw_f, *ce_f;    // per angular cell: unit-radius widths (a, b) and their unit directions
+  const float *r_f, *rm_f, *hdr2_f, *ish_f, *dr_f;   // r_k, shell middle, (r1^2 - r0^2) / 2, 3 / (r1^3 - r0^3), r1 - r0
+  const float *rho_cf, *p_cf, *rho_ff, *p_ff, *g_cf, *heat_f;
+  float gf, igm1f, ggm1f, gm1f, machf;
   int *dflag;
 };
 
@@ -367,14 +378,12 @@ template <typename R>
 struct SphWork {
   R *W;             // 8 deviations per cell, SoA
   R *FC, *EF;       // 5 integrated fluxes, 3 face-EMF components per face, SoA
-  R *EE;            // edge EMFs (E . l)
+  double *EE;       // edge EMF line integrals L (E . l), FP64 in both forms
   signed char *UP;  // contact direction per face
 };
 
-template <typename R>
-__device__ __forceinline__ R bg_rho(const SphDev &D, int k) { return D.rho_c ? (R)D.rho_c[k] : R(0); }
-template <typename R>
-__device__ __forceinline__ R bg_p(const SphDev &D, int k) { return D.p_c ? (R)D.p_c[k] : R(0); }
+__device__ __forceinline__ double bg_rho(const SphDev &D, int k) { return D.rho_c ? D.rho_c[k] : 0.0; }
+__device__ __forceinline__ double bg_p(const SphDev &D, int k) { return D.p_c ? D.p_c[k] : 0.0; }
 
 // The six faces of cell (a, k) in the order -a, +a, -b, +b, -r, +r: index,
 // outward sign, centre.
@@ -406,15 +415,6 @@ __device__ __forceinline__ double cell_vol(const SphDev &D, long a, int k) {
   return (r1 * r1 * r1 - r0 * r0 * r0) / 3.0 * D.com[a];
 }
 
-template <typename R>
-__device__ __forceinline__ void store_w(const SphDev &D, const SphWork<R> &Wk, long c, R drho, V3 u, V3 B, R dP) {
-  const long n = D.ncell;
-  Wk.W[SW_RHO * n + c] = drho;
-  Wk.W[(SW_U + 0) * n + c] = (R)u.x; Wk.W[(SW_U + 1) * n + c] = (R)u.y; Wk.W[(SW_U + 2) * n + c] = (R)u.z;
-  Wk.W[(SW_B + 0) * n + c] = (R)B.x; Wk.W[(SW_B + 1) * n + c] = (R)B.y; Wk.W[(SW_B + 2) * n + c] = (R)B.z;
-  Wk.W[SW_P * n + c] = dP;
-}
-
 __global__ void k_sph_prims(SphDev D, SphWork<double> Wk, const double *__restrict__ U, const double *__restrict__ phi) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= D.ncell) return;
@@ -432,48 +432,97 @@ __global__ void k_sph_prims(SphDev D, SphWork<double> Wk, const double *__restri
   const double P = (D.gamma - 1.0) * (U[4 * n + c] - 0.5 * rho * dot3(u, u) - 0.5 * dot3(B, B));
   if (!(rho > 0.0) || !(P > 0.0)) atomicOr(D.dflag, FLAG_NEG);
   if (!isfinite(rho) || !isfinite(P)) atomicOr(D.dflag, FLAG_NAN);
-  store_w<double>(D, Wk, c, rho - bg_rho<double>(D, k), u, B, P - bg_p<double>(D, k));
+  Wk.W[SW_RHO * n + c] = rho - bg_rho(D, k);
+  Wk.W[(SW_U + 0) * n + c] = u.x; Wk.W[(SW_U + 1) * n + c] = u.y; Wk.W[(SW_U + 2) * n + c] = u.z;
+  Wk.W[(SW_B + 0) * n + c] = B.x; Wk.W[(SW_B + 1) * n + c] = B.y; Wk.W[(SW_B + 2) * n + c] = B.z;
+  Wk.W[SW_P * n + c] = P - bg_p(D, k);
 }
 
-// Mixed form: the stage input is U^n + dU (dU null at the first stage) and
-// the stage's face fluxes.  The density and energy deviations start from the
-// FP64 differences rho^n - rho_hat and E^n - P_hat / (gamma - 1); the rest is
-// FP32.
-__global__ void k_sph_prims_mx(SphDev D, SphWork<float> Wk, const double *__restrict__ U, const float *__restrict__ dU,
-                               const double *__restrict__ phi) {
-  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (c >= D.ncell) return;
-  const int k = (int)(c / D.NC);
-  const long a = c - (long)k * D.NC, n = D.ncell;
-  CellFaces F;
-  cell_faces(D, a, k, F);
-  float bx = 0.f, by = 0.f, bz = 0.f;
+// the CFL rate (Eq. cfl) sum_d (|u . e_d| + c_f(e_d)) / width_d of one cell,
+// FP32 on the mixed form's tables
+__device__ __forceinline__ float cfl_rate_mx(const SphDev &D, long a, int k, float rho, float P, float ux, float uy,
+                                             float uz, float bx, float by, float bz) {
+  const float a2 = D.gf * P / rho, b2 = (bx * bx + by * by + bz * bz) / rho;
+  const float rm = D.rm_f[k];
+  float sum = 0.f;
 #pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    const float w = (float)(F.s[m] * phi[F.f[m]]);
-    bx += (float)F.x[m].x * w; by += (float)F.x[m].y * w; bz += (float)F.x[m].z * w;
+  for (int d = 0; d < 3; ++d) {
+    float ex, ey, ez, w;
+    if (d < 2) {
+      ex = D.ce_f[6 * a + 3 * d]; ey = D.ce_f[6 * a + 3 * d + 1]; ez = D.ce_f[6 * a + 3 * d + 2];
+      w = rm * D.cw_f[2 * a + d];
+    } else {
+      ex = D.cdc_f[3 * a]; ey = D.cdc_f[3 * a + 1]; ez = D.cdc_f[3 * a + 2];
+      w = D.dr_f[k];
+    }
+    const float bd = bx * ex + by * ey + bz * ez;
+    float disc = (a2 + b2) * (a2 + b2) - 4.f * a2 * bd * bd / rho;
+    disc = fmaxf(disc, 0.f);
+    sum += (fabsf(ux * ex + uy * ey + uz * ez) + sqrtf(0.5f * (a2 + b2 + sqrtf(disc)))) / w;
   }
-  const float iv = (float)(1.0 / cell_vol(D, a, k));
-  bx *= iv; by *= iv; bz *= iv;
-  const double rh = D.rho_c ? D.rho_c[k] : 0.0, eh = D.p_c ? D.p_c[k] / (D.gamma - 1.0) : 0.0;
-  float drho = (float)(U[c] - rh), dE = (float)(U[4 * n + c] - eh);
-  float mx = (float)U[n + c], my = (float)U[2 * n + c], mz = (float)U[3 * n + c];
-  if (dU) {
-    drho += dU[c]; dE += dU[4 * n + c];
-    mx += dU[n + c]; my += dU[2 * n + c]; mz += dU[3 * n + c];
+  return sum;
+}
+
+// Mixed form: primitives of U^n + dU (dU null at the first stage) and the
+// stage's face fluxes (FP32 copy).  The density and energy deviations start
+// from the FP64 differences rho^n - rho_hat and E^n - P_hat / (gamma - 1);
+// the rest is FP32.  With dmax, the CFL rate of every cell is folded into
+// dmax (the bits of a non-negative double).
+__global__ void __launch_bounds__(SPT) k_sph_prims_mx(SphDev D, SphWork<float> Wk, const double *__restrict__ U,
+                                                      const float *__restrict__ dU, const float *__restrict__ phif,
+                                                      unsigned long long *dmax) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  float rate = 0.f;
+  if (c < D.ncell) {
+    const int k = (int)(c / D.NC);
+    const long a = c - (long)k * D.NC, n = D.ncell;
+    const float rm = D.rm_f[k];
+    float bx = 0.f, by = 0.f, bz = 0.f;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int s = D.cs[4 * a + m];
+      const float w = (D.csg[4 * a + m] > 0 ? rm : -rm) * phif[(long)k * D.NS + s];
+      bx += D.smid_f[3 * s] * w; by += D.smid_f[3 * s + 1] * w; bz += D.smid_f[3 * s + 2] * w;
+    }
+    const float wr = D.r_f[k + 1] * phif[D.FA + (long)(k + 1) * D.NC + a] - D.r_f[k] * phif[D.FA + (long)k * D.NC + a];
+    bx += D.cdc_f[3 * a] * wr; by += D.cdc_f[3 * a + 1] * wr; bz += D.cdc_f[3 * a + 2] * wr;
+    const float iv = D.iom_f[a] * D.ish_f[k];
+    bx *= iv; by *= iv; bz *= iv;
+    float drho = (float)(D.rho_c ? U[c] - D.rho_c[k] : U[c]);
+    float dE = (float)(D.eh_c ? U[4 * n + c] - D.eh_c[k] : U[4 * n + c]);
+    float mx = (float)U[n + c], my = (float)U[2 * n + c], mz = (float)U[3 * n + c];
+    if (dU) {
+      drho += dU[c]; dE += dU[4 * n + c];
+      mx += dU[n + c]; my += dU[2 * n + c]; mz += dU[3 * n + c];
+    }
+    const float rhb = D.rho_cf ? D.rho_cf[k] : 0.f, pb = D.p_cf ? D.p_cf[k] : 0.f;
+    const float rho = rhb + drho, ir = 1.0f / rho;
+    const float ux = mx * ir, uy = my * ir, uz = mz * ir;
+    // P - P_hat = (gamma - 1) (E - E_hat - rho u^2 / 2 - B^2 / 2)
+    const float dP = D.gm1f * (dE - 0.5f * (mx * ux + my * uy + mz * uz) - 0.5f * (bx * bx + by * by + bz * bz));
+    const float P = pb + dP;
+    if (!(rho > 0.f) || !(P > 0.f)) atomicOr(D.dflag, FLAG_NEG);
+    if (!isfinite(rho) || !isfinite(P)) atomicOr(D.dflag, FLAG_NAN);
+    Wk.W[SW_RHO * n + c] = drho;
+    Wk.W[(SW_U + 0) * n + c] = ux; Wk.W[(SW_U + 1) * n + c] = uy; Wk.W[(SW_U + 2) * n + c] = uz;
+    Wk.W[(SW_B + 0) * n + c] = bx; Wk.W[(SW_B + 1) * n + c] = by; Wk.W[(SW_B + 2) * n + c] = bz;
+    Wk.W[SW_P * n + c] = dP;
+    if (dmax) {
+      rate = cfl_rate_mx(D, a, k, rho, P, ux, uy, uz, bx, by, bz);
+      if (!(rate == rate)) rate = INFINITY;
+    }
   }
-  const float rho = (float)rh + drho, ir = 1.0f / rho;
-  const float ux = mx * ir, uy = my * ir, uz = mz * ir;
-  const float gm1 = (float)(D.gamma - 1.0);
-  // P - P_hat = (gamma - 1) (E - E_hat - rho u^2 / 2 - B^2 / 2)
-  const float dP = gm1 * (dE - 0.5f * (mx * ux + my * uy + mz * uz) - 0.5f * (bx * bx + by * by + bz * bz));
-  const float P = (float)(D.p_c ? D.p_c[k] : 0.0) + dP;
-  if (!(rho > 0.f) || !(P > 0.f)) atomicOr(D.dflag, FLAG_NEG);
-  if (!isfinite(rho) || !isfinite(P)) atomicOr(D.dflag, FLAG_NAN);
-  Wk.W[SW_RHO * n + c] = drho;
-  Wk.W[(SW_U + 0) * n + c] = ux; Wk.W[(SW_U + 1) * n + c] = uy; Wk.W[(SW_U + 2) * n + c] = uz;
-  Wk.W[(SW_B + 0) * n + c] = bx; Wk.W[(SW_B + 1) * n + c] = by; Wk.W[(SW_B + 2) * n + c] = bz;
-  Wk.W[SW_P * n + c] = dP;
+  if (dmax) {   // block maximum; non-negative floats order like their bits
+    for (int o = 16; o > 0; o >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+    __shared__ float red[SPT / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rate;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float v = 0.f;
+      for (int w = 0; w < SPT / 32; ++w) v = fmaxf(v, red[w]);
+      atomicMax(dmax, (unsigned long long)__double_as_longlong((double)v));
+    }
+  }
 }
 
 // deviations of cell c, mirrored across a wall of unit normal (nx, ny, nz) when mir
@@ -496,13 +545,15 @@ __device__ __forceinline__ R vl_t(R a, R b, R c) {
   return dm * dp > R(0) ? R(2) * dm * dp / (dm + dp) : R(0);
 }
 
-template <typename R>
-__global__ void k_sph_flux(SphDev D, SphWork<R> Wk, const double *__restrict__ phi) {
+// Per-face flux of either form.  MX: the mixed form's FP32 tables and face
+// fluxes (phif); else FP64 tables and phi.
+template <typename R, bool MX>
+__global__ void __launch_bounds__(SPT) k_sph_flux(SphDev D, SphWork<R> Wk, const double *__restrict__ phi,
+                                                  const float *__restrict__ phif) {
   const long f = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (f >= D.NF) return;
   R wL[SW_N], wR[SW_N], wLL[SW_N], wRR[SW_N];
-  double nd[3], Ad;
-  R brho = R(0), bp = R(0);
+  R n0, n1, n2, A, brho = R(0), bp = R(0);
   bool wall = false;
   if (f < D.FA) {   // angular face (s, k)
     const int k = (int)(f / D.NS);
@@ -511,38 +562,49 @@ __global__ void k_sph_flux(SphDev D, SphWork<R> Wk, const double *__restrict__ p
     load_w<R>(D, Wk, base + D.sR[s], false, R(0), R(0), R(0), wR);
     load_w<R>(D, Wk, base + D.sLL[s], false, R(0), R(0), R(0), wLL);
     load_w<R>(D, Wk, base + D.sRR[s], false, R(0), R(0), R(0), wRR);
-    nd[0] = D.sn[3 * s]; nd[1] = D.sn[3 * s + 1]; nd[2] = D.sn[3 * s + 2];
-    const double r0 = D.r[k], r1 = D.r[k + 1];
-    Ad = 0.5 * (r1 * r1 - r0 * r0) * D.sth[s];
-    if (D.rho_c) { brho = (R)D.rho_c[k]; bp = (R)D.p_c[k]; }
+    if constexpr (MX) {
+      n0 = D.sn_f[3 * s]; n1 = D.sn_f[3 * s + 1]; n2 = D.sn_f[3 * s + 2];
+      A = D.hdr2_f[k] * D.sth_f[s];
+      if (D.rho_cf) { brho = D.rho_cf[k]; bp = D.p_cf[k]; }
+    } else {
+      n0 = D.sn[3 * s]; n1 = D.sn[3 * s + 1]; n2 = D.sn[3 * s + 2];
+      const double r0 = D.r[k], r1 = D.r[k + 1];
+      A = 0.5 * (r1 * r1 - r0 * r0) * D.sth[s];
+      if (D.rho_c) { brho = D.rho_c[k]; bp = D.p_c[k]; }
+    }
   } else {          // radial face (a, k)
     const long q = f - D.FA;
     const int k = (int)(q / D.NC), Nr = D.Nr;
     const long a = q - (long)k * D.NC;
-    nd[0] = D.cna[3 * a]; nd[1] = D.cna[3 * a + 1]; nd[2] = D.cna[3 * a + 2];
-    Ad = D.r[k] * D.r[k] * D.cva[a];
-    if (D.rho_c) { brho = (R)D.rho_f[k]; bp = (R)D.p_f[k]; }
-    const R nx = (R)nd[0], ny = (R)nd[1], nz = (R)nd[2];
+    if constexpr (MX) {
+      n0 = D.cna_f[3 * a]; n1 = D.cna_f[3 * a + 1]; n2 = D.cna_f[3 * a + 2];
+      A = D.r_f[k] * D.r_f[k] * D.cva_f[a];
+      if (D.rho_ff) { brho = D.rho_ff[k]; bp = D.p_ff[k]; }
+    } else {
+      n0 = D.cna[3 * a]; n1 = D.cna[3 * a + 1]; n2 = D.cna[3 * a + 2];
+      A = D.r[k] * D.r[k] * D.cva[a];
+      if (D.rho_f) { brho = D.rho_f[k]; bp = D.p_f[k]; }
+    }
     const long c0 = a, cst = D.NC;   // cell (a, kk) = c0 + kk cst
     if (k == 0) {            // inner wall: the ghost side mirrors cells 0 and 1
       wall = true;
-      load_w<R>(D, Wk, c0, false, nx, ny, nz, wR);
-      load_w<R>(D, Wk, c0 + cst, false, nx, ny, nz, wRR);
-      load_w<R>(D, Wk, c0, true, nx, ny, nz, wL);
-      load_w<R>(D, Wk, c0 + cst, true, nx, ny, nz, wLL);
+      load_w<R>(D, Wk, c0, false, n0, n1, n2, wR);
+      load_w<R>(D, Wk, c0 + cst, false, n0, n1, n2, wRR);
+      load_w<R>(D, Wk, c0, true, n0, n1, n2, wL);
+      load_w<R>(D, Wk, c0 + cst, true, n0, n1, n2, wLL);
     } else if (k == Nr) {    // outer wall
       wall = true;
-      load_w<R>(D, Wk, c0 + (Nr - 1) * cst, false, nx, ny, nz, wL);
-      load_w<R>(D, Wk, c0 + (Nr - 2) * cst, false, nx, ny, nz, wLL);
-      load_w<R>(D, Wk, c0 + (Nr - 1) * cst, true, nx, ny, nz, wR);
-      load_w<R>(D, Wk, c0 + (Nr - 2) * cst, true, nx, ny, nz, wRR);
+      load_w<R>(D, Wk, c0 + (Nr - 1) * cst, false, n0, n1, n2, wL);
+      load_w<R>(D, Wk, c0 + (Nr - 2) * cst, false, n0, n1, n2, wLL);
+      load_w<R>(D, Wk, c0 + (Nr - 1) * cst, true, n0, n1, n2, wR);
+      load_w<R>(D, Wk, c0 + (Nr - 2) * cst, true, n0, n1, n2, wRR);
     } else {                 // beside a wall the far cell is the near one's mirror
-      load_w<R>(D, Wk, c0 + (k - 1) * cst, false, nx, ny, nz, wL);
-      load_w<R>(D, Wk, c0 + k * cst, false, nx, ny, nz, wR);
-      if (k >= 2) load_w<R>(D, Wk, c0 + (k - 2) * cst, false, nx, ny, nz, wLL);
-      else load_w<R>(D, Wk, c0, true, nx, ny, nz, wLL);
-      if (k + 1 <= Nr - 1) load_w<R>(D, Wk, c0 + (k + 1) * cst, false, nx, ny, nz, wRR);
-      else load_w<R>(D, Wk, c0 + (Nr - 1) * cst, true, nx, ny, nz, wRR);
+      load_w<R>(D, Wk, c0 + (k - 1) * cst, false, n0, n1, n2, wL);
+      load_w<R>(D, Wk, c0 + k * cst, false, n0, n1, n2, wR);
+      if (k >= 2) load_w<R>(D, Wk, c0 + (k - 2) * cst, false, n0, n1, n2, wLL);
+      else load_w<R>(D, Wk, c0, true, n0, n1, n2, wLL);
+      if (k + 1 <= Nr - 1) load_w<R>(D, Wk, c0 + (k + 1) * cst, false, n0, n1, n2, wRR);
+      else load_w<R>(D, Wk, c0 + (Nr - 1) * cst, true, n0, n1, n2, wRR);
     }
   }
   R ql[SW_N], qr[SW_N];
@@ -551,11 +613,10 @@ __global__ void k_sph_flux(SphDev D, SphWork<R> Wk, const double *__restrict__ p
     ql[v] = wL[v] + R(0.5) * vl_t<R>(wLL[v], wL[v], wR[v]);
     qr[v] = wR[v] - R(0.5) * vl_t<R>(wL[v], wR[v], wRR[v]);
   }
-  // normal frame: tangents from the Cartesian axis least aligned with n
-  const R n0 = (R)nd[0], n1 = (R)nd[1], n2 = (R)nd[2];
+  // normal frame: t1 = unit(e_ax x n) for the Cartesian axis least aligned
+  // with n, t2 = n x t1
   const R an0 = fabs(n0), an1 = fabs(n1), an2 = fabs(n2);
   const int ax = an1 < an0 ? (an2 < an1 ? 2 : 1) : (an2 < an0 ? 2 : 0);
-  // t1 = unit(e_ax x n), t2 = n x t1
   R t1x = ax == 0 ? R(0) : (ax == 1 ? n2 : -n1);
   R t1y = ax == 0 ? -n2 : (ax == 1 ? R(0) : n0);
   R t1z = ax == 0 ? n1 : (ax == 1 ? -n0 : R(0));
@@ -576,14 +637,22 @@ __global__ void k_sph_flux(SphDev D, SphWork<R> Wk, const double *__restrict__ p
   if (!(brho + wl[RD_RHO] > R(0) && brho + wr[RD_RHO] > R(0) && bp + wl[RD_P] > R(0) && bp + wr[RD_P] > R(0)))
     atomicOr(D.dflag, FLAG_NEG);
   GasK<R> K;
-  K.g = (R)D.gamma;
-  K.igm1 = (R)(1.0 / (D.gamma - 1.0));
-  K.ggm1 = (R)(D.gamma / (D.gamma - 1.0));
-  const R A = (R)Ad;
-  const R ph = (R)phi[f];
+  R mthr, bn;
+  if constexpr (MX) {
+    K.g = D.gf; K.igm1 = D.igm1f; K.ggm1 = D.ggm1f;
+    mthr = D.machf;
+    bn = phif[f] / A;
+  } else {
+    K.g = D.gamma; K.igm1 = 1.0 / (D.gamma - 1.0); K.ggm1 = D.gamma * K.igm1;
+    mthr = D.mach;
+    bn = phi[f] / A;
+  }
   R fl[7];
   int up;
-  riemann_dev<R, 0, true>(wl, wr, ph / A, brho, bp, K.g, K.g, 0, D.riemann, (R)D.mach, fl, up, K);
+  // the mixed form takes the packed-FP32 solver (left and right sides as the
+  // two lanes of each f32x2 instruction): same formulas, FP32 rounding apart
+  if constexpr (MX) x2::riemann_ideal_lr(wl, wr, bn, brho, bp, D.riemann, mthr, fl, up, K);
+  else riemann_dev<R, 0, true>(wl, wr, bn, brho, bp, K.g, K.g, 0, D.riemann, mthr, fl, up, K);
   if (wall) {   // a symmetry plane: only the normal-momentum flux survives
 #pragma unroll
     for (int q = 0; q < 7; ++q)
@@ -634,20 +703,24 @@ __device__ __forceinline__ R contact_ct(const R *Ec, const R *Ef, const int *ms)
   return q * (Ea1 + Ea0 + Eb1 + Eb0) + q * (dlo - dup) + q * (dle - dri);
 }
 
-template <typename R>
-__global__ void k_sph_emf(SphDev D, SphWork<R> Wk) {
+template <typename R, bool MX>
+__global__ void __launch_bounds__(SPT) k_sph_emf(SphDev D, SphWork<R> Wk) {
   const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (e >= D.NE) return;
   R Ec[4], Ef[4];
   int ms[4];
+  double L;   // the edge's length: r1 - r0 (radial), r theta (angular)
   if (e < D.ER) {   // radial edge (v, k)
     const int k = (int)(e / D.NV);
     const long v = e - (long)k * D.NV, fb = (long)k * D.NS, cb = (long)k * D.NC;
-    const R lx = (R)D.vd[3 * v], ly = (R)D.vd[3 * v + 1], lz = (R)D.vd[3 * v + 2];
+    L = D.r[k + 1] - D.r[k];
+    const R lx = MX ? (R)D.vd_f[3 * v] : (R)D.vd[3 * v];
+    const R ly = MX ? (R)D.vd_f[3 * v + 1] : (R)D.vd[3 * v + 1];
+    const R lz = MX ? (R)D.vd_f[3 * v + 2] : (R)D.vd[3 * v + 2];
     if (D.vcnt[v] == 3) {   // a cube corner: the mean of the three face EMFs
       R t = R(0);
       for (int m = 0; m < 3; ++m) t += efl<R>(D, Wk, fb + D.vside[4 * v + m], lx, ly, lz);
-      Wk.EE[e] = t / R(3);
+      Wk.EE[e] = L * (double)(t / R(3));
       return;
     }
 #pragma unroll
@@ -661,8 +734,11 @@ __global__ void k_sph_emf(SphDev D, SphWork<R> Wk) {
     const long q = e - D.ER;
     const int k = (int)(q / D.NS);
     const long s = q - (long)k * D.NS;
-    if (k == 0 || k == D.Nr) { Wk.EE[e] = R(0); return; }
-    const R lx = (R)D.sl[3 * s], ly = (R)D.sl[3 * s + 1], lz = (R)D.sl[3 * s + 2];
+    if (k == 0 || k == D.Nr) { Wk.EE[e] = 0.0; return; }
+    L = D.r[k] * D.sth[s];
+    const R lx = MX ? (R)D.sl_f[3 * s] : (R)D.sl[3 * s];
+    const R ly = MX ? (R)D.sl_f[3 * s + 1] : (R)D.sl[3 * s + 1];
+    const R lz = MX ? (R)D.sl_f[3 * s + 2] : (R)D.sl[3 * s + 2];
     const long cL0 = (long)(k - 1) * D.NC + D.sL[s], cR0 = (long)(k - 1) * D.NC + D.sR[s];
     const long cL1 = (long)k * D.NC + D.sL[s], cR1 = (long)k * D.NC + D.sR[s];
     const long A0 = (long)(k - 1) * D.NS + s, A1 = (long)k * D.NS + s;
@@ -682,45 +758,33 @@ __global__ void k_sph_emf(SphDev D, SphWork<R> Wk) {
       ms[m] = Wk.UP[ff[m]];
     }
   }
-  Wk.EE[e] = contact_ct<R>(Ec, Ef, ms);
+  Wk.EE[e] = L * (double)contact_ct<R>(Ec, Ef, ms);
 }
 
-// R = (1/V) sum_f s_f F_f - S of cell (a, k) given its stage-input density
-// deviation and momentum
-template <typename R>
-__device__ __forceinline__ void residual(const SphDev &D, const SphWork<R> &Wk, long an, int k, R drho, R mx, R my,
-                                         R mz, R *r) {
-  CellFaces F;
-  cell_faces(D, an, k, F);
-  const long nf = D.NF;
-#pragma unroll
-  for (int v = 0; v < 5; ++v) r[v] = R(0);
-#pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    const R s = (R)F.s[m];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) r[v] += s * Wk.FC[v * nf + F.f[m]];
-  }
-  const R iv = (R)(1.0 / cell_vol(D, an, k));
-#pragma unroll
-  for (int v = 0; v < 5; ++v) r[v] *= iv;
-  const R g = D.g_c ? (R)D.g_c[k] : R(0);
-  const R gx = -g * (R)D.cdc[3 * an], gy = -g * (R)D.cdc[3 * an + 1], gz = -g * (R)D.cdc[3 * an + 2];   // inward
-  r[1] -= drho * gx; r[2] -= drho * gy; r[3] -= drho * gz;
-  R se = mx * gx + my * gy + mz * gz;
-  if (D.heat) se += (R)D.heat[k];
-  r[4] -= se;
-}
-
-// FP64: out = a base + b (in - dt R)
+// FP64: out = a base + b (in - dt R), R = (1/V) sum_f s_f F_f - S
 __global__ void k_sph_update_cells(SphDev D, SphWork<double> Wk, const double *Uin, const double *Ubase, double *Uout,
                                    double a, double b, const double *__restrict__ dtp) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= D.ncell) return;
   const int k = (int)(c / D.NC);
-  const long an = c - (long)k * D.NC, nc = D.ncell;
-  double r[5];
-  residual<double>(D, Wk, an, k, Uin[c] - bg_rho<double>(D, k), Uin[nc + c], Uin[2 * nc + c], Uin[3 * nc + c], r);
+  const long an = c - (long)k * D.NC, nc = D.ncell, nf = D.NF;
+  CellFaces F;
+  cell_faces(D, an, k, F);
+  double r[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+  for (int m = 0; m < 6; ++m)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) r[v] += F.s[m] * Wk.FC[v * nf + F.f[m]];
+  const double iv = 1.0 / cell_vol(D, an, k);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) r[v] *= iv;
+  const double g = D.g_c ? D.g_c[k] : 0.0;
+  const V3 gv = ld3(D.cdc, an) * -g;   // radial, inward
+  const double drho = Uin[c] - bg_rho(D, k);
+  r[1] -= drho * gv.x; r[2] -= drho * gv.y; r[3] -= drho * gv.z;
+  double se = Uin[nc + c] * gv.x + Uin[2 * nc + c] * gv.y + Uin[3 * nc + c] * gv.z;
+  if (D.heat) se += D.heat[k];
+  r[4] -= se;
   const double dt = *dtp;
   double o[5];
 #pragma unroll
@@ -731,20 +795,42 @@ __global__ void k_sph_update_cells(SphDev D, SphWork<double> Wk, const double *U
 
 // Mixed: dU_out = b (dU_in - dt R) (dU_in null at the first stage); the last
 // stage writes U^n + dU_out into U in FP64
-__global__ void k_sph_update_cells_mx(SphDev D, SphWork<float> Wk, double *U, const float *dUin, float *dUout, float b,
-                                      const double *__restrict__ dtp, int last) {
+__global__ void __launch_bounds__(SPT) k_sph_update_cells_mx(SphDev D, SphWork<float> Wk, double *U, const float *dUin,
+                                                             float *dUout, float b, const double *__restrict__ dtp,
+                                                             int last) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= D.ncell) return;
   const int k = (int)(c / D.NC);
-  const long an = c - (long)k * D.NC, nc = D.ncell;
+  const long an = c - (long)k * D.NC, nc = D.ncell, nf = D.NF;
   float du[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) du[v] = dUin ? dUin[v * nc + c] : 0.f;
-  const double rh = D.rho_c ? D.rho_c[k] : 0.0;
-  const float drho = (float)(U[c] - rh) + du[0];
+  long fi[6];
+  float sg[6];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    fi[m] = (long)k * D.NS + D.cs[4 * an + m];
+    sg[m] = D.csg[4 * an + m];
+  }
+  fi[4] = D.FA + (long)k * D.NC + an; sg[4] = -1.f;
+  fi[5] = D.FA + (long)(k + 1) * D.NC + an; sg[5] = 1.f;
+  float r[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int m = 0; m < 6; ++m)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) r[v] += sg[m] * Wk.FC[v * nf + fi[m]];
+  const float iv = D.iom_f[an] * D.ish_f[k];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) r[v] *= iv;
+  // sources of the stage input: (rho - rho_hat) g and rho u . g, heating
+  const float drho = (float)(D.rho_c ? U[c] - D.rho_c[k] : U[c]) + du[0];
   const float mx = (float)U[nc + c] + du[1], my = (float)U[2 * nc + c] + du[2], mz = (float)U[3 * nc + c] + du[3];
-  float r[5];
-  residual<float>(D, Wk, an, k, drho, mx, my, mz, r);
+  const float g = D.g_cf ? D.g_cf[k] : 0.f;
+  const float gx = -g * D.cdc_f[3 * an], gy = -g * D.cdc_f[3 * an + 1], gz = -g * D.cdc_f[3 * an + 2];
+  r[1] -= drho * gx; r[2] -= drho * gy; r[3] -= drho * gz;
+  float se = mx * gx + my * gy + mz * gz;
+  if (D.heat_f) se += D.heat_f[k];
+  r[4] -= se;
   const float dt = (float)*dtp;
   float o[5];
 #pragma unroll
@@ -758,71 +844,74 @@ __global__ void k_sph_update_cells_mx(SphDev D, SphWork<float> Wk, double *U, co
   }
 }
 
-// the circulation sum_e sigma l (E . l) about face f (Eq. induction), in
-// FP64 from the edge EMFs of either form: each edge's term is the same FP64
-// product (sign) r theta E or (sign) dr E in every face that has the edge
-template <typename R>
-__device__ __forceinline__ double circulation(const SphDev &D, const R *__restrict__ EE, long f) {
+// the circulation sum_e sigma L (E . l) about face f (Eq. induction), FP64
+// in both forms, from the edges' line integrals: every face that has an edge
+// adds the same FP64 value with its orientation's sign
+// x with the sign of s (s = +1 or -1) flipped in the integer unit: the FP64
+// pipe only sees the additions
+__device__ __forceinline__ double sgn_mul(signed char s, double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (s < 0 ? (long long)0x8000000000000000ULL : 0LL));
+}
+
+__device__ __forceinline__ double circulation(const SphDev &D, const double *__restrict__ EE, long f) {
   if (f < D.FA) {   // angular face (s, k): edges (s, k), (v1, k), (s, k+1), (v0, k)
     const int k = (int)(f / D.NS);
     const long s = f - (long)k * D.NS;
-    const double dr = D.r[k + 1] - D.r[k], th = D.sth[s], si = D.s_in[s];
-    double t = si * D.r[k] * th * (double)EE[D.ER + (long)k * D.NS + s];
-    t += D.s_v1[s] * dr * (double)EE[(long)k * D.NV + D.sv1[s]];
-    t += -si * D.r[k + 1] * th * (double)EE[D.ER + (long)(k + 1) * D.NS + s];
-    t += D.s_v0[s] * dr * (double)EE[(long)k * D.NV + D.sv0[s]];
-    return t;
+    const signed char si = D.s_in[s];
+    const double ein = sgn_mul(si, EE[D.ER + (long)k * D.NS + s]);
+    const double eout = sgn_mul((signed char)-si, EE[D.ER + (long)(k + 1) * D.NS + s]);
+    const double e1 = sgn_mul(D.s_v1[s], EE[(long)k * D.NV + D.sv1[s]]);
+    const double e0 = sgn_mul(D.s_v0[s], EE[(long)k * D.NV + D.sv0[s]]);
+    return ((ein + eout) + e1) + e0;
   }
   const long q = f - D.FA;   // radial face (a, k): the angular edges (s_m, k)
   const int k = (int)(q / D.NC);
-  const long an = q - (long)k * D.NC;
-  double t = 0.0;
+  const long an = q - (long)k * D.NC, eb = D.ER + (long)k * D.NS;
+  double e[4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int s = D.cs[4 * an + m];
-    t += D.crs[4 * an + m] * D.r[k] * D.sth[s] * (double)EE[D.ER + (long)k * D.NS + s];
-  }
-  return t;
+  for (int m = 0; m < 4; ++m) e[m] = sgn_mul(D.crs[4 * an + m], EE[eb + D.cs[4 * an + m]]);
+  return ((e[0] + e[1]) + e[2]) + e[3];
 }
 
-// out = a base + b (in - dt circulation), FP64 in both forms
-template <typename R>
-__global__ void k_sph_update_faces(SphDev D, const R *__restrict__ EE, const double *pin, const double *pbase,
-                                   double *pout, double a, double b, const double *__restrict__ dtp) {
+// out = a base + b (in - dt circulation) in FP64; phif (mixed form): the FP32
+// copy of out for the next stage's FP32 kernels
+__global__ void __launch_bounds__(SPT) k_sph_update_faces(SphDev D, const double *__restrict__ EE, const double *pin,
+                                                          const double *pbase, double *pout, double a, double b,
+                                                          const double *__restrict__ dtp, float *phif) {
   const long f = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (f >= D.NF) return;
-  const double t = circulation<R>(D, EE, f);
+  const double t = circulation(D, EE, f);
   const double o = a * pbase[f] + b * (pin[f] - *dtp * t);
   pout[f] = o;
+  if (phif) phif[f] = (float)o;
 }
 
-template <typename R>
-__global__ void k_sph_dt(SphDev D, SphWork<R> Wk, unsigned long long *dmax) {
+__global__ void k_sph_dt(SphDev D, SphWork<double> Wk, unsigned long long *dmax) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   double m = 0.0;
   if (c < D.ncell) {
     const long n = D.ncell;
     const int k = (int)(c / D.NC);
     const long a = c - (long)k * D.NC;
-    const R rho = Wk.W[SW_RHO * n + c] + bg_rho<R>(D, k);
-    const R P = Wk.W[SW_P * n + c] + bg_p<R>(D, k);
-    const R ux = Wk.W[SW_U * n + c], uy = Wk.W[(SW_U + 1) * n + c], uz = Wk.W[(SW_U + 2) * n + c];
-    const R bx = Wk.W[SW_B * n + c], by = Wk.W[(SW_B + 1) * n + c], bz = Wk.W[(SW_B + 2) * n + c];
-    const R a2 = (R)D.gamma * P / rho, b2 = (bx * bx + by * by + bz * bz) / rho;
+    const double rho = Wk.W[SW_RHO * n + c] + bg_rho(D, k);
+    const double P = Wk.W[SW_P * n + c] + bg_p(D, k);
+    const V3 u = v3(Wk.W[SW_U * n + c], Wk.W[(SW_U + 1) * n + c], Wk.W[(SW_U + 2) * n + c]);
+    const V3 b = v3(Wk.W[SW_B * n + c], Wk.W[(SW_B + 1) * n + c], Wk.W[(SW_B + 2) * n + c]);
+    const double a2 = D.gamma * P / rho, b2 = dot3(b, b) / rho;
     CellFaces F;
     cell_faces(D, a, k, F);
-    R sum = R(0);
+    double sum = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {   // the cell's three mesh directions
       const V3 span = F.x[2 * d + 1] - F.x[2 * d];
-      const double wd = len3(span);
-      const R ex = (R)(span.x / wd), ey = (R)(span.y / wd), ez = (R)(span.z / wd);
-      const R bd = bx * ex + by * ey + bz * ez;
-      R disc = (a2 + b2) * (a2 + b2) - R(4) * a2 * bd * bd / rho;
-      if (disc < R(0)) disc = R(0);
-      sum += (fabs(ux * ex + uy * ey + uz * ez) + sqrt(R(0.5) * (a2 + b2 + sqrt(disc)))) / (R)wd;
+      const double width = len3(span);
+      const V3 ed = span * (1.0 / width);
+      const double bd = dot3(b, ed);
+      double disc = (a2 + b2) * (a2 + b2) - 4.0 * a2 * bd * bd / rho;
+      if (disc < 0.0) disc = 0.0;
+      sum += (fabs(dot3(u, ed)) + sqrt(0.5 * (a2 + b2 + sqrt(disc)))) / width;
     }
-    m = (sum == sum) ? (double)sum : INFINITY;
+    m = (sum == sum) ? sum : INFINITY;
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   __shared__ double red[SPT / 32];
@@ -843,6 +932,10 @@ __global__ void k_sph_dt_fin(double cfl, unsigned long long *dmax, double *dt) {
 
 __global__ void k_sph_set(double v, double *p) { *p = v; }
 
+__global__ void k_sph_to_float(long n, const double *__restrict__ in, float *__restrict__ out) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (float)in[t];
+}
 // ABI <-> internal.  Cells: [v][p][k][j][i] <-> [v][k][a].  Faces: alpha
 // [p][k][j][i] (N + 1 per row), beta [p][k][j][i] (N + 1 rows), radial
 // [p][k][j][i] (Nr + 1 radii).
@@ -919,7 +1012,8 @@ struct phl_sphere {
   cudaStream_t s = nullptr;
   std::vector<void *> allocs;
   double *U = nullptr, *U1 = nullptr, *phi = nullptr, *phi1 = nullptr, *dt = nullptr, *abi_buf = nullptr;
-  float *dU = nullptr;   // mixed: the cells' stage increments
+  float *dU = nullptr;     // mixed: the cells' stage increments
+  float *phif = nullptr;   // mixed: FP32 copy of the stage's face fluxes
   unsigned long long *dmax = nullptr;
   long nabi = 0;
   long steps = 0;
@@ -951,6 +1045,14 @@ cudaError_t up_arr(phl_sphere *S, const double **dst, const double *src, long n)
   if (!src) { *dst = nullptr; return cudaSuccess; }
   return up_vec(S, dst, std::vector<double>(src, src + n));
 }
+cudaError_t up_arr_f(phl_sphere *S, const float **dst, const double *src, long n) {
+  if (!src) { *dst = nullptr; return cudaSuccess; }
+  std::vector<float> v(n);
+  for (long i = 0; i < n; ++i) v[i] = (float)src[i];
+  return up_vec(S, dst, v);
+}
+std::vector<float> to_f(const std::vector<double> &v) { return std::vector<float>(v.begin(), v.end()); }
+
 template <typename R>
 cudaError_t alloc_work(phl_sphere *S, SphWork<R> &Wk) {
   const SphDev &D = S->D;
@@ -980,24 +1082,19 @@ void timed(phl_sphere *S, int cls, F &&launch) {
   S->prof.end(S->s);
 }
 
-// primitives of the stage input (mixed: U^n + dU when inc)
-void sph_prims(phl_sphere *S, const double *U, const double *phi, bool inc) {
-  const SphDev &D = S->D;
-  if (S->mixed)
-    timed(S, KC_SPH_PRIM, [&] {
-      k_sph_prims_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->U, inc ? S->dU : nullptr, phi);
-    });
-  else
-    timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, U, phi); });
-}
-
 // the CFL step of U^n (Eq. cfl) into S->dt; leaves the primitives of U^n in W
 void sph_dt(phl_sphere *S) {
   const SphDev &D = S->D;
-  sph_prims(S, S->U, S->phi, false);
+  if (S->mixed) {   // folded into the primitives
+    timed(S, KC_SPH_PRIM, [&] {
+      k_sph_prims_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->U, nullptr, S->phif, S->dmax);
+    });
+    timed(S, KC_SPH_DT, [&] { k_sph_dt_fin<<<1, 1, 0, S->s>>>(D.cfl, S->dmax, S->dt); });
+    return;
+  }
+  timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, S->U, S->phi); });
   timed(S, KC_SPH_DT, [&] {
-    if (S->mixed) k_sph_dt<float><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->dmax);
-    else k_sph_dt<double><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, S->dmax);
+    k_sph_dt<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, S->dmax);
     k_sph_dt_fin<<<1, 1, 0, S->s>>>(D.cfl, S->dmax, S->dt);
   });
 }
@@ -1036,16 +1133,19 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
     return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: %s", ex.what());
   }
   SphDev &D = S->D;
-  D.N = d->N; D.Nr = d->Nr;
+  const int Nr = d->Nr;
+  D.N = d->N; D.Nr = Nr;
   D.NC = M.NC; D.NS = M.NS; D.NV = M.NV;
-  D.ncell = M.NC * d->Nr;
-  D.FA = M.NS * d->Nr;
-  D.NF = D.FA + M.NC * (d->Nr + 1);
-  D.ER = M.NV * d->Nr;
-  D.NE = D.ER + M.NS * (d->Nr + 1);
+  D.ncell = M.NC * Nr;
+  D.FA = M.NS * Nr;
+  D.NF = D.FA + M.NC * (Nr + 1);
+  D.ER = M.NV * Nr;
+  D.NE = D.ER + M.NS * (Nr + 1);
   D.gamma = d->gamma; D.cfl = d->cfl; D.mach = d->mach_thr; D.riemann = d->riemann;
-  std::vector<double> r(d->Nr + 1);
-  for (int k = 0; k <= d->Nr; ++k) r[k] = d->r_in + (d->r_out - d->r_in) * k / d->Nr;
+  D.gf = (float)d->gamma; D.gm1f = (float)(d->gamma - 1.0); D.igm1f = (float)(1.0 / (d->gamma - 1.0));
+  D.ggm1f = (float)(d->gamma / (d->gamma - 1.0)); D.machf = (float)d->mach_thr;
+  std::vector<double> r(Nr + 1);
+  for (int k = 0; k <= Nr; ++k) r[k] = d->r_in + (d->r_out - d->r_in) * k / Nr;
   cudaError_t e = up_vec(S, &D.r, r);
   auto U = [&](auto **dst, const auto &v) { if (e == cudaSuccess) e = up_vec(S, dst, v); };
   U(&D.vd, M.vd); U(&D.sn, M.sn); U(&D.sl, M.sl); U(&D.smid, M.smid); U(&D.sth, M.sth);
@@ -1055,24 +1155,63 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
   U(&D.s_in, M.s_in); U(&D.s_v0, M.s_v0); U(&D.s_v1, M.s_v1); U(&D.s_swap, M.s_swap);
   U(&D.csg, M.csg); U(&D.crs, M.crs); U(&D.vsgn, M.vsgn); U(&D.vcnt, M.vcnt);
   U(&S->AM.s, M.abi_s); U(&S->AM.sg, M.abi_sg); U(&S->AM.own, M.abi_own);
-  if (e == cudaSuccess) e = up_arr(S, &D.rho_c, d->rho_c, d->Nr);
-  if (e == cudaSuccess) e = up_arr(S, &D.p_c, d->p_c, d->Nr);
-  if (e == cudaSuccess) e = up_arr(S, &D.rho_f, d->rho_f, d->Nr + 1);
-  if (e == cudaSuccess) e = up_arr(S, &D.p_f, d->p_f, d->Nr + 1);
-  if (e == cudaSuccess) e = up_arr(S, &D.g_c, d->g_c, d->Nr);
-  if (e == cudaSuccess) e = up_arr(S, &D.heat, d->heat, d->Nr);
+  if (e == cudaSuccess) e = up_arr(S, &D.rho_c, d->rho_c, Nr);
+  if (e == cudaSuccess) e = up_arr(S, &D.p_c, d->p_c, Nr);
+  if (e == cudaSuccess) e = up_arr(S, &D.rho_f, d->rho_f, Nr + 1);
+  if (e == cudaSuccess) e = up_arr(S, &D.p_f, d->p_f, Nr + 1);
+  if (e == cudaSuccess) e = up_arr(S, &D.g_c, d->g_c, Nr);
+  if (e == cudaSuccess) e = up_arr(S, &D.heat, d->heat, Nr);
+  D.eh_c = nullptr;
+  if (d->p_c) {
+    std::vector<double> eh(Nr);
+    for (int k = 0; k < Nr; ++k) eh[k] = d->p_c[k] / (d->gamma - 1.0);
+    U(&D.eh_c, eh);
+  }
+  if (S->mixed) {   // FP32 copies of the geometry, radial factors and profiles
+    std::vector<float> iom(M.NC), cw(2 * M.NC), ce(6 * M.NC);
+    for (long a = 0; a < M.NC; ++a) {
+      iom[a] = (float)(1.0 / M.com[a]);
+      for (int dd = 0; dd < 2; ++dd) {   // the a and b directions: between the centres of opposite sides
+        const V3 span = ld3(M.smid.data(), M.cs[4 * a + 2 * dd + 1]) - ld3(M.smid.data(), M.cs[4 * a + 2 * dd]);
+        const double w = len3(span);
+        cw[2 * a + dd] = (float)w;
+        ce[6 * a + 3 * dd] = (float)(span.x / w); ce[6 * a + 3 * dd + 1] = (float)(span.y / w);
+        ce[6 * a + 3 * dd + 2] = (float)(span.z / w);
+      }
+    }
+    std::vector<float> rf(Nr + 1), rmf(Nr), hdr2(Nr), ish(Nr), drf(Nr);
+    for (int k = 0; k <= Nr; ++k) rf[k] = (float)r[k];
+    for (int k = 0; k < Nr; ++k) {
+      rmf[k] = (float)(0.5 * (r[k] + r[k + 1]));
+      hdr2[k] = (float)(0.5 * (r[k + 1] * r[k + 1] - r[k] * r[k]));
+      ish[k] = (float)(3.0 / (r[k + 1] * r[k + 1] * r[k + 1] - r[k] * r[k] * r[k]));
+      drf[k] = (float)(r[k + 1] - r[k]);
+    }
+    U(&D.vd_f, to_f(M.vd)); U(&D.sn_f, to_f(M.sn)); U(&D.sl_f, to_f(M.sl)); U(&D.smid_f, to_f(M.smid));
+    U(&D.sth_f, to_f(M.sth)); U(&D.cdc_f, to_f(M.cdc)); U(&D.cna_f, to_f(M.cna)); U(&D.cva_f, to_f(M.cva));
+    U(&D.iom_f, iom); U(&D.cw_f, cw); U(&D.ce_f, ce);
+    U(&D.r_f, rf); U(&D.rm_f, rmf); U(&D.hdr2_f, hdr2); U(&D.ish_f, ish); U(&D.dr_f, drf);
+    if (e == cudaSuccess) e = up_arr_f(S, &D.rho_cf, d->rho_c, Nr);
+    if (e == cudaSuccess) e = up_arr_f(S, &D.p_cf, d->p_c, Nr);
+    if (e == cudaSuccess) e = up_arr_f(S, &D.rho_ff, d->rho_f, Nr + 1);
+    if (e == cudaSuccess) e = up_arr_f(S, &D.p_ff, d->p_f, Nr + 1);
+    if (e == cudaSuccess) e = up_arr_f(S, &D.g_cf, d->g_c, Nr);
+    if (e == cudaSuccess) e = up_arr_f(S, &D.heat_f, d->heat, Nr);
+  }
   if (e == cudaSuccess) e = alloc_n(S, &D.dflag, 1);
   if (e == cudaSuccess) e = S->mixed ? alloc_work(S, S->W32) : alloc_work(S, S->W64);
   if (e == cudaSuccess) e = alloc_n(S, &S->U, 5 * D.ncell);
   if (e == cudaSuccess) e = alloc_n(S, &S->phi, D.NF);
   if (e == cudaSuccess) e = alloc_n(S, &S->phi1, D.NF);
-  if (e == cudaSuccess) {
-    if (S->mixed) e = alloc_n(S, &S->dU, 5 * D.ncell);
-    else e = alloc_n(S, &S->U1, 5 * D.ncell);
+  if (S->mixed) {
+    if (e == cudaSuccess) e = alloc_n(S, &S->dU, 5 * D.ncell);
+    if (e == cudaSuccess) e = alloc_n(S, &S->phif, D.NF);
+  } else {
+    if (e == cudaSuccess) e = alloc_n(S, &S->U1, 5 * D.ncell);
   }
   if (e == cudaSuccess) e = alloc_n(S, &S->dt, 1);
   if (e == cudaSuccess) e = alloc_n(S, &S->dmax, 1);
-  S->nabi = 2L * 6 * d->Nr * d->N * (d->N + 1) + 6L * (d->Nr + 1) * d->N * d->N;
+  S->nabi = 2L * 6 * Nr * d->N * (d->N + 1) + 6L * (Nr + 1) * d->N * d->N;
   if (e == cudaSuccess) e = alloc_n(S, &S->abi_buf, std::max<long>(S->nabi, 5 * D.ncell));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1145,6 +1284,10 @@ phl_status phl_sphere_set_state(phl_sphere *S, const double *cons, const double 
     k_sph_gather_faces<<<nblk(S->nabi), SPT, 0, S->s>>>(S->D, S->AM, S->nabi, S->abi_buf, S->phi);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && S->mixed) {
+    k_sph_to_float<<<nblk(S->D.NF), SPT, 0, S->s>>>(S->D.NF, S->phi, S->phif);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(S->D.dflag, 0, sizeof(int), S->s);
   if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
   if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_set_state: %s", cudaGetErrorString(e));
@@ -1189,7 +1332,7 @@ phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
     else sph_dt(S);   // leaves the primitives of U^n for the first stage
     // Shu-Osher SSP-RK3 (Sect. 2.9)
     for (int st = 0; st < 3; ++st) {
-      const bool last = st == 2;
+      const bool last = st == 2, prims = st > 0 || dt > 0.0;
       // faces (both forms): stage input phi1 (Phi^n at the first stage),
       // out = a Phi^n + b (in - dt circulation); each thread reads its own
       // element of in and base before writing out
@@ -1199,11 +1342,14 @@ phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
       if (S->mixed) {
         // cells: stage input U^n + dU; increments out dU = b (dU - dt R)
         const float *dUin = st == 0 ? nullptr : S->dU;
-        if (st > 0 || dt > 0.0) sph_prims(S, S->U, pin, st > 0);
-        timed(S, KC_SPH_FLUX, [&] { k_sph_flux<float><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin); });
-        timed(S, KC_SPH_EMF, [&] { k_sph_emf<float><<<nblk(D.NE), SPT, 0, S->s>>>(D, S->W32); });
+        if (prims)
+          timed(S, KC_SPH_PRIM, [&] {
+            k_sph_prims_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->U, dUin, S->phif, nullptr);
+          });
+        timed(S, KC_SPH_FLUX, [&] { k_sph_flux<float, true><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin, S->phif); });
+        timed(S, KC_SPH_EMF, [&] { k_sph_emf<float, true><<<nblk(D.NE), SPT, 0, S->s>>>(D, S->W32); });
         timed(S, KC_SPH_UPDATE_FACES, [&] {
-          k_sph_update_faces<float><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32.EE, pin, S->phi, pout, a, b, S->dt);
+          k_sph_update_faces<<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32.EE, pin, S->phi, pout, a, b, S->dt, S->phif);
         });
         timed(S, KC_SPH_UPDATE_CELLS, [&] {
           k_sph_update_cells_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->U, dUin, S->dU, (float)b, S->dt,
@@ -1213,11 +1359,12 @@ phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
         // cells: stage input U1 (U^n at the first stage): out = a U^n + b (in - dt R)
         const double *Uin = st == 0 ? S->U : S->U1;
         double *Uout = last ? S->U : S->U1;
-        if (st > 0 || dt > 0.0) sph_prims(S, Uin, pin, false);
-        timed(S, KC_SPH_FLUX, [&] { k_sph_flux<double><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64, pin); });
-        timed(S, KC_SPH_EMF, [&] { k_sph_emf<double><<<nblk(D.NE), SPT, 0, S->s>>>(D, S->W64); });
+        if (prims)
+          timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, Uin, pin); });
+        timed(S, KC_SPH_FLUX, [&] { k_sph_flux<double, false><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64, pin, nullptr); });
+        timed(S, KC_SPH_EMF, [&] { k_sph_emf<double, false><<<nblk(D.NE), SPT, 0, S->s>>>(D, S->W64); });
         timed(S, KC_SPH_UPDATE_FACES, [&] {
-          k_sph_update_faces<double><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64.EE, pin, S->phi, pout, a, b, S->dt);
+          k_sph_update_faces<<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64.EE, pin, S->phi, pout, a, b, S->dt, nullptr);
         });
         timed(S, KC_SPH_UPDATE_CELLS, [&] {
           k_sph_update_cells<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, Uin, S->U, Uout, a, b, S->dt);
