@@ -503,6 +503,9 @@ def stellar_c3(P, n, steps, warmup, stream, ws):
     f = out["forms"]
     out["mixed_mlp_over_fp64"] = f["mixed+mlp"]["value"] / f["fp64"]["value"]
     out["mixed_mlp_cold_only_over_fp64"] = f["mixed+mlp_cold_only"]["value"] / f["fp64"]["value"]
+    out["network_mode"] = ("default use_mlp = 2: the network guesses T only where no previous T exists; "
+                           "use_mlp = 1 (network first at every stage) loses in time stepping: its guess "
+                           "needs more Newton steps than the previous step's T")
     # per-field L1 of the mixed + network form against the FP64 form, 3 steps at a fixed dt
     g64 = P.Grid(pr, precision="fp64", eos_table=table)
     g64.load()
@@ -510,7 +513,7 @@ def stellar_c3(P, n, steps, warmup, stream, ws):
     g64.step(3, dt)
     a = g64.get_state()
     g64.close()
-    gm = P.Grid(pr, precision="mixed", eos_table=table, mlp=net, mlp_mode=1)
+    gm = P.Grid(pr, precision="mixed", eos_table=table, mlp=net, mlp_mode=2)
     gm.load()
     gm.step(3, dt)
     b = gm.get_state()

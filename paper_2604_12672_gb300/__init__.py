@@ -364,7 +364,7 @@ class Mlp:
 
 
 def make_desc(pr, precision="fp64", riemann=None, eps_sf=None, cfl=None, rk=3, wb=True, stream=None,
-              mach_thr=None, eos_table=None, newton_tol=1e-11, newton_maxit=50, mlp=None, mlp_mode=1):
+              mach_thr=None, eos_table=None, newton_tol=1e-11, newton_maxit=50, mlp=None, mlp_mode=2):
     """phl_grid_desc of a problem; returns (desc, arrays the desc points into)."""
     d = GridDesc()
     for k in range(3):
@@ -485,7 +485,7 @@ class Grid:
 
     def __init__(self, pr, precision="fp64", riemann=None, eps_sf=None, cfl=None, rk=3, wb=True,
                  stream=None, mach_thr=None, eos_table=None, newton_tol=1e-11, newton_maxit=50, mlp=None,
-                 mlp_mode=1, _handle=None):
+                 mlp_mode=2, _handle=None):
         self.pr = pr
         self.eos_table = eos_table
         self.mlp = mlp
