@@ -50,7 +50,7 @@ FP64_NOMINAL_TFLOPS = 1.25     # GB300 FP64 (profiling recipe's nominal table)
 BYTES_PER_CELL_STAGE = {1: 128.0, 2: 192.0, 3: 192.0}
 # FP64 flux kernel: FP64 operations per face (DADD + DMUL + 2 DFMA counted from
 # the ncu SASS counters of k_flux on the stratified box at 64^3, mean of the
-# three directions; profiles/fp64_stage_stratified_box_256.md).
+# three directions).
 FP64_FLOP_PER_FACE = 637.7
 # Mixed flux kernel: FP32 operations per face (FADD + FMUL + 2 FFMA from the ncu
 # SASS counters of k_flux<0/1/2, float> on the stratified box at 160^3, per sweep
