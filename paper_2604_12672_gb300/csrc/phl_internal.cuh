@@ -228,6 +228,22 @@ __device__ __forceinline__ double f2d_scaled(float f, int k) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// Exact division by a runtime divisor d for numerators below 2^31: with
+// s = ceil(log2 d) and m = floor(2^(32+s) / d) + 1 (< 2^33), t / d equals
+// (t * m) >> (32 + s) -- one wide multiply instead of an integer division.
+struct FastDiv {
+  unsigned long long m;
+  unsigned s, d;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  unsigned s = 0;
+  while ((1ull << s) < d) ++s;
+  return FastDiv{((1ull << (32 + s)) / d) + 1ull, s, d};
+}
+__device__ __forceinline__ unsigned fastdiv(unsigned t, const FastDiv &f) {
+  return (unsigned)(((unsigned long long)t * f.m) >> (32 + f.s));
+}
+
 // Kernel classes for the optional per-kernel event timing.
 enum KClass {
   KC_PRIM = 0, KC_FLAG_RAW, KC_FLAG_DILATE, KC_FLUX_X, KC_FLUX_Y, KC_FLUX_Z, KC_EMF, KC_UPDATE_CELLS,

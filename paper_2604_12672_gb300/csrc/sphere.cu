@@ -363,6 +363,7 @@ struct SphDev {
   const unsigned char *vcnt;
   const double *rho_c, *p_c, *rho_f, *p_f, *g_c, *heat;   // null when absent
   const double *eh_c;          // P_hat / (gamma - 1) per shell (null without a background)
+  FastDiv dNC, dNS, dNV;       // divisions of flat indices (all below 2^31) by NC, NS, NV
   // FP32 copies for the mixed form: geometry, per-radius factors, background
   const float *vd_f, *sn_f, *sl_f, *smid_f, *sth_f, *cdc_f, *cna_f, *cva_f;
   const float *iom_f;          // 1 / Omega per angular cell
@@ -376,8 +377,10 @@ struct SphDev {
 // work arrays of one form (R = double: FP64, float: mixed)
 template <typename R>
 struct SphWork {
-  R *W;             // 8 deviations per cell, SoA
-  R *FC, *EF;       // 5 integrated fluxes, 3 face-EMF components per face, SoA
+  R *W;             // 8 deviations per cell: FP64 SoA; mixed two float4 per cell
+                    // ((drho, u), (B, dP)), one 16-byte load each
+  R *FC, *EF;       // 5 integrated fluxes per face, SoA; face EMF: FP64 3 SoA
+                    // components, mixed one float4 per face (E, contact sign)
   double *EE;       // edge EMF line integrals L (E . l), FP64 in both forms
   signed char *UP;  // contact direction per face
 };
@@ -418,7 +421,7 @@ __device__ __forceinline__ double cell_vol(const SphDev &D, long a, int k) {
 __global__ void k_sph_prims(SphDev D, SphWork<double> Wk, const double *__restrict__ U, const double *__restrict__ phi) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= D.ncell) return;
-  const int k = (int)(c / D.NC);
+  const int k = (int)fastdiv((unsigned)c, D.dNC);
   const long a = c - (long)k * D.NC;
   CellFaces F;
   cell_faces(D, a, k, F);
@@ -474,7 +477,7 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_mx(SphDev D, SphWork<float> W
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   float rate = 0.f;
   if (c < D.ncell) {
-    const int k = (int)(c / D.NC);
+    const int k = (int)fastdiv((unsigned)c, D.dNC);
     const long a = c - (long)k * D.NC, n = D.ncell;
     const float rm = D.rm_f[k];
     float bx = 0.f, by = 0.f, bz = 0.f;
@@ -488,9 +491,10 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_mx(SphDev D, SphWork<float> W
     bx += D.cdc_f[3 * a] * wr; by += D.cdc_f[3 * a + 1] * wr; bz += D.cdc_f[3 * a + 2] * wr;
     const float iv = D.iom_f[a] * D.ish_f[k];
     bx *= iv; by *= iv; bz *= iv;
-    float drho = (float)(D.rho_c ? U[c] - D.rho_c[k] : U[c]);
-    float dE = (float)(D.eh_c ? U[4 * n + c] - D.eh_c[k] : U[4 * n + c]);
-    float mx = (float)U[n + c], my = (float)U[2 * n + c], mz = (float)U[3 * n + c];
+    // FP64 -> FP32 on the integer pipe (d2f_scaled): GB300 converts at the FP64 rate
+    float drho = d2f_scaled(D.rho_c ? U[c] - D.rho_c[k] : U[c], 0);
+    float dE = d2f_scaled(D.eh_c ? U[4 * n + c] - D.eh_c[k] : U[4 * n + c], 0);
+    float mx = d2f_scaled(U[n + c], 0), my = d2f_scaled(U[2 * n + c], 0), mz = d2f_scaled(U[3 * n + c], 0);
     if (dU) {
       drho += dU[c]; dE += dU[4 * n + c];
       mx += dU[n + c]; my += dU[2 * n + c]; mz += dU[3 * n + c];
@@ -503,10 +507,9 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_mx(SphDev D, SphWork<float> W
     const float P = pb + dP;
     if (!(rho > 0.f) || !(P > 0.f)) atomicOr(D.dflag, FLAG_NEG);
     if (!isfinite(rho) || !isfinite(P)) atomicOr(D.dflag, FLAG_NAN);
-    Wk.W[SW_RHO * n + c] = drho;
-    Wk.W[(SW_U + 0) * n + c] = ux; Wk.W[(SW_U + 1) * n + c] = uy; Wk.W[(SW_U + 2) * n + c] = uz;
-    Wk.W[(SW_B + 0) * n + c] = bx; Wk.W[(SW_B + 1) * n + c] = by; Wk.W[(SW_B + 2) * n + c] = bz;
-    Wk.W[SW_P * n + c] = dP;
+    float4 *W4 = reinterpret_cast<float4 *>(Wk.W);
+    W4[2 * c] = make_float4(drho, ux, uy, uz);
+    W4[2 * c + 1] = make_float4(bx, by, bz, dP);
     if (dmax) {
       rate = cfl_rate_mx(D, a, k, rho, P, ux, uy, uz, bx, by, bz);
       if (!(rate == rate)) rate = INFINITY;
@@ -529,8 +532,14 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_mx(SphDev D, SphWork<float> W
 template <typename R>
 __device__ __forceinline__ void load_w(const SphDev &D, const SphWork<R> &Wk, long c, bool mir, R nx, R ny, R nz,
                                        R *w) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 *W4 = reinterpret_cast<const float4 *>(Wk.W);
+    const float4 a = W4[2 * c], b = W4[2 * c + 1];
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+  } else {
 #pragma unroll
-  for (int v = 0; v < SW_N; ++v) w[v] = Wk.W[v * D.ncell + c];
+    for (int v = 0; v < SW_N; ++v) w[v] = Wk.W[v * D.ncell + c];
+  }
   if (mir) {
     const R un = R(2) * (w[SW_U] * nx + w[SW_U + 1] * ny + w[SW_U + 2] * nz);
     const R bn = R(2) * (w[SW_B] * nx + w[SW_B + 1] * ny + w[SW_B + 2] * nz);
@@ -556,7 +565,7 @@ __global__ void __launch_bounds__(SPT) k_sph_flux(SphDev D, SphWork<R> Wk, const
   R n0, n1, n2, A, brho = R(0), bp = R(0);
   bool wall = false;
   if (f < D.FA) {   // angular face (s, k)
-    const int k = (int)(f / D.NS);
+    const int k = (int)fastdiv((unsigned)f, D.dNS);
     const long s = f - (long)k * D.NS, base = (long)k * D.NC;
     load_w<R>(D, Wk, base + D.sL[s], false, R(0), R(0), R(0), wL);
     load_w<R>(D, Wk, base + D.sR[s], false, R(0), R(0), R(0), wR);
@@ -574,7 +583,7 @@ __global__ void __launch_bounds__(SPT) k_sph_flux(SphDev D, SphWork<R> Wk, const
     }
   } else {          // radial face (a, k)
     const long q = f - D.FA;
-    const int k = (int)(q / D.NC), Nr = D.Nr;
+    const int k = (int)fastdiv((unsigned)q, D.dNC), Nr = D.Nr;
     const long a = q - (long)k * D.NC;
     if constexpr (MX) {
       n0 = D.cna_f[3 * a]; n1 = D.cna_f[3 * a + 1]; n2 = D.cna_f[3 * a + 2];
@@ -668,21 +677,38 @@ __global__ void __launch_bounds__(SPT) k_sph_flux(SphDev D, SphWork<R> Wk, const
   // E_f = -n x F_B with F_B = t1 F_bt1 + t2 F_bt2
   const R fbx = t1x * fl[RF_BT1] + t2x * fl[RF_BT2], fby = t1y * fl[RF_BT1] + t2y * fl[RF_BT2],
           fbz = t1z * fl[RF_BT1] + t2z * fl[RF_BT2];
-  Wk.EF[f] = -(n1 * fbz - n2 * fby);
-  Wk.EF[nf + f] = -(n2 * fbx - n0 * fbz);
-  Wk.EF[2 * nf + f] = -(n0 * fby - n1 * fbx);
-  Wk.UP[f] = (signed char)up;
+  const R ex = -(n1 * fbz - n2 * fby), ey = -(n2 * fbx - n0 * fbz), ez = -(n0 * fby - n1 * fbx);
+  if constexpr (sizeof(R) == 4) {
+    reinterpret_cast<float4 *>(Wk.EF)[f] = make_float4(ex, ey, ez, (float)up);
+  } else {
+    Wk.EF[f] = ex; Wk.EF[nf + f] = ey; Wk.EF[2 * nf + f] = ez;
+    Wk.UP[f] = (signed char)up;
+  }
 }
 
 template <typename R>
-__device__ __forceinline__ R efl(const SphDev &D, const SphWork<R> &Wk, long f, R lx, R ly, R lz) {
-  return Wk.EF[f] * lx + Wk.EF[D.NF + f] * ly + Wk.EF[2 * D.NF + f] * lz;
+__device__ __forceinline__ R efl(const SphDev &D, const SphWork<R> &Wk, long f, R lx, R ly, R lz, int &up) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 e = reinterpret_cast<const float4 *>(Wk.EF)[f];
+    up = (int)e.w;
+    return e.x * lx + e.y * ly + e.z * lz;
+  } else {
+    up = Wk.UP[f];
+    return Wk.EF[f] * lx + Wk.EF[D.NF + f] * ly + Wk.EF[2 * D.NF + f] * lz;
+  }
 }
 template <typename R>
 __device__ __forceinline__ R ecl(const SphDev &D, const SphWork<R> &Wk, long c, R lx, R ly, R lz) {   // (-u x B) . l
-  const long n = D.ncell;
-  const R ux = Wk.W[SW_U * n + c], uy = Wk.W[(SW_U + 1) * n + c], uz = Wk.W[(SW_U + 2) * n + c];
-  const R bx = Wk.W[SW_B * n + c], by = Wk.W[(SW_B + 1) * n + c], bz = Wk.W[(SW_B + 2) * n + c];
+  R ux, uy, uz, bx, by, bz;
+  if constexpr (sizeof(R) == 4) {
+    const float4 *W4 = reinterpret_cast<const float4 *>(Wk.W);
+    const float4 a = W4[2 * c], b = W4[2 * c + 1];
+    ux = a.y; uy = a.z; uz = a.w; bx = b.x; by = b.y; bz = b.z;
+  } else {
+    const long n = D.ncell;
+    ux = Wk.W[SW_U * n + c]; uy = Wk.W[(SW_U + 1) * n + c]; uz = Wk.W[(SW_U + 2) * n + c];
+    bx = Wk.W[SW_B * n + c]; by = Wk.W[(SW_B + 1) * n + c]; bz = Wk.W[(SW_B + 2) * n + c];
+  }
   return -((uy * bz - uz * by) * lx + (uz * bx - ux * bz) * ly + (ux * by - uy * bx) * lz);
 }
 
@@ -711,7 +737,7 @@ __global__ void __launch_bounds__(SPT) k_sph_emf(SphDev D, SphWork<R> Wk) {
   int ms[4];
   double L;   // the edge's length: r1 - r0 (radial), r theta (angular)
   if (e < D.ER) {   // radial edge (v, k)
-    const int k = (int)(e / D.NV);
+    const int k = (int)fastdiv((unsigned)e, D.dNV);
     const long v = e - (long)k * D.NV, fb = (long)k * D.NS, cb = (long)k * D.NC;
     L = D.r[k + 1] - D.r[k];
     const R lx = MX ? (R)D.vd_f[3 * v] : (R)D.vd[3 * v];
@@ -719,20 +745,22 @@ __global__ void __launch_bounds__(SPT) k_sph_emf(SphDev D, SphWork<R> Wk) {
     const R lz = MX ? (R)D.vd_f[3 * v + 2] : (R)D.vd[3 * v + 2];
     if (D.vcnt[v] == 3) {   // a cube corner: the mean of the three face EMFs
       R t = R(0);
-      for (int m = 0; m < 3; ++m) t += efl<R>(D, Wk, fb + D.vside[4 * v + m], lx, ly, lz);
-      Wk.EE[e] = L * (double)(t / R(3));
+      int u3;
+      for (int m = 0; m < 3; ++m) t += efl<R>(D, Wk, fb + D.vside[4 * v + m], lx, ly, lz, u3);
+      Wk.EE[e] = L * (sizeof(R) == 4 ? f2d_scaled((float)(t / R(3)), 0) : (double)(t / R(3)));
       return;
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const long f = fb + D.vside[4 * v + m];
       Ec[m] = ecl<R>(D, Wk, cb + D.vcell[4 * v + m], lx, ly, lz);
-      Ef[m] = efl<R>(D, Wk, f, lx, ly, lz);
-      ms[m] = D.vsgn[4 * v + m] * Wk.UP[f];
+      int u;
+      Ef[m] = efl<R>(D, Wk, f, lx, ly, lz, u);
+      ms[m] = D.vsgn[4 * v + m] * u;
     }
   } else {          // angular edge (s, k); none on a wall
     const long q = e - D.ER;
-    const int k = (int)(q / D.NS);
+    const int k = (int)fastdiv((unsigned)q, D.dNS);
     const long s = q - (long)k * D.NS;
     if (k == 0 || k == D.Nr) { Wk.EE[e] = 0.0; return; }
     L = D.r[k] * D.sth[s];
@@ -754,11 +782,11 @@ __global__ void __launch_bounds__(SPT) k_sph_emf(SphDev D, SphWork<R> Wk) {
 #pragma unroll
     for (int m = 0; m < 4; ++m) {   // every face's -n cell is its from-cell here
       Ec[m] = ecl<R>(D, Wk, cc[m], lx, ly, lz);
-      Ef[m] = efl<R>(D, Wk, ff[m], lx, ly, lz);
-      ms[m] = Wk.UP[ff[m]];
+      Ef[m] = efl<R>(D, Wk, ff[m], lx, ly, lz, ms[m]);
     }
   }
-  Wk.EE[e] = L * (double)contact_ct<R>(Ec, Ef, ms);
+  const R ect = contact_ct<R>(Ec, Ef, ms);
+  Wk.EE[e] = L * (sizeof(R) == 4 ? f2d_scaled((float)ect, 0) : (double)ect);
 }
 
 // FP64: out = a base + b (in - dt R), R = (1/V) sum_f s_f F_f - S
@@ -766,7 +794,7 @@ __global__ void k_sph_update_cells(SphDev D, SphWork<double> Wk, const double *U
                                    double a, double b, const double *__restrict__ dtp) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= D.ncell) return;
-  const int k = (int)(c / D.NC);
+  const int k = (int)fastdiv((unsigned)c, D.dNC);
   const long an = c - (long)k * D.NC, nc = D.ncell, nf = D.NF;
   CellFaces F;
   cell_faces(D, an, k, F);
@@ -800,7 +828,7 @@ __global__ void __launch_bounds__(SPT) k_sph_update_cells_mx(SphDev D, SphWork<f
                                                              int last) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (c >= D.ncell) return;
-  const int k = (int)(c / D.NC);
+  const int k = (int)fastdiv((unsigned)c, D.dNC);
   const long an = c - (long)k * D.NC, nc = D.ncell, nf = D.NF;
   float du[5];
 #pragma unroll
@@ -823,8 +851,9 @@ __global__ void __launch_bounds__(SPT) k_sph_update_cells_mx(SphDev D, SphWork<f
 #pragma unroll
   for (int v = 0; v < 5; ++v) r[v] *= iv;
   // sources of the stage input: (rho - rho_hat) g and rho u . g, heating
-  const float drho = (float)(D.rho_c ? U[c] - D.rho_c[k] : U[c]) + du[0];
-  const float mx = (float)U[nc + c] + du[1], my = (float)U[2 * nc + c] + du[2], mz = (float)U[3 * nc + c] + du[3];
+  const float drho = d2f_scaled(D.rho_c ? U[c] - D.rho_c[k] : U[c], 0) + du[0];
+  const float mx = d2f_scaled(U[nc + c], 0) + du[1], my = d2f_scaled(U[2 * nc + c], 0) + du[2],
+              mz = d2f_scaled(U[3 * nc + c], 0) + du[3];
   const float g = D.g_cf ? D.g_cf[k] : 0.f;
   const float gx = -g * D.cdc_f[3 * an], gy = -g * D.cdc_f[3 * an + 1], gz = -g * D.cdc_f[3 * an + 2];
   r[1] -= drho * gx; r[2] -= drho * gy; r[3] -= drho * gz;
@@ -837,7 +866,7 @@ __global__ void __launch_bounds__(SPT) k_sph_update_cells_mx(SphDev D, SphWork<f
   for (int v = 0; v < 5; ++v) o[v] = b * (du[v] - dt * r[v]);
   if (last) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) U[v * nc + c] += (double)o[v];
+    for (int v = 0; v < 5; ++v) U[v * nc + c] += f2d_scaled(o[v], 0);
   } else {
 #pragma unroll
     for (int v = 0; v < 5; ++v) dUout[v * nc + c] = o[v];
@@ -855,7 +884,7 @@ __device__ __forceinline__ double sgn_mul(signed char s, double x) {
 
 __device__ __forceinline__ double circulation(const SphDev &D, const double *__restrict__ EE, long f) {
   if (f < D.FA) {   // angular face (s, k): edges (s, k), (v1, k), (s, k+1), (v0, k)
-    const int k = (int)(f / D.NS);
+    const int k = (int)fastdiv((unsigned)f, D.dNS);
     const long s = f - (long)k * D.NS;
     const signed char si = D.s_in[s];
     const double ein = sgn_mul(si, EE[D.ER + (long)k * D.NS + s]);
@@ -865,7 +894,7 @@ __device__ __forceinline__ double circulation(const SphDev &D, const double *__r
     return ((ein + eout) + e1) + e0;
   }
   const long q = f - D.FA;   // radial face (a, k): the angular edges (s_m, k)
-  const int k = (int)(q / D.NC);
+  const int k = (int)fastdiv((unsigned)q, D.dNC);
   const long an = q - (long)k * D.NC, eb = D.ER + (long)k * D.NS;
   double e[4];
 #pragma unroll
@@ -881,9 +910,10 @@ __global__ void __launch_bounds__(SPT) k_sph_update_faces(SphDev D, const double
   const long f = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (f >= D.NF) return;
   const double t = circulation(D, EE, f);
-  const double o = a * pbase[f] + b * (pin[f] - *dtp * t);
+  // the first stage (a = 0, b = 1) is in - dt circulation: one FMA
+  const double o = a == 0.0 && b == 1.0 ? fma(-*dtp, t, pin[f]) : a * pbase[f] + b * (pin[f] - *dtp * t);
   pout[f] = o;
-  if (phif) phif[f] = (float)o;
+  if (phif) phif[f] = d2f_scaled(o, 0);
 }
 
 __global__ void k_sph_dt(SphDev D, SphWork<double> Wk, unsigned long long *dmax) {
@@ -891,7 +921,7 @@ __global__ void k_sph_dt(SphDev D, SphWork<double> Wk, unsigned long long *dmax)
   double m = 0.0;
   if (c < D.ncell) {
     const long n = D.ncell;
-    const int k = (int)(c / D.NC);
+    const int k = (int)fastdiv((unsigned)c, D.dNC);
     const long a = c - (long)k * D.NC;
     const double rho = Wk.W[SW_RHO * n + c] + bg_rho(D, k);
     const double P = Wk.W[SW_P * n + c] + bg_p(D, k);
@@ -1058,9 +1088,9 @@ cudaError_t alloc_work(phl_sphere *S, SphWork<R> &Wk) {
   const SphDev &D = S->D;
   cudaError_t e = alloc_n(S, &Wk.W, SW_N * D.ncell);
   if (e == cudaSuccess) e = alloc_n(S, &Wk.FC, 5 * D.NF);
-  if (e == cudaSuccess) e = alloc_n(S, &Wk.EF, 3 * D.NF);
+  if (e == cudaSuccess) e = alloc_n(S, &Wk.EF, (sizeof(R) == 4 ? 4 : 3) * D.NF);
   if (e == cudaSuccess) e = alloc_n(S, &Wk.EE, D.NE);
-  if (e == cudaSuccess) e = alloc_n(S, &Wk.UP, D.NF);
+  if (e == cudaSuccess) e = alloc_n(S, &Wk.UP, sizeof(R) == 4 ? 1 : D.NF);
   return e;
 }
 
@@ -1142,6 +1172,7 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
   D.ER = M.NV * Nr;
   D.NE = D.ER + M.NS * (Nr + 1);
   D.gamma = d->gamma; D.cfl = d->cfl; D.mach = d->mach_thr; D.riemann = d->riemann;
+  D.dNC = make_fastdiv((unsigned)D.NC); D.dNS = make_fastdiv((unsigned)D.NS); D.dNV = make_fastdiv((unsigned)D.NV);
   D.gf = (float)d->gamma; D.gm1f = (float)(d->gamma - 1.0); D.igm1f = (float)(1.0 / (d->gamma - 1.0));
   D.ggm1f = (float)(d->gamma / (d->gamma - 1.0)); D.machf = (float)d->mach_thr;
   std::vector<double> r(Nr + 1);

@@ -21,22 +21,6 @@ constexpr int TPB = 256;
     if (prof) (prof)->end(s);                \
   } while (0)
 
-// Exact division by a runtime divisor d for numerators below 2^31: with
-// s = ceil(log2 d) and m = floor(2^(32+s) / d) + 1 (< 2^33), t / d equals
-// (t * m) >> (32 + s) -- one wide multiply instead of an integer division.
-struct FastDiv {
-  unsigned long long m;
-  unsigned s, d;
-};
-inline FastDiv make_fastdiv(unsigned d) {
-  unsigned s = 0;
-  while ((1ull << s) < d) ++s;
-  return FastDiv{((1ull << (32 + s)) / d) + 1ull, s, d};
-}
-__device__ __forceinline__ unsigned fastdiv(unsigned t, const FastDiv &f) {
-  return (unsigned)(((unsigned long long)t * f.m) >> (32 + f.s));
-}
-
 struct Box {
   int lo[3], hi[3];
   long n;
