@@ -692,7 +692,8 @@ def ensemble_c4(P, steps, warmup, stream, ws):
                         "mixed form", "boxes": [list(p.n) for p in probs], "cells": cells,
             "value": cells * STAGES * steps * ws / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
             "launch_shape": {"mode": ["persistent stage kernel", "one launch per phase",
-                                      "per-box kernel chains on concurrent streams"][info["mode"]],
+                                      "per-box kernel chains on concurrent streams",
+                                      "persistent stage kernel on the fused tiles"][info["mode"]],
                              "block": info["block"], "blocks_per_sm": info["blocks_per_sm"],
                              "streams": info["streams"]},
             "graph": info["graph"], "launches_per_step": info["launches_per_step"],
@@ -830,6 +831,7 @@ def main():
                     help="only the stellar-EOS box (its JSON object alone, for profiling)")
     ap.add_argument("--no-c4", action="store_true", help="skip the 24-box ensemble")
     ap.add_argument("--c4-steps", type=int, default=5)
+    ap.add_argument("--c4-only", action="store_true", help="only the 24-box ensemble (its JSON object alone)")
     ap.add_argument("--no-c5", action="store_true", help="skip the cubed-sphere shell")
     ap.add_argument("--c5-steps", type=int, default=2, help="cubed sphere: timed FP64 steps")
     ap.add_argument("--c5-steps-mixed", type=int, default=5, help="cubed sphere: timed mixed steps")
@@ -858,6 +860,11 @@ def main():
     if args.poisson_only:
         if rank == 0:
             print(json.dumps(poisson_sphere(P, args.n, stream, hbm_peak, peak_kind)))
+        return 0
+    if args.c4_only:
+        c4 = ensemble_c4(P, args.c4_steps, 2, stream, ws)
+        if rank == 0:
+            print(json.dumps(c4))
         return 0
     if args.c5_only:
         if rank == 0:

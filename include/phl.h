@@ -466,17 +466,25 @@ phl_status phl_mlp_train(phl_mlp *m, const phl_eos_table *t, const phl_mlp_train
  * grid-wide barriers); the step's three launches are captured as one CUDA
  * graph and replayed.  Alternatively each phase of a stage is its own launch
  * over all boxes (mode 1), or each box runs its own chain of per-kernel
- * launches on one of several concurrent streams (mode 2); the step is one
- * graph in every mode.  The mode and launch shape are chosen by
- * phl_ensemble_autotune or set explicitly. */
+ * launches on one of several concurrent streams (mode 2); or (mode 3) one
+ * persistent cooperative launch per stage runs the fused tile stage over a
+ * list of every box's 8^3 tiles, each tile staged by TMA from its box's own
+ * tensor map (primitives, raw shock flags, tiles with the flag dilation, edge
+ * EMFs and face updates as phases between grid-wide barriers; offered when
+ * every box runs the fused stage).  The step is one graph in every mode.
+ * The mode and launch shape are chosen by phl_ensemble_autotune or set
+ * explicitly. */
 typedef struct phl_ensemble phl_ensemble;
 
 typedef struct {
   int mode;                 /* 0: persistent stage kernel; 1: one launch per     */
                             /* phase of the stage (all boxes per launch); 2:     */
-                            /* each box's own kernel chain, concurrent streams  */
-  int block;                /* threads per block (128 or 256; modes 0, 1)       */
-  int blocks_per_sm;        /* mode 0: persistent blocks per SM                 */
+                            /* each box's own kernel chain, concurrent streams; */
+                            /* 3: persistent stage kernel on the fused tiles    */
+  int block;                /* threads per block (128 or 256; modes 0, 1; 288   */
+                            /* in mode 3)                                        */
+  int blocks_per_sm;        /* modes 0, 3: persistent blocks per SM (mode 3:    */
+                            /* fixed by its occupancy)                           */
   int streams;              /* mode 2: concurrent streams                       */
   double ms_per_step;       /* measured (autotune)                              */
 } phl_tune_entry;

@@ -193,7 +193,10 @@ struct phl_ensemble {
   long cells = 0;
   cudaStream_t stream = nullptr;
   int mode = 0;                      // 0: persistent cooperative stage kernel, 1: one launch per phase,
-                                     // 2: each box's own kernel chain, boxes on concurrent streams
+                                     // 2: each box's own kernel chain, boxes on concurrent streams,
+                                     // 3: persistent cooperative stage kernel on the fused tile body
+  EnsFused fz;                       // mode 3's records (fz_ok: every box fused-eligible)
+  bool fz_ok = false;
   int nstreams = 0;                  // mode 2
   int chain_launches = 0;            // mode 2: kernel launches per step
   std::vector<cudaStream_t> aux;     // mode 2 streams
@@ -314,6 +317,13 @@ cudaError_t launch_step_chains(phl_ensemble *E) {
 cudaError_t launch_step(phl_ensemble *E) {
   static const float b3[3] = {1.0f, 0.25f, 2.0f / 3.0f};
   if (E->mode == 2) return launch_step_chains(E);
+  if (E->mode == 3) {
+    for (int st = 0; st < 3; ++st) {
+      const cudaError_t e = launch_ens_fused(E->fz, st, 3, b3[st], E->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   for (int st = 0; st < 3; ++st) {
     cudaError_t e = E->mode == 0 ? launch_stage(E, st, 3, b3[st]) : launch_stage_phases(E, st, 3, b3[st]);
     if (e != cudaSuccess) return e;
@@ -474,6 +484,19 @@ phl_status phl_ensemble_create(const phl_grid_desc *descs, int nbox, int use_gra
   }
   E->block = 256;
   E->bps = E->max_bps[1];
+  {   // mode 3 when every box runs the fused stage
+    std::vector<GridView> views;
+    bool ok = true;
+    for (phl_grid *g : E->grids) {
+      views.push_back(grid_view(g));
+      ok = ok && views.back().tmapW != nullptr;
+    }
+    if (ok) {
+      const cudaError_t ef = ens_fused_create(views.data(), nbox, &E->fz);
+      E->fz_ok = ef == cudaSuccess;
+      if (!E->fz_ok) cudaGetLastError();
+    }
+  }
   *out = E;
   return PHL_OK;
 }
@@ -510,14 +533,16 @@ phl_status phl_ensemble_check(phl_ensemble *E) {
 
 phl_status phl_ensemble_set_shape(phl_ensemble *E, int mode, int block, int blocks_per_sm, int streams) {
   if (!E) return ens_fail(PHL_EINVAL, "null ensemble");
-  if (mode < 0 || mode > 2) return ens_fail(PHL_EINVAL, "mode must be 0 (persistent), 1 (phases) or 2 (chains)");
-  if (mode != 2 && block != 128 && block != 256) return ens_fail(PHL_EINVAL, "block must be 128 or 256");
+  if (mode < 0 || mode > 3)
+    return ens_fail(PHL_EINVAL, "mode must be 0 (persistent), 1 (phases), 2 (chains) or 3 (persistent fused)");
+  if (mode == 3 && !E->fz_ok) return ens_fail(PHL_EUNSUPPORTED, "mode 3 needs every box on the fused stage");
+  if (mode < 2 && block != 128 && block != 256) return ens_fail(PHL_EINVAL, "block must be 128 or 256");
   if (mode == 0 && (blocks_per_sm < 1 || blocks_per_sm > E->max_bps[block == 128 ? 0 : 1]))
     return ens_fail(PHL_EINVAL, "blocks per SM out of the co-resident range");
   if (mode == 2 && (streams < 1 || streams > 64)) return ens_fail(PHL_EINVAL, "streams must be 1..64");
   E->mode = mode;
-  E->block = mode == 2 ? 256 : block;
-  E->bps = mode == 0 ? blocks_per_sm : 0;
+  E->block = mode == 2 ? 256 : (mode == 3 ? 288 : block);
+  E->bps = mode == 0 ? blocks_per_sm : (mode == 3 ? E->fz.per_sm : 0);
   E->nstreams = mode == 2 ? streams : 0;
   drop_graph(E);
   return PHL_OK;
@@ -559,6 +584,11 @@ phl_status phl_ensemble_autotune(phl_ensemble *E, int trial_steps, phl_tune_entr
       c.mode = 0; c.blocks_per_sm = p;
       cand.push_back(c);
     }
+  }
+  if (E->fz_ok) {
+    phl_tune_entry c;
+    c.mode = 3; c.block = 288; c.blocks_per_sm = E->fz.per_sm; c.streams = 0; c.ms_per_step = 0.0;
+    cand.push_back(c);
   }
   for (int ns : {1, 4, 8, E->nbox}) {
     phl_tune_entry c;
@@ -623,7 +653,7 @@ phl_status phl_ensemble_get_info(const phl_ensemble *E, phl_ensemble_info *info)
   info->blocks_per_sm = E->bps;
   info->streams = E->nstreams;
   info->graph = E->graph_ok;
-  int nl = 3;
+  int nl = 3;   // modes 0 and 3: one launch per stage
   if (E->mode == 2) {
     nl = E->chain_launches;
   } else if (E->mode == 1) {
@@ -646,6 +676,7 @@ void phl_ensemble_destroy(phl_ensemble *E) {
   for (phl_grid *g : E->grids) phl_destroy(g);
   cudaFree(E->drec);
   cudaFree(E->dpref);
+  ens_fused_destroy(&E->fz);
   if (E->own_stream) cudaStreamDestroy(E->own_stream);
   delete E;
 }

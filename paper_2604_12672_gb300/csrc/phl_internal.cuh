@@ -356,6 +356,20 @@ struct GridView {
 };
 GridView grid_view(::phl_grid *g);
 
+// Boxes of an ensemble stepped by one persistent cooperative launch per RK
+// stage on the fused tile body (stage_fused.cu); every box fused-eligible and
+// with the same reconstruction.
+struct EnsFused {
+  void *boxes = nullptr;   // device records, one per box
+  void *tmaps = nullptr;   // the boxes' W tensor maps (device memory)
+  long *pref = nullptr;    // the phases' prefix sums of work items
+  int nbox = 0, blocks = 0, per_sm = 0;
+  bool pph = false;
+};
+cudaError_t ens_fused_create(const GridView *views, int nbox, EnsFused *out);
+void ens_fused_destroy(EnsFused *e);
+cudaError_t launch_ens_fused(const EnsFused &E, int stage, int nstages, float b, cudaStream_t s);
+
 // Stellar EOS path (kernels_stellar.cu)
 // cfl_dmax non-null: also the CFL step of this state into *dt (the step's
 // first stage; cfl_dmax is the grid's double-bits maximum, left at zero).

@@ -18,9 +18,12 @@
 // fluxes never round-trip through HBM, each face costs shared-memory loads
 // instead of global gathers with ghost remapping, and the only per-face global
 // traffic left is the normal field, two flag bytes and three EMF inputs.
+#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <math.h>
+
+#include <vector>
 
 #include "mixed_common.cuh"
 #include "riemann_x2.cuh"
@@ -386,31 +389,23 @@ __device__ __forceinline__ void tile_phase(const DevGeo &G, const StageMx &S, Fu
   __syncthreads();
 }
 
-// Tile kernel.  PHASED = false: all faces of the tile are evaluated in one
-// loop and kept in shared memory (5 x NFACE floats), then every cell sums its
-// six faces.  PHASED = true: one direction at a time through a buffer of one
-// direction's faces; each thread keeps the running residuals of its cells in
-// registers (same summation order x, y, z), so the CTA needs ~1/3 of the
-// shared memory and more CTAs fit on an SM.
-template <int NT, int MINB, bool PHASED, bool PAIRED = false, bool LR = false, bool PPH = false>
-__global__ void __launch_bounds__(NT, MINB)
-    k_flux_update_mx(const __grid_constant__ CUtensorMap tmW, DevGeo G, StageMx S, const uint8_t *__restrict__ flag,
-                     float *__restrict__ F0, float *__restrict__ F1, float *__restrict__ F2, int ntx, int nty,
-                     int *dflag, unsigned extra_tx, int raw_flags) {
-  extern __shared__ unsigned char smraw[];
-  FusedSmem &sm = *reinterpret_cast<FusedSmem *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
+// The work of one tile with lower corner (x0, y0, z0).  PHASED = false: all
+// faces of the tile are evaluated in one loop and kept in shared memory
+// (5 x NFACE floats), then every cell sums its six faces.  PHASED = true: one
+// direction at a time through a buffer of one direction's faces; each thread
+// keeps the running residuals of its cells in registers (same summation order
+// x, y, z), so the CTA needs ~1/3 of the shared memory and more CTAs fit on
+// an SM.  The TMA copy completes on the CTA's barrier sm.bar, whose phase of
+// this use is `parity`.  Returns false when the copy did not land within the
+// bounded wait (the error bit set, the copy waited for once more).
+template <int NT, bool PHASED, bool PAIRED, bool LR, bool PPH>
+__device__ __forceinline__ bool tile_body(const CUtensorMap *tmW, const DevGeo &G, const StageMx &S,
+                                          const uint8_t *__restrict__ flag, float *__restrict__ F0,
+                                          float *__restrict__ F1, float *__restrict__ F2, int x0, int y0, int z0,
+                                          int *dflag, unsigned extra_tx, int raw_flags, FusedSmem &sm,
+                                          unsigned parity) {
   const int tid = threadIdx.x;
-  int t = blockIdx.x;
-  const int tx = t % ntx;
-  t /= ntx;
-  const int ty = t % nty, tz = t / nty;
-  const int x0 = tx * FX, y0 = ty * FY, z0 = tz * FZ;
   const unsigned bar = smem_u32(&sm.bar);
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
   if (tid == 0) {
     // extra_tx is 0 except in the timeout test (bytes that never arrive)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(W_TILE_BYTES + extra_tx)
@@ -419,7 +414,7 @@ __global__ void __launch_bounds__(NT, MINB)
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(&sm.w[0][0])),
-        "l"((unsigned long long)&tmW), "r"(4 * x0), "r"(y0), "r"(z0), "r"(0), "r"(bar)
+        "l"((unsigned long long)tmW), "r"(4 * x0), "r"(y0), "r"(z0), "r"(0), "r"(bar)
         : "memory");
   }
   // while the copy is in flight: the tile's background profiles and the
@@ -523,11 +518,11 @@ __global__ void __launch_bounds__(NT, MINB)
       (&sm.flg[0][0][0])[q] = v;
     }
   }
-  const bool ok = mbar_wait_bounded(bar, 0u, 1000000000ull);
+  const bool ok = mbar_wait_bounded(bar, parity, 1000000000ull);
   if (__syncthreads_or(!ok)) {   // the copy did not land in 1 s: report, let it finish, leave
     if (tid == 0) atomicOr(dflag, FLAG_TIMEOUT);
-    mbar_wait_bounded(bar, 0u, 1000000000ull);
-    return;
+    mbar_wait_bounded(bar, parity, 1000000000ull);
+    return false;
   }
 
   GasK<float> K;
@@ -613,6 +608,29 @@ __global__ void __launch_bounds__(NT, MINB)
       else S.dU[q] = dout;
     }
   }
+  return true;
+}
+
+// Tile kernel: one CTA per tile.
+template <int NT, int MINB, bool PHASED, bool PAIRED = false, bool LR = false, bool PPH = false>
+__global__ void __launch_bounds__(NT, MINB)
+    k_flux_update_mx(const __grid_constant__ CUtensorMap tmW, DevGeo G, StageMx S, const uint8_t *__restrict__ flag,
+                     float *__restrict__ F0, float *__restrict__ F1, float *__restrict__ F2, int ntx, int nty,
+                     int *dflag, unsigned extra_tx, int raw_flags) {
+  extern __shared__ unsigned char smraw[];
+  FusedSmem &sm = *reinterpret_cast<FusedSmem *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
+  int t = blockIdx.x;
+  const int tx = t % ntx;
+  t /= ntx;
+  const int ty = t % nty, tz = t / nty;
+  if (threadIdx.x == 0) {
+    const unsigned bar = smem_u32(&sm.bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  tile_body<NT, PHASED, PAIRED, LR, PPH>(&tmW, G, S, flag, F0, F1, F2, tx * FX, ty * FY, tz * FZ, dflag, extra_tx,
+                                         raw_flags, sm, 0u);
 }
 
 // 5^3 dilation of the raw shock flags (Sect. 2.7) for one 8^3 tile of
@@ -622,15 +640,11 @@ __global__ void __launch_bounds__(NT, MINB)
 // x (byte shifts of the 16-byte window), y and z (word ORs) in turn -- the OR
 // over a box is the nested ORs over its axes.  Beyond a periodic boundary the
 // flags wrap; beyond any other boundary they count as unflagged.
-__global__ void __launch_bounds__(256) k_flag_dilate3(DevGeo G, const uint8_t *__restrict__ raw,
-                                                     uint8_t *__restrict__ dil, int ntx, int nty) {
-  __shared__ unsigned long long r0[HZ * HY][2];
-  __shared__ unsigned long long r1[HZ * HY], r2[HZ * FY];
-  int t = blockIdx.x;
-  const int tx = t % ntx;
-  t /= ntx;
-  const int ty = t % nty, tz = t / nty;
-  const int x0 = tx * FX, y0 = ty * FY, z0 = tz * FZ;
+// The dilation of the tile at (x0, y0, z0) with the CTA's threads; r0, r1, r2:
+// shared scratch of HZ HY 2, HZ HY and HZ FY words.
+__device__ __forceinline__ void dilate_tile(const DevGeo &G, const uint8_t *__restrict__ raw, uint8_t *__restrict__ dil,
+                                            int x0, int y0, int z0, unsigned long long (*r0)[2],
+                                            unsigned long long *r1, unsigned long long *r2) {
   const int nx = G.n[0], ny = G.n[1], nz = G.n[2];
   const int xs = x0 - 4;
   const bool wide = (nx % 8) == 0 && xs >= 0 && xs + 16 <= nx;   // aligned window inside the row
@@ -686,6 +700,17 @@ __global__ void __launch_bounds__(256) k_flag_dilate3(DevGeo G, const uint8_t *_
       for (int j = 0; j < 8 && x0 + j < nx; ++j) d[j] = (uint8_t)(o >> (8 * j));
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_flag_dilate3(DevGeo G, const uint8_t *__restrict__ raw,
+                                                     uint8_t *__restrict__ dil, int ntx, int nty) {
+  __shared__ unsigned long long r0[HZ * HY][2];
+  __shared__ unsigned long long r1[HZ * HY], r2[HZ * FY];
+  int t = blockIdx.x;
+  const int tx = t % ntx;
+  t /= ntx;
+  const int ty = t % nty, tz = t / nty;
+  dilate_tile(G, raw, dil, tx * FX, ty * FY, tz * FZ, r0, r1, r2);
 }
 
 // Contact-CT edge EMF along D at the lower corner (a-1/2, b-1/2) of cell c,
@@ -872,6 +897,198 @@ __global__ void k_update_faces3(DevGeo G, Box box, StageMx S) {
   if (c[0] < G.n[0] && c[1] < G.n[1]) face_update<2>(G, c, S, dt);
 }
 
+// ---------------------------------------------------------------------------
+// An ensemble of boxes in one persistent cooperative launch per RK stage, on
+// the tile kernel's body: phases over all boxes' items with a grid-wide
+// barrier between them -- (first stage: CFL rate per box, then its dt) ->
+// primitives -> raw shock flags -> their 5^3 dilation per tile -> tiles (each
+// CTA takes tiles from the concatenated tile list: TMA from the box's own
+// tensor map, faces, residual and cell update) -> edge EMFs -> face updates.  Every CTA reaches every barrier: a CTA whose copy timed out sets
+// the error bit and skips its remaining tiles, nothing returns early.
+
+struct FusedBox {
+  DevGeo G;
+  const CUtensorMap *tm;   // the box's W descriptor, in device memory
+  double *U, *B;
+  float *dU, *dB, *W, *F[3], *E;
+  uint8_t *raw;
+  double *dt;
+  unsigned int *fmax;
+  int *dflag;
+  Box b_int, b_work, b_site;
+  int ntx, nty;
+};
+enum { FE_DT, FE_PRIM, FE_RAW, FE_TILE, FE_SITE, FE_NPH };
+struct FusedEnsArgs {
+  const FusedBox *box;
+  const long *pref;   // [FE_NPH][nbox + 1] prefix sums of each phase's items
+  int nbox;
+  int stage, nstages;
+  float b;
+};
+constexpr int ENS_NT = 288, ENS_MINB = 3;
+
+__device__ __forceinline__ int ens_box(const long *p, int nbox, long w) {
+  int lo = 0, hi = nbox;   // p[lo] <= w < p[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (p[mid] <= w) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ StageMx ens_stage_bufs(const FusedBox &R, const FusedEnsArgs &a) {
+  StageMx S;
+  S.U = R.U; S.B = R.B; S.dU = R.dU; S.dB = R.dB;
+  S.first = a.stage == 0; S.last = a.stage == a.nstages - 1; S.b = a.b; S.dt = R.dt;
+  S.W = R.W; S.F[0] = R.F[0]; S.F[1] = R.F[1]; S.F[2] = R.F[2]; S.E = R.E;
+  return S;
+}
+
+// the box's geometry staged in shared memory (block-uniform), so that the
+// phases' per-item work reads it without dependent global loads
+__device__ __forceinline__ void ens_stage_geo(DevGeo *dst, const DevGeo &src) {
+  const unsigned *s = reinterpret_cast<const unsigned *>(&src);
+  unsigned *d = reinterpret_cast<unsigned *>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(DevGeo) / 4); i += blockDim.x) d[i] = s[i];
+}
+constexpr size_t ens_geo_offset() { return offsetof(FusedSmem, f) + sizeof(float) * 5 * NXF; }
+constexpr size_t ens_smem_bytes() { return smem_bytes(true) + sizeof(DevGeo) + 16; }
+
+template <bool PPH, int MINB>
+__global__ void __launch_bounds__(ENS_NT, MINB) k_ens_fused(FusedEnsArgs a) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ unsigned char smraw[];
+  unsigned char *base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);
+  FusedSmem &sm = *reinterpret_cast<FusedSmem *>(base);
+  DevGeo &G = *reinterpret_cast<DevGeo *>(base + ((ens_geo_offset() + 15) & ~(size_t)15));
+  const int tid = threadIdx.x;
+  const long nth = (long)gridDim.x * ENS_NT, t0 = (long)blockIdx.x * ENS_NT + tid;
+  const int nb = a.nbox;
+  const bool first = a.stage == 0;
+  if (tid == 0) {
+    const unsigned bar = smem_u32(&sm.bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto pref = [&](int ph) { return a.pref + (long)ph * (nb + 1); };
+  // one box after another (all blocks together), its items grid-strided
+  auto per_box = [&](int ph, auto &&item) {
+    const long *p = pref(ph);
+    for (int bx = 0; bx < nb; ++bx) {
+      const long n = p[bx + 1] - p[bx];
+      if (n == 0) continue;
+      __syncthreads();   // the previous box's readers are done
+      ens_stage_geo(&G, a.box[bx].G);
+      __syncthreads();
+      const FusedBox &R = a.box[bx];
+      for (long w = t0; w < n; w += nth) item(R, w);
+    }
+  };
+  if (first) {   // the CFL step of U^n per box (Eq. cfl)
+    per_box(FE_DT, [&](const FusedBox &R, long w) {
+      int c[3];
+      cell_at(R.b_int, w, c);
+      const unsigned r = __float_as_uint(dt_rate_mx(G, R.U, R.B, c, R.dflag));   // >= 0: bits order as floats
+      const unsigned m = __activemask();
+      const unsigned mx = __reduce_max_sync(m, r);   // one atomic per warp: the box is block-uniform
+      if ((int)(tid & 31) == __ffs(m) - 1) atomicMax(R.fmax, mx);
+    });
+    grid.sync();
+    if (t0 < nb) {
+      const FusedBox &R = a.box[t0];
+      *R.dt = R.G.cfl * R.G.sc_t / (double)__uint_as_float(*R.fmax);
+      *R.fmax = 0u;
+    }
+    grid.sync();
+  }
+  // primitive deviations and auxiliaries of the stage input (work layout)
+  per_box(FE_PRIM, [&](const FusedBox &R, long w) {
+    k_prim_mx_at(w, G, R.b_work, R.U, R.B, first ? nullptr : R.dU, first ? nullptr : R.dB, R.W, R.dflag);
+  });
+  grid.sync();
+  if (pref(FE_RAW)[nb] > 0) {   // raw shock flags of the boxes that flatten, then their 5^3 dilation per tile
+    per_box(FE_RAW, [&](const FusedBox &R, long w) { k_flag_raw_at<float>(w, G, R.b_int, R.W, R.raw); });
+    grid.sync();
+    const long *p = pref(FE_TILE);
+    // scratch in the face buffer, unused outside the tile phase
+    unsigned long long *scr = reinterpret_cast<unsigned long long *>(&sm.f[0][0]);
+    int bx = -1;
+    for (long w = blockIdx.x; w < p[nb]; w += gridDim.x) {
+      int nbx = bx < 0 ? 0 : bx;
+      while (w >= p[nbx + 1]) ++nbx;
+      __syncthreads();
+      if (nbx != bx) {
+        bx = nbx;
+        ens_stage_geo(&G, a.box[bx].G);
+        __syncthreads();
+      }
+      if (!(G.eps_sf > 0.0)) continue;   // block-uniform
+      const FusedBox &R = a.box[bx];
+      int t = (int)(w - p[bx]);
+      const int tx = t % R.ntx;
+      t /= R.ntx;
+      const int ty = t % R.nty, tz = t / R.nty;
+      dilate_tile(G, R.raw, R.raw + R.b_int.n, tx * FX, ty * FY, tz * FZ,
+                  reinterpret_cast<unsigned long long (*)[2]>(scr), scr + 2 * HZ * HY, scr + 3 * HZ * HY);
+    }
+    grid.sync();
+  }
+  {   // tiles: each CTA takes tiles from the concatenated list
+    const long *p = pref(FE_TILE);
+    unsigned parity = 0u;
+    bool dead = false;
+    int bx = -1;
+    for (long w = blockIdx.x; w < p[nb] && !dead; w += gridDim.x) {
+      int nbx = bx < 0 ? 0 : bx;
+      while (w >= p[nbx + 1]) ++nbx;
+      // the previous tile's shared-memory reads are done before the next copy lands
+      __syncthreads();
+      if (nbx != bx) {
+        bx = nbx;
+        ens_stage_geo(&G, a.box[bx].G);
+        __syncthreads();
+      }
+      const FusedBox &R = a.box[bx];
+      int t = (int)(w - p[bx]);
+      const int tx = t % R.ntx;
+      t /= R.ntx;
+      const int ty = t % R.nty, tz = t / R.nty;
+      const StageMx S = ens_stage_bufs(R, a);
+      const bool flags = G.eps_sf > 0.0;
+      if (tid == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      dead = !tile_body<ENS_NT, true, false, true, PPH>(R.tm, G, S, flags ? R.raw + R.b_int.n : nullptr, R.F[0],
+                                                        R.F[1], R.F[2], tx * FX, ty * FY, tz * FZ, R.dflag, 0u, 0,
+                                                        sm, parity);
+      parity ^= 1u;
+    }
+  }
+  grid.sync();
+  // Contact-CT edge EMFs at every site (Sect. 2.4)
+  per_box(FE_SITE, [&](const FusedBox &R, long w) {
+    int c[3];
+    cell_at(R.b_site, w, c);
+    const long q = widx(G, c[0], c[1], c[2]), wt = G.wtot;
+    const bool interior = c[0] >= 1 && c[0] < G.n[0] && c[1] >= 1 && c[1] < G.n[1] && c[2] >= 1 && c[2] < G.n[2];
+    if (c[0] < G.n[0]) R.E[q] = emf_edge<0>(G, c, interior, q, R.W, R.F[1], R.F[2]);
+    if (c[1] < G.n[1]) R.E[wt + q] = emf_edge<1>(G, c, interior, q, R.W, R.F[2], R.F[0]);
+    if (c[2] < G.n[2]) R.E[2 * wt + q] = emf_edge<2>(G, c, interior, q, R.W, R.F[0], R.F[1]);
+  });
+  grid.sync();
+  // face updates from the curl of the EMFs
+  per_box(FE_SITE, [&](const FusedBox &R, long w) {
+    int c[3];
+    cell_at(R.b_site, w, c);
+    const StageMx S = ens_stage_bufs(R, a);
+    const float dt = d2f_scaled(*S.dt, -G.e_t);
+    if (c[1] < G.n[1] && c[2] < G.n[2]) face_update<0>(G, c, S, dt);
+    if (c[0] < G.n[0] && c[2] < G.n[2]) face_update<1>(G, c, S, dt);
+    if (c[0] < G.n[0] && c[1] < G.n[1]) face_update<2>(G, c, S, dt);
+  });
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
@@ -1037,6 +1254,97 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   // the face update reads no neighbouring rows beyond one: the linear mapping measured faster
   PHL_LAUNCH(KC_UPDATE_FACES, prof, s, k_update_faces3<<<grid3(bs), block3(bs), 0, s>>>(G, bs, S));
   *nl += 2;
+}
+
+// The persistent fused ensemble: device records of the boxes, the phases'
+// prefix sums and the boxes' tensor maps; the grid is every SM times the
+// CTAs of the launch shape that fit on one (cooperative launch).
+cudaError_t ens_fused_create(const GridView *views, int nbox, EnsFused *out) {
+  *out = EnsFused();
+  cudaError_t e = fused_init();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ens_fused<false, ENS_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ens_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ens_fused<true, ENS_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ens_smem_bytes());
+  if (e != cudaSuccess) return e;
+  bool pph = false;
+  std::vector<FusedBox> h(nbox);
+  std::vector<CUtensorMap> tm(nbox);
+  std::vector<long> pref((size_t)FE_NPH * (nbox + 1), 0);
+  for (int b = 0; b < nbox; ++b) {
+    const GridView &v = views[b];
+    if (!v.tmapW || !fused_stage_ok(*v.G)) return cudaErrorInvalidValue;
+    const DevGeo &G = *v.G;
+    if (b == 0) pph = G.recon == PHL_RECON_PPH;
+    else if ((G.recon == PHL_RECON_PPH) != pph) return cudaErrorInvalidValue;   // one reconstruction per launch
+    FusedBox &R = h[b];
+    memset(&R, 0, sizeof(R));
+    R.G = G;
+    R.U = v.U; R.B = v.B; R.dU = v.dU; R.dB = v.dB; R.W = v.W;
+    for (int k = 0; k < 3; ++k) R.F[k] = v.F[k];
+    R.E = v.E; R.raw = v.raw; R.dt = v.dt; R.fmax = v.fmax; R.dflag = v.dflag;
+    memcpy(&tm[b], v.tmapW, sizeof(CUtensorMap));
+    const int n0 = G.n[0], n1 = G.n[1], n2 = G.n[2];
+    R.b_int = make_box(0, n0, 0, n1, 0, n2);
+    R.b_work = make_box(-G.ge[0], n0 + G.ge[0], -G.ge[1], n1 + G.ge[1], -G.ge[2], n2 + G.ge[2]);
+    R.b_site = make_box(0, n0 + 1, 0, n1 + 1, 0, n2 + 1);
+    R.ntx = (n0 + FX - 1) / FX;
+    R.nty = (n1 + FY - 1) / FY;
+    const long ntiles = (long)R.ntx * R.nty * ((n2 + FZ - 1) / FZ);
+    const long items[FE_NPH] = {R.b_int.n, R.b_work.n, G.eps_sf > 0.0 ? R.b_int.n : 0, ntiles, R.b_site.n};
+    for (int ph = 0; ph < FE_NPH; ++ph)
+      pref[(size_t)ph * (nbox + 1) + b + 1] = pref[(size_t)ph * (nbox + 1) + b] + items[ph];
+  }
+  void *db = nullptr, *dtm = nullptr, *dp = nullptr;
+  e = cudaMalloc(&db, sizeof(FusedBox) * nbox);
+  if (e == cudaSuccess) e = cudaMalloc(&dtm, sizeof(CUtensorMap) * nbox);   // 256-byte aligned: TMA descriptors
+  if (e == cudaSuccess) e = cudaMalloc(&dp, sizeof(long) * pref.size());
+  if (e == cudaSuccess) e = cudaMemcpy(dtm, tm.data(), sizeof(CUtensorMap) * nbox, cudaMemcpyHostToDevice);
+  for (int b = 0; b < nbox; ++b) h[b].tm = (const CUtensorMap *)dtm + b;
+  if (e == cudaSuccess) e = cudaMemcpy(db, h.data(), sizeof(FusedBox) * nbox, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dp, pref.data(), sizeof(long) * pref.size(), cudaMemcpyHostToDevice);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pph ? (const void *)k_ens_fused<true, ENS_MINB>
+                                                                    : (const void *)k_ens_fused<false, ENS_MINB>,
+                                                      ENS_NT, ens_smem_bytes());
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  if (e != cudaSuccess) {
+    cudaFree(db); cudaFree(dtm); cudaFree(dp);
+    return e;
+  }
+  out->boxes = db;
+  out->tmaps = dtm;
+  out->pref = (long *)dp;
+  out->nbox = nbox;
+  out->pph = pph;
+  out->blocks = per_sm * sms;
+  out->per_sm = per_sm;
+  return cudaSuccess;
+}
+
+void ens_fused_destroy(EnsFused *e) {
+  if (e->boxes) cudaFree(e->boxes);
+  if (e->tmaps) cudaFree(e->tmaps);
+  if (e->pref) cudaFree(e->pref);
+  *e = EnsFused();
+}
+
+cudaError_t launch_ens_fused(const EnsFused &E, int stage, int nstages, float b, cudaStream_t s) {
+  FusedEnsArgs a;
+  a.box = (const FusedBox *)E.boxes;
+  a.pref = E.pref;
+  a.nbox = E.nbox;
+  a.stage = stage;
+  a.nstages = nstages;
+  a.b = b;
+  void *args[] = {&a};
+  const void *fn = E.pph ? (const void *)k_ens_fused<true, ENS_MINB> : (const void *)k_ens_fused<false, ENS_MINB>;
+  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)E.blocks), dim3(ENS_NT), args, ens_smem_bytes(), s);
 }
 
 }  // namespace phl

@@ -89,7 +89,7 @@ def _deviation_l1(pr, a, b):
                   sum(np.abs(b[k]).sum() for k in ("bx", "by", "bz")))}
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_ensemble_boxes_match_the_oracle(P, mode):
     """Every box of a four-box ensemble, in each launch mode, against the CPU
     oracle stepping the same box alone (each side with its own CFL step: the
@@ -98,7 +98,9 @@ def test_ensemble_boxes_match_the_oracle(P, mode):
     probs = _boxes()
     E = P.Ensemble(probs)
     E.load()
-    E.set_shape(256, 1 if mode == 0 else 0, mode=mode, streams=4 if mode == 2 else 0)
+    E.set_shape(288 if mode == 3 else 256, 1 if mode == 0 else 0, mode=mode, streams=4 if mode == 2 else 0)
+    if mode == 3:
+        assert E.info()["launches_per_step"] == 3
     nsteps = 4
     E.step(nsteps)
     E.check()
@@ -122,8 +124,9 @@ def test_launch_shapes_and_autotune(P):
         return [g.get_state() for g in E.grids]
 
     # the same kernels give the same bits with any launch shape
-    ref = {0: run(0, 256, 1), 1: run(1, 256, 0), 2: run(2, 256, 0, 4)}
-    for mode, blk, bps, ns in ((0, 128, 1, 0), (0, 128, 2, 0), (1, 128, 0, 0), (2, 256, 0, 1), (2, 256, 0, 3)):
+    ref = {0: run(0, 256, 1), 1: run(1, 256, 0), 2: run(2, 256, 0, 4), 3: run(3, 288, 0)}
+    for mode, blk, bps, ns in ((0, 128, 1, 0), (0, 128, 2, 0), (1, 128, 0, 0), (2, 256, 0, 1), (2, 256, 0, 3),
+                               (3, 288, 0, 0)):
         for a, r in zip(run(mode, blk, bps, ns), ref[mode]):
             _same(a, r)
     # mode 2 runs each box's own per-kernel step: bit for bit the box alone
@@ -133,10 +136,13 @@ def test_launch_shapes_and_autotune(P):
     for m in (1, 2):
         for a, r, pr in zip(ref[0], ref[m], probs):
             _close(pr, a, r)
+    # the persistent fused kernel runs the fused tile body of the per-box chains
+    for a, r, pr in zip(ref[3], ref[2], probs):
+        _close(pr, a, r)
     E.load()
     res = E.autotune(trial_steps=1)
     assert len(res) >= 3 and all(r["ms_per_step"] > 0 for r in res)
-    assert {r["mode"] for r in res} == {0, 1, 2}
+    assert {r["mode"] for r in res} == {0, 1, 2, 3}
     info = E.info()
     best = min(res, key=lambda r: r["ms_per_step"])
     assert (info["mode"], info["block"], info["blocks_per_sm"], info["streams"]) == (
