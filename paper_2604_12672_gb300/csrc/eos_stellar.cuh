@@ -441,8 +441,30 @@ __device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, doub
     double e, cv;
     if (T > t.Tlo && T < t.Thi) {
       const double lnT = log(T);
-      if (eos_ecv_xy<double>(t, X, c, irho, T, lnT, iab, e, cv) && fabs(eint - e) < 1e-4 * fabs(eint))
+      if (eos_ecv_xy<double>(t, X, c, irho, T, lnT, iab, e, cv) && fabs(eint - e) < 1e-4 * fabs(eint)) {
+        const double de = eint - e;
+        // From |de|/e < 2e-6 one Newton step lands within ~(de/e)^2 < 1e-11
+        // of the root (quadratic convergence; d ln e / d ln T is 1..4 here):
+        // the full evaluation at that T1, carried to the root T1 + dT, dT =
+        // (e - e(T1)) / c_v(T1), to first order in dT -- P by P_T dT (error
+        // ~ dT^2), gamma_e = P / (rho e) + 1 from that P and e; gamma_c keeps
+        // its value at T1 (relative error ~ dT / T < 1e-11, wave speeds
+        // only).  The plain iteration would evaluate e, c_v at T1 once more
+        // and then the full EOS at T1 + dT.
+        if (fabs(de) >= tol * fabs(eint) && fabs(de) < 2e-6 * fabs(eint)) {
+          const double T1 = T + de / cv;
+          if (T1 > t.Tlo && T1 < t.Thi) {
+            if (!eos_rt_xy<double>(t, X, rho, irho, T1, next_lnT<double>(T, lnT, T1), iab, o, &c)) return -1;
+            const double dT = (eint - o.e) / o.cv;
+            o.P = fma(o.PT, dT, o.P);
+            o.e = eint;
+            o.ge = o.P / (rho * eint) + 1.0;
+            T = T1 + dT;
+            return 2;
+          }
+        }
         return newton_loop<double>(t, X, c, rho, irho, eint, iab, T, tol, maxit, o, true, e, cv, lnT);
+      }
     }
   }
   float Tf = (float)T;

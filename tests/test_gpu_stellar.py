@@ -72,8 +72,13 @@ def test_table_nodes_match_oracle(tables):
         assert (err <= bound).all(), (c, worst, va[worst + (c,)], vb[worst + (c,)])
 
 
+@pytest.mark.parametrize("guess_kind", ["far", "near"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_inversion_vs_oracle(P, tables, precision):
+def test_batch_inversion_vs_oracle(P, tables, precision, guess_kind):
+    """Far guesses (0.3 dex) take the mixed form's FP32 phase; near ones
+    (relative offsets 1e-13 .. 3e-5, as the previous step's T in a time step)
+    take its FP64 paths: converged at once, one Newton step and the full EOS
+    carried to the root to first order, or the plain iteration."""
     dt, ot = tables
     rng = np.random.Generator(np.random.PCG64(77))
     n = 400
@@ -85,7 +90,10 @@ def test_batch_inversion_vs_oracle(P, tables, precision):
     Tref = np.empty(n)
     Pref, ge, gc = np.empty(n), np.empty(n), np.empty(n)
     abar, ye = np.empty(n), np.empty(n)
-    guess = T * 10 ** rng.uniform(-0.3, 0.3, n)
+    if guess_kind == "far":
+        guess = T * 10 ** rng.uniform(-0.3, 0.3, n)
+    else:
+        guess = T * (1 + rng.choice([-1.0, 1.0], n) * 10 ** rng.uniform(-13, -4.5, n))
     for i in range(n):
         Xs = [Xo[i], 1 - Xo[i]]
         e[i] = O.eos_rt(cfg, rho[i], T[i], Xs)["e"]
