@@ -134,6 +134,14 @@ def lib():
         L.ora_sphere_run.argtypes = [C.c_void_p] + [_dp] * 4 + [C.c_int, C.c_double, _dp]
         L.ora_sphere_divb.restype = C.c_int
         L.ora_sphere_divb.argtypes = [C.c_void_p] + [_dp] * 4
+        L.ora_sphere_set_stellar.restype = C.c_int
+        L.ora_sphere_set_stellar.argtypes = [C.c_void_p, C.POINTER(OraCfg), _dp, C.c_double, C.c_double]
+        L.ora_sphere_from_prims.restype = C.c_int
+        L.ora_sphere_from_prims.argtypes = [C.c_void_p] + [_dp] * 7
+        L.ora_sphere_set_T.restype = C.c_int
+        L.ora_sphere_set_T.argtypes = [C.c_void_p, _dp]
+        L.ora_sphere_get_T.restype = C.c_int
+        L.ora_sphere_get_T.argtypes = [C.c_void_p, _dp]
         L.ora_ct_corner.restype = C.c_double
         L.ora_ct_corner.argtypes = [_dp, _dp, _dp, C.c_double, C.c_double]
         L.ora_fd.restype = C.c_double
@@ -407,9 +415,12 @@ def ct_corner(Ef, Ec, F, rho, smax):
 
 class Sphere:
     """The oracle's cubed-sphere shell (sphere.c) for a problem from
-    workloads.shell_problem: state arrays in the ABI layout."""
+    workloads.shell_problem: state arrays in the ABI layout.  A stellar
+    problem (given in primitives) needs the oracle's EosTable; its energy and
+    temperatures come from the oracle's EOS (self.state0)."""
 
-    def __init__(self, pr, riemann="lhlld", cfl=0.4, mach_thr=0.6, wb=True):
+    def __init__(self, pr, riemann="lhlld", cfl=0.4, mach_thr=0.6, wb=True, eos_table=None, newton_tol=1e-11,
+                 newton_maxit=50):
         self.pr = pr
         bg = pr.bg if wb and pr.bg is not None else None
         keep = []
@@ -427,6 +438,31 @@ class Sphere:
                                          arr(pr.g_c), arr(pr.heat), cfl, _RIEMANN[riemann], mach_thr)
         if not self.h:
             raise RuntimeError("oracle sphere creation failed")
+        self.stellar = pr.meta.get("eos") == "stellar"
+        self.state0 = dict(cons=pr.cons, pa=pr.pa, pb=pr.pb, pr=pr.pr)
+        if self.stellar:
+            if eos_table is None:
+                raise ValueError("a stellar shell needs the oracle's EosTable")
+            self._table = eos_table
+            self.ecfg = stellar_cfg(pr.meta["A"], pr.meta["Z"], eos_table, tol=newton_tol, maxit=newton_maxit)
+            X = np.ascontiguousarray(pr.meta["X"], dtype=np.float64)
+            self._keep.append(X)
+            if lib().ora_sphere_set_stellar(self.h, C.byref(self.ecfg), _ptr(X), pr.meta["rho_u"], pr.meta["p_u"]):
+                raise RuntimeError("oracle sphere: stellar background failed")
+            prim = pr.meta["prim"]
+            a = {k: np.ascontiguousarray(prim[k], dtype=np.float64) for k in ("rho", "vel", "p")}
+            st = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in self.state0.items()}
+            cons = np.zeros_like(st["cons"])
+            rc = lib().ora_sphere_from_prims(self.h, _ptr(a["rho"]), _ptr(a["vel"]), _ptr(a["p"]), _ptr(st["pa"]),
+                                             _ptr(st["pb"]), _ptr(st["pr"]), _ptr(cons))
+            if rc:
+                raise RuntimeError(f"oracle sphere: primitives to conserved failed ({rc})")
+            self.state0 = dict(st, cons=cons, T=self.get_T())
+
+    def get_T(self):
+        T = np.zeros(self.counts()["cells"])
+        lib().ora_sphere_get_T(self.h, _ptr(T))
+        return T
 
     def __del__(self):
         try:
@@ -447,7 +483,9 @@ class Sphere:
         return dict(vol=vol, xc=xc, S=S, xf=xf, csum=csum)
 
     def _state(self, st):
-        st = st or dict(cons=self.pr.cons, pa=self.pr.pa, pb=self.pr.pb, pr=self.pr.pr)
+        st = st or self.state0
+        if self.stellar and st.get("T") is not None:   # the temperatures the state came with: Newton guesses
+            lib().ora_sphere_set_T(self.h, _ptr(np.ascontiguousarray(st["T"], dtype=np.float64)))
         return {k: np.ascontiguousarray(st[k], dtype=np.float64).copy() for k in ("cons", "pa", "pb", "pr")}
 
     def dt(self, state=None):
@@ -461,6 +499,8 @@ class Sphere:
                                   float(dt_fixed), C.byref(last))
         if rc:
             raise RuntimeError(f"oracle sphere run failed ({rc})")
+        if self.stellar:
+            st["T"] = self.get_T()
         return st, last.value
 
     def divb(self, state=None):

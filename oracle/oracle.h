@@ -174,7 +174,8 @@ int ora_eos_invert(const ora_cfg *cfg, double rho, double eint, const double *X,
 
 /* ---------------- cubed-sphere shell (sphere.c) ----------------
  * Six equiangular patches of N x N angular cells times Nr radial cells, r in
- * [r_in, r_out] uniform; ideal gas; per-shell background rho_c, p_c (Nr, at
+ * [r_in, r_out] uniform; ideal gas (or the stellar EOS, ora_sphere_set_stellar);
+ * per-shell background rho_c, p_c (Nr, at
  * the shell's middle radius) and rho_f, p_f (Nr + 1, at the shell radii), or
  * NULL (no well-balancing); inward gravity g_c (Nr) and heating (Nr) or NULL.
  * Layouts: see sphere.c. */
@@ -194,6 +195,22 @@ double ora_sphere_dt(const ora_sphere *s, const double *cons, const double *pa, 
 int ora_sphere_run(const ora_sphere *s, double *cons, double *pa, double *pb, double *pr, int nsteps,
                    double dt_fixed, double *dt_last);
 int ora_sphere_divb(const ora_sphere *s, const double *pa, const double *pb, const double *pr, double *div);
+/* The stellar EOS on the shell (Sect. 2.2): eos supplies the table, the
+ * species' A, Z and the Newton settings; X the uniform mass fractions (the
+ * composition stays uniform, so Abar and Y_e are constants of the run);
+ * code density and pressure are rho_u and p_u times g/cm^3 and erg/cm^3.
+ * The background's gamma_e, gamma_c come from the EOS at (rho_hat, P_hat).
+ * Returns 0 or -1. */
+int ora_sphere_set_stellar(ora_sphere *s, const ora_cfg *eos, const double *X, double rho_u, double p_u);
+/* Conserved cells (5 x cells, ABI order) from primitives rho, vel[cells][3],
+ * P and the face fluxes (the cell field is the method's (1/V) sum s_f Phi_f
+ * x_f); with the stellar EOS T by P -> T and E from e(rho, T), kept as the
+ * cells' temperatures.  Returns 0, -1 or -3 (no temperature). */
+int ora_sphere_from_prims(ora_sphere *s, const double *rho, const double *vel, const double *P, const double *pa,
+                          const double *pb, const double *pr, double *cons);
+/* Cell temperatures (ABI order): each stellar inversion's guess and result. */
+int ora_sphere_set_T(ora_sphere *s, const double *T);
+int ora_sphere_get_T(const ora_sphere *s, double *T);
 void ora_riemann_up(const double *wl, const double *wr, double bn, int nspec, int solver, double mach_thr,
                     double *f, int *up);
 

@@ -113,6 +113,16 @@ struct ora_sphere {
   int *ecell;                    /* [ne][4] c00, c10, c11, c01 (or three cells) */
   int *eface;                    /* [ne][4] fa0, fb1, fa1, fb0 (or three faces) */
   signed char *eside;            /* [ne][4] mass-flux sign: +1 when the face's normal runs a0/b1/a1/b0-wise */
+  /* stellar EOS (ora_sphere_set_stellar).  The composition is uniform and
+   * stays so (a passive scalar that starts uniform is carried uniform by a
+   * conservative scheme), so it enters as constants; code density and
+   * pressure are rho_u and p_u times the EOS's g/cm^3 and erg/cm^3. */
+  int stellar;
+  ora_cfg ecfg;
+  double X[ORA_MAXSPEC];
+  double rho_u, p_u;
+  double *ge_c, *gc_c, *ge_f, *gc_f;   /* background gamma_e, gamma_c: shell middles (Nr), radii (Nr + 1) */
+  double *T;                     /* [nc] cell temperatures (K): each inversion's guess and result */
 };
 
 /* --------------------------------------------------------------------------
@@ -193,6 +203,7 @@ static void free_all(ora_sphere *s) {
   free(s->fkind); free(s->fk); free(s->fedge); free(s->fesign); free(s->abi_face); free(s->abi_fsign);
   free(s->abi_own);
   free(s->ldir); free(s->xe); free(s->elen); free(s->ekind); free(s->ecell); free(s->eface); free(s->eside);
+  free(s->T); free(s->ge_c); free(s->gc_c); free(s->ge_f); free(s->gc_f);
   free(s);
 }
 
@@ -579,10 +590,118 @@ int ora_sphere_geometry(const ora_sphere *s, double *vol, double *xc, double *S,
 /* --------------------------------------------------------------------------
  * the stage */
 
-enum { SW_RHO = 0, SW_U = 1, SW_B = 4, SW_P = 7, SW_N = 8 };   /* deviations: drho, u(3), B(3), dP */
+/* deviations: drho, u(3), B(3), dP, dgamma_e, dgamma_c */
+enum { SW_RHO = 0, SW_U = 1, SW_B = 4, SW_P = 7, SW_GE = 8, SW_GC = 9, SW_N = 10 };
 
 static double bg_rho_cell(const ora_sphere *s, int k) { return s->rho_c ? s->rho_c[k] : 0.0; }
 static double bg_p_cell(const ora_sphere *s, int k) { return s->p_c ? s->p_c[k] : 0.0; }
+/* the background's gamma_e, gamma_c at shell k's middle (face 0) or radius k (face 1) */
+static double bg_ge(const ora_sphere *s, int k, int face) {
+  const double *a = face ? s->ge_f : s->ge_c;
+  return s->stellar && a ? a[k] : s->gamma;
+}
+static double bg_gc(const ora_sphere *s, int k, int face) {
+  const double *a = face ? s->gc_f : s->gc_c;
+  return s->stellar && a ? a[k] : s->gamma;
+}
+
+static void load_phi(const ora_sphere *s, const double *pa, const double *pb, const double *pr, double *phi);
+
+/* T with P_EoS(rho, T) = P at fixed rho (EOS units): Newton on P from T,
+ * bracketed in [1e7, 1e10] K */
+static int p_to_T(const ora_cfg *cfg, double rho, double P, const double *X, double *T) {
+  double lo = 1e7, hi = 1e10, t = *T > lo && *T < hi ? *T : 1e9;
+  for (int it = 0; it < 200; ++it) {
+    double Pt, e, cv, dPdr, dPdT, ge, gc;
+    if (ora_eos_rt(cfg, rho, t, X, &Pt, &e, &cv, &dPdr, &dPdT, &ge, &gc)) return -1;
+    double dp = P - Pt;
+    if (fabs(dp) <= 1e-14 * P) { *T = t; return 0; }
+    if (dp > 0.0) lo = t; else hi = t;
+    double tn = t + dp / dPdT;
+    t = tn > lo && tn < hi ? tn : 0.5 * (lo + hi);
+  }
+  return -1;
+}
+
+int ora_sphere_set_stellar(ora_sphere *s, const ora_cfg *eos, const double *X, double rho_u, double p_u) {
+  if (!s || !eos || !eos->eos_table || !X || !(rho_u > 0.0) || !(p_u > 0.0)) return -1;
+  if (eos->nspec < 1 || eos->nspec > ORA_MAXSPEC) return -1;
+  s->stellar = 1;
+  s->ecfg = *eos;
+  s->ecfg.eos = ORA_EOS_STELLAR;
+  for (int l = 0; l < eos->nspec; ++l) s->X[l] = X[l];
+  s->rho_u = rho_u; s->p_u = p_u;
+  if (!s->T) s->T = calloc(s->nc, sizeof(double));
+  if (s->rho_c) {   /* the background's gamma_e, gamma_c from its (rho_hat, P_hat) */
+    const int Nr = s->Nr;
+    double **dst[4] = {&s->ge_c, &s->gc_c, &s->ge_f, &s->gc_f};
+    for (int q = 0; q < 4; ++q) { free(*dst[q]); *dst[q] = malloc(sizeof(double) * (Nr + 1)); }
+    for (int face = 0; face < 2; ++face) {
+      double T = 1e9;
+      for (int k = 0; k < Nr + face; ++k) {
+        double rho = (face ? s->rho_f[k] : s->rho_c[k]) * rho_u, P = (face ? s->p_f[k] : s->p_c[k]) * p_u;
+        double Pt, e, cv, dPdr, dPdT, ge, gc;
+        if (p_to_T(&s->ecfg, rho, P, s->X, &T) ||
+            ora_eos_rt(&s->ecfg, rho, T, s->X, &Pt, &e, &cv, &dPdr, &dPdT, &ge, &gc))
+          return -1;
+        (face ? s->ge_f : s->ge_c)[k] = ge;
+        (face ? s->gc_f : s->gc_c)[k] = gc;
+      }
+    }
+  }
+  return 0;
+}
+
+static v3 cell_field(const ora_sphere *s, const double *phi, long c) {
+  v3 Bc = mk(0, 0, 0);
+  for (int m = 0; m < 6; ++m) {
+    int f = s->cface[6 * c + m];
+    Bc = add(Bc, scl(s->xf[f], s->csign[6 * c + m] * phi[f]));
+  }
+  return scl(Bc, 1.0 / s->vol[c]);
+}
+
+int ora_sphere_from_prims(ora_sphere *s, const double *rho, const double *vel, const double *P, const double *pa,
+                          const double *pb, const double *pr, double *cons) {
+  if (!s || !rho || !vel || !P || !pa || !pb || !pr || !cons) return -1;
+  const long nc = s->nc;
+  double *phi = malloc(sizeof(double) * s->nf);
+  load_phi(s, pa, pb, pr, phi);
+  int rc = 0;
+  for (long c = 0; c < nc && !rc; ++c) {
+    v3 u = mk(vel[3 * c], vel[3 * c + 1], vel[3 * c + 2]), Bc = cell_field(s, phi, c);
+    double eden;   /* rho e_int */
+    if (s->stellar) {
+      double T = s->T[c] > 0.0 ? s->T[c] : 1e9, Pt, e, cv, dPdr, dPdT, ge, gc;
+      if (p_to_T(&s->ecfg, rho[c] * s->rho_u, P[c] * s->p_u, s->X, &T) ||
+          ora_eos_rt(&s->ecfg, rho[c] * s->rho_u, T, s->X, &Pt, &e, &cv, &dPdr, &dPdT, &ge, &gc)) {
+        rc = -3;
+        break;
+      }
+      s->T[c] = T;
+      eden = rho[c] * e * (s->rho_u / s->p_u);
+    } else {
+      eden = P[c] / (s->gamma - 1.0);
+    }
+    cons[c] = rho[c];
+    cons[nc + c] = rho[c] * u.x; cons[2 * nc + c] = rho[c] * u.y; cons[3 * nc + c] = rho[c] * u.z;
+    cons[4 * nc + c] = eden + 0.5 * rho[c] * dot(u, u) + 0.5 * dot(Bc, Bc);
+  }
+  free(phi);
+  return rc;
+}
+
+int ora_sphere_set_T(ora_sphere *s, const double *T) {
+  if (!s || !s->T || !T) return -1;
+  memcpy(s->T, T, sizeof(double) * s->nc);
+  return 0;
+}
+
+int ora_sphere_get_T(const ora_sphere *s, double *T) {
+  if (!s || !s->T || !T) return -1;
+  memcpy(T, s->T, sizeof(double) * s->nc);
+  return 0;
+}
 static int cell_k(const ora_sphere *s, long c) { return (int)((c / ((long)s->N * s->N)) % s->Nr); }
 
 /* Load (ABI) face fluxes into the unique faces: the owner's copy. */
@@ -608,15 +727,23 @@ static int sphere_prims(const ora_sphere *s, const double *cons, const double *p
   const long nc = s->nc;
   int rc = 0;
   for (long c = 0; c < nc; ++c) {
-    v3 Bc = mk(0, 0, 0);
-    for (int m = 0; m < 6; ++m) {
-      int f = s->cface[6 * c + m];
-      Bc = add(Bc, scl(s->xf[f], s->csign[6 * c + m] * phi[f]));
-    }
-    Bc = scl(Bc, 1.0 / s->vol[c]);
+    v3 Bc = cell_field(s, phi, c);
     double rho = cons[c];
     v3 u = mk(cons[nc + c] / rho, cons[2 * nc + c] / rho, cons[3 * nc + c] / rho);
-    double P = (s->gamma - 1.0) * (cons[4 * nc + c] - 0.5 * rho * dot(u, u) - 0.5 * dot(Bc, Bc));
+    double eden = cons[4 * nc + c] - 0.5 * rho * dot(u, u) - 0.5 * dot(Bc, Bc);   /* rho e_int */
+    double P, ge = s->gamma, gc = s->gamma;
+    if (!s->stellar) {
+      P = (s->gamma - 1.0) * eden;
+    } else {   /* the EOS in its own units: e_int per gram, T by Newton from the cell's last T */
+      double Pe;
+      int it;
+      if (!(rho > 0.0) || ora_eos_invert(&s->ecfg, rho * s->rho_u, eden / rho * (s->p_u / s->rho_u), s->X, &s->T[c],
+                                         &Pe, &ge, &gc, &it)) {
+        rc = -3;
+        continue;
+      }
+      P = Pe / s->p_u;
+    }
     if (!(rho > 0.0) || !(P > 0.0)) rc = -2;
     int k = cell_k(s, c);
     double *w = &W[SW_N * c];
@@ -624,6 +751,8 @@ static int sphere_prims(const ora_sphere *s, const double *cons, const double *p
     w[SW_U] = u.x; w[SW_U + 1] = u.y; w[SW_U + 2] = u.z;
     w[SW_B] = Bc.x; w[SW_B + 1] = Bc.y; w[SW_B + 2] = Bc.z;
     w[SW_P] = P - bg_p_cell(s, k);
+    w[SW_GE] = ge - bg_ge(s, k, 0);
+    w[SW_GC] = gc - bg_gc(s, k, 0);
   }
   return rc;
 }
@@ -697,6 +826,7 @@ static int sphere_fluxes(const ora_sphere *s, const double *W, const double *phi
     double brho, bp;
     if (s->fkind[f]) { brho = s->rho_f ? s->rho_f[s->fk[f]] : 0.0; bp = s->p_f ? s->p_f[s->fk[f]] : 0.0; }
     else { brho = bg_rho_cell(s, s->fk[f]); bp = bg_p_cell(s, s->fk[f]); }
+    const double bge = bg_ge(s, s->fk[f], s->fkind[f]), bgc = bg_gc(s, s->fk[f], s->fkind[f]);
     double rl[9], rr[9];
     v3 ul = mk(ql[SW_U], ql[SW_U + 1], ql[SW_U + 2]), ur = mk(qr[SW_U], qr[SW_U + 1], qr[SW_U + 2]);
     v3 bl = mk(ql[SW_B], ql[SW_B + 1], ql[SW_B + 2]), br = mk(qr[SW_B], qr[SW_B + 1], qr[SW_B + 2]);
@@ -706,14 +836,15 @@ static int sphere_fluxes(const ora_sphere *s, const double *W, const double *phi
     rl[4] = dot(bl, t1); rl[5] = dot(bl, t2);
     rr[4] = dot(br, t1); rr[5] = dot(br, t2);
     rl[6] = ql[SW_P] + bp; rr[6] = qr[SW_P] + bp;
-    rl[7] = rl[8] = rr[7] = rr[8] = s->gamma;
+    rl[7] = ql[SW_GE] + bge; rl[8] = ql[SW_GC] + bgc;
+    rr[7] = qr[SW_GE] + bge; rr[8] = qr[SW_GC] + bgc;
     if (!(rl[0] > 0.0 && rr[0] > 0.0 && rl[6] > 0.0 && rr[6] > 0.0)) rc = -2;
     double bn = phi[f] / s->farea[f];
     double fq[7], fh[7];
     int up;
     ora_riemann_up(rl, rr, bn, 0, s->riemann, s->mach_thr, fq, &up);
     if (s->rho_c) {   /* the flux of the face's hydrostatic state, F(W_hat, W_hat) */
-      double wh[9] = {brho, 0, 0, 0, 0, 0, bp, s->gamma, s->gamma};
+      double wh[9] = {brho, 0, 0, 0, 0, 0, bp, bge, bgc};
       ora_riemann(wh, wh, 0.0, 0, s->riemann, s->mach_thr, fh);
       for (int q = 0; q < 7; ++q) fq[q] -= fh[q];
     }
@@ -825,7 +956,7 @@ double ora_sphere_dt(const ora_sphere *s, const double *cons, const double *pa, 
     int k = cell_k(s, c);
     double rho = w[SW_RHO] + bg_rho_cell(s, k), P = w[SW_P] + bg_p_cell(s, k);
     v3 u = mk(w[SW_U], w[SW_U + 1], w[SW_U + 2]), b = mk(w[SW_B], w[SW_B + 1], w[SW_B + 2]);
-    double a2 = s->gamma * P / rho, b2 = dot(b, b) / rho;
+    double a2 = (w[SW_GC] + bg_gc(s, k, 0)) * P / rho, b2 = dot(b, b) / rho;
     double sum = 0.0;
     for (int d = 0; d < 3; ++d) {   /* the cell's three logical directions */
       int f0 = s->cface[6 * c + 2 * d], f1 = s->cface[6 * c + 2 * d + 1];

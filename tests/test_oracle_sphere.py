@@ -215,3 +215,63 @@ def test_rotation_symmetry():
     assert m_err <= 1e-12 * np.abs(b["cons"][1:4]).max()
     # the evolution is not trivial
     assert np.abs(a["cons"][1:4]).max() > 0 and np.abs(a["pa"] - pr.pa).max() > 0
+
+
+# ---------------------------------------------------------------- stellar EOS
+# The shell with the stellar EOS (Sect. 2.2): ions, radiation and the e-/e+
+# table of the oracle, 16O/28Si 0.5/0.5 everywhere, code units mapped to the
+# EOS's by constant factors.
+
+@pytest.fixture(scope="module")
+def otable():
+    return O.EosTable()
+
+
+def test_stellar_shell_temperatures_reproduce_the_pressure(otable):
+    # the energy of each cell comes from T with P_EoS(rho, T) = P: the EOS at
+    # that T gives back the workload's pressure
+    pr = WL.shell_problem(4, 3, eos="stellar")
+    sp = _sphere(pr, eos_table=otable)
+    T = sp.state0["T"]
+    prim = pr.meta["prim"]
+    rho = prim["rho"].ravel() * pr.meta["rho_u"]
+    P = prim["p"].ravel() * pr.meta["p_u"]
+    cfg = O.stellar_cfg(pr.meta["A"], pr.meta["Z"], otable)
+    for c in range(0, T.size, 7):
+        r = O.eos_rt(cfg, rho[c], T[c], pr.meta["X"])
+        assert abs(r["P"] / P[c] - 1.0) <= 1e-13
+    assert 1e8 < T.min() and T.max() < 3e9
+
+
+def test_stellar_well_balanced_rest_and_negative_control(otable):
+    # the polytrope at rest with the stellar EOS: the deviation form keeps it
+    # at rest to rounding (the background's gamma_e, gamma_c enter the
+    # subtracted hydrostatic flux); without the subtraction the truncation
+    # error of the pressure gradient drives flows
+    pr = WL.shell_problem(5, 6, eos="stellar", amp=0.0, beta=0, heat_frac=0)
+    cs = math.sqrt(5.0 / 3.0 * pr.bg["p_c"].max() / pr.bg["rho_c"].min())
+    sp = _sphere(pr, eos_table=otable)
+    st, _ = sp.run(4)
+    u = st["cons"][1:4] / st["cons"][0]
+    assert np.abs(u).max() <= 1e-13 * cs
+    assert np.abs(st["cons"][4] / sp.state0["cons"][4] - 1.0).max() <= 1e-14
+    assert np.abs(st["T"] / sp.state0["T"] - 1.0).max() <= 1e-12
+    st2, _ = _sphere(pr, eos_table=otable, wb=False).run(4)
+    u2 = st2["cons"][1:4] / st2["cons"][0]
+    assert np.abs(u2).max() > 1e-6 * cs
+
+
+def test_stellar_uniform_medium_conserves_mass_energy_and_div_b(otable):
+    pr = WL.shell_problem(5, 4, eos="stellar", uniform=True, heat_frac=0, amp=0.05, beta=1e3, vel_amp=0.05)
+    sp = _sphere(pr, eos_table=otable)
+    vol = _volumes(sp, pr)
+    c0 = sp.state0["cons"]
+    m0, e0 = (vol * c0[0]).sum(), (vol * c0[4]).sum()
+    st, dt = sp.run(6)
+    assert dt > 0
+    m1, e1 = (vol * st["cons"][0]).sum(), (vol * st["cons"][4]).sum()
+    assert abs(m1 - m0) <= 1e-14 * m0
+    assert abs(e1 - e0) <= 1e-14 * e0
+    assert np.abs(st["cons"][0] - c0[0]).max() > 1e-6 * c0[0].max()   # the state did evolve
+    scale = max(np.abs(pr.pa).max(), np.abs(pr.pr).max())
+    assert np.abs(sp.divb(st)).max() <= 1e-13 * scale

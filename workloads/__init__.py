@@ -695,7 +695,7 @@ def shell_fluxes_from_potential(N, Nr, r, A, device="cpu", ng=8):
 
 def shell_problem(N, Nr, r_in=0.2, r_out=1.0, seed=1234, amp=1e-3, beta=1e5, heat_frac=0.3, mach_heat=1e-3,
                   gamma=5.0 / 3.0, vel_amp=0.0, background=True, gravity=True, cfl=0.4, name=None,
-                  uniform=False, device="cpu"):
+                  uniform=False, device="cpu", eos="ideal"):
     """The cubed-sphere shell of the spherical configuration: a Lane-Emden
     n = 1.5 polytrope (surface at 1.2, so the whole shell r in [0.2, 1] is
     inside the star) in hydrostatic balance under its own radial gravity,
@@ -708,7 +708,15 @@ def shell_problem(N, Nr, r_in=0.2, r_out=1.0, seed=1234, amp=1e-3, beta=1e5, hea
     u = vel_amp c_s (z x r) / r.  uniform: density and pressure of the shell's
     middle everywhere, no gravity and no background (a medium in which the
     total energy is conserved).  device "cpu": numpy arrays; otherwise the
-    state arrays are torch tensors on that device (profiles stay numpy)."""
+    state arrays are torch tensors on that device (profiles stay numpy).
+
+    eos "stellar": the same shell in code units whose density and pressure
+    are rho_u = 1e7 g/cm^3 / rho_hat(r_in) and p_u = 1.8e24 erg/cm^3 /
+    P_hat(r_in) times the stellar EOS's (the stellar box's base state at the
+    inner wall, 1e7 -> 6.1e5 g/cm^3 across the shell), 16O/28Si mass fractions
+    0.5/0.5 everywhere.  Given as primitives (meta["prim"]: rho, velocity
+    (6, Nr, N, N, 3), P): the energy and temperature depend on the EOS, so
+    cons[4] is NaN and each implementation builds it with its own EOS."""
     import torch
     dev = torch.device(device)
     gen = torch.Generator(device=dev)
@@ -775,10 +783,20 @@ def shell_problem(N, Nr, r_in=0.2, r_out=1.0, seed=1234, amp=1e-3, beta=1e5, hea
     cons = torch.empty((5, 6, Nr, N, N), **f64)
     cons[0] = rho
     cons[1:4] = torch.movedim(rho[..., None] * vel, -1, 0)
-    cons[4] = p / (gamma - 1.0) + 0.5 * rho * (vel ** 2).sum(-1) + 0.5 * (bc ** 2).sum(-1)
+    meta = dict(seed=seed, amp=amp, beta=beta, r=r, r_mid=rm, eos=eos)
+    if eos == "stellar":
+        cons[4] = float("nan")
+        meta.update(rho_u=STELLAR_RHO_BASE / float(bg["rho_f"][0]), p_u=STELLAR_P_BASE / float(bg["p_f"][0]),
+                    A=list(STELLAR_A), Z=list(STELLAR_Z), X=list(STELLAR_X))
+    else:
+        cons[4] = p / (gamma - 1.0) + 0.5 * rho * (vel ** 2).sum(-1) + 0.5 * (bc ** 2).sum(-1)
     out = [cons, pa, pb, prr]
+    prim = dict(rho=rho, vel=vel, p=p)
     if dev.type == "cpu":
         out = [t.numpy() for t in out]
+        prim = {k: v.numpy() for k, v in prim.items()}
+    if eos == "stellar":
+        meta["prim"] = prim
     return ShellProblem(name=name or f"shell_{N}x{N}x{Nr}", N=N, Nr=Nr, r_in=r_in, r_out=r_out, gamma=gamma,
                         cons=out[0], pa=out[1], pb=out[2], pr=out[3], bg=bg if background else None, g_c=g_c,
-                        heat=heat, cfl=cfl, meta=dict(seed=seed, amp=amp, beta=beta, r=r, r_mid=rm))
+                        heat=heat, cfl=cfl, meta=meta)
