@@ -717,23 +717,35 @@ SPH_FP32_FLOP_PER_FACE = 534.2
 SPH_MX_FLUX_DRAM_BYTES_PER_FACE = 50.8
 
 
-def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, Nr=384, precision="fp64"):
-    """The cubed-sphere shell 6 x N x N x Nr (phl_sphere_*, FP64): the
-    n = 1.5 polytrope between r = 0.2 and 1 under its own radial gravity,
-    density noise 1e-3, a poloidal seed field at beta 1e5, heating in the
-    inner 30%, LHLLD, CFL 0.4, reflecting radial walls, well-balanced, in
-    the FP64 or the mixed form.  State resident on the device; CUDA events on
-    the sphere's stream around K steps after W warm-up steps; then one more
-    step with per-kernel timing for the dominant kernel's roofline."""
+def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, Nr=384, precision="fp64",
+                    eos="stellar", table=None, mlp=None):
+    """The cubed-sphere shell 6 x N x N x Nr (phl_sphere_*): the n = 1.5
+    polytrope between r = 0.2 and 1 under its own radial gravity, density
+    noise 1e-3, a poloidal seed field at beta 1e5, heating in the inner 30%,
+    LHLLD, CFL 0.4, reflecting radial walls, well-balanced, in the FP64 or
+    the mixed form; eos "stellar": the stellar EOS (ions + radiation + e-/e+
+    table, 16O/28Si 0.5/0.5, 1e7 -> 6.1e5 g/cm^3 across the shell), loaded
+    from primitives and then reloaded without temperatures, so that the first
+    (warm-up) inversion starts from the network's guess (a cold start) and
+    every later one from the previous stage's T.  State resident on the
+    device; CUDA events on the sphere's stream around K steps after W warm-up
+    steps; then one more step with per-kernel timing."""
     import torch
     import workloads as W
     torch.cuda.empty_cache()
-    pr = W.shell_problem(N, Nr, device="cuda")
-    S = P.Sphere.from_problem(pr, stream=stream.cuda_stream, precision=precision)
+    pr = W.shell_problem(N, Nr, device="cuda", eos=eos)
+    S = P.Sphere.from_problem(pr, stream=stream.cuda_stream, precision=precision, eos_table=table, mlp=mlp)
     torch.cuda.synchronize()          # the inputs were written on torch's stream
-    S.set_state(pr.cons, pr.pa, pr.pb, pr.pr)
+    S.load(pr)
     counts = S.counts()
     S.check()                         # synchronises the sphere's stream before the inputs go
+    if eos == "stellar":              # the same state without temperatures: a cold start
+        st = {k: torch.empty_like(getattr(pr, k)) for k in ("pa", "pb", "pr")}
+        st["cons"] = torch.empty_like(pr.cons)
+        S.get_state(st)
+        S.set_state(st["cons"], st["pa"], st["pb"], st["pr"])
+        S.check()
+        del st
     del pr
     torch.cuda.empty_cache()
     S.step(warmup)
@@ -755,15 +767,21 @@ def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, N
     cells, faces = counts["cells"], counts["faces"]
     name, (launches, kms) = max(kt.items(), key=lambda kv: kv[1][1])
     avg = kms / max(launches, 1)
+    eos_txt = ("stellar EOS (ions + radiation + e-/e+ table, 16O/28Si 0.5/0.5, rho 1e7 -> 6.1e5 g/cc; "
+               "temperature guesses: the network on the cold start, then the previous stage's T)"
+               if eos == "stellar" else "ideal gas gamma 5/3")
     out = {"workload": f"cubed-sphere shell 6 x {N} x {N} x {Nr} (r 0.2..1), n=1.5 polytrope, radial g, "
                        "density noise 1e-3 seed 1234, poloidal field beta 1e5, heating inner 30%, LHLLD, "
-                       f"CFL 0.4, reflecting walls, well-balanced, {precision}",
+                       f"CFL 0.4, reflecting walls, well-balanced, {eos_txt}, {precision}",
            "cells": cells, "faces": faces, "edges": counts["edges"],
            "value": cells * STAGES * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
            "steps": steps, "warmup": warmup, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
            "launches_per_step": sum(v[0] for v in kt.values())}
     roof = {"kernel": name, "avg_launch_ms": avg, "launches": launches}
-    if name == "sph_flux" and precision == "fp64":
+    if eos == "stellar":
+        roof["note"] = ("stellar EOS: the inversion (sph_prim) and the general-EOS solver (sph_flux) run FP64 "
+                        "table work bound by the FP64 pipe; no per-face operation count is taken for them")
+    elif name == "sph_flux" and precision == "fp64":
         # HBM view: W read once per cell, phi read and F, E, contact sign
         # written once per face
         b = cells * 64.0 + faces * (8.0 + 40.0 + 24.0 + 1.0)
@@ -794,12 +812,26 @@ def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, N
 
 
 def cubed_sphere_forms(P, args, stream, alu, hbm_peak, peak_kind):
-    """The shell in the mixed form (the value) and in the FP64 form beside it."""
+    """The stellar shell in the mixed form (the value) and in the FP64 form
+    beside it; the ideal-gas shell's mixed form for reference."""
+    import time
+    table = P.EosTable(nrho=321, nT=241)
+    mlp = P.Mlp(seed=7)
+    t0 = time.perf_counter()
+    mlp.train(table, nsamples=2_000_000, epochs=4, batch=1024, lr=1e-2, seed=2026)
+    t_train = time.perf_counter() - t0
     mx = cubed_sphere_c5(P, args.c5_steps_mixed, 2, stream, alu, hbm_peak, peak_kind, args.c5_n, args.c5_nr,
-                         "mixed")
-    f64 = cubed_sphere_c5(P, args.c5_steps, 1, stream, alu, hbm_peak, peak_kind, args.c5_n, args.c5_nr, "fp64")
+                         "mixed", "stellar", table, mlp)
+    f64 = cubed_sphere_c5(P, args.c5_steps, 1, stream, alu, hbm_peak, peak_kind, args.c5_n, args.c5_nr, "fp64",
+                          "stellar", table, mlp)
     mx["fp64"] = f64
     mx["mixed_over_fp64"] = mx["value"] / f64["value"]
+    mx["mlp_training_s"] = t_train
+    ideal = cubed_sphere_c5(P, args.c5_steps_mixed, 2, stream, alu, hbm_peak, peak_kind, args.c5_n, args.c5_nr,
+                            "mixed", "ideal")
+    mx["ideal_gas_mixed"] = {k: ideal[k] for k in ("workload", "value", "unit", "ms_per_step", "kernels", "roofline")}
+    mlp.close()
+    table.close()
     return mx
 
 
@@ -836,6 +868,9 @@ def main():
     ap.add_argument("--c5-steps", type=int, default=2, help="cubed sphere: timed FP64 steps")
     ap.add_argument("--c5-steps-mixed", type=int, default=5, help="cubed sphere: timed mixed steps")
     ap.add_argument("--c5-precision", default="both", choices=["fp64", "mixed", "both"])
+    ap.add_argument("--c5-eos", default="stellar", choices=["stellar", "ideal"],
+                    help="cubed sphere with one precision: the EOS (both precisions: stellar, plus the ideal gas's "
+                         "mixed form for reference)")
     ap.add_argument("--c5-only", action="store_true", help="only the cubed-sphere shell (its JSON object alone)")
     ap.add_argument("--c5-n", type=int, default=256, help="cubed sphere: angular cells per patch side")
     ap.add_argument("--c5-nr", type=int, default=384, help="cubed sphere: radial cells")
@@ -872,8 +907,13 @@ def main():
                 print(json.dumps(cubed_sphere_forms(P, args, stream, alu, hbm_peak, peak_kind)))
             else:
                 steps = args.c5_steps if args.c5_precision == "fp64" else args.c5_steps_mixed
+                table = mlp = None
+                if args.c5_eos == "stellar":
+                    table = P.EosTable(nrho=321, nT=241)
+                    mlp = P.Mlp(seed=7)
+                    mlp.train(table, nsamples=2_000_000, epochs=4, batch=1024, lr=1e-2, seed=2026)
                 print(json.dumps(cubed_sphere_c5(P, steps, 1, stream, alu, hbm_peak, peak_kind, args.c5_n,
-                                                 args.c5_nr, args.c5_precision)))
+                                                 args.c5_nr, args.c5_precision, args.c5_eos, table, mlp)))
         return 0
     if args.c3_only:
         c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws)

@@ -594,7 +594,12 @@ phl_status phl_poisson_gravity(phl_poisson *p, const double *phi, double *gx, do
  * and field as Cartesian vectors, van Leer PLM along the mesh lines (Sect.
  * 2.5), LHLLD / HLLD / HLL (Sect. 2.6) in each face's normal frame, the
  * deviation form with a radial background (Sect. 2.8), radial gravity and
- * heating, SSP-RK3 (Sect. 2.9), reflecting radial walls.  Ideal gas.
+ * heating, SSP-RK3 (Sect. 2.9), reflecting radial walls.  Ideal gas, or the
+ * stellar EOS (Sect. 2.2: ions, radiation, the e-/e+ table) with a uniform
+ * composition: a passive scalar that starts uniform stays uniform under a
+ * conservative scheme, so the mass fractions enter as constants and are not
+ * transported.  The shell's density and pressure are code values; the EOS
+ * sees rho * rho_unit (g/cm^3) and P * p_unit (erg/cm^3).
  *
  * State layout (doubles, host or device as `where` says):
  *   cons  [5][6][Nr][N][N]: rho, m_x, m_y, m_z, E (Cartesian components);
@@ -622,6 +627,17 @@ typedef struct {
   const double *g_c;        /* host, nullable: inward gravity per shell (Nr)    */
   const double *heat;       /* host, nullable: heating per unit volume (Nr)     */
   void *stream;             /* cudaStream_t (null: the legacy default stream)   */
+  /* stellar EOS (eos = PHL_EOS_STELLAR; zero-initialised fields: ideal gas) */
+  int eos;                  /* PHL_EOS_IDEAL (gamma) or PHL_EOS_STELLAR         */
+  const struct phl_eos_table *eos_table;  /* the EOS table (not owned)        */
+  int nspec;                /* species of the uniform composition, 1..4         */
+  double A[PHL_MAXSPEC], Z[PHL_MAXSPEC], X[PHL_MAXSPEC];  /* mass number,    */
+                            /* charge, mass fraction of each species            */
+  double rho_unit, p_unit;  /* g/cm^3 and erg/cm^3 per code density, pressure   */
+  double newton_tol;        /* Newton tolerance (0: 1e-11)                      */
+  int newton_maxit;         /* (0: 50)                                          */
+  const struct phl_mlp *mlp;  /* nullable: temperature-guess network for cells */
+                              /* without a temperature (cold start only)      */
 } phl_sphere_desc;
 typedef struct phl_sphere phl_sphere;
 
@@ -641,6 +657,22 @@ phl_status phl_sphere_set_state(phl_sphere *s, const double *cons, const double 
  * PHL_ENAN when a kernel since set_state met rho <= 0, P <= 0 or a
  * non-finite value. */
 phl_status phl_sphere_get_state(phl_sphere *s, double *cons, double *pa, double *pb, double *pr, int where);
+/* Loads a state given in primitives (stellar shells are given so: the
+ * energy and temperature depend on the EOS): rho, P [6][Nr][N][N] (code
+ * units), vel [6][Nr][N][N][3], the fluxes as in set_state.  The cell field
+ * is the method's (1/V) sum_f s_f Phi_f x_f; with the stellar EOS each cell's
+ * T solves P_EoS(rho, T) = P (Newton on P, bracketed in the table's range)
+ * and E = rho e(rho, T) + rho u^2 / 2 + B^2 / 2.  PHL_ENEWTON when a
+ * temperature was not found.  Host sources: synchronous. */
+phl_status phl_sphere_set_prims(phl_sphere *s, const double *rho, const double *vel, const double *P,
+                                const double *pa, const double *pb, const double *pr, int where);
+/* Cell temperatures (K) of a stellar shell, [6][Nr][N][N]: each inversion's
+ * Newton guess and result.  set: values <= 0 mark cells without one (a cold
+ * start: the network's guess where desc.mlp is given, else the shell
+ * background's temperature); set_state leaves every cell cold.  get:
+ * synchronous for host memory.  PHL_EINVAL on an ideal-gas shell. */
+phl_status phl_sphere_set_temperature(phl_sphere *s, const double *T, int where);
+phl_status phl_sphere_get_temperature(phl_sphere *s, double *T, int where);
 /* The CFL step of the current state (Eq. cfl with the fast speed along each
  * cell's three mesh directions over the distance between its opposite face
  * centres), to host memory; synchronous. */
@@ -649,7 +681,8 @@ phl_status phl_sphere_compute_dt(phl_sphere *s, double *dt_out);
  * on the device); asynchronous on the stream.  Errors show in
  * phl_sphere_check / get_state. */
 phl_status phl_sphere_step(phl_sphere *s, double dt, int nsteps);
-/* Synchronises the stream; PHL_ENEGATIVE / PHL_ENAN as in get_state. */
+/* Synchronises the stream; PHL_ENEGATIVE / PHL_ENAN as in get_state,
+ * PHL_ENEWTON when a stellar inversion did not converge. */
 phl_status phl_sphere_check(phl_sphere *s);
 /* Per-kernel CUDA-event timing of the sphere's launches, as phl_set_timing /
  * phl_kernel_times for a grid (classes "sph_prim", "sph_flux", "sph_emf",

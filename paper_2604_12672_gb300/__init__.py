@@ -151,6 +151,9 @@ _SIGS = {
     "phl_sphere_compute_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "phl_sphere_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "phl_sphere_check": (C.c_int, [C.c_void_p]),
+    "phl_sphere_set_prims": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_int]),
+    "phl_sphere_set_temperature": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_sphere_get_temperature": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "phl_sphere_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_sphere_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
 }
@@ -677,7 +680,11 @@ class SphereDesc(C.Structure):
     _fields_ = [("N", C.c_int), ("Nr", C.c_int), ("r_in", C.c_double), ("r_out", C.c_double),
                 ("gamma", C.c_double), ("cfl", C.c_double), ("riemann", C.c_int), ("mach_thr", C.c_double),
                 ("precision", C.c_int), ("rho_c", C.c_void_p), ("p_c", C.c_void_p), ("rho_f", C.c_void_p), ("p_f", C.c_void_p),
-                ("g_c", C.c_void_p), ("heat", C.c_void_p), ("stream", C.c_void_p)]
+                ("g_c", C.c_void_p), ("heat", C.c_void_p), ("stream", C.c_void_p),
+                ("eos", C.c_int), ("eos_table", C.c_void_p), ("nspec", C.c_int),
+                ("A", C.c_double * 4), ("Z", C.c_double * 4), ("X", C.c_double * 4),
+                ("rho_unit", C.c_double), ("p_unit", C.c_double), ("newton_tol", C.c_double),
+                ("newton_maxit", C.c_int), ("mlp", C.c_void_p)]
 
 
 class Sphere:
@@ -686,10 +693,12 @@ class Sphere:
     is cons [5][6][Nr][N][N] and the face fluxes pa [6][Nr][N][N+1],
     pb [6][Nr][N+1][N], pr [6][Nr+1][N][N], as numpy float64 arrays (host)
     or CUDA tensors (device).  `bg` holds rho_c, p_c (Nr) and rho_f, p_f
-    (Nr + 1), or is None for full-state fluxes."""
+    (Nr + 1), or is None for full-state fluxes.  `stellar` (a dict of
+    eos_table, A, Z, X, rho_u, p_u, and optionally mlp, newton_tol) selects
+    the stellar EOS with a uniform composition."""
 
     def __init__(self, N, Nr, r_in, r_out, gamma=5.0 / 3.0, cfl=0.4, riemann="lhlld", mach_thr=0.6, bg=None,
-                 g_c=None, heat=None, stream=None, precision="fp64"):
+                 g_c=None, heat=None, stream=None, precision="fp64", stellar=None):
         self.N, self.Nr = int(N), int(Nr)
         keep = []
 
@@ -706,17 +715,45 @@ class Sphere:
         if bg is not None:
             d.rho_c, d.p_c, d.rho_f, d.p_f = (arr(bg[k]) for k in ("rho_c", "p_c", "rho_f", "p_f"))
         d.g_c, d.heat, d.stream = arr(g_c), arr(heat), stream
+        self.stellar = stellar is not None
+        if self.stellar:
+            d.eos, d.eos_table = 1, stellar["eos_table"].h
+            d.nspec = len(stellar["A"])
+            for l in range(d.nspec):
+                d.A[l], d.Z[l], d.X[l] = stellar["A"][l], stellar["Z"][l], stellar["X"][l]
+            d.rho_unit, d.p_unit = float(stellar["rho_u"]), float(stellar["p_u"])
+            d.newton_tol = float(stellar.get("newton_tol", 1e-11))
+            d.newton_maxit = int(stellar.get("newton_maxit", 50))
+            m = stellar.get("mlp")
+            d.mlp = m.h if m is not None else None
+            self._stellar_refs = (stellar["eos_table"], m)   # the handles must outlive the shell
         h = C.c_void_p()
         _check(lib().phl_sphere_create(C.byref(d), C.byref(h)))
         self.h = h
 
     @classmethod
-    def from_problem(cls, pr, wb=True, stream=None, precision="fp64"):
+    def from_problem(cls, pr, wb=True, stream=None, precision="fp64", eos_table=None, mlp=None):
         """From a workloads.ShellProblem (its solver, CFL, background, gravity
-        and heating); wb=False drops the background."""
+        and heating); wb=False drops the background.  A stellar problem needs
+        an EosTable (and takes an optional Mlp for cold starts)."""
+        stellar = None
+        if pr.meta.get("eos") == "stellar":
+            if eos_table is None:
+                raise ValueError("a stellar shell needs an EosTable")
+            stellar = dict(eos_table=eos_table, A=pr.meta["A"], Z=pr.meta["Z"], X=pr.meta["X"],
+                           rho_u=pr.meta["rho_u"], p_u=pr.meta["p_u"], mlp=mlp)
         return cls(pr.N, pr.Nr, pr.r_in, pr.r_out, gamma=pr.gamma, cfl=pr.cfl, riemann=pr.riemann,
                    mach_thr=pr.mach_thr, bg=pr.bg if wb else None, g_c=pr.g_c, heat=pr.heat, stream=stream,
-                   precision=precision)
+                   precision=precision, stellar=stellar)
+
+    def load(self, pr):
+        """The problem's initial state: set_state, or for a stellar problem
+        (given in primitives) set_prims."""
+        if pr.meta.get("eos") == "stellar":
+            p = pr.meta["prim"]
+            self.set_prims(p["rho"], p["vel"], p["p"], pr.pa, pr.pb, pr.pr)
+        else:
+            self.set_state(pr.cons, pr.pa, pr.pb, pr.pr)
 
     def shapes(self):
         N, Nr = self.N, self.Nr
@@ -733,6 +770,29 @@ class Sphere:
             assert tuple(a.shape) == shp, (k, tuple(a.shape), shp)
         assert len({w for _, w in ptrs}) == 1, "all state arrays must live in the same memory"
         _check(lib().phl_sphere_set_state(self.h, *[p for p, _ in ptrs], ptrs[0][1]))
+
+    def set_prims(self, rho, vel, P, pa, pb, pr):
+        """rho, P [6][Nr][N][N], vel [6][Nr][N][N][3] (code units) and the fluxes."""
+        N, Nr = self.N, self.Nr
+        arrs = (rho, vel, P, pa, pb, pr)
+        shp = [(6, Nr, N, N), (6, Nr, N, N, 3), (6, Nr, N, N)] + [self.shapes()[k] for k in ("pa", "pb", "pr")]
+        for a, s_ in zip(arrs, shp):
+            assert tuple(a.shape) == s_, (tuple(a.shape), s_)
+        ptrs = [_ptr(a) for a in arrs]
+        assert len({w for _, w in ptrs}) == 1, "all arrays must live in the same memory"
+        _check(lib().phl_sphere_set_prims(self.h, *[p for p, _ in ptrs], ptrs[0][1]))
+
+    def set_temperature(self, T):
+        p, w = _ptr(T)
+        _check(lib().phl_sphere_set_temperature(self.h, p, w))
+
+    def get_temperature(self, out=None):
+        """Cell temperatures [6][Nr][N][N] (K) of a stellar shell."""
+        if out is None:
+            out = np.zeros((6, self.Nr, self.N, self.N))
+        p, w = _ptr(out)
+        _check(lib().phl_sphere_get_temperature(self.h, p, w))
+        return out
 
     def get_state(self, out=None):
         """Returns dict(cons, pa, pb, pr); `out` (a dict of arrays or tensors of

@@ -44,6 +44,8 @@
 #include <utility>
 #include <vector>
 
+#include "eos_stellar.cuh"
+#include "mlp_dev.cuh"
 #include "phl.h"
 #include "phl_internal.cuh"
 #include "riemann.cuh"
@@ -349,7 +351,9 @@ void build_ang(int N, Ang &M) {
 // fluxes feeds the FP32 kernels.  GB300 runs FP64 at 1/64 of its FP32 rate,
 // so the mixed kernels keep FP64 instructions to the few that the form needs.
 
-enum { SW_RHO = 0, SW_U = 1, SW_B = 4, SW_P = 7, SW_N = 8 };
+// deviations per cell: drho, u (3), B (3), dP; the stellar EOS adds
+// dgamma_e, dgamma_c (SW_NS)
+enum { SW_RHO = 0, SW_U = 1, SW_B = 4, SW_P = 7, SW_N = 8, SW_GE = 8, SW_GC = 9, SW_NS = 10 };
 
 struct SphDev {
   int N, Nr;
@@ -372,13 +376,28 @@ struct SphDev {
   const float *rho_cf, *p_cf, *rho_ff, *p_ff, *g_cf, *heat_f;
   float gf, igm1f, ggm1f, gm1f, machf;
   int *dflag;
+  // stellar EOS (Sect. 2.2) with a uniform composition: the table, Abar and
+  // Y_e, code density / pressure / specific energy -> g/cm^3, erg/cm^3, erg/g
+  int stellar;
+  eos::Table tab;
+  double abar, ye, rho_u, p_u, e_u, ntol;
+  int nmaxit;
+  const double *ge_c, *gc_c, *ge_f, *gc_f;   // background gamma_e, gamma_c: shells (Nr), radii (Nr + 1)
+  const float *ge_cf, *gc_cf, *ge_ff, *gc_ff;
+  const double *T_c;           // the background's temperature per shell (cold-start guess)
+  double *T;                   // cell temperatures (internal order); <= 0: none yet
+  int wq;                      // mixed W: float4 records per cell (2; 3 with the stellar EOS)
+  mlp::Dev mlp;                // temperature-guess network (cold starts), when use_mlp
+  int use_mlp;
+  float mlp_x0;                // its composition input X_0 / (X_0 + X_1)
 };
 
 // work arrays of one form (R = double: FP64, float: mixed)
 template <typename R>
 struct SphWork {
-  R *W;             // 8 deviations per cell: FP64 SoA; mixed two float4 per cell
-                    // ((drho, u), (B, dP)), one 16-byte load each
+  R *W;             // 8 (10 stellar) deviations per cell: FP64 SoA; mixed two
+                    // float4 per cell ((drho, u), (B, dP)), one 16-byte load
+                    // each, and (dgamma_e, dgamma_c, 0, 0) for the stellar EOS
   R *FC, *EF;       // 5 integrated fluxes per face, SoA; face EMF: FP64 3 SoA
                     // components, mixed one float4 per face (E, contact sign)
   double *EE;       // edge EMF line integrals L (E . l), FP64 in both forms
@@ -444,8 +463,8 @@ __global__ void k_sph_prims(SphDev D, SphWork<double> Wk, const double *__restri
 // the CFL rate (Eq. cfl) sum_d (|u . e_d| + c_f(e_d)) / width_d of one cell,
 // FP32 on the mixed form's tables
 __device__ __forceinline__ float cfl_rate_mx(const SphDev &D, long a, int k, float rho, float P, float ux, float uy,
-                                             float uz, float bx, float by, float bz) {
-  const float a2 = D.gf * P / rho, b2 = (bx * bx + by * by + bz * bz) / rho;
+                                             float uz, float bx, float by, float bz, float gam) {
+  const float a2 = gam * P / rho, b2 = (bx * bx + by * by + bz * bz) / rho;
   const float rm = D.rm_f[k];
   float sum = 0.f;
 #pragma unroll
@@ -511,7 +530,7 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_mx(SphDev D, SphWork<float> W
     W4[2 * c] = make_float4(drho, ux, uy, uz);
     W4[2 * c + 1] = make_float4(bx, by, bz, dP);
     if (dmax) {
-      rate = cfl_rate_mx(D, a, k, rho, P, ux, uy, uz, bx, by, bz);
+      rate = cfl_rate_mx(D, a, k, rho, P, ux, uy, uz, bx, by, bz, D.gf);
       if (!(rate == rate)) rate = INFINITY;
     }
   }
@@ -528,17 +547,257 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_mx(SphDev D, SphWork<float> W
   }
 }
 
-// deviations of cell c, mirrored across a wall of unit normal (nx, ny, nz) when mir
+// ---------------------------------------------------------------------------
+// stellar EOS on the shell (Sect. 2.2)
+
+// the background's gamma_e, gamma_c at shell k's middle (radial = false) or
+// at radius k; gamma without a background
 template <typename R>
+__device__ __forceinline__ void bg_gammas(const SphDev &D, int k, bool radial, R &ge, R &gc) {
+  if constexpr (sizeof(R) == 4) {
+    const float *e = radial ? D.ge_ff : D.ge_cf, *g = radial ? D.gc_ff : D.gc_cf;
+    ge = e ? e[k] : D.gf;
+    gc = g ? g[k] : D.gf;
+  } else {
+    const double *e = radial ? D.ge_f : D.ge_c, *g = radial ? D.gc_f : D.gc_c;
+    ge = e ? e[k] : D.gamma;
+    gc = g ? g[k] : D.gamma;
+  }
+}
+
+// T with P_EoS(rho, T) = P at fixed rho (EOS units): Newton on P from T,
+// bracketed in the table's temperature range; o holds the EOS at that T
+__device__ bool sph_p_to_T(const eos::Table &t, double rho, double P, double abar, double ye, double &T,
+                           eos::EosOut<double> &o) {
+  double lo = t.Tlo, hi = t.Thi;
+  if (!(T > lo && T < hi)) T = sqrt(lo * hi);
+  for (int it = 0; it < 200; ++it) {
+    if (!eos::eos_rt<double>(t, rho, T, abar, ye, o)) return false;
+    const double dp = P - o.P;
+    if (fabs(dp) <= 1e-14 * P) return true;
+    if (dp > 0.0) lo = T; else hi = T;
+    double Tn = T + dp / o.PT;
+    if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+    T = Tn;
+  }
+  return false;
+}
+
+// gamma_e, gamma_c and T of the background at the Nr shell middles (i < Nr)
+// and the Nr + 1 radii: out[0..] = ge_c, gc_c, T_c (Nr each), ge_f, gc_f
+__global__ void k_sph_bg_stellar(SphDev D, const double *rho_c, const double *p_c, const double *rho_f,
+                                 const double *p_f, double *out, int *fail) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, Nr = D.Nr;
+  if (i >= 2 * Nr + 1) return;
+  const bool radial = i >= Nr;
+  const int k = radial ? i - Nr : i;
+  const double rho = (radial ? rho_f[k] : rho_c[k]) * D.rho_u, P = (radial ? p_f[k] : p_c[k]) * D.p_u;
+  double T = 1e9;
+  eos::EosOut<double> o;
+  if (!sph_p_to_T(D.tab, rho, P, D.abar, D.ye, T, o)) { atomicOr(fail, 1); return; }
+  if (radial) {
+    out[3 * Nr + k] = o.ge;
+    out[4 * Nr + 1 + k] = o.gc;
+  } else {
+    out[k] = o.ge;
+    out[Nr + k] = o.gc;
+    out[2 * Nr + k] = T;
+  }
+}
+
+// ABI cell u -> internal cell c
+__device__ __forceinline__ long sph_cell_of_abi(const SphDev &D, long u) {
+  const long per = (long)D.N * D.N;
+  const long pk = u / per, rem = u - pk * per;
+  const long p = pk / D.Nr, k = pk - p * D.Nr;
+  return k * D.NC + p * per + rem;
+}
+
+// the method's cell field (1/V) sum_f s_f Phi_f x_f (FP64)
+__device__ __forceinline__ V3 cell_field(const SphDev &D, long a, int k, const double *__restrict__ phi) {
+  CellFaces F;
+  cell_faces(D, a, k, F);
+  V3 B = v3(0, 0, 0);
+#pragma unroll
+  for (int m = 0; m < 6; ++m) B = B + F.x[m] * (F.s[m] * phi[F.f[m]]);
+  return B * (1.0 / cell_vol(D, a, k));
+}
+
+// primitives (ABI order) -> conserved cells (internal order) and, with the
+// stellar EOS, the cells' temperatures
+__global__ void k_sph_from_prims(SphDev D, const double *__restrict__ rho_in, const double *__restrict__ vel,
+                                 const double *__restrict__ P_in, const double *__restrict__ phi,
+                                 double *__restrict__ U) {
+  const long u = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (u >= D.ncell) return;
+  const long c = sph_cell_of_abi(D, u), n = D.ncell;
+  const int k = (int)fastdiv((unsigned)c, D.dNC);
+  const long a = c - (long)k * D.NC;
+  const V3 B = cell_field(D, a, k, phi);
+  const double rho = rho_in[u], P = P_in[u];
+  const V3 v = v3(vel[3 * u], vel[3 * u + 1], vel[3 * u + 2]);
+  double eden;   // rho e_int
+  if (D.stellar) {
+    double T = D.T_c ? D.T_c[k] : 1e9;
+    eos::EosOut<double> o;
+    if (!sph_p_to_T(D.tab, rho * D.rho_u, P * D.p_u, D.abar, D.ye, T, o)) {
+      atomicOr(D.dflag, FLAG_NEWTON);
+      T = -1.0;
+    }
+    D.T[c] = T;
+    eden = rho * (o.e / D.e_u);
+  } else {
+    eden = P / (D.gamma - 1.0);
+  }
+  U[c] = rho;
+  U[n + c] = rho * v.x; U[2 * n + c] = rho * v.y; U[3 * n + c] = rho * v.z;
+  U[4 * n + c] = eden + 0.5 * rho * dot3(v, v) + 0.5 * dot3(B, B);
+}
+
+// ABI <-> internal cell temperatures
+__global__ void k_sph_temps(SphDev D, const double *__restrict__ in, double *__restrict__ out, int to_int) {
+  const long u = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (u >= D.ncell) return;
+  const long c = sph_cell_of_abi(D, u);
+  if (to_int) out[c] = in[u];
+  else out[u] = in[c];
+}
+
+// Cold cells (T <= 0) take the network's guess (cold starts only): warp-
+// collective inference on (log10 rho, log10 e_int, X_0) in EOS units from
+// U^n and the FP64 face fluxes; the other cells keep their temperature.  No
+// thread leaves before the inference (the MMA needs the whole warp).
+__global__ void __launch_bounds__(SPT) k_sph_mlp_guess(SphDev D, const double *__restrict__ U,
+                                                       const double *__restrict__ phi) {
+  const long c0 = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const bool in = c0 < D.ncell;
+  const long c = in ? c0 : 0;
+  const double T = D.T[c];
+  const bool need = in && !(T > 0.0);
+  if (!__any_sync(0xffffffffu, need)) return;
+  const long n = D.ncell;
+  const int k = (int)fastdiv((unsigned)c, D.dNC);
+  const long a = c - (long)k * D.NC;
+  const V3 B = cell_field(D, a, k, phi);
+  const double rho = U[c];
+  const V3 m = v3(U[n + c], U[2 * n + c], U[3 * n + c]);
+  const double eint = (U[4 * n + c] - 0.5 * dot3(m, m) / rho - 0.5 * dot3(B, B)) / rho;
+  const bool ok = rho > 0.0 && eint > 0.0;
+  const float lr = ok ? (float)log10(rho * D.rho_u) : D.mlp.c[0];
+  const float le = ok ? (float)log10(eint * D.e_u) : D.mlp.c[1];
+  const float lt = mlp::guess_log10T(D.mlp, lr, le, D.mlp_x0);
+  if (need) D.T[c] = ok ? exp10((double)lt) : (D.T_c ? D.T_c[k] : 1e9);
+}
+
+// Stellar primitives: e_int -> T by Newton (Sect. 2.2) from the cell's last
+// temperature (the shell background's where it has none), then P, gamma_e,
+// gamma_c.  FP64 form (R = double): U is the stage state, the field from the
+// FP64 fluxes phi, W in SoA; mixed form (R = float): U^n + dU (FP64 sums: the
+// low-Mach deviations need P to ~1e-12), the field from the FP32 fluxes phif,
+// FP64 Newton (FP32 iterations first from a far guess, eos_invert_mixed),
+// three float4 records per cell, and with dmax the CFL rate folded in.
+template <typename R>
+__global__ void __launch_bounds__(SPT) k_sph_prims_st(SphDev D, SphWork<R> Wk, const double *__restrict__ U,
+                                                      const float *__restrict__ dU, const double *__restrict__ phi,
+                                                      const float *__restrict__ phif, unsigned long long *dmax) {
+  const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  float rate = 0.f;
+  if (c < D.ncell) {
+    const int k = (int)fastdiv((unsigned)c, D.dNC);
+    const long a = c - (long)k * D.NC, n = D.ncell;
+    double bx, by, bz;
+    if constexpr (sizeof(R) == 4) {   // as k_sph_prims_mx
+      const float rm = D.rm_f[k];
+      float fx = 0.f, fy = 0.f, fz = 0.f;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int s = D.cs[4 * a + m];
+        const float w = (D.csg[4 * a + m] > 0 ? rm : -rm) * phif[(long)k * D.NS + s];
+        fx += D.smid_f[3 * s] * w; fy += D.smid_f[3 * s + 1] * w; fz += D.smid_f[3 * s + 2] * w;
+      }
+      const float wr = D.r_f[k + 1] * phif[D.FA + (long)(k + 1) * D.NC + a] - D.r_f[k] * phif[D.FA + (long)k * D.NC + a];
+      fx += D.cdc_f[3 * a] * wr; fy += D.cdc_f[3 * a + 1] * wr; fz += D.cdc_f[3 * a + 2] * wr;
+      const float iv = D.iom_f[a] * D.ish_f[k];
+      bx = fx * iv; by = fy * iv; bz = fz * iv;
+    } else {
+      const V3 B = cell_field(D, a, k, phi);
+      bx = B.x; by = B.y; bz = B.z;
+    }
+    double rho = U[c], mx = U[n + c], my = U[2 * n + c], mz = U[3 * n + c], E = U[4 * n + c];
+    if (sizeof(R) == 4 && dU) {
+      rho += (double)dU[c]; mx += (double)dU[n + c]; my += (double)dU[2 * n + c]; mz += (double)dU[3 * n + c];
+      E += (double)dU[4 * n + c];
+    }
+    const double ir = 1.0 / rho;
+    const double ux = mx * ir, uy = my * ir, uz = mz * ir;
+    const double eint = (E - 0.5 * (mx * ux + my * uy + mz * uz) - 0.5 * (bx * bx + by * by + bz * bz)) * ir;
+    double T = D.T[c];
+    if (!(T > 0.0)) T = D.T_c ? D.T_c[k] : 1e9;
+    eos::EosOut<double> o;
+    const int it = sizeof(R) == 8
+                       ? eos::eos_invert<double>(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o)
+                       : eos::eos_invert_mixed(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o);
+    if (it < 0) atomicOr(D.dflag, FLAG_NEWTON);
+    D.T[c] = T;
+    const double P = o.P / D.p_u;
+    if (!(rho > 0.0) || !(P > 0.0)) atomicOr(D.dflag, FLAG_NEG);
+    if (!isfinite(rho) || !isfinite(P)) atomicOr(D.dflag, FLAG_NAN);
+    double geh, gch;
+    bg_gammas<double>(D, k, false, geh, gch);
+    const double dP = P - bg_p(D, k), dge = o.ge - geh, dgc = o.gc - gch;
+    if constexpr (sizeof(R) == 4) {
+      // FP64 -> FP32 on the integer pipe (d2f_scaled)
+      float drho = d2f_scaled(D.rho_c ? U[c] - D.rho_c[k] : U[c], 0);
+      if (dU) drho += dU[c];
+      const float fux = d2f_scaled(ux, 0), fuy = d2f_scaled(uy, 0), fuz = d2f_scaled(uz, 0);
+      const float fbx = d2f_scaled(bx, 0), fby = d2f_scaled(by, 0), fbz = d2f_scaled(bz, 0);
+      const float fdP = d2f_scaled(dP, 0);
+      float4 *W4 = reinterpret_cast<float4 *>(Wk.W);
+      W4[3 * c] = make_float4(drho, fux, fuy, fuz);
+      W4[3 * c + 1] = make_float4(fbx, fby, fbz, fdP);
+      W4[3 * c + 2] = make_float4((float)dge, (float)dgc, 0.f, 0.f);
+      if (dmax) {
+        const float frho = (D.rho_cf ? D.rho_cf[k] : 0.f) + drho, fP = (D.p_cf ? D.p_cf[k] : 0.f) + fdP;
+        rate = cfl_rate_mx(D, a, k, frho, fP, fux, fuy, fuz, fbx, fby, fbz, (float)o.gc);
+        if (!(rate == rate)) rate = INFINITY;
+      }
+    } else {
+      Wk.W[SW_RHO * n + c] = rho - bg_rho(D, k);
+      Wk.W[(SW_U + 0) * n + c] = ux; Wk.W[(SW_U + 1) * n + c] = uy; Wk.W[(SW_U + 2) * n + c] = uz;
+      Wk.W[(SW_B + 0) * n + c] = bx; Wk.W[(SW_B + 1) * n + c] = by; Wk.W[(SW_B + 2) * n + c] = bz;
+      Wk.W[SW_P * n + c] = dP;
+      Wk.W[SW_GE * n + c] = dge;
+      Wk.W[SW_GC * n + c] = dgc;
+    }
+  }
+  if (sizeof(R) == 4 && dmax) {   // block maximum; non-negative floats order like their bits
+    for (int o2 = 16; o2 > 0; o2 >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, o2));
+    __shared__ float red[SPT / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rate;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float v = 0.f;
+      for (int w = 0; w < SPT / 32; ++w) v = fmaxf(v, red[w]);
+      atomicMax(dmax, (unsigned long long)__double_as_longlong((double)v));
+    }
+  }
+}
+
+// deviations of cell c, mirrored across a wall of unit normal (nx, ny, nz) when mir
+template <typename R, bool ST = false>
 __device__ __forceinline__ void load_w(const SphDev &D, const SphWork<R> &Wk, long c, bool mir, R nx, R ny, R nz,
                                        R *w) {
   if constexpr (sizeof(R) == 4) {
-    const float4 *W4 = reinterpret_cast<const float4 *>(Wk.W);
-    const float4 a = W4[2 * c], b = W4[2 * c + 1];
+    const float4 *W4 = reinterpret_cast<const float4 *>(Wk.W) + (ST ? 3 : 2) * c;
+    const float4 a = W4[0], b = W4[1];
     w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w; w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    if constexpr (ST) {
+      const float4 g = W4[2];
+      w[SW_GE] = g.x; w[SW_GC] = g.y;
+    }
   } else {
 #pragma unroll
-    for (int v = 0; v < SW_N; ++v) w[v] = Wk.W[v * D.ncell + c];
+    for (int v = 0; v < (ST ? SW_NS : SW_N); ++v) w[v] = Wk.W[v * D.ncell + c];
   }
   if (mir) {
     const R un = R(2) * (w[SW_U] * nx + w[SW_U + 1] * ny + w[SW_U + 2] * nz);
@@ -555,22 +814,26 @@ __device__ __forceinline__ R vl_t(R a, R b, R c) {
 }
 
 // Per-face flux of either form.  MX: the mixed form's FP32 tables and face
-// fluxes (phif); else FP64 tables and phi.
-template <typename R, bool MX>
+// fluxes (phif); else FP64 tables and phi.  ST: the stellar EOS (gamma_e,
+// gamma_c reconstructed as deviations from the face's background, the
+// general-EOS solver).
+template <typename R, bool MX, bool ST = false>
 __global__ void __launch_bounds__(SPT) k_sph_flux(SphDev D, SphWork<R> Wk, const double *__restrict__ phi,
                                                   const float *__restrict__ phif) {
   const long f = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (f >= D.NF) return;
-  R wL[SW_N], wR[SW_N], wLL[SW_N], wRR[SW_N];
-  R n0, n1, n2, A, brho = R(0), bp = R(0);
+  constexpr int NW = ST ? SW_NS : SW_N;
+  R wL[NW], wR[NW], wLL[NW], wRR[NW];
+  R n0, n1, n2, A, brho = R(0), bp = R(0), bge = R(0), bgc = R(0);
   bool wall = false;
   if (f < D.FA) {   // angular face (s, k)
     const int k = (int)fastdiv((unsigned)f, D.dNS);
     const long s = f - (long)k * D.NS, base = (long)k * D.NC;
-    load_w<R>(D, Wk, base + D.sL[s], false, R(0), R(0), R(0), wL);
-    load_w<R>(D, Wk, base + D.sR[s], false, R(0), R(0), R(0), wR);
-    load_w<R>(D, Wk, base + D.sLL[s], false, R(0), R(0), R(0), wLL);
-    load_w<R>(D, Wk, base + D.sRR[s], false, R(0), R(0), R(0), wRR);
+    load_w<R, ST>(D, Wk, base + D.sL[s], false, R(0), R(0), R(0), wL);
+    load_w<R, ST>(D, Wk, base + D.sR[s], false, R(0), R(0), R(0), wR);
+    load_w<R, ST>(D, Wk, base + D.sLL[s], false, R(0), R(0), R(0), wLL);
+    load_w<R, ST>(D, Wk, base + D.sRR[s], false, R(0), R(0), R(0), wRR);
+    if constexpr (ST) bg_gammas<R>(D, k, false, bge, bgc);
     if constexpr (MX) {
       n0 = D.sn_f[3 * s]; n1 = D.sn_f[3 * s + 1]; n2 = D.sn_f[3 * s + 2];
       A = D.hdr2_f[k] * D.sth_f[s];
@@ -595,30 +858,31 @@ __global__ void __launch_bounds__(SPT) k_sph_flux(SphDev D, SphWork<R> Wk, const
       if (D.rho_f) { brho = D.rho_f[k]; bp = D.p_f[k]; }
     }
     const long c0 = a, cst = D.NC;   // cell (a, kk) = c0 + kk cst
+    if constexpr (ST) bg_gammas<R>(D, k, true, bge, bgc);
     if (k == 0) {            // inner wall: the ghost side mirrors cells 0 and 1
       wall = true;
-      load_w<R>(D, Wk, c0, false, n0, n1, n2, wR);
-      load_w<R>(D, Wk, c0 + cst, false, n0, n1, n2, wRR);
-      load_w<R>(D, Wk, c0, true, n0, n1, n2, wL);
-      load_w<R>(D, Wk, c0 + cst, true, n0, n1, n2, wLL);
+      load_w<R, ST>(D, Wk, c0, false, n0, n1, n2, wR);
+      load_w<R, ST>(D, Wk, c0 + cst, false, n0, n1, n2, wRR);
+      load_w<R, ST>(D, Wk, c0, true, n0, n1, n2, wL);
+      load_w<R, ST>(D, Wk, c0 + cst, true, n0, n1, n2, wLL);
     } else if (k == Nr) {    // outer wall
       wall = true;
-      load_w<R>(D, Wk, c0 + (Nr - 1) * cst, false, n0, n1, n2, wL);
-      load_w<R>(D, Wk, c0 + (Nr - 2) * cst, false, n0, n1, n2, wLL);
-      load_w<R>(D, Wk, c0 + (Nr - 1) * cst, true, n0, n1, n2, wR);
-      load_w<R>(D, Wk, c0 + (Nr - 2) * cst, true, n0, n1, n2, wRR);
+      load_w<R, ST>(D, Wk, c0 + (Nr - 1) * cst, false, n0, n1, n2, wL);
+      load_w<R, ST>(D, Wk, c0 + (Nr - 2) * cst, false, n0, n1, n2, wLL);
+      load_w<R, ST>(D, Wk, c0 + (Nr - 1) * cst, true, n0, n1, n2, wR);
+      load_w<R, ST>(D, Wk, c0 + (Nr - 2) * cst, true, n0, n1, n2, wRR);
     } else {                 // beside a wall the far cell is the near one's mirror
-      load_w<R>(D, Wk, c0 + (k - 1) * cst, false, n0, n1, n2, wL);
-      load_w<R>(D, Wk, c0 + k * cst, false, n0, n1, n2, wR);
-      if (k >= 2) load_w<R>(D, Wk, c0 + (k - 2) * cst, false, n0, n1, n2, wLL);
-      else load_w<R>(D, Wk, c0, true, n0, n1, n2, wLL);
-      if (k + 1 <= Nr - 1) load_w<R>(D, Wk, c0 + (k + 1) * cst, false, n0, n1, n2, wRR);
-      else load_w<R>(D, Wk, c0 + (Nr - 1) * cst, true, n0, n1, n2, wRR);
+      load_w<R, ST>(D, Wk, c0 + (k - 1) * cst, false, n0, n1, n2, wL);
+      load_w<R, ST>(D, Wk, c0 + k * cst, false, n0, n1, n2, wR);
+      if (k >= 2) load_w<R, ST>(D, Wk, c0 + (k - 2) * cst, false, n0, n1, n2, wLL);
+      else load_w<R, ST>(D, Wk, c0, true, n0, n1, n2, wLL);
+      if (k + 1 <= Nr - 1) load_w<R, ST>(D, Wk, c0 + (k + 1) * cst, false, n0, n1, n2, wRR);
+      else load_w<R, ST>(D, Wk, c0 + (Nr - 1) * cst, true, n0, n1, n2, wRR);
     }
   }
-  R ql[SW_N], qr[SW_N];
+  R ql[NW], qr[NW];
 #pragma unroll
-  for (int v = 0; v < SW_N; ++v) {
+  for (int v = 0; v < NW; ++v) {
     ql[v] = wL[v] + R(0.5) * vl_t<R>(wLL[v], wL[v], wR[v]);
     qr[v] = wR[v] - R(0.5) * vl_t<R>(wL[v], wR[v], wRR[v]);
   }
@@ -658,10 +922,17 @@ __global__ void __launch_bounds__(SPT) k_sph_flux(SphDev D, SphWork<R> Wk, const
   }
   R fl[7];
   int up;
-  // the mixed form takes the packed-FP32 solver (left and right sides as the
-  // two lanes of each f32x2 instruction): same formulas, FP32 rounding apart
-  if constexpr (MX) x2::riemann_ideal_lr(wl, wr, bn, brho, bp, D.riemann, mthr, fl, up, K);
-  else riemann_dev<R, 0, true>(wl, wr, bn, brho, bp, K.g, K.g, 0, D.riemann, mthr, fl, up, K);
+  if constexpr (ST) {   // the general-EOS solver on the reconstructed gamma deviations
+    wl[RD_GE] = ql[SW_GE]; wl[RD_GC] = ql[SW_GC];
+    wr[RD_GE] = qr[SW_GE]; wr[RD_GC] = qr[SW_GC];
+    riemann_dev<R, 0, false>(wl, wr, bn, brho, bp, bge, bgc, 0, D.riemann, mthr, fl, up);
+  } else if constexpr (MX) {
+    // the mixed form takes the packed-FP32 solver (left and right sides as the
+    // two lanes of each f32x2 instruction): same formulas, FP32 rounding apart
+    x2::riemann_ideal_lr(wl, wr, bn, brho, bp, D.riemann, mthr, fl, up, K);
+  } else {
+    riemann_dev<R, 0, true>(wl, wr, bn, brho, bp, K.g, K.g, 0, D.riemann, mthr, fl, up, K);
+  }
   if (wall) {   // a symmetry plane: only the normal-momentum flux survives
 #pragma unroll
     for (int q = 0; q < 7; ++q)
@@ -701,8 +972,8 @@ template <typename R>
 __device__ __forceinline__ R ecl(const SphDev &D, const SphWork<R> &Wk, long c, R lx, R ly, R lz) {   // (-u x B) . l
   R ux, uy, uz, bx, by, bz;
   if constexpr (sizeof(R) == 4) {
-    const float4 *W4 = reinterpret_cast<const float4 *>(Wk.W);
-    const float4 a = W4[2 * c], b = W4[2 * c + 1];
+    const float4 *W4 = reinterpret_cast<const float4 *>(Wk.W) + (long)D.wq * c;
+    const float4 a = W4[0], b = W4[1];
     ux = a.y; uy = a.z; uz = a.w; bx = b.x; by = b.y; bz = b.z;
   } else {
     const long n = D.ncell;
@@ -927,7 +1198,13 @@ __global__ void k_sph_dt(SphDev D, SphWork<double> Wk, unsigned long long *dmax)
     const double P = Wk.W[SW_P * n + c] + bg_p(D, k);
     const V3 u = v3(Wk.W[SW_U * n + c], Wk.W[(SW_U + 1) * n + c], Wk.W[(SW_U + 2) * n + c]);
     const V3 b = v3(Wk.W[SW_B * n + c], Wk.W[(SW_B + 1) * n + c], Wk.W[(SW_B + 2) * n + c]);
-    const double a2 = D.gamma * P / rho, b2 = dot3(b, b) / rho;
+    double gam = D.gamma;
+    if (D.stellar) {
+      double geh;
+      bg_gammas<double>(D, k, false, geh, gam);
+      gam += Wk.W[SW_GC * n + c];
+    }
+    const double a2 = gam * P / rho, b2 = dot3(b, b) / rho;
     CellFaces F;
     cell_faces(D, a, k, F);
     double sum = 0.0;
@@ -1047,6 +1324,7 @@ struct phl_sphere {
   unsigned long long *dmax = nullptr;
   long nabi = 0;
   long steps = 0;
+  bool cold = false;       // stellar: cells without a temperature (the network's guess pending)
 };
 
 namespace {
@@ -1086,7 +1364,7 @@ std::vector<float> to_f(const std::vector<double> &v) { return std::vector<float
 template <typename R>
 cudaError_t alloc_work(phl_sphere *S, SphWork<R> &Wk) {
   const SphDev &D = S->D;
-  cudaError_t e = alloc_n(S, &Wk.W, SW_N * D.ncell);
+  cudaError_t e = alloc_n(S, &Wk.W, (sizeof(R) == 4 ? 4 * D.wq : (D.stellar ? SW_NS : SW_N)) * D.ncell);
   if (e == cudaSuccess) e = alloc_n(S, &Wk.FC, 5 * D.NF);
   if (e == cudaSuccess) e = alloc_n(S, &Wk.EF, (sizeof(R) == 4 ? 4 : 3) * D.NF);
   if (e == cudaSuccess) e = alloc_n(S, &Wk.EE, D.NE);
@@ -1101,6 +1379,7 @@ phl_status sph_flags(phl_sphere *S) {
   if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "sphere: %s", cudaGetErrorString(e));
   if (f & FLAG_NAN) return (phl_status)set_error(PHL_ENAN, "sphere: non-finite value in the state");
   if (f & FLAG_NEG) return (phl_status)set_error(PHL_ENEGATIVE, "sphere: non-positive density or pressure");
+  if (f & FLAG_NEWTON) return (phl_status)set_error(PHL_ENEWTON, "sphere: EOS temperature not found");
   return PHL_OK;
 }
 
@@ -1112,17 +1391,36 @@ void timed(phl_sphere *S, int cls, F &&launch) {
   S->prof.end(S->s);
 }
 
+// The primitives of a stage input: U (FP64 form: the stage state; mixed:
+// U^n, with the increments dU from the second stage on), its face fluxes
+// (phi FP64, phif the mixed form's FP32 copy); dmax (mixed): fold the CFL
+// rate.  A stellar shell whose cells lack temperatures first takes the
+// network's guesses (U^n and the FP64 fluxes of the state).
+void sph_prims(phl_sphere *S, const double *U, const float *dU, const double *phi, unsigned long long *dmax) {
+  const SphDev &D = S->D;
+  timed(S, KC_SPH_PRIM, [&] {
+    if (S->cold && D.use_mlp) k_sph_mlp_guess<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->U, S->phi);
+    S->cold = false;
+    if (D.stellar) {
+      if (S->mixed) k_sph_prims_st<float><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, U, dU, nullptr, S->phif, dmax);
+      else k_sph_prims_st<double><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, U, nullptr, phi, nullptr, nullptr);
+    } else if (S->mixed) {
+      k_sph_prims_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, U, dU, S->phif, dmax);
+    } else {
+      k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, U, phi);
+    }
+  });
+}
+
 // the CFL step of U^n (Eq. cfl) into S->dt; leaves the primitives of U^n in W
 void sph_dt(phl_sphere *S) {
   const SphDev &D = S->D;
   if (S->mixed) {   // folded into the primitives
-    timed(S, KC_SPH_PRIM, [&] {
-      k_sph_prims_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->U, nullptr, S->phif, S->dmax);
-    });
+    sph_prims(S, S->U, nullptr, S->phi, S->dmax);
     timed(S, KC_SPH_DT, [&] { k_sph_dt_fin<<<1, 1, 0, S->s>>>(D.cfl, S->dmax, S->dt); });
     return;
   }
-  timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, S->U, S->phi); });
+  sph_prims(S, S->U, nullptr, S->phi, nullptr);
   timed(S, KC_SPH_DT, [&] {
     k_sph_dt<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, S->dmax);
     k_sph_dt_fin<<<1, 1, 0, S->s>>>(D.cfl, S->dmax, S->dt);
@@ -1144,6 +1442,19 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
     return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: bad solver");
   if (d->precision != PHL_FP64 && d->precision != PHL_MIXED)
     return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: bad precision");
+  if (d->eos != PHL_EOS_IDEAL && d->eos != PHL_EOS_STELLAR)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: bad eos");
+  if (d->eos == PHL_EOS_STELLAR) {
+    bool ok = d->eos_table && d->nspec >= 1 && d->nspec <= PHL_MAXSPEC && d->rho_unit > 0.0 && d->p_unit > 0.0;
+    double xs = 0.0;
+    for (int l = 0; ok && l < d->nspec; ++l) {
+      ok = d->A[l] > 0.0 && d->Z[l] > 0.0 && d->X[l] >= 0.0;
+      xs += d->X[l];
+    }
+    if (!ok || !(xs > 0.0))
+      return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: the stellar EOS needs eos_table, nspec 1..%d, "
+                                               "A, Z > 0, X >= 0 (not all 0), rho_unit, p_unit > 0", PHL_MAXSPEC);
+  }
   const bool any = d->rho_c || d->p_c || d->rho_f || d->p_f, all = d->rho_c && d->p_c && d->rho_f && d->p_f;
   if (any && !all) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_create: the background needs all four profiles");
   // face and edge indices must fit int32 per shell and long overall
@@ -1197,6 +1508,53 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
     std::vector<double> eh(Nr);
     for (int k = 0; k < Nr; ++k) eh[k] = d->p_c[k] / (d->gamma - 1.0);
     U(&D.eh_c, eh);
+  }
+  D.wq = 2;
+  if (d->eos == PHL_EOS_STELLAR && e == cudaSuccess) {
+    D.stellar = 1;
+    D.wq = 3;
+    D.tab = *eos_table_view(d->eos_table);
+    double inv_abar = 0.0, ye = 0.0;
+    for (int l = 0; l < d->nspec; ++l) {
+      inv_abar += d->X[l] / d->A[l];
+      ye += d->X[l] * d->Z[l] / d->A[l];
+    }
+    D.abar = 1.0 / inv_abar;
+    D.ye = ye;
+    D.rho_u = d->rho_unit; D.p_u = d->p_unit; D.e_u = d->p_unit / d->rho_unit;
+    D.ntol = d->newton_tol > 0.0 ? d->newton_tol : 1e-11;
+    D.nmaxit = d->newton_maxit > 0 ? d->newton_maxit : 50;
+    if (d->mlp) {
+      D.use_mlp = 1;
+      D.mlp = mlp_view(d->mlp);
+      D.mlp_x0 = (float)(d->nspec > 1 ? d->X[0] / (d->X[0] + d->X[1]) : 1.0);
+    }
+    e = alloc_n(S, &D.T, D.ncell);
+    if (e == cudaSuccess && d->rho_c) {   // the background's gamma_e, gamma_c and T from the EOS
+      double *bg = nullptr;
+      int *fail = nullptr;
+      e = alloc_n(S, &bg, 5L * Nr + 2);
+      if (e == cudaSuccess) e = alloc_n(S, &fail, 1);
+      if (e == cudaSuccess) {
+        k_sph_bg_stellar<<<(2 * Nr + 1 + 63) / 64, 64>>>(D, D.rho_c, D.p_c, D.rho_f, D.p_f, bg, fail);
+        e = cudaGetLastError();
+      }
+      std::vector<double> h(5L * Nr + 2);
+      int f = 0;
+      if (e == cudaSuccess) e = cudaMemcpy(&f, fail, sizeof(int), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(h.data(), bg, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && f) {
+        phl_sphere_destroy(S);
+        return (phl_status)set_error(PHL_ENEWTON, "phl_sphere_create: no EOS temperature for the background");
+      }
+      D.ge_c = bg; D.gc_c = bg + Nr; D.T_c = bg + 2 * Nr; D.ge_f = bg + 3 * Nr; D.gc_f = bg + 4 * Nr + 1;
+      if (S->mixed && e == cudaSuccess) {
+        U(&D.ge_cf, std::vector<float>(h.begin(), h.begin() + Nr));
+        U(&D.gc_cf, std::vector<float>(h.begin() + Nr, h.begin() + 2 * Nr));
+        U(&D.ge_ff, std::vector<float>(h.begin() + 3 * Nr, h.begin() + 4 * Nr + 1));
+        U(&D.gc_ff, std::vector<float>(h.begin() + 4 * Nr + 1, h.end()));
+      }
+    }
   }
   if (S->mixed) {   // FP32 copies of the geometry, radial factors and profiles
     std::vector<float> iom(M.NC), cw(2 * M.NC), ce(6 * M.NC);
@@ -1319,9 +1677,79 @@ phl_status phl_sphere_set_state(phl_sphere *S, const double *cons, const double 
     k_sph_to_float<<<nblk(S->D.NF), SPT, 0, S->s>>>(S->D.NF, S->phi, S->phif);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && S->D.stellar) {   // no temperatures yet: a cold start
+    e = cudaMemsetAsync(S->D.T, 0, S->D.ncell * sizeof(double), S->s);
+    S->cold = true;
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(S->D.dflag, 0, sizeof(int), S->s);
   if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
   if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_set_state: %s", cudaGetErrorString(e));
+  return PHL_OK;
+}
+
+phl_status phl_sphere_set_prims(phl_sphere *S, const double *rho, const double *vel, const double *P,
+                                const double *pa, const double *pb, const double *pr, int where) {
+  if (!S || !rho || !vel || !P || !pa || !pb || !pr)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_prims: null argument");
+  if (where != PHL_HOST && where != PHL_DEVICE)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_prims: bad where");
+  const cudaMemcpyKind kd = where == PHL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const SphDev &D = S->D;
+  const long N = D.N, Nr = D.Nr, na = 6 * Nr * N * (N + 1), nr = 6 * (Nr + 1) * N * N, nc = D.ncell;
+  cudaError_t e = cudaMemcpyAsync(S->abi_buf, pa, na * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->abi_buf + na, pb, na * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->abi_buf + 2 * na, pr, nr * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) {
+    k_sph_gather_faces<<<nblk(S->nabi), SPT, 0, S->s>>>(D, S->AM, S->nabi, S->abi_buf, S->phi);
+    e = cudaGetLastError();
+  }
+  // the primitives in the buffer: rho, P, then vel (3 per cell)
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->abi_buf, rho, nc * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->abi_buf + nc, P, nc * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->abi_buf + 2 * nc, vel, 3 * nc * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(D.dflag, 0, sizeof(int), S->s);
+  if (e == cudaSuccess) {
+    k_sph_from_prims<<<nblk(nc), SPT, 0, S->s>>>(D, S->abi_buf, S->abi_buf + 2 * nc, S->abi_buf + nc, S->phi, S->U);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && S->mixed) {
+    k_sph_to_float<<<nblk(D.NF), SPT, 0, S->s>>>(D.NF, S->phi, S->phif);
+    e = cudaGetLastError();
+  }
+  S->cold = false;
+  if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_set_prims: %s", cudaGetErrorString(e));
+  return where == PHL_HOST ? sph_flags(S) : PHL_OK;
+}
+
+phl_status phl_sphere_set_temperature(phl_sphere *S, const double *T, int where) {
+  if (!S || !T) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_temperature: null argument");
+  if (!S->D.stellar) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_temperature: an ideal-gas shell");
+  if (where != PHL_HOST && where != PHL_DEVICE)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_temperature: bad where");
+  const cudaMemcpyKind kd = where == PHL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaMemcpyAsync(S->abi_buf, T, S->D.ncell * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) {
+    k_sph_temps<<<nblk(S->D.ncell), SPT, 0, S->s>>>(S->D, S->abi_buf, S->D.T, 1);
+    e = cudaGetLastError();
+  }
+  S->cold = true;   // any value <= 0 marks a cell without one
+  if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_set_temperature: %s", cudaGetErrorString(e));
+  return PHL_OK;
+}
+
+phl_status phl_sphere_get_temperature(phl_sphere *S, double *T, int where) {
+  if (!S || !T) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_get_temperature: null argument");
+  if (!S->D.stellar) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_get_temperature: an ideal-gas shell");
+  if (where != PHL_HOST && where != PHL_DEVICE)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_get_temperature: bad where");
+  const cudaMemcpyKind kd = where == PHL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  k_sph_temps<<<nblk(S->D.ncell), SPT, 0, S->s>>>(S->D, S->D.T, S->abi_buf, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(T, S->abi_buf, S->D.ncell * sizeof(double), kd, S->s);
+  if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_get_temperature: %s", cudaGetErrorString(e));
   return PHL_OK;
 }
 
@@ -1373,11 +1801,11 @@ phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
       if (S->mixed) {
         // cells: stage input U^n + dU; increments out dU = b (dU - dt R)
         const float *dUin = st == 0 ? nullptr : S->dU;
-        if (prims)
-          timed(S, KC_SPH_PRIM, [&] {
-            k_sph_prims_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, S->U, dUin, S->phif, nullptr);
-          });
-        timed(S, KC_SPH_FLUX, [&] { k_sph_flux<float, true><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin, S->phif); });
+        if (prims) sph_prims(S, S->U, dUin, pin, nullptr);
+        timed(S, KC_SPH_FLUX, [&] {
+          if (D.stellar) k_sph_flux<float, true, true><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin, S->phif);
+          else k_sph_flux<float, true><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin, S->phif);
+        });
         timed(S, KC_SPH_EMF, [&] { k_sph_emf<float, true><<<nblk(D.NE), SPT, 0, S->s>>>(D, S->W32); });
         timed(S, KC_SPH_UPDATE_FACES, [&] {
           k_sph_update_faces<<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32.EE, pin, S->phi, pout, a, b, S->dt, S->phif);
@@ -1390,9 +1818,11 @@ phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
         // cells: stage input U1 (U^n at the first stage): out = a U^n + b (in - dt R)
         const double *Uin = st == 0 ? S->U : S->U1;
         double *Uout = last ? S->U : S->U1;
-        if (prims)
-          timed(S, KC_SPH_PRIM, [&] { k_sph_prims<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, Uin, pin); });
-        timed(S, KC_SPH_FLUX, [&] { k_sph_flux<double, false><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64, pin, nullptr); });
+        if (prims) sph_prims(S, Uin, nullptr, pin, nullptr);
+        timed(S, KC_SPH_FLUX, [&] {
+          if (D.stellar) k_sph_flux<double, false, true><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64, pin, nullptr);
+          else k_sph_flux<double, false><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64, pin, nullptr);
+        });
         timed(S, KC_SPH_EMF, [&] { k_sph_emf<double, false><<<nblk(D.NE), SPT, 0, S->s>>>(D, S->W64); });
         timed(S, KC_SPH_UPDATE_FACES, [&] {
           k_sph_update_faces<<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W64.EE, pin, S->phi, pout, a, b, S->dt, nullptr);

@@ -202,6 +202,9 @@ SPHERE_CASES = [
     ("unknown precision", set_field("precision", 7), "bad precision"),
     ("partial background", set_field("p_f", None), "all four profiles"),
     ("too many faces", lambda d: (setattr(d, "N", 8000), setattr(d, "Nr", 8000)), "2^31"),
+    ("unknown eos", set_field("eos", 3), "bad eos"),
+    ("stellar without a table", lambda d: (setattr(d, "eos", 1), setattr(d, "nspec", 1), setattr(d, "rho_unit", 1.0),
+                                           setattr(d, "p_unit", 1.0)), "eos_table"),
 ]
 
 
@@ -225,4 +228,7 @@ def test_sphere_null_handles(P):
     assert L.phl_sphere_set_state(None, None, None, None, None, 0) == EINVAL
     assert L.phl_sphere_get_state(None, None, None, None, None, 0) == EINVAL
     assert L.phl_sphere_compute_dt(None, None) == EINVAL
+    assert L.phl_sphere_set_prims(None, None, None, None, None, None, None, 0) == EINVAL
+    assert L.phl_sphere_set_temperature(None, None, 0) == EINVAL
+    assert L.phl_sphere_get_temperature(None, None, 0) == EINVAL
     L.phl_sphere_destroy(None)

@@ -292,3 +292,144 @@ def test_full_shell_divb_and_conservation(P, precision, cons_tol):
     assert float((st["cons"][1:4] - pr.cons[1:4]).abs().max()) > 0
     del st, pr
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# the stellar EOS on the shell (Sect. 2.2: ions, radiation, the e-/e+ table;
+# 16O/28Si 0.5/0.5 everywhere).  The problem comes in primitives: the device
+# and the oracle each build the energy and the temperatures with their own
+# EOS table.
+
+
+@pytest.fixture(scope="module")
+def st_tables(P):
+    return P.EosTable(), O.EosTable()
+
+
+def stellar_pair(P, pr, tables, precision="fp64", mlp=None, wb=True):
+    dtab, otab = tables
+    o = O.Sphere(pr, riemann=pr.riemann, cfl=pr.cfl, mach_thr=pr.mach_thr, eos_table=otab, wb=wb)
+    s = P.Sphere.from_problem(pr, precision=precision, eos_table=dtab, mlp=mlp, wb=wb)
+    s.load(pr)
+    return s, o
+
+
+def temps(pr, T):
+    return np.asarray(T).reshape(6, pr.Nr, pr.N, pr.N)
+
+
+STELLAR_CASES = [
+    ("polytrope_field_heat", dict(N=5, Nr=4, amp=2e-2, beta=1e2, vel_amp=0.05, heat_frac=0.3, mach_heat=0.05), 5,
+     "lhlld", True),
+    ("no_background", dict(N=5, Nr=4, amp=2e-2, beta=1e2, vel_amp=0.05, heat_frac=0.3, mach_heat=0.05), 4,
+     "lhlld", False),
+    ("hlld", dict(N=4, Nr=4, amp=2e-2, beta=30.0, vel_amp=0.1, heat_frac=0.0), 4, "hlld", True),
+    ("uniform_medium", dict(N=4, Nr=3, uniform=True, amp=5e-2, beta=1e3, vel_amp=0.05, heat_frac=0.0), 5,
+     "lhlld", True),
+]
+
+
+@pytest.mark.parametrize("name,kw,nsteps,solver,wb", STELLAR_CASES, ids=[c[0] for c in STELLAR_CASES])
+def test_stellar_sphere_matches_oracle(P, st_tables, name, kw, nsteps, solver, wb):
+    kw = dict(kw)
+    N, Nr = kw.pop("N"), kw.pop("Nr")
+    pr = W.shell_problem(N, Nr, eos="stellar", **kw)
+    pr.riemann = solver
+    s, o = stellar_pair(P, pr, st_tables, wb=wb)
+    # the loaded state: E and T from the primitives by each side's EOS
+    e0 = errors(s.get_state(), o.state0)
+    assert all(v <= TOL for v in e0.values()), e0
+    assert rel_linf(s.get_temperature(), temps(pr, o.state0["T"])) <= TOL
+    ref, _ = o.run(nsteps)
+    s.step(nsteps)
+    st = s.get_state()
+    err = errors(st, ref)
+    err["T"] = rel_linf(s.get_temperature(), temps(pr, ref["T"]))
+    s.close()
+    print(name, {k: f"{v:.2e}" for k, v in err.items()})
+    assert all(v <= TOL for v in err.values()), err
+    assert np.abs(ref["cons"][1:4] - o.state0["cons"][1:4]).max() > 0
+    assert np.abs(o.divb(st)).max() <= 1e-13 * max(np.abs(st["pa"]).max(), np.abs(st["pr"]).max(), 1e-300)
+
+
+def stellar_e_hat(pr, otab):
+    """The background's energy density rho_hat e(rho_hat, T_hat) per shell
+    (code units), from the oracle's EOS."""
+    cfg = O.stellar_cfg(pr.meta["A"], pr.meta["Z"], otab)
+    ru, pu = pr.meta["rho_u"], pr.meta["p_u"]
+    out = np.zeros(pr.Nr)
+    T = 1e9
+    for k in range(pr.Nr):
+        rho, p = pr.bg["rho_c"][k] * ru, pr.bg["p_c"][k] * pu
+        T = O.p_to_T(cfg, rho, p, pr.meta["X"], T)
+        out[k] = pr.bg["rho_c"][k] * O.eos_rt(cfg, rho, T, pr.meta["X"])["e"] * ru / pu
+    return out
+
+
+def test_stellar_sphere_mixed_l1_deviations(P, st_tables):
+    """The mixed form (FP32 deviations, FP64 inversion) of the stellar shell,
+    each step with the oracle's CFL step: L1 of the deviations from the
+    background per field within 1e-5 of the FP64 oracle."""
+    pr = W.shell_problem(8, 8, eos="stellar", amp=1e-2, beta=1e3, vel_amp=0.02, mach_heat=0.02)
+    s, o = stellar_pair(P, pr, st_tables, precision="mixed")
+    st = o.state0
+    for _ in range(20):
+        dt = o.dt(st)
+        st, _ = o.run(1, state=st, dt_fixed=dt)
+        s.step(1, dt=dt)
+    out = s.get_state()
+    T = s.get_temperature()
+    s.close()
+    rho_hat = pr.bg["rho_c"][None, :, None, None]
+    e_hat = stellar_e_hat(pr, st_tables[1])[None, :, None, None]
+    l1 = {}
+    for name, v, hat in (("rho", 0, rho_hat), ("E", 4, e_hat)):
+        a, b = out["cons"][v] - hat, st["cons"][v] - hat
+        l1[name] = np.abs(a - b).sum() / np.abs(b).sum()
+    l1["m"] = np.abs(out["cons"][1:4] - st["cons"][1:4]).sum() / np.abs(st["cons"][1:4]).sum()
+    l1["B"] = sum(np.abs(out[k] - st[k]).sum() for k in ("pa", "pb", "pr")) / \
+        sum(np.abs(st[k]).sum() for k in ("pa", "pb", "pr"))
+    print("stellar sphere mixed L1 of deviations:", {k: f"{v:.2e}" for k, v in l1.items()})
+    for k, v in l1.items():
+        assert v <= 1e-5, (k, v)
+    assert rel_linf(T, temps(pr, st["T"])) <= 1e-6
+    assert np.abs(o.divb(out)).max() <= 1e-13 * max(np.abs(out["pa"]).max(), np.abs(out["pr"]).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stellar_sphere_rest(P, st_tables, precision):
+    """The stellar polytrope at rest stays at rest (both forms)."""
+    pr = W.shell_problem(6, 6, eos="stellar", amp=0.0, beta=0.0, heat_frac=0.0)
+    s, _ = stellar_pair(P, pr, st_tables, precision=precision)
+    st0 = s.get_state()
+    s.step(4)
+    st = s.get_state()
+    s.close()
+    cs = math.sqrt(5.0 / 3.0 * pr.bg["p_c"].max() / pr.bg["rho_c"].min())
+    assert np.abs(st["cons"][1:4] / st["cons"][0]).max() <= 1e-12 * cs
+    assert np.abs(st["cons"][4] / st0["cons"][4] - 1.0).max() <= 1e-13
+
+
+def test_stellar_sphere_cold_start_network_guess(P, st_tables):
+    """A state loaded without temperatures: the first inversion starts from
+    the network's guess (cold start) or from the shell background's
+    temperature; both converge to the temperatures the loaded primitives
+    gave, and the steps agree with the warm run to the Newton tolerance."""
+    pr = W.shell_problem(5, 4, eos="stellar", amp=2e-2, beta=1e2, vel_amp=0.05, heat_frac=0.3, mach_heat=0.05)
+    m = P.Mlp(seed=11)
+    m.train(st_tables[0], nsamples=2_000_000, epochs=4, batch=1024, lr=1e-2, seed=99)
+    warm, _ = stellar_pair(P, pr, st_tables)
+    st0 = warm.get_state()
+    T0 = warm.get_temperature()
+    warm.step(2, dt=1e-3)
+    ref, Tref = warm.get_state(), warm.get_temperature()
+    for mlp in (m, None):
+        s = P.Sphere.from_problem(pr, eos_table=st_tables[0], mlp=mlp)
+        s.set_state(st0["cons"], st0["pa"], st0["pb"], st0["pr"])
+        s.step(2, dt=1e-3)
+        out, T = s.get_state(), s.get_temperature()
+        s.close()
+        assert rel_linf(T, Tref) <= 1e-12
+        err = errors(out, ref)
+        assert all(v <= 1e-12 for v in err.values()), (mlp is not None, err)
+    assert np.abs(T0 - Tref).max() > 0   # the temperatures did move
