@@ -748,6 +748,7 @@ def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, N
         del st
     del pr
     torch.cuda.empty_cache()
+    S.set_graph(True)                 # each step one captured CUDA graph
     S.step(warmup)
     S.check()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -776,7 +777,7 @@ def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, N
            "cells": cells, "faces": faces, "edges": counts["edges"],
            "value": cells * STAGES * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
            "steps": steps, "warmup": warmup, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
-           "launches_per_step": sum(v[0] for v in kt.values())}
+           "launches_per_step": sum(v[0] for v in kt.values()), "graph": True}
     roof = {"kernel": name, "avg_launch_ms": avg, "launches": launches}
     if eos == "stellar":
         roof["note"] = ("stellar EOS: the inversion (sph_prim) and the general-EOS solver (sph_flux) run FP64 "

@@ -681,6 +681,12 @@ phl_status phl_sphere_compute_dt(phl_sphere *s, double *dt_out);
  * on the device); asynchronous on the stream.  Errors show in
  * phl_sphere_check / get_state. */
 phl_status phl_sphere_step(phl_sphere *s, double dt, int nsteps);
+/* on != 0: phl_sphere_step replays one captured CUDA graph per step (the
+ * step's launches, captured at the first step of each dt mode: the device
+ * CFL step, or a fixed dt, whose value is part of the capture); the
+ * results are those of the direct launches.  Needs desc.stream; not used
+ * while per-kernel timing is on or for a cold start's first step. */
+phl_status phl_sphere_set_graph(phl_sphere *s, int on);
 /* Synchronises the stream; PHL_ENEGATIVE / PHL_ENAN as in get_state,
  * PHL_ENEWTON when a stellar inversion did not converge. */
 phl_status phl_sphere_check(phl_sphere *s);

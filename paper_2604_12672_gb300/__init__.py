@@ -152,6 +152,7 @@ _SIGS = {
     "phl_sphere_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "phl_sphere_check": (C.c_int, [C.c_void_p]),
     "phl_sphere_set_prims": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_int]),
+    "phl_sphere_set_graph": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_sphere_set_temperature": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "phl_sphere_get_temperature": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "phl_sphere_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -813,6 +814,10 @@ class Sphere:
 
     def check(self):
         _check(lib().phl_sphere_check(self.h))
+
+    def set_graph(self, on=True):
+        """Replay each step as one captured CUDA graph (needs a stream)."""
+        _check(lib().phl_sphere_set_graph(self.h, int(bool(on))))
 
     def set_timing(self, on=True):
         _check(lib().phl_sphere_set_timing(self.h, int(bool(on))))

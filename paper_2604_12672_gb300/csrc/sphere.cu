@@ -1325,6 +1325,12 @@ struct phl_sphere {
   long nabi = 0;
   long steps = 0;
   bool cold = false;       // stellar: cells without a temperature (the network's guess pending)
+  // the step as a CUDA graph (phl_sphere_set_graph): captured for one dt mode
+  // (device CFL step, or a fixed dt whose value is part of the capture)
+  bool use_graph = false;
+  cudaGraphExec_t gexec = nullptr;
+  bool g_fixed = false;
+  double g_dt = 0.0;
 };
 
 namespace {
@@ -1613,6 +1619,7 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
 
 void phl_sphere_destroy(phl_sphere *S) {
   if (!S) return;
+  if (S->gexec) cudaGraphExecDestroy(S->gexec);
   S->prof.release();
   for (void *p : S->allocs) cudaFree(p);
   delete S;
@@ -1782,8 +1789,57 @@ phl_status phl_sphere_compute_dt(phl_sphere *S, double *dt_out) {
   return sph_flags(S);
 }
 
-phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
-  if (!S || nsteps < 0 || !(dt == dt)) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_step: bad arguments");
+phl_status phl_sphere_set_graph(phl_sphere *S, int on) {
+  if (!S) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_graph: null sphere");
+  if (on && !S->s) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_graph: needs a stream of its own");
+  S->use_graph = on != 0;
+  if (!S->use_graph && S->gexec) {
+    cudaGraphExecDestroy(S->gexec);
+    S->gexec = nullptr;
+  }
+  return PHL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+void sph_steps(phl_sphere *S, double dt, int nsteps);
+
+// The step captured as a graph, for the current dt mode; false: not
+// available (the caller launches the kernels directly).
+bool sph_graph(phl_sphere *S, double dt) {
+  const bool fixed = dt > 0.0;
+  if (S->gexec && S->g_fixed == fixed && (!fixed || dt == S->g_dt)) return true;
+  if (S->gexec) {
+    cudaGraphExecDestroy(S->gexec);
+    S->gexec = nullptr;
+  }
+  if (cudaStreamBeginCapture(S->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  sph_steps(S, dt, 1);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e1 = cudaGetLastError(), e2 = cudaStreamEndCapture(S->s, &g);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  const cudaError_t e3 = cudaGraphInstantiate(&S->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) {
+    cudaGetLastError();
+    S->gexec = nullptr;
+    return false;
+  }
+  S->g_fixed = fixed;
+  S->g_dt = dt;
+  return true;
+}
+
+// nsteps SSP-RK3 steps by direct launches
+void sph_steps(phl_sphere *S, double dt, int nsteps) {
   static const double A3[3] = {0.0, 0.75, 1.0 / 3.0}, B3[3] = {1.0, 0.25, 2.0 / 3.0};
   const SphDev &D = S->D;
   for (int n = 0; n < nsteps; ++n) {
@@ -1832,8 +1888,27 @@ phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
         });
       }
     }
-    ++S->steps;
   }
+}
+}  // namespace
+
+extern "C" {
+
+phl_status phl_sphere_step(phl_sphere *S, double dt, int nsteps) {
+  if (!S || nsteps < 0 || !(dt == dt)) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_step: bad arguments");
+  int done = 0;
+  if (nsteps > 0 && S->cold) {   // a cold start's first step launches the network's guesses once
+    sph_steps(S, dt, 1);
+    done = 1;
+  }
+  if (S->use_graph && !S->prof.on && done < nsteps && sph_graph(S, dt)) {
+    for (; done < nsteps; ++done) {
+      const cudaError_t e = cudaGraphLaunch(S->gexec, S->s);
+      if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_step: %s", cudaGetErrorString(e));
+    }
+  }
+  sph_steps(S, dt, nsteps - done);
+  S->steps += nsteps;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_step: %s", cudaGetErrorString(e));
   return PHL_OK;

@@ -433,3 +433,29 @@ def test_stellar_sphere_cold_start_network_guess(P, st_tables):
         err = errors(out, ref)
         assert all(v <= 1e-12 for v in err.values()), (mlp is not None, err)
     assert np.abs(T0 - Tref).max() > 0   # the temperatures did move
+
+
+@pytest.mark.parametrize("eos", ["ideal", "stellar"])
+def test_sphere_graph_steps_equal_direct_launches(P, st_tables, eos):
+    """Steps replayed as a captured CUDA graph give the direct launches'
+    results bit for bit, through a change of dt mode (device CFL step, then a
+    fixed dt) and, for the stellar shell, after a cold start."""
+    import torch
+    pr = W.shell_problem(5, 4, eos=eos, amp=1e-2, beta=1e2, vel_amp=0.05, heat_frac=0.3, mach_heat=0.05)
+    outs = []
+    for graph in (False, True):
+        stream = torch.cuda.Stream()
+        s = P.Sphere.from_problem(pr, precision="mixed", stream=stream.cuda_stream,
+                                  eos_table=st_tables[0] if eos == "stellar" else None)
+        s.set_graph(graph)
+        s.load(pr)
+        if eos == "stellar":   # reload without temperatures: a cold start
+            st = s.get_state()
+            s.set_state(st["cons"], st["pa"], st["pb"], st["pr"])
+        s.step(3)
+        s.step(2, dt=1e-3)
+        s.step(2, dt=1e-3)
+        outs.append(s.get_state())
+        s.close()
+    for k in ("cons", "pa", "pb", "pr"):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
