@@ -267,7 +267,8 @@ __device__ __forceinline__ bool table_eval(const Table &t, R x, R y, TV<R> &o) {
   return table_eval_xb<R>(t, xbasis<R>(t, x), y, o);
 }
 
-template <typename R> struct EosOut { R P, e, cv, Pr, PT, ge, gc; };
+// er: de/drho at fixed T (the next inversion's first guess, eos_invert_pred)
+template <typename R> struct EosOut { R P, e, cv, Pr, PT, ge, gc, er; };
 
 // Full EOS at (rho, T) for a mixture with mean mass number abar and Y_e
 // (irho = 1/rho and iab = 1/abar: fixed during an inversion, formed once).
@@ -295,6 +296,8 @@ __device__ __forceinline__ bool eos_rt_xy(const Table &t, const XB<R> &X, R rho,
   }
   o.P = Pe + rho * Rg * T * iab + aT4 / R(3);
   o.e = ee + R(1.5) * Rg * T * iab + aT4 * irho;
+  // d/drho = (1/rho) d/dx at fixed T: ((f_x - f_xy) - (f - f_y)) / rho^2 and -a T^4 / rho^2
+  o.er = ((q.fx - q.fxy) - (q.f - q.fy) - aT4) * irho * irho;
   o.cv = cve + R(1.5) * Rg * iab + R(4) * aT3 * irho;
   o.PT = PeT + rho * Rg * iab + R(4) / R(3) * aT3;
   o.Pr = Per + Rg * T * iab;
@@ -472,6 +475,50 @@ __device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, doub
   if (isfinite(Tf) && Tf > 0.0f) T = (double)Tf;
   const int it64 = newton_loop<double>(t, X, c, rho, irho, eint, iab, T, tol, maxit, o, false, 0.0, 0.0, 0.0);
   return it64 < 0 ? -1 : it64 + (it32 > 0 ? it32 : 12);
+}
+
+// The last inversion of a cell, for the next one's first guess: its rho and
+// e_int, c_v and de/drho|_T there, and ln T.
+struct Pred {
+  double rho, e, cv, er, lnT;
+};
+
+// Mixed-precision inversion from the cell's previous inversion pr (taken at
+// (rho_p, e_p) with the result T): the first-order guess
+//   T1 = T + (e - e_p - (de/drho)_T (rho - rho_p)) / c_v,
+// within ~(relative change since then)^2 of the root, the full EOS there and,
+// where |e - e(T1)| / e < 2e-6, its first-order carry to the root as in
+// eos_invert_mixed (P + P_T dT, gamma_e from that P and e); otherwise Newton
+// from T1.  One full evaluation in place of e and c_v at T, a Newton step and
+// the full evaluation.  Writes the record of this inversion to pr.
+__device__ __forceinline__ int eos_invert_pred(const Table &t, double rho, double eint, double abar, double ye,
+                                               double &T, double tol, int maxit, EosOut<double> &o, Pred &pr) {
+  const double T1 = T + (eint - pr.e - pr.er * (rho - pr.rho)) / pr.cv;
+  if (pr.cv > 0.0 && T > t.Tlo && T < t.Thi && T1 > t.Tlo && T1 < t.Thi) {
+    const XB<double> X = xbasis<double>(t, log(rho * ye * NAV));
+    const double irho = 1.0 / rho, iab = 1.0 / abar;
+    const double lnT1 = next_lnT<double>(T, pr.lnT, T1);
+    YC<double, 1> c;
+    c.j = -1;
+    if (!eos_rt_xy<double>(t, X, rho, irho, T1, lnT1, iab, o)) return -1;
+    const double de = eint - o.e;
+    if (fabs(de) < 2e-6 * fabs(eint)) {
+      const double dT = de / o.cv;
+      pr = Pred{rho, eint, o.cv, o.er, next_lnT<double>(T1, lnT1, T1 + dT)};
+      o.P = fma(o.PT, dT, o.P);
+      o.e = eint;
+      o.ge = o.P / (rho * eint) + 1.0;
+      T = T1 + dT;
+      return 1;
+    }
+    T = T1;   // a larger change: Newton from T1, where e and c_v are known
+    const int it = newton_loop<double>(t, X, c, rho, irho, eint, iab, T, tol, maxit, o, true, o.e, o.cv, lnT1);
+    if (it > 0) pr = Pred{rho, eint, o.cv, o.er, log(T)};
+    return it < 0 ? -1 : it + 1;
+  }
+  const int it = eos_invert_mixed(t, rho, eint, abar, ye, T, tol, maxit, o);
+  if (it > 0) pr = Pred{rho, eint, o.cv, o.er, log(T)};
+  return it;
 }
 
 }  // namespace eos

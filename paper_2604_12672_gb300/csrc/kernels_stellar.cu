@@ -98,12 +98,14 @@ __global__ void k_mlp_guess(DevGeo G, Box box, const double *__restrict__ U, con
 // network the previous temperature is the fallback.  Writes W and T_out.
 // One interior cell of k_eos_cells: inversion, deviations, and (rate) the
 // CFL sum of the cell, returned (0 otherwise).
+// pm (mixed form, G.pred): 1 writes the record of each cell's inversion,
+// 2 also starts from the previous one's (eos_invert_pred), 0 neither.
 template <typename R>
 __device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, const double *__restrict__ U,
                                                 const double *__restrict__ Bf, const float *__restrict__ dU,
                                                 const float *__restrict__ dB, const double *__restrict__ Tin,
                                                 double *__restrict__ Tout, R *__restrict__ W, int *dflag,
-                                                bool rate) {
+                                                bool rate, int pm) {
   const long p = sidx(G, c[0], c[1], c[2]);
   const CellState cs = cell_state(G, p, U, Bf, dU, dB);
   const double rho = cs.rho, eint = cs.eint;
@@ -115,8 +117,18 @@ __device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, c
   mixture<double>(G, X, abar, ye);
   double T = G.use_mlp ? Tout[p] : Tin[p];   // Tout holds the network's guesses (k_mlp_guess)
   eos::EosOut<double> o;
-  int it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o)
-                          : eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
+  int it;
+  if (sizeof(R) == 4 && pm) {
+    const long pl = G.plane;
+    eos::Pred pr{0.0, 0.0, 0.0, 0.0, 0.0};
+    if (pm == 2) pr = eos::Pred{G.pred[p], G.pred[pl + p], G.pred[2 * pl + p], G.pred[3 * pl + p], G.pred[4 * pl + p]};
+    it = eos::eos_invert_pred(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o, pr);
+    G.pred[p] = pr.rho; G.pred[pl + p] = pr.e; G.pred[2 * pl + p] = pr.cv; G.pred[3 * pl + p] = pr.er;
+    G.pred[4 * pl + p] = pr.lnT;
+  } else {
+    it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o)
+                        : eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);
+  }
   if (it < 0 && G.use_mlp) {   // the plain Newton from the previous temperature is the fallback
     T = Tin[p];
     it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o)
@@ -170,12 +182,12 @@ __global__ void __launch_bounds__(256, 2) k_eos_cells(DevGeo G, Box box, const d
                                                        const double *__restrict__ Bf, const float *__restrict__ dU,
                                                        const float *__restrict__ dB, const double *__restrict__ Tin,
                                                        double *__restrict__ Tout, R *__restrict__ W, int *dflag,
-                                                       unsigned long long *cfl_dmax) {
+                                                       unsigned long long *cfl_dmax, int pm) {
   int c[3];
   const bool in = cell3(box, c);
   if (cfl_dmax) {   // the CFL rate of the step's own state (Eq. cfl), from this inversion
     double m = 0.0;
-    if (in) m = eos_cell_step<R>(G, c, U, Bf, dU, dB, Tin, Tout, W, dflag, true);
+    if (in) m = eos_cell_step<R>(G, c, U, Bf, dU, dB, Tin, Tout, W, dflag, true, pm);
     for (int o2 = 16; o2 > 0; o2 >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o2));
     __shared__ double red[8];
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -188,7 +200,7 @@ __global__ void __launch_bounds__(256, 2) k_eos_cells(DevGeo G, Box box, const d
     return;
   }
   if (!in) return;
-  eos_cell_step<R>(G, c, U, Bf, dU, dB, Tin, Tout, W, dflag, false);
+  eos_cell_step<R>(G, c, U, Bf, dU, dB, Tin, Tout, W, dflag, false, pm);
 }
 
 // Cells of the work layout outside the interior take the deviations of the
@@ -362,14 +374,15 @@ __global__ void k_prim_to_cons(DevGeo G, Box box, const double *__restrict__ pri
 template <typename R>
 void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
                       const double *Tin, double *Tout, R *W, int *dflag, cudaStream_t s, int *nl, Prof *prof,
-                      unsigned long long *cfl_dmax, double *dt) {
+                      unsigned long long *cfl_dmax, double *dt, int pm) {
   Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
   if (G.use_mlp) {
     PHL_LAUNCH(KC_PRIM, prof, s, k_mlp_guess<<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout));
     if (nl) *nl += 1;
   }
   PHL_LAUNCH(KC_PRIM, prof, s,
-             k_eos_cells<R><<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout, W, dflag, cfl_dmax));
+             k_eos_cells<R><<<grid3(bi), block3(bi), 0, s>>>(G, bi, U, Bf, dU, dB, Tin, Tout, W, dflag, cfl_dmax,
+                                                             G.pred ? pm : 0));
   if (cfl_dmax) {   // the step's CFL step from the rates this inversion folded in
     PHL_LAUNCH(KC_DT, prof, s, k_dt_finalize_st<<<1, 1, 0, s>>>(G.cfl, cfl_dmax, dt));
     if (nl) *nl += 1;
@@ -384,10 +397,10 @@ void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const 
 }
 template void launch_eos_cells<double>(const DevGeo &, const double *, const double *, const float *, const float *,
                                        const double *, double *, double *, int *, cudaStream_t, int *, Prof *,
-                                       unsigned long long *, double *);
+                                       unsigned long long *, double *, int);
 template void launch_eos_cells<float>(const DevGeo &, const double *, const double *, const float *, const float *,
                                       const double *, double *, float *, int *, cudaStream_t, int *, Prof *,
-                                      unsigned long long *, double *);
+                                      unsigned long long *, double *, int);
 
 void launch_dt_stellar(const DevGeo &G, bool fp32, const double *U, const double *Bf, const double *T,
                        unsigned long long *dmax, double *dt, int *dflag, cudaStream_t s, int *nl, Prof *prof) {

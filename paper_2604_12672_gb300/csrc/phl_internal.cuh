@@ -80,6 +80,7 @@ struct DevGeo {
   int use_mlp;                 // first Newton guess from the network
   mlp::Dev mlp;
   unsigned long long *niter;   // Newton iterations summed over cells (device)
+  double *pred;                // mixed stellar form: 5 planes, each cell's last inversion (eos::Pred)
 };
 
 __host__ __device__ __forceinline__ long sidx(const DevGeo &G, int i, int j, int k) {
@@ -376,7 +377,7 @@ cudaError_t launch_ens_fused(const EnsFused &E, int stage, int nstages, float b,
 template <typename R>
 void launch_eos_cells(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
                       const double *Tin, double *Tout, R *W, int *dflag, cudaStream_t s, int *nl, Prof *prof,
-                      unsigned long long *cfl_dmax = nullptr, double *dt = nullptr);
+                      unsigned long long *cfl_dmax = nullptr, double *dt = nullptr, int pm = 0);
 void launch_dt_stellar(const DevGeo &G, bool fp32, const double *U, const double *Bf, const double *T,
                        unsigned long long *dmax, double *dt, int *dflag, cudaStream_t s, int *nl, Prof *prof);
 cudaError_t stellar_background(const DevGeo &G, int L, double *bg, const double *bgX_host);

@@ -386,6 +386,7 @@ struct SphDev {
   const float *ge_cf, *gc_cf, *ge_ff, *gc_ff;
   const double *T_c;           // the background's temperature per shell (cold-start guess)
   double *T;                   // cell temperatures (internal order); <= 0: none yet
+  double *pred;                // mixed form: 5 per cell, each cell's last inversion (eos::Pred, SoA)
   int wq;                      // mixed W: float4 records per cell (2; 3 with the stellar EOS)
   mlp::Dev mlp;                // temperature-guess network (cold starts), when use_mlp
   int use_mlp;
@@ -696,10 +697,13 @@ __global__ void __launch_bounds__(SPT) k_sph_mlp_guess(SphDev D, const double *_
 // low-Mach deviations need P to ~1e-12), the field from the FP32 fluxes phif,
 // FP64 Newton (FP32 iterations first from a far guess, eos_invert_mixed),
 // three float4 records per cell, and with dmax the CFL rate folded in.
+// pm (mixed form): 1 records each cell's inversion in D.pred, 2 also starts
+// from the previous record (eos_invert_pred; the second and third stages).
 template <typename R>
 __global__ void __launch_bounds__(SPT) k_sph_prims_st(SphDev D, SphWork<R> Wk, const double *__restrict__ U,
                                                       const float *__restrict__ dU, const double *__restrict__ phi,
-                                                      const float *__restrict__ phif, unsigned long long *dmax) {
+                                                      const float *__restrict__ phif, unsigned long long *dmax,
+                                                      int pm) {
   const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
   float rate = 0.f;
   if (c < D.ncell) {
@@ -734,9 +738,18 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_st(SphDev D, SphWork<R> Wk, c
     double T = D.T[c];
     if (!(T > 0.0)) T = D.T_c ? D.T_c[k] : 1e9;
     eos::EosOut<double> o;
-    const int it = sizeof(R) == 8
-                       ? eos::eos_invert<double>(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o)
-                       : eos::eos_invert_mixed(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o);
+    int it;
+    if (sizeof(R) == 4 && pm) {
+      eos::Pred pr{0.0, 0.0, 0.0, 0.0, 0.0};
+      if (pm == 2) pr = eos::Pred{D.pred[c], D.pred[n + c], D.pred[2 * n + c], D.pred[3 * n + c], D.pred[4 * n + c]};
+      it = eos::eos_invert_pred(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o, pr);
+      D.pred[c] = pr.rho; D.pred[n + c] = pr.e; D.pred[2 * n + c] = pr.cv; D.pred[3 * n + c] = pr.er;
+      D.pred[4 * n + c] = pr.lnT;
+    } else {
+      it = sizeof(R) == 8
+               ? eos::eos_invert<double>(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o)
+               : eos::eos_invert_mixed(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o);
+    }
     if (it < 0) atomicOr(D.dflag, FLAG_NEWTON);
     D.T[c] = T;
     const double P = o.P / D.p_u;
@@ -1402,14 +1415,19 @@ void timed(phl_sphere *S, int cls, F &&launch) {
 // (phi FP64, phif the mixed form's FP32 copy); dmax (mixed): fold the CFL
 // rate.  A stellar shell whose cells lack temperatures first takes the
 // network's guesses (U^n and the FP64 fluxes of the state).
-void sph_prims(phl_sphere *S, const double *U, const float *dU, const double *phi, unsigned long long *dmax) {
+// pm: the stellar mixed form's inversion record (k_sph_prims_st): 1 at a
+// step's first stage, 2 after.
+void sph_prims(phl_sphere *S, const double *U, const float *dU, const double *phi, unsigned long long *dmax,
+               int pm = 1) {
   const SphDev &D = S->D;
   timed(S, KC_SPH_PRIM, [&] {
     if (S->cold && D.use_mlp) k_sph_mlp_guess<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->U, S->phi);
     S->cold = false;
     if (D.stellar) {
-      if (S->mixed) k_sph_prims_st<float><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, U, dU, nullptr, S->phif, dmax);
-      else k_sph_prims_st<double><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, U, nullptr, phi, nullptr, nullptr);
+      if (S->mixed)
+        k_sph_prims_st<float><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, U, dU, nullptr, S->phif, dmax,
+                                                              D.pred ? pm : 0);
+      else k_sph_prims_st<double><<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W64, U, nullptr, phi, nullptr, nullptr, 0);
     } else if (S->mixed) {
       k_sph_prims_mx<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->W32, U, dU, S->phif, dmax);
     } else {
@@ -1536,6 +1554,7 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
       D.mlp_x0 = (float)(d->nspec > 1 ? d->X[0] / (d->X[0] + d->X[1]) : 1.0);
     }
     e = alloc_n(S, &D.T, D.ncell);
+    if (e == cudaSuccess && S->mixed) e = alloc_n(S, &D.pred, 5 * D.ncell);
     if (e == cudaSuccess && d->rho_c) {   // the background's gamma_e, gamma_c and T from the EOS
       double *bg = nullptr;
       int *fail = nullptr;
@@ -1857,7 +1876,7 @@ void sph_steps(phl_sphere *S, double dt, int nsteps) {
       if (S->mixed) {
         // cells: stage input U^n + dU; increments out dU = b (dU - dt R)
         const float *dUin = st == 0 ? nullptr : S->dU;
-        if (prims) sph_prims(S, S->U, dUin, pin, nullptr);
+        if (prims) sph_prims(S, S->U, dUin, pin, nullptr, st == 0 ? 1 : 2);
         timed(S, KC_SPH_FLUX, [&] {
           if (D.stellar) k_sph_flux<float, true, true><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin, S->phif);
           else k_sph_flux<float, true><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin, S->phif);
