@@ -19,6 +19,7 @@ struct phl_eos_table {
   Table t;
   double *dv = nullptr;
   float *dvf = nullptr;
+  double *dd = nullptr;   // per table cell: the corner values in difference form (Table::d)
 };
 
 namespace {
@@ -55,6 +56,24 @@ __global__ void k_table_nodes(int nx, int ny, double x0, double dx, double y0, d
   const int i = idx % nx, j = idx / nx;
   if (!eosn::node_values(exp(x0 + i * dx), exp(y0 + j * dy), lam3, gl, gl + GLN, v + (long)NQ * idx))
     atomicOr(fail, 1);
+}
+
+// Per table cell (i, j) and node slot s: q00 and the differences q10 - q00,
+// q01 - q00, (q11 - q01) - (q10 - q00) of its corners (x first, then y),
+// the same FP64 operations the contraction would do at every evaluation.
+__global__ void k_table_diffs(int nx, int ny, const double *__restrict__ v, double *__restrict__ d) {
+  const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (q >= (long)(nx - 1) * (ny - 1) * NQ) return;
+  const int s = (int)(q % NQ);
+  const long cell = q / NQ;
+  const int i = (int)(cell % (nx - 1)), j = (int)(cell / (nx - 1));
+  const long k0 = ((long)j * nx + i) * NQ + s, k1 = k0 + (long)nx * NQ;
+  const double q00 = v[k0], q10 = v[k0 + NQ], q01 = v[k1], q11 = v[k1 + NQ];
+  double *o = d + cell * 4 * NQ + 4 * s;
+  o[0] = q00;
+  o[1] = q10 - q00;
+  o[2] = q01 - q00;
+  o[3] = (q11 - q01) - (q10 - q00);
 }
 
 template <typename R>
@@ -135,8 +154,19 @@ phl_status phl_eos_table_create(double lrhoye_lo, double lrhoye_hi, int nrho, do
   std::vector<float> hf(nv);
   for (long q = 0; q < nv; ++q) hf[q] = (float)h[q];
   cudaMemcpy(t->dvf, hf.data(), nv * sizeof(float), cudaMemcpyHostToDevice);
+  const long nd = 4L * NQ * (nrho - 1) * (nT - 1);
+  e = cudaMalloc(&t->dd, nd * sizeof(double));
+  if (e == cudaSuccess) {
+    k_table_diffs<<<(unsigned)((nd / 4 + 255) / 256), 256>>>(nrho, nT, t->dv, t->dd);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    cudaFree(t->dv); cudaFree(t->dvf); cudaFree(t->dd); delete t;
+    return (phl_status)set_error(PHL_ECUDA, "eos table: %s", cudaGetErrorString(e));
+  }
   t->t.v = t->dv;
   t->t.vf = t->dvf;
+  t->t.d = t->dd;
   *out = t;
   return PHL_OK;
 }
@@ -145,6 +175,7 @@ void phl_eos_table_destroy(phl_eos_table *t) {
   if (!t) return;
   cudaFree(t->dv);
   cudaFree(t->dvf);
+  cudaFree(t->dd);
   delete t;
 }
 

@@ -49,6 +49,8 @@ struct Table {
   double x0, dx, y0, dy;      // x = ln n_e, y = ln T
   const double *v;            // [ny][nx][NQ] (device)
   const float *vf;            // FP32 copy
+  const double *d;            // [ny-1][nx-1][NQ][4]: each table cell's corner values in difference
+                              // form (D00, D10, D01, D11 below), formed once; null: formed per use
   float x0f, dxf, y0f, dyf;
   double idx, idy;            // 1/dx, 1/dy: the evaluation multiplies (FP64 division
   float idxf, idyf;           // is a dozen FP64-pipe instructions on this GPU)
@@ -151,8 +153,10 @@ template <typename R, int M> struct YC {
 template <typename R, int M, int M0 = 0>
 __device__ __forceinline__ void contract(const Table &t, const XB<R> &X, int j, YC<R, M> &c) {
   c.j = j;
+  const bool pre = sizeof(R) == 8 && t.d;   // the differences stored with the table
   const long k0 = ((long)j * t.nx + X.i) * NQ, k1 = k0 + (long)t.nx * NQ;
-  R q[2][2][NQ];   // [b][a][slot]
+  const double *dc = pre ? t.d + ((long)j * (t.nx - 1) + X.i) * 4 * NQ : nullptr;
+  R q[2][2][NQ];   // [b][a][slot]; with pre: [0][0] D00, [0][1] D10, [1][0] D01, [1][1] D11
 #pragma unroll
   for (int b = 0; b < 2; ++b)
 #pragma unroll
@@ -160,7 +164,7 @@ __device__ __forceinline__ void contract(const Table &t, const XB<R> &X, int j, 
 #pragma unroll
       for (int s = 0; s < NQ; ++s) {
         const long k = (b ? k1 : k0) + a * NQ + s;
-        q[b][a][s] = sizeof(R) == 8 ? (R)t.v[k] : (R)t.vf[k];
+        q[b][a][s] = pre ? (R)dc[4 * s + 2 * b + a] : (sizeof(R) == 8 ? (R)t.v[k] : (R)t.vf[k]);
       }
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -168,8 +172,10 @@ __device__ __forceinline__ void contract(const Table &t, const XB<R> &X, int j, 
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
       const int sl = qslot(p, r);
-      const R D00 = q[0][0][sl], D10 = q[0][1][sl] - q[0][0][sl], D01 = q[1][0][sl] - q[0][0][sl];
-      const R D11 = (q[1][1][sl] - q[0][1][sl]) - (q[1][0][sl] - q[0][0][sl]);
+      const R D00 = q[0][0][sl];
+      const R D10 = pre ? q[0][1][sl] : q[0][1][sl] - q[0][0][sl];
+      const R D01 = pre ? q[1][0][sl] : q[1][0][sl] - q[0][0][sl];
+      const R D11 = pre ? q[1][1][sl] : (q[1][1][sl] - q[0][1][sl]) - (q[1][0][sl] - q[0][0][sl]);
       if (M0 == 0) {
         g0 += D00 * X.h[0][p] + D10 * X.h[1][p];
         d0 += D01 * X.h[0][p] + D11 * X.h[1][p];
@@ -477,48 +483,126 @@ __device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, doub
   return it64 < 0 ? -1 : it64 + (it32 > 0 ? it32 : 12);
 }
 
-// The last inversion of a cell, for the next one's first guess: its rho and
-// e_int, c_v and de/drho|_T there, and ln T.
+// The last inversion of a cell, for the next one's first guess: its rho,
+// e_int, 1/c_v and de/drho|_T there, ln T and 1/T of the result, and
+// x = ln(n_e N_A) with n_e = rho Y_e (ne).
 struct Pred {
-  double rho, e, cv, er, lnT;
+  double rho, e, icv, er, lnT, iT, x, ne;
 };
 
-// Mixed-precision inversion from the cell's previous inversion pr (taken at
-// (rho_p, e_p) with the result T): the first-order guess
-//   T1 = T + (e - e_p - (de/drho)_T (rho - rho_p)) / c_v,
-// within ~(relative change since then)^2 of the root, the full EOS there and,
-// where |e - e(T1)| / e < 2e-6, its first-order carry to the root as in
-// eos_invert_mixed (P + P_T dT, gamma_e from that P and e); otherwise Newton
-// from T1.  One full evaluation in place of e and c_v at T, a Newton step and
-// the full evaluation.  Writes the record of this inversion to pr.
-__device__ __forceinline__ int eos_invert_pred(const Table &t, double rho, double eint, double abar, double ye,
-                                               double &T, double tol, int maxit, EosOut<double> &o, Pred &pr) {
-  const double T1 = T + (eint - pr.e - pr.er * (rho - pr.rho)) / pr.cv;
-  if (pr.cv > 0.0 && T > t.Tlo && T < t.Thi && T1 > t.Tlo && T1 < t.Thi) {
-    const XB<double> X = xbasis<double>(t, log(rho * ye * NAV));
-    const double irho = 1.0 / rho, iab = 1.0 / abar;
-    const double lnT1 = next_lnT<double>(T, pr.lnT, T1);
-    YC<double, 1> c;
-    c.j = -1;
-    if (!eos_rt_xy<double>(t, X, rho, irho, T1, lnT1, iab, o)) return -1;
-    const double de = eint - o.e;
-    if (fabs(de) < 2e-6 * fabs(eint)) {
-      const double dT = de / o.cv;
-      pr = Pred{rho, eint, o.cv, o.er, next_lnT<double>(T1, lnT1, T1 + dT)};
-      o.P = fma(o.PT, dT, o.P);
-      o.e = eint;
-      o.ge = o.P / (rho * eint) + 1.0;
-      T = T1 + dT;
-      return 1;
+// ln(a) from ln(a_p) for a = a_p (1 + d): the series of ln(1 + d) to d^4
+// below |d| = 2^-10 (as next_lnT), else fall back.
+__device__ __forceinline__ double ln_step(double lnp, double d, double fallback_arg) {
+  if (!(fabs(d) < 1.0 / 1024.0)) return log(fallback_arg);
+  return lnp + d * (1.0 - d * (0.5 - d * (1.0 / 3.0 - d * 0.25)));
+}
+
+// The full EOS at (rho, T) for the recorded mixed inversion: P, e, P_T,
+// 1/c_v, de/drho|_T, c_s^2 and 1/T, the reciprocals formed once (gamma_e and
+// gamma_c follow from the carried P in rec_carry).
+struct EosC {
+  double P, e, PT, icv, er, cs2, iT;
+};
+__device__ __forceinline__ bool eos_rt_c(const Table &t, const XB<double> &X, double rho, double irho, double T,
+                                         double lnT, double iab, EosC &o, const YC<double, 1> *c1) {
+  TV<double> q;
+  if (!table_eval_xb<double>(t, X, lnT, q, c1)) return false;
+  const double iT = 1.0 / T;
+  const double Rg = RGAS;
+  const double aT3 = ARAD * T * T * T, aT4 = aT3 * T;
+  o.P = (q.fx - q.f) + rho * Rg * T * iab + aT4 * (1.0 / 3.0);
+  o.e = (q.f - q.fy) * irho + 1.5 * Rg * T * iab + aT4 * irho;
+  o.icv = 1.0 / ((q.fy - q.fyy) * irho * iT + 1.5 * Rg * iab + 4.0 * aT3 * irho);
+  o.PT = (q.fxy - q.fy) * iT + rho * Rg * iab + (4.0 / 3.0) * aT3;
+  const double Pr = (q.fxx - q.fx) * irho + Rg * T * iab;
+  o.cs2 = Pr + (T * o.PT * irho) * (o.PT * irho * o.icv);
+  o.er = ((q.fx - q.fxy) - (q.f - q.fy) - aT4) * irho * irho;
+  o.iT = iT;
+  return true;
+}
+
+// The carry of a full evaluation c at T1 (within ~2e-6 of the root in e) to
+// the root T1 + dT, dT = (e - e(T1)) / c_v, to first order: P + P_T dT;
+// gamma_e = P / (rho e) + 1 from that P and e; gamma_c = rho c_s^2 / P
+// (c_s^2 at T1: relative error ~dT/T, wave speeds only); one reciprocal for
+// both.  Writes the record of the inversion.
+__device__ __forceinline__ void rec_carry(double rho, double eint, double ne, double x, double T1, double lnT1,
+                                          const EosC &c, EosOut<double> &o, double &T, Pred &pr) {
+  const double dT = (eint - c.e) * c.icv;
+  const double P = fma(c.PT, dT, c.P);
+  const double re = rho * eint;
+  const double inv = 1.0 / (P * re);   // 1/(rho e) = P inv, 1/P = rho e inv
+  o.P = P;
+  o.e = eint;
+  o.ge = P * (P * inv) + 1.0;
+  o.gc = rho * c.cs2 * (re * inv);
+  o.cv = 0.0;   // not formed on this path
+  o.er = c.er;
+  T = T1 + dT;
+  const double dd = dT * c.iT;
+  pr = Pred{rho, eint, c.icv, c.er, lnT1 + dd * (1.0 - dd * (0.5 - dd * (1.0 / 3.0))), c.iT * (1.0 - dd), x, ne};
+}
+
+// Mixed-precision inversion with a per-cell record (rec: the record holds
+// the cell's previous inversion).  With a record, the first-order guess
+//   T1 = T + (e - e_p - (de/drho)_T (rho - rho_p)) / c_v
+// lies within ~(relative change since then)^2 of the root: one full
+// evaluation there and, where |e - e(T1)| / e < 2e-6, its carry to the root
+// (rec_carry); ln(n_e N_A) and ln T1 follow from the record's by the series
+// of ln(1 + d).  Without a record (or where the change was larger) the
+// mixed inversion's own steps: e, c_v at T; from within 2e-6 one Newton
+// step, the full evaluation and the carry; from within 1e-4 the FP64 Newton
+// loop; else FP32 iterations first.  Writes the record; returns the count
+// of evaluations at distinct temperatures (1 for the recorded path) or -1.
+__device__ __forceinline__ int eos_invert_rec(const Table &t, double rho, double eint, double abar, double ye,
+                                              double &T, double tol, int maxit, EosOut<double> &o, Pred &pr,
+                                              bool rec) {
+  const double ne = rho * ye, irho = 1.0 / rho, iab = 1.0 / abar;
+  const double x = rec ? ln_step(pr.x, (ne - pr.ne) / pr.ne, ne * NAV) : log(ne * NAV);
+  const XB<double> X = xbasis<double>(t, x);
+  YC<double, 1> c;
+  c.j = -1;
+  EosC f;
+  if (rec && pr.icv > 0.0 && T > t.Tlo && T < t.Thi) {
+    const double T1 = T + (eint - pr.e - pr.er * (rho - pr.rho)) * pr.icv;
+    if (T1 > t.Tlo && T1 < t.Thi) {
+      const double lnT1 = ln_step(pr.lnT, (T1 - T) * pr.iT, T1);
+      if (!eos_rt_c(t, X, rho, irho, T1, lnT1, iab, f, nullptr)) return -1;
+      if (fabs(eint - f.e) < 2e-6 * fabs(eint)) {
+        rec_carry(rho, eint, ne, x, T1, lnT1, f, o, T, pr);
+        return 1;
+      }
+      T = T1;   // a larger change: the steps below from T1
     }
-    T = T1;   // a larger change: Newton from T1, where e and c_v are known
-    const int it = newton_loop<double>(t, X, c, rho, irho, eint, iab, T, tol, maxit, o, true, o.e, o.cv, lnT1);
-    if (it > 0) pr = Pred{rho, eint, o.cv, o.er, log(T)};
-    return it < 0 ? -1 : it + 1;
   }
-  const int it = eos_invert_mixed(t, rho, eint, abar, ye, T, tol, maxit, o);
-  if (it > 0) pr = Pred{rho, eint, o.cv, o.er, log(T)};
-  return it;
+  int it0 = -2;   // -2: a far guess, FP32 iterations first
+  if (T > t.Tlo && T < t.Thi) {
+    const double lnT = log(T);
+    double e, cv;
+    if (eos_ecv_xy<double>(t, X, c, irho, T, lnT, iab, e, cv) && fabs(eint - e) < 1e-4 * fabs(eint)) {
+      const double de = eint - e;
+      if (fabs(de) < 2e-6 * fabs(eint)) {
+        const double T1 = T + de / cv;
+        if (T1 > t.Tlo && T1 < t.Thi) {
+          const double lnT1 = next_lnT<double>(T, lnT, T1);
+          if (!eos_rt_c(t, X, rho, irho, T1, lnT1, iab, f, &c)) return -1;
+          rec_carry(rho, eint, ne, x, T1, lnT1, f, o, T, pr);
+          return 2;
+        }
+      }
+      it0 = newton_loop<double>(t, X, c, rho, irho, eint, iab, T, tol, maxit, o, true, e, cv, lnT);
+    }
+  }
+  if (it0 == -2) {
+    float Tf = (float)T;
+    const int it32 = newton_fp32(t, (float)rho, (float)eint, (float)abar, (float)ye, Tf, 1e-5f, maxit < 12 ? maxit : 12);
+    if (isfinite(Tf) && Tf > 0.0f) T = (double)Tf;
+    const int it64 = newton_loop<double>(t, X, c, rho, irho, eint, iab, T, tol, maxit, o, false, 0.0, 0.0, 0.0);
+    it0 = it64 < 0 ? -1 : it64 + (it32 > 0 ? it32 : 12);
+  }
+  if (it0 > 0)   // the record of a Newton-loop result (the rare paths)
+    pr = Pred{rho, eint, 1.0 / o.cv, o.er, log(T), 1.0 / T, x, ne};
+  return it0;
 }
 
 }  // namespace eos

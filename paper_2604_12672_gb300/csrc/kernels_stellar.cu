@@ -99,7 +99,7 @@ __global__ void k_mlp_guess(DevGeo G, Box box, const double *__restrict__ U, con
 // One interior cell of k_eos_cells: inversion, deviations, and (rate) the
 // CFL sum of the cell, returned (0 otherwise).
 // pm (mixed form, G.pred): 1 writes the record of each cell's inversion,
-// 2 also starts from the previous one's (eos_invert_pred), 0 neither.
+// 2 also starts from the previous one's (eos_invert_rec), 0 neither.
 template <typename R>
 __device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, const double *__restrict__ U,
                                                 const double *__restrict__ Bf, const float *__restrict__ dU,
@@ -120,11 +120,12 @@ __device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, c
   int it;
   if (sizeof(R) == 4 && pm) {
     const long pl = G.plane;
-    eos::Pred pr{0.0, 0.0, 0.0, 0.0, 0.0};
-    if (pm == 2) pr = eos::Pred{G.pred[p], G.pred[pl + p], G.pred[2 * pl + p], G.pred[3 * pl + p], G.pred[4 * pl + p]};
-    it = eos::eos_invert_pred(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o, pr);
-    G.pred[p] = pr.rho; G.pred[pl + p] = pr.e; G.pred[2 * pl + p] = pr.cv; G.pred[3 * pl + p] = pr.er;
-    G.pred[4 * pl + p] = pr.lnT;
+    eos::Pred pr{};
+    double *rp = G.pred + p;
+    if (pm == 2) pr = eos::Pred{rp[0], rp[pl], rp[2 * pl], rp[3 * pl], rp[4 * pl], rp[5 * pl], rp[6 * pl], rp[7 * pl]};
+    it = eos::eos_invert_rec(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o, pr, pm == 2);
+    rp[0] = pr.rho; rp[pl] = pr.e; rp[2 * pl] = pr.icv; rp[3 * pl] = pr.er;
+    rp[4 * pl] = pr.lnT; rp[5 * pl] = pr.iT; rp[6 * pl] = pr.x; rp[7 * pl] = pr.ne;
   } else {
     it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o)
                         : eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);

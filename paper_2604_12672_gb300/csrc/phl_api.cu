@@ -427,7 +427,7 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     AL(&g->niter, 1);
     G.niter = g->niter;
     if (g->mixed) {   // each cell's last inversion (eos::Pred): the next stage's first guess
-      AL(&G.pred, 5 * G.plane);
+      AL(&G.pred, 8 * G.plane);
     }
   }
   AL(&g->flag, G.wtot);

@@ -80,7 +80,7 @@ struct DevGeo {
   int use_mlp;                 // first Newton guess from the network
   mlp::Dev mlp;
   unsigned long long *niter;   // Newton iterations summed over cells (device)
-  double *pred;                // mixed stellar form: 5 planes, each cell's last inversion (eos::Pred)
+  double *pred;                // mixed stellar form: 8 planes, each cell's last inversion (eos::Pred)
 };
 
 __host__ __device__ __forceinline__ long sidx(const DevGeo &G, int i, int j, int k) {

@@ -386,7 +386,7 @@ struct SphDev {
   const float *ge_cf, *gc_cf, *ge_ff, *gc_ff;
   const double *T_c;           // the background's temperature per shell (cold-start guess)
   double *T;                   // cell temperatures (internal order); <= 0: none yet
-  double *pred;                // mixed form: 5 per cell, each cell's last inversion (eos::Pred, SoA)
+  double *pred;                // mixed form: 8 per cell, each cell's last inversion (eos::Pred, SoA)
   int wq;                      // mixed W: float4 records per cell (2; 3 with the stellar EOS)
   mlp::Dev mlp;                // temperature-guess network (cold starts), when use_mlp
   int use_mlp;
@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(SPT) k_sph_mlp_guess(SphDev D, const double *_
 // FP64 Newton (FP32 iterations first from a far guess, eos_invert_mixed),
 // three float4 records per cell, and with dmax the CFL rate folded in.
 // pm (mixed form): 1 records each cell's inversion in D.pred, 2 also starts
-// from the previous record (eos_invert_pred; the second and third stages).
+// from the previous record (eos_invert_rec; the second and third stages).
 template <typename R>
 __global__ void __launch_bounds__(SPT) k_sph_prims_st(SphDev D, SphWork<R> Wk, const double *__restrict__ U,
                                                       const float *__restrict__ dU, const double *__restrict__ phi,
@@ -740,11 +740,12 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_st(SphDev D, SphWork<R> Wk, c
     eos::EosOut<double> o;
     int it;
     if (sizeof(R) == 4 && pm) {
-      eos::Pred pr{0.0, 0.0, 0.0, 0.0, 0.0};
-      if (pm == 2) pr = eos::Pred{D.pred[c], D.pred[n + c], D.pred[2 * n + c], D.pred[3 * n + c], D.pred[4 * n + c]};
-      it = eos::eos_invert_pred(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o, pr);
-      D.pred[c] = pr.rho; D.pred[n + c] = pr.e; D.pred[2 * n + c] = pr.cv; D.pred[3 * n + c] = pr.er;
-      D.pred[4 * n + c] = pr.lnT;
+      eos::Pred pr{};
+      double *rp = D.pred + c;
+      if (pm == 2) pr = eos::Pred{rp[0], rp[n], rp[2 * n], rp[3 * n], rp[4 * n], rp[5 * n], rp[6 * n], rp[7 * n]};
+      it = eos::eos_invert_rec(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o, pr, pm == 2);
+      rp[0] = pr.rho; rp[n] = pr.e; rp[2 * n] = pr.icv; rp[3 * n] = pr.er;
+      rp[4 * n] = pr.lnT; rp[5 * n] = pr.iT; rp[6 * n] = pr.x; rp[7 * n] = pr.ne;
     } else {
       it = sizeof(R) == 8
                ? eos::eos_invert<double>(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o)
@@ -1554,7 +1555,7 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
       D.mlp_x0 = (float)(d->nspec > 1 ? d->X[0] / (d->X[0] + d->X[1]) : 1.0);
     }
     e = alloc_n(S, &D.T, D.ncell);
-    if (e == cudaSuccess && S->mixed) e = alloc_n(S, &D.pred, 5 * D.ncell);
+    if (e == cudaSuccess && S->mixed) e = alloc_n(S, &D.pred, 8 * D.ncell);
     if (e == cudaSuccess && d->rho_c) {   // the background's gamma_e, gamma_c and T from the EOS
       double *bg = nullptr;
       int *fail = nullptr;
