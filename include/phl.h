@@ -139,6 +139,16 @@ phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx,
                          const double *by, const double *bz, const double *T,
                          int where);
 
+/* The mixed stellar form's inversion record (Sect. 2.2 Newton inversion):
+ * per cell rho, e_int, 1/c_v, de/drho at fixed T, ln T, 1/T, ln(n_e N_A) and
+ * n_e = rho Y_e of the cell's last inversion, rec[8][nz][ny][nx]; each
+ * inversion starts from the first-order guess they give.  set_state and
+ * set_state_prim clear it (the next inversions start plainly); restoring it
+ * with the state and T makes a resumed run repeat the uninterrupted one bit
+ * for bit.  PHL_EINVAL on grids without one (FP64 or ideal gas). */
+phl_status phl_get_eos_record(phl_grid *g, double *rec, int where);
+phl_status phl_set_eos_record(phl_grid *g, const double *rec, int where);
+
 /* Load the state from primitive fields: prim[(5 + nspec)][nz][ny][nx] =
  * rho, u_x, u_y, u_z, P, X_l (mass fractions), plus the face fields.  The
  * conserved energy is rho e(rho, T) + rho u^2/2 + B^2/2 with T from
@@ -673,6 +683,11 @@ phl_status phl_sphere_set_prims(phl_sphere *s, const double *rho, const double *
  * synchronous for host memory.  PHL_EINVAL on an ideal-gas shell. */
 phl_status phl_sphere_set_temperature(phl_sphere *s, const double *T, int where);
 phl_status phl_sphere_get_temperature(phl_sphere *s, double *T, int where);
+/* The mixed stellar shell's inversion record, rec[8][6][Nr][N][N] (the
+ * eight values of phl_get_eos_record per cell); set_state, set_prims and
+ * set_temperature clear it.  PHL_EINVAL without one. */
+phl_status phl_sphere_get_eos_record(phl_sphere *s, double *rec, int where);
+phl_status phl_sphere_set_eos_record(phl_sphere *s, const double *rec, int where);
 /* The CFL step of the current state (Eq. cfl with the fast speed along each
  * cell's three mesh directions over the distance between its opposite face
  * centres), to host memory; synchronous. */

@@ -153,6 +153,10 @@ _SIGS = {
     "phl_sphere_check": (C.c_int, [C.c_void_p]),
     "phl_sphere_set_prims": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_int]),
     "phl_sphere_set_graph": (C.c_int, [C.c_void_p, C.c_int]),
+    "phl_sphere_get_eos_record": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_sphere_set_eos_record": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_get_eos_record": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "phl_set_eos_record": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "phl_sphere_set_temperature": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "phl_sphere_get_temperature": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "phl_sphere_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -553,6 +557,16 @@ class Grid:
         self.get_state_into(cons, bx, by, bz, T)
         return dict(cons=cons, bx=bx, by=by, bz=bz, T=T)
 
+    def get_eos_record(self):
+        """The mixed stellar form's inversion record [8][nz][ny][nx]."""
+        out = np.zeros((8,) + self.pr.cons.shape[1:])
+        _check(lib().phl_get_eos_record(self.h, out.ctypes.data, HOST))
+        return out
+
+    def set_eos_record(self, rec):
+        rec = np.ascontiguousarray(rec, dtype=np.float64)
+        _check(lib().phl_set_eos_record(self.h, rec.ctypes.data, HOST))
+
     def step(self, nsteps=1, dt=0.0):
         _check(lib().phl_step(self.h, float(dt), int(nsteps)))
 
@@ -786,6 +800,16 @@ class Sphere:
     def set_temperature(self, T):
         p, w = _ptr(T)
         _check(lib().phl_sphere_set_temperature(self.h, p, w))
+
+    def get_eos_record(self):
+        """The mixed stellar shell's inversion record [8][6][Nr][N][N]."""
+        out = np.zeros((8, 6, self.Nr, self.N, self.N))
+        _check(lib().phl_sphere_get_eos_record(self.h, out.ctypes.data, HOST))
+        return out
+
+    def set_eos_record(self, rec):
+        p, w = _ptr(np.ascontiguousarray(rec, dtype=np.float64) if isinstance(rec, np.ndarray) else rec)
+        _check(lib().phl_sphere_set_eos_record(self.h, p, w))
 
     def get_temperature(self, out=None):
         """Cell temperatures [6][Nr][N][N] (K) of a stellar shell."""

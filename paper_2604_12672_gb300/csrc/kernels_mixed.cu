@@ -92,13 +92,11 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
     for (int d = 0; d < 3; ++d) rng(d, G.ge[d], G.ge[d], l[d], h[d]);
     Box bx = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
     if (G.eos == 1) {
-      // from the second stage on each cell starts from its previous stage's
-      // inversion; the first stage's record depends only on U^n and T, so a
-      // run resumed from (U^n, T) repeats it bit for bit (network-first mode:
-      // the network's guess instead)
+      // each cell starts from its previous inversion's record (a cleared
+      // record falls back to the plain start); network-first mode: the
+      // network's guess instead
       launch_eos_cells<float>(G, M.U, M.B, dU, dB, M.Tin, M.Tout, M.W, M.dflag, s, &nl, prof,
-                              first ? M.cfl_dmax : nullptr, const_cast<double *>(M.dt),
-                              G.use_mlp == 1 ? 0 : (first ? 1 : 2));
+                              first ? M.cfl_dmax : nullptr, const_cast<double *>(M.dt), G.use_mlp == 1 ? 0 : 2);
     } else {
       PHL_LAUNCH(KC_PRIM, prof, s, k_prim_mx<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, dU, dB, M.W, M.dflag));
       ++nl;

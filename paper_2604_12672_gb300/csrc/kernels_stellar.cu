@@ -99,7 +99,8 @@ __global__ void k_mlp_guess(DevGeo G, Box box, const double *__restrict__ U, con
 // One interior cell of k_eos_cells: inversion, deviations, and (rate) the
 // CFL sum of the cell, returned (0 otherwise).
 // pm (mixed form, G.pred): 1 writes the record of each cell's inversion,
-// 2 also starts from the previous one's (eos_invert_rec), 0 neither.
+// 2 also starts from the previous one's (eos_invert_rec; a cleared record,
+// 1/c_v = 0, gives the plain start), 0 neither.
 template <typename R>
 __device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, const double *__restrict__ U,
                                                 const double *__restrict__ Bf, const float *__restrict__ dU,

@@ -529,6 +529,8 @@ phl_status phl_set_state(phl_grid *g, const double *cons, const double *bx, cons
       CK(cudaMemsetAsync(g->T, 0, G.plane * sizeof(double), g->stream), "clear T");
     }
   }
+  if (G.pred)   // no inversion record (phl_set_eos_record restores one)
+    CK(cudaMemsetAsync(G.pred, 0, 8 * G.plane * sizeof(double), g->stream), "clear the inversion record");
   CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream), "reset flags");
   if (where == PHL_HOST) CK(cudaStreamSynchronize(g->stream), "sync");
   return PHL_OK;
@@ -546,6 +548,34 @@ phl_status phl_get_state(phl_grid *g, double *cons, double *bx, double *by, doub
   if (g->T && T)
     if ((st = copy_field(g, g->T, nullptr, T, nx, ny, nz, false)) != PHL_OK) return st;
   return check_flags(g);
+}
+
+phl_status phl_get_eos_record(phl_grid *g, double *rec, int where) {
+  if (!g || !rec) return fail(PHL_EINVAL, "phl_get_eos_record: null argument");
+  if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
+  const DevGeo &G = g->G;
+  if (!G.pred) return fail(PHL_EINVAL, "phl_get_eos_record: no record (mixed stellar grids only)");
+  const long nc = (long)G.n[0] * G.n[1] * G.n[2];
+  phl_status st;
+  for (int q = 0; q < 8; ++q)
+    if ((st = copy_field(g, G.pred + q * G.plane, nullptr, rec + q * nc, G.n[0], G.n[1], G.n[2], false)) != PHL_OK)
+      return st;
+  if (where == PHL_HOST) CK(cudaStreamSynchronize(g->stream), "sync");
+  return PHL_OK;
+}
+
+phl_status phl_set_eos_record(phl_grid *g, const double *rec, int where) {
+  if (!g || !rec) return fail(PHL_EINVAL, "phl_set_eos_record: null argument");
+  if (where != PHL_HOST && where != PHL_DEVICE) return fail(PHL_EINVAL, "bad 'where'");
+  const DevGeo &G = g->G;
+  if (!G.pred) return fail(PHL_EINVAL, "phl_set_eos_record: no record (mixed stellar grids only)");
+  const long nc = (long)G.n[0] * G.n[1] * G.n[2];
+  phl_status st;
+  for (int q = 0; q < 8; ++q)
+    if ((st = copy_field(g, G.pred + q * G.plane, rec + q * nc, nullptr, G.n[0], G.n[1], G.n[2], true)) != PHL_OK)
+      return st;
+  if (where == PHL_HOST) CK(cudaStreamSynchronize(g->stream), "sync");
+  return PHL_OK;
 }
 
 phl_status phl_set_state_prim(phl_grid *g, const double *prim, const double *bx, const double *by,
@@ -572,6 +602,8 @@ phl_status phl_set_state_prim(phl_grid *g, const double *prim, const double *bx,
   CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream), "reset flags");
   launch_prim_to_cons(G, dprim, g->U, g->B, g->T, g->dflag, g->stream);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && G.pred)   // no inversion record
+    e = cudaMemsetAsync(G.pred, 0, 8 * G.plane * sizeof(double), g->stream);
   if (tmp) {
     cudaStreamSynchronize(g->stream);
     cudaFree(tmp);

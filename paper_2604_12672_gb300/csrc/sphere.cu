@@ -655,13 +655,16 @@ __global__ void k_sph_from_prims(SphDev D, const double *__restrict__ rho_in, co
   U[4 * n + c] = eden + 0.5 * rho * dot3(v, v) + 0.5 * dot3(B, B);
 }
 
-// ABI <-> internal cell temperatures
-__global__ void k_sph_temps(SphDev D, const double *__restrict__ in, double *__restrict__ out, int to_int) {
-  const long u = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (u >= D.ncell) return;
-  const long c = sph_cell_of_abi(D, u);
-  if (to_int) out[c] = in[u];
-  else out[u] = in[c];
+// ABI <-> internal cell values, nplanes planes of ncell each (temperatures:
+// one; the inversion record: eight)
+__global__ void k_sph_temps(SphDev D, const double *__restrict__ in, double *__restrict__ out, int to_int,
+                            int nplanes = 1) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= nplanes * D.ncell) return;
+  const long q = t / D.ncell, u = t - q * D.ncell;
+  const long c = q * D.ncell + sph_cell_of_abi(D, u);
+  if (to_int) out[c] = in[t];
+  else out[t] = in[c];
 }
 
 // Cold cells (T <= 0) take the network's guess (cold starts only): warp-
@@ -1416,10 +1419,10 @@ void timed(phl_sphere *S, int cls, F &&launch) {
 // (phi FP64, phif the mixed form's FP32 copy); dmax (mixed): fold the CFL
 // rate.  A stellar shell whose cells lack temperatures first takes the
 // network's guesses (U^n and the FP64 fluxes of the state).
-// pm: the stellar mixed form's inversion record (k_sph_prims_st): 1 at a
-// step's first stage, 2 after.
+// The stellar mixed form starts each inversion from the cell's record
+// (k_sph_prims_st pm = 2; a cleared record gives the plain start).
 void sph_prims(phl_sphere *S, const double *U, const float *dU, const double *phi, unsigned long long *dmax,
-               int pm = 1) {
+               int pm = 2) {
   const SphDev &D = S->D;
   timed(S, KC_SPH_PRIM, [&] {
     if (S->cold && D.use_mlp) k_sph_mlp_guess<<<nblk(D.ncell), SPT, 0, S->s>>>(D, S->U, S->phi);
@@ -1708,6 +1711,7 @@ phl_status phl_sphere_set_state(phl_sphere *S, const double *cons, const double 
     e = cudaMemsetAsync(S->D.T, 0, S->D.ncell * sizeof(double), S->s);
     S->cold = true;
   }
+  if (e == cudaSuccess && S->D.pred) e = cudaMemsetAsync(S->D.pred, 0, 8 * S->D.ncell * sizeof(double), S->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(S->D.dflag, 0, sizeof(int), S->s);
   if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
   if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_set_state: %s", cudaGetErrorString(e));
@@ -1743,6 +1747,7 @@ phl_status phl_sphere_set_prims(phl_sphere *S, const double *rho, const double *
     k_sph_to_float<<<nblk(D.NF), SPT, 0, S->s>>>(D.NF, S->phi, S->phif);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && D.pred) e = cudaMemsetAsync(D.pred, 0, 8 * D.ncell * sizeof(double), S->s);
   S->cold = false;
   if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
   if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_set_prims: %s", cudaGetErrorString(e));
@@ -1761,8 +1766,49 @@ phl_status phl_sphere_set_temperature(phl_sphere *S, const double *T, int where)
     e = cudaGetLastError();
   }
   S->cold = true;   // any value <= 0 marks a cell without one
+  if (e == cudaSuccess && S->D.pred) e = cudaMemsetAsync(S->D.pred, 0, 8 * S->D.ncell * sizeof(double), S->s);
   if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
   if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_set_temperature: %s", cudaGetErrorString(e));
+  return PHL_OK;
+}
+
+phl_status phl_sphere_get_eos_record(phl_sphere *S, double *rec, int where) {
+  if (!S || !rec) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_get_eos_record: null argument");
+  if (!S->D.pred) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_get_eos_record: no record (mixed stellar shells)");
+  if (where != PHL_HOST && where != PHL_DEVICE)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_get_eos_record: bad where");
+  const cudaMemcpyKind kd = where == PHL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const long n = 8 * S->D.ncell;
+  double *buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, n * sizeof(double), S->s);
+  if (e == cudaSuccess) {
+    k_sph_temps<<<nblk(n), SPT, 0, S->s>>>(S->D, S->D.pred, buf, 0, 8);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rec, buf, n * sizeof(double), kd, S->s);
+  if (buf) cudaFreeAsync(buf, S->s);
+  if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_get_eos_record: %s", cudaGetErrorString(e));
+  return PHL_OK;
+}
+
+phl_status phl_sphere_set_eos_record(phl_sphere *S, const double *rec, int where) {
+  if (!S || !rec) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_eos_record: null argument");
+  if (!S->D.pred) return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_eos_record: no record (mixed stellar shells)");
+  if (where != PHL_HOST && where != PHL_DEVICE)
+    return (phl_status)set_error(PHL_EINVAL, "phl_sphere_set_eos_record: bad where");
+  const cudaMemcpyKind kd = where == PHL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const long n = 8 * S->D.ncell;
+  double *buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, n * sizeof(double), S->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf, rec, n * sizeof(double), kd, S->s);
+  if (e == cudaSuccess) {
+    k_sph_temps<<<nblk(n), SPT, 0, S->s>>>(S->D, buf, S->D.pred, 1, 8);
+    e = cudaGetLastError();
+  }
+  if (buf) cudaFreeAsync(buf, S->s);
+  if (e == cudaSuccess && where == PHL_HOST) e = cudaStreamSynchronize(S->s);
+  if (e != cudaSuccess) return (phl_status)set_error(PHL_ECUDA, "phl_sphere_set_eos_record: %s", cudaGetErrorString(e));
   return PHL_OK;
 }
 
@@ -1877,7 +1923,7 @@ void sph_steps(phl_sphere *S, double dt, int nsteps) {
       if (S->mixed) {
         // cells: stage input U^n + dU; increments out dU = b (dU - dt R)
         const float *dUin = st == 0 ? nullptr : S->dU;
-        if (prims) sph_prims(S, S->U, dUin, pin, nullptr, st == 0 ? 1 : 2);
+        if (prims) sph_prims(S, S->U, dUin, pin, nullptr);
         timed(S, KC_SPH_FLUX, [&] {
           if (D.stellar) k_sph_flux<float, true, true><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin, S->phif);
           else k_sph_flux<float, true><<<nblk(D.NF), SPT, 0, S->s>>>(D, S->W32, pin, S->phif);

@@ -232,4 +232,6 @@ def test_sphere_null_handles(P):
     assert L.phl_sphere_set_temperature(None, None, 0) == EINVAL
     assert L.phl_sphere_get_temperature(None, None, 0) == EINVAL
     assert L.phl_sphere_set_graph(None, 1) == EINVAL
+    assert L.phl_sphere_get_eos_record(None, None, 0) == EINVAL
+    assert L.phl_sphere_set_eos_record(None, None, 0) == EINVAL
     L.phl_sphere_destroy(None)

@@ -459,3 +459,30 @@ def test_sphere_graph_steps_equal_direct_launches(P, st_tables, eos):
         s.close()
     for k in ("cons", "pa", "pb", "pr"):
         assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+def test_stellar_sphere_resume_with_record(P, st_tables):
+    """The mixed stellar shell resumed from its state, temperatures and
+    inversion record repeats the uninterrupted run bit for bit."""
+    pr = W.shell_problem(4, 4, eos="stellar", amp=2e-2, beta=1e2, vel_amp=0.05, heat_frac=0.3, mach_heat=0.05)
+    def fresh():
+        s = P.Sphere.from_problem(pr, precision="mixed", eos_table=st_tables[0])
+        s.load(pr)
+        return s
+    a = fresh()
+    a.step(4, dt=1e-3)
+    whole = a.get_state()
+    a.close()
+    b = fresh()
+    b.step(2, dt=1e-3)
+    mid, T, rec = b.get_state(), b.get_temperature(), b.get_eos_record()
+    b.close()
+    c = fresh()
+    c.set_state(mid["cons"], mid["pa"], mid["pb"], mid["pr"])
+    c.set_temperature(T)
+    c.set_eos_record(rec)
+    c.step(2, dt=1e-3)
+    out = c.get_state()
+    c.close()
+    for k in ("cons", "pa", "pb", "pr"):
+        assert np.array_equal(out[k], whole[k]), k
