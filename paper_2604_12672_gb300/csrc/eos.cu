@@ -61,7 +61,8 @@ __global__ void k_table_nodes(int nx, int ny, double x0, double dx, double y0, d
 // Per table cell (i, j) and node slot s: q00 and the differences q10 - q00,
 // q01 - q00, (q11 - q01) - (q10 - q00) of its corners (x first, then y),
 // the same FP64 operations the contraction would do at every evaluation.
-__global__ void k_table_diffs(int nx, int ny, const double *__restrict__ v, double *__restrict__ d) {
+__global__ void k_table_diffs(int nx, int ny, double dx, double dy, const double *__restrict__ v,
+                              double *__restrict__ d) {
   const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (q >= (long)(nx - 1) * (ny - 1) * NQ) return;
   const int s = (int)(q % NQ);
@@ -69,11 +70,16 @@ __global__ void k_table_diffs(int nx, int ny, const double *__restrict__ v, doub
   const int i = (int)(cell % (nx - 1)), j = (int)(cell / (nx - 1));
   const long k0 = ((long)j * nx + i) * NQ + s, k1 = k0 + (long)nx * NQ;
   const double q00 = v[k0], q10 = v[k0 + NQ], q01 = v[k1], q11 = v[k1 + NQ];
+  // the slot's derivative orders (p in x, r in y; slot = qslot(p, r)): in
+  // units of the cell, times dx^p dy^r
+  const int p = (s == 1 || s == 5 || s == 7) ? 1 : ((s == 3 || s == 6 || s == 8) ? 2 : 0);
+  const int r = (s == 2 || s == 5 || s == 6) ? 1 : ((s == 4 || s == 7 || s == 8) ? 2 : 0);
+  const double sc = (p == 0 ? 1.0 : (p == 1 ? dx : dx * dx)) * (r == 0 ? 1.0 : (r == 1 ? dy : dy * dy));
   double *o = d + cell * 4 * NQ + 4 * s;
-  o[0] = q00;
-  o[1] = q10 - q00;
-  o[2] = q01 - q00;
-  o[3] = (q11 - q01) - (q10 - q00);
+  o[0] = q00 * sc;
+  o[1] = (q10 - q00) * sc;
+  o[2] = (q01 - q00) * sc;
+  o[3] = ((q11 - q01) - (q10 - q00)) * sc;
 }
 
 template <typename R>
@@ -122,6 +128,7 @@ phl_status phl_eos_table_create(double lrhoye_lo, double lrhoye_hi, int nrho, do
   t->t.dy = (lT_hi - lT_lo) * log(10.0) / (nT - 1);
   t->t.x0f = (float)t->t.x0; t->t.dxf = (float)t->t.dx; t->t.y0f = (float)t->t.y0; t->t.dyf = (float)t->t.dy;
   t->t.idx = 1.0 / t->t.dx; t->t.idy = 1.0 / t->t.dy;
+  t->t.idx2 = t->t.idx * t->t.idx; t->t.idy2 = t->t.idy * t->t.idy; t->t.idxdy = t->t.idx * t->t.idy;
   t->t.idxf = (float)t->t.idx; t->t.idyf = (float)t->t.idy;
   t->t.Tlo = exp(t->t.y0); t->t.Thi = exp(t->t.y0 + (nT - 1) * t->t.dy);
   t->t.Tlof = (float)t->t.Tlo; t->t.Thif = (float)t->t.Thi;
@@ -157,7 +164,7 @@ phl_status phl_eos_table_create(double lrhoye_lo, double lrhoye_hi, int nrho, do
   const long nd = 4L * NQ * (nrho - 1) * (nT - 1);
   e = cudaMalloc(&t->dd, nd * sizeof(double));
   if (e == cudaSuccess) {
-    k_table_diffs<<<(unsigned)((nd / 4 + 255) / 256), 256>>>(nrho, nT, t->dv, t->dd);
+    k_table_diffs<<<(unsigned)((nd / 4 + 255) / 256), 256>>>(nrho, nT, t->t.dx, t->t.dy, t->dv, t->dd);
     e = cudaDeviceSynchronize();
   }
   if (e != cudaSuccess) {

@@ -50,7 +50,11 @@ struct Table {
   const double *v;            // [ny][nx][NQ] (device)
   const float *vf;            // FP32 copy
   const double *d;            // [ny-1][nx-1][NQ][4]: each table cell's corner values in difference
-                              // form (D00, D10, D01, D11 below), formed once; null: formed per use
+                              // form (D00, D10, D01, D11 below), each slot times dx^p dy^r (its
+                              // derivative orders in units of the cell), formed once; null: formed
+                              // per use.  With d the FP64 evaluation works in cell units and scales
+                              // its results once (idx2 = idx^2, idy2 = idy^2, idxdy = idx idy).
+  double idx2, idy2, idxdy;
   float x0f, dxf, y0f, dyf;
   double idx, idy;            // 1/dx, 1/dy: the evaluation multiplies (FP64 division
   float idxf, idyf;           // is a dozen FP64-pipe instructions on this GPU)
@@ -133,6 +137,7 @@ __device__ __forceinline__ XB<R> xbasis(const Table &t, R x) {
   diff_basis<R>(X.h, R(1));
   diff_basis<R>(X.d, R(0));
   diff_basis<R>(X.e, R(0));
+  if (sizeof(R) == 8 && t.d) return X;   // cell units: the table's differences carry dx^p
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
     X.h[a][1] *= dx; X.h[a][2] *= dx * dx;
@@ -225,6 +230,7 @@ __device__ __forceinline__ bool yloc(const Table &t, R y, int &j, R &v) {
 template <typename R, int M>
 __device__ __forceinline__ void yeval(const Table &t, const YC<R, M> &c, R v, TV<R> &o) {
   const R dy = sizeof(R) == 8 ? (R)t.dy : (R)t.dyf, idy = sizeof(R) == 8 ? (R)t.idy : (R)t.idyf;
+  const bool pre = sizeof(R) == 8 && t.d;   // cell units: scale the results once
   R h[2][3], d[2][3], e[2][3];
   quintic<R, 2>(v, h, d, e);
   diff_basis<R>(h, R(1));
@@ -233,9 +239,9 @@ __device__ __forceinline__ void yeval(const Table &t, const YC<R, M> &c, R v, TV
   R a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, c0 = 0;
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
-    const R sh[3] = {h[b][0], h[b][1] * dy, h[b][2] * dy * dy};
-    const R sd[3] = {d[b][0] * idy, d[b][1], d[b][2] * dy};
-    const R se[3] = {e[b][0] * idy * idy, e[b][1] * idy, e[b][2]};
+    const R sh[3] = {h[b][0], pre ? h[b][1] : h[b][1] * dy, pre ? h[b][2] : h[b][2] * dy * dy};
+    const R sd[3] = {pre ? d[b][0] : d[b][0] * idy, d[b][1], pre ? d[b][2] : d[b][2] * dy};
+    const R se[3] = {pre ? e[b][0] : e[b][0] * idy * idy, pre ? e[b][1] : e[b][1] * idy, e[b][2]};
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const R g0 = b ? c.dg[0][r] : c.g[0][r];
@@ -250,8 +256,13 @@ __device__ __forceinline__ void yeval(const Table &t, const YC<R, M> &c, R v, TV
       if (M > 2) c0 += (b ? c.dg[2][r] : c.g[2][r]) * sh[r];
     }
   }
-  o.f = a0; o.fy = a1; o.fyy = a2;
-  o.fx = b0; o.fxy = b1; o.fxx = c0;
+  if (pre) {
+    o.f = a0; o.fy = a1 * R(t.idy); o.fyy = a2 * R(t.idy2);
+    o.fx = b0 * R(t.idx); o.fxy = b1 * R(t.idxdy); o.fxx = c0 * R(t.idx2);
+  } else {
+    o.f = a0; o.fy = a1; o.fyy = a2;
+    o.fx = b0; o.fxy = b1; o.fxx = c0;
+  }
 }
 
 // Biquintic evaluation of f and its derivatives up to second order at
