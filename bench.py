@@ -714,6 +714,10 @@ SPH_FLUX_DRAM_BYTES_PER_FACE = 109.1
 # f32x2 instructions those counters leave out), and its DRAM bytes per face
 # (241.0 MB in the capture of the packed-lane kernel)
 SPH_FP32_FLOP_PER_FACE = 534.2
+# the stellar shell's mixed inversion (k_sph_prims_st<float>, recorded path): FP64 operations and
+# FP64-pipe instructions per cell-stage, ncu on the 6 x 64^3 stellar shell
+SPH_ST_FP64_FLOP_PER_CELL = 722.0
+SPH_ST_FP64_INST_PER_CELL = 507.1
 SPH_MX_FLUX_DRAM_BYTES_PER_FACE = 50.8
 
 
@@ -779,9 +783,21 @@ def cubed_sphere_c5(P, steps, warmup, stream, alu, hbm_peak, peak_kind, N=256, N
            "steps": steps, "warmup": warmup, "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()},
            "launches_per_step": sum(v[0] for v in kt.values()), "graph": True}
     roof = {"kernel": name, "avg_launch_ms": avg, "launches": launches}
-    if eos == "stellar":
+    if eos == "stellar" and name == "sph_prim" and precision == "mixed":
+        # the inversion: FP64-pipe bound; operation counts per cell from ncu (recorded path)
+        tf = cells * SPH_ST_FP64_FLOP_PER_CELL / (avg * 1e-3) / 1e12
+        inst = cells * SPH_ST_FP64_INST_PER_CELL / (avg * 1e-3) / 1e12
+        roof.update({"bound": "fp64", "achieved": tf, "peak": alu["fp64"], "unit": "TFLOP/s",
+                     "frac": tf / alu["fp64"], "flop_per_cell": SPH_ST_FP64_FLOP_PER_CELL,
+                     "fp64_pipe_inst_per_cell": SPH_ST_FP64_INST_PER_CELL,
+                     "fp64_pipe_inst_rate_frac": inst / (alu["fp64"] / 2.0),
+                     "traffic": None,
+                     "note": "DADD + DMUL + 2 DFMA per cell from ncu on the 6 x 64^3 stellar shell; the "
+                             "instruction rate against the DFMA probe's (one FP64-pipe instruction per DFMA)",
+                     "peak_kind": "measured FP64 DFMA rate (phl_probe_alu)"})
+    elif eos == "stellar":
         roof["note"] = ("stellar EOS: the inversion (sph_prim) and the general-EOS solver (sph_flux) run FP64 "
-                        "table work bound by the FP64 pipe; no per-face operation count is taken for them")
+                        "table work bound by the FP64 pipe; no per-cell operation count is taken for the FP64 form")
     elif name == "sph_flux" and precision == "fp64":
         # HBM view: W read once per cell, phi read and F, E, contact sign
         # written once per face
