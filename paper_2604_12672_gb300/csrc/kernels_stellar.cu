@@ -19,12 +19,15 @@ __device__ __forceinline__ void mixture(const DevGeo &G, const R *X, R &abar, R 
 #pragma unroll
   for (int l = 0; l < PHL_NSPEC_MAX; ++l)
     if (l < G.nspec) sx += X[l];
+  // 1/A and Z/A of each species are constants of the grid: two reciprocals
+  // per cell (GB300's FP64 divisions are a dozen FP64-pipe instructions)
+  const R isx = R(1) / sx;
 #pragma unroll
   for (int l = 0; l < PHL_NSPEC_MAX; ++l)
     if (l < G.nspec) {
-      const R x = X[l] / sx;
-      sa += x / (R)G.Acomp[l];
-      sz += (R)G.Zcomp[l] * x / (R)G.Acomp[l];
+      const R x = X[l] * isx;
+      sa += x * (R)G.iAcomp[l];
+      sz += x * (R)G.ZoAcomp[l];
     }
   abar = R(1) / sa;
   ye = sz;
@@ -41,27 +44,32 @@ __device__ __forceinline__ CellState cell_state(const DevGeo &G, long p, const d
   CellState c;
   const long pl = G.plane;
   double u[5 + PHL_NSPEC_MAX];
+  // the FP32 increments enter through the integer pipe (f2d_scaled: the
+  // conversion and the power-of-two unit scale in one; GB300 converts
+  // FP32 -> FP64 at the FP64 rate)
 #pragma unroll
   for (int v = 0; v < 5 + PHL_NSPEC_MAX; ++v) {
     if (v >= G.nv) continue;
     u[v] = U[v * pl + p];
-    if (dU) u[v] += (double)dU[v * pl + p] * usc(G, v);
+    if (dU) u[v] += f2d_scaled(dU[v * pl + p], uexp(G, v));
   }
   double bl[3] = {Bf[p], Bf[pl + p], Bf[2 * pl + p]};
   double bh[3] = {Bf[p + 1], Bf[pl + p + G.sy], Bf[2 * pl + p + G.sz]};
   if (dB) {
-    const double s = G.sc_b;
-    bl[0] += dB[p] * s; bl[1] += dB[pl + p] * s; bl[2] += dB[2 * pl + p] * s;
-    bh[0] += dB[p + 1] * s; bh[1] += dB[pl + p + G.sy] * s; bh[2] += dB[2 * pl + p + G.sz] * s;
+    const int k = G.e_b;
+    bl[0] += f2d_scaled(dB[p], k); bl[1] += f2d_scaled(dB[pl + p], k); bl[2] += f2d_scaled(dB[2 * pl + p], k);
+    bh[0] += f2d_scaled(dB[p + 1], k); bh[1] += f2d_scaled(dB[pl + p + G.sy], k);
+    bh[2] += f2d_scaled(dB[2 * pl + p + G.sz], k);
   }
   c.rho = u[0];
-  c.v[0] = u[1] / c.rho; c.v[1] = u[2] / c.rho; c.v[2] = u[3] / c.rho;
+  const double ir = 1.0 / c.rho;   // one reciprocal for the cell
+  c.v[0] = u[1] * ir; c.v[1] = u[2] * ir; c.v[2] = u[3] * ir;
   c.b[0] = 0.5 * (bl[0] + bh[0]); c.b[1] = 0.5 * (bl[1] + bh[1]); c.b[2] = 0.5 * (bl[2] + bh[2]);
-  c.eint = u[4] / c.rho - 0.5 * (c.v[0] * c.v[0] + c.v[1] * c.v[1] + c.v[2] * c.v[2]) -
-           0.5 * (c.b[0] * c.b[0] + c.b[1] * c.b[1] + c.b[2] * c.b[2]) / c.rho;
+  c.eint = u[4] * ir - 0.5 * (c.v[0] * c.v[0] + c.v[1] * c.v[1] + c.v[2] * c.v[2]) -
+           0.5 * (c.b[0] * c.b[0] + c.b[1] * c.b[1] + c.b[2] * c.b[2]) * ir;
 #pragma unroll
   for (int l = 0; l < PHL_NSPEC_MAX; ++l)
-    if (l < G.nspec) c.X[l] = u[5 + l] / c.rho;
+    if (l < G.nspec) c.X[l] = u[5 + l] * ir;
   return c;
 }
 
@@ -146,19 +154,32 @@ __device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, c
   const Bg b = bg_cell(G, c[2]);
   const long q = widx(G, c[0], c[1], c[2]);
   const long wt = G.wtot;
-  // FP32 deviations are held in the mixed form's power-of-two units
-  const bool f32 = sizeof(R) == 4;
-  const double sr = f32 ? G.isc_rho : 1.0, sv = f32 ? G.isc_v : 1.0, sb = f32 ? G.isc_b : 1.0,
-               sp = f32 ? G.isc_e : 1.0;
-  W[wix<R>(G, W_RHO, q)] = (R)((rho - b.rho) * sr);
-  W[wix<R>(G, W_VX, q)] = (R)(vx * sv); W[wix<R>(G, W_VY, q)] = (R)(vy * sv); W[wix<R>(G, W_VZ, q)] = (R)(vz * sv);
-  W[wix<R>(G, W_BX, q)] = (R)(bx * sb); W[wix<R>(G, W_BY, q)] = (R)(by * sb); W[wix<R>(G, W_BZ, q)] = (R)(bz * sb);
-  W[wix<R>(G, W_P, q)] = (R)((o.P - b.p) * sp);
-  W[wix<R>(G, W_GE, q)] = (R)(o.ge - b.ge);
-  W[wix<R>(G, W_GC, q)] = (R)(o.gc - b.gc);
+  if constexpr (sizeof(R) == 4) {
+    // FP32 deviations in the mixed form's power-of-two units, converted on
+    // the integer pipe (d2f_scaled: the unit scale folded into the exponent)
+    const int ev = G.e_m - G.e_rho;   // v_s = rho_s v_s / rho_s
+    W[wix<R>(G, W_RHO, q)] = d2f_scaled(rho - b.rho, -G.e_rho);
+    W[wix<R>(G, W_VX, q)] = d2f_scaled(vx, -ev); W[wix<R>(G, W_VY, q)] = d2f_scaled(vy, -ev);
+    W[wix<R>(G, W_VZ, q)] = d2f_scaled(vz, -ev);
+    W[wix<R>(G, W_BX, q)] = d2f_scaled(bx, -G.e_b); W[wix<R>(G, W_BY, q)] = d2f_scaled(by, -G.e_b);
+    W[wix<R>(G, W_BZ, q)] = d2f_scaled(bz, -G.e_b);
+    W[wix<R>(G, W_P, q)] = d2f_scaled(o.P - b.p, -G.e_e);
+    W[wix<R>(G, W_GE, q)] = d2f_scaled(o.ge - b.ge, 0);
+    W[wix<R>(G, W_GC, q)] = d2f_scaled(o.gc - b.gc, 0);
 #pragma unroll
-  for (int l = 0; l < PHL_NSPEC_MAX; ++l)
-    if (l < G.nspec) W[wix<R>(G, W_X0 + l, q)] = (R)X[l];
+    for (int l = 0; l < PHL_NSPEC_MAX; ++l)
+      if (l < G.nspec) W[wix<R>(G, W_X0 + l, q)] = d2f_scaled(X[l], 0);
+  } else {
+    W[wix<R>(G, W_RHO, q)] = rho - b.rho;
+    W[wix<R>(G, W_VX, q)] = vx; W[wix<R>(G, W_VY, q)] = vy; W[wix<R>(G, W_VZ, q)] = vz;
+    W[wix<R>(G, W_BX, q)] = bx; W[wix<R>(G, W_BY, q)] = by; W[wix<R>(G, W_BZ, q)] = bz;
+    W[wix<R>(G, W_P, q)] = o.P - b.p;
+    W[wix<R>(G, W_GE, q)] = o.ge - b.ge;
+    W[wix<R>(G, W_GC, q)] = o.gc - b.gc;
+#pragma unroll
+    for (int l = 0; l < PHL_NSPEC_MAX; ++l)
+      if (l < G.nspec) W[wix<R>(G, W_X0 + l, q)] = X[l];
+  }
   if constexpr (sizeof(R) == 4) {
     float w[W_P + 1];
 #pragma unroll
@@ -167,16 +188,35 @@ __device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, c
   }
   if (!rate) return 0.0;
   // CFL sum of the cell (as k_dt_stellar, from this stage's inversion)
-  const double a2 = o.gc * o.P / rho, b2 = (bx * bx + by * by + bz * bz) / rho;
-  const double vv[3] = {vx, vy, vz}, bb[3] = {bx, by, bz};
-  double sum = 0.0;
-  for (int d = 0; d < 3; ++d) {
-    if (!G.act[d]) continue;
-    const double bd2 = bb[d] * bb[d] / rho;
-    const double disc = fmax((a2 + b2) * (a2 + b2) - 4.0 * a2 * bd2, 0.0);
-    sum += (fabs(vv[d]) + sqrt(0.5 * (a2 + b2 + sqrt(disc)))) / G.dx[d];
+  if constexpr (sizeof(R) == 4) {
+    // the mixed form's CFL step needs a few digits: FP32 (CGS magnitudes stay
+    // inside its range: a^2 ~ 1e17, (a^2 + b^2)^2 ~ 1e34), the FP64 values
+    // converted on the integer pipe
+    const float fr = d2f_scaled(rho, 0), ifr = 1.0f / fr;
+    const float a2 = d2f_scaled(o.gc * o.P, 0) * ifr;
+    const float fv[3] = {d2f_scaled(vx, 0), d2f_scaled(vy, 0), d2f_scaled(vz, 0)};
+    const float fb[3] = {d2f_scaled(bx, 0), d2f_scaled(by, 0), d2f_scaled(bz, 0)};
+    const float b2 = (fb[0] * fb[0] + fb[1] * fb[1] + fb[2] * fb[2]) * ifr;
+    float sum = 0.0f;
+    for (int d = 0; d < 3; ++d) {
+      if (!G.act[d]) continue;
+      const float bd2 = fb[d] * fb[d] * ifr;
+      const float disc = fmaxf((a2 + b2) * (a2 + b2) - 4.0f * a2 * bd2, 0.0f);
+      sum += (fabsf(fv[d]) + sqrtf(0.5f * (a2 + b2 + sqrtf(disc)))) * (float)G.idx[d];
+    }
+    return (sum == sum) ? (double)sum : INFINITY;
+  } else {
+    const double a2 = o.gc * o.P / rho, b2 = (bx * bx + by * by + bz * bz) / rho;
+    const double vv[3] = {vx, vy, vz}, bb[3] = {bx, by, bz};
+    double sum = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      if (!G.act[d]) continue;
+      const double bd2 = bb[d] * bb[d] / rho;
+      const double disc = fmax((a2 + b2) * (a2 + b2) - 4.0 * a2 * bd2, 0.0);
+      sum += (fabs(vv[d]) + sqrt(0.5 * (a2 + b2 + sqrt(disc)))) / G.dx[d];
+    }
+    return (sum == sum) ? sum : INFINITY;
   }
-  return (sum == sum) ? sum : INFINITY;
 }
 
 template <typename R>

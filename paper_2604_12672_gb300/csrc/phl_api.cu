@@ -374,7 +374,12 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
   G.epsf = (float)d->eps_sf;
   G.newton_tol = d->newton_tol > 0.0 ? d->newton_tol : 1e-11;
   G.newton_maxit = d->newton_maxit > 0 ? d->newton_maxit : 50;
-  for (int l = 0; l < PHL_NSPEC_MAX; ++l) { G.Acomp[l] = d->A[l]; G.Zcomp[l] = d->Z[l]; }
+  for (int l = 0; l < PHL_NSPEC_MAX; ++l) {
+    G.Acomp[l] = d->A[l];
+    G.Zcomp[l] = d->Z[l];
+    G.iAcomp[l] = d->A[l] > 0.0 ? 1.0 / d->A[l] : 0.0;
+    G.ZoAcomp[l] = d->A[l] > 0.0 ? d->Z[l] / d->A[l] : 0.0;
+  }
   if (d->eos == PHL_EOS_STELLAR) G.tab = *eos_table_view(d->eos_table);
   if (d->use_mlp) {
     G.use_mlp = d->use_mlp;

@@ -75,6 +75,7 @@ struct DevGeo {
   // stellar EOS
   eos::Table tab;
   double Acomp[PHL_NSPEC_MAX], Zcomp[PHL_NSPEC_MAX];
+  double iAcomp[PHL_NSPEC_MAX], ZoAcomp[PHL_NSPEC_MAX];   // 1/A and Z/A per species
   double newton_tol;
   int newton_maxit;
   int use_mlp;                 // first Newton guess from the network

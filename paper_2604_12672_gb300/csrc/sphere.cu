@@ -725,15 +725,16 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_st(SphDev D, SphWork<R> Wk, c
       const float wr = D.r_f[k + 1] * phif[D.FA + (long)(k + 1) * D.NC + a] - D.r_f[k] * phif[D.FA + (long)k * D.NC + a];
       fx += D.cdc_f[3 * a] * wr; fy += D.cdc_f[3 * a + 1] * wr; fz += D.cdc_f[3 * a + 2] * wr;
       const float iv = D.iom_f[a] * D.ish_f[k];
-      bx = fx * iv; by = fy * iv; bz = fz * iv;
+      // FP32 -> FP64 on the integer pipe (f2d_scaled; GB300 converts at the FP64 rate)
+      bx = f2d_scaled(fx * iv, 0); by = f2d_scaled(fy * iv, 0); bz = f2d_scaled(fz * iv, 0);
     } else {
       const V3 B = cell_field(D, a, k, phi);
       bx = B.x; by = B.y; bz = B.z;
     }
     double rho = U[c], mx = U[n + c], my = U[2 * n + c], mz = U[3 * n + c], E = U[4 * n + c];
     if (sizeof(R) == 4 && dU) {
-      rho += (double)dU[c]; mx += (double)dU[n + c]; my += (double)dU[2 * n + c]; mz += (double)dU[3 * n + c];
-      E += (double)dU[4 * n + c];
+      rho += f2d_scaled(dU[c], 0); mx += f2d_scaled(dU[n + c], 0); my += f2d_scaled(dU[2 * n + c], 0);
+      mz += f2d_scaled(dU[3 * n + c], 0); E += f2d_scaled(dU[4 * n + c], 0);
     }
     const double ir = 1.0 / rho;
     const double ux = mx * ir, uy = my * ir, uz = mz * ir;
