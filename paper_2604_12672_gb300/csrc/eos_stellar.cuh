@@ -496,10 +496,17 @@ __device__ __forceinline__ int eos_invert_mixed(const Table &t, double rho, doub
 
 // The last inversion of a cell, for the next one's first guess: its rho,
 // e_int, 1/c_v and de/drho|_T there, ln T and 1/T of the result, and
-// x = ln(n_e N_A) with n_e = rho Y_e (ne).
+// x = ln(n_e N_A) and 1/n_e with n_e = rho Y_e.
 struct Pred {
-  double rho, e, icv, er, lnT, iT, x, ne;
+  double rho, e, icv, er, lnT, iT, x, ine;
 };
+
+// 1/(a (1 + d)) from ia = 1/a: the series 1 - d + d^2 - d^3 + d^4 below
+// |d| = 2^-10 (truncation below 2^-50), else the division.
+__device__ __forceinline__ double inv_step(double ia, double d, double a_new) {
+  if (!(fabs(d) < 1.0 / 1024.0)) return 1.0 / a_new;
+  return ia * (1.0 - d * (1.0 - d * (1.0 - d * (1.0 - d))));
+}
 
 // ln(a) from ln(a_p) for a = a_p (1 + d): the series of ln(1 + d) to d^4
 // below |d| = 2^-10 (as next_lnT), else fall back.
@@ -515,10 +522,9 @@ struct EosC {
   double P, e, PT, icv, er, cs2, iT;
 };
 __device__ __forceinline__ bool eos_rt_c(const Table &t, const XB<double> &X, double rho, double irho, double T,
-                                         double lnT, double iab, EosC &o, const YC<double, 1> *c1) {
+                                         double lnT, double iT, double iab, EosC &o, const YC<double, 1> *c1) {
   TV<double> q;
   if (!table_eval_xb<double>(t, X, lnT, q, c1)) return false;
-  const double iT = 1.0 / T;
   const double Rg = RGAS;
   const double aT3 = ARAD * T * T * T, aT4 = aT3 * T;
   o.P = (q.fx - q.f) + rho * Rg * T * iab + aT4 * (1.0 / 3.0);
@@ -537,7 +543,7 @@ __device__ __forceinline__ bool eos_rt_c(const Table &t, const XB<double> &X, do
 // gamma_e = P / (rho e) + 1 from that P and e; gamma_c = rho c_s^2 / P
 // (c_s^2 at T1: relative error ~dT/T, wave speeds only); one reciprocal for
 // both.  Writes the record of the inversion.
-__device__ __forceinline__ void rec_carry(double rho, double eint, double ne, double x, double T1, double lnT1,
+__device__ __forceinline__ void rec_carry(double rho, double eint, double ine, double x, double T1, double lnT1,
                                           const EosC &c, EosOut<double> &o, double &T, Pred &pr) {
   const double dT = (eint - c.e) * c.icv;
   const double P = fma(c.PT, dT, c.P);
@@ -551,7 +557,7 @@ __device__ __forceinline__ void rec_carry(double rho, double eint, double ne, do
   o.er = c.er;
   T = T1 + dT;
   const double dd = dT * c.iT;
-  pr = Pred{rho, eint, c.icv, c.er, lnT1 + dd * (1.0 - dd * (0.5 - dd * (1.0 / 3.0))), c.iT * (1.0 - dd), x, ne};
+  pr = Pred{rho, eint, c.icv, c.er, lnT1 + dd * (1.0 - dd * (0.5 - dd * (1.0 / 3.0))), c.iT * (1.0 - dd), x, ine};
 }
 
 // Mixed-precision inversion with a per-cell record (rec: the record holds
@@ -563,13 +569,17 @@ __device__ __forceinline__ void rec_carry(double rho, double eint, double ne, do
 // of ln(1 + d).  Without a record (or where the change was larger) the
 // mixed inversion's own steps: e, c_v at T; from within 2e-6 one Newton
 // step, the full evaluation and the carry; from within 1e-4 the FP64 Newton
-// loop; else FP32 iterations first.  Writes the record; returns the count
-// of evaluations at distinct temperatures (1 for the recorded path) or -1.
-__device__ __forceinline__ int eos_invert_rec(const Table &t, double rho, double eint, double abar, double ye,
-                                              double &T, double tol, int maxit, EosOut<double> &o, Pred &pr,
-                                              bool rec) {
-  const double ne = rho * ye, irho = 1.0 / rho, iab = 1.0 / abar;
-  const double x = rec ? ln_step(pr.x, (ne - pr.ne) / pr.ne, ne * NAV) : log(ne * NAV);
+// loop; else FP32 iterations first.  irho = 1/rho and iab = 1/Abar come
+// with the arguments.  Writes the record; returns the count of evaluations
+// at distinct temperatures (1 for the recorded path) or -1.
+__device__ __forceinline__ int eos_invert_rec(const Table &t, double rho, double irho, double eint, double abar,
+                                              double iab, double ye, double &T, double tol, int maxit,
+                                              EosOut<double> &o, Pred &pr, bool rec) {
+  const double ne = rho * ye;
+  rec = rec && pr.ine > 0.0;
+  const double dn = rec ? ne * pr.ine - 1.0 : 0.0;   // n_e = n_e,p (1 + dn)
+  const double x = rec ? ln_step(pr.x, dn, ne * NAV) : log(ne * NAV);
+  const double ine = rec ? inv_step(pr.ine, dn, ne) : 1.0 / ne;
   const XB<double> X = xbasis<double>(t, x);
   YC<double, 1> c;
   c.j = -1;
@@ -577,10 +587,11 @@ __device__ __forceinline__ int eos_invert_rec(const Table &t, double rho, double
   if (rec && pr.icv > 0.0 && T > t.Tlo && T < t.Thi) {
     const double T1 = T + (eint - pr.e - pr.er * (rho - pr.rho)) * pr.icv;
     if (T1 > t.Tlo && T1 < t.Thi) {
-      const double lnT1 = ln_step(pr.lnT, (T1 - T) * pr.iT, T1);
-      if (!eos_rt_c(t, X, rho, irho, T1, lnT1, iab, f, nullptr)) return -1;
+      const double dT = (T1 - T) * pr.iT;   // T1 = T (1 + dT)
+      const double lnT1 = ln_step(pr.lnT, dT, T1);
+      if (!eos_rt_c(t, X, rho, irho, T1, lnT1, inv_step(pr.iT, dT, T1), iab, f, nullptr)) return -1;
       if (fabs(eint - f.e) < 2e-6 * fabs(eint)) {
-        rec_carry(rho, eint, ne, x, T1, lnT1, f, o, T, pr);
+        rec_carry(rho, eint, ine, x, T1, lnT1, f, o, T, pr);
         return 1;
       }
       T = T1;   // a larger change: the steps below from T1
@@ -596,8 +607,8 @@ __device__ __forceinline__ int eos_invert_rec(const Table &t, double rho, double
         const double T1 = T + de / cv;
         if (T1 > t.Tlo && T1 < t.Thi) {
           const double lnT1 = next_lnT<double>(T, lnT, T1);
-          if (!eos_rt_c(t, X, rho, irho, T1, lnT1, iab, f, &c)) return -1;
-          rec_carry(rho, eint, ne, x, T1, lnT1, f, o, T, pr);
+          if (!eos_rt_c(t, X, rho, irho, T1, lnT1, 1.0 / T1, iab, f, &c)) return -1;
+          rec_carry(rho, eint, ine, x, T1, lnT1, f, o, T, pr);
           return 2;
         }
       }
@@ -612,7 +623,7 @@ __device__ __forceinline__ int eos_invert_rec(const Table &t, double rho, double
     it0 = it64 < 0 ? -1 : it64 + (it32 > 0 ? it32 : 12);
   }
   if (it0 > 0)   // the record of a Newton-loop result (the rare paths)
-    pr = Pred{rho, eint, 1.0 / o.cv, o.er, log(T), 1.0 / T, x, ne};
+    pr = Pred{rho, eint, 1.0 / o.cv, o.er, log(T), 1.0 / T, x, ine};
   return it0;
 }
 

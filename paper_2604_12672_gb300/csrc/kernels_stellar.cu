@@ -14,7 +14,7 @@ namespace {
 
 // Mean mass number and electron fraction of normalised mass fractions.
 template <typename R>
-__device__ __forceinline__ void mixture(const DevGeo &G, const R *X, R &abar, R &ye) {
+__device__ __forceinline__ void mixture(const DevGeo &G, const R *X, R &abar, R &ye, R *iabar = nullptr) {
   R sx = R(0), sa = R(0), sz = R(0);
 #pragma unroll
   for (int l = 0; l < PHL_NSPEC_MAX; ++l)
@@ -31,12 +31,13 @@ __device__ __forceinline__ void mixture(const DevGeo &G, const R *X, R &abar, R 
     }
   abar = R(1) / sa;
   ye = sz;
+  if (iabar) *iabar = sa;
 }
 
 // Stage-input state of interior cell p: density, velocity, cell-centred B,
 // specific internal energy, mass fractions.
 struct CellState {
-  double rho, v[3], b[3], eint, X[PHL_NSPEC_MAX];
+  double rho, irho, v[3], b[3], eint, X[PHL_NSPEC_MAX];
 };
 __device__ __forceinline__ CellState cell_state(const DevGeo &G, long p, const double *__restrict__ U,
                                                 const double *__restrict__ Bf, const float *__restrict__ dU,
@@ -63,6 +64,7 @@ __device__ __forceinline__ CellState cell_state(const DevGeo &G, long p, const d
   }
   c.rho = u[0];
   const double ir = 1.0 / c.rho;   // one reciprocal for the cell
+  c.irho = ir;
   c.v[0] = u[1] * ir; c.v[1] = u[2] * ir; c.v[2] = u[3] * ir;
   c.b[0] = 0.5 * (bl[0] + bh[0]); c.b[1] = 0.5 * (bl[1] + bh[1]); c.b[2] = 0.5 * (bl[2] + bh[2]);
   c.eint = u[4] * ir - 0.5 * (c.v[0] * c.v[0] + c.v[1] * c.v[1] + c.v[2] * c.v[2]) -
@@ -122,8 +124,8 @@ __device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, c
   double X[PHL_NSPEC_MAX];
 #pragma unroll
   for (int l = 0; l < PHL_NSPEC_MAX; ++l) X[l] = cs.X[l];
-  double abar, ye;
-  mixture<double>(G, X, abar, ye);
+  double abar, ye, iab;
+  mixture<double>(G, X, abar, ye, &iab);
   double T = G.use_mlp ? Tout[p] : Tin[p];   // Tout holds the network's guesses (k_mlp_guess)
   eos::EosOut<double> o;
   int it;
@@ -132,9 +134,10 @@ __device__ __forceinline__ double eos_cell_step(const DevGeo &G, const int *c, c
     eos::Pred pr{};
     double *rp = G.pred + p;
     if (pm == 2) pr = eos::Pred{rp[0], rp[pl], rp[2 * pl], rp[3 * pl], rp[4 * pl], rp[5 * pl], rp[6 * pl], rp[7 * pl]};
-    it = eos::eos_invert_rec(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o, pr, pm == 2);
+    it = eos::eos_invert_rec(G.tab, rho, cs.irho, eint, abar, iab, ye, T, G.newton_tol, G.newton_maxit, o, pr,
+                             pm == 2);
     rp[0] = pr.rho; rp[pl] = pr.e; rp[2 * pl] = pr.icv; rp[3 * pl] = pr.er;
-    rp[4 * pl] = pr.lnT; rp[5 * pl] = pr.iT; rp[6 * pl] = pr.x; rp[7 * pl] = pr.ne;
+    rp[4 * pl] = pr.lnT; rp[5 * pl] = pr.iT; rp[6 * pl] = pr.x; rp[7 * pl] = pr.ine;
   } else {
     it = sizeof(R) == 8 ? eos::eos_invert<double>(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o)
                         : eos::eos_invert_mixed(G.tab, rho, eint, abar, ye, T, G.newton_tol, G.newton_maxit, o);

@@ -381,6 +381,7 @@ struct SphDev {
   int stellar;
   eos::Table tab;
   double abar, ye, rho_u, p_u, e_u, ntol;
+  double irho_u, iabar;        // 1 / rho_u, 1 / Abar
   int nmaxit;
   const double *ge_c, *gc_c, *ge_f, *gc_f;   // background gamma_e, gamma_c: shells (Nr), radii (Nr + 1)
   const float *ge_cf, *gc_cf, *ge_ff, *gc_ff;
@@ -747,9 +748,10 @@ __global__ void __launch_bounds__(SPT) k_sph_prims_st(SphDev D, SphWork<R> Wk, c
       eos::Pred pr{};
       double *rp = D.pred + c;
       if (pm == 2) pr = eos::Pred{rp[0], rp[n], rp[2 * n], rp[3 * n], rp[4 * n], rp[5 * n], rp[6 * n], rp[7 * n]};
-      it = eos::eos_invert_rec(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o, pr, pm == 2);
+      it = eos::eos_invert_rec(D.tab, rho * D.rho_u, ir * D.irho_u, eint * D.e_u, D.abar, D.iabar, D.ye, T, D.ntol,
+                               D.nmaxit, o, pr, pm == 2);
       rp[0] = pr.rho; rp[n] = pr.e; rp[2 * n] = pr.icv; rp[3 * n] = pr.er;
-      rp[4 * n] = pr.lnT; rp[5 * n] = pr.iT; rp[6 * n] = pr.x; rp[7 * n] = pr.ne;
+      rp[4 * n] = pr.lnT; rp[5 * n] = pr.iT; rp[6 * n] = pr.x; rp[7 * n] = pr.ine;
     } else {
       it = sizeof(R) == 8
                ? eos::eos_invert<double>(D.tab, rho * D.rho_u, eint * D.e_u, D.abar, D.ye, T, D.ntol, D.nmaxit, o)
@@ -1549,8 +1551,9 @@ phl_status phl_sphere_create(const phl_sphere_desc *d, phl_sphere **out) {
       ye += d->X[l] * d->Z[l] / d->A[l];
     }
     D.abar = 1.0 / inv_abar;
+    D.iabar = inv_abar;
     D.ye = ye;
-    D.rho_u = d->rho_unit; D.p_u = d->p_unit; D.e_u = d->p_unit / d->rho_unit;
+    D.rho_u = d->rho_unit; D.p_u = d->p_unit; D.e_u = d->p_unit / d->rho_unit; D.irho_u = 1.0 / d->rho_unit;
     D.ntol = d->newton_tol > 0.0 ? d->newton_tol : 1e-11;
     D.nmaxit = d->newton_maxit > 0 ? d->newton_maxit : 50;
     if (d->mlp) {
