@@ -461,7 +461,12 @@ def l1_mixed_vs_fp64(P, pr, steps=3):
             "note": "||mixed - fp64||_1 / ||fp64 - initial||_1 per field at the same fixed dt"}
 
 
-def stellar_c3(P, n, steps, warmup, stream, ws):
+# the stellar box's mixed inversion (k_eos_cells<float> from each cell's record): FP64 operations
+# per cell-stage, ncu on the 128^3 box (DADD + DMUL + 2 DFMA)
+EOS_FP64_FLOP_PER_CELL = 721.0
+
+
+def stellar_c3(P, n, steps, warmup, stream, ws, alu=None):
     """The same box with the stellar EOS (ions + radiation + e-/e+ pairs, 16O/28Si
     0.5/0.5, rho 1e5-1e7 g/cc): plain FP64 form (Newton from the previous T)
     vs the mixed form with the network's first guess, trained here on 1e7
@@ -497,10 +502,28 @@ def stellar_c3(P, n, steps, warmup, stream, ws):
         ms = allreduce_max(e0.elapsed_time(e1), ws)
         g.check()
         it = g.stats()["newton_iters"] - it0
+        kt = None
+        if name == "mixed+mlp_cold_only":   # one more step with per-kernel events: the inversion's roofline
+            g.set_timing(True)
+            g.step(1)
+            kt = g.kernel_times(reset=True)
+            g.set_timing(False)
         g.close()
         out["forms"][name] = {"value": pr.ncells * STAGES * steps * ws / (ms * 1e-3), "unit": UNIT,
                               "ms_per_step": ms / steps,
                               "newton_iters_per_cell_stage": it / (pr.ncells * STAGES * steps)}
+        if kt and "prim" in kt and alu:
+            launches, kms = kt["prim"]
+            avg = kms / max(launches, 1)
+            tf = pr.ncells * EOS_FP64_FLOP_PER_CELL / (avg * 1e-3) / 1e12
+            out["forms"][name]["kernels"] = {k: {"launches": v[0], "ms": v[1]} for k, v in kt.items()}
+            out["roofline"] = {"kernel": "k_eos_cells (inversion, class prim)", "avg_launch_ms": avg,
+                               "bound": "fp64", "achieved": tf, "peak": alu["fp64"], "unit": "TFLOP/s",
+                               "frac": tf / alu["fp64"], "flop_per_cell": EOS_FP64_FLOP_PER_CELL,
+                               "traffic": None,
+                               "note": "DADD + DMUL + 2 DFMA per cell from ncu at 128^3 (recorded path); the class "
+                                       "also holds the ghost fill",
+                               "peak_kind": "measured FP64 DFMA rate (phl_probe_alu)"}
     f = out["forms"]
     out["mixed_mlp_over_fp64"] = f["mixed+mlp"]["value"] / f["fp64"]["value"]
     out["mixed_mlp_cold_only_over_fp64"] = f["mixed+mlp_cold_only"]["value"] / f["fp64"]["value"]
@@ -933,7 +956,7 @@ def main():
                                                  args.c5_nr, args.c5_precision, args.c5_eos, table, mlp)))
         return 0
     if args.c3_only:
-        c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws)
+        c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws, alu)
         if rank == 0:
             print(json.dumps(c3))
         return 0
@@ -968,7 +991,7 @@ def main():
         l1 = l1_mixed_vs_fp64(P, pr)
     c3 = None
     if not args.no_c3 and len(forms) == 2:
-        c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws)
+        c3 = stellar_c3(P, args.n, args.c3_steps, 2, stream, ws, alu)
     c4 = None
     if not args.no_c4 and len(forms) == 2:
         c4 = ensemble_c4(P, args.c4_steps, 2, stream, ws)
