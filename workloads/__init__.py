@@ -276,7 +276,10 @@ def polytrope_profile(z, n_poly=1.5, g0=1.0, rho_b=1.0, rho_top=0.1, ztop=1.0):
     rho^(1/n)(z) = rho_b^(1/n) - g0 z / (K (n+1)); K fixed by rho(ztop) = rho_top.
     """
     K = g0 * ztop / ((n_poly + 1.0) * (rho_b ** (1.0 / n_poly) - rho_top ** (1.0 / n_poly)))
-    base = rho_b ** (1.0 / n_poly) - g0 * z / (K * (n_poly + 1.0))
+    # beyond the polytrope's surface (z > 1.27 for the defaults: only the
+    # top ghost layers of boxes with nz < 12 reach it) density and pressure
+    # are zero
+    base = np.maximum(rho_b ** (1.0 / n_poly) - g0 * z / (K * (n_poly + 1.0)), 0.0)
     rho = base ** n_poly
     return rho, K * rho ** (1.0 + 1.0 / n_poly), K
 
