@@ -14,6 +14,29 @@ __global__ void k_prim_mx(DevGeo G, Box box, const double *__restrict__ U, const
   k_prim_mx_at(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, U, Bf, dU, dB, W, dflag);
 }
 
+// The first stage's primitives of U^n with the CFL rate of the interior
+// cells folded in (the rate as k_dt_mx, from the U^n and face values the
+// thread has just read): block maximum, one atomicMax per block.
+__global__ void __launch_bounds__(256) k_prim_mx_cfl(DevGeo G, Box box, const double *__restrict__ U,
+                                                     const double *__restrict__ Bf, float *__restrict__ W, int *dflag,
+                                                     unsigned int *fmax_bits) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  k_prim_mx_at(t, G, box, U, Bf, nullptr, nullptr, W, dflag);
+  float m = 0.0f;
+  int c[3];
+  if (cell_at(box, t, c) && c[0] >= 0 && c[0] < G.n[0] && c[1] >= 0 && c[1] < G.n[1] && c[2] >= 0 && c[2] < G.n[2])
+    m = dt_rate_mx(G, U, Bf, c, dflag);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) atomicMax(fmax_bits, __float_as_uint(v));
+  }
+}
+
 __global__ void k_update_cells_mx(DevGeo G, Box box, StageMx S) {
   k_update_cells_mx_at(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, S);
 }
@@ -98,8 +121,15 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
       launch_eos_cells<float>(G, M.U, M.B, dU, dB, M.Tin, M.Tout, M.W, M.dflag, s, &nl, prof,
                               first ? M.cfl_dmax : nullptr, const_cast<double *>(M.dt), G.use_mlp == 1 ? 0 : 2);
     } else {
-      PHL_LAUNCH(KC_PRIM, prof, s, k_prim_mx<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, dU, dB, M.W, M.dflag));
-      ++nl;
+      if (first && M.cfl_fmax) {   // the step's CFL step from the same pass over U^n
+        PHL_LAUNCH(KC_PRIM, prof, s,
+                   k_prim_mx_cfl<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, M.W, M.dflag, M.cfl_fmax));
+        PHL_LAUNCH(KC_DT, prof, s, k_dt_mx_finalize<<<1, 1, 0, s>>>(G.cfl, G.sc_t, M.cfl_fmax, const_cast<double *>(M.dt)));
+        nl += 2;
+      } else {
+        PHL_LAUNCH(KC_PRIM, prof, s, k_prim_mx<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, dU, dB, M.W, M.dflag));
+        ++nl;
+      }
     }
     if (three && G.eps_sf > 0.0) {
       Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);

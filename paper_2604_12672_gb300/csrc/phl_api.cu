@@ -644,10 +644,14 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
         launch_set_scalar(g->dt, dt, g->stream, g->prof.on ? &g->prof : nullptr);
         ++nl;
       }
-    } else if (g->G.eos != PHL_EOS_STELLAR) {
+    } else if (g->G.eos != PHL_EOS_STELLAR && !(g->mixed && !three)) {
       launch_dt(g, &nl);
       if (three) CK(cudaMemsetAsync(g->fmax, 0, sizeof(unsigned int), g->stream), "clear CFL maximum");
     }
+    // ideal-gas mixed form (six launches per stage) with the device CFL step:
+    // the first stage's primitives of U^n give it
+    unsigned int *cfl_fmax = (g->mixed && !three && g->G.eos != PHL_EOS_STELLAR && !(dt > 0.0)) ? g->fmax + 1
+                                                                                                 : nullptr;
     // stellar EOS with the device CFL step: the first stage's inversion gives it
     unsigned long long *cfl_dmax = (g->G.eos == PHL_EOS_STELLAR && !(dt > 0.0)) ? g->dmax : nullptr;
     if (g->mixed) {
@@ -664,6 +668,7 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
       M.primed = primed;
       M.fmax = g->fmax;
       M.cfl_dmax = cfl_dmax;
+      M.cfl_fmax = cfl_fmax;
       for (int st = 0; st < ns; ++st) {
         M.Tin = g->T;
         M.Tout = g->T2;

@@ -310,6 +310,9 @@ struct MixedBufs {
   // stage after the state was set from outside
   bool primed = false;
   unsigned int *fmax = nullptr; // CFL rate maximum the last stage folds into (pipeline3)
+  // ideal gas, device CFL step: the first stage's primitives of U^n also
+  // fold the CFL rate into this maximum and set dt (no separate CFL pass)
+  unsigned int *cfl_fmax = nullptr;
 };
 void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
                         int *nlaunch, Prof *prof);
