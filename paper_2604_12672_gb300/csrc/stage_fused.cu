@@ -781,13 +781,50 @@ inline dim3 site_grid(const DevGeo &G) {
   return dim3((unsigned)((G.n[0] + EB_X) / EB_X), (unsigned)((G.n[1] + EB_Y) / EB_Y), (unsigned)((G.n[2] + EB_Z) / EB_Z));
 }
 
+// Contact-CT of one edge from its four face EMFs (a1, a0, b1, b0), their
+// mass-flux signs and the four cell EMFs (emf_edge's formula).
+__device__ __forceinline__ float ct_corner(float Ea1, float Ea0, float Eb1, float Eb0, float ma1, float ma0,
+                                           float mb1, float mb0, float E00, float E10, float E01, float E11) {
+  const float lo_l = Eb0 - E00, lo_r = Eb1 - E10;
+  const float up_l = E01 - Eb0, up_r = E11 - Eb1;
+  const float h = 0.5f, q4 = 0.25f;
+  const float dlo = ma0 > 0.0f ? lo_l : (ma0 < 0.0f ? lo_r : h * (lo_l + lo_r));
+  const float dup = ma1 > 0.0f ? up_l : (ma1 < 0.0f ? up_r : h * (up_l + up_r));
+  const float le_d = Ea0 - E00, le_u = Ea1 - E01;
+  const float ri_d = E10 - Ea0, ri_u = E11 - Ea1;
+  const float dle = mb0 > 0.0f ? le_d : (mb0 < 0.0f ? le_u : h * (le_d + le_u));
+  const float dri = mb1 > 0.0f ? ri_d : (mb1 < 0.0f ? ri_u : h * (ri_d + ri_u));
+  return q4 * (Ea1 + Ea0 + Eb1 + Eb0) + q4 * (dlo - dup) + q4 * (dle - dri);
+}
+
 __global__ void k_emf3(DevGeo G, Box box, const float *__restrict__ W, const float *__restrict__ F0,
                        const float *__restrict__ F1, const float *__restrict__ F2, float *__restrict__ E) {
   int c[3];
   if (!site3(G, c)) return;
-  const long p = widx(G, c[0], c[1], c[2]);
   const long wt = G.wtot;
   const bool interior = c[0] >= 1 && c[0] < G.n[0] && c[1] >= 1 && c[1] < G.n[1] && c[2] >= 1 && c[2] < G.n[2];
+  if (interior && wt < 0x7fffffffL) {
+    // an interior site (nearly all of them): every face and cell it reads is
+    // interior; 32-bit offsets within each plane (the same values and
+    // formula as emf_edge)
+    const int p = (int)(c[0] + G.ge[0]) + (int)G.wy * (c[1] + G.ge[1]) + (int)G.wz * (c[2] + G.ge[2]);
+    const int wy = (int)G.wy, wz = (int)G.wz;
+    const float *xBy = F0 + (F_BX + 1) * wt, *xBz = F0 + (F_BX + 2) * wt, *ux = F0 + (long)G.nf * wt;
+    const float *yBz = F1 + (F_BX + 2) * wt, *yBx = F1 + (F_BX + 0) * wt, *uy = F1 + (long)G.nf * wt;
+    const float *zBx = F2 + (F_BX + 0) * wt, *zBy = F2 + (F_BX + 1) * wt, *uz = F2 + (long)G.nf * wt;
+    const float *e0 = W + waux(G, AUX_E + 0, 0), *e1 = W + waux(G, AUX_E + 1, 0), *e2 = W + waux(G, AUX_E + 2, 0);
+    // x-edges: a = y-faces, b = z-faces
+    E[p] = ct_corner(-yBz[p], -yBz[p - wz], zBy[p], zBy[p - wy], uy[p], uy[p - wz], uz[p], uz[p - wy],
+                     e0[p - wy - wz], e0[p - wz], e0[p - wy], e0[p]);
+    // y-edges: a = z-faces, b = x-faces
+    E[wt + p] = ct_corner(-zBx[p], -zBx[p - 1], xBz[p], xBz[p - wz], uz[p], uz[p - 1], ux[p], ux[p - wz],
+                          e1[p - wz - 1], e1[p - 1], e1[p - wz], e1[p]);
+    // z-edges: a = x-faces, b = y-faces
+    E[2 * wt + p] = ct_corner(-xBy[p], -xBy[p - wy], yBx[p], yBx[p - 1], ux[p], ux[p - wy], uy[p], uy[p - 1],
+                              e2[p - 1 - wy], e2[p - wy], e2[p - 1], e2[p]);
+    return;
+  }
+  const long p = widx(G, c[0], c[1], c[2]);
   if (c[0] < G.n[0]) E[p] = emf_edge<0>(G, c, interior, p, W, F1, F2);
   if (c[1] < G.n[1]) E[wt + p] = emf_edge<1>(G, c, interior, p, W, F2, F0);
   if (c[2] < G.n[2]) E[2 * wt + p] = emf_edge<2>(G, c, interior, p, W, F0, F1);
