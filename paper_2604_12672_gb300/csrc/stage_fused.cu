@@ -146,7 +146,8 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
   const float brho = D == 2 ? sm.bgf[0][k] : sm.bgc[0][k], bp = D == 2 ? sm.bgf[1][k] : sm.bgc[1][k];
   if (!(brho + wl[RD_RHO] > 0.0f && brho + wr[RD_RHO] > 0.0f && bp + wl[RD_P] > 0.0f && bp + wr[RD_P] > 0.0f))
     atomicOr(dflag, FLAG_NEG);
-  const long qb = (long)D * G.plane + sidx(G, c[0], c[1], c[2]);
+  // 32-bit offsets (fused_stage_ok bounds the planes)
+  const int qb = D * (int)G.plane + c[0] + (int)G.sy * c[1] + (int)G.sz * c[2];
   const float b0 = d2f_scaled(S.B[qb], -G.e_b);
   const float bn = S.first ? b0 : b0 + S.dB[qb];
   // dilated shock flags of the two cells; local cell (i, j, k) sits at flg[k+1][j+1][i+1]
@@ -167,11 +168,11 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
 #pragma unroll
   for (int q = 0; q < 5; ++q) out[q] = fl[q];
   if (own) {
-    const long wt = G.wtot;
-    const long pR = widx(G, c[0], c[1], c[2]);
+    const int wt = (int)G.wtot;
+    const int pR = (c[0] + G.ge[0]) + (int)G.wy * (c[1] + G.ge[1]) + (int)G.wz * (c[2] + G.ge[2]);
     Fd[(F_BX + T1) * wt + pR] = fl[RF_BT1];
     Fd[(F_BX + T2) * wt + pR] = fl[RF_BT2];
-    Fd[(long)G.nf * wt + pR] = (float)up;
+    Fd[G.nf * wt + pR] = (float)up;
   }
 }
 
@@ -598,10 +599,10 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap *tmW, const DevGeo &
     }
     if (G.heatf) se += G.heatf[c2];
     r[U_E] -= se;
-    const long ps = sidx(G, c0, c1, c2);
+    const int ps = c0 + (int)G.sy * c1 + (int)G.sz * c2;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const long q = v * G.plane + ps;
+      const int q = v * (int)G.plane + ps;
       const float din = S.first ? 0.0f : S.dU[q];
       const float dout = S.b * (din - dt * r[v]);
       if (S.last) S.U[q] += f2d_scaled(dout, uexp(G, v));
@@ -1207,7 +1208,9 @@ cudaError_t fused_init() {
 bool fused_stage_ok(const DevGeo &G) {
   return G.eos == PHL_EOS_IDEAL && G.nspec == 0 && G.wstr == 8 && G.act[0] && G.act[1] && G.act[2] &&
          G.n[0] >= 4 && G.n[1] >= 4 && G.n[2] >= 4 &&
-         G.recon != PHL_RECON_PQH;   // the tile stages two ghost layers; PQH needs three
+         G.recon != PHL_RECON_PQH &&   // the tile stages two ghost layers; PQH needs three
+         // the tile kernel indexes the state's and the face fluxes' planes with 32-bit offsets
+         5 * G.plane < 0x7fffffffL && (long)(G.nf + 1) * G.wtot < 0x7fffffffL;
 }
 
 // TMA descriptor of W's two float4 planes as a 4-D tensor (x * 4 floats, y, z,
