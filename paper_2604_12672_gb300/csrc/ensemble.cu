@@ -294,7 +294,8 @@ cudaError_t launch_step_chains(phl_ensemble *E) {
     MixedBufs M;
     M.U = v.U; M.B = v.B; M.dU = v.dU; M.dB = v.dB; M.W = v.W;
     for (int k = 0; k < 3; ++k) M.F[k] = v.F[k];
-    M.E = v.E; M.raw = v.raw; M.flag = v.flag; M.dt = v.dt; M.dflag = v.dflag; M.Tin = nullptr; M.Tout = nullptr;
+    M.E = v.E; M.raw = v.raw; M.flag = v.flag; M.anyraw = v.anyraw; M.dt = v.dt; M.dflag = v.dflag;
+    M.Tin = nullptr; M.Tout = nullptr;
     M.tmapW = v.tmapW; M.fused_variant = v.fused;   // the box's own stage decomposition
     M.pipeline3 = v.pipeline3;
     M.primed = false;   // each replay forms W from the state it finds

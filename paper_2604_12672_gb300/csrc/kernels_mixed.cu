@@ -14,6 +14,14 @@ __global__ void k_prim_mx(DevGeo G, Box box, const double *__restrict__ U, const
   k_prim_mx_at(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, U, Bf, dU, dB, W, dflag);
 }
 
+// Five CTAs per SM (48 registers, a few spilled to L1): the pass is bound by
+// the loads in flight, and this cap measured fastest (3 .. 8 tried).
+__global__ void __launch_bounds__(256, 5) k_prim_mx2(DevGeo G, Box hbox, const double *__restrict__ U,
+                                                  const double *__restrict__ Bf, const float *__restrict__ dU,
+                                                  const float *__restrict__ dB, float *__restrict__ W, int *dflag) {
+  k_prim_mx2_at(blockIdx.x * (long)blockDim.x + threadIdx.x, G, hbox, U, Bf, dU, dB, W, dflag);
+}
+
 // The first stage's primitives of U^n with the CFL rate of the interior
 // cells folded in (the rate as k_dt_mx, from the U^n and face values the
 // thread has just read): block maximum, one atomicMax per block.
@@ -126,6 +134,11 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
                    k_prim_mx_cfl<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, M.W, M.dflag, M.cfl_fmax));
         PHL_LAUNCH(KC_DT, prof, s, k_dt_mx_finalize<<<1, 1, 0, s>>>(G.cfl, G.sc_t, M.cfl_fmax, const_cast<double *>(M.dt)));
         nl += 2;
+      } else if (prim_pairs_ok(G)) {   // two cells of a row per thread
+        Box hb = make_box(0, (G.n[0] + 2 * G.ge[0]) / 2, l[1], h[1], l[2], h[2]);
+        PHL_LAUNCH(KC_PRIM, prof, s,
+                   k_prim_mx2<<<grid3(hb), block3(hb), 0, s>>>(G, hb, M.U, M.B, dU, dB, M.W, M.dflag));
+        ++nl;
       } else {
         PHL_LAUNCH(KC_PRIM, prof, s, k_prim_mx<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, dU, dB, M.W, M.dflag));
         ++nl;

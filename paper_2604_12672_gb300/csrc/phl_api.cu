@@ -73,6 +73,7 @@ struct phl_grid {
   // mixed precision: FP32 increments and work arrays
   float *dUf = nullptr, *dBf = nullptr, *Wf = nullptr, *Ff[3] = {nullptr, nullptr, nullptr}, *Ef = nullptr;
   unsigned int *fmax = nullptr;         // [0]: the step's CFL maximum (three-launch path), [1]: phl_compute_dt
+  unsigned int *anyraw = nullptr;       // fused path: some cell carries a raw shock flag (this stage)
   bool mixed = false;
   bool pipeline3 = false;               // fused mixed stage in three launches (phl_set_fused 201..209)
   bool w_valid = false;                 // W, raw flags and fmax[0] hold the current state's (three-launch path)
@@ -250,7 +251,7 @@ GridView grid_view(phl_grid *g) {
   v.dU = g->dUf; v.dB = g->dBf; v.W = g->Wf;
   for (int k = 0; k < 3; ++k) v.F[k] = g->Ff[k];
   v.E = g->Ef;
-  v.raw = g->raw; v.flag = g->flag;
+  v.raw = g->raw; v.flag = g->flag; v.anyraw = g->anyraw;
   v.dt = g->dt; v.fmax = g->fmax + 1; v.dflag = g->dflag;
   v.w_valid = &g->w_valid;
   v.pipeline3 = g->pipeline3;
@@ -426,6 +427,7 @@ phl_status phl_create_grid(const phl_grid_desc *d, phl_grid **out) {
     }
   }
   AL(&g->raw, 2 * ncell);   // raw flags + one dilation pass buffer
+  AL(&g->anyraw, 1);
   if (d->eos == PHL_EOS_STELLAR) {
     AL(&g->T, G.plane);
     AL(&g->T2, G.plane);
@@ -669,6 +671,7 @@ phl_status phl_step(phl_grid *g, double dt, int nsteps) {
       M.fmax = g->fmax;
       M.cfl_dmax = cfl_dmax;
       M.cfl_fmax = cfl_fmax;
+      M.anyraw = g->anyraw;
       for (int st = 0; st < ns; ++st) {
         M.Tin = g->T;
         M.Tout = g->T2;

@@ -313,6 +313,9 @@ struct MixedBufs {
   // ideal gas, device CFL step: the first stage's primitives of U^n also
   // fold the CFL rate into this maximum and set dt (no separate CFL pass)
   unsigned int *cfl_fmax = nullptr;
+  // fused six-launch path: the raw-flag kernel's "some cell is flagged" vote
+  // (zeroed before it); null = always dilate and load the flags
+  unsigned int *anyraw = nullptr;
 };
 void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
                         int *nlaunch, Prof *prof);
@@ -348,6 +351,7 @@ struct GridView {
   double *U, *B;
   float *dU, *dB, *W, *F[3], *E;
   uint8_t *raw, *flag;
+  unsigned int *anyraw;        // the raw-flag kernel's vote (fused six-launch stage)
   double *dt;
   unsigned int *fmax;
   int *dflag;

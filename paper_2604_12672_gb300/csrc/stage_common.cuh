@@ -130,10 +130,10 @@ __device__ __forceinline__ R mp5_face(R a, R b, R c, R d, R e) {
 __device__ __forceinline__ long wstride(const DevGeo &G, int d) { return d == 0 ? 1L : (d == 1 ? G.wy : G.wz); }
 
 template <typename R>
-__device__ __forceinline__ void k_flag_raw_at(long tl, const DevGeo &G, const Box &box, const R *__restrict__ W, uint8_t *__restrict__ raw) {
+__device__ __forceinline__ bool k_flag_raw_at(long tl, const DevGeo &G, const Box &box, const R *__restrict__ W, uint8_t *__restrict__ raw) {
   {
     int c[3];
-    if (!cell_at(box, tl, c)) return;
+    if (!cell_at(box, tl, c)) return false;
     const long q = widx(G, c[0], c[1], c[2]);
     auto P = [&](long r) {
       if constexpr (sizeof(R) == 4) return W[waux(G, AUX_P, r)];
@@ -149,12 +149,20 @@ __device__ __forceinline__ void k_flag_raw_at(long tl, const DevGeo &G, const Bo
       const R Pm = P(q - sd) + bg_cell_t<R>(G, km).p;
       sum += fabs(Pp - Pm);
     }
-    raw[c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2])] = (sum / (eps_sf_t<R>(G) * P0) > R(1)) ? 1 : 0;
+    const bool f = sum / (eps_sf_t<R>(G) * P0) > R(1);
+    raw[c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2])] = f ? 1 : 0;
+    return f;
   }
 }
+// any (optional, zeroed before the launch): set to 1 when some cell of the
+// box is flagged -- one atomic per warp that holds a flagged cell, none in a
+// flow without shocks, where the dilation and its loads are then skipped.
+// The block size is a multiple of 32 and no thread leaves before the vote.
 template <typename R>
-__global__ void k_flag_raw(DevGeo G, Box box, const R *__restrict__ W, uint8_t *__restrict__ raw) {
-  k_flag_raw_at<R>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, W, raw);
+__global__ void k_flag_raw(DevGeo G, Box box, const R *__restrict__ W, uint8_t *__restrict__ raw,
+                           unsigned int *any = nullptr) {
+  const bool f = k_flag_raw_at<R>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, box, W, raw);
+  if (any && __any_sync(0xffffffffu, f) && (threadIdx.x & 31) == 0) atomicOr(any, 1u);
 }
 
 // 5^d dilation of the raw shock flags (Sect. 2.7), done as one 5-wide OR per

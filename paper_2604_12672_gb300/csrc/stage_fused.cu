@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "mixed_common.cuh"
@@ -617,8 +618,9 @@ template <int NT, int MINB, bool PHASED, bool PAIRED = false, bool LR = false, b
 __global__ void __launch_bounds__(NT, MINB)
     k_flux_update_mx(const __grid_constant__ CUtensorMap tmW, DevGeo G, StageMx S, const uint8_t *__restrict__ flag,
                      float *__restrict__ F0, float *__restrict__ F1, float *__restrict__ F2, int ntx, int nty,
-                     int *dflag, unsigned extra_tx, int raw_flags) {
+                     int *dflag, unsigned extra_tx, int raw_flags, const unsigned int *__restrict__ any) {
   extern __shared__ unsigned char smraw[];
+  if (any && *any == 0u) flag = nullptr;   // no cell flagged: the tile stages zero flags
   FusedSmem &sm = *reinterpret_cast<FusedSmem *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
   int t = blockIdx.x;
   const int tx = t % ntx;
@@ -703,15 +705,23 @@ __device__ __forceinline__ void dilate_tile(const DevGeo &G, const uint8_t *__re
   }
 }
 
+// any (optional): the raw-flag kernel's vote; zero means no cell is flagged,
+// the dilation is all zero and the tile kernel, reading the same vote, loads
+// none of it -- nothing is written.
 __global__ void __launch_bounds__(256) k_flag_dilate3(DevGeo G, const uint8_t *__restrict__ raw,
-                                                     uint8_t *__restrict__ dil, int ntx, int nty) {
+                                                     uint8_t *__restrict__ dil, int ntx, int nty,
+                                                     const unsigned int *__restrict__ any) {
   __shared__ unsigned long long r0[HZ * HY][2];
   __shared__ unsigned long long r1[HZ * HY], r2[HZ * FY];
-  int t = blockIdx.x;
-  const int tx = t % ntx;
-  t /= ntx;
-  const int ty = t % nty, tz = t / nty;
-  dilate_tile(G, raw, dil, tx * FX, ty * FY, tz * FZ, r0, r1, r2);
+  if (any && *any == 0u) return;
+  const int nb = ntx * nty * ((G.n[2] + FZ - 1) / FZ);
+  for (int t0 = blockIdx.x; t0 < nb; t0 += gridDim.x) {   // the block's tiles; the grid fills the SMs once
+    int t = t0;
+    const int tx = t % ntx;
+    t /= ntx;
+    const int ty = t % nty, tz = t / nty;
+    dilate_tile(G, raw, dil, tx * FX, ty * FY, tz * FZ, r0, r1, r2);
+  }
 }
 
 // Contact-CT edge EMF along D at the lower corner (a-1/2, b-1/2) of cell c,
@@ -1243,15 +1253,24 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   const int nb = ntx * nty * ntz;
   const long ncell = (long)G.n[0] * G.n[1] * G.n[2];
   const uint8_t *dil = nullptr;
+  const unsigned int *any = nullptr;
   int raw_mode = 0;
   if (G.eps_sf > 0.0 && M.pipeline3) {   // the tile kernel dilates the raw flags itself
     dil = M.raw;
     raw_mode = 1;
   } else if (G.eps_sf > 0.0) {   // raw flags, then their 5^3 dilation, both on the interior layout
     Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
-    PHL_LAUNCH(KC_FLAG_RAW, prof, s, k_flag_raw<float><<<grid3(bi), block3(bi), 0, s>>>(G, bi, M.W, M.raw));
-    PHL_LAUNCH(KC_FLAG_DILATE, prof, s, k_flag_dilate3<<<nb, 256, 0, s>>>(G, M.raw, M.raw + ncell, ntx, nty));
+    if (M.anyraw) cudaMemsetAsync(M.anyraw, 0, sizeof(unsigned int), s);
+    PHL_LAUNCH(KC_FLAG_RAW, prof, s,
+               k_flag_raw<float><<<grid3(bi), block3(bi), 0, s>>>(G, bi, M.W, M.raw, M.anyraw));
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int nbd = std::min(nb, 8 * std::max(nsm, 1));   // eight 256-thread CTAs per SM
+    PHL_LAUNCH(KC_FLAG_DILATE, prof, s,
+               k_flag_dilate3<<<nbd, 256, 0, s>>>(G, M.raw, M.raw + ncell, ntx, nty, M.anyraw));
     dil = M.raw + ncell;
+    any = M.anyraw;
     *nl += 2;
   }
   const CUtensorMap *tm = (const CUtensorMap *)M.tmapW;
@@ -1260,7 +1279,7 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   PHL_LAUNCH(KC_FLUX_UPDATE, prof, s,                                                                          \
              (k_flux_update_mx<NT, MB, PH, PA, LRS, PP><<<nb, NT, smem_bytes(PH), s>>>(*tm, G, S, dil, M.F[0],   \
                                                                                    M.F[1], M.F[2], ntx, nty,     \
-                                                                                   M.dflag, M.test_extra_tx, raw_mode)))
+                                                                                   M.dflag, M.test_extra_tx, raw_mode, any)))
   // the reconstruction is a template parameter: the van Leer kernels carry no PPH code
 #define PHL_FUSED(NT, MB, PH, PA, LRS)                      \
   do {                                                     \

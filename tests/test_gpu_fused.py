@@ -129,6 +129,36 @@ def test_fused_blast_with_flags(P):
         assert abs(fu["cons"][v_].sum() - t0) <= 1e-9 * abs(t0), v_
 
 
+def test_fused_flag_vote_is_taken_every_stage(P):
+    """The raw-flag kernel votes whether any cell is flagged; with no vote the
+    dilation is skipped (its buffer keeps an older stage's flags) and the tile
+    kernel stages zero flags.  One grid switched between a flagged state (the
+    blast) and a flag-free one (the same box at uniform pressure) must give,
+    after each switch, exactly what a fresh grid gives: no stale flag or vote
+    leaks from one state into the other."""
+    pr = blast(21, 18, 11)
+    calm = pr.copy()   # uniform pressure 1: the internal energy of every cell replaced
+    b = (0.3, 0.2, 0.1)
+    rho, m = pr.cons[0], pr.cons[1:4]
+    calm.cons[4] = 1.0 / (pr.gamma - 1.0) + 0.5 * (m ** 2).sum(axis=0) / rho + 0.5 * sum(c * c for c in b)
+
+    def fresh(state_pr, nsteps):
+        return run(P, state_pr, True, nsteps, 2e-3)
+
+    ref_calm, ref_blast = fresh(calm, 2), fresh(pr, 2)
+    g = P.Grid(pr, precision="mixed")
+    g.set_fused(True)
+    for src, ref in ((pr, ref_blast), (calm, ref_calm), (pr, ref_blast), (calm, ref_calm)):
+        g.set_state(src.cons, src.bx, src.by, src.bz)
+        g.step(2, 2e-3)
+        got = g.get_state()
+        for k in ("cons", "bx", "by", "bz"):
+            assert np.array_equal(got[k], ref[k]), k
+    g.close()
+    # the two states really differ in their flags: the calm run is not the blast run
+    assert not np.array_equal(ref_calm["cons"], ref_blast["cons"])
+
+
 def test_fused_divergence_free(P):
     """Contact-CT on the fused path keeps div B at round-off (Eq. divb).  The
     mixed form adds FP32 face increments (each a discrete curl rounded once in

@@ -146,6 +146,35 @@ def test_mixed_long_run_c2_physics(P):
         assert worst[k] <= 1e-5, (k, worst[k])
 
 
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("bcx", [(0, 0), (1, 1), (2, 2)])
+def test_prim_pairs_equal_single_cells(P, fused, bcx):
+    """Boxes of even n_x form the primitives two cells of a row per thread
+    (FP64 pairs, one shared x-face) except in the first stage of a step with
+    the device CFL step, whose pass over U^n also takes the CFL rate cell by
+    cell.  A step with the device CFL step and a step with a fixed dt equal to
+    it (compute_dt gives the same rate and reduction) therefore differ only
+    in which form built the first stage's W: the results must be
+    bit-identical, with x-ghost pairs of every boundary kind."""
+    pr = W.stratified_box(24, 14, 18, amp=3e-2, beta=1e3, mach_heat=3e-2)
+    pr.bc = (bcx, (0, 0), (1, 1))
+    out = []
+    for fixed in (False, True):
+        g = P.Grid(pr, precision="mixed")
+        g.set_fused(fused)
+        g.load()
+        if fixed:
+            dt = g.compute_dt()
+            g.step(1, dt)
+        else:
+            g.step(1)
+        out.append(g.get_state())
+        g.close()
+    for k in ("cons", "bx", "by", "bz"):
+        assert np.array_equal(out[0][k], out[1][k]), k
+    assert not np.array_equal(out[0]["cons"], pr.cons)
+
+
 def test_mixed_orszag_tang_close_to_oracle(P):
     pr = W.orszag_tang(64)
     g = P.Grid(pr, precision="mixed")
