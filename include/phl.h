@@ -290,6 +290,29 @@ phl_status phl_set_fused(phl_grid *g, int on);
  * PHL_EUNSUPPORTED if the grid does not run the fused kernel. */
 phl_status phl_test_tile_wait_timeout(phl_grid *g, int on);
 
+/* Test of the two forms of the mixed stage's primitive deviations (Sect. 2.8,
+ * the deviations from the hydrostatic background of the stage-input state):
+ * forms W for the whole work box (interior cells and their ghost images) of a
+ * mixed ideal-gas grid and copies it to the host.
+ *   form       0: one cell per thread; 1: two cells of a row per thread from
+ *              aligned FP64 pairs (grids with an even number of cells along x
+ *              and no species); 2 / 3: forms 0 / 1 of the first stage, with the
+ *              CFL rate of U^n taken from the same deviations
+ *   increments != 0 (forms 0 and 1): add the grid's current FP32 stage
+ *              increments, as the second and third stages do
+ *   w_out      host, cap floats; receives (wstr + 4) x wtot floats: the W
+ *              planes and their auxiliary planes in the work layout (two ghost
+ *              layers per active axis, x fastest), zero where no cell is formed
+ *              (phl_test_prims_size gives the count)
+ *   rate_out   host, optional: the largest CFL rate in scaled units (forms 2, 3;
+ *              0 otherwise)
+ * W is clobbered (the next phl_step forms it again).  Synchronous on the
+ * grid's stream.  PHL_EUNSUPPORTED for FP64 or stellar grids, or form 1 / 3 on
+ * a grid without the pair form; PHL_EINVAL for a bad form or a short buffer. */
+phl_status phl_test_prims(phl_grid *g, int form, int increments, float *w_out, long cap, float *rate_out);
+/* The number of floats phl_test_prims writes (0 for an FP64 grid). */
+phl_status phl_test_prims_size(phl_grid *g, long *nfloat);
+
 /* Device pointer of the last computed dt (double), valid for the grid's
  * lifetime; lets callers enqueue reads without a synchronisation. */
 phl_status phl_dt_device_ptr(phl_grid *g, const double **ptr);

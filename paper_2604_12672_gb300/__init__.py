@@ -102,6 +102,8 @@ _SIGS = {
     "phl_set_fused": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_diffuse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     "phl_test_tile_wait_timeout": (C.c_int, [C.c_void_p, C.c_int]),
+    "phl_test_prims": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_long, C.POINTER(C.c_float)]),
+    "phl_test_prims_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_long)]),
     "phl_convert_batch": (C.c_int, [C.c_long, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "phl_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "phl_destroy": (None, [C.c_void_p]),
@@ -604,6 +606,18 @@ class Grid:
         """Make the fused tile kernel's bounded TMA wait run out (a test of the
         failure path; see phl_test_tile_wait_timeout)."""
         _check(lib().phl_test_tile_wait_timeout(self.h, int(bool(on))))
+
+    def test_prims(self, form, increments=True):
+        """The mixed stage's primitive deviations of the whole work box in one
+        form (phl_test_prims): returns (W and auxiliary planes as float32,
+        the CFL rate for forms 2 and 3)."""
+        n = C.c_long(0)
+        _check(lib().phl_test_prims_size(self.h, C.byref(n)))
+        out = np.zeros(n.value, dtype=np.float32)
+        rate = C.c_float(0.0)
+        _check(lib().phl_test_prims(self.h, int(form), int(bool(increments)), out.ctypes.data, n.value,
+                                    C.byref(rate)))
+        return out, rate.value
 
     def set_fused(self, on=1):
         """Mixed-precision stage decomposition (phl_set_fused): 0/False = one

@@ -19,21 +19,12 @@ __global__ void k_prim_mx(DevGeo G, Box box, const double *__restrict__ U, const
 __global__ void __launch_bounds__(256, 5) k_prim_mx2(DevGeo G, Box hbox, const double *__restrict__ U,
                                                   const double *__restrict__ Bf, const float *__restrict__ dU,
                                                   const float *__restrict__ dB, float *__restrict__ W, int *dflag) {
-  k_prim_mx2_at(blockIdx.x * (long)blockDim.x + threadIdx.x, G, hbox, U, Bf, dU, dB, W, dflag);
+  k_prim_mx2_at<false>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, hbox, U, Bf, dU, dB, W, dflag);
 }
 
-// The first stage's primitives of U^n with the CFL rate of the interior
-// cells folded in (the rate as k_dt_mx, from the U^n and face values the
-// thread has just read): block maximum, one atomicMax per block.
-__global__ void __launch_bounds__(256) k_prim_mx_cfl(DevGeo G, Box box, const double *__restrict__ U,
-                                                     const double *__restrict__ Bf, float *__restrict__ W, int *dflag,
-                                                     unsigned int *fmax_bits) {
-  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  k_prim_mx_at(t, G, box, U, Bf, nullptr, nullptr, W, dflag);
-  float m = 0.0f;
-  int c[3];
-  if (cell_at(box, t, c) && c[0] >= 0 && c[0] < G.n[0] && c[1] >= 0 && c[1] < G.n[1] && c[2] >= 0 && c[2] < G.n[2])
-    m = dt_rate_mx(G, U, Bf, c, dflag);
+// Block maximum of the CFL rates, one atomicMax per block (non-negative
+// floats order like their bit patterns).
+__device__ __forceinline__ void block_rate_max(float m, unsigned int *fmax_bits) {
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   __shared__ float red[8];
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -43,6 +34,29 @@ __global__ void __launch_bounds__(256) k_prim_mx_cfl(DevGeo G, Box box, const do
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (threadIdx.x == 0) atomicMax(fmax_bits, __float_as_uint(v));
   }
+}
+
+// The first stage's primitives of U^n, two cells per thread, with the CFL
+// rate of the interior cells taken from the same deviations.
+__global__ void __launch_bounds__(256, 5) k_prim_mx2_cfl(DevGeo G, Box hbox, const double *__restrict__ U,
+                                                       const double *__restrict__ Bf, float *__restrict__ W,
+                                                       int *dflag, unsigned int *fmax_bits) {
+  const float m = k_prim_mx2_at<true>(blockIdx.x * (long)blockDim.x + threadIdx.x, G, hbox, U, Bf, nullptr, nullptr,
+                                      W, dflag);
+  block_rate_max(m, fmax_bits);
+}
+
+// The first stage's primitives of U^n with the CFL rate of the interior
+// cells folded in (the rate as k_dt_mx, from the deviations the thread has
+// just formed): block maximum, one atomicMax per block.
+__global__ void __launch_bounds__(256) k_prim_mx_cfl(DevGeo G, Box box, const double *__restrict__ U,
+                                                     const double *__restrict__ Bf, float *__restrict__ W, int *dflag,
+                                                     unsigned int *fmax_bits) {
+  float m = 0.0f;
+  int c[3];
+  if (cell_at(box, blockIdx.x * (long)blockDim.x + threadIdx.x, c))
+    prim_store_cell(G, c, U, Bf, nullptr, nullptr, W, dflag, &m);
+  block_rate_max(m, fmax_bits);
 }
 
 __global__ void k_update_cells_mx(DevGeo G, Box box, StageMx S) {
@@ -104,6 +118,24 @@ void launch_dt_mixed_from_max(const DevGeo &G, double fixed_dt, unsigned int *fm
   if (nlaunch) *nlaunch += 1;
 }
 
+cudaError_t launch_prims_form(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
+                              float *W, int *dflag, int form, unsigned int *fmax_bits, cudaStream_t s) {
+  int l[3], h[3];
+  for (int d = 0; d < 3; ++d) {
+    if (G.act[d]) { l[d] = -G.ge[d]; h[d] = G.n[d] + G.ge[d]; }
+    else { l[d] = 0; h[d] = 1; }
+  }
+  const Box bx = make_box(l[0], h[0], l[1], h[1], l[2], h[2]);
+  const Box hb = make_box(0, (G.n[0] + 2 * G.ge[0]) / 2, l[1], h[1], l[2], h[2]);
+  switch (form) {
+    case 0: k_prim_mx<<<grid3(bx), block3(bx), 0, s>>>(G, bx, U, Bf, dU, dB, W, dflag); break;
+    case 1: k_prim_mx2<<<grid3(hb), block3(hb), 0, s>>>(G, hb, U, Bf, dU, dB, W, dflag); break;
+    case 2: k_prim_mx_cfl<<<grid3(bx), block3(bx), 0, s>>>(G, bx, U, Bf, W, dflag, fmax_bits); break;
+    default: k_prim_mx2_cfl<<<grid3(hb), block3(hb), 0, s>>>(G, hb, U, Bf, W, dflag, fmax_bits); break;
+  }
+  return cudaGetLastError();
+}
+
 void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
                         int *nlaunch, Prof *prof) {
   int nl = 0;
@@ -130,8 +162,14 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
                               first ? M.cfl_dmax : nullptr, const_cast<double *>(M.dt), G.use_mlp == 1 ? 0 : 2);
     } else {
       if (first && M.cfl_fmax) {   // the step's CFL step from the same pass over U^n
-        PHL_LAUNCH(KC_PRIM, prof, s,
-                   k_prim_mx_cfl<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, M.W, M.dflag, M.cfl_fmax));
+        if (prim_pairs_ok(G)) {
+          Box hb = make_box(0, (G.n[0] + 2 * G.ge[0]) / 2, l[1], h[1], l[2], h[2]);
+          PHL_LAUNCH(KC_PRIM, prof, s,
+                     k_prim_mx2_cfl<<<grid3(hb), block3(hb), 0, s>>>(G, hb, M.U, M.B, M.W, M.dflag, M.cfl_fmax));
+        } else {
+          PHL_LAUNCH(KC_PRIM, prof, s,
+                     k_prim_mx_cfl<<<grid3(bx), block3(bx), 0, s>>>(G, bx, M.U, M.B, M.W, M.dflag, M.cfl_fmax));
+        }
         PHL_LAUNCH(KC_DT, prof, s, k_dt_mx_finalize<<<1, 1, 0, s>>>(G.cfl, G.sc_t, M.cfl_fmax, const_cast<double *>(M.dt)));
         nl += 2;
       } else if (prim_pairs_ok(G)) {   // two cells of a row per thread

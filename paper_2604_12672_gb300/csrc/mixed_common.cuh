@@ -81,19 +81,45 @@ __device__ __forceinline__ void cell_prims_mx(const DevGeo &G, const double *__r
   }
 }
 
+// CFL rate sum_d (|u_d| + c_f,d) / dx_d of a cell from its deviations w at
+// height k, in scaled units.
+__device__ __forceinline__ float dt_rate_w(const DevGeo &G, const float *w, int k) {
+  const BgT<float> b = bg_cell_t<float>(G, k);
+  const float rho = b.rho + w[W_RHO], P = b.p + w[W_P], gc = b.gc + w[W_GC];
+  const float ir = 1.0f / rho;
+  const float a2 = gc * P * ir;
+  const float b2 = (w[W_BX] * w[W_BX] + w[W_BY] * w[W_BY] + w[W_BZ] * w[W_BZ]) * ir;
+  float s = 0.0f;
+  for (int d = 0; d < 3; ++d) {
+    if (!G.act[d]) continue;
+    const float bd2 = w[W_BX + d] * w[W_BX + d] * ir;
+    float disc = (a2 + b2) * (a2 + b2) - 4.0f * a2 * bd2;
+    disc = fmaxf(disc, 0.0f);
+    const float cf = sqrtf(0.5f * (a2 + b2 + sqrtf(disc)));
+    s += (fabsf(w[W_VX + d]) + cf) * G.idxf[d];
+  }
+  return (s == s) ? s : INFINITY;
+}
+
 // Deviations of work cell c (ghosts from their source cells, mirrored where
-// a reflecting wall applies) stored into W and its auxiliary planes.
+// a reflecting wall applies) stored into W and its auxiliary planes.  rate
+// (optional): the CFL rate of an interior cell from the same deviations (the
+// operations of dt_rate_mx), 0 for a ghost.
 __device__ __forceinline__ void prim_store_cell(const DevGeo &G, const int *c, const double *__restrict__ U,
                                                 const double *__restrict__ Bf, const float *__restrict__ dU,
-                                                const float *__restrict__ dB, float *__restrict__ W, int *dflag) {
+                                                const float *__restrict__ dB, float *__restrict__ W, int *dflag,
+                                                float *rate = nullptr) {
   int s[3];
   bool fl[3];
+  bool in = true;
   for (int d = 0; d < 3; ++d) {
     fl[d] = false;
     s[d] = G.act[d] ? cell_src(c[d], G.n[d], G.bc[d][0], G.bc[d][1], fl[d]) : 0;
+    in = in && c[d] >= 0 && c[d] < G.n[d];
   }
   float w[NW_MAX];
   cell_prims_mx(G, U, Bf, dU, dB, s[0], s[1], s[2], w, dflag);
+  if (rate) *rate = in ? dt_rate_w(G, w, c[2]) : 0.0f;
   for (int d = 0; d < 3; ++d)
     if (fl[d]) { w[W_VX + d] = -w[W_VX + d]; w[W_BX + d] = -w[W_BX + d]; }
   const long q = widx(G, c[0], c[1], c[2]);
@@ -117,19 +143,6 @@ __device__ __forceinline__ void k_prim_mx_at(long tl, const DevGeo &G, const Box
   prim_store_cell(G, c, U, Bf, dU, dB, W, dflag);
 }
 
-// The pair form of the primitives needs: an ideal gas without species (W in
-// two float4 planes), an active x axis of even length and an even number of
-// ghost layers along x, so that the source cells of every pair of work cells
-// (2m - ge, 2m - ge + 1) lie in one aligned pair of state cells (2a, 2a + 1)
-// -- interior pairs are their own sources; periodic ghost pairs map to the
-// pair at the other end, reflecting ones to the mirrored boundary pair,
-// outflow ones to the boundary cell twice -- and rows and planes of the
-// state have even pitches, so every such pair is a 16-byte FP64 load.
-__host__ __device__ inline bool prim_pairs_ok(const DevGeo &G) {
-  return G.wstr == 8 && G.nspec == 0 && G.eos == 0 && G.act[0] && G.n[0] % 2 == 0 && G.ge[0] % 2 == 0 &&
-         G.sy % 2 == 0 && G.sz % 2 == 0 && G.plane % 2 == 0;
-}
-
 // Two neighbouring work cells of one row per thread: element (m, j, k) of
 // hbox (x extent (n_x + 2 ge_x) / 2) is the pair x0 = 2m - ge_x, x0 + 1.  The
 // thread reads the aligned state pair holding both cells' sources (each
@@ -137,11 +150,14 @@ __host__ __device__ inline bool prim_pairs_ok(const DevGeo &G) {
 // 2a .. 2a + 2), picks each cell's values by its offset in the pair and
 // forms it with the operations of the single-cell path (bit-identical W),
 // with no branch between interior and ghost pairs.
-__device__ __forceinline__ void k_prim_mx2_at(long tl, const DevGeo &G, const Box &hbox, const double *__restrict__ U,
-                                              const double *__restrict__ Bf, const float *__restrict__ dU,
-                                              const float *__restrict__ dB, float *__restrict__ W, int *dflag) {
+// CFL: also returns the larger CFL rate of the pair's interior cells (0 if
+// none), from the same deviations (the operations of dt_rate_mx).
+template <bool CFL>
+__device__ __forceinline__ float k_prim_mx2_at(long tl, const DevGeo &G, const Box &hbox, const double *__restrict__ U,
+                                               const double *__restrict__ Bf, const float *__restrict__ dU,
+                                               const float *__restrict__ dB, float *__restrict__ W, int *dflag) {
   int c[3];
-  if (!cell_at(hbox, tl, c)) return;
+  if (!cell_at(hbox, tl, c)) return 0.0f;
   c[0] = 2 * c[0] - G.ge[0];
   bool flA = false, flB = false, fl[3] = {false, false, false};
   const int sA = cell_src(c[0], G.n[0], G.bc[0][0], G.bc[0][1], flA);
@@ -199,6 +215,12 @@ __device__ __forceinline__ void k_prim_mx2_at(long tl, const DevGeo &G, const Bo
   float wA[NW_MAX], wB[NW_MAX];
   prims_mx_finish(G, bf, drA, m0A, m1A, m2A, dEA, bxlA, bxhA, bylA, byhA, bzlA, bzhA, wA, dflag);
   prims_mx_finish(G, bf, drB, m0B, m1B, m2B, dEB, bxlB, bxhB, bylB, byhB, bzlB, bzhB, wB, dflag);
+  float rate = 0.0f;
+  if (CFL) {
+    const bool row = (!G.act[1] || (c[1] >= 0 && c[1] < G.n[1])) && (!G.act[2] || (c[2] >= 0 && c[2] < G.n[2]));
+    if (row && c[0] >= 0 && c[0] < G.n[0]) rate = dt_rate_w(G, wA, c[2]);
+    if (row && c[0] + 1 >= 0 && c[0] + 1 < G.n[0]) rate = fmaxf(rate, dt_rate_w(G, wB, c[2]));
+  }
   if (flA) { wA[W_VX] = -wA[W_VX]; wA[W_BX] = -wA[W_BX]; }
   if (flB) { wB[W_VX] = -wB[W_VX]; wB[W_BX] = -wB[W_BX]; }
   for (int d = 1; d < 3; ++d)
@@ -214,6 +236,7 @@ __device__ __forceinline__ void k_prim_mx2_at(long tl, const DevGeo &G, const Bo
   W4[G.wtot + q + 1] = make_float4(wB[W_BX], wB[W_BY], wB[W_BZ], wB[W_P]);
   write_aux(G, W, q, wA);
   write_aux(G, W, q + 1, wB);
+  return rate;
 }
 
 struct StageMx {
@@ -291,26 +314,6 @@ __device__ __forceinline__ void k_update_faces_mx_at(long tl, const DevGeo &G, c
   }
 }
 
-
-// CFL rate sum_d (|u_d| + c_f,d) / dx_d of a cell from its deviations w at
-// height k, in scaled units.
-__device__ __forceinline__ float dt_rate_w(const DevGeo &G, const float *w, int k) {
-  const BgT<float> b = bg_cell_t<float>(G, k);
-  const float rho = b.rho + w[W_RHO], P = b.p + w[W_P], gc = b.gc + w[W_GC];
-  const float ir = 1.0f / rho;
-  const float a2 = gc * P * ir;
-  const float b2 = (w[W_BX] * w[W_BX] + w[W_BY] * w[W_BY] + w[W_BZ] * w[W_BZ]) * ir;
-  float s = 0.0f;
-  for (int d = 0; d < 3; ++d) {
-    if (!G.act[d]) continue;
-    const float bd2 = w[W_BX + d] * w[W_BX + d] * ir;
-    float disc = (a2 + b2) * (a2 + b2) - 4.0f * a2 * bd2;
-    disc = fmaxf(disc, 0.0f);
-    const float cf = sqrtf(0.5f * (a2 + b2 + sqrtf(disc)));
-    s += (fabsf(w[W_VX + d]) + cf) * G.idxf[d];
-  }
-  return (s == s) ? s : INFINITY;
-}
 
 // CFL rate of one interior cell of U^n, in scaled units.
 __device__ __forceinline__ float dt_rate_mx(const DevGeo &G, const double *__restrict__ U,

@@ -801,6 +801,36 @@ phl_status phl_test_tile_wait_timeout(phl_grid *g, int on) {
   return PHL_OK;
 }
 
+phl_status phl_test_prims(phl_grid *g, int form, int increments, float *w_out, long cap, float *rate_out) {
+  if (!g) return fail(PHL_EINVAL, "null grid");
+  if (!w_out) return fail(PHL_EINVAL, "null output");
+  if (form < 0 || form > 3) return fail(PHL_EINVAL, "form must be 0..3");
+  if (!g->mixed || g->G.eos != PHL_EOS_IDEAL)
+    return fail(PHL_EUNSUPPORTED, "primitive forms exist for mixed ideal-gas grids only");
+  if ((form & 1) && !prim_pairs_ok(g->G)) return fail(PHL_EUNSUPPORTED, "the grid does not admit the pair form");
+  const long nw = (long)(g->G.wstr + NAUX) * g->G.wtot;
+  if (cap < nw) return fail(PHL_EINVAL, "output holds fewer floats than W and its auxiliary planes");
+  g->w_valid = false;
+  const bool inc = increments && form < 2;
+  CK(cudaMemsetAsync(g->Wf, 0, nw * sizeof(float), g->stream), "clear W");
+  CK(cudaMemsetAsync(g->fmax + 1, 0, sizeof(unsigned int), g->stream), "clear rate");
+  CK(launch_prims_form(g->G, g->U, g->B, inc ? g->dUf : nullptr, inc ? g->dBf : nullptr, g->Wf, g->dflag, form,
+                       g->fmax + 1, g->stream),
+     "primitives");
+  CK(cudaMemcpyAsync(w_out, g->Wf, nw * sizeof(float), cudaMemcpyDeviceToHost, g->stream), "read W");
+  unsigned int bits = 0;
+  CK(cudaMemcpyAsync(&bits, g->fmax + 1, sizeof(unsigned int), cudaMemcpyDeviceToHost, g->stream), "read rate");
+  CK(cudaStreamSynchronize(g->stream), "sync");
+  if (rate_out) memcpy(rate_out, &bits, sizeof(float));
+  return PHL_OK;
+}
+
+phl_status phl_test_prims_size(phl_grid *g, long *nfloat) {
+  if (!g || !nfloat) return fail(PHL_EINVAL, "null argument");
+  *nfloat = g->mixed ? (long)(g->G.wstr + NAUX) * g->G.wtot : 0;
+  return PHL_OK;
+}
+
 phl_status phl_dt_device_ptr(phl_grid *g, const double **ptr) {
   if (!g || !ptr) return fail(PHL_EINVAL, "null argument");
   *ptr = g->dt;

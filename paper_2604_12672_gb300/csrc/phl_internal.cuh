@@ -319,6 +319,24 @@ struct MixedBufs {
 };
 void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nstages, double b, cudaStream_t s,
                         int *nlaunch, Prof *prof);
+// The mixed-form primitives of the whole work box in one form (phl_test_prims):
+// 0 cell by cell, 1 in pairs of cells, 2 / 3 the same with the CFL rate of
+// U^n into fmax_bits (dU, dB ignored).
+cudaError_t launch_prims_form(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
+                              float *W, int *dflag, int form, unsigned int *fmax_bits, cudaStream_t s);
+// The pair form of the primitives needs: an ideal gas without species (W in
+// two float4 planes), an active x axis of even length and an even number of
+// ghost layers along x, so that the source cells of every pair of work cells
+// (2m - ge, 2m - ge + 1) lie in one aligned pair of state cells (2a, 2a + 1)
+// -- interior pairs are their own sources; periodic ghost pairs map to the
+// pair at the other end, reflecting ones to the mirrored boundary pair,
+// outflow ones to the boundary cell twice -- and rows and planes of the
+// state have even pitches, so every such pair is a 16-byte FP64 load.
+__host__ __device__ inline bool prim_pairs_ok(const DevGeo &G) {
+  return G.wstr == 8 && G.nspec == 0 && G.eos == 0 && G.act[0] && G.n[0] % 2 == 0 && G.ge[0] % 2 == 0 &&
+         G.sy % 2 == 0 && G.sz % 2 == 0 && G.plane % 2 == 0;
+}
+
 void launch_dt_mixed(const DevGeo &G, const double *U, const double *Bf, unsigned int *fmax_bits, double *dt,
                      int *dflag, cudaStream_t s, int *nlaunch, Prof *prof);
 // The step length from the CFL maximum the previous step's last stage folded

@@ -146,33 +146,35 @@ def test_mixed_long_run_c2_physics(P):
         assert worst[k] <= 1e-5, (k, worst[k])
 
 
-@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("bcx", [(0, 0), (1, 1), (2, 2)])
-def test_prim_pairs_equal_single_cells(P, fused, bcx):
-    """Boxes of even n_x form the primitives two cells of a row per thread
-    (FP64 pairs, one shared x-face) except in the first stage of a step with
-    the device CFL step, whose pass over U^n also takes the CFL rate cell by
-    cell.  A step with the device CFL step and a step with a fixed dt equal to
-    it (compute_dt gives the same rate and reduction) therefore differ only
-    in which form built the first stage's W: the results must be
-    bit-identical, with x-ghost pairs of every boundary kind."""
+def test_prim_pairs_equal_single_cells(P, bcx):
+    """Boxes of even n_x form the primitive deviations two cells of a row per
+    thread from aligned FP64 pairs.  The pair form and the cell-by-cell form
+    must give bit-identical W and auxiliary planes over the whole work box
+    (interior cells and the ghost images of every boundary kind along x,
+    mirrored along z), with and without the stage increments, and the same
+    CFL rate in the first-stage forms."""
     pr = W.stratified_box(24, 14, 18, amp=3e-2, beta=1e3, mach_heat=3e-2)
     pr.bc = (bcx, (0, 0), (1, 1))
-    out = []
-    for fixed in (False, True):
-        g = P.Grid(pr, precision="mixed")
-        g.set_fused(fused)
-        g.load()
-        if fixed:
-            dt = g.compute_dt()
-            g.step(1, dt)
-        else:
-            g.step(1)
-        out.append(g.get_state())
-        g.close()
-    for k in ("cons", "bx", "by", "bz"):
-        assert np.array_equal(out[0][k], out[1][k]), k
-    assert not np.array_equal(out[0]["cons"], pr.cons)
+    g = P.Grid(pr, precision="mixed")
+    g.load()
+    g.step(1)   # leaves nonzero stage increments behind
+    for inc in (False, True):
+        a, _ = g.test_prims(0, inc)
+        b, _ = g.test_prims(1, inc)
+        assert np.count_nonzero(a) > a.size // 4
+        assert np.array_equal(a, b), inc
+    a, ra = g.test_prims(2)
+    b, rb = g.test_prims(3)
+    c, _ = g.test_prims(0, False)
+    assert ra > 0 and ra == rb
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    g.close()
+    odd = W.stratified_box(23, 14, 18, amp=3e-2)
+    h = P.Grid(odd, precision="mixed")
+    with pytest.raises(P.PhlError):
+        h.test_prims(1)
+    h.close()
 
 
 def test_mixed_orszag_tang_close_to_oracle(P):
