@@ -313,6 +313,19 @@ phl_status phl_test_prims(phl_grid *g, int form, int increments, float *w_out, l
 /* The number of floats phl_test_prims writes (0 for an FP64 grid). */
 phl_status phl_test_prims_size(phl_grid *g, long *nfloat);
 
+/* Test of the two forms of the raw shock flags (Sect. 2.7: sum over the axes
+ * of |P_(i+1) - P_(i-1)| against eps_sf P_i) of a mixed grid, from the W that
+ * the last phl_test_prims formed.
+ *   form     0: one cell per thread; 1: four cells of a row per thread (n_x a
+ *            multiple of 4)
+ *   out      host, cap bytes; receives nx*ny*nz flags (0 / 1), x fastest
+ *   any_out  host, optional: the kernel's vote, 1 if some cell is flagged
+ * The grid's flag buffers are clobbered (the next phl_step forms them again).
+ * Synchronous on the grid's stream.  PHL_EUNSUPPORTED for an FP64 grid or
+ * form 1 on a grid without the four-cell form; PHL_EINVAL for a bad form or a
+ * short buffer. */
+phl_status phl_test_raw_flags(phl_grid *g, int form, unsigned char *out, long cap, int *any_out);
+
 /* Device pointer of the last computed dt (double), valid for the grid's
  * lifetime; lets callers enqueue reads without a synchronisation. */
 phl_status phl_dt_device_ptr(phl_grid *g, const double **ptr);

@@ -104,6 +104,7 @@ _SIGS = {
     "phl_test_tile_wait_timeout": (C.c_int, [C.c_void_p, C.c_int]),
     "phl_test_prims": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_long, C.POINTER(C.c_float)]),
     "phl_test_prims_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_long)]),
+    "phl_test_raw_flags": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.POINTER(C.c_int)]),
     "phl_convert_batch": (C.c_int, [C.c_long, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "phl_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int]),
     "phl_destroy": (None, [C.c_void_p]),
@@ -618,6 +619,15 @@ class Grid:
         _check(lib().phl_test_prims(self.h, int(form), int(bool(increments)), out.ctypes.data, n.value,
                                     C.byref(rate)))
         return out, rate.value
+
+    def test_raw_flags(self, form):
+        """Raw shock flags of the W the last test_prims formed, in one form
+        (phl_test_raw_flags): returns (flags as uint8 (nz, ny, nx), the vote)."""
+        nx, ny, nz = self.pr.n
+        out = np.zeros((nz, ny, nx), dtype=np.uint8)
+        anyf = C.c_int(0)
+        _check(lib().phl_test_raw_flags(self.h, int(form), out.ctypes.data, out.size, C.byref(anyf)))
+        return out, anyf.value
 
     def set_fused(self, on=1):
         """Mixed-precision stage decomposition (phl_set_fused): 0/False = one

@@ -825,6 +825,27 @@ phl_status phl_test_prims(phl_grid *g, int form, int increments, float *w_out, l
   return PHL_OK;
 }
 
+phl_status phl_test_raw_flags(phl_grid *g, int form, unsigned char *out, long cap, int *any_out) {
+  if (!g) return fail(PHL_EINVAL, "null grid");
+  if (!out) return fail(PHL_EINVAL, "null output");
+  if (form < 0 || form > 1) return fail(PHL_EINVAL, "form must be 0 or 1");
+  if (!g->mixed) return fail(PHL_EUNSUPPORTED, "raw-flag forms exist for mixed grids only");
+  if (form == 1 && !(g->G.act[0] && g->G.n[0] % 4 == 0))
+    return fail(PHL_EUNSUPPORTED, "the four-cell form needs n_x a multiple of 4");
+  const long nc = (long)g->G.n[0] * g->G.n[1] * g->G.n[2];
+  if (cap < nc) return fail(PHL_EINVAL, "output holds fewer bytes than cells");
+  g->w_valid = false;
+  CK(cudaMemsetAsync(g->raw, 0, nc, g->stream), "clear flags");
+  CK(cudaMemsetAsync(g->anyraw, 0, sizeof(unsigned int), g->stream), "clear vote");
+  CK(launch_raw_flags_form(g->G, g->Wf, g->raw, form, g->anyraw, g->stream), "raw flags");
+  CK(cudaMemcpyAsync(out, g->raw, nc, cudaMemcpyDeviceToHost, g->stream), "read flags");
+  unsigned int any = 0;
+  CK(cudaMemcpyAsync(&any, g->anyraw, sizeof(unsigned int), cudaMemcpyDeviceToHost, g->stream), "read vote");
+  CK(cudaStreamSynchronize(g->stream), "sync");
+  if (any_out) *any_out = (int)any;
+  return PHL_OK;
+}
+
 phl_status phl_test_prims_size(phl_grid *g, long *nfloat) {
   if (!g || !nfloat) return fail(PHL_EINVAL, "null argument");
   *nfloat = g->mixed ? (long)(g->G.wstr + NAUX) * g->G.wtot : 0;

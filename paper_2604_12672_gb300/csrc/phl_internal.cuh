@@ -324,6 +324,11 @@ void launch_stage_mixed(const DevGeo &G, const MixedBufs &M, int stage, int nsta
 // U^n into fmax_bits (dU, dB ignored).
 cudaError_t launch_prims_form(const DevGeo &G, const double *U, const double *Bf, const float *dU, const float *dB,
                               float *W, int *dflag, int form, unsigned int *fmax_bits, cudaStream_t s);
+// Raw shock flags of the interior from W (phl_test_raw_flags): form 0 one
+// cell per thread, 1 four cells of a row per thread; any: the flag vote.
+cudaError_t launch_raw_flags_form(const DevGeo &G, const float *W, uint8_t *raw, int form, unsigned int *any,
+                                  cudaStream_t s);
+
 // The pair form of the primitives needs: an ideal gas without species (W in
 // two float4 planes), an active x axis of even length and an even number of
 // ghost layers along x, so that the source cells of every pair of work cells

@@ -165,6 +165,50 @@ __global__ void k_flag_raw(DevGeo G, Box box, const R *__restrict__ W, uint8_t *
   if (any && __any_sync(0xffffffffu, f) && (threadIdx.x & 31) == 0) atomicOr(any, 1u);
 }
 
+// The raw flags of four cells of a row per thread (x0 = 4m .. 4m + 3; the
+// mixed form with n_x a multiple of 4): each cell's test with the operations
+// of k_flag_raw_at (bit-identical flags), the x-neighbours' pressures shared
+// between the four, the background read once, one 4-byte store.  box: the
+// interior with its x extent divided by 4.  any: as k_flag_raw.
+__global__ void __launch_bounds__(256) k_flag_raw4(DevGeo G, Box box, const float *__restrict__ W,
+                                                   uint8_t *__restrict__ raw, unsigned int *any) {
+  int c[3];
+  unsigned fw = 0u;
+  if (cell_at(box, blockIdx.x * (long)blockDim.x + threadIdx.x, c)) {
+    c[0] *= 4;
+    const float *P = W + waux(G, AUX_P, 0);
+    const long q = widx(G, c[0], c[1], c[2]);
+    const float b0 = bg_cell_t<float>(G, c[2]).p;
+    float px[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) px[i] = P[q - 1 + i] + b0;
+    float sy[4], sz[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { sy[i] = 0.0f; sz[i] = 0.0f; }
+    if (G.act[1]) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) sy[i] = fabsf((P[q + i + G.wy] + b0) - (P[q + i - G.wy] + b0));
+    }
+    if (G.act[2]) {
+      const float bp = bg_cell_t<float>(G, c[2] + 1).p, bm = bg_cell_t<float>(G, c[2] - 1).p;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) sz[i] = fabsf((P[q + i + G.wz] + bp) - (P[q + i - G.wz] + bm));
+    }
+    const float e = eps_sf_t<float>(G);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float sum = 0.0f;
+      sum += fabsf(px[i + 2] - px[i]);   // x is active on this path
+      if (G.act[1]) sum += sy[i];
+      if (G.act[2]) sum += sz[i];
+      if (sum / (e * px[i + 1]) > 1.0f) fw |= 1u << (8 * i);
+    }
+    *reinterpret_cast<unsigned *>(raw + c[0] + (long)G.n[0] * (c[1] + (long)G.n[1] * c[2])) = fw;
+  }
+  if (any && __any_sync(0xffffffffu, fw != 0u) && (threadIdx.x & 31) == 0) atomicOr(any, 1u);
+}
+__host__ __device__ inline bool flag_raw4_ok(const DevGeo &G) { return G.act[0] && G.n[0] % 4 == 0; }
+
 // 5^d dilation of the raw shock flags (Sect. 2.7), done as one 5-wide OR per
 // active axis: OR over a box equals the nested ORs over its axes.  Neighbours
 // beyond a periodic boundary wrap, beyond any other boundary are skipped.

@@ -1243,6 +1243,18 @@ int make_fused_tmap(const DevGeo &G, const float *W, void *tmap128) {
 // Faces, EMFs and updates of one mixed stage on the fused path (prim and
 // flags already done): k_flux_update_mx, three EMF launches, three face
 // updates.
+cudaError_t launch_raw_flags_form(const DevGeo &G, const float *W, uint8_t *raw, int form, unsigned int *any,
+                                  cudaStream_t s) {
+  if (form == 1) {
+    Box b4 = make_box(0, G.n[0] / 4, 0, G.n[1], 0, G.n[2]);
+    k_flag_raw4<<<grid3(b4), block3(b4), 0, s>>>(G, b4, W, raw, any);
+  } else {
+    Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
+    k_flag_raw<float><<<grid3(bi), block3(bi), 0, s>>>(G, bi, W, raw, any);
+  }
+  return cudaGetLastError();
+}
+
 void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool last, double b, cudaStream_t s,
                        int *nl, Prof *prof) {
   StageMx S;
@@ -1261,8 +1273,13 @@ void launch_fused_tail(const DevGeo &G, const MixedBufs &M, bool first, bool las
   } else if (G.eps_sf > 0.0) {   // raw flags, then their 5^3 dilation, both on the interior layout
     Box bi = make_box(0, G.n[0], 0, G.n[1], 0, G.n[2]);
     if (M.anyraw) cudaMemsetAsync(M.anyraw, 0, sizeof(unsigned int), s);
-    PHL_LAUNCH(KC_FLAG_RAW, prof, s,
-               k_flag_raw<float><<<grid3(bi), block3(bi), 0, s>>>(G, bi, M.W, M.raw, M.anyraw));
+    if (flag_raw4_ok(G)) {   // four cells of a row per thread
+      Box b4 = make_box(0, G.n[0] / 4, 0, G.n[1], 0, G.n[2]);
+      PHL_LAUNCH(KC_FLAG_RAW, prof, s, k_flag_raw4<<<grid3(b4), block3(b4), 0, s>>>(G, b4, M.W, M.raw, M.anyraw));
+    } else {
+      PHL_LAUNCH(KC_FLAG_RAW, prof, s,
+                 k_flag_raw<float><<<grid3(bi), block3(bi), 0, s>>>(G, bi, M.W, M.raw, M.anyraw));
+    }
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

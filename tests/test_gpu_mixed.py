@@ -177,6 +177,34 @@ def test_prim_pairs_equal_single_cells(P, bcx):
     h.close()
 
 
+@pytest.mark.parametrize("bcx", [(0, 0), (1, 1), (2, 2)])
+@pytest.mark.parametrize("eps", [0.5, 5.0])
+def test_raw_flags_four_cells_equal_single_cells(P, bcx, eps):
+    """Boxes with n_x a multiple of 4 take the raw shock flags four cells of a
+    row per thread; the flags and the vote must equal the cell-by-cell
+    kernel's bit for bit -- with flagged cells next to unflagged ones (on
+    16 cells the stratification alone gives 0.25 at the bottom and 1.1 at
+    the top; a slab of raised pressure adds jumps) and with none (a
+    threshold above every cell's jump)."""
+    pr = W.stratified_box(24, 12, 16, amp=3e-2, beta=1e3, mach_heat=3e-2)
+    pr.bc = (bcx, (0, 0), (1, 1))
+    pr.eps_sf = eps
+    if eps < 1.0:   # a pressure jump across a slab: flagged cells next to unflagged ones
+        pr.cons[4, :, :, 9:14] *= 1.5
+    g = P.Grid(pr, precision="mixed")
+    g.load()
+    g.test_prims(0, False)
+    a, va = g.test_raw_flags(0)
+    b, vb = g.test_raw_flags(1)
+    assert np.array_equal(a, b)
+    assert va == vb == int(a.any())
+    if eps < 1.0:
+        assert 0 < a.sum() < a.size
+    else:
+        assert a.sum() == 0
+    g.close()
+
+
 def test_mixed_orszag_tang_close_to_oracle(P):
     pr = W.orszag_tang(64)
     g = P.Grid(pr, precision="mixed")
