@@ -936,13 +936,36 @@ __device__ __forceinline__ void face_update(const DevGeo &G, const int *c, const
   else S.dB[q] = dout;
 }
 
+// face_update with 32-bit offsets: on the fused path every W-layout array
+// (E: three planes) and every state array (B, dB: three planes) is below 2^31
+// elements.  p: the site's work index, ps: its state index.
+template <int D>
+__device__ __forceinline__ void face_update32(const DevGeo &G, unsigned p, unsigned ps, const StageMx &S, float dt) {
+  constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+  const unsigned wt = (unsigned)G.wtot;
+  const unsigned sA = A == 0 ? 1u : (A == 1 ? (unsigned)G.wy : (unsigned)G.wz);
+  const unsigned sB = B == 0 ? 1u : (B == 1 ? (unsigned)G.wy : (unsigned)G.wz);
+  const float *EB = S.E + B * wt, *EA = S.E + A * wt;
+  float r = 0.0f;
+  r += (EB[p + sA] - EB[p]) * G.idxf[A];
+  r -= (EA[p + sB] - EA[p]) * G.idxf[B];
+  const unsigned q = D * (unsigned)G.plane + ps;
+  const float din = S.first ? 0.0f : S.dB[q];
+  const float dout = S.b * (din - dt * r);
+  if (S.last) S.B[q] += f2d_scaled(dout, G.e_b);
+  else S.dB[q] = dout;
+}
+
 __global__ void k_update_faces3(DevGeo G, Box box, StageMx S) {
   int c[3];
   if (!cell3(box, c)) return;
   const float dt = d2f_scaled(*S.dt, -G.e_t);
-  if (c[1] < G.n[1] && c[2] < G.n[2]) face_update<0>(G, c, S, dt);
-  if (c[0] < G.n[0] && c[2] < G.n[2]) face_update<1>(G, c, S, dt);
-  if (c[0] < G.n[0] && c[1] < G.n[1]) face_update<2>(G, c, S, dt);
+  const unsigned p = (unsigned)(c[0] + G.ge[0]) + (unsigned)G.wy * (unsigned)(c[1] + G.ge[1]) +
+                     (unsigned)G.wz * (unsigned)(c[2] + G.ge[2]);
+  const unsigned ps = (unsigned)c[0] + (unsigned)G.sy * (unsigned)c[1] + (unsigned)G.sz * (unsigned)c[2];
+  if (c[1] < G.n[1] && c[2] < G.n[2]) face_update32<0>(G, p, ps, S, dt);
+  if (c[0] < G.n[0] && c[2] < G.n[2]) face_update32<1>(G, p, ps, S, dt);
+  if (c[0] < G.n[0] && c[1] < G.n[1]) face_update32<2>(G, p, ps, S, dt);
 }
 
 // ---------------------------------------------------------------------------
