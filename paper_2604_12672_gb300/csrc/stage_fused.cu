@@ -576,15 +576,35 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap *tmW, const DevGeo &
     }
   }
 
-  // R = sum_d (F_d(+) - F_d(-)) / dx_d - (S - S_hat), then the RK increment
+  // R = sum_d (F_d(+) - F_d(-)) / dx_d - (S - S_hat), then the RK increment.
+  // The cells' increments (and, in the last stage, their FP64 state) are
+  // read before anything is stored: a read of dU or U after a store to the
+  // same array cannot move above it, so interleaving them would leave one
+  // memory round trip per value at the end of every tile.
   const float dt = d2f_scaled(*S.dt, -G.e_t);
+  int psc[CPT];
+  float din[CPT][5];
+  double uin[CPT][5];
 #pragma unroll
   for (int m = 0; m < CPT; ++m) {
     const int cc = tid + m * NT;
-    if (cc >= NC) continue;
     const int i = cc % FX, j = (cc / FX) % FY, k = cc / (FX * FY);
     const int c0 = x0 + i, c1 = y0 + j, c2 = z0 + k;
-    if (c0 >= G.n[0] || c1 >= G.n[1] || c2 >= G.n[2]) continue;
+    const bool ok = cc < NC && c0 < G.n[0] && c1 < G.n[1] && c2 < G.n[2];
+    psc[m] = ok ? c0 + (int)G.sy * c1 + (int)G.sz * c2 : -1;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const int q = v * (int)G.plane + psc[m];
+      din[m][v] = (ok && !S.first) ? S.dU[q] : 0.0f;
+      uin[m][v] = (ok && S.last) ? S.U[q] : 0.0;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < CPT; ++m) {
+    if (psc[m] < 0) continue;
+    const int cc = tid + m * NT;
+    const int i = cc % FX, j = (cc / FX) % FY, k = cc / (FX * FY);
+    const int c2 = z0 + k;
     float *r = racc[m];
     // sources S - S_hat: (rho - rho_hat) g on momentum, rho u . g (+ heating) on energy
     const float4 wa = sm.w[0][((k + NGW) * HY + (j + NGW)) * HX + (i + NGW)];
@@ -600,13 +620,11 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap *tmW, const DevGeo &
     }
     if (G.heatf) se += G.heatf[c2];
     r[U_E] -= se;
-    const int ps = c0 + (int)G.sy * c1 + (int)G.sz * c2;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const int q = v * (int)G.plane + ps;
-      const float din = S.first ? 0.0f : S.dU[q];
-      const float dout = S.b * (din - dt * r[v]);
-      if (S.last) S.U[q] += f2d_scaled(dout, uexp(G, v));
+      const int q = v * (int)G.plane + psc[m];
+      const float dout = S.b * (din[m][v] - dt * r[v]);
+      if (S.last) S.U[q] = uin[m][v] + f2d_scaled(dout, uexp(G, v));
       else S.dU[q] = dout;
     }
   }
