@@ -68,10 +68,11 @@ FP32_NOMINAL_TFLOPS = 80.5
 # an 8^3 tile evaluates; the algorithmic count is 3 faces per cell x 414 =
 # 1243.  The default shape evaluates the same operations, partly as packed
 # FP32x2 instructions that those per-opcode counters do not include.  DRAM
-# bytes per cell of the current default shape: 111.6 (stage 1, no increment
-# to read) and 144.4 (stages 2-3), 133.5 on average over an RK3 step.
+# bytes per cell of the current default shape: 111.8 (stage 1, no increment
+# to read), 144.6 (stage 2) and 205.3 (stage 3, which also reads and writes
+# the FP64 state), 153.9 on average over an RK3 step.
 FUSED_FLOP_PER_CELL = 3.0 * 414.3
-FUSED_DRAM_BYTES_PER_CELL = (111.6 + 2.0 * 144.4) / 3.0
+FUSED_DRAM_BYTES_PER_CELL = (111.8 + 144.6 + 205.3) / 3.0
 
 
 def read_peaks():
