@@ -101,6 +101,9 @@ def test_calls_on_a_null_grid_are_rejected(P):
         "phl_check": lambda: L.phl_check(None),
         "phl_set_fused": lambda: L.phl_set_fused(None, 1),
         "phl_diffuse": lambda: L.phl_diffuse(None, C.byref(diff), 0.1, 100, C.byref(n)),
+        "phl_test_prims": lambda: L.phl_test_prims(None, 0, 0, p, 8, None),
+        "phl_test_prims_size": lambda: L.phl_test_prims_size(None, C.byref(C.c_long())),
+        "phl_test_raw_flags": lambda: L.phl_test_raw_flags(None, 0, p, 8, None),
     }
     for name, call in calls.items():
         st, msg = status_and_message(P, call())
