@@ -116,8 +116,17 @@ __device__ __forceinline__ void fused_face(const DevGeo &G, const StageMx &S, co
         ql[v] = pphL ? pph_right(w0, w1, w2) : w1 + 0.5f * vl_slope(w0, w1, w2);
         qr[v] = pphR ? pph_left(w1, w2, w3) : w2 - 0.5f * vl_slope(w1, w2, w3);
       } else {
-        ql[v] = w1 + 0.5f * vl_slope(w0, w1, w2);
-        qr[v] = w2 - 0.5f * vl_slope(w1, w2, w3);
+        // the two van Leer slopes (cell i for the left state, cell i+1 for
+        // the right) as one FP32x2 pair: differences, products, sums and the
+        // face values packed; the quotient 2 dm dp / (dm + dp) per lane by
+        // the fast division (its denominators are O(1) in scaled units)
+        const x2::V dm = x2::vv(w1, w2) - x2::vv(w0, w1), dp = x2::vv(w2, w3) - x2::vv(w1, w2);
+        const x2::V pr = dm * dp, den = dm + dp;
+        const x2::V sl = x2::vv(pr.x > 0.0f ? __fdividef(pr.x + pr.x, den.x) : 0.0f,
+                                pr.y > 0.0f ? __fdividef(pr.y + pr.y, den.y) : 0.0f);
+        const x2::V q = x2::fma(x2::vv(0.5f, -0.5f), sl, x2::vv(w1, w2));
+        ql[v] = q.x;
+        qr[v] = q.y;
       }
     };
     plm(W_RHO, a[0].x, a[1].x, a[2].x, a[3].x);
