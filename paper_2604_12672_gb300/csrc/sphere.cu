@@ -827,10 +827,12 @@ __device__ __forceinline__ void load_w(const SphDev &D, const SphWork<R> &Wk, lo
   }
 }
 
+// (FP32: the fast division, the deviations being O(1) in scaled units)
 template <typename R>
 __device__ __forceinline__ R vl_t(R a, R b, R c) {
   const R dm = b - a, dp = c - b;
-  return dm * dp > R(0) ? R(2) * dm * dp / (dm + dp) : R(0);
+  if constexpr (sizeof(R) == 4) return dm * dp > R(0) ? __fdividef(R(2) * dm * dp, dm + dp) : R(0);
+  else return dm * dp > R(0) ? R(2) * dm * dp / (dm + dp) : R(0);
 }
 
 // Per-face flux of either form.  MX: the mixed form's FP32 tables and face

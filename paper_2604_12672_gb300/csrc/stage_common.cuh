@@ -70,11 +70,15 @@ inline int nblocks(long n) {
   return (int)b;
 }
 
-// van Leer harmonic limited slope (Sect. 2.5, item i)
+// van Leer harmonic limited slope (Sect. 2.5, item i).  In FP32 (the mixed
+// form, O(1) deviations in scaled units) the quotient takes the fast
+// division, as the tile kernel's paired slopes do, so a cell reconstructs
+// the same way on every path.
 template <typename R>
 __device__ __forceinline__ R vl_slope(R a, R b, R c) {
   const R dm = b - a, dp = c - b;
-  return (dm * dp > R(0)) ? R(2) * dm * dp / (dm + dp) : R(0);
+  if constexpr (sizeof(R) == 4) return (dm * dp > R(0)) ? __fdividef(R(2) * dm * dp, dm + dp) : R(0);
+  else return (dm * dp > R(0)) ? R(2) * dm * dp / (dm + dp) : R(0);
 }
 
 // PPH (Sect. 2.5, item ii): the parabola whose averages over cells i-1, i,
